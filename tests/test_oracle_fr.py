@@ -1,0 +1,120 @@
+"""Pins of the oracle's f(R) scalaron solver (CPU)."""
+import numpy as np
+import pytest
+
+from oracle import fr, mesh, poisson
+from oracle.cosmology import c_tilde
+
+
+def test_cubic_root_all_branches_vs_numpy_roots():
+    rng = np.random.default_rng(0)
+    p = np.concatenate([[0.0], rng.uniform(0.01, 3, 50), rng.uniform(-3, -0.01, 200), rng.uniform(-1e-4, 1e-4, 20)])
+    q = -rng.uniform(1e-6, 2.0, p.size)
+    u = fr.depressed_cubic_root(p, q)
+    d0, d1 = -3 * p, 27 * q
+    disc = d1 ** 2 - 4 * d0 ** 3
+    assert np.any((p < 0) & (disc > 0)) and np.any((p < 0) & (disc <= 0)) and np.any(p > 0)
+    for pi, qi, ui in zip(p, q, u):
+        r = np.roots([1.0, 0.0, pi, qi])
+        pos = r[(np.abs(r.imag) < 1e-9) & (r.real > 0)].real
+        assert pos.size == 1
+        assert ui == pytest.approx(pos[0], rel=1e-9, abs=1e-12)
+
+
+def test_cubic_root_vs_bisection_operating_range():
+    """The f(R) regime: p close to -1, small negative q."""
+    rng = np.random.default_rng(1)
+    p = -1.0 + rng.uniform(-0.05, 0.05, 100)
+    q = -rng.uniform(1e-4, 1e-2, 100)
+    u = fr.depressed_cubic_root(p, q)
+    lo, hi = np.zeros_like(p), np.full_like(p, 10.0)
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        neg = mid ** 3 + p * mid + q < 0
+        lo = np.where(neg, mid, lo)
+        hi = np.where(neg, hi, mid)
+    assert np.abs(u - 0.5 * (lo + hi)).max() < 1e-13
+
+
+def test_q_negative(golden):
+    for a in (0.05, 0.3, 1.0):
+        fbar, kappa, _ = fr.background(a, fr.FRModel())
+        assert fbar < 0 and (1.0 / 64) ** 2 * kappa / (6 * fbar) < 0
+
+
+def test_background_today_is_fR0():
+    m = fr.FRModel(fR0=-3e-6)
+    fbar, _, _ = fr.background(1.0, m)
+    assert fbar == pytest.approx(-3e-6, rel=1e-15)
+
+
+def test_uniform_density_fixed_point():
+    n = 8
+    m = fr.FRModel(boxsize=8.0)
+    fbar, kappa, _ = fr.background(0.5, m)
+    u = np.ones((n, n, n))
+    assert np.abs(fr.operator(u, 1.0 / n, fbar, kappa)).max() == 0.0
+    fr.gs_sweep(u, np.zeros_like(u), 1.0 / n, fbar, kappa)
+    assert np.abs(u - 1.0).max() < 1e-13
+
+
+def _yukawa_prediction(delta, a, model, n):
+    """Linearised field equation: (lambda_k - mu^2) df_k = -(Om a / c~^2) delta_k,
+    mu^2 = a^4 R~ / (6 c~^2 |fbar|), lambda_k the 7-point Laplacian symbol."""
+    h = 1.0 / n
+    Rbar = 3 * model.Om * (a ** -3 + 4 * model.OL / model.Om)
+    Rbar0 = 3 * model.Om * (1 + 4 * model.OL / model.Om)
+    fbar = a * a * model.fR0 * (Rbar0 / Rbar) ** 2
+    c2 = c_tilde(model.boxsize) ** 2
+    mu2 = a ** 4 * Rbar / (6 * c2 * abs(fbar))
+    m = np.fft.fftfreq(n) * n
+    mz = np.fft.rfftfreq(n) * n
+    lam = -(4 / h ** 2) * (np.sin(np.pi * m / n)[:, None, None] ** 2 + np.sin(np.pi * m / n)[None, :, None] ** 2
+                            + np.sin(np.pi * mz / n)[None, None, :] ** 2)
+    dk = np.fft.rfftn(delta)
+    dfk = -(model.Om * a / c2) * dk / (lam - mu2)
+    return np.fft.irfftn(dfk, s=delta.shape, axes=(0, 1, 2)), fbar, mu2
+
+
+def test_linear_regime_matches_yukawa_closed_form():
+    n = 16
+    a = 0.6
+    model = fr.FRModel(boxsize=16.0)
+    i = np.arange(n)
+    delta = 1e-4 * (np.cos(2 * np.pi * 2 * i / n)[:, None, None] + np.sin(2 * np.pi * 5 * i / n)[None, None, :])
+    delta = np.broadcast_to(delta, (n, n, n)).copy()
+    rho = 1.0 + delta
+    u, hist = fr.fr_solve(rho, a, model, prm=fr.FASParams(coarsest=4), tol=1e-11)
+    df_pred, fbar, mu2 = _yukawa_prediction(delta, a, model, n)
+    df = fbar * (u * u - 1.0)
+    assert np.abs(df - df_pred).max() < 2e-3 * np.abs(df_pred).max()
+
+
+def test_force_enhancement_limits():
+    """Fifth force: the combined potential phi - (c~^2/2) f~_R is 4/3 of the
+    Newtonian one for k^2 >> mu^2 and equal to it for k^2 << mu^2 (§2.x / §3.10)."""
+    n = 16
+    i = np.arange(n)
+    for boxsize, m, lo, hi in ((1.0, 1, 1.30, 1.34), (1000.0, 1, 1.0, 1.02)):
+        model = fr.FRModel(boxsize=boxsize)
+        a = 1.0
+        delta = np.broadcast_to(1e-5 * np.cos(2 * np.pi * m * i / n)[:, None, None], (n, n, n)).copy()
+        u, _ = fr.fr_solve(1.0 + delta, a, model, prm=fr.FASParams(coarsest=4), tol=1e-9)
+        phiN = poisson.solve_fft7(1.5 * a * model.Om * delta, 1.0 / n)
+        Phi = phiN + fr.scalaron_potential(u, a, model)
+        gN = mesh.force_from_potential(phiN, 1.0 / n)[0]
+        g = mesh.force_from_potential(Phi, 1.0 / n)[0]
+        ratio = np.abs(g).max() / np.abs(gN).max()
+        assert lo < ratio < hi, (boxsize, ratio)
+
+
+def test_fas_f_cycle_rate(golden):
+    n = 32
+    model = fr.FRModel(boxsize=32.0)
+    rng = np.random.default_rng(1)
+    rho = np.exp(0.8 * rng.standard_normal((n, n, n)))
+    rho /= rho.mean()
+    u, hist = fr.fr_solve(rho, 0.5, model, prm=fr.FASParams(coarsest=4), cycles=3)
+    rate = (hist[0] / hist[-1]) ** (1 / 3)
+    assert rate > golden["multigrid_convergence"]["f_cycle"] / 2
+    assert u.min() > 0

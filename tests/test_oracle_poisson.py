@@ -1,0 +1,108 @@
+"""Pins of the oracle's Poisson solvers (CPU)."""
+import itertools
+
+import numpy as np
+import pytest
+
+from oracle import mesh, poisson
+
+
+def test_fft7_sine_plane_wave_closed_form():
+    n = 16
+    h = 1.0 / n
+    i = np.arange(n)
+    m = (2, 0, 3)
+    f = np.sin(2 * np.pi * (m[0] * i[:, None, None] + m[2] * i[None, None, :]) / n) * np.ones((1, n, 1))
+    lam = -(4.0 / h ** 2) * sum(np.sin(np.pi * mm / n) ** 2 for mm in m)
+    assert np.abs(poisson.solve_fft7(f, h) - f / lam).max() < 1e-14 * np.abs(f / lam).max() * 10
+
+
+def test_fft7_equals_dense_direct_solve_8cubed():
+    """Dense 512 x 512 system assembled cell by cell from the 7-point stencil,
+    solved with the zero-mean constraint by least squares."""
+    n = 8
+    h = 1.0 / n
+    N = n ** 3
+    A = np.zeros((N, N))
+    idx = lambda i, j, k: ((i % n) * n + (j % n)) * n + (k % n)
+    for i, j, k in itertools.product(range(n), repeat=3):
+        r = idx(i, j, k)
+        A[r, r] -= 6.0 / h ** 2
+        for d in ((1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0), (0, 0, 1), (0, 0, -1)):
+            A[r, idx(i + d[0], j + d[1], k + d[2])] += 1.0 / h ** 2
+    f = np.random.default_rng(0).standard_normal(N)
+    f -= f.mean()
+    Ac = np.vstack([A, np.ones((1, N))])
+    u = np.linalg.lstsq(Ac, np.append(f, 0.0), rcond=None)[0]
+    phi = poisson.solve_fft7(f.reshape(n, n, n), h).ravel()
+    assert np.abs(u - phi).max() < 1e-12 * np.abs(phi).max()
+
+
+def test_restrict_and_prolong_basic(golden):
+    rng = np.random.default_rng(1)
+    d = rng.standard_normal((8, 8, 8))
+    assert poisson.restrict(d).mean() == pytest.approx(d.mean(), abs=1e-15)
+    w = golden["prolongation_weights"]["by_near_axes"]
+    assert [poisson.PROLONG_WEIGHT_BY_NEAR_AXES[k] for k in range(4)] == [w[str(k)] for k in range(4)]
+    # weights of one fine cell sum to one: 27 + 3*9 + 3*3 + 1 = 64
+    assert poisson.prolong(np.ones((4, 4, 4))) == pytest.approx(np.ones((8, 8, 8)), abs=1e-15)
+    # a single coarse spike spreads exactly the printed weights to its children's neighbourhood
+    vH = np.zeros((4, 4, 4))
+    vH[1, 1, 1] = 1.0
+    P = poisson.prolong(vH)
+    assert P[2, 2, 2] == pytest.approx(27 / 64)     # child, all three axes near
+    assert P[1, 2, 2] == pytest.approx(9 / 64)      # one axis far
+    assert P[1, 1, 2] == pytest.approx(3 / 64)
+    assert P[1, 1, 1] == pytest.approx(1 / 64)
+    assert P[0, 2, 2] == 0.0                         # beyond 1.5 fine cells
+
+
+def test_prolong_reproduces_linear_fields_in_interior():
+    nH = 8
+    I = np.arange(nH) + 0.5                          # coarse centres in coarse units
+    vH = np.broadcast_to(3.0 * I[:, None, None] - 2.0 * I[None, None, :], (nH, nH, nH))
+    P = poisson.prolong(np.ascontiguousarray(vH))
+    i = (np.arange(2 * nH) + 0.5) / 2.0              # fine centres in coarse units
+    exact = 3.0 * i[:, None, None] - 2.0 * i[None, None, :]
+    sl = slice(2, 2 * nH - 2)
+    assert np.abs(P[sl, :, sl] - np.broadcast_to(exact, P.shape)[sl, :, sl]).max() < 1e-12
+
+
+def test_jacobi_first_guess(golden):
+    f = np.random.default_rng(2).standard_normal((4, 4, 4))
+    h = 0.25
+    assert poisson.jacobi_first_guess(f, h) == pytest.approx(golden["jacobi_first_guess_factor"]["value"] * h * h * f)
+
+
+def test_multigrid_converges_to_fft7():
+    n = 32
+    h = 1.0 / n
+    f = np.random.default_rng(3).standard_normal((n, n, n))
+    prm = poisson.MGParams(coarsest=4, tol=1e-12)
+    u, hist = poisson.mg_solve(f, h, prm=prm)
+    phi = poisson.solve_fft7(f, h)
+    assert hist[-1] <= 1e-12 * np.linalg.norm(f - f.mean())
+    assert np.abs((u - u.mean()) - phi).max() < 1e-10 * np.abs(phi).max()
+
+
+@pytest.mark.parametrize("omega,key", [(1.0, "v_no_sor"), (1.25, "v_sor_1p25")])
+def test_multigrid_convergence_rate(golden, omega, key):
+    """Appendix C: a V-cycle cuts the residual by ~10x without SOR and 20-30x
+    with omega = 1.25 (soft: within a factor 2 of the printed rate)."""
+    n = 32
+    h = 1.0 / n
+    f = np.random.default_rng(4).standard_normal((n, n, n))
+    prm = poisson.MGParams(coarsest=4, omega=omega)
+    _, hist = poisson.mg_solve(f, h, prm=prm, cycles=5)
+    rate = (hist[1] / hist[-1]) ** (1.0 / 4)
+    assert rate > golden["multigrid_convergence"][key] / 2
+
+
+def test_truncation_error_of_smooth_field_is_second_order():
+    errs = []
+    for n in (16, 32):
+        h = 1.0 / n
+        x = (np.arange(n) + 0.5) * h
+        u = np.broadcast_to(np.sin(2 * np.pi * x)[:, None, None], (n, n, n)).copy()
+        errs.append(np.abs(poisson.truncation_error(u, mesh.laplacian7(u, h), h)).max())
+    assert np.log2(errs[0] / errs[1]) == pytest.approx(2.0, abs=0.15)

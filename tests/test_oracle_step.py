@@ -1,0 +1,91 @@
+"""Pins of the oracle's force evaluation, integrator, cosmology and P(k) (CPU)."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import cosmology, mesh, power, step
+
+
+def test_dt_eds_closed_form():
+    a0, a1 = 0.02, 0.2
+    assert cosmology.dt_supercomoving(a0, a1, 1.0, 0.0) == pytest.approx(2 * (a0 ** -0.5 - a1 ** -0.5), rel=1e-12)
+
+
+def test_growth_eds_and_lcdm(golden):
+    a = np.array([0.01, 0.1, 1.0])
+    D, E, f1, f2 = cosmology.growth_factors(a, 1.0, 0.0)
+    assert D / a == pytest.approx(np.ones(3), rel=1e-6)
+    assert E / D ** 2 == pytest.approx(np.full(3, golden["growth_eds"]["D2_over_D1sq"]), rel=1e-5)
+    # LCDM growing mode: D proportional to E(a) * int_0^a da' / (a' E(a'))^3
+    Om, OL = 0.3, 0.7
+    a = np.array([0.1, 0.5, 1.0])
+    D, _, _, _ = cosmology.growth_factors(a, Om, OL)
+    from scipy.integrate import quad
+    heath = np.array([cosmology.hubble_E(x, Om, OL) * quad(lambda y: (y * cosmology.hubble_E(y, Om, OL)) ** -3,
+                                                           0, x, epsrel=1e-12)[0] for x in a])
+    assert D / D[-1] == pytest.approx(heath / heath[-1], rel=1e-6)
+
+
+def test_momentum_conservation_and_no_self_force():
+    prm = step.PMParams(n=16, Om=1.0, OL=0.0)
+    pos = np.random.default_rng(9).random((300, 3))
+    acc, _, _ = step.accelerations(pos, 0.5, prm)
+    assert np.abs(acc.sum(axis=0)).max() < 1e-11 * np.abs(acc).sum()
+    one = np.array([[0.3141, 0.5926, 0.5358]])
+    acc1, _, _ = step.accelerations(one, 0.5, prm)
+    assert np.abs(acc1).max() < 1e-14
+
+
+def test_kdk_time_reversible():
+    prm = step.PMParams(n=16, Om=1.0, OL=0.0)
+    rng = np.random.default_rng(10)
+    pos0 = rng.random((200, 3))
+    vel0 = 1e-3 * rng.standard_normal((200, 3))
+    a = list(np.linspace(0.1, 0.3, 6))
+    pos1, vel1 = step.run_kdk(pos0, vel0, a, prm)
+    pos2, vel2 = step.run_kdk(pos1, vel1, a[::-1], prm)
+    d = (pos2 - pos0 + 0.5) % 1.0 - 0.5
+    assert np.abs(d).max() < 1e-12
+    assert np.abs(vel2 - vel0).max() < 1e-12
+
+
+def _plane_wave_growth(n, m=1):
+    """EdS Zel'dovich plane wave along x, amplitude chosen pre-shell-crossing;
+    returns the growth of the displacement amplitude divided by a_end/a_start."""
+    a0, a1, steps = 0.02, 0.2, 20
+    A1 = 0.3 / (2 * np.pi * m)                  # D |dPsi/dq| = 0.3 at a1
+    A0 = A1 * a0 / a1
+    q = (np.arange(n) + 0.5) / n
+    qx, qy, qz = np.meshgrid(q, q, q, indexing="ij")
+    psi = A0 * np.sin(2 * np.pi * m * qx)
+    pos = np.stack([(qx + psi).ravel(), qy.ravel(), qz.ravel()], axis=1)
+    vel = np.zeros_like(pos)
+    vel[:, 0] = (psi * math.sqrt(a0)).ravel()
+    prm = step.PMParams(n=n, Om=1.0, OL=0.0)
+    pos, _ = step.run_kdk(pos, vel, list(np.linspace(a0, a1, steps + 1)), prm)
+    dx = (pos[:, 0] - qx.ravel() + 0.5) % 1.0 - 0.5
+    amp = 2 * np.mean(dx * np.sin(2 * np.pi * m * qx.ravel()))
+    return (amp / A0) / (a1 / a0)
+
+
+@pytest.mark.slow
+def test_zeldovich_growth_eds():
+    """D = a in Einstein-de Sitter before shell crossing (§3.3 / Appendix A);
+    the PM deficit comes from the discrete operators (TSC window, 7-point
+    Laplacian, 5-point gradient) and from 20 leapfrog steps, and shrinks with
+    resolution."""
+    g16, g32, g64 = (_plane_wave_growth(n) for n in (16, 32, 64))
+    assert abs(g64 - 1.0) < 0.01
+    assert (1.0 - g16) > (1.0 - g32) > (1.0 - g64) > 0.0
+
+
+def test_power_spectrum_plane_wave_total():
+    n, L, A, m = 32, 100.0, 0.1, 3
+    i = np.arange(n)
+    delta = A * np.cos(2 * np.pi * m * i / n)[:, None, None] * np.ones((1, n, n))
+    k, P, cnt = power.power_spectrum(1.0 + delta, L)
+    total = P * cnt
+    assert total[m - 1] == pytest.approx(L ** 3 * A ** 2 / 2, rel=1e-12)
+    assert np.abs(np.delete(total, m - 1)).max() < 1e-20
+    assert abs(k[m - 1] - 2 * np.pi * m / L) < 0.5 * 2 * np.pi / L   # mode-averaged shell wavenumber
