@@ -1,0 +1,267 @@
+/*
+ * pm_api.h - C ABI of the GB300 (sm_103a) particle-mesh force step of
+ * PySCo (arXiv 2410.20501).
+ *
+ * The library computes, on one GPU, the per-step PM force evaluation of §3.4-§3.10
+ * and the kick-drift-kick update of §3.4 ("Integrator"):
+ *   cell keys + stable cell sort  ->  TSC mass assignment (§3.4)
+ *   -> multigrid Poisson solve of the 7-point Laplacian (§3.5, §3.6.1)
+ *   -> [f(R)] FAS multigrid for the Hu-Sawicki scalaron (§3.6.2, §3.10)
+ *   -> central-difference gradient (Table 1) -> inverse TSC (§3.4)
+ *   -> kick-drift-kick with uint32 fixed-point positions.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - n is the number of cells per side, a power of two, 4 <= n <= 1024.
+ *  - Scalar grids are float32 [n][n][n] in C order (cell (i,j,k) at index
+ *    (i*n + j)*n + k, cell centres at (i + 1/2)/n), as in §3.2.  Vector grids
+ *    are three such planes, x then y then z.
+ *  - Particle positions are uint32 fixed-point box coordinates, three planes
+ *    [3][np]: x = X * 2^-32 in [0, 1), so periodic wrap is exact.  Velocities
+ *    and accelerations are float32 planes [3][np] in supercomoving units (§3.1:
+ *    box length 1, time unit t_* = a^2/H0).
+ *  - Every pointer argument is caller-owned DEVICE memory unless the
+ *    description says "host".  The library never allocates device memory: work
+ *    buffers come from the caller as one workspace of pm_workspace_size() bytes,
+ *    aligned to 256 bytes.  Arrays must not alias unless stated.
+ *  - Work is enqueued asynchronously on `stream` (a cudaStream_t; NULL = the
+ *    legacy default stream).  Argument errors are detected synchronously and
+ *    nothing is enqueued.  Entry points that test convergence (mg_solve,
+ *    fr_solve, pm_step with tolerances) synchronise `stream` once per cycle to
+ *    read an 8-byte residual norm; with fixed cycle counts they never sync.
+ *  - Results are deterministic: no floating-point atomics are used anywhere,
+ *    every reduction has a fixed order, so reruns are bitwise identical.
+ *  - Not thread-safe: calls must come from one host thread at a time.
+ */
+#ifndef PM_API_H
+#define PM_API_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int pm_status;
+enum {
+  PM_OK = 0,
+  PM_EINVAL = 1,    /* bad size, null pointer or parameter                       */
+  PM_ENOMEM = 2,    /* workspace smaller than pm_workspace_size()                 */
+  PM_ENOCONV = 3,   /* solver hit max_cycles without meeting its tolerance        */
+  PM_ENAN = 4,      /* a residual norm was not finite                             */
+  PM_ETIMEOUT = 5,  /* a device-side bounded wait gave up                         */
+  PM_ECUDA = 6      /* a CUDA runtime call failed (see pm_last_cuda_error)        */
+};
+
+/* Human-readable name of a status code (static string). */
+const char* pm_status_string(pm_status s);
+/* Last CUDA error string seen by the library (static string, "" if none). */
+const char* pm_last_cuda_error(void);
+/* Library version, e.g. "1.0.0". */
+const char* pm_version(void);
+
+/* Flags for pm_workspace_size: which entry points the workspace must serve. */
+enum {
+  PM_WS_SORT = 1,      /* pm_sort, pm_deposit                                  */
+  PM_WS_MG = 2,        /* mg_solve                                             */
+  PM_WS_FR = 4,        /* fr_solve                                             */
+  PM_WS_STEP = 8,      /* pm_step, pm_step_host (includes all of the above)    */
+  PM_WS_IDS = 16       /* pm_step carries particle ids (pm_state.id != NULL)   */
+};
+
+/* Bytes of workspace needed for grids of n^3 cells and np particles.
+ * Returns PM_EINVAL for a bad n or np < 0.  *bytes is a host pointer. */
+pm_status pm_workspace_size(int n, int64_t np, uint32_t flags, size_t* bytes);
+
+/* ---------------------------------------------------------------- sorting --
+ * Cell ordering that replaces the periodic Morton reordering of §3.2 and
+ * Appendix E: key = (i*n + j)*n + k of the cell containing each particle
+ * (i = floor(x n)), then a stable sort (ties keep input order).
+ *   X          [3][np] uint32 positions (read)
+ *   perm       [np]    out: perm[r] = input index of the particle of rank r
+ *   cellstart  [n^3+1] out: particles of cell c are ranks cellstart[c] ..
+ *                      cellstart[c+1]-1 (cellstart[n^3] = np)
+ * Either output may be NULL (not written).  Integer results are bit-exact. */
+pm_status pm_sort(const uint32_t* X, int64_t np, int n, uint32_t* perm,
+                  uint32_t* cellstart, void* ws, size_t ws_bytes, void* stream);
+
+/* --------------------------------------------------------------- deposit --
+ * TSC mass assignment (§3.4, W_TSC) as a deterministic cell-sorted gather:
+ *   rho[c] = (n^3/np) * sum_p prod_d W_TSC(n x_p,d - (c_d + 1/2)),
+ * so the grid sums to n^3 (mean density 1; equals the paper's
+ * sum rho = N_part when np = n^3).  np = 0 gives rho = 0.
+ *   X    [3][np] uint32 positions (read);  rho [n^3] float32 (written). */
+pm_status pm_deposit(const uint32_t* X, int64_t np, int n, float* rho,
+                     void* ws, size_t ws_bytes, void* stream);
+
+/* ------------------------------------------------------------- multigrid -- */
+enum { MG_GUESS_INPUT = 0, MG_GUESS_JACOBI = 1, MG_GUESS_SCALED = 2 };
+
+typedef struct {
+  int npre, npost;        /* Gauss-Seidel sweeps before / after the coarse
+                             correction (§3.6.1 Npre / Npost)                    */
+  float omega;            /* SOR factor (§3.6.1, 1.25); omega = 1 is applied on
+                             the first pre-sweep and the last post-sweep         */
+  int coarsest;           /* size of the coarsest level (§3.6.1: 16)           */
+  int coarse_max_sweeps;  /* coarsest level: at most this many sweeps ...      */
+  float coarse_drop;      /* ... or until its residual dropped by this factor  */
+  int max_cycles;         /* cap on cycles (PM_ENOCONV beyond)                  */
+  int fixed_cycles;       /* > 0: run exactly this many cycles, no norms, no
+                             host synchronisation (CUDA-graph capturable)       */
+  double tol;             /* stop when ||f - L phi||_2 <= tol ||f||_2           */
+  double stall;           /* also stop (PM_OK) when a cycle reduced the residual
+                             by less than 1/stall: the float32 floor            */
+  int first_guess;        /* MG_GUESS_INPUT: phi holds the guess;
+                             MG_GUESS_JACOBI: -h^2 f / 6 (Eq. multigrid_initial_guess);
+                             MG_GUESS_SCALED: guess_scale * phi (the warm start
+                             of Eq. rescaming_newtonian_potential)              */
+  float guess_scale;
+} mg_params;
+
+typedef struct {
+  int status;             /* pm_status of the solve                            */
+  int cycles;             /* cycles run                                        */
+  double norm_f;          /* ||f - <f>||_2                                      */
+  double res0;            /* residual norm before the first cycle (only with
+                             tolerances; computed after the first cycle
+                             otherwise: -1)                                      */
+  double res;             /* residual norm after the last cycle (-1 if fixed)  */
+} mg_stats;
+
+/* Default parameters: npre = npost = 2, omega = 1.25, coarsest = 16,
+ * coarse_max_sweeps = 200, coarse_drop = 1e-3, max_cycles = 30,
+ * fixed_cycles = 0, tol = 1e-7, stall = 0.5, first_guess = MG_GUESS_INPUT. */
+void mg_default_params(mg_params* p);
+
+/* Solve the periodic Poisson problem (L(phi) - 6 phi)/h^2 = f - <f>, h = 1/n,
+ * with red-black SOR V-cycles (§3.5, §3.6.1): restriction by 8-child average,
+ * prolongation 27/9/3/1 over 64, zero initial guess for the coarse error,
+ * Jacobi-type sweeps on the coarsest level.  Smoothing and transfers run in
+ * float32; the finest-level residual is evaluated with compensated float32
+ * arithmetic and its norm accumulated in float64.
+ *   f    [n^3] float32 right-hand side (read; its float64 mean is removed)
+ *   phi  [n^3] float32 in: guess (see first_guess), out: solution
+ *   st   host mg_stats (may be NULL) */
+pm_status mg_solve(const float* f, float* phi, int n, const mg_params* prm,
+                   mg_stats* st, void* ws, size_t ws_bytes, void* stream);
+
+/* ------------------------------------------------------------------ f(R) -- */
+typedef struct {
+  double a;          /* scale factor                                          */
+  double Om, OL;     /* density parameters today (flat)                       */
+  double fR0;        /* f_R0 < 0 (Hu-Sawicki, n = 1)                          */
+  double boxsize;    /* box size in Mpc/h (sets c~ = c / (H0 L))              */
+  int cycle;         /* 0 = V-cycle, 1 = F-cycle (default: one F-cycle, §3.10) */
+  int npre, npost, coarsest, coarse_max_sweeps;
+  float coarse_drop;
+  int cycles;        /* cycles to run when tol <= 0                           */
+  double tol;        /* > 0: cycle until ||b - N(u)|| <= tol ||b|| (synchronises) */
+  int max_cycles;
+} fr_params;
+
+void fr_default_params(fr_params* p);
+
+/* Hu-Sawicki n = 1 scalaron (§3.10, Eq. fr_sim_2) by non-linear FAS multigrid
+ * (§3.6.2).  With u = (f~_R / fbar)^(1/2) the discrete equation is
+ *   (fbar/h^2)(L(u^2) - 6u^2) - kappa (1/u - 1) = -(Om a / c~^2)(rho - <rho>),
+ * kappa = a^4 R~ / (3 c~^2), R~ = 3 Om (a^-3 + 4 OL/Om), fbar = a^2 fR0 (R~0/R~)^2,
+ * each Gauss-Seidel update being the positive root of the depressed cubic of
+ * Eq. fr_depressed_equation.  The unknown is stored as eps = u - 1 and the
+ * cubic solved in that variable in float32 (safeguarded Newton).
+ *   rho  [n^3] float32 density (read)
+ *   eps  [n^3] float32 in: guess (0 = background), out: solution
+ *   st   host mg_stats (may be NULL) */
+pm_status fr_solve(const float* rho, float* eps, int n, const fr_params* prm,
+                   mg_stats* st, void* ws, size_t ws_bytes, void* stream);
+
+/* -------------------------------------------------------------- gradient --
+ * g = -grad(phi) with the central stencils of Table 1 (order 3, 5 or 7),
+ * periodic.  phi [n^3] (read), g [3][n^3] (written). */
+pm_status pm_gradient(const float* phi, float* g, int n, int order, void* stream);
+
+/* ---------------------------------------------------------- interpolation --
+ * Inverse TSC (§3.4): acc_p = sum_c W_TSC(x_p - x_c) g_c over the 27 cells.
+ *   g [3][n^3] (read), X [3][np] (read), acc [3][np] (written). */
+pm_status pm_interp(const float* g, const uint32_t* X, int64_t np, int n,
+                    float* acc, void* stream);
+
+/* ------------------------------------------------------------------ step -- */
+typedef struct {
+  int n;
+  int64_t np;
+  uint32_t* X;     /* [3][np] positions, updated in place                     */
+  float* V;        /* [3][np] velocities, updated in place                    */
+  uint32_t* id;    /* [np] particle ids permuted along, or NULL               */
+  float* phi;      /* [n^3] potential: previous step's on input (warm start),
+                      this step's on output                                   */
+  float* eps;      /* [n^3] f(R) eps = u - 1 (previous / this step), or NULL  */
+  float* acc;      /* [3][np] if not NULL: accelerations of this step, in the
+                      particles' new (sorted) order                           */
+  void* ws;
+  size_t ws_bytes;
+  int have_prev;   /* 0 before the first step: Jacobi first guess for phi and
+                      u = 1 for f(R); set to 1 by pm_step                     */
+} pm_state;
+
+enum { PM_GRAVITY_NEWTON = 0, PM_GRAVITY_FR = 1 };
+
+typedef struct {
+  double a;            /* scale factor of this force evaluation              */
+  double Om, OL;       /* cosmology (flat)                                   */
+  double boxsize;      /* Mpc/h                                              */
+  int gravity;         /* PM_GRAVITY_NEWTON or PM_GRAVITY_FR                 */
+  double fR0;          /* for PM_GRAVITY_FR                                  */
+  int grad_order;      /* 3, 5 or 7 (Table 1); 5 by default                  */
+  double dt_kick;      /* v += acc * dt_kick (sum of the two half kicks of
+                          the leapfrog around this force evaluation)         */
+  double dt_drift;     /* then x += v * dt_drift (0: kick only)              */
+  double phi_rescale;  /* warm start: phi_guess = phi_rescale * phi_prev     */
+  mg_params mg;        /* Poisson multigrid                                  */
+  fr_params fr;        /* f(R) solver (a, Om, OL, fR0, boxsize taken from above) */
+} pm_step_params;
+
+typedef struct {
+  int status;
+  mg_stats mg;         /* Poisson solve                                      */
+  mg_stats fr;         /* f(R) solve                                         */
+} pm_stats;
+
+/* One PM step on the device-resident state (§3.4-§3.10): sort particles by
+ * cell (X, V and id are permuted into cell order), deposit, solve (f(R) first
+ * if requested, then Poisson for phi), force g = -grad(phi - (c~^2/2) f~_R),
+ * inverse TSC, then v += acc dt_kick and x += v dt_drift with exact periodic
+ * wrap.  Kicks of consecutive leapfrog steps are merged by the caller through
+ * dt_kick = (dt_{i-1} + dt_i)/2.  `st` is a host pointer (may be NULL). */
+pm_status pm_step(pm_state* s, const pm_step_params* prm, pm_stats* st, void* stream);
+
+/* pm_step with HOST particle buffers: copies X_in, V_in (host, ideally pinned)
+ * into s->X, s->V, runs pm_step and copies the new X, V back into X_out, V_out
+ * (host).  The copies are enqueued on `stream`; the call returns after the
+ * device-to-host copies have completed. */
+pm_status pm_step_host(pm_state* s, const pm_step_params* prm, pm_stats* st,
+                       const uint32_t* X_in, const float* V_in,
+                       uint32_t* X_out, float* V_out, void* stream);
+
+/* ------------------------------------------------------ host utilities ---- */
+/* Supercomoving time between a0 and a1 (§3.1): integral of da/(a^3 E(a)),
+ * E(a) = sqrt(Om a^-3 + OL).  Host computation, float64. */
+double pm_dt_supercomoving(double Om, double OL, double a0, double a1);
+/* Linear growth factor D(a) (Appendix A, growing mode, D ~ a early on). */
+double pm_growth_D(double Om, double OL, double a);
+
+/* --------------------------------------------------------- instrumentation */
+/* Number of kernels this library has launched since load. */
+uint64_t pm_launch_count(void);
+/* Enable (1) / disable (0) CUDA-event timing of every launch, recorded on the
+ * launch stream.  Enabling clears previous records. */
+pm_status pm_timing_enable(int on);
+/* Synchronises, then reports per kernel class: total milliseconds and
+ * launches since pm_timing_enable(1).  Arrays are host, length cap; returns
+ * the number of classes written.  names[i] are static strings. */
+int pm_timing_collect(const char** names, double* ms, int64_t* launches, int cap);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PM_API_H */

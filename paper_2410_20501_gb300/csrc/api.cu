@@ -1,0 +1,430 @@
+// C ABI of libpmgb: argument checks, workspace layout, the step pipeline,
+// host-side cosmology utilities and launch instrumentation.
+#include <math.h>
+#include <string.h>
+
+#include <vector>
+
+#include "pm_internal.cuh"
+
+namespace pmgb {
+
+const char* const kKernelClassNames[K_NCLASS] = {
+    "cell_keys",   "radix_upsweep", "radix_scan",  "radix_downsweep", "cellstart",  "permute",
+    "tsc_deposit", "reduce",        "mg_guess",    "mg_smooth",       "mg_restrict", "mg_prolong",
+    "mg_coarse",   "mg_norm",       "fr_smooth",   "fr_restrict",     "fr_coarse_op", "fr_prolong",
+    "fr_coarse",   "fr_norm",       "gradient",    "interp_kdk",      "misc"};
+
+namespace {
+
+uint64_t g_launches = 0;
+char g_last_error[256] = "";
+
+struct TimingPool {
+  bool on = false;
+  std::vector<cudaEvent_t> start, stop;
+  std::vector<int> cls;
+  size_t used = 0;
+};
+TimingPool g_timing;
+constexpr size_t kTimingCap = 1 << 15;
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+}  // namespace
+
+void launch_begin(int cls, cudaStream_t s) {
+  (void)cls;
+  ++g_launches;
+  if (g_timing.on && g_timing.used < g_timing.start.size()) cudaEventRecord(g_timing.start[g_timing.used], s);
+}
+
+void launch_end(int cls, cudaStream_t s) {
+  if (g_timing.on && g_timing.used < g_timing.start.size()) {
+    cudaEventRecord(g_timing.stop[g_timing.used], s);
+    g_timing.cls[g_timing.used] = cls;
+    ++g_timing.used;
+  }
+}
+
+pm_status cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return PM_OK;
+  strncpy(g_last_error, cudaGetErrorString(e), sizeof(g_last_error) - 1);
+  return PM_ECUDA;
+}
+
+size_t layout_workspace(Workspace* w, void* base, int n, int64_t np, uint32_t flags) {
+  Workspace tmp;
+  if (!w) w = &tmp;
+  memset(w, 0, sizeof(*w));
+  const bool step = flags & PM_WS_STEP;
+  const bool sort = step || (flags & PM_WS_SORT);
+  const bool mg = step || (flags & PM_WS_MG);
+  const bool fr = step || (flags & PM_WS_FR);
+  const int64_t N = (int64_t)n * n * n;
+  size_t off = 0;
+  char* b = (char*)base;
+  auto take = [&](size_t bytes) -> char* {
+    off = align256(off);
+    char* p = b ? b + off : nullptr;
+    off += bytes;
+    return p;
+  };
+  if (sort) {
+    const size_t kb = (size_t)np * 4;
+    w->keys_a = (uint32_t*)take(kb);
+    w->keys_b = (uint32_t*)take(kb);
+    w->vals_a = (uint32_t*)take(kb);
+    w->vals_b = (uint32_t*)take(kb);
+    w->counts = (uint32_t*)take((size_t)512 * radix_tiles(np) * 4 + 4);
+    w->scan_blocks = (uint32_t*)take((size_t)radix_scan_blocks(np) * 4 + 4);
+    w->cellstart = (uint32_t*)take((size_t)(N + 1) * 4);
+    w->Xs = (uint32_t*)take(3 * kb);
+  }
+  if (step) {
+    w->Vs = (float*)take((size_t)np * 12);
+    if (flags & PM_WS_IDS) w->ids = (uint32_t*)take((size_t)np * 4);
+    w->rho = (float*)take((size_t)N * 4);
+    w->g = (float*)take((size_t)N * 12);
+  }
+  w->partials = (double*)take((size_t)2 * reduce_partials_capacity(n, np) * 8);
+  w->scalars = (double*)take(64 * 8);
+  for (int l = 1; l < 12; ++l) {
+    const int nl = n >> l;
+    if (nl < 4) break;
+    const size_t bytes = (size_t)nl * nl * nl * 4;
+    if (mg) {
+      w->mg_u[l] = (float*)take(bytes);
+      w->mg_f[l] = (float*)take(bytes);
+    }
+    if (fr) {
+      w->fr_e[l] = (float*)take(bytes);
+      w->fr_r[l] = (float*)take(bytes);
+      w->fr_b[l] = (float*)take(bytes);
+    }
+  }
+  w->base = b;
+  w->total = align256(off);
+  w->np = np;
+  w->n = n;
+  return w->total;
+}
+
+}  // namespace pmgb
+
+using namespace pmgb;
+
+namespace {
+
+cudaStream_t as_stream(void* s) { return (cudaStream_t)s; }
+
+bool aligned(const void* p) { return ((uintptr_t)p & 255) == 0; }
+
+pm_status check_ws(Workspace& w, void* ws, size_t ws_bytes, int n, int64_t np, uint32_t flags) {
+  const size_t need = layout_workspace(nullptr, nullptr, n, np, flags);
+  if (!ws || !aligned(ws)) return PM_EINVAL;
+  if (ws_bytes < need) return PM_ENOMEM;
+  layout_workspace(&w, ws, n, np, flags);
+  return PM_OK;
+}
+
+bool valid_np(int64_t np) { return np >= 0 && np < ((int64_t)1 << 31); }
+
+bool valid_mg(const mg_params* p) {
+  return p && p->npre >= 0 && p->npost >= 0 && p->npre + p->npost > 0 && p->coarsest >= 4 &&
+         p->coarsest <= 16 && p->coarse_max_sweeps >= 0 && p->max_cycles >= 1 && p->omega > 0.0f &&
+         p->omega < 2.0f && p->first_guess >= MG_GUESS_INPUT && p->first_guess <= MG_GUESS_SCALED;
+}
+
+bool valid_fr(const fr_params* p) {
+  return p && p->a > 0.0 && p->Om > 0.0 && p->fR0 < 0.0 && p->boxsize > 0.0 && p->npre >= 0 && p->npost >= 0 &&
+         p->coarsest >= 4 && p->coarsest <= 16 && p->coarse_max_sweeps >= 0 && (p->cycle == 0 || p->cycle == 1) &&
+         (p->tol > 0.0 ? p->max_cycles >= 1 : p->cycles >= 0);
+}
+
+// Adaptive Simpson quadrature of da / (a^3 E(a)).
+double integrand(double Om, double OL, double a) { return 1.0 / (a * a * a * sqrt(Om / (a * a * a) + OL)); }
+
+double simpson(double Om, double OL, double a, double b, double fa, double fm, double fb, double whole, double eps,
+               int depth) {
+  const double m = 0.5 * (a + b), lm = 0.5 * (a + m), rm = 0.5 * (m + b);
+  const double flm = integrand(Om, OL, lm), frm = integrand(Om, OL, rm);
+  const double left = (m - a) / 6.0 * (fa + 4.0 * flm + fm), right = (b - m) / 6.0 * (fm + 4.0 * frm + fb);
+  const double delta = left + right - whole;
+  if (depth <= 0 || fabs(delta) <= 15.0 * eps) return left + right + delta / 15.0;
+  return simpson(Om, OL, a, m, fa, flm, fm, left, 0.5 * eps, depth - 1) +
+         simpson(Om, OL, m, b, fm, frm, fb, right, 0.5 * eps, depth - 1);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* pm_status_string(pm_status s) {
+  switch (s) {
+    case PM_OK: return "PM_OK";
+    case PM_EINVAL: return "PM_EINVAL: invalid argument";
+    case PM_ENOMEM: return "PM_ENOMEM: workspace too small";
+    case PM_ENOCONV: return "PM_ENOCONV: solver did not converge";
+    case PM_ENAN: return "PM_ENAN: non-finite residual";
+    case PM_ETIMEOUT: return "PM_ETIMEOUT: device wait timed out";
+    case PM_ECUDA: return "PM_ECUDA: CUDA error";
+    default: return "unknown status";
+  }
+}
+
+const char* pm_last_cuda_error(void) { return g_last_error; }
+const char* pm_version(void) { return "1.0.0"; }
+uint64_t pm_launch_count(void) { return g_launches; }
+
+pm_status pm_workspace_size(int n, int64_t np, uint32_t flags, size_t* bytes) {
+  if (!valid_n(n) || !valid_np(np) || !bytes) return PM_EINVAL;
+  *bytes = layout_workspace(nullptr, nullptr, n, np, flags);
+  return PM_OK;
+}
+
+void mg_default_params(mg_params* p) {
+  if (!p) return;
+  p->npre = 2;
+  p->npost = 2;
+  p->omega = 1.25f;
+  p->coarsest = 16;
+  p->coarse_max_sweeps = 200;
+  p->coarse_drop = 1e-3f;
+  p->max_cycles = 30;
+  p->fixed_cycles = 0;
+  p->tol = 1e-7;
+  p->stall = 0.5;
+  p->first_guess = MG_GUESS_INPUT;
+  p->guess_scale = 1.0f;
+}
+
+void fr_default_params(fr_params* p) {
+  if (!p) return;
+  p->a = 1.0;
+  p->Om = 0.3;
+  p->OL = 0.7;
+  p->fR0 = -1e-5;
+  p->boxsize = 512.0;
+  p->cycle = 1;
+  p->npre = 2;
+  p->npost = 2;
+  p->coarsest = 16;
+  p->coarse_max_sweeps = 200;
+  p->coarse_drop = 1e-3f;
+  p->cycles = 1;
+  p->tol = 0.0;
+  p->max_cycles = 30;
+}
+
+pm_status pm_sort(const uint32_t* X, int64_t np, int n, uint32_t* perm, uint32_t* cellstart, void* ws,
+                  size_t ws_bytes, void* stream) {
+  if (!valid_n(n) || !valid_np(np) || (np > 0 && !X)) return PM_EINVAL;
+  Workspace w;
+  PM_TRY(check_ws(w, ws, ws_bytes, n, np, PM_WS_SORT));
+  cudaStream_t s = as_stream(stream);
+  uint32_t *p, *k;
+  PM_TRY(sort_particles(X, np, n, w, s, &p, &k));
+  if (perm && np > 0) PM_TRY(cuda_status(cudaMemcpyAsync(perm, p, np * 4, cudaMemcpyDeviceToDevice, s)));
+  if (cellstart) PM_TRY(build_cellstart(k, np, n, cellstart, s));
+  return launch_status();
+}
+
+pm_status pm_deposit(const uint32_t* X, int64_t np, int n, float* rho, void* ws, size_t ws_bytes, void* stream) {
+  if (!valid_n(n) || !valid_np(np) || (np > 0 && !X) || !rho) return PM_EINVAL;
+  Workspace w;
+  PM_TRY(check_ws(w, ws, ws_bytes, n, np, PM_WS_SORT));
+  cudaStream_t s = as_stream(stream);
+  uint32_t *p, *k;
+  PM_TRY(sort_particles(X, np, n, w, s, &p, &k));
+  PM_TRY(build_cellstart(k, np, n, w.cellstart, s));
+  PM_TRY(permute_particles(p, np, X, nullptr, nullptr, w.Xs, nullptr, nullptr, s));
+  PM_TRY(deposit_sorted(w.Xs, np, w.cellstart, n, rho, w.partials, w.scalars, s));
+  return launch_status();
+}
+
+pm_status mg_solve(const float* f, float* phi, int n, const mg_params* prm, mg_stats* st, void* ws,
+                   size_t ws_bytes, void* stream) {
+  if (!valid_n(n) || !f || !phi || !valid_mg(prm)) return PM_EINVAL;
+  Workspace w;
+  PM_TRY(check_ws(w, ws, ws_bytes, n, 0, PM_WS_MG));
+  cudaStream_t s = as_stream(stream);
+  PM_TRY(grid_mean(f, (int64_t)n * n * n, w.partials, w.scalars + 1, s));
+  return mg_solve_src(Src{f, 1.0f, w.scalars + 1}, phi, n, *prm, st, w, s);
+}
+
+pm_status fr_solve(const float* rho, float* eps, int n, const fr_params* prm, mg_stats* st, void* ws,
+                   size_t ws_bytes, void* stream) {
+  if (!valid_n(n) || !rho || !eps || !valid_fr(prm)) return PM_EINVAL;
+  Workspace w;
+  PM_TRY(check_ws(w, ws, ws_bytes, n, 0, PM_WS_FR));
+  cudaStream_t s = as_stream(stream);
+  PM_TRY(grid_mean(rho, (int64_t)n * n * n, w.partials, w.scalars + 2, s));
+  double fbar, kappa, c2;
+  fr_background(*prm, &fbar, &kappa, &c2);
+  const float sb = (float)(-prm->Om * prm->a / c2);
+  return fr_solve_src(Src{rho, sb, w.scalars + 2}, eps, n, *prm, st, w, s);
+}
+
+pm_status pm_gradient(const float* phi, float* g, int n, int order, void* stream) {
+  if (!valid_n(n) || !phi || !g || (order != 3 && order != 5 && order != 7)) return PM_EINVAL;
+  return gradient_launch(phi, nullptr, 0.0f, g, n, order, as_stream(stream));
+}
+
+pm_status pm_interp(const float* g, const uint32_t* X, int64_t np, int n, float* acc, void* stream) {
+  if (!valid_n(n) || !valid_np(np) || !g || (np > 0 && (!X || !acc))) return PM_EINVAL;
+  return interp_launch(g, X, nullptr, nullptr, np, n, acc, nullptr, nullptr, nullptr, 0.0f, 0.0f, 0,
+                       as_stream(stream));
+}
+
+pm_status pm_step(pm_state* st_, const pm_step_params* prm, pm_stats* stats, void* stream) {
+  if (!st_ || !prm) return PM_EINVAL;
+  pm_state& S = *st_;
+  const int n = S.n;
+  const int64_t np = S.np;
+  if (!valid_n(n) || !valid_np(np) || (np > 0 && (!S.X || !S.V)) || !S.phi) return PM_EINVAL;
+  if (prm->gravity != PM_GRAVITY_NEWTON && prm->gravity != PM_GRAVITY_FR) return PM_EINVAL;
+  if (prm->gravity == PM_GRAVITY_FR && !S.eps) return PM_EINVAL;
+  if (prm->grad_order != 3 && prm->grad_order != 5 && prm->grad_order != 7) return PM_EINVAL;
+  if (!(prm->a > 0.0) || !valid_mg(&prm->mg)) return PM_EINVAL;
+  fr_params frp = prm->fr;
+  frp.a = prm->a;
+  frp.Om = prm->Om;
+  frp.OL = prm->OL;
+  frp.fR0 = prm->fR0;
+  frp.boxsize = prm->boxsize;
+  if (prm->gravity == PM_GRAVITY_FR && !valid_fr(&frp)) return PM_EINVAL;
+  const uint32_t flags = PM_WS_STEP | (S.id ? PM_WS_IDS : 0);
+  Workspace w;
+  PM_TRY(check_ws(w, S.ws, S.ws_bytes, n, np, flags));
+  cudaStream_t s = as_stream(stream);
+  const int64_t N = (int64_t)n * n * n;
+  pm_stats local;
+  memset(&local, 0, sizeof(local));
+
+  uint32_t *perm, *skeys;
+  PM_TRY(sort_particles(S.X, np, n, w, s, &perm, &skeys));
+  PM_TRY(build_cellstart(skeys, np, n, w.cellstart, s));
+  PM_TRY(permute_particles(perm, np, S.X, S.V, S.id, w.Xs, w.Vs, w.ids, s));
+  PM_TRY(deposit_sorted(w.Xs, np, w.cellstart, n, w.rho, w.partials, w.scalars, s));
+
+  double fbar = 0.0, kappa = 0.0, c2 = 0.0;
+  pm_status solve_status = PM_OK;
+  if (prm->gravity == PM_GRAVITY_FR) {
+    fr_background(frp, &fbar, &kappa, &c2);
+    if (!S.have_prev) PM_TRY(cuda_status(cudaMemsetAsync(S.eps, 0, N * sizeof(float), s)));
+    const float sb = (float)(-prm->Om * prm->a / c2);
+    pm_status r = fr_solve_src(Src{w.rho, sb, w.scalars}, S.eps, n, frp, &local.fr, w, s);
+    if (r != PM_OK && r != PM_ENOCONV) return r;
+    if (r != PM_OK) solve_status = r;
+  }
+  mg_params mp = prm->mg;
+  mp.first_guess = S.have_prev ? MG_GUESS_SCALED : MG_GUESS_JACOBI;
+  mp.guess_scale = (float)prm->phi_rescale;
+  {
+    pm_status r = mg_solve_src(Src{w.rho, (float)(1.5 * prm->a * prm->Om), w.scalars}, S.phi, n, mp, &local.mg, w, s);
+    if (r != PM_OK && r != PM_ENOCONV) return r;
+    if (r != PM_OK) solve_status = r;
+  }
+  const float alpha = (float)(-0.5 * c2 * fbar);
+  PM_TRY(gradient_launch(S.phi, prm->gravity == PM_GRAVITY_FR ? S.eps : nullptr, alpha, w.g, n, prm->grad_order, s));
+  PM_TRY(interp_launch(w.g, w.Xs, w.Vs, w.ids, np, n, S.acc, S.X, S.V, S.id, (float)prm->dt_kick,
+                       (float)prm->dt_drift, 1, s));
+  S.have_prev = 1;
+  local.status = solve_status;
+  if (stats) *stats = local;
+  PM_TRY(launch_status());
+  return solve_status;
+}
+
+pm_status pm_step_host(pm_state* st_, const pm_step_params* prm, pm_stats* stats, const uint32_t* X_in,
+                       const float* V_in, uint32_t* X_out, float* V_out, void* stream) {
+  if (!st_ || !X_in || !V_in || !X_out || !V_out) return PM_EINVAL;
+  cudaStream_t s = as_stream(stream);
+  const size_t bytes = (size_t)st_->np * 12;
+  PM_TRY(cuda_status(cudaMemcpyAsync(st_->X, X_in, bytes, cudaMemcpyHostToDevice, s)));
+  PM_TRY(cuda_status(cudaMemcpyAsync(st_->V, V_in, bytes, cudaMemcpyHostToDevice, s)));
+  pm_status r = pm_step(st_, prm, stats, stream);
+  if (r != PM_OK && r != PM_ENOCONV) return r;
+  PM_TRY(cuda_status(cudaMemcpyAsync(X_out, st_->X, bytes, cudaMemcpyDeviceToHost, s)));
+  PM_TRY(cuda_status(cudaMemcpyAsync(V_out, st_->V, bytes, cudaMemcpyDeviceToHost, s)));
+  PM_TRY(cuda_status(cudaStreamSynchronize(s)));
+  return r;
+}
+
+double pm_dt_supercomoving(double Om, double OL, double a0, double a1) {
+  if (!(a0 > 0.0) || !(a1 > 0.0)) return NAN;
+  if (a0 == a1) return 0.0;
+  const double sign = a1 > a0 ? 1.0 : -1.0;
+  const double lo = a1 > a0 ? a0 : a1, hi = a1 > a0 ? a1 : a0;
+  const double fa = integrand(Om, OL, lo), fb = integrand(Om, OL, hi), fm = integrand(Om, OL, 0.5 * (lo + hi));
+  const double whole = (hi - lo) / 6.0 * (fa + 4.0 * fm + fb);
+  return sign * simpson(Om, OL, lo, hi, fa, fm, fb, whole, 1e-15 * fabs(whole), 50);
+}
+
+double pm_growth_D(double Om, double OL, double a) {
+  if (!(a > 0.0)) return NAN;
+  // D'' = -gamma D' + beta D in x = ln a (Appendix A), RK4 from the
+  // matter-dominated growing mode D = a at a = 1e-5.
+  const double x0 = log(1e-5), x1 = log(a);
+  const int steps = 20000;
+  const double hstep = (x1 - x0) / steps;
+  double D = 1e-5, dD = 1e-5;
+  auto rhs = [&](double x, double d, double dd, double* o1, double* o2) {
+    const double aa = exp(x), a3 = aa * aa * aa;
+    const double e2 = Om / a3 + OL;
+    const double beta = 1.5 * (Om / a3) / e2, gamma = 0.5 * (1.0 + 3.0 * OL / e2);
+    *o1 = dd;
+    *o2 = -gamma * dd + beta * d;
+  };
+  double x = x0;
+  for (int i = 0; i < steps; ++i) {
+    double k1a, k1b, k2a, k2b, k3a, k3b, k4a, k4b;
+    rhs(x, D, dD, &k1a, &k1b);
+    rhs(x + 0.5 * hstep, D + 0.5 * hstep * k1a, dD + 0.5 * hstep * k1b, &k2a, &k2b);
+    rhs(x + 0.5 * hstep, D + 0.5 * hstep * k2a, dD + 0.5 * hstep * k2b, &k3a, &k3b);
+    rhs(x + hstep, D + hstep * k3a, dD + hstep * k3b, &k4a, &k4b);
+    D += hstep / 6.0 * (k1a + 2 * k2a + 2 * k3a + k4a);
+    dD += hstep / 6.0 * (k1b + 2 * k2b + 2 * k3b + k4b);
+    x += hstep;
+  }
+  return D;
+}
+
+pm_status pm_timing_enable(int on) {
+  if (on && g_timing.start.empty()) {
+    g_timing.start.resize(kTimingCap);
+    g_timing.stop.resize(kTimingCap);
+    g_timing.cls.resize(kTimingCap);
+    for (size_t i = 0; i < kTimingCap; ++i) {
+      PM_TRY(cuda_status(cudaEventCreate(&g_timing.start[i])));
+      PM_TRY(cuda_status(cudaEventCreate(&g_timing.stop[i])));
+    }
+  }
+  g_timing.on = on != 0;
+  g_timing.used = 0;
+  return PM_OK;
+}
+
+int pm_timing_collect(const char** names, double* ms, int64_t* launches, int cap) {
+  if (cudaDeviceSynchronize() != cudaSuccess) return 0;
+  double tot[K_NCLASS] = {0};
+  int64_t cnt[K_NCLASS] = {0};
+  for (size_t i = 0; i < g_timing.used; ++i) {
+    float t = 0.0f;
+    if (cudaEventElapsedTime(&t, g_timing.start[i], g_timing.stop[i]) == cudaSuccess) {
+      tot[g_timing.cls[i]] += t;
+      cnt[g_timing.cls[i]] += 1;
+    }
+  }
+  int k = 0;
+  for (int c = 0; c < K_NCLASS && k < cap; ++c) {
+    if (names) names[k] = kKernelClassNames[c];
+    if (ms) ms[k] = tot[c];
+    if (launches) launches[k] = cnt[c];
+    ++k;
+  }
+  return k;
+}
+
+}  // extern "C"

@@ -1,0 +1,175 @@
+// TSC mass assignment (§3.4) as a deterministic gather over cell-sorted
+// particles, and fixed-order float64 grid reductions.
+//
+// One CTA owns a T^3 tile of destination cells.  Stage 1: for every source
+// cell of the tile plus a one-cell halo, one thread walks that cell's particles
+// in sorted order and accumulates the 27 "moments" m[o] = sum_p W_x W_y W_z
+// (the weight each neighbour o = -1..1 per axis receives) into shared memory.
+// Stage 2: every destination cell sums the 27 moments that point at it, in a
+// fixed order.  No atomics; the result is bitwise reproducible.
+#include "pm_device.cuh"
+#include "pm_internal.cuh"
+
+namespace pmgb {
+
+namespace {
+
+template <int T>
+__global__ void __launch_bounds__(T * T * T) k_deposit(const uint32_t* __restrict__ Xs, int64_t np,
+                                                       const uint32_t* __restrict__ cellstart, int n,
+                                                       int log2n, float scale, float* __restrict__ rho,
+                                                       double* __restrict__ partial) {
+  constexpr int E = T + 2, S = E * E * E, NT = T * T * T;
+  extern __shared__ float M[];  // [27][S]
+  __shared__ double wsum[NT / 32];
+  const int tiles = n / T;
+  const int b = blockIdx.x;
+  const int bz = b % tiles, by = (b / tiles) % tiles, bx = b / (tiles * tiles);
+  const int tid = threadIdx.x;
+  const int mask = n - 1;
+
+  for (int s = tid; s < S; s += NT) {
+    const int sx = s / (E * E), sy = (s / E) % E, sz = s % E;
+    const uint32_t cx = (bx * T + sx - 1) & mask, cy = (by * T + sy - 1) & mask,
+                   cz = (bz * T + sz - 1) & mask;
+    const uint32_t c = (((cx << log2n) | cy) << log2n) | cz;
+    const uint32_t beg = __ldg(cellstart + c), end = __ldg(cellstart + c + 1);
+    float m[27];
+#pragma unroll
+    for (int o = 0; o < 27; ++o) m[o] = 0.0f;
+    for (uint32_t p = beg; p < end; ++p) {
+      float wx[3], wy[3], wz[3];
+      tsc_weights(cell_offset(__ldg(Xs + p), log2n), wx);
+      tsc_weights(cell_offset(__ldg(Xs + np + p), log2n), wy);
+      tsc_weights(cell_offset(__ldg(Xs + 2 * np + p), log2n), wz);
+#pragma unroll
+      for (int ox = 0; ox < 3; ++ox)
+#pragma unroll
+        for (int oy = 0; oy < 3; ++oy) {
+          const float wxy = wx[ox] * wy[oy];
+#pragma unroll
+          for (int oz = 0; oz < 3; ++oz) m[(ox * 3 + oy) * 3 + oz] = fmaf(wxy, wz[oz], m[(ox * 3 + oy) * 3 + oz]);
+        }
+    }
+#pragma unroll
+    for (int o = 0; o < 27; ++o) M[o * S + s] = m[o];
+  }
+  __syncthreads();
+
+  const int tz = tid % T, ty = (tid / T) % T, tx = tid / (T * T);
+  float acc = 0.0f;
+#pragma unroll
+  for (int ox = 0; ox < 3; ++ox)
+#pragma unroll
+    for (int oy = 0; oy < 3; ++oy)
+#pragma unroll
+      for (int oz = 0; oz < 3; ++oz)
+        acc += M[((ox * 3 + oy) * 3 + oz) * S + ((tx + 2 - ox) * E + (ty + 2 - oy)) * E + (tz + 2 - oz)];
+  const float r = acc * scale;
+  const int64_t cell = (((int64_t)(bx * T + tx) << log2n | (by * T + ty)) << log2n) | (bz * T + tz);
+  rho[cell] = r;
+
+  double ws = warp_sum_comp(r);
+  if ((tid & 31) == 0) wsum[tid >> 5] = ws;
+  __syncthreads();
+  if (tid == 0) {
+    double t = 0.0;
+    for (int w = 0; w < NT / 32; ++w) t += wsum[w];
+    partial[b] = t;
+  }
+}
+
+// Sum of a float32 array: per-block float64 partials (fixed order).
+__global__ void __launch_bounds__(256) k_sum_partials(const float* __restrict__ f, int64_t count,
+                                                      double* __restrict__ partial) {
+  __shared__ double wsum[8];
+  float v = 0.0f, c = 0.0f;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    float y = __ldg(f + i) - c;   // Kahan
+    float t = v + y;
+    c = (t - v) - y;
+    v = t;
+  }
+  double ws = warp_sum_comp(v - c);
+  if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = ws;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < 8; ++w) t += wsum[w];
+    partial[blockIdx.x] = t;
+  }
+}
+
+// out[k] = scale * sum_i partial[k * stride + i], i < count, for k < nout
+// (one block, fixed order: strided per-thread sums then a tree).
+__global__ void __launch_bounds__(1024) k_reduce_partials(const double* __restrict__ partial,
+                                                          int64_t count, int64_t stride, int nout,
+                                                          double scale, double* __restrict__ out) {
+  __shared__ double red[1024];
+  for (int k = 0; k < nout; ++k) {
+    double t = 0.0;
+    for (int64_t i = threadIdx.x; i < count; i += blockDim.x) t += partial[k * stride + i];
+    red[threadIdx.x] = t;
+    __syncthreads();
+    for (int o = 512; o > 0; o >>= 1) {
+      if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) out[k] = red[0] * scale;
+    __syncthreads();
+  }
+}
+
+template <int T>
+pm_status launch_deposit(const uint32_t* Xs, int64_t np, const uint32_t* cellstart, int n,
+                         float* rho, double* partials, double* mean_out, cudaStream_t s) {
+  constexpr int E = T + 2;
+  constexpr size_t smem = sizeof(float) * 27 * E * E * E;
+  static bool attr = false;
+  if (!attr) {
+    PM_TRY(cuda_status(cudaFuncSetAttribute(k_deposit<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)smem)));
+    attr = true;
+  }
+  const int tiles = n / T;
+  const int64_t nblocks = (int64_t)tiles * tiles * tiles;
+  const float scale = np > 0 ? (float)((double)n * n * n / (double)np) : 0.0f;
+  PM_LAUNCH(K_DEPOSIT, k_deposit<T>, (unsigned)nblocks, T * T * T, smem, s, Xs, np, cellstart, n,
+            ilog2(n), scale, rho, partials);
+  PM_LAUNCH(K_REDUCE, k_reduce_partials, 1, 1024, 0, s, partials, nblocks, (int64_t)0, 1,
+            1.0 / ((double)n * n * n), mean_out);
+  return launch_status();
+}
+
+}  // namespace
+
+int64_t reduce_partials_capacity(int n, int64_t np) {
+  (void)np;
+  int64_t t = (int64_t)n / 4;
+  int64_t c = t * t * t;               // deposit blocks with 4^3 tiles (upper bound)
+  return c > 152 * 64 ? c : 152 * 64;
+}
+
+pm_status deposit_sorted(const uint32_t* Xs, int64_t np, const uint32_t* cellstart, int n,
+                         float* rho, double* partials, double* mean_out, cudaStream_t s) {
+  if (n >= 8) return launch_deposit<8>(Xs, np, cellstart, n, rho, partials, mean_out, s);
+  return launch_deposit<4>(Xs, np, cellstart, n, rho, partials, mean_out, s);
+}
+
+pm_status grid_mean(const float* f, int64_t count, double* partials, double* mean_out,
+                    cudaStream_t s) {
+  const unsigned nb = grid_for(count, 256, 152 * 8);
+  PM_LAUNCH(K_REDUCE, k_sum_partials, nb, 256, 0, s, f, count, partials);
+  PM_LAUNCH(K_REDUCE, k_reduce_partials, 1, 1024, 0, s, partials, (int64_t)nb, (int64_t)0, 1,
+            1.0 / (double)count, mean_out);
+  return launch_status();
+}
+
+pm_status reduce_partials(const double* partials, int64_t count, int64_t stride, int nout,
+                          double scale, double* out, cudaStream_t s) {
+  PM_LAUNCH(K_REDUCE, k_reduce_partials, 1, 1024, 0, s, partials, count, stride, nout, scale, out);
+  return launch_status();
+}
+
+}  // namespace pmgb

@@ -1,0 +1,354 @@
+// Hu-Sawicki f(R) scalaron (n = 1) by non-linear FAS multigrid (§3.6.2, §3.10).
+//
+// Unknown: eps = u - 1 with u = (f~_R / fbar)^(1/2).  Discrete operator
+//   N_h(eps) = (fbar/h^2) sum_nb (eps_nb - eps)(2 + eps_nb + eps) + kappa eps/(1 + eps)
+// (= (fbar/h^2)(L(u^2) - 6u^2) - kappa (1/u - 1) written in differences, so the
+// O(1) background cancels analytically), equation N_h(eps) = b.
+// Gauss-Seidel: with the neighbours fixed, u solves the depressed cubic
+// u^3 + p u + q = 0 of Eq. fr_depressed_equation; in eps it reads
+//   eps^3 + 3 eps^2 + c1 eps + c0 = 0,
+//   c1 = 2 + beta (b - kappa) - S/6,  c0 = beta b - S/6,
+//   S = sum_nb eps_nb (2 + eps_nb),   beta = h^2 / (6 fbar),  q = beta kappa < 0,
+// whose unique root eps > -1 is found in float32 by safeguarded Newton (the
+// paper evaluates the closed-form root in float64, which the eps form makes
+// unnecessary: no term of size 1 is ever subtracted).
+#include <math.h>
+
+#include "pm_device.cuh"
+#include "pm_internal.cuh"
+
+namespace pmgb {
+
+namespace {
+
+__device__ __forceinline__ float load_mean(const Src& f) { return f.mean ? (float)*f.mean : 0.0f; }
+__device__ __forceinline__ float src_at(const Src& f, int64_t i, float mean) {
+  return f.s * (__ldg(f.p + i) - mean);
+}
+__device__ __forceinline__ int64_t idx3(int i, int j, int k, int log2n) {
+  return ((int64_t)i << (2 * log2n)) | ((int64_t)j << log2n) | k;
+}
+
+// Root eps > -1 of g(e) = e^3 + 3e^2 + c1 e + c0 (g(-1) = q < 0, g convex on
+// e > -1).  Newton from the current value, kept inside a shrinking bracket
+// [lo, hi] with bisection as the fallback; hi starts at the bound
+// u* <= sqrt(max(-p, 0)) + (-q)^(1/3), p = c1 - 3.
+__device__ __forceinline__ float fr_root(float e, float c1, float c0, float q) {
+  float lo = -1.0f;
+  float hi = sqrtf(fmaxf(3.0f - c1, 0.0f)) + cbrtf(-q) - 1.0f;
+  if (!(e > lo && e < hi)) e = hi;
+  for (int it = 0; it < 40; ++it) {
+    const float g = ((e + 3.0f) * e + c1) * e + c0;
+    const float gp = (3.0f * e + 6.0f) * e + c1;
+    if (g > 0.0f) hi = fminf(hi, e);
+    else if (g < 0.0f) lo = fmaxf(lo, e);
+    else return e;
+    float en = gp > 0.0f ? e - __fdividef(g, gp) : 0.5f * (lo + hi);
+    if (!(en > lo && en < hi)) en = 0.5f * (lo + hi);
+    const bool done = fabsf(en - e) <= 1e-7f * fabsf(en) + 1e-30f;
+    e = en;
+    if (done) break;
+  }
+  return e;
+}
+
+__device__ __forceinline__ void load_nb(const float* u, int i, int j, int k, int log2n, float nb[6]) {
+  const int m = (1 << log2n) - 1;
+  nb[0] = u[idx3((i + 1) & m, j, k, log2n)];
+  nb[1] = u[idx3((i - 1) & m, j, k, log2n)];
+  nb[2] = u[idx3(i, (j + 1) & m, k, log2n)];
+  nb[3] = u[idx3(i, (j - 1) & m, k, log2n)];
+  nb[4] = u[idx3(i, j, (k + 1) & m, log2n)];
+  nb[5] = u[idx3(i, j, (k - 1) & m, log2n)];
+}
+
+__device__ __forceinline__ float fr_op(float ec, const float nb[6], float alpha, float kappa) {
+  float L = 0.0f;
+#pragma unroll
+  for (int q = 0; q < 6; ++q) L = fmaf(nb[q] - ec, 2.0f + nb[q] + ec, L);
+  return alpha * L + kappa * ec / (1.0f + ec);
+}
+
+__device__ __forceinline__ float fr_update(float ec, const float nb[6], float bv, float beta, float kappa,
+                                           float q) {
+  float S = 0.0f;
+#pragma unroll
+  for (int t = 0; t < 6; ++t) S = fmaf(nb[t], 2.0f + nb[t], S);
+  const float S6 = S * (1.0f / 6.0f);
+  const float c1 = 2.0f + beta * (bv - kappa) - S6;
+  const float c0 = beta * bv - S6;
+  return fr_root(ec, c1, c0, q);
+}
+
+__global__ void k_fr_sweep(float* __restrict__ e, Src b, int log2n, int colour, float beta, float kappa,
+                           float q) {
+  const int m = (1 << log2n) - 1, half = log2n - 1;
+  const float mean = load_mean(b);
+  const int64_t total = (int64_t)1 << (3 * log2n - 1);
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int kk = (int)(t & ((1 << half) - 1));
+    const int64_t rest = t >> half;
+    const int j = (int)(rest & m), i = (int)(rest >> log2n);
+    const int k = 2 * kk + ((colour + i + j) & 1);
+    const int64_t c = idx3(i, j, k, log2n);
+    float nb[6];
+    load_nb(e, i, j, k, log2n, nb);
+    e[c] = fr_update(e[c], nb, src_at(b, c, mean), beta, kappa, q);
+  }
+}
+
+// eH = rH = R eps, bH = R(b - N_h eps).
+__global__ void k_fr_restrict(const float* __restrict__ e, Src b, int log2n, float alpha, float kappa,
+                              float* __restrict__ eH, float* __restrict__ rH, float* __restrict__ bH) {
+  const int lc = log2n - 1, mc = (1 << lc) - 1;
+  const float mean = load_mean(b);
+  const int64_t total = (int64_t)1 << (3 * lc);
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int K = (int)(t & mc), J = (int)((t >> lc) & mc), I = (int)(t >> (2 * lc));
+    float se = 0.0f, sd = 0.0f;
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+      for (int bb = 0; bb < 2; ++bb)
+#pragma unroll
+        for (int cc = 0; cc < 2; ++cc) {
+          const int i = 2 * I + a, j = 2 * J + bb, k = 2 * K + cc;
+          const int64_t c = idx3(i, j, k, log2n);
+          float nb[6];
+          load_nb(e, i, j, k, log2n, nb);
+          const float ec = e[c];
+          se += ec;
+          sd += src_at(b, c, mean) - fr_op(ec, nb, alpha, kappa);
+        }
+    eH[t] = 0.125f * se;
+    rH[t] = 0.125f * se;
+    bH[t] = 0.125f * sd;
+  }
+}
+
+// bH += N_H(eH).
+__global__ void k_fr_coarse_op(const float* __restrict__ eH, float* __restrict__ bH, int log2n, float alpha,
+                               float kappa) {
+  const int m = (1 << log2n) - 1;
+  const int64_t total = (int64_t)1 << (3 * log2n);
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < total;
+       c += (int64_t)gridDim.x * blockDim.x) {
+    const int k = (int)(c & m), j = (int)((c >> log2n) & m), i = (int)(c >> (2 * log2n));
+    float nb[6];
+    load_nb(eH, i, j, k, log2n, nb);
+    bH[c] += fr_op(eH[c], nb, alpha, kappa);
+  }
+}
+
+__global__ void __launch_bounds__(256) k_fr_norm(const float* __restrict__ e, Src b, int log2n, float alpha,
+                                                 float kappa, double* __restrict__ partial) {
+  __shared__ double scratch[32];
+  const float mean = load_mean(b);
+  const int m = (1 << log2n) - 1;
+  const int64_t total = (int64_t)1 << (3 * log2n);
+  float sd = 0.0f, cd = 0.0f, sb = 0.0f, cb = 0.0f;
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < total;
+       c += (int64_t)gridDim.x * blockDim.x) {
+    const int k = (int)(c & m), j = (int)((c >> log2n) & m), i = (int)(c >> (2 * log2n));
+    float nb[6];
+    load_nb(e, i, j, k, log2n, nb);
+    const float bv = src_at(b, c, mean);
+    const float d = bv - fr_op(e[c], nb, alpha, kappa);
+    kahan_add(sd, cd, d * d);
+    kahan_add(sb, cb, bv * bv);
+  }
+  block_sum_to(partial + blockIdx.x, sd, cd, scratch);
+  block_sum_to(partial + gridDim.x + blockIdx.x, sb, cb, scratch);
+}
+
+// Coarsest level (n <= 16) in one CTA: non-linear sweeps until the residual
+// dropped by `drop` or `max_sweeps` sweeps.
+__global__ void __launch_bounds__(1024) k_fr_coarse(float* __restrict__ e, Src b, int log2n, float alpha,
+                                                    float beta, float kappa, float q, int max_sweeps,
+                                                    float drop) {
+  __shared__ float se[4096], sbv[4096];
+  __shared__ double scratch[32];
+  __shared__ double r2;
+  const int n = 1 << log2n, m = n - 1, N = n * n * n;
+  const float mean = load_mean(b);
+  for (int c = threadIdx.x; c < N; c += blockDim.x) {
+    se[c] = e[c];
+    sbv[c] = src_at(b, c, mean);
+  }
+  __syncthreads();
+  auto nbs = [&](int c, float nb[6]) {
+    const int k = c & m, j = (c >> log2n) & m, i = c >> (2 * log2n);
+    nb[0] = se[(((i + 1) & m) << (2 * log2n)) | (j << log2n) | k];
+    nb[1] = se[(((i - 1) & m) << (2 * log2n)) | (j << log2n) | k];
+    nb[2] = se[(i << (2 * log2n)) | (((j + 1) & m) << log2n) | k];
+    nb[3] = se[(i << (2 * log2n)) | (((j - 1) & m) << log2n) | k];
+    nb[4] = se[(i << (2 * log2n)) | (j << log2n) | ((k + 1) & m)];
+    nb[5] = se[(i << (2 * log2n)) | (j << log2n) | ((k - 1) & m)];
+  };
+  auto norm2 = [&]() -> double {
+    float s = 0.0f, cmp = 0.0f;
+    for (int c = threadIdx.x; c < N; c += blockDim.x) {
+      float nb[6];
+      nbs(c, nb);
+      const float d = sbv[c] - fr_op(se[c], nb, alpha, kappa);
+      kahan_add(s, cmp, d * d);
+    }
+    block_sum_to(&r2, s, cmp, scratch);
+    return r2;
+  };
+  const double target = (double)drop * (double)drop * norm2();
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    for (int colour = 0; colour < 2; ++colour) {
+      for (int c = threadIdx.x; c < N; c += blockDim.x) {
+        const int k = c & m, j = (c >> log2n) & m, i = c >> (2 * log2n);
+        if (((i + j + k) & 1) != colour) continue;
+        float nb[6];
+        nbs(c, nb);
+        se[c] = fr_update(se[c], nb, sbv[c], beta, kappa, q);
+      }
+      __syncthreads();
+    }
+    if (norm2() <= target) break;
+  }
+  for (int c = threadIdx.x; c < N; c += blockDim.x) e[c] = se[c];
+}
+
+struct FR {
+  int n0;
+  const fr_params* p;
+  cudaStream_t s;
+  float* e[12];
+  float* r[12];
+  Src b[12];
+  double fbar, kappa;
+};
+
+struct LevelConst {
+  int n, log2n;
+  float alpha, beta, kappa, q;
+};
+
+LevelConst level_const(const FR& f, int l) {
+  LevelConst c;
+  c.n = f.n0 >> l;
+  c.log2n = ilog2(c.n);
+  const double h = 1.0 / c.n, h2 = h * h;
+  c.alpha = (float)(f.fbar / h2);
+  c.beta = (float)(h2 / (6.0 * f.fbar));
+  c.kappa = (float)f.kappa;
+  c.q = (float)(h2 * f.kappa / (6.0 * f.fbar));
+  return c;
+}
+
+pm_status fr_smooth(FR& f, int l, int count) {
+  const LevelConst c = level_const(f, l);
+  const unsigned grid = grid_for(((int64_t)c.n * c.n * c.n) / 2, 256);
+  for (int it = 0; it < count; ++it)
+    for (int colour = 0; colour < 2; ++colour)
+      PM_LAUNCH(K_FR_SMOOTH, k_fr_sweep, grid, 256, 0, f.s, f.e[l], f.b[l], c.log2n, colour, c.beta, c.kappa,
+                c.q);
+  return PM_OK;
+}
+
+bool is_coarsest(const FR& f, int l) {
+  const int n = f.n0 >> l;
+  return n <= f.p->coarsest || n <= 4;
+}
+
+pm_status fr_coarse(FR& f, int l) {
+  const LevelConst c = level_const(f, l);
+  PM_LAUNCH(K_FR_COARSE, k_fr_coarse, 1, 1024, 0, f.s, f.e[l], f.b[l], c.log2n, c.alpha, c.beta, c.kappa,
+            c.q, f.p->coarse_max_sweeps, f.p->coarse_drop);
+  return PM_OK;
+}
+
+// Pre-smooth level l, then build the FAS coarse problem on level l + 1.
+pm_status fr_to_coarse(FR& f, int l) {
+  PM_TRY(fr_smooth(f, l, f.p->npre));
+  const LevelConst c = level_const(f, l), cH = level_const(f, l + 1);
+  const int64_t nc = (int64_t)cH.n * cH.n * cH.n;
+  PM_LAUNCH(K_FR_RESTRICT, k_fr_restrict, grid_for(nc, 256), 256, 0, f.s, f.e[l], f.b[l], c.log2n, c.alpha,
+            c.kappa, f.e[l + 1], f.r[l + 1], const_cast<float*>(f.b[l + 1].p));
+  PM_LAUNCH(K_FR_COARSEOP, k_fr_coarse_op, grid_for(nc, 256), 256, 0, f.s, f.e[l + 1],
+            const_cast<float*>(f.b[l + 1].p), cH.log2n, cH.alpha, cH.kappa);
+  return PM_OK;
+}
+
+pm_status fr_v(FR& f, int l) {
+  if (is_coarsest(f, l)) return fr_coarse(f, l);
+  PM_TRY(fr_to_coarse(f, l));
+  PM_TRY(fr_v(f, l + 1));
+  PM_TRY(prolong_correct_launch(f.e[l], f.e[l + 1], f.r[l + 1], f.n0 >> l, K_FR_PROLONG, f.s));
+  return fr_smooth(f, l, f.p->npost);
+}
+
+pm_status fr_f(FR& f, int l) {
+  if (is_coarsest(f, l)) return fr_coarse(f, l);
+  PM_TRY(fr_to_coarse(f, l));
+  PM_TRY(fr_f(f, l + 1));
+  PM_TRY(prolong_correct_launch(f.e[l], f.e[l + 1], f.r[l + 1], f.n0 >> l, K_FR_PROLONG, f.s));
+  return fr_v(f, l);
+}
+
+}  // namespace
+
+void fr_background(const fr_params& p, double* fbar, double* kappa, double* c2) {
+  const double a = p.a;
+  const double Rbar = 3.0 * p.Om * (1.0 / (a * a * a) + 4.0 * p.OL / p.Om);
+  const double Rbar0 = 3.0 * p.Om * (1.0 + 4.0 * p.OL / p.Om);
+  const double ratio = Rbar0 / Rbar;
+  *fbar = a * a * p.fR0 * ratio * ratio;
+  const double ct = 299792.458 / (100.0 * p.boxsize);
+  *c2 = ct * ct;
+  *kappa = a * a * a * a * Rbar / (3.0 * *c2);
+}
+
+pm_status fr_solve_src(Src b, float* eps, int n, const fr_params& prm, mg_stats* st, Workspace& w,
+                       cudaStream_t s) {
+  FR f;
+  f.n0 = n;
+  f.p = &prm;
+  f.s = s;
+  f.e[0] = eps;
+  f.r[0] = nullptr;
+  f.b[0] = b;
+  for (int l = 1; l < 12; ++l) {
+    f.e[l] = w.fr_e[l];
+    f.r[l] = w.fr_r[l];
+    f.b[l] = Src{w.fr_b[l], 1.0f, nullptr};
+  }
+  double c2;
+  fr_background(prm, &f.fbar, &f.kappa, &c2);
+  mg_stats local{PM_OK, 0, -1.0, -1.0, -1.0};
+  auto one = [&]() { return prm.cycle == 1 ? fr_f(f, 0) : fr_v(f, 0); };
+  if (prm.tol <= 0.0) {
+    for (int c = 0; c < prm.cycles; ++c) PM_TRY(one());
+    local.cycles = prm.cycles;
+    if (st) *st = local;
+    return launch_status();
+  }
+  const LevelConst c0 = level_const(f, 0);
+  const int64_t N = (int64_t)n * n * n;
+  const unsigned nb = grid_for(N, 256, 152 * 8);
+  pm_status status = PM_ENOCONV;
+  for (int c = 0; c < prm.max_cycles; ++c) {
+    PM_TRY(one());
+    local.cycles = c + 1;
+    PM_LAUNCH(K_FR_NORM, k_fr_norm, nb, 256, 0, s, eps, b, c0.log2n, c0.alpha, c0.kappa, w.partials);
+    PM_TRY(reduce_partials(w.partials, nb, nb, 2, 1.0, w.scalars + 8, s));
+    double h[2];
+    PM_TRY(fetch_scalars(w.scalars + 8, h, 2, s));
+    local.res = sqrt(h[0]);
+    local.norm_f = sqrt(h[1]);
+    if (!isfinite(local.res)) { status = PM_ENAN; break; }
+    if (local.res <= prm.tol * local.norm_f) { status = PM_OK; break; }
+  }
+  local.status = status;
+  if (st) *st = local;
+  PM_TRY(launch_status());
+  return status;
+}
+
+}  // namespace pmgb

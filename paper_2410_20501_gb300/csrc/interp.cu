@@ -1,0 +1,157 @@
+// Force from the potential and its interpolation to the particles:
+//  - g = -grad(Phi) with the central stencils of Table 1, where for f(R)
+//    Phi = phi + alpha (2 eps + eps^2), alpha = -(c~^2/2) fbar, i.e. the
+//    force F = F_N + (c~^2/2) grad f~_R of §3.10 (the constant background part
+//    of f~_R = fbar (1 + eps)^2 has no gradient);
+//  - inverse TSC (§3.4) at the cell-sorted particles, optionally fused with
+//    the kick v += a dt_kick and the drift x += v dt_drift on uint32
+//    fixed-point positions (exact periodic wrap).
+#include "pm_device.cuh"
+#include "pm_internal.cuh"
+
+namespace pmgb {
+
+namespace {
+
+__device__ __forceinline__ int64_t idx3(int i, int j, int k, int log2n) {
+  return ((int64_t)i << (2 * log2n)) | ((int64_t)j << log2n) | k;
+}
+
+template <bool FR>
+__device__ __forceinline__ float pot(const float* __restrict__ phi, const float* __restrict__ eps, float alpha,
+                                     int64_t c) {
+  float v = __ldg(phi + c);
+  if (FR) {
+    const float e = __ldg(eps + c);
+    v = fmaf(alpha, e * (2.0f + e), v);
+  }
+  return v;
+}
+
+// Table 1 coefficients c_1..c_3 of the antisymmetric central derivative
+// (1/h) sum_k c_k (u_{i+k} - u_{i-k}).
+template <int ORDER> struct Stencil;
+template <> struct Stencil<3> { static constexpr int R = 1; __device__ static float c(int k) { return 0.5f; } };
+template <> struct Stencil<5> {
+  static constexpr int R = 2;
+  __device__ static float c(int k) { return k == 1 ? 2.0f / 3.0f : -1.0f / 12.0f; }
+};
+template <> struct Stencil<7> {
+  static constexpr int R = 3;
+  __device__ static float c(int k) { return k == 1 ? 0.75f : (k == 2 ? -0.15f : 1.0f / 60.0f); }
+};
+
+template <int ORDER, bool FR>
+__global__ void k_gradient(const float* __restrict__ phi, const float* __restrict__ eps, float alpha,
+                           float* __restrict__ g, int log2n, float inv_h) {
+  const int m = (1 << log2n) - 1;
+  const int64_t total = (int64_t)1 << (3 * log2n);
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < total;
+       c += (int64_t)gridDim.x * blockDim.x) {
+    const int k = (int)(c & m), j = (int)((c >> log2n) & m), i = (int)(c >> (2 * log2n));
+    float gx = 0.0f, gy = 0.0f, gz = 0.0f;
+#pragma unroll
+    for (int q = Stencil<ORDER>::R; q >= 1; --q) {
+      const float w = Stencil<ORDER>::c(q);
+      gx = fmaf(w, pot<FR>(phi, eps, alpha, idx3((i + q) & m, j, k, log2n)) -
+                       pot<FR>(phi, eps, alpha, idx3((i - q) & m, j, k, log2n)), gx);
+      gy = fmaf(w, pot<FR>(phi, eps, alpha, idx3(i, (j + q) & m, k, log2n)) -
+                       pot<FR>(phi, eps, alpha, idx3(i, (j - q) & m, k, log2n)), gy);
+      gz = fmaf(w, pot<FR>(phi, eps, alpha, idx3(i, j, (k + q) & m, log2n)) -
+                       pot<FR>(phi, eps, alpha, idx3(i, j, (k - q) & m, log2n)), gz);
+    }
+    const int64_t N = total;
+    g[c] = -gx * inv_h;
+    g[N + c] = -gy * inv_h;
+    g[2 * N + c] = -gz * inv_h;
+  }
+}
+
+// Inverse TSC; mode 1 also kicks and drifts.  Particles are read in cell
+// order (Xs, Vs) and written in the same order (Xo, Vo).
+__global__ void __launch_bounds__(256) k_interp_kdk(const float* __restrict__ g, const uint32_t* __restrict__ Xs,
+                                                    const float* __restrict__ Vs,
+                                                    const uint32_t* __restrict__ ids_in, int64_t np, int log2n,
+                                                    float* __restrict__ acc, uint32_t* __restrict__ Xo,
+                                                    float* __restrict__ Vo, uint32_t* __restrict__ ids_out,
+                                                    float dt_kick, float drift_scale, int mode) {
+  const int m = (1 << log2n) - 1, sh = 32 - log2n;
+  const int64_t N = (int64_t)1 << (3 * log2n);
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < np;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t x = __ldg(Xs + p), y = __ldg(Xs + np + p), z = __ldg(Xs + 2 * np + p);
+    float wx[3], wy[3], wz[3];
+    tsc_weights(cell_offset(x, log2n), wx);
+    tsc_weights(cell_offset(y, log2n), wy);
+    tsc_weights(cell_offset(z, log2n), wz);
+    const int ix = (int)(x >> sh), iy = (int)(y >> sh), iz = (int)(z >> sh);
+    float ax = 0.0f, ay = 0.0f, az = 0.0f;
+#pragma unroll
+    for (int ox = 0; ox < 3; ++ox) {
+      const int ci = (ix + ox - 1) & m;
+#pragma unroll
+      for (int oy = 0; oy < 3; ++oy) {
+        const int cj = (iy + oy - 1) & m;
+        const float wxy = wx[ox] * wy[oy];
+#pragma unroll
+        for (int oz = 0; oz < 3; ++oz) {
+          const int64_t c = idx3(ci, cj, (iz + oz - 1) & m, log2n);
+          const float w = wxy * wz[oz];
+          ax = fmaf(w, __ldg(g + c), ax);
+          ay = fmaf(w, __ldg(g + N + c), ay);
+          az = fmaf(w, __ldg(g + 2 * N + c), az);
+        }
+      }
+    }
+    if (acc) {
+      acc[p] = ax;
+      acc[np + p] = ay;
+      acc[2 * np + p] = az;
+    }
+    if (mode == 1) {
+      const float vx = fmaf(ax, dt_kick, __ldg(Vs + p));
+      const float vy = fmaf(ay, dt_kick, __ldg(Vs + np + p));
+      const float vz = fmaf(az, dt_kick, __ldg(Vs + 2 * np + p));
+      Vo[p] = vx;
+      Vo[np + p] = vy;
+      Vo[2 * np + p] = vz;
+      Xo[p] = x + (uint32_t)__float2int_rn(vx * drift_scale);
+      Xo[np + p] = y + (uint32_t)__float2int_rn(vy * drift_scale);
+      Xo[2 * np + p] = z + (uint32_t)__float2int_rn(vz * drift_scale);
+      if (ids_out) ids_out[p] = __ldg(ids_in + p);
+    }
+  }
+}
+
+template <int ORDER>
+void launch_grad(const float* phi, const float* eps, float alpha, float* g, int n, cudaStream_t s) {
+  const int64_t N = (int64_t)n * n * n;
+  const unsigned grid = grid_for(N, 256);
+  if (eps)
+    PM_LAUNCH(K_GRADIENT, (k_gradient<ORDER, true>), grid, 256, 0, s, phi, eps, alpha, g, ilog2(n), (float)n);
+  else
+    PM_LAUNCH(K_GRADIENT, (k_gradient<ORDER, false>), grid, 256, 0, s, phi, eps, alpha, g, ilog2(n), (float)n);
+}
+
+}  // namespace
+
+pm_status gradient_launch(const float* phi, const float* eps, float alpha, float* g, int n, int order,
+                          cudaStream_t s) {
+  if (order == 3) launch_grad<3>(phi, eps, alpha, g, n, s);
+  else if (order == 5) launch_grad<5>(phi, eps, alpha, g, n, s);
+  else if (order == 7) launch_grad<7>(phi, eps, alpha, g, n, s);
+  else return PM_EINVAL;
+  return launch_status();
+}
+
+pm_status interp_launch(const float* g, const uint32_t* Xs, const float* Vs, const uint32_t* ids_in, int64_t np,
+                        int n, float* acc, uint32_t* Xo, float* Vo, uint32_t* ids_out, float dt_kick,
+                        float dt_drift, int mode, cudaStream_t s) {
+  if (np == 0) return PM_OK;
+  const float drift_scale = (float)((double)dt_drift * 4294967296.0);
+  PM_LAUNCH(K_INTERP, k_interp_kdk, grid_for(np, 256), 256, 0, s, g, Xs, Vs, ids_in, np, ilog2(n), acc, Xo, Vo,
+            ids_out, dt_kick, drift_scale, mode);
+  return launch_status();
+}
+
+}  // namespace pmgb

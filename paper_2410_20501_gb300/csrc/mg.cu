@@ -1,0 +1,387 @@
+// Linear multigrid for the periodic 7-point Poisson problem (§3.5, §3.6.1):
+// red-black SOR smoothing (Eq. jacobi_sweep_laplacian with over-relaxation),
+// residual + 8-child-average restriction, 27/9/3/1 prolongation and
+// correction, a single-CTA coarsest-level solve, V-cycles.
+//
+// Precision: smoothing and transfers in float32.  The finest-level residual is
+// formed as sum_nb (u_nb - u) with every difference and partial sum kept
+// exactly (TwoSum), so the float32-stored iterate is tested against f with
+// float64-class accuracy; norms are accumulated in float64.
+#include <math.h>
+
+#include "pm_device.cuh"
+#include "pm_internal.cuh"
+
+namespace pmgb {
+
+namespace {
+
+constexpr float kSixth = 1.0f / 6.0f;
+
+__device__ __forceinline__ float load_mean(const Src& f) { return f.mean ? (float)*f.mean : 0.0f; }
+__device__ __forceinline__ float src_at(const Src& f, int64_t i, float mean) {
+  return f.s * (__ldg(f.p + i) - mean);
+}
+
+__device__ __forceinline__ int64_t idx3(int i, int j, int k, int log2n) {
+  return ((int64_t)i << (2 * log2n)) | ((int64_t)j << log2n) | k;
+}
+
+// sum_nb (u_nb - u) with TwoSum on every difference and partial sum: S + E.
+__device__ __forceinline__ void lap_diff_comp(float uc, const float nb[6], float& S, float& E) {
+  float s, e, t;
+  two_sum(nb[0], -uc, S, E);
+#pragma unroll
+  for (int q = 1; q < 6; ++q) {
+    two_sum(nb[q], -uc, s, e);
+    two_sum(S, s, S, t);
+    E += t + e;
+  }
+}
+
+__device__ __forceinline__ void load_nb(const float* __restrict__ u, int i, int j, int k, int log2n,
+                                        float nb[6]) {
+  const int m = (1 << log2n) - 1;
+  nb[0] = __ldg(u + idx3((i + 1) & m, j, k, log2n));
+  nb[1] = __ldg(u + idx3((i - 1) & m, j, k, log2n));
+  nb[2] = __ldg(u + idx3(i, (j + 1) & m, k, log2n));
+  nb[3] = __ldg(u + idx3(i, (j - 1) & m, k, log2n));
+  nb[4] = __ldg(u + idx3(i, j, (k + 1) & m, log2n));
+  nb[5] = __ldg(u + idx3(i, j, (k - 1) & m, log2n));
+}
+
+// u = -h^2 f / 6 (Eq. multigrid_initial_guess).
+__global__ void k_jacobi_guess(float* __restrict__ u, Src f, int64_t count, float h2) {
+  const float mean = load_mean(f);
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < count;
+       c += (int64_t)gridDim.x * blockDim.x)
+    u[c] = -h2 * src_at(f, c, mean) * kSixth;
+}
+
+__global__ void k_scale(float* __restrict__ u, int64_t count, float a) {
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < count;
+       c += (int64_t)gridDim.x * blockDim.x)
+    u[c] *= a;
+}
+
+// One colour of a red-black SOR sweep.  zero_guess: u is taken as 0 (the
+// coarse-level error starts from zero); gscale multiplies every value read
+// (fuses the warm-start rescale into the first sweep).
+__global__ void k_rb_sweep(float* __restrict__ u, Src f, int log2n, int colour, float omega,
+                           float h2, float gscale, int zero_guess) {
+  const int m = (1 << log2n) - 1, half = log2n - 1;
+  const float mean = load_mean(f);
+  const int64_t total = (int64_t)1 << (3 * log2n - 1);
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int kk = (int)(t & ((1 << half) - 1));
+    const int64_t rest = t >> half;
+    const int j = (int)(rest & m), i = (int)(rest >> log2n);
+    const int k = 2 * kk + ((colour + i + j) & 1);
+    const int64_t c = idx3(i, j, k, log2n);
+    const float fv = src_at(f, c, mean);
+    float unew;
+    if (zero_guess) {
+      unew = omega * (-h2 * fv) * kSixth;
+    } else {
+      const float s = u[idx3((i + 1) & m, j, k, log2n)] + u[idx3((i - 1) & m, j, k, log2n)] +
+                      u[idx3(i, (j + 1) & m, k, log2n)] + u[idx3(i, (j - 1) & m, k, log2n)] +
+                      u[idx3(i, j, (k + 1) & m, log2n)] + u[idx3(i, j, (k - 1) & m, log2n)];
+      const float ugs = (gscale * s - h2 * fv) * kSixth;
+      unew = (omega == 1.0f) ? ugs : omega * ugs + (1.0f - omega) * (gscale * u[c]);
+    }
+    u[c] = unew;
+  }
+}
+
+// Coarse right-hand side fc = R(f - L u): residual of the 8 children, averaged.
+template <bool COMP>
+__global__ void k_resid_restrict(const float* __restrict__ u, Src f, int log2n, float inv_h2,
+                                 float* __restrict__ fc) {
+  const int lc = log2n - 1, mc = (1 << lc) - 1;
+  const float mean = load_mean(f);
+  const int64_t total = (int64_t)1 << (3 * lc);
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int K = (int)(t & mc), J = (int)((t >> lc) & mc), I = (int)(t >> (2 * lc));
+    float sum = 0.0f;
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+      for (int b = 0; b < 2; ++b)
+#pragma unroll
+        for (int cc = 0; cc < 2; ++cc) {
+          const int i = 2 * I + a, j = 2 * J + b, k = 2 * K + cc;
+          const int64_t c = idx3(i, j, k, log2n);
+          float nb[6];
+          load_nb(u, i, j, k, log2n, nb);
+          const float uc = __ldg(u + c), fv = src_at(f, c, mean);
+          float d;
+          if (COMP) {
+            float S, E;
+            lap_diff_comp(uc, nb, S, E);
+            d = fmaf(-inv_h2, S, fv) - inv_h2 * E;
+          } else {
+            const float L = ((nb[0] - uc) + (nb[1] - uc)) + ((nb[2] - uc) + (nb[3] - uc)) +
+                            ((nb[4] - uc) + (nb[5] - uc));
+            d = fv - inv_h2 * L;
+          }
+          sum += d;
+        }
+    fc[t] = 0.125f * sum;
+  }
+}
+
+// Residual norm^2 and source norm^2 partials (finest level, compensated
+// residual): partial[blockIdx] and partial[gridDim + blockIdx].
+__global__ void __launch_bounds__(256) k_resid_norm(const float* __restrict__ u, Src f, int log2n,
+                                                    float inv_h2, double* __restrict__ partial) {
+  __shared__ double scratch[32];
+  const float mean = load_mean(f);
+  const int m = (1 << log2n) - 1;
+  const int64_t total = (int64_t)1 << (3 * log2n);
+  float sd = 0.0f, cd = 0.0f, sf = 0.0f, cf = 0.0f;
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < total;
+       c += (int64_t)gridDim.x * blockDim.x) {
+    const int k = (int)(c & m), j = (int)((c >> log2n) & m), i = (int)(c >> (2 * log2n));
+    float nb[6];
+    load_nb(u, i, j, k, log2n, nb);
+    const float uc = __ldg(u + c), fv = src_at(f, c, mean);
+    float S, E;
+    lap_diff_comp(uc, nb, S, E);
+    const float d = fmaf(-inv_h2, S, fv) - inv_h2 * E;
+    kahan_add(sd, cd, d * d);
+    kahan_add(sf, cf, fv * fv);
+  }
+  block_sum_to(partial + blockIdx.x, sd, cd, scratch);
+  block_sum_to(partial + gridDim.x + blockIdx.x, sf, cf, scratch);
+}
+
+// u += P(uc - uc2): cell-centred trilinear prolongation, weights 27/9/3/1 over
+// 64 (§3.6.1); uc2 may be NULL.
+__global__ void k_prolong_correct(float* __restrict__ u, const float* __restrict__ uc,
+                                  const float* __restrict__ uc2, int log2n) {
+  const int m = (1 << log2n) - 1, lc = log2n - 1, mc = (1 << lc) - 1;
+  const int64_t total = (int64_t)1 << (3 * log2n);
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < total;
+       c += (int64_t)gridDim.x * blockDim.x) {
+    const int k = (int)(c & m), j = (int)((c >> log2n) & m), i = (int)(c >> (2 * log2n));
+    const int I0 = i >> 1, J0 = j >> 1, K0 = k >> 1;
+    const int I1 = (i & 1) ? ((I0 + 1) & mc) : ((I0 - 1) & mc);
+    const int J1 = (j & 1) ? ((J0 + 1) & mc) : ((J0 - 1) & mc);
+    const int K1 = (k & 1) ? ((K0 + 1) & mc) : ((K0 - 1) & mc);
+    const int Is[2] = {I0, I1}, Js[2] = {J0, J1}, Ks[2] = {K0, K1};
+    const float w[2] = {0.75f, 0.25f};
+    float v = 0.0f;
+#pragma unroll
+    for (int a = 0; a < 2; ++a) {
+      float vy = 0.0f;
+#pragma unroll
+      for (int b = 0; b < 2; ++b) {
+        float vz = 0.0f;
+#pragma unroll
+        for (int cc = 0; cc < 2; ++cc) {
+          const int64_t q = idx3(Is[a], Js[b], Ks[cc], lc);
+          float x = __ldg(uc + q);
+          if (uc2) x -= __ldg(uc2 + q);
+          vz = fmaf(w[cc], x, vz);
+        }
+        vy = fmaf(w[b], vz, vy);
+      }
+      v = fmaf(w[a], vy, v);
+    }
+    u[c] += v;
+  }
+}
+
+// Coarsest level (n <= 16) in one CTA: red-black SOR sweeps until the residual
+// norm dropped by `drop` or `max_sweeps` sweeps.
+__global__ void __launch_bounds__(1024) k_mg_coarse(float* __restrict__ u, Src f, int log2n, float h2,
+                                                    float omega, int max_sweeps, float drop,
+                                                    int zero_guess) {
+  __shared__ float su[4096], sf[4096];
+  __shared__ double scratch[32];
+  __shared__ double r2;
+  const int n = 1 << log2n, m = n - 1, N = n * n * n;
+  const float mean = load_mean(f);
+  for (int c = threadIdx.x; c < N; c += blockDim.x) {
+    su[c] = zero_guess ? 0.0f : u[c];
+    sf[c] = src_at(f, c, mean);
+  }
+  __syncthreads();
+  auto norm2 = [&]() -> double {
+    float s = 0.0f, cmp = 0.0f;
+    for (int c = threadIdx.x; c < N; c += blockDim.x) {
+      const int k = c & m, j = (c >> log2n) & m, i = c >> (2 * log2n);
+      const float uc = su[c];
+      const float L = (su[(((i + 1) & m) << (2 * log2n)) | (j << log2n) | k] - uc) +
+                      (su[(((i - 1) & m) << (2 * log2n)) | (j << log2n) | k] - uc) +
+                      (su[(i << (2 * log2n)) | (((j + 1) & m) << log2n) | k] - uc) +
+                      (su[(i << (2 * log2n)) | (((j - 1) & m) << log2n) | k] - uc) +
+                      (su[(i << (2 * log2n)) | (j << log2n) | ((k + 1) & m)] - uc) +
+                      (su[(i << (2 * log2n)) | (j << log2n) | ((k - 1) & m)] - uc);
+      const float d = sf[c] - L / h2;
+      kahan_add(s, cmp, d * d);
+    }
+    block_sum_to(&r2, s, cmp, scratch);
+    return r2;
+  };
+  const double r0 = norm2();
+  const double target = (double)drop * (double)drop * r0;
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    for (int colour = 0; colour < 2; ++colour) {
+      for (int c = threadIdx.x; c < N; c += blockDim.x) {
+        const int k = c & m, j = (c >> log2n) & m, i = c >> (2 * log2n);
+        if (((i + j + k) & 1) != colour) continue;
+        const float s = su[(((i + 1) & m) << (2 * log2n)) | (j << log2n) | k] +
+                        su[(((i - 1) & m) << (2 * log2n)) | (j << log2n) | k] +
+                        su[(i << (2 * log2n)) | (((j + 1) & m) << log2n) | k] +
+                        su[(i << (2 * log2n)) | (((j - 1) & m) << log2n) | k] +
+                        su[(i << (2 * log2n)) | (j << log2n) | ((k + 1) & m)] +
+                        su[(i << (2 * log2n)) | (j << log2n) | ((k - 1) & m)];
+        const float ugs = (s - h2 * sf[c]) * kSixth;
+        su[c] = (omega == 1.0f) ? ugs : omega * ugs + (1.0f - omega) * su[c];
+      }
+      __syncthreads();
+    }
+    if (norm2() <= target) break;
+  }
+  for (int c = threadIdx.x; c < N; c += blockDim.x) u[c] = su[c];
+}
+
+struct MG {
+  int n0;
+  const mg_params* p;
+  cudaStream_t s;
+  float* u[12];
+  Src f[12];
+  bool first_cycle;
+  float gscale;
+};
+
+pm_status sweep(MG& g, int l, float omega, bool zero_guess, float gscale) {
+  const int n = g.n0 >> l, log2n = ilog2(n);
+  const float h2 = 1.0f / ((float)n * (float)n);
+  const int64_t half = ((int64_t)n * n * n) / 2;
+  const unsigned grid = grid_for(half, 256);
+  PM_LAUNCH(K_MG_SMOOTH, k_rb_sweep, grid, 256, 0, g.s, g.u[l], g.f[l], log2n, 0, omega, h2, gscale,
+            zero_guess ? 1 : 0);
+  PM_LAUNCH(K_MG_SMOOTH, k_rb_sweep, grid, 256, 0, g.s, g.u[l], g.f[l], log2n, 1, omega, h2, 1.0f, 0);
+  return PM_OK;
+}
+
+pm_status v_cycle(MG& g, int l, bool zero_guess) {
+  const int n = g.n0 >> l, log2n = ilog2(n);
+  const mg_params& p = *g.p;
+  const float h2 = 1.0f / ((float)n * (float)n);
+  if (n <= p.coarsest || n <= 4) {
+    float* u = g.u[l];
+    if (!zero_guess && l == 0 && g.first_cycle && g.gscale != 1.0f) {
+      const int64_t N = (int64_t)n * n * n;
+      PM_LAUNCH(K_MG_GUESS, k_scale, grid_for(N, 256), 256, 0, g.s, u, N, g.gscale);
+    }
+    PM_LAUNCH(K_MG_COARSE, k_mg_coarse, 1, 1024, 0, g.s, u, g.f[l], log2n, h2, p.omega,
+              p.coarse_max_sweeps, p.coarse_drop, zero_guess ? 1 : 0);
+    return PM_OK;
+  }
+  const bool fuse_scale = (l == 0 && g.first_cycle && g.gscale != 1.0f);
+  if (p.npre == 0) {
+    const int64_t N = (int64_t)n * n * n;
+    if (zero_guess) PM_TRY(cuda_status(cudaMemsetAsync(g.u[l], 0, N * sizeof(float), g.s)));
+    else if (fuse_scale) PM_LAUNCH(K_MG_GUESS, k_scale, grid_for(N, 256), 256, 0, g.s, g.u[l], N, g.gscale);
+  }
+  for (int si = 0; si < p.npre; ++si) {
+    const float om = si == 0 ? 1.0f : p.omega;
+    PM_TRY(sweep(g, l, om, zero_guess && si == 0, (fuse_scale && si == 0) ? g.gscale : 1.0f));
+  }
+  const int64_t nc = ((int64_t)n * n * n) / 8;
+  const unsigned grid = grid_for(nc, 256);
+  if (l == 0)
+    PM_LAUNCH(K_MG_RESTRICT, k_resid_restrict<true>, grid, 256, 0, g.s, g.u[l], g.f[l], log2n,
+              (float)n * (float)n, const_cast<float*>(g.f[l + 1].p));
+  else
+    PM_LAUNCH(K_MG_RESTRICT, k_resid_restrict<false>, grid, 256, 0, g.s, g.u[l], g.f[l], log2n,
+              (float)n * (float)n, const_cast<float*>(g.f[l + 1].p));
+  PM_TRY(v_cycle(g, l + 1, true));
+  PM_LAUNCH(K_MG_PROLONG, k_prolong_correct, grid_for(nc * 8, 256), 256, 0, g.s, g.u[l], g.u[l + 1],
+            (const float*)nullptr, log2n);
+  for (int si = 0; si < p.npost; ++si) {
+    const float om = si == p.npost - 1 ? 1.0f : p.omega;
+    PM_TRY(sweep(g, l, om, false, 1.0f));
+  }
+  return PM_OK;
+}
+
+}  // namespace
+
+pm_status prolong_correct_launch(float* u, const float* uc, const float* uc2, int n_fine, int cls,
+                                 cudaStream_t s) {
+  const int64_t N = (int64_t)n_fine * n_fine * n_fine;
+  PM_LAUNCH(cls, k_prolong_correct, grid_for(N, 256), 256, 0, s, u, uc, uc2, ilog2(n_fine));
+  return PM_OK;
+}
+
+pm_status fetch_scalars(const double* dev, double* host, int count, cudaStream_t s) {
+  static double* pinned = nullptr;
+  if (!pinned) PM_TRY(cuda_status(cudaHostAlloc((void**)&pinned, 64 * sizeof(double), cudaHostAllocDefault)));
+  PM_TRY(cuda_status(cudaMemcpyAsync(pinned, dev, count * sizeof(double), cudaMemcpyDeviceToHost, s)));
+  PM_TRY(cuda_status(cudaStreamSynchronize(s)));
+  for (int i = 0; i < count; ++i) host[i] = pinned[i];
+  return PM_OK;
+}
+
+pm_status mg_solve_src(Src f, float* phi, int n, const mg_params& prm, mg_stats* st, Workspace& w,
+                       cudaStream_t s) {
+  MG g;
+  g.n0 = n;
+  g.p = &prm;
+  g.s = s;
+  g.u[0] = phi;
+  g.f[0] = f;
+  for (int l = 1; l < 12; ++l) {
+    g.u[l] = w.mg_u[l];
+    g.f[l] = Src{w.mg_f[l], 1.0f, nullptr};
+  }
+  g.first_cycle = true;
+  g.gscale = prm.first_guess == MG_GUESS_SCALED ? prm.guess_scale : 1.0f;
+  const int64_t N = (int64_t)n * n * n;
+  const float h2 = 1.0f / ((float)n * (float)n);
+  if (prm.first_guess == MG_GUESS_JACOBI)
+    PM_LAUNCH(K_MG_GUESS, k_jacobi_guess, grid_for(N, 256), 256, 0, s, phi, f, N, h2);
+  mg_stats local{PM_OK, 0, -1.0, -1.0, -1.0};
+  if (prm.fixed_cycles > 0) {
+    for (int c = 0; c < prm.fixed_cycles; ++c) {
+      PM_TRY(v_cycle(g, 0, false));
+      g.first_cycle = false;
+    }
+    local.cycles = prm.fixed_cycles;
+    if (st) *st = local;
+    return launch_status();
+  }
+  const int log2n = ilog2(n);
+  const unsigned nb = grid_for(N, 256, 152 * 8);
+  double prev = -1.0;
+  pm_status status = PM_ENOCONV;
+  for (int c = 0; c < prm.max_cycles; ++c) {
+    PM_TRY(v_cycle(g, 0, false));
+    g.first_cycle = false;
+    local.cycles = c + 1;
+    PM_LAUNCH(K_MG_NORM, k_resid_norm, nb, 256, 0, s, phi, f, log2n, (float)n * (float)n, w.partials);
+    PM_TRY(reduce_partials(w.partials, nb, nb, 2, 1.0, w.scalars + 4, s));
+    double h[2];
+    PM_TRY(fetch_scalars(w.scalars + 4, h, 2, s));
+    const double res = sqrt(h[0]), nf = sqrt(h[1]);
+    local.res = res;
+    local.norm_f = nf;
+    if (!isfinite(res)) { status = PM_ENAN; break; }
+    if (res <= prm.tol * nf) { status = PM_OK; break; }
+    if (prev > 0.0 && prm.stall > 0.0 && res > prm.stall * prev) { status = PM_OK; break; }
+    prev = res;
+  }
+  local.status = status;
+  if (st) *st = local;
+  PM_TRY(launch_status());
+  return status;
+}
+
+}  // namespace pmgb

@@ -1,0 +1,129 @@
+// Internal declarations shared by the CUDA translation units of libpmgb.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "pm_api.h"
+
+namespace pmgb {
+
+// Kernel classes for launch counting and CUDA-event timing.
+enum KernelClass {
+  K_KEYS, K_SORT_UP, K_SORT_SCAN, K_SORT_DOWN, K_CELLSTART, K_PERMUTE,
+  K_DEPOSIT, K_REDUCE,
+  K_MG_GUESS, K_MG_SMOOTH, K_MG_RESTRICT, K_MG_PROLONG, K_MG_COARSE, K_MG_NORM,
+  K_FR_SMOOTH, K_FR_RESTRICT, K_FR_COARSEOP, K_FR_PROLONG, K_FR_COARSE, K_FR_NORM,
+  K_GRADIENT, K_INTERP, K_MISC,
+  K_NCLASS
+};
+
+extern const char* const kKernelClassNames[K_NCLASS];
+
+void launch_begin(int cls, cudaStream_t s);
+void launch_end(int cls, cudaStream_t s);
+
+// Records a CUDA error string and maps it to PM_ECUDA (PM_OK on cudaSuccess).
+pm_status cuda_status(cudaError_t e);
+// cudaGetLastError() after a batch of launches.
+inline pm_status launch_status() { return cuda_status(cudaGetLastError()); }
+
+inline int ilog2(int64_t v) { int l = 0; while ((int64_t(1) << (l + 1)) <= v) ++l; return l; }
+inline bool valid_n(int n) { return n >= 4 && n <= 1024 && (n & (n - 1)) == 0; }
+
+// Grid size for a grid-stride loop over `count` items with `threads` per block.
+inline unsigned grid_for(int64_t count, int threads, int64_t cap = 152 * 32) {
+  int64_t b = (count + threads - 1) / threads;
+  if (b < 1) b = 1;
+  if (b > cap) b = cap;
+  return (unsigned)b;
+}
+
+// A level-0 source term  s * (p[i] - mean)  with `mean` read from device
+// memory (float64), or a plain array (s = 1, mean = NULL).
+struct Src {
+  const float* p;
+  float s;
+  const double* mean;
+};
+
+// ------------------------------------------------------------ workspace --
+// Byte offsets of every buffer inside the caller's workspace.
+struct Workspace {
+  char* base;
+  size_t total;
+  // sort
+  uint32_t* keys_a; uint32_t* keys_b; uint32_t* vals_a; uint32_t* vals_b;
+  uint32_t* counts; uint32_t* scan_blocks; uint32_t* cellstart;
+  // particles in cell order
+  uint32_t* Xs; float* Vs; uint32_t* ids;
+  // grids
+  float* rho; float* g;
+  // reductions (float64 partials) and device scalars
+  double* partials; double* scalars;
+  // multigrid pyramids: level l >= 1 arrays (index 0 unused)
+  float* mg_u[12]; float* mg_f[12];
+  float* fr_e[12]; float* fr_r[12]; float* fr_b[12];
+  int64_t np; int n;
+};
+
+// Computes the layout for (n, np, flags); with base == NULL only sizes.
+size_t layout_workspace(Workspace* w, void* base, int n, int64_t np, uint32_t flags);
+
+// Sizes of the scratch pieces.
+int64_t radix_tiles(int64_t np);
+int64_t radix_scan_blocks(int64_t np);
+int64_t reduce_partials_capacity(int n, int64_t np);
+
+// ------------------------------------------------------ stage launchers --
+pm_status sort_particles(const uint32_t* X, int64_t np, int n, Workspace& w,
+                         cudaStream_t s, uint32_t** perm_out, uint32_t** skeys_out);
+pm_status build_cellstart(const uint32_t* skeys, int64_t np, int n, uint32_t* cellstart,
+                          cudaStream_t s);
+pm_status permute_particles(const uint32_t* perm, int64_t np, const uint32_t* X, const float* V,
+                            const uint32_t* id, uint32_t* Xs, float* Vs, uint32_t* ids,
+                            cudaStream_t s);
+// rho = (n^3/np) TSC sum over cell-sorted particles; writes sum(rho)/n^3 to *mean_out.
+pm_status deposit_sorted(const uint32_t* Xs, int64_t np, const uint32_t* cellstart, int n,
+                         float* rho, double* partials, double* mean_out, cudaStream_t s);
+// out[k] = scale * sum_{i < count} partials[k * stride + i] for k < nout (one block).
+pm_status reduce_partials(const double* partials, int64_t count, int64_t stride, int nout,
+                          double scale, double* out, cudaStream_t s);
+// Mean of a float32 grid into *mean_out (float64, fixed-order reduction).
+pm_status grid_mean(const float* f, int64_t count, double* partials, double* mean_out,
+                    cudaStream_t s);
+
+pm_status mg_solve_src(Src f, float* phi, int n, const mg_params& prm, mg_stats* st,
+                       Workspace& w, cudaStream_t s);
+pm_status fr_solve_src(Src b, float* eps, int n, const fr_params& prm, mg_stats* st,
+                       Workspace& w, cudaStream_t s);
+// u_fine += P(uc - uc2) (27/9/3/1 prolongation; uc2 may be NULL).
+pm_status prolong_correct_launch(float* u, const float* uc, const float* uc2, int n_fine, int cls,
+                                 cudaStream_t s);
+// Background constants of the f(R) equation (host, float64).
+void fr_background(const fr_params& p, double* fbar, double* kappa, double* c2);
+
+pm_status gradient_launch(const float* phi, const float* eps, float alpha, float* g, int n,
+                          int order, cudaStream_t s);
+// mode 0: acc only; mode 1: kick + drift into Xo/Vo (and acc if non-NULL).
+pm_status interp_launch(const float* g, const uint32_t* Xs, const float* Vs, const uint32_t* ids_in,
+                        int64_t np, int n, float* acc, uint32_t* Xo, float* Vo, uint32_t* ids_out,
+                        float dt_kick, float dt_drift, int mode, cudaStream_t s);
+
+// Copies `count` doubles of device reduction results to host (synchronises).
+pm_status fetch_scalars(const double* dev, double* host, int count, cudaStream_t s);
+
+}  // namespace pmgb
+
+#define PM_LAUNCH(cls, kern, grid, block, smem, st, ...)              \
+  do {                                                                 \
+    ::pmgb::launch_begin((cls), (st));                                 \
+    kern<<<(grid), (block), (smem), (st)>>>(__VA_ARGS__);              \
+    ::pmgb::launch_end((cls), (st));                                   \
+  } while (0)
+
+#define PM_TRY(expr)                       \
+  do {                                     \
+    pm_status _st = (expr);                \
+    if (_st != PM_OK) return _st;          \
+  } while (0)

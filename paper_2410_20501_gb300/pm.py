@@ -1,0 +1,347 @@
+"""Thin ctypes binding of libpmgb (include/pm_api.h) over torch device memory.
+
+Argument marshalling only: every stage runs in the CUDA library.  torch
+provides device memory (tensors, workspace) and the current CUDA stream.
+If the library is missing this module raises instead of falling back.
+
+Layouts: positions are uint32 fixed point stored in int32 tensors [3, np]
+(same bits); velocities / accelerations float32 [3, np]; scalar grids float32
+[n, n, n]; vector grids float32 [3, n, n, n].
+"""
+import ctypes
+import os
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libpmgb.so")
+
+PM_WS_SORT, PM_WS_MG, PM_WS_FR, PM_WS_STEP, PM_WS_IDS = 1, 2, 4, 8, 16
+MG_GUESS_INPUT, MG_GUESS_JACOBI, MG_GUESS_SCALED = 0, 1, 2
+PM_GRAVITY_NEWTON, PM_GRAVITY_FR = 0, 1
+STATUS = {0: "PM_OK", 1: "PM_EINVAL", 2: "PM_ENOMEM", 3: "PM_ENOCONV", 4: "PM_ENAN", 5: "PM_ETIMEOUT",
+          6: "PM_ECUDA"}
+
+
+class PMError(RuntimeError):
+    def __init__(self, code, where):
+        self.code = code
+        msg = f"{where}: {STATUS.get(code, code)}"
+        if code == 6 and _lib is not None:
+            msg += f" ({_lib.pm_last_cuda_error().decode()})"
+        super().__init__(msg)
+
+
+class mg_params(ctypes.Structure):
+    _fields_ = [("npre", ctypes.c_int), ("npost", ctypes.c_int), ("omega", ctypes.c_float),
+                ("coarsest", ctypes.c_int), ("coarse_max_sweeps", ctypes.c_int), ("coarse_drop", ctypes.c_float),
+                ("max_cycles", ctypes.c_int), ("fixed_cycles", ctypes.c_int), ("tol", ctypes.c_double),
+                ("stall", ctypes.c_double), ("first_guess", ctypes.c_int), ("guess_scale", ctypes.c_float)]
+
+
+class mg_stats(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("cycles", ctypes.c_int), ("norm_f", ctypes.c_double),
+                ("res0", ctypes.c_double), ("res", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class fr_params(ctypes.Structure):
+    _fields_ = [("a", ctypes.c_double), ("Om", ctypes.c_double), ("OL", ctypes.c_double),
+                ("fR0", ctypes.c_double), ("boxsize", ctypes.c_double), ("cycle", ctypes.c_int),
+                ("npre", ctypes.c_int), ("npost", ctypes.c_int), ("coarsest", ctypes.c_int),
+                ("coarse_max_sweeps", ctypes.c_int), ("coarse_drop", ctypes.c_float), ("cycles", ctypes.c_int),
+                ("tol", ctypes.c_double), ("max_cycles", ctypes.c_int)]
+
+
+class pm_state(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int), ("np", ctypes.c_int64), ("X", ctypes.c_void_p), ("V", ctypes.c_void_p),
+                ("id", ctypes.c_void_p), ("phi", ctypes.c_void_p), ("eps", ctypes.c_void_p),
+                ("acc", ctypes.c_void_p), ("ws", ctypes.c_void_p), ("ws_bytes", ctypes.c_size_t),
+                ("have_prev", ctypes.c_int)]
+
+
+class pm_step_params(ctypes.Structure):
+    _fields_ = [("a", ctypes.c_double), ("Om", ctypes.c_double), ("OL", ctypes.c_double),
+                ("boxsize", ctypes.c_double), ("gravity", ctypes.c_int), ("fR0", ctypes.c_double),
+                ("grad_order", ctypes.c_int), ("dt_kick", ctypes.c_double), ("dt_drift", ctypes.c_double),
+                ("phi_rescale", ctypes.c_double), ("mg", mg_params), ("fr", fr_params)]
+
+
+class pm_stats(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("mg", mg_stats), ("fr", mg_stats)]
+
+
+_lib = None
+
+_SIGS = {
+    "pm_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "pm_last_cuda_error": (ctypes.c_char_p, []),
+    "pm_version": (ctypes.c_char_p, []),
+    "pm_workspace_size": (ctypes.c_int, [ctypes.c_int, ctypes.c_int64, ctypes.c_uint32,
+                                         ctypes.POINTER(ctypes.c_size_t)]),
+    "pm_sort": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                               ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
+    "pm_deposit": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_void_p,
+                                  ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
+    "mg_default_params": (None, [ctypes.POINTER(mg_params)]),
+    "mg_solve": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(mg_params),
+                                ctypes.POINTER(mg_stats), ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
+    "fr_default_params": (None, [ctypes.POINTER(fr_params)]),
+    "fr_solve": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(fr_params),
+                                ctypes.POINTER(mg_stats), ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
+    "pm_gradient": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p]),
+    "pm_interp": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_void_p,
+                                 ctypes.c_void_p]),
+    "pm_step": (ctypes.c_int, [ctypes.POINTER(pm_state), ctypes.POINTER(pm_step_params), ctypes.POINTER(pm_stats),
+                               ctypes.c_void_p]),
+    "pm_step_host": (ctypes.c_int, [ctypes.POINTER(pm_state), ctypes.POINTER(pm_step_params),
+                                    ctypes.POINTER(pm_stats), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                    ctypes.c_void_p, ctypes.c_void_p]),
+    "pm_dt_supercomoving": (ctypes.c_double, [ctypes.c_double] * 4),
+    "pm_growth_D": (ctypes.c_double, [ctypes.c_double] * 3),
+    "pm_launch_count": (ctypes.c_uint64, []),
+    "pm_timing_enable": (ctypes.c_int, [ctypes.c_int]),
+    "pm_timing_collect": (ctypes.c_int, [ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_double),
+                                         ctypes.POINTER(ctypes.c_int64), ctypes.c_int]),
+}
+
+
+def lib():
+    """Load libpmgb.so (built by ``build.build()``); raises if it is missing."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libpmgb.so not built ({LIB_PATH}); run paper_2410_20501_gb300.build.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(code, where):
+    if code != 0:
+        raise PMError(code, where)
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _p(t, dtype=None):
+    if t is None:
+        return None
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError(f"expected {dtype}, got {t.dtype}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def positions_to_device(X, device="cuda"):
+    """uint32 numpy [3, np] -> int32 CUDA tensor with the same bits."""
+    return torch.from_numpy(np.ascontiguousarray(X, dtype=np.uint32).view(np.int32)).to(device)
+
+
+def positions_to_host(t):
+    return t.cpu().numpy().view(np.uint32)
+
+
+def workspace_size(n, np_, flags):
+    b = ctypes.c_size_t()
+    _check(lib().pm_workspace_size(n, int(np_), flags, ctypes.byref(b)), "pm_workspace_size")
+    return b.value
+
+
+def workspace(n, np_, flags, device="cuda"):
+    return torch.empty(workspace_size(n, np_, flags), dtype=torch.uint8, device=device)
+
+
+def default_mg(**kw):
+    p = mg_params()
+    lib().mg_default_params(ctypes.byref(p))
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+def default_fr(**kw):
+    p = fr_params()
+    lib().fr_default_params(ctypes.byref(p))
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+def sort(X, n, ws=None):
+    """Stable cell sort: returns (perm int32 [np], cellstart int32 [n^3 + 1])."""
+    np_ = X.shape[1]
+    ws = ws if ws is not None else workspace(n, np_, PM_WS_SORT, X.device)
+    perm = torch.empty(np_, dtype=torch.int32, device=X.device)
+    cs = torch.empty(n ** 3 + 1, dtype=torch.int32, device=X.device)
+    _check(lib().pm_sort(_p(X, torch.int32), np_, n, _p(perm), _p(cs), _p(ws), ws.numel(), _stream()), "pm_sort")
+    return perm, cs
+
+
+def deposit(X, n, ws=None):
+    """TSC density rho~ [n, n, n] (mean 1)."""
+    np_ = X.shape[1]
+    ws = ws if ws is not None else workspace(n, np_, PM_WS_SORT, X.device)
+    rho = torch.empty((n, n, n), dtype=torch.float32, device=X.device)
+    _check(lib().pm_deposit(_p(X, torch.int32), np_, n, _p(rho), _p(ws), ws.numel(), _stream()), "pm_deposit")
+    return rho
+
+
+def mg_solve(f, phi=None, ws=None, **params):
+    """Multigrid Poisson solve; returns (phi, stats dict)."""
+    n = f.shape[0]
+    prm = default_mg(**params)
+    if phi is None:
+        phi = torch.zeros_like(f)
+        if "first_guess" not in params:
+            prm.first_guess = MG_GUESS_JACOBI
+    ws = ws if ws is not None else workspace(n, 0, PM_WS_MG, f.device)
+    st = mg_stats()
+    code = lib().mg_solve(_p(f, torch.float32), _p(phi, torch.float32), n, ctypes.byref(prm), ctypes.byref(st),
+                          _p(ws), ws.numel(), _stream())
+    if code not in (0, 3):
+        _check(code, "mg_solve")
+    return phi, st.as_dict()
+
+
+def fr_solve(rho, eps=None, ws=None, **params):
+    """f(R) scalaron eps = u - 1; returns (eps, stats dict)."""
+    n = rho.shape[0]
+    prm = default_fr(**params)
+    eps = eps if eps is not None else torch.zeros_like(rho)
+    ws = ws if ws is not None else workspace(n, 0, PM_WS_FR, rho.device)
+    st = mg_stats()
+    code = lib().fr_solve(_p(rho, torch.float32), _p(eps, torch.float32), n, ctypes.byref(prm), ctypes.byref(st),
+                          _p(ws), ws.numel(), _stream())
+    if code not in (0, 3):
+        _check(code, "fr_solve")
+    return eps, st.as_dict()
+
+
+def gradient(phi, order=5):
+    n = phi.shape[0]
+    g = torch.empty((3, n, n, n), dtype=torch.float32, device=phi.device)
+    _check(lib().pm_gradient(_p(phi, torch.float32), _p(g), n, order, _stream()), "pm_gradient")
+    return g
+
+
+def interp(g, X):
+    n = g.shape[1]
+    np_ = X.shape[1]
+    acc = torch.empty((3, np_), dtype=torch.float32, device=X.device)
+    _check(lib().pm_interp(_p(g, torch.float32), _p(X, torch.int32), np_, n, _p(acc), _stream()), "pm_interp")
+    return acc
+
+
+def dt_supercomoving(Om, OL, a0, a1):
+    return lib().pm_dt_supercomoving(Om, OL, a0, a1)
+
+
+def growth_D(Om, OL, a):
+    return lib().pm_growth_D(Om, OL, a)
+
+
+def launch_count():
+    return int(lib().pm_launch_count())
+
+
+def timing_enable(on=True):
+    _check(lib().pm_timing_enable(1 if on else 0), "pm_timing_enable")
+
+
+def timing_collect():
+    cap = 64
+    names = (ctypes.c_char_p * cap)()
+    ms = (ctypes.c_double * cap)()
+    cnt = (ctypes.c_int64 * cap)()
+    k = lib().pm_timing_collect(names, ms, cnt, cap)
+    return {names[i].decode(): (ms[i], cnt[i]) for i in range(k)}
+
+
+class Simulation:
+    """Device-resident particle state stepped by pm_step.
+
+    X: uint32 numpy [3, np]; V: float32/float64 numpy [3, np].  Particles are
+    kept in cell order (permuted every step); ``ids`` follows them if
+    track_ids."""
+
+    def __init__(self, X, V, n, Om, OL, boxsize, gravity="newton", fR0=-1e-5, grad_order=5, mg=None, fr=None,
+                 track_ids=False, keep_acc=False, device="cuda"):
+        self.n = n
+        self.np = X.shape[1]
+        self.Om, self.OL, self.boxsize, self.fR0 = Om, OL, boxsize, fR0
+        self.gravity = PM_GRAVITY_FR if gravity == "fr" else PM_GRAVITY_NEWTON
+        self.grad_order = grad_order
+        self.X = positions_to_device(X, device)
+        self.V = torch.from_numpy(np.ascontiguousarray(V, dtype=np.float32)).to(device)
+        self.ids = torch.arange(self.np, dtype=torch.int32, device=device) if track_ids else None
+        self.phi = torch.zeros((n, n, n), dtype=torch.float32, device=device)
+        self.eps = torch.zeros((n, n, n), dtype=torch.float32, device=device) if self.gravity else None
+        self.acc = torch.empty((3, self.np), dtype=torch.float32, device=device) if keep_acc else None
+        flags = PM_WS_STEP | (PM_WS_IDS if track_ids else 0)
+        self.ws = workspace(n, self.np, flags, device)
+        self.mg = mg if mg is not None else default_mg()
+        self.fr = fr if fr is not None else default_fr()
+        self.state = pm_state(n=n, np=self.np, X=_p(self.X).value, V=_p(self.V).value,
+                              id=_p(self.ids).value if track_ids else None, phi=_p(self.phi).value,
+                              eps=_p(self.eps).value if self.eps is not None else None,
+                              acc=_p(self.acc).value if keep_acc else None, ws=_p(self.ws).value,
+                              ws_bytes=self.ws.numel(), have_prev=0)
+
+    def params(self, a, dt_kick, dt_drift, phi_rescale=1.0):
+        return pm_step_params(a=a, Om=self.Om, OL=self.OL, boxsize=self.boxsize, gravity=self.gravity,
+                              fR0=self.fR0, grad_order=self.grad_order, dt_kick=dt_kick, dt_drift=dt_drift,
+                              phi_rescale=phi_rescale, mg=self.mg, fr=self.fr)
+
+    def step(self, a, dt_kick, dt_drift, phi_rescale=1.0):
+        st = pm_stats()
+        prm = self.params(a, dt_kick, dt_drift, phi_rescale)
+        code = lib().pm_step(ctypes.byref(self.state), ctypes.byref(prm), ctypes.byref(st), _stream())
+        if code not in (0, 3):
+            _check(code, "pm_step")
+        return {"status": st.status, "mg": st.mg.as_dict(), "fr": st.fr.as_dict()}
+
+    def step_host(self, a, dt_kick, dt_drift, X_in, V_in, X_out, V_out, phi_rescale=1.0):
+        """pm_step_host with pinned host tensors (int32 [3,np], float32 [3,np])."""
+        st = pm_stats()
+        prm = self.params(a, dt_kick, dt_drift, phi_rescale)
+        code = lib().pm_step_host(ctypes.byref(self.state), ctypes.byref(prm), ctypes.byref(st),
+                                  ctypes.c_void_p(X_in.data_ptr()), ctypes.c_void_p(V_in.data_ptr()),
+                                  ctypes.c_void_p(X_out.data_ptr()), ctypes.c_void_p(V_out.data_ptr()), _stream())
+        if code not in (0, 3):
+            _check(code, "pm_step_host")
+        return {"status": st.status, "mg": st.mg.as_dict(), "fr": st.fr.as_dict()}
+
+    def run(self, a_steps, rescale_potential=True):
+        """Kick-drift-kick through the scale factors a_steps (fused kicks):
+        force at a_i, kick by (dt_{i-1} + dt_i)/2, drift by dt_i; a final
+        half kick at a_N.  Returns per-step stats."""
+        Om, OL = self.Om, self.OL
+        dts = [dt_supercomoving(Om, OL, a_steps[i], a_steps[i + 1]) for i in range(len(a_steps) - 1)]
+        D = [growth_D(Om, OL, a) for a in a_steps]
+        out = []
+        for i, a in enumerate(a_steps):
+            prev = dts[i - 1] if i > 0 else 0.0
+            cur = dts[i] if i < len(dts) else 0.0
+            resc = (a * D[i]) / (a_steps[i - 1] * D[i - 1]) if (i > 0 and rescale_potential) else 1.0
+            out.append(self.step(a, 0.5 * (prev + cur), cur, resc))
+        return out
+
+    def positions(self):
+        return positions_to_host(self.X)
+
+    def velocities(self):
+        return self.V.cpu().numpy()
+
+    def particle_ids(self):
+        return None if self.ids is None else self.ids.cpu().numpy()

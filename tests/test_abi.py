@@ -1,0 +1,78 @@
+"""The C ABI without a GPU: the library builds and loads, exports every function
+declared in include/pm_api.h, validates arguments before touching the device,
+and its host utilities agree with the oracle."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_2410_20501_gb300 import build, pm
+    if not os.path.exists(pm.LIB_PATH):
+        build.build()
+    return pm.lib()
+
+
+def header_functions():
+    src = open(os.path.join(ROOT, "include", "pm_api.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"^[A-Za-z_][\w\s\*]*?\b([A-Za-z_]\w*)\s*\([^;{]*\)\s*;", src, flags=re.M)
+    return sorted(set(names))
+
+
+def test_header_declares_the_boundary():
+    names = header_functions()
+    for must in ("pm_deposit", "mg_solve", "fr_solve", "pm_gradient", "pm_interp", "pm_step", "pm_sort"):
+        assert must in names
+
+
+def test_every_declared_symbol_is_exported(L):
+    missing = [f for f in header_functions() if not hasattr(L, f)]
+    assert not missing, missing
+
+
+def test_status_strings_and_version(L):
+    assert L.pm_status_string(0) == b"PM_OK"
+    assert b"EINVAL" in L.pm_status_string(1)
+    assert L.pm_version().decode().count(".") == 2
+
+
+def test_argument_errors_are_synchronous(L):
+    from paper_2410_20501_gb300 import pm
+    fake = ctypes.c_void_p(0x100000)      # never dereferenced: rejected before any CUDA call
+    assert L.pm_deposit(fake, 10, 3, fake, fake, 1 << 20, None) == 1          # n not a power of two
+    assert L.pm_deposit(fake, -1, 8, fake, fake, 1 << 20, None) == 1          # np < 0
+    assert L.pm_deposit(fake, 10, 8, fake, fake, 16, None) == 2               # workspace too small
+    assert L.pm_deposit(fake, 10, 8, fake, ctypes.c_void_p(0x100001), 1 << 30, None) == 1  # misaligned ws
+    assert L.pm_gradient(fake, fake, 16, 4, None) == 1                        # bad stencil order
+    prm = pm.default_mg(coarsest=32)
+    assert L.mg_solve(fake, fake, 64, ctypes.byref(prm), None, fake, 1 << 30, None) == 1
+    fr = pm.default_fr(fR0=1e-5)
+    assert L.fr_solve(fake, fake, 64, ctypes.byref(fr), None, fake, 1 << 30, None) == 1
+
+
+def test_workspace_size_monotone(L):
+    from paper_2410_20501_gb300 import pm
+    a = pm.workspace_size(32, 32 ** 3, pm.PM_WS_STEP)
+    b = pm.workspace_size(64, 64 ** 3, pm.PM_WS_STEP)
+    assert 0 < a < b
+    assert pm.workspace_size(64, 64 ** 3, pm.PM_WS_STEP | pm.PM_WS_IDS) > b
+
+
+def test_host_cosmology_matches_oracle(L):
+    from oracle import cosmology
+    from paper_2410_20501_gb300 import pm
+    for Om, OL in ((1.0, 0.0), (0.3, 0.7)):
+        for a0, a1 in ((0.02, 0.03), (1 / 31, 0.5), (0.5, 1.0)):
+            assert pm.dt_supercomoving(Om, OL, a0, a1) == pytest.approx(
+                cosmology.dt_supercomoving(a0, a1, Om, OL), rel=1e-10)
+        a = np.array([0.05, 0.3, 1.0])
+        D = cosmology.growth_factors(a, Om, OL)[0]
+        Dc = np.array([pm.growth_D(Om, OL, x) for x in a])
+        assert Dc / Dc[-1] == pytest.approx(D / D[-1], rel=1e-7)

@@ -1,0 +1,245 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle, stage by
+stage, on seeded inputs spanning several tiles and ragged sizes."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import fr as ofr
+from oracle import mesh, poisson, step
+from paper_2410_20501_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pm():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import os
+    from paper_2410_20501_gb300 import build, pm as _pm
+    if not os.path.exists(_pm.LIB_PATH):
+        build.build()
+    _pm.lib()
+    return _pm
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(np.asarray(a, dtype=np.float64) - b) / np.linalg.norm(b))
+
+
+def displaced_lattice(n, seed, amp=0.3):
+    """n^3 particles at cell centres displaced by up to amp cells (seeded)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    pos = inputs.lattice(n) + rng.uniform(-amp, amp, (3, n ** 3)) / n
+    return inputs.to_fixed_point(pos)
+
+
+# ------------------------------------------------------------------ sort ---
+
+@pytest.mark.parametrize("n,N", [(16, 0), (16, 1), (32, 5000), (32, 32 ** 3 + 777), (64, 100003)])
+def test_sort_bit_exact(pm, n, N):
+    X = inputs.uniform_particles(N, 100 + N)
+    perm, cs = pm.sort(pm.positions_to_device(X), n)
+    ref = mesh.stable_cell_order(X, n)
+    assert np.array_equal(perm.cpu().numpy().view(np.uint32), ref)
+    keys = mesh.cell_key(X, n)[ref]
+    ref_cs = np.searchsorted(keys, np.arange(n ** 3 + 1), side="left").astype(np.uint32)
+    assert np.array_equal(cs.cpu().numpy().view(np.uint32), ref_cs)
+
+
+def test_sort_nearly_sorted_with_many_ties(pm):
+    n = 32
+    X = displaced_lattice(n, 7, amp=0.49)
+    X = np.concatenate([X, X[:, ::3]], axis=1)      # duplicates: ties must keep input order
+    perm, _ = pm.sort(pm.positions_to_device(X), n)
+    assert np.array_equal(perm.cpu().numpy().view(np.uint32), mesh.stable_cell_order(X, n))
+
+
+# --------------------------------------------------------------- deposit ---
+
+@pytest.mark.parametrize("n,kind", [(8, "lattice"), (32, "lattice"), (64, "lattice"), (32, "random"),
+                                    (16, "single")])
+def test_deposit_parity(pm, n, kind):
+    if kind == "lattice":
+        X = displaced_lattice(n, 11)
+    elif kind == "random":
+        X = inputs.uniform_particles(12345, 3)
+    else:
+        X = inputs.to_fixed_point(np.array([[0.31], [0.5 / n], [0.999]]))
+    rho = pm.deposit(pm.positions_to_device(X), n).cpu().numpy()
+    ref = mesh.deposit_tsc(mesh.positions_from_fixed_point(X), n)
+    assert np.abs(rho - ref).max() <= 2e-6 * np.abs(ref).max()
+    rho2 = pm.deposit(pm.positions_to_device(X), n).cpu().numpy()
+    assert np.array_equal(rho, rho2)                  # deterministic
+
+
+def test_deposit_empty(pm):
+    rho = pm.deposit(torch.zeros((3, 0), dtype=torch.int32, device="cuda"), 16)
+    assert float(rho.abs().max()) == 0.0
+
+
+# ------------------------------------------------------------ multigrid ---
+
+def random_source(n, seed):
+    return inputs.random_field(n, seed)
+
+
+@pytest.mark.parametrize("n", [16, 32, 64])
+def test_mg_converged_matches_fft7(pm, n):
+    f = random_source(n, 21)
+    h = 1.0 / n
+    phi, st = pm.mg_solve(torch.from_numpy(f.astype(np.float32)).cuda(), tol=1e-9, max_cycles=40,
+                          coarsest=8 if n == 16 else 16)
+    phi = phi.cpu().numpy().astype(np.float64)
+    ref = poisson.solve_fft7(f.astype(np.float32).astype(np.float64), h)
+    assert st["status"] == 0
+    assert rel_l2(phi - phi.mean(), ref) < 2e-6
+    g = mesh.force_from_potential(phi, h)
+    gr = mesh.force_from_potential(ref, h)
+    assert rel_l2(np.stack(g), np.stack(gr)) < 1e-5
+
+
+@pytest.mark.parametrize("n,cycles", [(32, 1), (32, 2), (64, 1)])
+def test_mg_fixed_cycles_match_oracle_multigrid(pm, n, cycles):
+    """Same algorithm steps (Jacobi first guess, V-cycles with omega = 1 on the
+    first pre- and last post-sweep, coarsest 16) in float32 vs float64."""
+    f = random_source(n, 5).astype(np.float32).astype(np.float64)
+    h = 1.0 / n
+    phi, _ = pm.mg_solve(torch.from_numpy(f.astype(np.float32)).cuda(), fixed_cycles=cycles,
+                         first_guess=pm.MG_GUESS_JACOBI)
+    ref, _ = poisson.mg_solve(f, h, prm=poisson.MGParams(), cycles=cycles)
+    assert rel_l2(phi.cpu().numpy(), ref) < 1e-5
+
+
+def test_mg_warm_start_scaled_guess(pm):
+    n = 32
+    f = random_source(n, 9).astype(np.float32).astype(np.float64)
+    h = 1.0 / n
+    guess = 0.9 * poisson.solve_fft7(f, h)
+    phi_t = torch.from_numpy((guess / 1.1).astype(np.float32)).cuda()
+    phi, _ = pm.mg_solve(torch.from_numpy(f.astype(np.float32)).cuda(), phi=phi_t, fixed_cycles=1,
+                         first_guess=pm.MG_GUESS_SCALED, guess_scale=1.1)
+    ref, _ = poisson.mg_solve(f, h, u0=(guess / 1.1).astype(np.float32).astype(np.float64) * 1.1,
+                              prm=poisson.MGParams(), cycles=1)
+    assert rel_l2(phi.cpu().numpy(), ref) < 1e-5
+
+
+# -------------------------------------------------------------- gradient ---
+
+@pytest.mark.parametrize("order", [3, 5, 7])
+def test_gradient_parity(pm, order):
+    n = 32
+    phi = random_source(n, 4).astype(np.float32)
+    g = pm.gradient(torch.from_numpy(phi).cuda(), order).cpu().numpy()
+    ref = np.stack(mesh.force_from_potential(phi.astype(np.float64), 1.0 / n, order))
+    assert np.abs(g - ref).max() <= 1e-5 * np.abs(ref).max()
+
+
+# ----------------------------------------------------------------- interp ---
+
+@pytest.mark.parametrize("n,N", [(32, 20000), (64, 1000)])
+def test_interp_parity(pm, n, N):
+    g = np.stack([random_source(n, 30 + d) for d in range(3)]).astype(np.float32)
+    X = inputs.uniform_particles(N, 77)
+    acc = pm.interp(torch.from_numpy(g).cuda(), pm.positions_to_device(X)).cpu().numpy()
+    pos = mesh.positions_from_fixed_point(X)
+    ref = mesh.interp_tsc([g[d].astype(np.float64) for d in range(3)], pos).T
+    assert np.abs(acc - ref).max() <= 2e-6 * np.abs(ref).max()
+
+
+# ------------------------------------------------------------------ f(R) ---
+
+def lognormal_density(n, seed, sigma=0.8):
+    rho = np.exp(sigma * inputs.random_field(n, seed))
+    return rho / rho.mean()
+
+
+@pytest.mark.parametrize("a", [0.3, 1.0])
+def test_fr_one_f_cycle_matches_oracle(pm, a):
+    n = 32
+    rho = lognormal_density(n, 8).astype(np.float32).astype(np.float64)
+    model = ofr.FRModel(Om=0.3, OL=0.7, fR0=-1e-5, boxsize=float(n))
+    eps, _ = pm.fr_solve(torch.from_numpy(rho.astype(np.float32)).cuda(), a=a, Om=0.3, OL=0.7, fR0=-1e-5,
+                         boxsize=float(n), coarsest=16, cycles=1)
+    u, _ = ofr.fr_solve(rho, a, model, prm=ofr.FASParams(coarsest=16), cycles=1)
+    assert rel_l2(eps.cpu().numpy(), u - 1.0) < 1e-4
+
+
+def test_fr_converged_matches_oracle(pm):
+    n = 32
+    rho = lognormal_density(n, 12, 1.2).astype(np.float32).astype(np.float64)
+    model = ofr.FRModel(Om=0.3, OL=0.7, fR0=-1e-5, boxsize=float(n))
+    eps, st = pm.fr_solve(torch.from_numpy(rho.astype(np.float32)).cuda(), a=0.8, Om=0.3, OL=0.7, fR0=-1e-5,
+                          boxsize=float(n), coarsest=8, tol=1e-6, max_cycles=20)
+    u, _ = ofr.fr_solve(rho, 0.8, model, prm=ofr.FASParams(coarsest=8), tol=1e-10)
+    assert st["status"] == 0
+    assert rel_l2(eps.cpu().numpy(), u - 1.0) < 2e-5
+
+
+# ------------------------------------------------------------------ step ---
+
+def gpu_accelerations(pm, X, V, n, a, gravity="newton", boxsize=64.0, Om=1.0, OL=0.0, **kw):
+    sim = pm.Simulation(X, V, n, Om=Om, OL=OL, boxsize=boxsize, gravity=gravity, track_ids=True, keep_acc=True,
+                        **kw)
+    sim.step(a=a, dt_kick=0.0, dt_drift=0.0)
+    out = np.empty((3, X.shape[1]))
+    out[:, sim.particle_ids()] = sim.acc.cpu().numpy()
+    return out, sim
+
+
+def test_step_accelerations_c1(pm):
+    n = 32
+    X, V = inputs.zeldovich_powerlaw_ics(n, seed=1)
+    acc, _ = gpu_accelerations(pm, X, V, n, 0.02)
+    ref, _, _ = step.accelerations(mesh.positions_from_fixed_point(X), 0.02,
+                                   step.PMParams(n=n, Om=1.0, OL=0.0, boxsize=64.0))
+    assert rel_l2(acc.T, ref) < 1e-5
+
+
+def test_step_accelerations_fr(pm):
+    n = 32
+    X = displaced_lattice(n, 13, amp=0.45)
+    V = np.zeros((3, n ** 3))
+    mgp = pm.default_mg(tol=1e-9)
+    frp = pm.default_fr(coarsest=16, cycles=1)
+    acc, _ = gpu_accelerations(pm, X, V, n, 0.7, gravity="fr", boxsize=float(n), Om=0.3, OL=0.7, mg=mgp, fr=frp)
+    prm = step.PMParams(n=n, Om=0.3, OL=0.7, boxsize=float(n), gravity="fr", fR0=-1e-5)
+    ref, _, _ = step.accelerations(mesh.positions_from_fixed_point(X), 0.7, prm)
+    assert rel_l2(acc.T, ref) < 1e-5
+
+
+def test_step_is_deterministic(pm):
+    n = 32
+    X, V = inputs.zeldovich_powerlaw_ics(n, seed=2)
+    outs = []
+    for _ in range(2):
+        sim = pm.Simulation(X, V, n, Om=1.0, OL=0.0, boxsize=64.0, track_ids=True)
+        sim.run([0.02, 0.03, 0.04])
+        outs.append((sim.positions(), sim.velocities(), sim.particle_ids()))
+    for a, b in zip(outs[0], outs[1]):
+        assert np.array_equal(a, b)
+
+
+def test_c1_twenty_steps_positions_and_power(pm):
+    """Configuration C1: 32^3 EdS, Zel'dovich ICs at a = 0.02, 20 KDK steps
+    uniform in a to 0.2.  Spec bars: final positions RMS <= 1e-4 cell,
+    P(k) within 0.1% below half Nyquist."""
+    from oracle import power
+    n = 32
+    X, V = inputs.zeldovich_powerlaw_ics(n, seed=1)
+    a_steps = list(np.linspace(0.02, 0.2, 21))
+    sim = pm.Simulation(X, V, n, Om=1.0, OL=0.0, boxsize=64.0, track_ids=True, mg=pm.default_mg(tol=1e-9))
+    sim.run(a_steps)
+    ids = sim.particle_ids()
+    Xg = np.empty_like(X)
+    Xg[:, ids] = sim.positions()
+    pos_ref, _ = step.run_kdk(mesh.positions_from_fixed_point(X), V.T, a_steps,
+                              step.PMParams(n=n, Om=1.0, OL=0.0, boxsize=64.0))
+    d = (mesh.positions_from_fixed_point(Xg) - pos_ref + 0.5) % 1.0 - 0.5
+    rms_cells = np.sqrt((d ** 2).sum(axis=1).mean()) * n
+    assert rms_cells <= 1e-4
+    k, P, _ = power.power_spectrum(mesh.deposit_tsc(mesh.positions_from_fixed_point(Xg), n), 64.0)
+    kr, Pr, _ = power.power_spectrum(mesh.deposit_tsc(pos_ref, n), 64.0)
+    sel = k < 0.5 * np.pi * n / 64.0
+    assert np.abs(P[sel] / Pr[sel] - 1.0).max() < 1e-3
