@@ -1,0 +1,320 @@
+"""Throughput of the PM step (particle-steps/s) on the 512^3 Hu-Sawicki f(R)
+configuration: 512^3 particles on a 512^3 grid, L = 512 Mpc/h, Omega_m = 0.3,
+sigma8 = 0.8, f_R0 = -1e-5, 2LPT initial conditions at z = 30 (seed 5), steps
+uniform in ln a.  One step = cell sort, TSC deposit, one FAS F-cycle for the
+scalaron, Poisson V-cycles to the float32 floor, gradient of the combined
+potential, inverse TSC, kick and drift.  The Newtonian step on the same
+particles is reported beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line.  N > 1 (under torchrun) runs N independent replicas, one
+per GPU: the step has no exchange between boxes.  ``--impl reference`` times
+the FP64 CPU oracle on a bounded sample of the same workload instead.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_GRID = 512
+BOX = 512.0
+OM, OL = 0.3, 0.7
+FR0 = -1e-5
+Z_INI = 30.0
+SEED = 5
+N_STEPS_RUN = 100
+METRIC = "particle-steps/s at 512^3 (Hu-Sawicki f(R) PM step)"
+
+
+def schedule():
+    a0 = 1.0 / (1.0 + Z_INI)
+    return list(np.exp(np.linspace(math.log(a0), 0.0, N_STEPS_RUN + 1)))
+
+
+def dist_env():
+    return int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")), \
+        int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def init_dist(world, backend):
+    import torch.distributed as dist
+    if world > 1 and not dist.is_initialized():
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group(backend=backend)
+    return dist
+
+
+def max_over_ranks(value, world, device="cpu"):
+    """Max of a float over ranks (the timing rule: slowest rank)."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+class ClockSampler:
+    """nvidia-smi sampling during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        if self.path and os.path.exists(self.path):
+            for line in open(self.path):
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+            os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def load_ncu_traffic():
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    return json.load(open(path)) if os.path.exists(path) else {}
+
+
+# --------------------------------------------------------------- oracle arm --
+
+def oracle_sample(steps):
+    """The FP64 oracle, unchanged, on a bounded sample of the workload: 32^3
+    particles on a 32^3 grid in a 32 Mpc/h box (the 1 Mpc/h cells of the
+    512^3 run), same cosmology, f_R0 and 2LPT start at z = 30, advanced through
+    the first ``steps`` steps of the same schedule with f(R) forces (exact
+    discrete Poisson inverse, one FAS F-cycle) and kick-drift-kick.  Returns
+    (particle-steps/s, seconds, sample description)."""
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ.setdefault(v, "1")
+    from oracle import mesh, step
+    from paper_2410_20501_gb300 import inputs
+    n = 32
+    X, V = inputs.lpt_ics(n, float(n), OM, OL, 1.0 / (1.0 + Z_INI), SEED, order=2)
+    prm = step.PMParams(n=n, Om=OM, OL=OL, boxsize=float(n), gravity="fr", fR0=FR0)
+    a = schedule()[:steps + 1]
+    t0 = time.perf_counter()
+    step.run_kdk(mesh.positions_from_fixed_point(X), V.T, a, prm, warm_start=False)
+    dt = time.perf_counter() - t0
+    return n ** 3 * steps / dt, dt, (f"FP64 oracle, {steps} f(R) PM steps (deposit, exact 7-point Poisson "
+                                     f"inverse, one FAS F-cycle, 5-point gradient, inverse TSC, KDK) of 32^3 "
+                                     f"particles on a 32^3 grid with the 1 Mpc/h cells of the 512^3 run")
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if world > 1:
+        init_dist(world, "gloo")
+    if rank != 0:
+        return 0
+    value, secs, sample = oracle_sample(max(1, args.steps))
+    line = {"metric": METRIC, "value": value, "unit": "particle-steps/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / max(1, args.steps),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference",
+            "config": {"workload": "hu-sawicki f(R) pm step, bounded oracle sample", "n": 32},
+            "cpu_baseline": {"value": value, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "particle-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# ------------------------------------------------------------------ GPU arm --
+
+def timed_steps(sim, a, first, count, host_buffers=None):
+    """Runs steps first .. first+count-1 of the schedule; returns device ms."""
+    import torch
+    from paper_2410_20501_gb300 import pm
+    s = torch.cuda.current_stream()
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    Om, OL = sim.Om, sim.OL
+    stats = []
+    start.record(s)
+    for i in range(first, first + count):
+        prev = pm.dt_supercomoving(Om, OL, a[i - 1], a[i]) if i > 0 else 0.0
+        cur = pm.dt_supercomoving(Om, OL, a[i], a[i + 1])
+        resc = (a[i] * pm.growth_D(Om, OL, a[i])) / (a[i - 1] * pm.growth_D(Om, OL, a[i - 1])) if i > 0 else 1.0
+        if host_buffers is None:
+            stats.append(sim.step(a[i], 0.5 * (prev + cur), cur, resc))
+        else:
+            Xh, Vh = host_buffers
+            stats.append(sim.step_host(a[i], 0.5 * (prev + cur), cur, Xh, Vh, Xh, Vh, resc))
+    end.record(s)
+    torch.cuda.synchronize()
+    return start.elapsed_time(end), stats
+
+
+def run_gpu(args):
+    import torch
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    init_dist(world, "nccl")
+    from paper_2410_20501_gb300 import build, inputs, pm
+    if not os.path.exists(pm.LIB_PATH):
+        if rank == 0:
+            build.build()
+        barrier(world)
+    pm.lib()
+    a = schedule()
+    n = N_GRID
+    X, V = inputs.lpt_ics(n, BOX, OM, OL, a[0], SEED + rank, order=2, device="cuda")
+    npart = X.shape[1]
+    mg = pm.default_mg(tol=1e-7, stall=0.5, max_cycles=12)
+    fr = pm.default_fr(cycle=1, cycles=1)
+    W, K = args.warmup, args.steps
+    results = {}
+    for gravity in ("fr", "newton"):
+        sim = pm.Simulation(X, V, n, OM, OL, BOX, gravity=gravity, fR0=FR0, mg=mg, fr=fr)
+        timed_steps(sim, a, 0, W)
+        barrier(world)
+        torch.cuda.synchronize()
+        launches0 = pm.launch_count()
+        if gravity == "fr":
+            pm.timing_enable(True)
+        with ClockSampler(local) as clk:
+            ms, stats = timed_steps(sim, a, W, K)
+        launches = pm.launch_count() - launches0
+        kern = pm.timing_collect() if gravity == "fr" else None
+        if gravity == "fr":
+            pm.timing_enable(False)
+        ms = max_over_ranks(ms, world, "cuda")
+        results[gravity] = {"ms": ms, "stats": stats, "clocks": clk.summary(), "launches": launches,
+                            "kernels": kern}
+        if gravity == "fr":
+            # end to end through the C ABI with host buffers: H2D of X, V and D2H of X, V every step
+            Xh = torch.empty((3, npart), dtype=torch.int32).pin_memory()
+            Vh = torch.empty((3, npart), dtype=torch.float32).pin_memory()
+            Xh.copy_(sim.X)
+            Vh.copy_(sim.V)
+            barrier(world)
+            ms_e2e, _ = timed_steps(sim, a, W + K, K, host_buffers=(Xh, Vh))
+            results["e2e_ms"] = max_over_ranks(ms_e2e, world, "cuda")
+            results["e2e_bytes"] = int(Xh.numel() * 4 + Vh.numel() * 4)
+            del Xh, Vh
+        del sim
+        torch.cuda.empty_cache()
+    if rank != 0:
+        return 0
+
+    fr_res, nw_res = results["fr"], results["newton"]
+    total = world * npart * K
+    value = total / (fr_res["ms"] / 1e3)
+    peak, peak_kind = load_peaks()
+    kern = fr_res["kernels"]
+    dom = max(kern.items(), key=lambda kv: kv[1][0])
+    dname, (dms, dcount, dbytes) = dom
+    traffic = load_ncu_traffic().get(dname)
+    achieved = (dbytes / dcount) / (dms / dcount / 1e3) / 1e9 if dcount else None
+    roof = {"bound": "hbm", "kernel": dname, "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak if achieved else None,
+            "traffic": traffic.get("bytes_per_launch") if traffic else None,
+            "peak_source": peak_kind,
+            "launches": dcount, "avg_launch_ms": dms / dcount if dcount else None,
+            "share_of_step": dms / fr_res["ms"] if fr_res["ms"] else None}
+    per_kernel = {k: {"ms": round(v[0], 4), "launches": v[1],
+                      "GB/s": round(v[2] / (v[0] / 1e3) / 1e9, 1) if v[0] > 0 else None}
+                  for k, v in kern.items() if v[1] > 0}
+    line = {
+        "metric": METRIC, "value": value, "unit": "particle-steps/s", "n_gpus": world, "steps": K,
+        "warmup": W, "ms_per_step": fr_res["ms"] / K, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "hu-sawicki f(R) n=1 pm step, 512^3 particles, 512^3 grid, L=512 Mpc/h, "
+                               "2LPT z=30", "global_batch": world * npart, "n_grid": n, "boxsize_mpc_h": BOX,
+                   "fR0": FR0, "parallelism": f"replicas{world}", "l2": "inputs larger than L2 (every array "
+                   ">= 537 MB)", "poisson": "V-cycles to relative residual 1e-7 or float32 floor",
+                   "fr": "one FAS F-cycle per step"},
+        "newton": {"value": total / (nw_res["ms"] / 1e3), "ms_per_step": nw_res["ms"] / K,
+                   "gpu_launches": nw_res["launches"],
+                   "mg_cycles": [s["mg"]["cycles"] for s in nw_res["stats"]]},
+        "mg_cycles": [s["mg"]["cycles"] for s in fr_res["stats"]],
+        "e2e": {"value": total / (results["e2e_ms"] / 1e3), "unit": "particle-steps/s",
+                "h2d_bytes_per_step": results["e2e_bytes"], "d2h_bytes_per_step": results["e2e_bytes"]},
+        "gpu_launches": fr_res["launches"],
+        "roofline": roof,
+        "kernels": per_kernel,
+        "clocks": fr_res["clocks"],
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        cv, secs, sample = oracle_sample(1)
+        line["cpu_baseline"] = {"value": cv, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
+                                "sample": sample, "seconds": secs}
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -256,10 +256,12 @@ uint64_t pm_launch_count(void);
 /* Enable (1) / disable (0) CUDA-event timing of every launch, recorded on the
  * launch stream.  Enabling clears previous records. */
 pm_status pm_timing_enable(int on);
-/* Synchronises, then reports per kernel class: total milliseconds and
- * launches since pm_timing_enable(1).  Arrays are host, length cap; returns
- * the number of classes written.  names[i] are static strings. */
-int pm_timing_collect(const char** names, double* ms, int64_t* launches, int cap);
+/* Synchronises, then reports per kernel class since pm_timing_enable(1): total
+ * milliseconds, launches and algorithmic bytes (the compulsory DRAM traffic
+ * of each launch: data read once, results written once).  Arrays are host,
+ * length cap (any may be NULL); returns the number of classes written.
+ * names[i] are static strings. */
+int pm_timing_collect(const char** names, double* ms, int64_t* launches, double* bytes, int cap);
 
 #ifdef __cplusplus
 }

@@ -24,6 +24,7 @@ struct TimingPool {
   bool on = false;
   std::vector<cudaEvent_t> start, stop;
   std::vector<int> cls;
+  std::vector<double> bytes;
   size_t used = 0;
 };
 TimingPool g_timing;
@@ -33,16 +34,19 @@ size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 }  // namespace
 
-void launch_begin(int cls, cudaStream_t s) {
-  (void)cls;
+void launch_begin(int cls, double bytes, cudaStream_t s) {
   ++g_launches;
-  if (g_timing.on && g_timing.used < g_timing.start.size()) cudaEventRecord(g_timing.start[g_timing.used], s);
+  if (g_timing.on && g_timing.used < g_timing.start.size()) {
+    g_timing.cls[g_timing.used] = cls;
+    g_timing.bytes[g_timing.used] = bytes;
+    cudaEventRecord(g_timing.start[g_timing.used], s);
+  }
 }
 
 void launch_end(int cls, cudaStream_t s) {
   if (g_timing.on && g_timing.used < g_timing.start.size()) {
+    (void)cls;
     cudaEventRecord(g_timing.stop[g_timing.used], s);
-    g_timing.cls[g_timing.used] = cls;
     ++g_timing.used;
   }
 }
@@ -396,6 +400,7 @@ pm_status pm_timing_enable(int on) {
     g_timing.start.resize(kTimingCap);
     g_timing.stop.resize(kTimingCap);
     g_timing.cls.resize(kTimingCap);
+    g_timing.bytes.resize(kTimingCap);
     for (size_t i = 0; i < kTimingCap; ++i) {
       PM_TRY(cuda_status(cudaEventCreate(&g_timing.start[i])));
       PM_TRY(cuda_status(cudaEventCreate(&g_timing.stop[i])));
@@ -406,14 +411,15 @@ pm_status pm_timing_enable(int on) {
   return PM_OK;
 }
 
-int pm_timing_collect(const char** names, double* ms, int64_t* launches, int cap) {
+int pm_timing_collect(const char** names, double* ms, int64_t* launches, double* bytes, int cap) {
   if (cudaDeviceSynchronize() != cudaSuccess) return 0;
-  double tot[K_NCLASS] = {0};
+  double tot[K_NCLASS] = {0}, byt[K_NCLASS] = {0};
   int64_t cnt[K_NCLASS] = {0};
   for (size_t i = 0; i < g_timing.used; ++i) {
     float t = 0.0f;
     if (cudaEventElapsedTime(&t, g_timing.start[i], g_timing.stop[i]) == cudaSuccess) {
       tot[g_timing.cls[i]] += t;
+      byt[g_timing.cls[i]] += g_timing.bytes[i];
       cnt[g_timing.cls[i]] += 1;
     }
   }
@@ -422,6 +428,7 @@ int pm_timing_collect(const char** names, double* ms, int64_t* launches, int cap
     if (names) names[k] = kKernelClassNames[c];
     if (ms) ms[k] = tot[c];
     if (launches) launches[k] = cnt[c];
+    if (bytes) bytes[k] = byt[c];
     ++k;
   }
   return k;

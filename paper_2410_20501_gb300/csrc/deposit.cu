@@ -135,9 +135,9 @@ pm_status launch_deposit(const uint32_t* Xs, int64_t np, const uint32_t* cellsta
   const int tiles = n / T;
   const int64_t nblocks = (int64_t)tiles * tiles * tiles;
   const float scale = np > 0 ? (float)((double)n * n * n / (double)np) : 0.0f;
-  PM_LAUNCH(K_DEPOSIT, k_deposit<T>, (unsigned)nblocks, T * T * T, smem, s, Xs, np, cellstart, n,
+  PM_LAUNCH(K_DEPOSIT, 12.0 * np + 8.0 * n * n * (double)n + 4.0, k_deposit<T>, (unsigned)nblocks, T * T * T, smem, s, Xs, np, cellstart, n,
             ilog2(n), scale, rho, partials);
-  PM_LAUNCH(K_REDUCE, k_reduce_partials, 1, 1024, 0, s, partials, nblocks, (int64_t)0, 1,
+  PM_LAUNCH(K_REDUCE, 8.0 * nblocks, k_reduce_partials, 1, 1024, 0, s, partials, nblocks, (int64_t)0, 1,
             1.0 / ((double)n * n * n), mean_out);
   return launch_status();
 }
@@ -160,15 +160,15 @@ pm_status deposit_sorted(const uint32_t* Xs, int64_t np, const uint32_t* cellsta
 pm_status grid_mean(const float* f, int64_t count, double* partials, double* mean_out,
                     cudaStream_t s) {
   const unsigned nb = grid_for(count, 256, 152 * 8);
-  PM_LAUNCH(K_REDUCE, k_sum_partials, nb, 256, 0, s, f, count, partials);
-  PM_LAUNCH(K_REDUCE, k_reduce_partials, 1, 1024, 0, s, partials, (int64_t)nb, (int64_t)0, 1,
+  PM_LAUNCH(K_REDUCE, 4.0 * count, k_sum_partials, nb, 256, 0, s, f, count, partials);
+  PM_LAUNCH(K_REDUCE, 8.0 * nb, k_reduce_partials, 1, 1024, 0, s, partials, (int64_t)nb, (int64_t)0, 1,
             1.0 / (double)count, mean_out);
   return launch_status();
 }
 
 pm_status reduce_partials(const double* partials, int64_t count, int64_t stride, int nout,
                           double scale, double* out, cudaStream_t s) {
-  PM_LAUNCH(K_REDUCE, k_reduce_partials, 1, 1024, 0, s, partials, count, stride, nout, scale, out);
+  PM_LAUNCH(K_REDUCE, 8.0 * count * nout, k_reduce_partials, 1, 1024, 0, s, partials, count, stride, nout, scale, out);
   return launch_status();
 }
 

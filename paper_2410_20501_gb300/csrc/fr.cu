@@ -247,7 +247,7 @@ pm_status fr_smooth(FR& f, int l, int count) {
   const unsigned grid = grid_for(((int64_t)c.n * c.n * c.n) / 2, 256);
   for (int it = 0; it < count; ++it)
     for (int colour = 0; colour < 2; ++colour)
-      PM_LAUNCH(K_FR_SMOOTH, k_fr_sweep, grid, 256, 0, f.s, f.e[l], f.b[l], c.log2n, colour, c.beta, c.kappa,
+      PM_LAUNCH(K_FR_SMOOTH, 8.0 * c.n * c.n * (double)c.n, k_fr_sweep, grid, 256, 0, f.s, f.e[l], f.b[l], c.log2n, colour, c.beta, c.kappa,
                 c.q);
   return PM_OK;
 }
@@ -259,7 +259,7 @@ bool is_coarsest(const FR& f, int l) {
 
 pm_status fr_coarse(FR& f, int l) {
   const LevelConst c = level_const(f, l);
-  PM_LAUNCH(K_FR_COARSE, k_fr_coarse, 1, 1024, 0, f.s, f.e[l], f.b[l], c.log2n, c.alpha, c.beta, c.kappa,
+  PM_LAUNCH(K_FR_COARSE, 12.0 * c.n * c.n * (double)c.n, k_fr_coarse, 1, 1024, 0, f.s, f.e[l], f.b[l], c.log2n, c.alpha, c.beta, c.kappa,
             c.q, f.p->coarse_max_sweeps, f.p->coarse_drop);
   return PM_OK;
 }
@@ -269,9 +269,9 @@ pm_status fr_to_coarse(FR& f, int l) {
   PM_TRY(fr_smooth(f, l, f.p->npre));
   const LevelConst c = level_const(f, l), cH = level_const(f, l + 1);
   const int64_t nc = (int64_t)cH.n * cH.n * cH.n;
-  PM_LAUNCH(K_FR_RESTRICT, k_fr_restrict, grid_for(nc, 256), 256, 0, f.s, f.e[l], f.b[l], c.log2n, c.alpha,
+  PM_LAUNCH(K_FR_RESTRICT, 76.0 * nc, k_fr_restrict, grid_for(nc, 256), 256, 0, f.s, f.e[l], f.b[l], c.log2n, c.alpha,
             c.kappa, f.e[l + 1], f.r[l + 1], const_cast<float*>(f.b[l + 1].p));
-  PM_LAUNCH(K_FR_COARSEOP, k_fr_coarse_op, grid_for(nc, 256), 256, 0, f.s, f.e[l + 1],
+  PM_LAUNCH(K_FR_COARSEOP, 12.0 * nc, k_fr_coarse_op, grid_for(nc, 256), 256, 0, f.s, f.e[l + 1],
             const_cast<float*>(f.b[l + 1].p), cH.log2n, cH.alpha, cH.kappa);
   return PM_OK;
 }
@@ -336,7 +336,7 @@ pm_status fr_solve_src(Src b, float* eps, int n, const fr_params& prm, mg_stats*
   for (int c = 0; c < prm.max_cycles; ++c) {
     PM_TRY(one());
     local.cycles = c + 1;
-    PM_LAUNCH(K_FR_NORM, k_fr_norm, nb, 256, 0, s, eps, b, c0.log2n, c0.alpha, c0.kappa, w.partials);
+    PM_LAUNCH(K_FR_NORM, 8.0 * N, k_fr_norm, nb, 256, 0, s, eps, b, c0.log2n, c0.alpha, c0.kappa, w.partials);
     PM_TRY(reduce_partials(w.partials, nb, nb, 2, 1.0, w.scalars + 8, s));
     double h[2];
     PM_TRY(fetch_scalars(w.scalars + 8, h, 2, s));

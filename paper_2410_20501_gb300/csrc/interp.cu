@@ -128,9 +128,9 @@ void launch_grad(const float* phi, const float* eps, float alpha, float* g, int 
   const int64_t N = (int64_t)n * n * n;
   const unsigned grid = grid_for(N, 256);
   if (eps)
-    PM_LAUNCH(K_GRADIENT, (k_gradient<ORDER, true>), grid, 256, 0, s, phi, eps, alpha, g, ilog2(n), (float)n);
+    PM_LAUNCH(K_GRADIENT, 20.0 * N, (k_gradient<ORDER, true>), grid, 256, 0, s, phi, eps, alpha, g, ilog2(n), (float)n);
   else
-    PM_LAUNCH(K_GRADIENT, (k_gradient<ORDER, false>), grid, 256, 0, s, phi, eps, alpha, g, ilog2(n), (float)n);
+    PM_LAUNCH(K_GRADIENT, 16.0 * N, (k_gradient<ORDER, false>), grid, 256, 0, s, phi, eps, alpha, g, ilog2(n), (float)n);
 }
 
 }  // namespace
@@ -149,7 +149,7 @@ pm_status interp_launch(const float* g, const uint32_t* Xs, const float* Vs, con
                         float dt_drift, int mode, cudaStream_t s) {
   if (np == 0) return PM_OK;
   const float drift_scale = (float)((double)dt_drift * 4294967296.0);
-  PM_LAUNCH(K_INTERP, k_interp_kdk, grid_for(np, 256), 256, 0, s, g, Xs, Vs, ids_in, np, ilog2(n), acc, Xo, Vo,
+  PM_LAUNCH(K_INTERP, 12.0 * n * n * (double)n + np * (12.0 + (mode ? 36.0 : 0.0) + (acc ? 12.0 : 0.0) + (ids_out ? 8.0 : 0.0)), k_interp_kdk, grid_for(np, 256), 256, 0, s, g, Xs, Vs, ids_in, np, ilog2(n), acc, Xo, Vo,
             ids_out, dt_kick, drift_scale, mode);
   return launch_status();
 }

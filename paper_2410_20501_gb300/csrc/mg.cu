@@ -264,9 +264,9 @@ pm_status sweep(MG& g, int l, float omega, bool zero_guess, float gscale) {
   const float h2 = 1.0f / ((float)n * (float)n);
   const int64_t half = ((int64_t)n * n * n) / 2;
   const unsigned grid = grid_for(half, 256);
-  PM_LAUNCH(K_MG_SMOOTH, k_rb_sweep, grid, 256, 0, g.s, g.u[l], g.f[l], log2n, 0, omega, h2, gscale,
+  PM_LAUNCH(K_MG_SMOOTH, (zero_guess ? 4.0 : 8.0) * half * 2.0, k_rb_sweep, grid, 256, 0, g.s, g.u[l], g.f[l], log2n, 0, omega, h2, gscale,
             zero_guess ? 1 : 0);
-  PM_LAUNCH(K_MG_SMOOTH, k_rb_sweep, grid, 256, 0, g.s, g.u[l], g.f[l], log2n, 1, omega, h2, 1.0f, 0);
+  PM_LAUNCH(K_MG_SMOOTH, 8.0 * half * 2.0, k_rb_sweep, grid, 256, 0, g.s, g.u[l], g.f[l], log2n, 1, omega, h2, 1.0f, 0);
   return PM_OK;
 }
 
@@ -278,9 +278,9 @@ pm_status v_cycle(MG& g, int l, bool zero_guess) {
     float* u = g.u[l];
     if (!zero_guess && l == 0 && g.first_cycle && g.gscale != 1.0f) {
       const int64_t N = (int64_t)n * n * n;
-      PM_LAUNCH(K_MG_GUESS, k_scale, grid_for(N, 256), 256, 0, g.s, u, N, g.gscale);
+      PM_LAUNCH(K_MG_GUESS, 8.0 * N, k_scale, grid_for(N, 256), 256, 0, g.s, u, N, g.gscale);
     }
-    PM_LAUNCH(K_MG_COARSE, k_mg_coarse, 1, 1024, 0, g.s, u, g.f[l], log2n, h2, p.omega,
+    PM_LAUNCH(K_MG_COARSE, 12.0 * n * n * n, k_mg_coarse, 1, 1024, 0, g.s, u, g.f[l], log2n, h2, p.omega,
               p.coarse_max_sweeps, p.coarse_drop, zero_guess ? 1 : 0);
     return PM_OK;
   }
@@ -288,7 +288,7 @@ pm_status v_cycle(MG& g, int l, bool zero_guess) {
   if (p.npre == 0) {
     const int64_t N = (int64_t)n * n * n;
     if (zero_guess) PM_TRY(cuda_status(cudaMemsetAsync(g.u[l], 0, N * sizeof(float), g.s)));
-    else if (fuse_scale) PM_LAUNCH(K_MG_GUESS, k_scale, grid_for(N, 256), 256, 0, g.s, g.u[l], N, g.gscale);
+    else if (fuse_scale) PM_LAUNCH(K_MG_GUESS, 8.0 * N, k_scale, grid_for(N, 256), 256, 0, g.s, g.u[l], N, g.gscale);
   }
   for (int si = 0; si < p.npre; ++si) {
     const float om = si == 0 ? 1.0f : p.omega;
@@ -297,13 +297,13 @@ pm_status v_cycle(MG& g, int l, bool zero_guess) {
   const int64_t nc = ((int64_t)n * n * n) / 8;
   const unsigned grid = grid_for(nc, 256);
   if (l == 0)
-    PM_LAUNCH(K_MG_RESTRICT, k_resid_restrict<true>, grid, 256, 0, g.s, g.u[l], g.f[l], log2n,
+    PM_LAUNCH(K_MG_RESTRICT, 68.0 * nc, k_resid_restrict<true>, grid, 256, 0, g.s, g.u[l], g.f[l], log2n,
               (float)n * (float)n, const_cast<float*>(g.f[l + 1].p));
   else
-    PM_LAUNCH(K_MG_RESTRICT, k_resid_restrict<false>, grid, 256, 0, g.s, g.u[l], g.f[l], log2n,
+    PM_LAUNCH(K_MG_RESTRICT, 68.0 * nc, k_resid_restrict<false>, grid, 256, 0, g.s, g.u[l], g.f[l], log2n,
               (float)n * (float)n, const_cast<float*>(g.f[l + 1].p));
   PM_TRY(v_cycle(g, l + 1, true));
-  PM_LAUNCH(K_MG_PROLONG, k_prolong_correct, grid_for(nc * 8, 256), 256, 0, g.s, g.u[l], g.u[l + 1],
+  PM_LAUNCH(K_MG_PROLONG, 68.0 * nc, k_prolong_correct, grid_for(nc * 8, 256), 256, 0, g.s, g.u[l], g.u[l + 1],
             (const float*)nullptr, log2n);
   for (int si = 0; si < p.npost; ++si) {
     const float om = si == p.npost - 1 ? 1.0f : p.omega;
@@ -317,7 +317,7 @@ pm_status v_cycle(MG& g, int l, bool zero_guess) {
 pm_status prolong_correct_launch(float* u, const float* uc, const float* uc2, int n_fine, int cls,
                                  cudaStream_t s) {
   const int64_t N = (int64_t)n_fine * n_fine * n_fine;
-  PM_LAUNCH(cls, k_prolong_correct, grid_for(N, 256), 256, 0, s, u, uc, uc2, ilog2(n_fine));
+  PM_LAUNCH(cls, 8.0 * N + (uc2 ? 1.0 : 0.5) * N, k_prolong_correct, grid_for(N, 256), 256, 0, s, u, uc, uc2, ilog2(n_fine));
   return PM_OK;
 }
 
@@ -347,7 +347,7 @@ pm_status mg_solve_src(Src f, float* phi, int n, const mg_params& prm, mg_stats*
   const int64_t N = (int64_t)n * n * n;
   const float h2 = 1.0f / ((float)n * (float)n);
   if (prm.first_guess == MG_GUESS_JACOBI)
-    PM_LAUNCH(K_MG_GUESS, k_jacobi_guess, grid_for(N, 256), 256, 0, s, phi, f, N, h2);
+    PM_LAUNCH(K_MG_GUESS, 8.0 * N, k_jacobi_guess, grid_for(N, 256), 256, 0, s, phi, f, N, h2);
   mg_stats local{PM_OK, 0, -1.0, -1.0, -1.0};
   if (prm.fixed_cycles > 0) {
     for (int c = 0; c < prm.fixed_cycles; ++c) {
@@ -366,7 +366,7 @@ pm_status mg_solve_src(Src f, float* phi, int n, const mg_params& prm, mg_stats*
     PM_TRY(v_cycle(g, 0, false));
     g.first_cycle = false;
     local.cycles = c + 1;
-    PM_LAUNCH(K_MG_NORM, k_resid_norm, nb, 256, 0, s, phi, f, log2n, (float)n * (float)n, w.partials);
+    PM_LAUNCH(K_MG_NORM, 8.0 * N, k_resid_norm, nb, 256, 0, s, phi, f, log2n, (float)n * (float)n, w.partials);
     PM_TRY(reduce_partials(w.partials, nb, nb, 2, 1.0, w.scalars + 4, s));
     double h[2];
     PM_TRY(fetch_scalars(w.scalars + 4, h, 2, s));

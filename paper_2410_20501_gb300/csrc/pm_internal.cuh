@@ -20,7 +20,7 @@ enum KernelClass {
 
 extern const char* const kKernelClassNames[K_NCLASS];
 
-void launch_begin(int cls, cudaStream_t s);
+void launch_begin(int cls, double bytes, cudaStream_t s);
 void launch_end(int cls, cudaStream_t s);
 
 // Records a CUDA error string and maps it to PM_ECUDA (PM_OK on cudaSuccess).
@@ -115,9 +115,11 @@ pm_status fetch_scalars(const double* dev, double* host, int count, cudaStream_t
 
 }  // namespace pmgb
 
-#define PM_LAUNCH(cls, kern, grid, block, smem, st, ...)              \
+// Launch with instrumentation: `bytes` is the kernel's algorithmic (compulsory)
+// DRAM traffic for this launch, accumulated per class while timing is on.
+#define PM_LAUNCH(cls, bytes, kern, grid, block, smem, st, ...)       \
   do {                                                                 \
-    ::pmgb::launch_begin((cls), (st));                                 \
+    ::pmgb::launch_begin((cls), (double)(bytes), (st));                \
     kern<<<(grid), (block), (smem), (st)>>>(__VA_ARGS__);              \
     ::pmgb::launch_end((cls), (st));                                   \
   } while (0)

@@ -247,9 +247,9 @@ __global__ void k_permute(const uint32_t* __restrict__ perm, int64_t np,
 pm_status scan_u32(uint32_t* a, int64_t len, uint32_t* sums, cudaStream_t s) {
   int64_t nb = (len + SCAN_CHUNK - 1) / SCAN_CHUNK;
   if (nb == 0) return PM_OK;
-  PM_LAUNCH(K_SORT_SCAN, k_scan_reduce, (unsigned)nb, SCAN_T, 0, s, a, len, sums);
-  PM_LAUNCH(K_SORT_SCAN, k_scan_sums, 1, SCAN_T, 0, s, sums, nb);
-  PM_LAUNCH(K_SORT_SCAN, k_scan_apply, (unsigned)nb, SCAN_T, 0, s, a, len, sums);
+  PM_LAUNCH(K_SORT_SCAN, 4.0 * len, k_scan_reduce, (unsigned)nb, SCAN_T, 0, s, a, len, sums);
+  PM_LAUNCH(K_SORT_SCAN, 8.0 * nb, k_scan_sums, 1, SCAN_T, 0, s, sums, nb);
+  PM_LAUNCH(K_SORT_SCAN, 8.0 * len, k_scan_apply, (unsigned)nb, SCAN_T, 0, s, a, len, sums);
   return PM_OK;
 }
 
@@ -273,7 +273,7 @@ pm_status sort_particles(const uint32_t* X, int64_t np, int n, Workspace& w, cud
   *perm_out = w.vals_a;
   *skeys_out = w.keys_a;
   if (np == 0) return PM_OK;
-  PM_LAUNCH(K_KEYS, k_cell_keys, grid_for(np, 256), 256, 0, s, X, np, log2n, w.keys_a);
+  PM_LAUNCH(K_KEYS, 16.0 * np, k_cell_keys, grid_for(np, 256), 256, 0, s, X, np, log2n, w.keys_a);
   const int keybits = 3 * log2n;
   const int passes = (keybits + 8) / 9;
   const int bpp = (keybits + passes - 1) / passes;
@@ -285,9 +285,9 @@ pm_status sort_particles(const uint32_t* X, int64_t np, int n, Workspace& w, cud
     const int64_t len = ((int64_t)1 << rb) * ntiles;
     uint32_t* kout = (kin == w.keys_a) ? w.keys_b : w.keys_a;
     uint32_t* vout = (vin == w.vals_b) ? w.vals_a : w.vals_b;
-    PM_LAUNCH(K_SORT_UP, k_radix_up, (unsigned)ntiles, RT, 0, s, kin, np, shift, rb, w.counts, ntiles);
+    PM_LAUNCH(K_SORT_UP, 4.0 * np, k_radix_up, (unsigned)ntiles, RT, 0, s, kin, np, shift, rb, w.counts, ntiles);
     PM_TRY(scan_u32(w.counts, len, w.scan_blocks, s));
-    PM_LAUNCH(K_SORT_DOWN, k_radix_down, (unsigned)ntiles, RT, kDownSmem, s, kin, vin, np, shift, rb,
+    PM_LAUNCH(K_SORT_DOWN, (vin ? 16.0 : 12.0) * np, k_radix_down, (unsigned)ntiles, RT, kDownSmem, s, kin, vin, np, shift, rb,
               w.counts, ntiles, kout, vout);
     kin = kout;
     vin = vout;
@@ -300,7 +300,7 @@ pm_status sort_particles(const uint32_t* X, int64_t np, int n, Workspace& w, cud
 pm_status build_cellstart(const uint32_t* skeys, int64_t np, int n, uint32_t* cellstart,
                           cudaStream_t s) {
   const uint32_t ncells = (uint32_t)((int64_t)n * n * n);
-  PM_LAUNCH(K_CELLSTART, k_cellstart, grid_for(np + 1, 256), 256, 0, s, skeys, np, ncells, cellstart);
+  PM_LAUNCH(K_CELLSTART, 4.0 * np + 4.0 * (ncells + 1.0), k_cellstart, grid_for(np + 1, 256), 256, 0, s, skeys, np, ncells, cellstart);
   return launch_status();
 }
 
@@ -308,7 +308,7 @@ pm_status permute_particles(const uint32_t* perm, int64_t np, const uint32_t* X,
                             const uint32_t* id, uint32_t* Xs, float* Vs, uint32_t* ids,
                             cudaStream_t s) {
   if (np == 0) return PM_OK;
-  PM_LAUNCH(K_PERMUTE, k_permute, grid_for(np, 256), 256, 0, s, perm, np, X, V, id, Xs, Vs, ids);
+  PM_LAUNCH(K_PERMUTE, (28.0 + (V ? 24.0 : 0.0) + (id ? 8.0 : 0.0)) * np, k_permute, grid_for(np, 256), 256, 0, s, perm, np, X, V, id, Xs, Vs, ids);
   return launch_status();
 }
 

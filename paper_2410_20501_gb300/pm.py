@@ -105,7 +105,8 @@ _SIGS = {
     "pm_launch_count": (ctypes.c_uint64, []),
     "pm_timing_enable": (ctypes.c_int, [ctypes.c_int]),
     "pm_timing_collect": (ctypes.c_int, [ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_double),
-                                         ctypes.POINTER(ctypes.c_int64), ctypes.c_int]),
+                                         ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double),
+                                         ctypes.c_int]),
 }
 
 
@@ -260,12 +261,14 @@ def timing_enable(on=True):
 
 
 def timing_collect():
+    """{kernel class: (total ms, launches, algorithmic bytes)} since timing_enable()."""
     cap = 64
     names = (ctypes.c_char_p * cap)()
     ms = (ctypes.c_double * cap)()
     cnt = (ctypes.c_int64 * cap)()
-    k = lib().pm_timing_collect(names, ms, cnt, cap)
-    return {names[i].decode(): (ms[i], cnt[i]) for i in range(k)}
+    byt = (ctypes.c_double * cap)()
+    k = lib().pm_timing_collect(names, ms, cnt, byt, cap)
+    return {names[i].decode(): (ms[i], cnt[i], byt[i]) for i in range(k)}
 
 
 class Simulation:
