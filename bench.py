@@ -180,24 +180,34 @@ def run_reference(args):
 
 # ------------------------------------------------------------------ GPU arm --
 
-def timed_steps(sim, a, first, count, host_buffers=None):
-    """Runs steps first .. first+count-1 of the schedule; returns device ms."""
-    import torch
+def step_coefficients(Om, OL, a):
+    """Per step i of the schedule: (a_i, kick, drift, potential rescale), with
+    the two half kicks around a_i merged: kick_i = (dt_{i-1} + dt_i)/2."""
     from paper_2410_20501_gb300 import pm
+    dts = [pm.dt_supercomoving(Om, OL, a[i], a[i + 1]) for i in range(len(a) - 1)]
+    D = [pm.growth_D(Om, OL, x) for x in a]
+    out = []
+    for i in range(len(a) - 1):
+        prev = dts[i - 1] if i > 0 else 0.0
+        resc = (a[i] * D[i]) / (a[i - 1] * D[i - 1]) if i > 0 else 1.0
+        out.append((a[i], 0.5 * (prev + dts[i]), dts[i], resc))
+    return out
+
+
+def timed_steps(sim, coeffs, first, count, host_buffers=None):
+    """Runs steps first .. first+count-1; returns (device ms, per-step stats)."""
+    import torch
     s = torch.cuda.current_stream()
     start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    Om, OL = sim.Om, sim.OL
     stats = []
     start.record(s)
     for i in range(first, first + count):
-        prev = pm.dt_supercomoving(Om, OL, a[i - 1], a[i]) if i > 0 else 0.0
-        cur = pm.dt_supercomoving(Om, OL, a[i], a[i + 1])
-        resc = (a[i] * pm.growth_D(Om, OL, a[i])) / (a[i - 1] * pm.growth_D(Om, OL, a[i - 1])) if i > 0 else 1.0
+        a, kick, drift, resc = coeffs[i]
         if host_buffers is None:
-            stats.append(sim.step(a[i], 0.5 * (prev + cur), cur, resc))
+            stats.append(sim.step(a, kick, drift, resc))
         else:
             Xh, Vh = host_buffers
-            stats.append(sim.step_host(a[i], 0.5 * (prev + cur), cur, Xh, Vh, Xh, Vh, resc))
+            stats.append(sim.step_host(a, kick, drift, Xh, Vh, Xh, Vh, resc))
     end.record(s)
     torch.cuda.synchronize()
     return start.elapsed_time(end), stats
@@ -215,6 +225,7 @@ def run_gpu(args):
         barrier(world)
     pm.lib()
     a = schedule()
+    coeffs = step_coefficients(OM, OL, a)
     n = N_GRID
     X, V = inputs.lpt_ics(n, BOX, OM, OL, a[0], SEED + rank, order=2, device="cuda")
     npart = X.shape[1]
@@ -222,16 +233,16 @@ def run_gpu(args):
     fr = pm.default_fr(cycle=1, cycles=1)
     W, K = args.warmup, args.steps
     results = {}
-    for gravity in ("fr", "newton"):
+    for gravity in (("fr",) if args.lean else ("fr", "newton")):
         sim = pm.Simulation(X, V, n, OM, OL, BOX, gravity=gravity, fR0=FR0, mg=mg, fr=fr)
-        timed_steps(sim, a, 0, W)
+        timed_steps(sim, coeffs, 0, W)
         barrier(world)
         torch.cuda.synchronize()
         launches0 = pm.launch_count()
         if gravity == "fr":
             pm.timing_enable(True)
         with ClockSampler(local) as clk:
-            ms, stats = timed_steps(sim, a, W, K)
+            ms, stats = timed_steps(sim, coeffs, W, K)
         launches = pm.launch_count() - launches0
         kern = pm.timing_collect() if gravity == "fr" else None
         if gravity == "fr":
@@ -239,14 +250,14 @@ def run_gpu(args):
         ms = max_over_ranks(ms, world, "cuda")
         results[gravity] = {"ms": ms, "stats": stats, "clocks": clk.summary(), "launches": launches,
                             "kernels": kern}
-        if gravity == "fr":
+        if gravity == "fr" and not args.lean:
             # end to end through the C ABI with host buffers: H2D of X, V and D2H of X, V every step
             Xh = torch.empty((3, npart), dtype=torch.int32).pin_memory()
             Vh = torch.empty((3, npart), dtype=torch.float32).pin_memory()
             Xh.copy_(sim.X)
             Vh.copy_(sim.V)
             barrier(world)
-            ms_e2e, _ = timed_steps(sim, a, W + K, K, host_buffers=(Xh, Vh))
+            ms_e2e, _ = timed_steps(sim, coeffs, W + K, K, host_buffers=(Xh, Vh))
             results["e2e_ms"] = max_over_ranks(ms_e2e, world, "cuda")
             results["e2e_bytes"] = int(Xh.numel() * 4 + Vh.numel() * 4)
             del Xh, Vh
@@ -255,7 +266,7 @@ def run_gpu(args):
     if rank != 0:
         return 0
 
-    fr_res, nw_res = results["fr"], results["newton"]
+    fr_res, nw_res = results["fr"], results.get("newton")
     total = world * npart * K
     value = total / (fr_res["ms"] / 1e3)
     peak, peak_kind = load_peaks()
@@ -282,19 +293,20 @@ def run_gpu(args):
                    "fR0": FR0, "parallelism": f"replicas{world}", "l2": "inputs larger than L2 (every array "
                    ">= 537 MB)", "poisson": "V-cycles to relative residual 1e-7 or float32 floor",
                    "fr": "one FAS F-cycle per step"},
-        "newton": {"value": total / (nw_res["ms"] / 1e3), "ms_per_step": nw_res["ms"] / K,
-                   "gpu_launches": nw_res["launches"],
-                   "mg_cycles": [s["mg"]["cycles"] for s in nw_res["stats"]]},
+        "newton": None if nw_res is None else {
+            "value": total / (nw_res["ms"] / 1e3), "ms_per_step": nw_res["ms"] / K,
+            "gpu_launches": nw_res["launches"], "mg_cycles": [s["mg"]["cycles"] for s in nw_res["stats"]]},
         "mg_cycles": [s["mg"]["cycles"] for s in fr_res["stats"]],
-        "e2e": {"value": total / (results["e2e_ms"] / 1e3), "unit": "particle-steps/s",
-                "h2d_bytes_per_step": results["e2e_bytes"], "d2h_bytes_per_step": results["e2e_bytes"]},
+        "e2e": None if "e2e_ms" not in results else {
+            "value": total / (results["e2e_ms"] / 1e3), "unit": "particle-steps/s",
+            "h2d_bytes_per_step": results["e2e_bytes"], "d2h_bytes_per_step": results["e2e_bytes"]},
         "gpu_launches": fr_res["launches"],
         "roofline": roof,
         "kernels": per_kernel,
         "clocks": fr_res["clocks"],
     }
-    if world == 1 and not args.no_cpu_baseline:
-        cv, secs, sample = oracle_sample(1)
+    if world == 1 and not args.no_cpu_baseline and not args.lean:
+        cv, secs, sample = oracle_sample(8)
         line["cpu_baseline"] = {"value": cv, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
                                 "sample": sample, "seconds": secs}
     print(json.dumps(line))
@@ -308,6 +320,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--lean", action="store_true",
+                    help="f(R) device-timed steps only (no Newtonian line, e2e or CPU baseline): for profilers")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
