@@ -96,11 +96,15 @@ class FASParams:
 
 
 def _coarse(u, b, h, fbar, kappa, prm):
-    r0 = np.linalg.norm(b - operator(u, h, fbar, kappa))
+    """Coarsest level: non-linear sweeps until the residual dropped by
+    ``coarse_drop``, a sweep no longer lowers it, or ``coarse_max_sweeps``."""
+    r0 = prev = np.linalg.norm(b - operator(u, h, fbar, kappa))
     for _ in range(prm.coarse_max_sweeps):
         gs_sweep(u, b, h, fbar, kappa)
-        if np.linalg.norm(b - operator(u, h, fbar, kappa)) <= prm.coarse_drop * r0:
+        r = np.linalg.norm(b - operator(u, h, fbar, kappa))
+        if r <= prm.coarse_drop * r0 or r >= prev:
             break
+        prev = r
     return u
 
 

@@ -105,13 +105,16 @@ class MGParams:
 
 def coarse_solve(u, f, h, prm):
     """Coarsest level: red-black SOR sweeps until the level residual has dropped
-    by ``coarse_drop`` or ``coarse_max_sweeps`` sweeps (the paper does not state
-    the coarsest-level method; this is the reading used throughout)."""
-    r0 = np.linalg.norm(residual(u, f, h))
+    by ``coarse_drop``, a sweep no longer lowers it, or ``coarse_max_sweeps``
+    sweeps (the paper does not state the coarsest-level method; this is the
+    reading used throughout)."""
+    r0 = prev = np.linalg.norm(residual(u, f, h))
     for _ in range(prm.coarse_max_sweeps):
         rbgs_sweep(u, f, h, prm.omega)
-        if np.linalg.norm(residual(u, f, h)) <= prm.coarse_drop * r0:
+        r = np.linalg.norm(residual(u, f, h))
+        if r <= prm.coarse_drop * r0 or r >= prev:
             break
+        prev = r
     return u
 
 

@@ -30,24 +30,30 @@ __device__ __forceinline__ int64_t idx3(int i, int j, int k, int log2n) {
 }
 
 // Root eps > -1 of g(e) = e^3 + 3e^2 + c1 e + c0 (g(-1) = q < 0, g convex on
-// e > -1).  Newton from the current value, kept inside a shrinking bracket
-// [lo, hi] with bisection as the fallback; hi starts at the bound
-// u* <= sqrt(max(-p, 0)) + (-q)^(1/3), p = c1 - 3.
+// e > -1, so the root is unique).  Newton from the current value inside a
+// shrinking bracket [lo, hi]; when a step leaves the bracket (or g' <= 0) the
+// upper end is set from the bound u* <= sqrt(max(-p, 0)) + (-q)^(1/3),
+// p = c1 - 3, and the step falls back to bisection.  Stops when g is at its
+// float32 rounding level or the step is below 1e-6 relative.
 __device__ __forceinline__ float fr_root(float e, float c1, float c0, float q) {
-  float lo = -1.0f;
-  float hi = sqrtf(fmaxf(3.0f - c1, 0.0f)) + cbrtf(-q) - 1.0f;
-  if (!(e > lo && e < hi)) e = hi;
-  for (int it = 0; it < 40; ++it) {
+  float lo = -1.0f, hi = __int_as_float(0x7f800000);  // +inf until needed
+  if (!(e > lo)) e = 0.0f;
+  for (int it = 0; it < 30; ++it) {
+    const float e2 = e * e;
     const float g = ((e + 3.0f) * e + c1) * e + c0;
     const float gp = (3.0f * e + 6.0f) * e + c1;
     if (g > 0.0f) hi = fminf(hi, e);
     else if (g < 0.0f) lo = fmaxf(lo, e);
     else return e;
-    float en = gp > 0.0f ? e - __fdividef(g, gp) : 0.5f * (lo + hi);
-    if (!(en > lo && en < hi)) en = 0.5f * (lo + hi);
-    const bool done = fabsf(en - e) <= 1e-7f * fabsf(en) + 1e-30f;
+    const float noise = 4e-7f * (fabsf(c0) + fabsf(c1 * e) + 3.0f * e2 + fabsf(e2 * e));
+    if (fabsf(g) <= noise) return e;
+    float en = gp > 0.0f ? e - __fdividef(g, gp) : lo;
+    if (!(en > lo && en < hi)) {
+      if (isinf(hi)) hi = fmaxf(sqrtf(fmaxf(3.0f - c1, 0.0f)) + cbrtf(-q) - 1.0f, lo);
+      en = 0.5f * (lo + hi);
+    }
+    if (fabsf(en - e) <= 1e-6f * fabsf(en) + 1e-12f) return en;
     e = en;
-    if (done) break;
   }
   return e;
 }
@@ -164,7 +170,8 @@ __global__ void __launch_bounds__(256) k_fr_norm(const float* __restrict__ e, Sr
 }
 
 // Coarsest level (n <= 16) in one CTA: non-linear sweeps until the residual
-// dropped by `drop` or `max_sweeps` sweeps.
+// dropped by `drop`, a sweep no longer lowers it (float32 floor), or
+// `max_sweeps` sweeps.
 __global__ void __launch_bounds__(1024) k_fr_coarse(float* __restrict__ e, Src b, int log2n, float alpha,
                                                     float beta, float kappa, float q, int max_sweeps,
                                                     float drop) {
@@ -198,7 +205,8 @@ __global__ void __launch_bounds__(1024) k_fr_coarse(float* __restrict__ e, Src b
     block_sum_to(&r2, s, cmp, scratch);
     return r2;
   };
-  const double target = (double)drop * (double)drop * norm2();
+  double prev = norm2();
+  const double target = (double)drop * (double)drop * prev;
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
     for (int colour = 0; colour < 2; ++colour) {
       for (int c = threadIdx.x; c < N; c += blockDim.x) {
@@ -210,7 +218,9 @@ __global__ void __launch_bounds__(1024) k_fr_coarse(float* __restrict__ e, Src b
       }
       __syncthreads();
     }
-    if (norm2() <= target) break;
+    const double r = norm2();
+    if (r <= target || r >= prev) break;   // converged, or at the float32 floor
+    prev = r;
   }
   for (int c = threadIdx.x; c < N; c += blockDim.x) e[c] = se[c];
 }

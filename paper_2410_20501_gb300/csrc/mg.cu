@@ -195,7 +195,8 @@ __global__ void k_prolong_correct(float* __restrict__ u, const float* __restrict
 }
 
 // Coarsest level (n <= 16) in one CTA: red-black SOR sweeps until the residual
-// norm dropped by `drop` or `max_sweeps` sweeps.
+// norm dropped by `drop`, a sweep no longer lowers it (float32 floor), or
+// `max_sweeps` sweeps.
 __global__ void __launch_bounds__(1024) k_mg_coarse(float* __restrict__ u, Src f, int log2n, float h2,
                                                     float omega, int max_sweeps, float drop,
                                                     int zero_guess) {
@@ -226,8 +227,8 @@ __global__ void __launch_bounds__(1024) k_mg_coarse(float* __restrict__ u, Src f
     block_sum_to(&r2, s, cmp, scratch);
     return r2;
   };
-  const double r0 = norm2();
-  const double target = (double)drop * (double)drop * r0;
+  double prev = norm2();
+  const double target = (double)drop * (double)drop * prev;
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
     for (int colour = 0; colour < 2; ++colour) {
       for (int c = threadIdx.x; c < N; c += blockDim.x) {
@@ -244,7 +245,9 @@ __global__ void __launch_bounds__(1024) k_mg_coarse(float* __restrict__ u, Src f
       }
       __syncthreads();
     }
-    if (norm2() <= target) break;
+    const double r = norm2();
+    if (r <= target || r >= prev) break;   // converged, or at the float32 floor
+    prev = r;
   }
   for (int c = threadIdx.x; c < N; c += blockDim.x) u[c] = su[c];
 }

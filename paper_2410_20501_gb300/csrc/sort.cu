@@ -33,6 +33,8 @@ __global__ void k_cell_keys(const uint32_t* __restrict__ X, int64_t np, int log2
 }
 
 // Per-tile digit histogram, written digit-major: counts[d * ntiles + tile].
+// Each thread counts RI consecutive keys and adds runs of equal digits with
+// one shared atomic (cell-ordered input has long runs in the high digits).
 __global__ void __launch_bounds__(RT) k_radix_up(const uint32_t* __restrict__ keys, int64_t np,
                                                  int shift, int rbits,
                                                  uint32_t* __restrict__ counts, int64_t ntiles) {
@@ -40,15 +42,32 @@ __global__ void __launch_bounds__(RT) k_radix_up(const uint32_t* __restrict__ ke
   const int R = 1 << rbits;
   for (int d = threadIdx.x; d < R; d += RT) hist[d] = 0;
   __syncthreads();
-  const int64_t base = (int64_t)blockIdx.x * RTILE;
-  const int lane = threadIdx.x & 31;
-  for (int r = 0; r < RI; ++r) {
-    int64_t i = base + (int64_t)r * RT + threadIdx.x;
-    bool valid = i < np;
-    uint32_t d = valid ? ((__ldg(keys + i) >> shift) & (R - 1)) : (uint32_t)R;
-    uint32_t peers = __match_any_sync(0xffffffffu, d);
-    if (valid && lane == __ffs(peers) - 1) atomicAdd(&hist[d], (uint32_t)__popc(peers));
+  const int64_t base = (int64_t)blockIdx.x * RTILE + (int64_t)threadIdx.x * RI;
+  uint32_t k[RI];
+  if (base + RI <= np) {
+    const uint4* v = reinterpret_cast<const uint4*>(keys + base);
+#pragma unroll
+    for (int q = 0; q < RI / 4; ++q) {
+      const uint4 t = __ldg(v + q);
+      k[4 * q] = t.x; k[4 * q + 1] = t.y; k[4 * q + 2] = t.z; k[4 * q + 3] = t.w;
+    }
+  } else {
+#pragma unroll
+    for (int r = 0; r < RI; ++r) k[r] = base + r < np ? __ldg(keys + base + r) : 0xffffffffu;
   }
+  uint32_t cur = 0xffffffffu, run = 0;
+#pragma unroll
+  for (int r = 0; r < RI; ++r) {
+    if (base + r >= np) break;
+    const uint32_t d = (k[r] >> shift) & (R - 1);
+    if (d != cur) {
+      if (run) atomicAdd(&hist[cur], run);
+      cur = d;
+      run = 0;
+    }
+    ++run;
+  }
+  if (run) atomicAdd(&hist[cur], run);
   __syncthreads();
   for (int d = threadIdx.x; d < R; d += RT) counts[(int64_t)d * ntiles + blockIdx.x] = hist[d];
 }
