@@ -111,12 +111,16 @@ typedef struct {
                              host synchronisation (CUDA-graph capturable)       */
   double tol;             /* stop when ||f - L phi||_2 <= tol ||f||_2           */
   double stall;           /* also stop (PM_OK) when a cycle reduced the residual
-                             by less than 1/stall: the float32 floor            */
+                             by less than 1/stall while it is below 1e-3 ||f||:
+                             the float32 floor of the stored iterate           */
   int first_guess;        /* MG_GUESS_INPUT: phi holds the guess;
                              MG_GUESS_JACOBI: -h^2 f / 6 (Eq. multigrid_initial_guess);
                              MG_GUESS_SCALED: guess_scale * phi (the warm start
                              of Eq. rescaming_newtonian_potential)              */
   float guess_scale;
+  int smoother;           /* 0: streaming red-black kernel (two sweeps per pass
+                             over memory) on levels with n >= 128, colour
+                             passes below; 1: colour passes everywhere         */
 } mg_params;
 
 typedef struct {
@@ -131,7 +135,8 @@ typedef struct {
 
 /* Default parameters: npre = npost = 2, omega = 1.25, coarsest = 16,
  * coarse_max_sweeps = 200, coarse_drop = 1e-3, max_cycles = 30,
- * fixed_cycles = 0, tol = 1e-7, stall = 0.5, first_guess = MG_GUESS_INPUT. */
+ * fixed_cycles = 0, tol = 1e-7, stall = 0.5, first_guess = MG_GUESS_INPUT,
+ * smoother = 0. */
 void mg_default_params(mg_params* p);
 
 /* Solve the periodic Poisson problem (L(phi) - 6 phi)/h^2 = f - <f>, h = 1/n,
@@ -158,6 +163,7 @@ typedef struct {
   int cycles;        /* cycles to run when tol <= 0                           */
   double tol;        /* > 0: cycle until ||b - N(u)|| <= tol ||b|| (synchronises) */
   int max_cycles;
+  int smoother;      /* as mg_params.smoother                                   */
 } fr_params;
 
 void fr_default_params(fr_params* p);

@@ -97,14 +97,21 @@ class FASParams:
 
 def _coarse(u, b, h, fbar, kappa, prm):
     """Coarsest level: non-linear sweeps until the residual dropped by
-    ``coarse_drop``, a sweep no longer lowers it, or ``coarse_max_sweeps``."""
-    r0 = prev = np.linalg.norm(b - operator(u, h, fbar, kappa))
+    ``coarse_drop``, its running minimum stalls (no 0.1% gain in 5 sweeps),
+    or ``coarse_max_sweeps``."""
+    r0 = best = np.linalg.norm(b - operator(u, h, fbar, kappa))
+    stale = 0
     for _ in range(prm.coarse_max_sweeps):
         gs_sweep(u, b, h, fbar, kappa)
         r = np.linalg.norm(b - operator(u, h, fbar, kappa))
-        if r <= prm.coarse_drop * r0 or r >= prev:
+        if r <= prm.coarse_drop * r0:
             break
-        prev = r
+        if r < 0.999 * best:
+            best, stale = r, 0
+        else:
+            stale += 1
+            if stale >= 5:
+                break
     return u
 
 

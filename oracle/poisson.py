@@ -105,16 +105,22 @@ class MGParams:
 
 def coarse_solve(u, f, h, prm):
     """Coarsest level: red-black SOR sweeps until the level residual has dropped
-    by ``coarse_drop``, a sweep no longer lowers it, or ``coarse_max_sweeps``
-    sweeps (the paper does not state the coarsest-level method; this is the
+    by ``coarse_drop``, its running minimum has not improved by 0.1% for 5
+    sweeps (a plateau: the rounding floor), or ``coarse_max_sweeps`` sweeps (the paper does not state the coarsest-level method; this is the
     reading used throughout)."""
-    r0 = prev = np.linalg.norm(residual(u, f, h))
+    r0 = best = np.linalg.norm(residual(u, f, h))
+    stale = 0
     for _ in range(prm.coarse_max_sweeps):
         rbgs_sweep(u, f, h, prm.omega)
         r = np.linalg.norm(residual(u, f, h))
-        if r <= prm.coarse_drop * r0 or r >= prev:
+        if r <= prm.coarse_drop * r0:
             break
-        prev = r
+        if r < 0.999 * best:
+            best, stale = r, 0
+        else:
+            stale += 1
+            if stale >= 5:
+                break
     return u
 
 

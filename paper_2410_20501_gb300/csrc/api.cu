@@ -93,18 +93,25 @@ size_t layout_workspace(Workspace* w, void* base, int n, int64_t np, uint32_t fl
   }
   w->partials = (double*)take((size_t)2 * reduce_partials_capacity(n, np) * 8);
   w->scalars = (double*)take(64 * 8);
-  for (int l = 1; l < 12; ++l) {
+  for (int l = 0; l < 12; ++l) {
     const int nl = n >> l;
     if (nl < 4) break;
     const size_t bytes = (size_t)nl * nl * nl * 4;
+    const bool streamed = nl >= 128;   // levels smoothed by the streaming kernel need a ping-pong partner
     if (mg) {
-      w->mg_u[l] = (float*)take(bytes);
-      w->mg_f[l] = (float*)take(bytes);
+      if (l > 0) {
+        w->mg_u[l] = (float*)take(bytes);
+        w->mg_f[l] = (float*)take(bytes);
+      }
+      if (streamed) w->mg_alt[l] = (float*)take(bytes);
     }
     if (fr) {
-      w->fr_e[l] = (float*)take(bytes);
-      w->fr_r[l] = (float*)take(bytes);
-      w->fr_b[l] = (float*)take(bytes);
+      if (l > 0) {
+        w->fr_e[l] = (float*)take(bytes);
+        w->fr_r[l] = (float*)take(bytes);
+        w->fr_b[l] = (float*)take(bytes);
+      }
+      if (streamed) w->fr_alt[l] = (float*)take(bytes);
     }
   }
   w->base = b;
@@ -137,13 +144,14 @@ bool valid_np(int64_t np) { return np >= 0 && np < ((int64_t)1 << 31); }
 bool valid_mg(const mg_params* p) {
   return p && p->npre >= 0 && p->npost >= 0 && p->npre + p->npost > 0 && p->coarsest >= 4 &&
          p->coarsest <= 16 && p->coarse_max_sweeps >= 0 && p->max_cycles >= 1 && p->omega > 0.0f &&
-         p->omega < 2.0f && p->first_guess >= MG_GUESS_INPUT && p->first_guess <= MG_GUESS_SCALED;
+         p->omega < 2.0f && p->first_guess >= MG_GUESS_INPUT && p->first_guess <= MG_GUESS_SCALED &&
+         (p->smoother == 0 || p->smoother == 1);
 }
 
 bool valid_fr(const fr_params* p) {
   return p && p->a > 0.0 && p->Om > 0.0 && p->fR0 < 0.0 && p->boxsize > 0.0 && p->npre >= 0 && p->npost >= 0 &&
          p->coarsest >= 4 && p->coarsest <= 16 && p->coarse_max_sweeps >= 0 && (p->cycle == 0 || p->cycle == 1) &&
-         (p->tol > 0.0 ? p->max_cycles >= 1 : p->cycles >= 0);
+         (p->tol > 0.0 ? p->max_cycles >= 1 : p->cycles >= 0) && (p->smoother == 0 || p->smoother == 1);
 }
 
 // Adaptive Simpson quadrature of da / (a^3 E(a)).
@@ -201,6 +209,7 @@ void mg_default_params(mg_params* p) {
   p->stall = 0.5;
   p->first_guess = MG_GUESS_INPUT;
   p->guess_scale = 1.0f;
+  p->smoother = 0;
 }
 
 void fr_default_params(fr_params* p) {
@@ -219,6 +228,7 @@ void fr_default_params(fr_params* p) {
   p->cycles = 1;
   p->tol = 0.0;
   p->max_cycles = 30;
+  p->smoother = 0;
 }
 
 pm_status pm_sort(const uint32_t* X, int64_t np, int n, uint32_t* perm, uint32_t* cellstart, void* ws,

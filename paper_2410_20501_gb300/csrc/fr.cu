@@ -16,6 +16,7 @@
 
 #include "pm_device.cuh"
 #include "pm_internal.cuh"
+#include "rb_stream.cuh"
 
 namespace pmgb {
 
@@ -170,7 +171,7 @@ __global__ void __launch_bounds__(256) k_fr_norm(const float* __restrict__ e, Sr
 }
 
 // Coarsest level (n <= 16) in one CTA: non-linear sweeps until the residual
-// dropped by `drop`, a sweep no longer lowers it (float32 floor), or
+// dropped by `drop`, its running minimum stalls for 5 sweeps (float32 floor), or
 // `max_sweeps` sweeps.
 __global__ void __launch_bounds__(1024) k_fr_coarse(float* __restrict__ e, Src b, int log2n, float alpha,
                                                     float beta, float kappa, float q, int max_sweeps,
@@ -205,8 +206,9 @@ __global__ void __launch_bounds__(1024) k_fr_coarse(float* __restrict__ e, Src b
     block_sum_to(&r2, s, cmp, scratch);
     return r2;
   };
-  double prev = norm2();
-  const double target = (double)drop * (double)drop * prev;
+  double best = norm2();
+  const double target = (double)drop * (double)drop * best;
+  int stale = 0;
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
     for (int colour = 0; colour < 2; ++colour) {
       for (int c = threadIdx.x; c < N; c += blockDim.x) {
@@ -219,17 +221,31 @@ __global__ void __launch_bounds__(1024) k_fr_coarse(float* __restrict__ e, Src b
       __syncthreads();
     }
     const double r = norm2();
-    if (r <= target || r >= prev) break;   // converged, or at the float32 floor
-    prev = r;
+    if (r <= target) break;
+    if (r < 0.998 * best) {   // squared norms: a 0.1% improvement of the norm
+      best = r;
+      stale = 0;
+    } else if (++stale >= 5) {
+      break;                  // no progress for 5 sweeps: the float32 floor
+    }
   }
   for (int c = threadIdx.x; c < N; c += blockDim.x) e[c] = se[c];
 }
+
+// The non-linear Gauss-Seidel update as a functor for the streaming smoother.
+struct FRUpdate {
+  float beta, kappa, q;
+  __device__ __forceinline__ float operator()(float old, const float nb[6], float bv, int, bool, bool) const {
+    return fr_update(old, nb, bv, beta, kappa, q);
+  }
+};
 
 struct FR {
   int n0;
   const fr_params* p;
   cudaStream_t s;
   float* e[12];
+  float* alt[12];   // ping-pong partner for the streaming smoother (or NULL)
   float* r[12];
   Src b[12];
   double fbar, kappa;
@@ -252,12 +268,45 @@ LevelConst level_const(const FR& f, int l) {
   return c;
 }
 
+pm_status stream_attributes() {
+  static bool done = false;
+  if (!done) {
+    PM_TRY(cuda_status(cudaFuncSetAttribute(k_rb_stream<2, FRUpdate>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)StreamGeom<2>::smem_bytes)));
+    PM_TRY(cuda_status(cudaFuncSetAttribute(k_rb_stream<1, FRUpdate>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)StreamGeom<1>::smem_bytes)));
+    done = true;
+  }
+  return PM_OK;
+}
+
 pm_status fr_smooth(FR& f, int l, int count) {
   const LevelConst c = level_const(f, l);
+  const double N = (double)c.n * c.n * c.n;
+  if (f.p->smoother == 0 && stream_ok(c.n) && f.alt[l]) {
+    int chunk, nitems;
+    stream_plan(c.n, &chunk, &nitems);
+    const unsigned grid = (unsigned)(nitems < 152 * 3 ? nitems : 152 * 3);
+    const FRUpdate upd{c.beta, c.kappa, c.q};
+    for (int done = 0; done < count;) {
+      const int S = (count - done) >= 2 ? 2 : 1;
+      if (S == 2)
+        PM_LAUNCH(K_FR_SMOOTH, 12.0 * N, (k_rb_stream<2, FRUpdate>), grid, kStreamThreads, StreamGeom<2>::smem_bytes,
+                  f.s, f.e[l], f.alt[l], f.b[l], c.log2n, chunk, nitems, 0, upd);
+      else
+        PM_LAUNCH(K_FR_SMOOTH, 12.0 * N, (k_rb_stream<1, FRUpdate>), grid, kStreamThreads, StreamGeom<1>::smem_bytes,
+                  f.s, f.e[l], f.alt[l], f.b[l], c.log2n, chunk, nitems, 0, upd);
+      float* t = f.e[l];
+      f.e[l] = f.alt[l];
+      f.alt[l] = t;
+      done += S;
+    }
+    return PM_OK;
+  }
   const unsigned grid = grid_for(((int64_t)c.n * c.n * c.n) / 2, 256);
   for (int it = 0; it < count; ++it)
     for (int colour = 0; colour < 2; ++colour)
-      PM_LAUNCH(K_FR_SMOOTH, 8.0 * c.n * c.n * (double)c.n, k_fr_sweep, grid, 256, 0, f.s, f.e[l], f.b[l], c.log2n, colour, c.beta, c.kappa,
+      PM_LAUNCH(K_FR_SMOOTH, 8.0 * N, k_fr_sweep, grid, 256, 0, f.s, f.e[l], f.b[l], c.log2n, colour, c.beta, c.kappa,
                 c.q);
   return PM_OK;
 }
@@ -324,15 +373,28 @@ pm_status fr_solve_src(Src b, float* eps, int n, const fr_params& prm, mg_stats*
   f.e[0] = eps;
   f.r[0] = nullptr;
   f.b[0] = b;
-  for (int l = 1; l < 12; ++l) {
-    f.e[l] = w.fr_e[l];
-    f.r[l] = w.fr_r[l];
-    f.b[l] = Src{w.fr_b[l], 1.0f, nullptr};
+  for (int l = 0; l < 12; ++l) {
+    if (l > 0) {
+      f.e[l] = w.fr_e[l];
+      f.r[l] = w.fr_r[l];
+      f.b[l] = Src{w.fr_b[l], 1.0f, nullptr};
+    }
+    f.alt[l] = w.fr_alt[l];
   }
+  PM_TRY(stream_attributes());
   double c2;
   fr_background(prm, &f.fbar, &f.kappa, &c2);
   mg_stats local{PM_OK, 0, -1.0, -1.0, -1.0};
-  auto one = [&]() { return prm.cycle == 1 ? fr_f(f, 0) : fr_v(f, 0); };
+  const int64_t N0 = (int64_t)n * n * n;
+  auto one = [&]() -> pm_status {
+    PM_TRY(prm.cycle == 1 ? fr_f(f, 0) : fr_v(f, 0));
+    if (f.e[0] != eps) {   // the iterate ended in the ping-pong partner: bring it home
+      PM_TRY(cuda_status(cudaMemcpyAsync(eps, f.e[0], N0 * sizeof(float), cudaMemcpyDeviceToDevice, s)));
+      f.alt[0] = f.e[0];
+      f.e[0] = eps;
+    }
+    return PM_OK;
+  };
   if (prm.tol <= 0.0) {
     for (int c = 0; c < prm.cycles; ++c) PM_TRY(one());
     local.cycles = prm.cycles;

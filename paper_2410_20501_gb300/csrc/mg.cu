@@ -11,6 +11,7 @@
 
 #include "pm_device.cuh"
 #include "pm_internal.cuh"
+#include "rb_stream.cuh"
 
 namespace pmgb {
 
@@ -64,11 +65,12 @@ __global__ void k_scale(float* __restrict__ u, int64_t count, float a) {
     u[c] *= a;
 }
 
-// One colour of a red-black SOR sweep.  zero_guess: u is taken as 0 (the
-// coarse-level error starts from zero); gscale multiplies every value read
-// (fuses the warm-start rescale into the first sweep).
-__global__ void k_rb_sweep(float* __restrict__ u, Src f, int log2n, int colour, float omega,
-                           float h2, float gscale, int zero_guess) {
+// One colour of a red-black SOR sweep (the update rule is PoissonUpdate,
+// shared with the streaming smoother).  zero: the values of this level are
+// taken as 0 (the coarse-level error starts from zero): the red pass reads
+// nothing, the black pass ignores its own old value.
+__global__ void k_rb_sweep(float* __restrict__ u, Src f, int log2n, int colour, PoissonUpdate upd,
+                           int nb_old, int own_old, int zero) {
   const int m = (1 << log2n) - 1, half = log2n - 1;
   const float mean = load_mean(f);
   const int64_t total = (int64_t)1 << (3 * log2n - 1);
@@ -79,18 +81,18 @@ __global__ void k_rb_sweep(float* __restrict__ u, Src f, int log2n, int colour, 
     const int j = (int)(rest & m), i = (int)(rest >> log2n);
     const int k = 2 * kk + ((colour + i + j) & 1);
     const int64_t c = idx3(i, j, k, log2n);
-    const float fv = src_at(f, c, mean);
-    float unew;
-    if (zero_guess) {
-      unew = omega * (-h2 * fv) * kSixth;
-    } else {
-      const float s = u[idx3((i + 1) & m, j, k, log2n)] + u[idx3((i - 1) & m, j, k, log2n)] +
-                      u[idx3(i, (j + 1) & m, k, log2n)] + u[idx3(i, (j - 1) & m, k, log2n)] +
-                      u[idx3(i, j, (k + 1) & m, log2n)] + u[idx3(i, j, (k - 1) & m, log2n)];
-      const float ugs = (gscale * s - h2 * fv) * kSixth;
-      unew = (omega == 1.0f) ? ugs : omega * ugs + (1.0f - omega) * (gscale * u[c]);
+    float nb[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+    float old = 0.0f;
+    if (!(zero && colour == 0)) {
+      nb[0] = u[idx3((i + 1) & m, j, k, log2n)];
+      nb[1] = u[idx3((i - 1) & m, j, k, log2n)];
+      nb[2] = u[idx3(i, (j + 1) & m, k, log2n)];
+      nb[3] = u[idx3(i, (j - 1) & m, k, log2n)];
+      nb[4] = u[idx3(i, j, (k + 1) & m, log2n)];
+      nb[5] = u[idx3(i, j, (k - 1) & m, log2n)];
     }
-    u[c] = unew;
+    if (!zero) old = u[c];
+    u[c] = upd(old, nb, src_at(f, c, mean), 0, nb_old != 0, own_old != 0);
   }
 }
 
@@ -195,7 +197,7 @@ __global__ void k_prolong_correct(float* __restrict__ u, const float* __restrict
 }
 
 // Coarsest level (n <= 16) in one CTA: red-black SOR sweeps until the residual
-// norm dropped by `drop`, a sweep no longer lowers it (float32 floor), or
+// norm dropped by `drop`, its running minimum stalls for 5 sweeps (float32 floor), or
 // `max_sweeps` sweeps.
 __global__ void __launch_bounds__(1024) k_mg_coarse(float* __restrict__ u, Src f, int log2n, float h2,
                                                     float omega, int max_sweeps, float drop,
@@ -227,8 +229,9 @@ __global__ void __launch_bounds__(1024) k_mg_coarse(float* __restrict__ u, Src f
     block_sum_to(&r2, s, cmp, scratch);
     return r2;
   };
-  double prev = norm2();
-  const double target = (double)drop * (double)drop * prev;
+  double best = norm2();
+  const double target = (double)drop * (double)drop * best;
+  int stale = 0;
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
     for (int colour = 0; colour < 2; ++colour) {
       for (int c = threadIdx.x; c < N; c += blockDim.x) {
@@ -246,8 +249,13 @@ __global__ void __launch_bounds__(1024) k_mg_coarse(float* __restrict__ u, Src f
       __syncthreads();
     }
     const double r = norm2();
-    if (r <= target || r >= prev) break;   // converged, or at the float32 floor
-    prev = r;
+    if (r <= target) break;
+    if (r < 0.998 * best) {   // squared norms: a 0.1% improvement of the norm
+      best = r;
+      stale = 0;
+    } else if (++stale >= 5) {
+      break;                  // no progress for 5 sweeps: the float32 floor
+    }
   }
   for (int c = threadIdx.x; c < N; c += blockDim.x) u[c] = su[c];
 }
@@ -256,20 +264,65 @@ struct MG {
   int n0;
   const mg_params* p;
   cudaStream_t s;
-  float* u[12];
+  float* u[12];     // current iterate of each level
+  float* alt[12];   // ping-pong partner for the streaming smoother (or NULL)
   Src f[12];
   bool first_cycle;
   float gscale;
 };
 
-pm_status sweep(MG& g, int l, float omega, bool zero_guess, float gscale) {
+pm_status stream_attributes() {
+  static bool done = false;
+  if (!done) {
+    PM_TRY(cuda_status(cudaFuncSetAttribute(k_rb_stream<2, PoissonUpdate>,
+                                            cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)StreamGeom<2>::smem_bytes)));
+    PM_TRY(cuda_status(cudaFuncSetAttribute(k_rb_stream<1, PoissonUpdate>,
+                                            cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)StreamGeom<1>::smem_bytes)));
+    done = true;
+  }
+  return PM_OK;
+}
+
+// `count` smoothing sweeps on level l with SOR factors w[0..count-1].
+// zero: the level's values start at 0; scale: warm-start factor applied to the
+// values present before the first sweep.
+pm_status smooth(MG& g, int l, int count, const float* w, bool zero, float scale) {
   const int n = g.n0 >> l, log2n = ilog2(n);
   const float h2 = 1.0f / ((float)n * (float)n);
-  const int64_t half = ((int64_t)n * n * n) / 2;
-  const unsigned grid = grid_for(half, 256);
-  PM_LAUNCH(K_MG_SMOOTH, (zero_guess ? 4.0 : 8.0) * half * 2.0, k_rb_sweep, grid, 256, 0, g.s, g.u[l], g.f[l], log2n, 0, omega, h2, gscale,
-            zero_guess ? 1 : 0);
-  PM_LAUNCH(K_MG_SMOOTH, 8.0 * half * 2.0, k_rb_sweep, grid, 256, 0, g.s, g.u[l], g.f[l], log2n, 1, omega, h2, 1.0f, 0);
+  const int64_t N = (int64_t)n * n * n;
+  int done = 0;
+  if (g.p->smoother == 0 && stream_ok(n) && g.alt[l]) {
+    int chunk, nitems;
+    stream_plan(n, &chunk, &nitems);
+    while (done < count) {
+      const int S = (count - done) >= 2 ? 2 : 1;
+      PoissonUpdate upd{h2, {w[done], S == 2 ? w[done + 1] : 1.0f}, done == 0 ? scale : 1.0f};
+      const int z = (done == 0 && zero) ? 1 : 0;
+      const unsigned grid = (unsigned)(nitems < 152 * 3 ? nitems : 152 * 3);
+      if (S == 2)
+        PM_LAUNCH(K_MG_SMOOTH, (z ? 8.0 : 12.0) * N, (k_rb_stream<2, PoissonUpdate>), grid, kStreamThreads,
+                  StreamGeom<2>::smem_bytes, g.s, g.u[l], g.alt[l], g.f[l], log2n, chunk, nitems, z, upd);
+      else
+        PM_LAUNCH(K_MG_SMOOTH, (z ? 8.0 : 12.0) * N, (k_rb_stream<1, PoissonUpdate>), grid, kStreamThreads,
+                  StreamGeom<1>::smem_bytes, g.s, g.u[l], g.alt[l], g.f[l], log2n, chunk, nitems, z, upd);
+      float* t = g.u[l];
+      g.u[l] = g.alt[l];
+      g.alt[l] = t;
+      done += S;
+    }
+    return PM_OK;
+  }
+  const unsigned grid = grid_for(N / 2, 256);
+  for (; done < count; ++done) {
+    PoissonUpdate upd{h2, {w[done], 1.0f}, done == 0 ? scale : 1.0f};
+    const int z = (done == 0 && zero) ? 1 : 0;
+    const int first = done == 0 ? 1 : 0;
+    PM_LAUNCH(K_MG_SMOOTH, (z ? 4.0 : 8.0) * N, k_rb_sweep, grid, 256, 0, g.s, g.u[l], g.f[l], log2n, 0, upd,
+              first, first, z);
+    PM_LAUNCH(K_MG_SMOOTH, 8.0 * N, k_rb_sweep, grid, 256, 0, g.s, g.u[l], g.f[l], log2n, 1, upd, 0, first, z);
+  }
   return PM_OK;
 }
 
@@ -277,9 +330,10 @@ pm_status v_cycle(MG& g, int l, bool zero_guess) {
   const int n = g.n0 >> l, log2n = ilog2(n);
   const mg_params& p = *g.p;
   const float h2 = 1.0f / ((float)n * (float)n);
+  const bool scaled = (l == 0 && g.first_cycle && g.gscale != 1.0f);
   if (n <= p.coarsest || n <= 4) {
     float* u = g.u[l];
-    if (!zero_guess && l == 0 && g.first_cycle && g.gscale != 1.0f) {
+    if (!zero_guess && scaled) {
       const int64_t N = (int64_t)n * n * n;
       PM_LAUNCH(K_MG_GUESS, 8.0 * N, k_scale, grid_for(N, 256), 256, 0, g.s, u, N, g.gscale);
     }
@@ -287,15 +341,14 @@ pm_status v_cycle(MG& g, int l, bool zero_guess) {
               p.coarse_max_sweeps, p.coarse_drop, zero_guess ? 1 : 0);
     return PM_OK;
   }
-  const bool fuse_scale = (l == 0 && g.first_cycle && g.gscale != 1.0f);
+  float w[64];
   if (p.npre == 0) {
     const int64_t N = (int64_t)n * n * n;
     if (zero_guess) PM_TRY(cuda_status(cudaMemsetAsync(g.u[l], 0, N * sizeof(float), g.s)));
-    else if (fuse_scale) PM_LAUNCH(K_MG_GUESS, 8.0 * N, k_scale, grid_for(N, 256), 256, 0, g.s, g.u[l], N, g.gscale);
-  }
-  for (int si = 0; si < p.npre; ++si) {
-    const float om = si == 0 ? 1.0f : p.omega;
-    PM_TRY(sweep(g, l, om, zero_guess && si == 0, (fuse_scale && si == 0) ? g.gscale : 1.0f));
+    else if (scaled) PM_LAUNCH(K_MG_GUESS, 8.0 * N, k_scale, grid_for(N, 256), 256, 0, g.s, g.u[l], N, g.gscale);
+  } else {
+    for (int si = 0; si < p.npre; ++si) w[si] = si == 0 ? 1.0f : p.omega;
+    PM_TRY(smooth(g, l, p.npre, w, zero_guess, scaled ? g.gscale : 1.0f));
   }
   const int64_t nc = ((int64_t)n * n * n) / 8;
   const unsigned grid = grid_for(nc, 256);
@@ -308,9 +361,9 @@ pm_status v_cycle(MG& g, int l, bool zero_guess) {
   PM_TRY(v_cycle(g, l + 1, true));
   PM_LAUNCH(K_MG_PROLONG, 68.0 * nc, k_prolong_correct, grid_for(nc * 8, 256), 256, 0, g.s, g.u[l], g.u[l + 1],
             (const float*)nullptr, log2n);
-  for (int si = 0; si < p.npost; ++si) {
-    const float om = si == p.npost - 1 ? 1.0f : p.omega;
-    PM_TRY(sweep(g, l, om, false, 1.0f));
+  if (p.npost > 0) {
+    for (int si = 0; si < p.npost; ++si) w[si] = si == p.npost - 1 ? 1.0f : p.omega;
+    PM_TRY(smooth(g, l, p.npost, w, false, 1.0f));
   }
   return PM_OK;
 }
@@ -341,10 +394,14 @@ pm_status mg_solve_src(Src f, float* phi, int n, const mg_params& prm, mg_stats*
   g.s = s;
   g.u[0] = phi;
   g.f[0] = f;
-  for (int l = 1; l < 12; ++l) {
-    g.u[l] = w.mg_u[l];
-    g.f[l] = Src{w.mg_f[l], 1.0f, nullptr};
+  for (int l = 0; l < 12; ++l) {
+    if (l > 0) {
+      g.u[l] = w.mg_u[l];
+      g.f[l] = Src{w.mg_f[l], 1.0f, nullptr};
+    }
+    g.alt[l] = w.mg_alt[l];
   }
+  PM_TRY(stream_attributes());
   g.first_cycle = true;
   g.gscale = prm.first_guess == MG_GUESS_SCALED ? prm.guess_scale : 1.0f;
   const int64_t N = (int64_t)n * n * n;
@@ -352,11 +409,18 @@ pm_status mg_solve_src(Src f, float* phi, int n, const mg_params& prm, mg_stats*
   if (prm.first_guess == MG_GUESS_JACOBI)
     PM_LAUNCH(K_MG_GUESS, 8.0 * N, k_jacobi_guess, grid_for(N, 256), 256, 0, s, phi, f, N, h2);
   mg_stats local{PM_OK, 0, -1.0, -1.0, -1.0};
-  if (prm.fixed_cycles > 0) {
-    for (int c = 0; c < prm.fixed_cycles; ++c) {
-      PM_TRY(v_cycle(g, 0, false));
-      g.first_cycle = false;
+  auto cycle = [&]() -> pm_status {
+    PM_TRY(v_cycle(g, 0, false));
+    g.first_cycle = false;
+    if (g.u[0] != phi) {   // the iterate ended in the ping-pong partner: bring it home
+      PM_TRY(cuda_status(cudaMemcpyAsync(phi, g.u[0], N * sizeof(float), cudaMemcpyDeviceToDevice, s)));
+      g.alt[0] = g.u[0];
+      g.u[0] = phi;
     }
+    return PM_OK;
+  };
+  if (prm.fixed_cycles > 0) {
+    for (int c = 0; c < prm.fixed_cycles; ++c) PM_TRY(cycle());
     local.cycles = prm.fixed_cycles;
     if (st) *st = local;
     return launch_status();
@@ -366,8 +430,7 @@ pm_status mg_solve_src(Src f, float* phi, int n, const mg_params& prm, mg_stats*
   double prev = -1.0;
   pm_status status = PM_ENOCONV;
   for (int c = 0; c < prm.max_cycles; ++c) {
-    PM_TRY(v_cycle(g, 0, false));
-    g.first_cycle = false;
+    PM_TRY(cycle());
     local.cycles = c + 1;
     PM_LAUNCH(K_MG_NORM, 8.0 * N, k_resid_norm, nb, 256, 0, s, phi, f, log2n, (float)n * (float)n, w.partials);
     PM_TRY(reduce_partials(w.partials, nb, nb, 2, 1.0, w.scalars + 4, s));
@@ -378,7 +441,9 @@ pm_status mg_solve_src(Src f, float* phi, int n, const mg_params& prm, mg_stats*
     local.norm_f = nf;
     if (!isfinite(res)) { status = PM_ENAN; break; }
     if (res <= prm.tol * nf) { status = PM_OK; break; }
-    if (prev > 0.0 && prm.stall > 0.0 && res > prm.stall * prev) { status = PM_OK; break; }
+    // a cycle that gained less than 1/stall ends the solve only near the
+    // float32 floor of the stored iterate (residual below 1e-3 of the source)
+    if (prev > 0.0 && prm.stall > 0.0 && res > prm.stall * prev && res <= 1e-3 * nf) { status = PM_OK; break; }
     prev = res;
   }
   local.status = status;

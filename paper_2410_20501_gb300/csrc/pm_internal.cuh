@@ -62,8 +62,8 @@ struct Workspace {
   // reductions (float64 partials) and device scalars
   double* partials; double* scalars;
   // multigrid pyramids: level l >= 1 arrays (index 0 unused)
-  float* mg_u[12]; float* mg_f[12];
-  float* fr_e[12]; float* fr_r[12]; float* fr_b[12];
+  float* mg_u[12]; float* mg_f[12]; float* mg_alt[12];
+  float* fr_e[12]; float* fr_r[12]; float* fr_b[12]; float* fr_alt[12];
   int64_t np; int n;
 };
 

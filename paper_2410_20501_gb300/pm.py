@@ -37,7 +37,8 @@ class mg_params(ctypes.Structure):
     _fields_ = [("npre", ctypes.c_int), ("npost", ctypes.c_int), ("omega", ctypes.c_float),
                 ("coarsest", ctypes.c_int), ("coarse_max_sweeps", ctypes.c_int), ("coarse_drop", ctypes.c_float),
                 ("max_cycles", ctypes.c_int), ("fixed_cycles", ctypes.c_int), ("tol", ctypes.c_double),
-                ("stall", ctypes.c_double), ("first_guess", ctypes.c_int), ("guess_scale", ctypes.c_float)]
+                ("stall", ctypes.c_double), ("first_guess", ctypes.c_int), ("guess_scale", ctypes.c_float),
+                ("smoother", ctypes.c_int)]
 
 
 class mg_stats(ctypes.Structure):
@@ -53,7 +54,7 @@ class fr_params(ctypes.Structure):
                 ("fR0", ctypes.c_double), ("boxsize", ctypes.c_double), ("cycle", ctypes.c_int),
                 ("npre", ctypes.c_int), ("npost", ctypes.c_int), ("coarsest", ctypes.c_int),
                 ("coarse_max_sweeps", ctypes.c_int), ("coarse_drop", ctypes.c_float), ("cycles", ctypes.c_int),
-                ("tol", ctypes.c_double), ("max_cycles", ctypes.c_int)]
+                ("tol", ctypes.c_double), ("max_cycles", ctypes.c_int), ("smoother", ctypes.c_int)]
 
 
 class pm_state(ctypes.Structure):
