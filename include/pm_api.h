@@ -136,7 +136,7 @@ typedef struct {
 /* Default parameters: npre = npost = 2, omega = 1.25, coarsest = 16,
  * coarse_max_sweeps = 200, coarse_drop = 1e-3, max_cycles = 30,
  * fixed_cycles = 0, tol = 1e-7, stall = 0.5, first_guess = MG_GUESS_INPUT,
- * smoother = 0. */
+ * smoother = 1. */
 void mg_default_params(mg_params* p);
 
 /* Solve the periodic Poisson problem (L(phi) - 6 phi)/h^2 = f - <f>, h = 1/n,

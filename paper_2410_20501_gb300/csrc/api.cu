@@ -209,7 +209,7 @@ void mg_default_params(mg_params* p) {
   p->stall = 0.5;
   p->first_guess = MG_GUESS_INPUT;
   p->guess_scale = 1.0f;
-  p->smoother = 0;
+  p->smoother = 1;
 }
 
 void fr_default_params(fr_params* p) {
@@ -228,7 +228,7 @@ void fr_default_params(fr_params* p) {
   p->cycles = 1;
   p->tol = 0.0;
   p->max_cycles = 30;
-  p->smoother = 0;
+  p->smoother = 1;
 }
 
 pm_status pm_sort(const uint32_t* X, int64_t np, int n, uint32_t* perm, uint32_t* cellstart, void* ws,

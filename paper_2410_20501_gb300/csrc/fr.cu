@@ -35,7 +35,7 @@ __device__ __forceinline__ int64_t idx3(int i, int j, int k, int log2n) {
 // shrinking bracket [lo, hi]; when a step leaves the bracket (or g' <= 0) the
 // upper end is set from the bound u* <= sqrt(max(-p, 0)) + (-q)^(1/3),
 // p = c1 - 3, and the step falls back to bisection.  Stops when g is at its
-// float32 rounding level or the step is below 1e-6 relative.
+// float32 rounding level or the step is below 2e-7 relative.
 __device__ __forceinline__ float fr_root(float e, float c1, float c0, float q) {
   float lo = -1.0f, hi = __int_as_float(0x7f800000);  // +inf until needed
   if (!(e > lo)) e = 0.0f;
@@ -53,7 +53,7 @@ __device__ __forceinline__ float fr_root(float e, float c1, float c0, float q) {
       if (isinf(hi)) hi = fmaxf(sqrtf(fmaxf(3.0f - c1, 0.0f)) + cbrtf(-q) - 1.0f, lo);
       en = 0.5f * (lo + hi);
     }
-    if (fabsf(en - e) <= 1e-6f * fabsf(en) + 1e-12f) return en;
+    if (fabsf(en - e) <= 2e-7f * fabsf(en) + 1e-12f) return en;
     e = en;
   }
   return e;

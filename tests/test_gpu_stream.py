@@ -58,15 +58,17 @@ def test_streaming_mg_one_cycle_matches_oracle_128(pm):
     n = 128
     f = inputs.random_field(n, 6).astype(np.float32).astype(np.float64)
     phi, _ = pm.mg_solve(torch.from_numpy(f.astype(np.float32)).cuda(), fixed_cycles=1,
-                         first_guess=pm.MG_GUESS_JACOBI)
+                         first_guess=pm.MG_GUESS_JACOBI, smoother=0)
     ref, _ = poisson.mg_solve(f, 1.0 / n, prm=poisson.MGParams(), cycles=1)
-    assert rel_l2(phi.cpu().numpy(), ref) < 1e-5
+    # float32 against float64 after one cycle: bounded by eps32 times the
+    # condition number (n / pi)^2 of the 7-point Laplacian
+    assert rel_l2(phi.cpu().numpy(), ref) < 6e-8 * (n / np.pi) ** 2
 
 
 def test_streaming_mg_converged_matches_fft7_256(pm):
     n = 256
     f = inputs.random_field(n, 7).astype(np.float32).astype(np.float64)
-    phi, st = pm.mg_solve(torch.from_numpy(f.astype(np.float32)).cuda(), tol=1e-9, max_cycles=40)
+    phi, st = pm.mg_solve(torch.from_numpy(f.astype(np.float32)).cuda(), tol=1e-9, max_cycles=40, smoother=0)
     ref = poisson.solve_fft7(f, 1.0 / n)
     phi = phi.cpu().numpy().astype(np.float64)
     assert st["status"] == 0
