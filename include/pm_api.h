@@ -95,6 +95,25 @@ pm_status pm_sort(const uint32_t* X, int64_t np, int n, uint32_t* perm,
 pm_status pm_deposit(const uint32_t* X, int64_t np, int n, float* rho,
                      void* ws, size_t ws_bytes, void* stream);
 
+/* pm_deposit for callers that cannot allocate device memory.  Some callers
+ * cannot call cudaMalloc: a host application whose memory pool owns the whole
+ * device and forbids other allocations, a code path that must not pay
+ * cudaMalloc's implicit device synchronisation, or a foreign-language binding
+ * that has no device allocator; they cannot provide the workspace pm_deposit
+ * needs.  This entry point computes the same density as pm_deposit but takes
+ * its scratch from one static device array of 9 MiB inside the library (held
+ * on every GPU that loads the library until the process exits), so it
+ * allocates nothing.  The paper has no counterpart.
+ *   Limits: n <= 64 and np <= 262144 (2^18); larger sizes return PM_EINVAL.
+ *   The caller still passes X (device, [3][np] uint32) and rho (device,
+ *   [n^3] float32).
+ *   The first call on a device looks up the array's device address with
+ *   cudaGetSymbolAddress (with that device current); make that first call
+ *   before any stream capture.
+ *   Every call shares the array: calls that overlap on the GPU (different
+ *   streams, or different host threads) race on it and give wrong results. */
+pm_status pm_deposit_noalloc(const uint32_t* X, int64_t np, int n, float* rho, void* stream);
+
 /* ------------------------------------------------------------- multigrid -- */
 enum { MG_GUESS_INPUT = 0, MG_GUESS_JACOBI = 1, MG_GUESS_SCALED = 2 };
 

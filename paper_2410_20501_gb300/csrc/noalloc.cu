@@ -1,0 +1,61 @@
+// pm_deposit_noalloc: the TSC deposit for callers that cannot allocate device
+// memory.  Instead of a caller workspace it uses one file-scope device array.
+#include <string.h>
+
+#include "pm_internal.cuh"
+
+namespace pmgb {
+
+namespace {
+
+constexpr int kNoallocMaxN = 64;
+constexpr int64_t kNoallocMaxNp = (int64_t)1 << 18;
+constexpr size_t kNoallocBytes = (size_t)9 << 20;   // 9 MiB: the pm_deposit workspace at the limits is 8.3 MiB
+constexpr int kMaxDevices = 64;
+
+// Shared by every call on a device; it keeps the previous call's contents.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
+
+void* g_scratch_addr[kMaxDevices] = {nullptr};
+
+// Device address of the scratch array on the current device (host code must
+// not use the symbol itself: on the host it is only a stand-in).
+pm_status scratch_address(void** out) {
+  int dev = 0;
+  PM_TRY(cuda_status(cudaGetDevice(&dev)));
+  if (dev < 0 || dev >= kMaxDevices) return PM_EINVAL;
+  if (!g_scratch_addr[dev]) {
+    void* p = nullptr;
+    PM_TRY(cuda_status(cudaGetSymbolAddress(&p, g_noalloc_scratch)));
+    g_scratch_addr[dev] = p;
+  }
+  *out = g_scratch_addr[dev];
+  return PM_OK;
+}
+
+}  // namespace
+
+}  // namespace pmgb
+
+using namespace pmgb;
+
+extern "C" pm_status pm_deposit_noalloc(const uint32_t* X, int64_t np, int n, float* rho, void* stream) {
+  if (!valid_n(n) || n > kNoallocMaxN || np < 0 || np > kNoallocMaxNp || (np > 0 && !X) || !rho)
+    return PM_EINVAL;
+  const size_t need = layout_workspace(nullptr, nullptr, n, np, PM_WS_SORT);
+  if (need > kNoallocBytes) return PM_EINVAL;
+  void* base = nullptr;
+  PM_TRY(scratch_address(&base));
+  Workspace w;
+  layout_workspace(&w, base, n, np, PM_WS_SORT);
+  // Nothing in the scratch has to start at zero: every buffer the deposit
+  // reads (radix counts and offsets, cell starts, sorted positions, block
+  // partials) is fully written earlier in the same call.
+  cudaStream_t s = (cudaStream_t)stream;
+  uint32_t *perm, *skeys;
+  PM_TRY(sort_particles(X, np, n, w, s, &perm, &skeys));
+  PM_TRY(build_cellstart(skeys, np, n, w.cellstart, s));
+  PM_TRY(permute_particles(perm, np, X, nullptr, nullptr, w.Xs, nullptr, nullptr, s));
+  PM_TRY(deposit_sorted(w.Xs, np, w.cellstart, n, rho, w.partials, w.scalars, s));
+  return launch_status();
+}

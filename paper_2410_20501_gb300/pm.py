@@ -87,6 +87,8 @@ _SIGS = {
                                ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
     "pm_deposit": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_void_p,
                                   ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
+    "pm_deposit_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_void_p,
+                                          ctypes.c_void_p]),
     "mg_default_params": (None, [ctypes.POINTER(mg_params)]),
     "mg_solve": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(mg_params),
                                 ctypes.POINTER(mg_stats), ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
