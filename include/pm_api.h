@@ -242,7 +242,9 @@ typedef struct {
                           the leapfrog around this force evaluation)         */
   double dt_drift;     /* then x += v * dt_drift (0: kick only)              */
   double phi_rescale;  /* warm start: phi_guess = phi_rescale * phi_prev     */
-  mg_params mg;        /* Poisson multigrid                                  */
+  mg_params mg;        /* Poisson multigrid; fixed_cycles applies to warm-
+                          started steps only (have_prev = 1): the first step
+                          always cycles to tol from the Jacobi guess         */
   fr_params fr;        /* f(R) solver (a, Om, OL, fR0, boxsize taken from above) */
 } pm_step_params;
 

@@ -335,6 +335,7 @@ pm_status pm_step(pm_state* st_, const pm_step_params* prm, pm_stats* stats, voi
   mg_params mp = prm->mg;
   mp.first_guess = S.have_prev ? MG_GUESS_SCALED : MG_GUESS_JACOBI;
   mp.guess_scale = (float)prm->phi_rescale;
+  if (!S.have_prev) mp.fixed_cycles = 0;   // a cold start always iterates to the tolerance
   {
     pm_status r = mg_solve_src(Src{w.rho, (float)(1.5 * prm->a * prm->Om), w.scalars}, S.phi, n, mp, &local.mg, w, s);
     if (r != PM_OK && r != PM_ENOCONV) return r;

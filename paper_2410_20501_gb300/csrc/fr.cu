@@ -46,7 +46,7 @@ __device__ __forceinline__ float fr_root(float e, float c1, float c0, float q) {
     if (g > 0.0f) hi = fminf(hi, e);
     else if (g < 0.0f) lo = fmaxf(lo, e);
     else return e;
-    const float noise = 4e-7f * (fabsf(c0) + fabsf(c1 * e) + 3.0f * e2 + fabsf(e2 * e));
+    const float noise = 1.5e-7f * (fabsf(c0) + fabsf(c1 * e) + 3.0f * e2 + fabsf(e2 * e));
     if (fabsf(g) <= noise) return e;
     float en = gp > 0.0f ? e - __fdividef(g, gp) : lo;
     if (!(en > lo && en < hi)) {

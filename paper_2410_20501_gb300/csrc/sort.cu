@@ -172,12 +172,22 @@ __global__ void __launch_bounds__(RT) k_radix_down(const uint32_t* __restrict__ 
   const int64_t wbase = base + (int64_t)warp * (RI * 32);
   const uint32_t lt = (1u << lane) - 1u;
   uint32_t k[RI], v[RI], rk[RI];
+  // issue every load of the tile before the ranking rounds
+#pragma unroll
+  for (int r = 0; r < RI; ++r) {
+    const int64_t i = wbase + r * 32 + lane;
+    k[r] = i < np ? __ldg(keys_in + i) : 0u;
+  }
+#pragma unroll
+  for (int r = 0; r < RI; ++r) {
+    const int64_t i = wbase + r * 32 + lane;
+    v[r] = i < np ? (vals_in ? __ldg(vals_in + i) : (uint32_t)i) : 0u;
+  }
 #pragma unroll
   for (int r = 0; r < RI; ++r) {
     int64_t i = wbase + r * 32 + lane;
     bool valid = i < np;
-    uint32_t key = valid ? keys_in[i] : 0u;
-    uint32_t val = valid ? (vals_in ? vals_in[i] : (uint32_t)i) : 0u;
+    uint32_t key = k[r];
     uint32_t d = valid ? ((key >> shift) & (R - 1)) : (uint32_t)R;
     uint32_t peers = __match_any_sync(0xffffffffu, d);
     int leader = __ffs(peers) - 1;
@@ -186,8 +196,6 @@ __global__ void __launch_bounds__(RT) k_radix_down(const uint32_t* __restrict__ 
     __syncwarp();
     if (valid && lane == leader) whist[warp * RMAXBINS + d] = b + __popc(peers);
     __syncwarp();
-    k[r] = key;
-    v[r] = val;
     rk[r] = valid ? b + __popc(peers & lt) : 0xffffffffu;
   }
   __syncthreads();
