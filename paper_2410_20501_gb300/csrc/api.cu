@@ -89,7 +89,7 @@ size_t layout_workspace(Workspace* w, void* base, int n, int64_t np, uint32_t fl
     w->Vs = (float*)take((size_t)np * 12);
     if (flags & PM_WS_IDS) w->ids = (uint32_t*)take((size_t)np * 4);
     w->rho = (float*)take((size_t)N * 4);
-    w->g = (float*)take((size_t)N * 12);
+    w->g = (float*)take((size_t)N * 16);   // three planes, or float4 per cell
   }
   w->partials = (double*)take((size_t)2 * reduce_partials_capacity(n, np) * 8);
   w->scalars = (double*)take(64 * 8);
@@ -282,12 +282,12 @@ pm_status fr_solve(const float* rho, float* eps, int n, const fr_params* prm, mg
 
 pm_status pm_gradient(const float* phi, float* g, int n, int order, void* stream) {
   if (!valid_n(n) || !phi || !g || (order != 3 && order != 5 && order != 7)) return PM_EINVAL;
-  return gradient_launch(phi, nullptr, 0.0f, g, n, order, as_stream(stream));
+  return gradient_launch(phi, nullptr, 0.0f, g, n, order, false, as_stream(stream));
 }
 
 pm_status pm_interp(const float* g, const uint32_t* X, int64_t np, int n, float* acc, void* stream) {
   if (!valid_n(n) || !valid_np(np) || !g || (np > 0 && (!X || !acc))) return PM_EINVAL;
-  return interp_launch(g, X, nullptr, nullptr, np, n, acc, nullptr, nullptr, nullptr, 0.0f, 0.0f, 0,
+  return interp_launch(g, X, nullptr, nullptr, np, n, acc, nullptr, nullptr, nullptr, 0.0f, 0.0f, 0, false,
                        as_stream(stream));
 }
 
@@ -342,9 +342,11 @@ pm_status pm_step(pm_state* st_, const pm_step_params* prm, pm_stats* stats, voi
     if (r != PM_OK) solve_status = r;
   }
   const float alpha = (float)(-0.5 * c2 * fbar);
-  PM_TRY(gradient_launch(S.phi, prm->gravity == PM_GRAVITY_FR ? S.eps : nullptr, alpha, w.g, n, prm->grad_order, s));
+  const bool vec4 = n >= 64;   // g interleaved as float4: one 16-byte load per cell in the interpolation
+  PM_TRY(gradient_launch(S.phi, prm->gravity == PM_GRAVITY_FR ? S.eps : nullptr, alpha, w.g, n, prm->grad_order,
+                         vec4, s));
   PM_TRY(interp_launch(w.g, w.Xs, w.Vs, w.ids, np, n, S.acc, S.X, S.V, S.id, (float)prm->dt_kick,
-                       (float)prm->dt_drift, 1, s));
+                       (float)prm->dt_drift, 1, vec4, s));
   S.have_prev = 1;
   local.status = solve_status;
   if (stats) *stats = local;

@@ -67,8 +67,70 @@ __global__ void k_gradient(const float* __restrict__ phi, const float* __restric
   }
 }
 
+// Streaming gradient for n >= 64: a CTA owns a 16 x 64 (y, z) column and a
+// chunk of x planes, keeps the 2R + 1 planes of Phi (with a halo of R in y and
+// z) that the stencil needs in shared memory, so every Phi value is read from
+// HBM once (plus halos).  Same arithmetic order as k_gradient.  VEC4 writes
+// g interleaved as float4 (gx, gy, gz, 0) for the interpolation.
+constexpr int GTY = 16, GTZ = 64, GNT = 256;
+
+template <int ORDER, bool FR, bool VEC4>
+__global__ void __launch_bounds__(GNT) k_gradient_stream(const float* __restrict__ phi,
+                                                        const float* __restrict__ eps, float alpha,
+                                                        float* __restrict__ g, int log2n, float inv_h,
+                                                        int chunk, int nitems) {
+  constexpr int R = Stencil<ORDER>::R, W = 2 * R + 1, EY = GTY + 2 * R, EZ = GTZ + 2 * R, PL = EY * EZ;
+  extern __shared__ float P[];   // [W][EY][EZ]
+  const int n = 1 << log2n, m = n - 1;
+  const int tiles_z = n / GTZ, tiles = (n / GTY) * tiles_z;
+  const int64_t N = (int64_t)1 << (3 * log2n);
+  const int tid = threadIdx.x;
+  for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
+    const int tile = item % tiles, xc = item / tiles;
+    const int y0 = (tile / tiles_z) * GTY, z0 = (tile % tiles_z) * GTZ;
+    const int x0 = xc * chunk, x1 = x0 + chunk;
+    for (int t = x0 - R; t < x1 + R; ++t) {
+      float* Pt = P + (((t % W) + W) % W) * PL;
+      const int64_t pb = (int64_t)(t & m) << (2 * log2n);
+      for (int e = tid; e < PL; e += GNT) {
+        const int ly = e / EZ, lz = e - ly * EZ;
+        Pt[e] = pot<FR>(phi, eps, alpha, pb | ((int64_t)((y0 - R + ly) & m) << log2n) | ((z0 - R + lz) & m));
+      }
+      __syncthreads();
+      const int xo = t - R;
+      if (xo >= x0) {
+        const float* Pc = P + (((xo % W) + W) % W) * PL;
+        for (int e = tid; e < GTY * GTZ; e += GNT) {
+          const int ly = e / GTZ, lz = e - ly * GTZ;
+          const int c = (ly + R) * EZ + lz + R;
+          float gx = 0.0f, gy = 0.0f, gz = 0.0f;
+#pragma unroll
+          for (int q = R; q >= 1; --q) {
+            const float w = Stencil<ORDER>::c(q);
+            const float* Pp = P + ((((xo + q) % W) + W) % W) * PL;
+            const float* Pm = P + ((((xo - q) % W) + W) % W) * PL;
+            gx = fmaf(w, Pp[c] - Pm[c], gx);
+            gy = fmaf(w, Pc[c + q * EZ] - Pc[c - q * EZ], gy);
+            gz = fmaf(w, Pc[c + q] - Pc[c - q], gz);
+          }
+          const int64_t cell = ((int64_t)xo << (2 * log2n)) | ((int64_t)(y0 + ly) << log2n) | (z0 + lz);
+          if (VEC4) {
+            reinterpret_cast<float4*>(g)[cell] = make_float4(-gx * inv_h, -gy * inv_h, -gz * inv_h, 0.0f);
+          } else {
+            g[cell] = -gx * inv_h;
+            g[N + cell] = -gy * inv_h;
+            g[2 * N + cell] = -gz * inv_h;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
 // Inverse TSC; mode 1 also kicks and drifts.  Particles are read in cell
 // order (Xs, Vs) and written in the same order (Xo, Vo).
+template <bool VEC4>
 __global__ void __launch_bounds__(256) k_interp_kdk(const float* __restrict__ g, const uint32_t* __restrict__ Xs,
                                                     const float* __restrict__ Vs,
                                                     const uint32_t* __restrict__ ids_in, int64_t np, int log2n,
@@ -97,9 +159,16 @@ __global__ void __launch_bounds__(256) k_interp_kdk(const float* __restrict__ g,
         for (int oz = 0; oz < 3; ++oz) {
           const int64_t c = idx3(ci, cj, (iz + oz - 1) & m, log2n);
           const float w = wxy * wz[oz];
-          ax = fmaf(w, __ldg(g + c), ax);
-          ay = fmaf(w, __ldg(g + N + c), ay);
-          az = fmaf(w, __ldg(g + 2 * N + c), az);
+          if (VEC4) {
+            const float4 v = __ldg(reinterpret_cast<const float4*>(g) + c);
+            ax = fmaf(w, v.x, ax);
+            ay = fmaf(w, v.y, ay);
+            az = fmaf(w, v.z, az);
+          } else {
+            ax = fmaf(w, __ldg(g + c), ax);
+            ay = fmaf(w, __ldg(g + N + c), ay);
+            az = fmaf(w, __ldg(g + 2 * N + c), az);
+          }
         }
       }
     }
@@ -124,33 +193,60 @@ __global__ void __launch_bounds__(256) k_interp_kdk(const float* __restrict__ g,
 }
 
 template <int ORDER>
-void launch_grad(const float* phi, const float* eps, float alpha, float* g, int n, cudaStream_t s) {
+pm_status launch_grad(const float* phi, const float* eps, float alpha, float* g, int n, bool vec4, cudaStream_t s) {
   const int64_t N = (int64_t)n * n * n;
+  const double bytes = (eps ? 8.0 : 4.0) * N + (vec4 ? 16.0 : 12.0) * N;
+  if (n >= 64) {
+    constexpr int R = Stencil<ORDER>::R;
+    constexpr size_t smem = sizeof(float) * (2 * R + 1) * (GTY + 2 * R) * (GTZ + 2 * R);
+    const int tiles = (n / GTY) * (n / GTZ);
+    int chunk = n;
+    while (chunk > 16 && (int64_t)tiles * (n / chunk) < 8 * 152) chunk >>= 1;
+    const int nitems = tiles * (n / chunk);
+    const unsigned grid = (unsigned)(nitems < 152 * 4 ? nitems : 152 * 4);
+#define PM_GRAD_STREAM(FRB, V4)                                                                                    \
+  PM_LAUNCH(K_GRADIENT, bytes, (k_gradient_stream<ORDER, FRB, V4>), grid, GNT, smem, s, phi, eps, alpha, g, ilog2(n), \
+            (float)n, chunk, nitems)
+    if (eps) {
+      if (vec4) PM_GRAD_STREAM(true, true); else PM_GRAD_STREAM(true, false);
+    } else {
+      if (vec4) PM_GRAD_STREAM(false, true); else PM_GRAD_STREAM(false, false);
+    }
+#undef PM_GRAD_STREAM
+    return launch_status();
+  }
+  if (vec4) return PM_EINVAL;
   const unsigned grid = grid_for(N, 256);
   if (eps)
-    PM_LAUNCH(K_GRADIENT, 20.0 * N, (k_gradient<ORDER, true>), grid, 256, 0, s, phi, eps, alpha, g, ilog2(n), (float)n);
+    PM_LAUNCH(K_GRADIENT, bytes, (k_gradient<ORDER, true>), grid, 256, 0, s, phi, eps, alpha, g, ilog2(n), (float)n);
   else
-    PM_LAUNCH(K_GRADIENT, 16.0 * N, (k_gradient<ORDER, false>), grid, 256, 0, s, phi, eps, alpha, g, ilog2(n), (float)n);
+    PM_LAUNCH(K_GRADIENT, bytes, (k_gradient<ORDER, false>), grid, 256, 0, s, phi, eps, alpha, g, ilog2(n), (float)n);
+  return launch_status();
 }
 
 }  // namespace
 
-pm_status gradient_launch(const float* phi, const float* eps, float alpha, float* g, int n, int order,
+pm_status gradient_launch(const float* phi, const float* eps, float alpha, float* g, int n, int order, bool vec4,
                           cudaStream_t s) {
-  if (order == 3) launch_grad<3>(phi, eps, alpha, g, n, s);
-  else if (order == 5) launch_grad<5>(phi, eps, alpha, g, n, s);
-  else if (order == 7) launch_grad<7>(phi, eps, alpha, g, n, s);
-  else return PM_EINVAL;
-  return launch_status();
+  if (order == 3) return launch_grad<3>(phi, eps, alpha, g, n, vec4, s);
+  if (order == 5) return launch_grad<5>(phi, eps, alpha, g, n, vec4, s);
+  if (order == 7) return launch_grad<7>(phi, eps, alpha, g, n, vec4, s);
+  return PM_EINVAL;
 }
 
 pm_status interp_launch(const float* g, const uint32_t* Xs, const float* Vs, const uint32_t* ids_in, int64_t np,
                         int n, float* acc, uint32_t* Xo, float* Vo, uint32_t* ids_out, float dt_kick,
-                        float dt_drift, int mode, cudaStream_t s) {
+                        float dt_drift, int mode, bool vec4, cudaStream_t s) {
   if (np == 0) return PM_OK;
   const float drift_scale = (float)((double)dt_drift * 4294967296.0);
-  PM_LAUNCH(K_INTERP, 12.0 * n * n * (double)n + np * (12.0 + (mode ? 36.0 : 0.0) + (acc ? 12.0 : 0.0) + (ids_out ? 8.0 : 0.0)), k_interp_kdk, grid_for(np, 256), 256, 0, s, g, Xs, Vs, ids_in, np, ilog2(n), acc, Xo, Vo,
-            ids_out, dt_kick, drift_scale, mode);
+  const double bytes = (vec4 ? 16.0 : 12.0) * n * n * (double)n +
+                       np * (12.0 + (mode ? 36.0 : 0.0) + (acc ? 12.0 : 0.0) + (ids_out ? 8.0 : 0.0));
+  if (vec4)
+    PM_LAUNCH(K_INTERP, bytes, k_interp_kdk<true>, grid_for(np, 256), 256, 0, s, g, Xs, Vs, ids_in, np, ilog2(n), acc,
+              Xo, Vo, ids_out, dt_kick, drift_scale, mode);
+  else
+    PM_LAUNCH(K_INTERP, bytes, k_interp_kdk<false>, grid_for(np, 256), 256, 0, s, g, Xs, Vs, ids_in, np, ilog2(n),
+              acc, Xo, Vo, ids_out, dt_kick, drift_scale, mode);
   return launch_status();
 }
 

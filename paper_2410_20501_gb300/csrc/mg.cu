@@ -160,39 +160,56 @@ __global__ void __launch_bounds__(256) k_resid_norm(const float* __restrict__ u,
 }
 
 // u += P(uc - uc2): cell-centred trilinear prolongation, weights 27/9/3/1 over
-// 64 (§3.6.1); uc2 may be NULL.
+// 64 (§3.6.1); uc2 may be NULL.  One thread per coarse cell: it reads the
+// 3x3x3 coarse neighbourhood once and corrects its 8 children (pairs along z
+// as float2).  Per child the interpolation runs z, then y, then x, parent
+// (weight 3/4) before neighbour (1/4), in fused multiply-adds.
 __global__ void k_prolong_correct(float* __restrict__ u, const float* __restrict__ uc,
                                   const float* __restrict__ uc2, int log2n) {
-  const int m = (1 << log2n) - 1, lc = log2n - 1, mc = (1 << lc) - 1;
-  const int64_t total = (int64_t)1 << (3 * log2n);
-  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < total;
-       c += (int64_t)gridDim.x * blockDim.x) {
-    const int k = (int)(c & m), j = (int)((c >> log2n) & m), i = (int)(c >> (2 * log2n));
-    const int I0 = i >> 1, J0 = j >> 1, K0 = k >> 1;
-    const int I1 = (i & 1) ? ((I0 + 1) & mc) : ((I0 - 1) & mc);
-    const int J1 = (j & 1) ? ((J0 + 1) & mc) : ((J0 - 1) & mc);
-    const int K1 = (k & 1) ? ((K0 + 1) & mc) : ((K0 - 1) & mc);
-    const int Is[2] = {I0, I1}, Js[2] = {J0, J1}, Ks[2] = {K0, K1};
-    const float w[2] = {0.75f, 0.25f};
-    float v = 0.0f;
+  const int lc = log2n - 1, mc = (1 << lc) - 1;
+  const int64_t total = (int64_t)1 << (3 * lc);
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int K = (int)(t & mc), J = (int)((t >> lc) & mc), I = (int)(t >> (2 * lc));
+    float c[3][3][3];   // [x][y][z], index 1 = this coarse cell
 #pragma unroll
-    for (int a = 0; a < 2; ++a) {
-      float vy = 0.0f;
+    for (int a = 0; a < 3; ++a)
 #pragma unroll
-      for (int b = 0; b < 2; ++b) {
-        float vz = 0.0f;
+      for (int b = 0; b < 3; ++b)
 #pragma unroll
-        for (int cc = 0; cc < 2; ++cc) {
-          const int64_t q = idx3(Is[a], Js[b], Ks[cc], lc);
+        for (int cc = 0; cc < 3; ++cc) {
+          const int64_t q = idx3((I + a - 1) & mc, (J + b - 1) & mc, (K + cc - 1) & mc, lc);
           float x = __ldg(uc + q);
           if (uc2) x -= __ldg(uc2 + q);
-          vz = fmaf(w[cc], x, vz);
+          c[a][b][cc] = x;
         }
-        vy = fmaf(w[b], vz, vy);
+    // z then y contractions: vy[x][b][cz] for child offsets b (y) and cz (z)
+    float vy[3][2][2];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 2; ++b)
+#pragma unroll
+        for (int cz = 0; cz < 2; ++cz) {
+          const int jn = b ? 2 : 0, kn = cz ? 2 : 0;
+          const float vz0 = fmaf(0.25f, c[a][1][kn], fmaf(0.75f, c[a][1][1], 0.0f));
+          const float vz1 = fmaf(0.25f, c[a][jn][kn], fmaf(0.75f, c[a][jn][1], 0.0f));
+          vy[a][b][cz] = fmaf(0.25f, vz1, fmaf(0.75f, vz0, 0.0f));
+        }
+#pragma unroll
+    for (int ax = 0; ax < 2; ++ax) {
+      const int in = ax ? 2 : 0;
+#pragma unroll
+      for (int b = 0; b < 2; ++b) {
+        const float v0 = fmaf(0.25f, vy[in][b][0], fmaf(0.75f, vy[1][b][0], 0.0f));
+        const float v1 = fmaf(0.25f, vy[in][b][1], fmaf(0.75f, vy[1][b][1], 0.0f));
+        float2* dst = reinterpret_cast<float2*>(u + idx3(2 * I + ax, 2 * J + b, 2 * K, log2n));
+        float2 w = *dst;
+        w.x += v0;
+        w.y += v1;
+        *dst = w;
       }
-      v = fmaf(w[a], vy, v);
     }
-    u[c] += v;
   }
 }
 
@@ -359,7 +376,7 @@ pm_status v_cycle(MG& g, int l, bool zero_guess) {
     PM_LAUNCH(K_MG_RESTRICT, 68.0 * nc, k_resid_restrict<false>, grid, 256, 0, g.s, g.u[l], g.f[l], log2n,
               (float)n * (float)n, const_cast<float*>(g.f[l + 1].p));
   PM_TRY(v_cycle(g, l + 1, true));
-  PM_LAUNCH(K_MG_PROLONG, 68.0 * nc, k_prolong_correct, grid_for(nc * 8, 256), 256, 0, g.s, g.u[l], g.u[l + 1],
+  PM_LAUNCH(K_MG_PROLONG, 68.0 * nc, k_prolong_correct, grid_for(nc, 256), 256, 0, g.s, g.u[l], g.u[l + 1],
             (const float*)nullptr, log2n);
   if (p.npost > 0) {
     for (int si = 0; si < p.npost; ++si) w[si] = si == p.npost - 1 ? 1.0f : p.omega;
@@ -373,7 +390,8 @@ pm_status v_cycle(MG& g, int l, bool zero_guess) {
 pm_status prolong_correct_launch(float* u, const float* uc, const float* uc2, int n_fine, int cls,
                                  cudaStream_t s) {
   const int64_t N = (int64_t)n_fine * n_fine * n_fine;
-  PM_LAUNCH(cls, 8.0 * N + (uc2 ? 1.0 : 0.5) * N, k_prolong_correct, grid_for(N, 256), 256, 0, s, u, uc, uc2, ilog2(n_fine));
+  PM_LAUNCH(cls, 8.0 * N + (uc2 ? 1.0 : 0.5) * N, k_prolong_correct, grid_for(N / 8, 256), 256, 0, s, u, uc, uc2,
+            ilog2(n_fine));
   return PM_OK;
 }
 

@@ -103,12 +103,15 @@ pm_status prolong_correct_launch(float* u, const float* uc, const float* uc2, in
 // Background constants of the f(R) equation (host, float64).
 void fr_background(const fr_params& p, double* fbar, double* kappa, double* c2);
 
+// g = -grad(phi [+ alpha (2 eps + eps^2)]); vec4: g interleaved as float4
+// (gx, gy, gz, 0) per cell (n >= 64 only), else three planes.
 pm_status gradient_launch(const float* phi, const float* eps, float alpha, float* g, int n,
-                          int order, cudaStream_t s);
-// mode 0: acc only; mode 1: kick + drift into Xo/Vo (and acc if non-NULL).
+                          int order, bool vec4, cudaStream_t s);
+// mode 0: acc only; mode 1: kick + drift into Xo/Vo (and acc if non-NULL);
+// vec4: g interleaved as float4.
 pm_status interp_launch(const float* g, const uint32_t* Xs, const float* Vs, const uint32_t* ids_in,
                         int64_t np, int n, float* acc, uint32_t* Xo, float* Vo, uint32_t* ids_out,
-                        float dt_kick, float dt_drift, int mode, cudaStream_t s);
+                        float dt_kick, float dt_drift, int mode, bool vec4, cudaStream_t s);
 
 // Copies `count` doubles of device reduction results to host (synchronises).
 pm_status fetch_scalars(const double* dev, double* host, int count, cudaStream_t s);

@@ -127,9 +127,8 @@ def test_mg_warm_start_scaled_guess(pm):
 
 # -------------------------------------------------------------- gradient ---
 
-@pytest.mark.parametrize("order", [3, 5, 7])
-def test_gradient_parity(pm, order):
-    n = 32
+@pytest.mark.parametrize("order,n", [(3, 32), (5, 32), (7, 32), (3, 64), (5, 128), (7, 64)])
+def test_gradient_parity(pm, order, n):
     phi = random_source(n, 4).astype(np.float32)
     g = pm.gradient(torch.from_numpy(phi).cuda(), order).cpu().numpy()
     ref = np.stack(mesh.force_from_potential(phi.astype(np.float64), 1.0 / n, order))
@@ -206,6 +205,19 @@ def test_step_accelerations_fr(pm):
     acc, _ = gpu_accelerations(pm, X, V, n, 0.7, gravity="fr", boxsize=float(n), Om=0.3, OL=0.7, mg=mgp, fr=frp)
     prm = step.PMParams(n=n, Om=0.3, OL=0.7, boxsize=float(n), gravity="fr", fR0=-1e-5)
     ref, _, _ = step.accelerations(mesh.positions_from_fixed_point(X), 0.7, prm)
+    assert rel_l2(acc.T, ref) < 1e-5
+
+
+@pytest.mark.parametrize("gravity", ["newton", "fr"])
+def test_step_accelerations_64_lcdm(pm, gravity):
+    """64^3 LCDM 2LPT particles (the float4 gradient / interpolation path of
+    pm_step for n >= 64)."""
+    n = 64
+    X, V = inputs.lpt_ics(n, float(n), 0.3, 0.7, 0.25, seed=9, order=2)
+    mgp = pm.default_mg(tol=1e-9)
+    acc, _ = gpu_accelerations(pm, X, V, n, 0.25, gravity=gravity, boxsize=float(n), Om=0.3, OL=0.7, mg=mgp)
+    prm = step.PMParams(n=n, Om=0.3, OL=0.7, boxsize=float(n), gravity=gravity, fR0=-1e-5)
+    ref, _, _ = step.accelerations(mesh.positions_from_fixed_point(X), 0.25, prm)
     assert rel_l2(acc.T, ref) < 1e-5
 
 
