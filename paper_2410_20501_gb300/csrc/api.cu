@@ -342,7 +342,9 @@ pm_status pm_step(pm_state* st_, const pm_step_params* prm, pm_stats* stats, voi
     if (r != PM_OK) solve_status = r;
   }
   const float alpha = (float)(-0.5 * c2 * fbar);
-  const bool vec4 = n >= 64;   // g interleaved as float4: one 16-byte load per cell in the interpolation
+  // three planes: the interpolation is bound by L1 wavefronts, and 16-byte
+  // gathers of an interleaved float4 layout measured slower than three 4-byte ones
+  const bool vec4 = false;
   PM_TRY(gradient_launch(S.phi, prm->gravity == PM_GRAVITY_FR ? S.eps : nullptr, alpha, w.g, n, prm->grad_order,
                          vec4, s));
   PM_TRY(interp_launch(w.g, w.Xs, w.Vs, w.ids, np, n, S.acc, S.X, S.V, S.id, (float)prm->dt_kick,

@@ -286,7 +286,7 @@ pm_status fr_smooth(FR& f, int l, int count) {
   if (f.p->smoother == 0 && stream_ok(c.n) && f.alt[l]) {
     int chunk, nitems;
     stream_plan(c.n, &chunk, &nitems);
-    const unsigned grid = (unsigned)(nitems < 152 * 3 ? nitems : 152 * 3);
+    const unsigned grid = (unsigned)(nitems < 152 * 2 ? nitems : 152 * 2);   // 2 CTAs/SM (shared memory)
     const FRUpdate upd{c.beta, c.kappa, c.q};
     for (int done = 0; done < count;) {
       const int S = (count - done) >= 2 ? 2 : 1;

@@ -317,7 +317,7 @@ pm_status smooth(MG& g, int l, int count, const float* w, bool zero, float scale
       const int S = (count - done) >= 2 ? 2 : 1;
       PoissonUpdate upd{h2, {w[done], S == 2 ? w[done + 1] : 1.0f}, done == 0 ? scale : 1.0f};
       const int z = (done == 0 && zero) ? 1 : 0;
-      const unsigned grid = (unsigned)(nitems < 152 * 3 ? nitems : 152 * 3);
+      const unsigned grid = (unsigned)(nitems < 152 * 2 ? nitems : 152 * 2);   // 2 CTAs/SM (shared memory)
       if (S == 2)
         PM_LAUNCH(K_MG_SMOOTH, (z ? 8.0 : 12.0) * N, (k_rb_stream<2, PoissonUpdate>), grid, kStreamThreads,
                   StreamGeom<2>::smem_bytes, g.s, g.u[l], g.alt[l], g.f[l], log2n, chunk, nitems, z, upd);
