@@ -82,48 +82,66 @@ __global__ void __launch_bounds__(T * T * T) k_deposit(const uint32_t* __restric
 // Streaming variant for n >= 32: a CTA owns a DTY x DTZ column of
 // destination cells and a chunk of x planes; it walks the source planes in
 // order, computes the 27 moments of each source cell of the plane (column
-// plus a one-cell halo in y and z) into shared memory, and lets every
-// destination cell of the column add, in a fixed order, the moments that point
-// at it into a ring of three destination-plane accumulators.  A destination
-// plane is complete (and written) once the source plane after it has been
-// added.  Each source cell is computed 1.2x on average instead of ~2x.
-constexpr int DTY = 16, DTZ = 32, DEY = DTY + 2, DEZ = DTZ + 2, DNT = DTY * DTZ;
+// plus a one-cell halo in y and z: one cell per thread) into shared memory,
+// and lets every destination cell of the column add, in a fixed order, the
+// moments that point at it into a ring of three destination-plane
+// accumulators.  A destination plane is complete (and written) once the
+// source plane after it has been added.  The cell starts of plane x + 2 and
+// the first particle of plane x + 1 are loaded while plane x is processed.
+constexpr int DTY = 16, DTZ = 32, DEY = DTY + 2, DEZ = DTZ + 2, DNT = DTY * DTZ, DTHREADS = 1024;
 constexpr size_t kDepositStreamSmem = sizeof(float) * (27 * DEY * DEZ + 3 * DNT);
+static_assert(DEY * DEZ <= DTHREADS, "one source cell per thread");
 
-__global__ void __launch_bounds__(DNT) k_deposit_stream(const uint32_t* __restrict__ Xs, int64_t np,
-                                                       const uint32_t* __restrict__ cellstart, int log2n,
-                                                       int chunk, int nitems, float scale,
-                                                       float* __restrict__ rho, double* __restrict__ partial) {
+__global__ void __launch_bounds__(DTHREADS, 1) k_deposit_stream(const uint32_t* __restrict__ Xs, int64_t np,
+                                                                const uint32_t* __restrict__ cellstart, int log2n,
+                                                                int chunk, int nitems, float scale,
+                                                                float* __restrict__ rho, double* __restrict__ partial) {
   extern __shared__ float sm[];
   float* Mom = sm;                      // [27][DEY * DEZ]
   float* Acc = sm + 27 * DEY * DEZ;     // [3][DNT]
-  __shared__ double wsum[DNT / 32];
+  __shared__ double wsum[DTHREADS / 32];
   constexpr int PL = DEY * DEZ;
   const int n = 1 << log2n, mask = n - 1;
   const int tiles_z = n / DTZ, tiles = (n / DTY) * tiles_z;
   const int tid = threadIdx.x;
-  const int ty = tid / DTZ, tz = tid - ty * DTZ;
+  const bool src = tid < PL, dst = tid < DNT;
+  const int sly = tid / DEZ, slz = tid - sly * DEZ;            // source cell of this thread (if src)
+  const int ty = tid / DTZ, tz = tid - ty * DTZ;               // destination cell (if dst)
   for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
     const int tile = item % tiles, xc = item / tiles;
     const int y0 = (tile / tiles_z) * DTY, z0 = (tile % tiles_z) * DTZ;
     const int x0 = xc * chunk, x1 = x0 + chunk;
-    for (int q = 0; q < 3; ++q) Acc[q * DNT + tid] = 0.0f;
+    const uint32_t cy = (uint32_t)((y0 - 1 + sly) & mask), cz = (uint32_t)((z0 - 1 + slz) & mask);
+    auto cell_of = [&](int x) -> uint32_t { return ((((uint32_t)(x & mask)) << log2n | cy) << log2n) | cz; };
+    if (dst)
+      for (int q = 0; q < 3; ++q) Acc[q * DNT + tid] = 0.0f;
     float wsum_s = 0.0f, wsum_c = 0.0f;
+    // pipeline registers: cell starts of planes xs and xs + 1, first particle of plane xs
+    uint32_t b0 = 0, e0 = 0, b1 = 0, e1 = 0, fx = 0, fy = 0, fz = 0;
+    if (src) {
+      const uint32_t c0 = cell_of(x0 - 1), c1 = cell_of(x0);
+      b0 = __ldg(cellstart + c0); e0 = __ldg(cellstart + c0 + 1);
+      b1 = __ldg(cellstart + c1); e1 = __ldg(cellstart + c1 + 1);
+      if (b0 < e0) { fx = __ldg(Xs + b0); fy = __ldg(Xs + np + b0); fz = __ldg(Xs + 2 * np + b0); }
+    }
     for (int xs = x0 - 1; xs <= x1; ++xs) {
-      const uint32_t cx = (uint32_t)(xs & mask);
-      for (int e = tid; e < PL; e += DNT) {
-        const int ly = e / DEZ, lz = e - ly * DEZ;
-        const uint32_t cy = (uint32_t)((y0 - 1 + ly) & mask), cz = (uint32_t)((z0 - 1 + lz) & mask);
-        const uint32_t c = (((cx << log2n) | cy) << log2n) | cz;
-        const uint32_t beg = __ldg(cellstart + c), end = __ldg(cellstart + c + 1);
+      uint32_t nfx = 0, nfy = 0, nfz = 0, b2 = 0, e2 = 0;
+      if (src) {
+        if (b1 < e1) { nfx = __ldg(Xs + b1); nfy = __ldg(Xs + np + b1); nfz = __ldg(Xs + 2 * np + b1); }
+        if (xs + 2 <= x1) {
+          const uint32_t c2 = cell_of(xs + 2);
+          b2 = __ldg(cellstart + c2); e2 = __ldg(cellstart + c2 + 1);
+        }
         float m[27];
 #pragma unroll
         for (int o = 0; o < 27; ++o) m[o] = 0.0f;
-        for (uint32_t p = beg; p < end; ++p) {
+        uint32_t px = fx, py = fy, pz = fz;
+        for (uint32_t p = b0; p < e0; ++p) {
+          if (p > b0) { px = __ldg(Xs + p); py = __ldg(Xs + np + p); pz = __ldg(Xs + 2 * np + p); }
           float wx[3], wy[3], wz[3];
-          tsc_weights(cell_offset(__ldg(Xs + p), log2n), wx);
-          tsc_weights(cell_offset(__ldg(Xs + np + p), log2n), wy);
-          tsc_weights(cell_offset(__ldg(Xs + 2 * np + p), log2n), wz);
+          tsc_weights(cell_offset(px, log2n), wx);
+          tsc_weights(cell_offset(py, log2n), wy);
+          tsc_weights(cell_offset(pz, log2n), wz);
 #pragma unroll
           for (int ox = 0; ox < 3; ++ox)
 #pragma unroll
@@ -134,39 +152,43 @@ __global__ void __launch_bounds__(DNT) k_deposit_stream(const uint32_t* __restri
             }
         }
 #pragma unroll
-        for (int o = 0; o < 27; ++o) Mom[o * PL + e] = m[o];
+        for (int o = 0; o < 27; ++o) Mom[o * PL + tid] = m[o];
       }
       __syncthreads();
-      // destination plane xs + ox - 1 receives the moments with x offset ox - 1
+      if (dst) {
+        // destination plane xs + ox - 1 receives the moments with x offset ox - 1
 #pragma unroll
-      for (int ox = 0; ox < 3; ++ox) {
-        const int d = xs + ox - 1;
-        if (d < x0 || d >= x1) continue;
-        float a = 0.0f;
+        for (int ox = 0; ox < 3; ++ox) {
+          const int d = xs + ox - 1;
+          if (d < x0 || d >= x1) continue;
+          float a = 0.0f;
 #pragma unroll
-        for (int oy = 0; oy < 3; ++oy)
+          for (int oy = 0; oy < 3; ++oy)
 #pragma unroll
-          for (int oz = 0; oz < 3; ++oz)
-            a += Mom[((ox * 3 + oy) * 3 + oz) * PL + (ty + 2 - oy) * DEZ + (tz + 2 - oz)];
-        Acc[(d % 3) * DNT + tid] += a;
-      }
-      // plane xs - 1 has now received its three source planes
-      const int done = xs - 1;
-      if (done >= x0 && done < x1) {
-        float* slot = Acc + (done % 3) * DNT;
-        const float r = slot[tid] * scale;
-        rho[((((int64_t)done << log2n) | (y0 + ty)) << log2n) | (z0 + tz)] = r;
-        kahan_add(wsum_s, wsum_c, r);
-        slot[tid] = 0.0f;
+            for (int oz = 0; oz < 3; ++oz)
+              a += Mom[((ox * 3 + oy) * 3 + oz) * PL + (ty + 2 - oy) * DEZ + (tz + 2 - oz)];
+          Acc[(d % 3) * DNT + tid] += a;
+        }
+        // plane xs - 1 has now received its three source planes
+        const int done = xs - 1;
+        if (done >= x0 && done < x1) {
+          float* slot = Acc + (done % 3) * DNT;
+          const float r = slot[tid] * scale;
+          rho[((((int64_t)done << log2n) | (y0 + ty)) << log2n) | (z0 + tz)] = r;
+          kahan_add(wsum_s, wsum_c, r);
+          slot[tid] = 0.0f;
+        }
       }
       __syncthreads();
+      b0 = b1; e0 = e1; b1 = b2; e1 = e2;
+      fx = nfx; fy = nfy; fz = nfz;
     }
     const double ws = warp_sum_comp(wsum_s - wsum_c);
     if ((tid & 31) == 0) wsum[tid >> 5] = ws;
     __syncthreads();
     if (tid == 0) {
       double t = 0.0;
-      for (int w = 0; w < DNT / 32; ++w) t += wsum[w];
+      for (int w = 0; w < DTHREADS / 32; ++w) t += wsum[w];
       partial[item] = t;
     }
     __syncthreads();
@@ -265,8 +287,8 @@ pm_status deposit_sorted(const uint32_t* Xs, int64_t np, const uint32_t* cellsta
     int chunk, nitems;
     deposit_stream_plan(n, &chunk, &nitems);
     const float scale = np > 0 ? (float)((double)n * n * n / (double)np) : 0.0f;
-    const unsigned grid = (unsigned)(nitems < 152 * 2 ? nitems : 152 * 2);   // 2 CTAs/SM (registers)
-    PM_LAUNCH(K_DEPOSIT, 12.0 * np + 8.0 * n * n * (double)n + 4.0, k_deposit_stream, grid, DNT, kDepositStreamSmem,
+    const unsigned grid = (unsigned)(nitems < 152 ? nitems : 152);   // one 1024-thread CTA per SM
+    PM_LAUNCH(K_DEPOSIT, 12.0 * np + 8.0 * n * n * (double)n + 4.0, k_deposit_stream, grid, DTHREADS, kDepositStreamSmem,
               s, Xs, np, cellstart, ilog2(n), chunk, nitems, scale, rho, partials);
     PM_LAUNCH(K_REDUCE, 8.0 * nitems, k_reduce_partials, 1, 1024, 0, s, partials, (int64_t)nitems, (int64_t)0, 1,
               1.0 / ((double)n * n * n), mean_out);

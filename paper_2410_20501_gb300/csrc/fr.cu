@@ -114,21 +114,24 @@ __global__ void k_fr_restrict(const float* __restrict__ e, Src b, int log2n, flo
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
        t += (int64_t)gridDim.x * blockDim.x) {
     const int K = (int)(t & mc), J = (int)((t >> lc) & mc), I = (int)(t >> (2 * lc));
+    float core[2][2][4], xf[2][2][2], yf[2][2][2];
+    load_children_block(e, I, J, K, log2n, core, xf, yf);
     float se = 0.0f, sd = 0.0f;
 #pragma unroll
     for (int a = 0; a < 2; ++a)
 #pragma unroll
-      for (int bb = 0; bb < 2; ++bb)
+      for (int bb = 0; bb < 2; ++bb) {
+        const float2 br = __ldg(reinterpret_cast<const float2*>(b.p + idx3(2 * I + a, 2 * J + bb, 2 * K, log2n)));
+        const float bz[2] = {b.s * (br.x - mean), b.s * (br.y - mean)};
 #pragma unroll
         for (int cc = 0; cc < 2; ++cc) {
-          const int i = 2 * I + a, j = 2 * J + bb, k = 2 * K + cc;
-          const int64_t c = idx3(i, j, k, log2n);
           float nb[6];
-          load_nb(e, i, j, k, log2n, nb);
-          const float ec = e[c];
+          child_nb(core, xf, yf, a, bb, cc, nb);
+          const float ec = core[a][bb][cc + 1];
           se += ec;
-          sd += src_at(b, c, mean) - fr_op(ec, nb, alpha, kappa);
+          sd += bz[cc] - fr_op(ec, nb, alpha, kappa);
         }
+      }
     eH[t] = 0.125f * se;
     rH[t] = 0.125f * se;
     bH[t] = 0.125f * sd;

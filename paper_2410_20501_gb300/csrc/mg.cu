@@ -106,18 +106,20 @@ __global__ void k_resid_restrict(const float* __restrict__ u, Src f, int log2n, 
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
        t += (int64_t)gridDim.x * blockDim.x) {
     const int K = (int)(t & mc), J = (int)((t >> lc) & mc), I = (int)(t >> (2 * lc));
+    float core[2][2][4], xf[2][2][2], yf[2][2][2];
+    load_children_block(u, I, J, K, log2n, core, xf, yf);
     float sum = 0.0f;
 #pragma unroll
     for (int a = 0; a < 2; ++a)
 #pragma unroll
-      for (int b = 0; b < 2; ++b)
+      for (int b = 0; b < 2; ++b) {
+        const float2 fr = __ldg(reinterpret_cast<const float2*>(f.p + idx3(2 * I + a, 2 * J + b, 2 * K, log2n)));
+        const float fz[2] = {f.s * (fr.x - mean), f.s * (fr.y - mean)};
 #pragma unroll
         for (int cc = 0; cc < 2; ++cc) {
-          const int i = 2 * I + a, j = 2 * J + b, k = 2 * K + cc;
-          const int64_t c = idx3(i, j, k, log2n);
           float nb[6];
-          load_nb(u, i, j, k, log2n, nb);
-          const float uc = __ldg(u + c), fv = src_at(f, c, mean);
+          child_nb(core, xf, yf, a, b, cc, nb);
+          const float uc = core[a][b][cc + 1], fv = fz[cc];
           float d;
           if (COMP) {
             float S, E;
@@ -130,6 +132,7 @@ __global__ void k_resid_restrict(const float* __restrict__ u, Src f, int log2n, 
           }
           sum += d;
         }
+      }
     fc[t] = 0.125f * sum;
   }
 }

@@ -68,4 +68,56 @@ __device__ __forceinline__ void block_sum_to(double* out, float sum, float comp,
   __syncthreads();
 }
 
+// The 32 values of u that the 8 children of coarse cell (I, J, K) and their
+// face neighbours touch on the fine grid (n = 2^log2n), z pairs as float2:
+//   core[a][b][t]: x = 2I + a, y = 2J + b, z = 2K - 1 + t (t = 0..3)
+//   xf[0|1][b][c]: x = 2I - 1 | 2I + 2, y = 2J + b, z = 2K + c
+//   yf[a][0|1][c]: x = 2I + a, y = 2J - 1 | 2J + 2, z = 2K + c
+// The 6 neighbours of child (a, b, c) in the order x+, x-, y+, y-, z+, z- then
+// come from child_nb().
+__device__ __forceinline__ void load_children_block(const float* __restrict__ u, int I, int J, int K, int log2n,
+                                                    float core[2][2][4], float xf[2][2][2], float yf[2][2][2]) {
+  const int m = (1 << log2n) - 1;
+  auto at = [&](int x, int y, int z) -> int64_t {
+    return ((int64_t)(x & m) << (2 * log2n)) | ((int64_t)(y & m) << log2n) | (z & m);
+  };
+  const int x0 = 2 * I, y0 = 2 * J, z0 = 2 * K;
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+      const float2 c2 = __ldg(reinterpret_cast<const float2*>(u + at(x0 + a, y0 + b, z0)));
+      core[a][b][0] = __ldg(u + at(x0 + a, y0 + b, z0 - 1));
+      core[a][b][1] = c2.x;
+      core[a][b][2] = c2.y;
+      core[a][b][3] = __ldg(u + at(x0 + a, y0 + b, z0 + 2));
+    }
+#pragma unroll
+  for (int side = 0; side < 2; ++side)
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+      const float2 v = __ldg(reinterpret_cast<const float2*>(u + at(side ? x0 + 2 : x0 - 1, y0 + b, z0)));
+      xf[side][b][0] = v.x;
+      xf[side][b][1] = v.y;
+    }
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+      const float2 v = __ldg(reinterpret_cast<const float2*>(u + at(x0 + a, side ? y0 + 2 : y0 - 1, z0)));
+      yf[a][side][0] = v.x;
+      yf[a][side][1] = v.y;
+    }
+}
+
+__device__ __forceinline__ void child_nb(const float core[2][2][4], const float xf[2][2][2], const float yf[2][2][2],
+                                         int a, int b, int c, float nb[6]) {
+  nb[0] = a ? xf[1][b][c] : core[1][b][c + 1];
+  nb[1] = a ? core[0][b][c + 1] : xf[0][b][c];
+  nb[2] = b ? yf[a][1][c] : core[a][1][c + 1];
+  nb[3] = b ? core[a][0][c + 1] : yf[a][0][c];
+  nb[4] = core[a][b][c + 2];
+  nb[5] = core[a][b][c];
+}
+
 }  // namespace pmgb
