@@ -283,6 +283,13 @@ def run_gpu(args):
             "peak_source": peak_kind,
             "launches": dcount, "avg_launch_ms": dms / dcount if dcount else None,
             "share_of_step": dms / fr_res["ms"] if fr_res["ms"] else None}
+    mg_classes = [k for k in kern if k.startswith("mg_")]
+    mg_ms = sum(kern[k][0] for k in mg_classes)
+    mg_bytes = sum(kern[k][2] for k in mg_classes)
+    vcycle = {"achieved": mg_bytes / (mg_ms / 1e3) / 1e9 if mg_ms else None, "unit": "GB/s",
+              "ms_per_step": mg_ms / K, "frac": (mg_bytes / (mg_ms / 1e3) / 1e9) / peak if mg_ms else None,
+              "what": "algorithmic bytes of every Poisson multigrid kernel (all levels, smoothing, transfers, "
+                      "coarsest solve) / their CUDA-event time, 512^3"}
     per_kernel = {k: {"ms": round(v[0], 4), "launches": v[1],
                       "GB/s": round(v[2] / (v[0] / 1e3) / 1e9, 1) if v[0] > 0 else None}
                   for k, v in kern.items() if v[1] > 0}
@@ -304,6 +311,7 @@ def run_gpu(args):
             "h2d_bytes_per_step": results["e2e_bytes"], "d2h_bytes_per_step": results["e2e_bytes"]},
         "gpu_launches": fr_res["launches"],
         "roofline": roof,
+        "vcycle_hbm": vcycle,
         "kernels": per_kernel,
         "clocks": fr_res["clocks"],
     }
