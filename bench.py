@@ -332,8 +332,12 @@ def run_stage(args):
     if not os.path.exists(pm.LIB_PATH):
         build.build()
     n = args.n
-    X = pm.positions_to_device(inputs.uniform_particles(n ** 3, 61)) if args.stage in ("sort", "deposit",
-                                                                                       "interp") else None
+    X = None
+    if args.stage in ("sort", "deposit"):
+        X = pm.positions_to_device(inputs.uniform_particles(n ** 3, 61))
+    elif args.stage == "interp":   # cell-ordered particles, as pm_step interpolates them
+        rng = np.random.Generator(np.random.PCG64(61))
+        X = pm.positions_to_device(inputs.to_fixed_point(inputs.lattice(n) + rng.uniform(-0.45, 0.45, (3, n ** 3)) / n))
     rho = None
     if args.stage in ("mg", "fr"):
         g = inputs.random_field(n, 62)

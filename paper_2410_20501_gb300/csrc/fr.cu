@@ -31,7 +31,8 @@ __device__ __forceinline__ int64_t idx3(int i, int j, int k, int log2n) {
 }
 
 // Root eps > -1 of g(e) = e^3 + 3e^2 + c1 e + c0 (g(-1) = q < 0, g convex on
-// e > -1, so the root is unique).  Newton from the current value inside a
+// e > -1, so the root is unique).  Two plain Newton steps from the current
+// value usually reach float32 resolution; otherwise Newton continues inside a
 // shrinking bracket [lo, hi]; when a step leaves the bracket (or g' <= 0) the
 // upper end is set from the bound u* <= sqrt(max(-p, 0)) + (-q)^(1/3),
 // p = c1 - 3, and the step falls back to bisection.  Stops when g is at its
@@ -39,6 +40,15 @@ __device__ __forceinline__ int64_t idx3(int i, int j, int k, int log2n) {
 __device__ __forceinline__ float fr_root(float e, float c1, float c0, float q) {
   float lo = -1.0f, hi = __int_as_float(0x7f800000);  // +inf until needed
   if (!(e > lo)) e = 0.0f;
+  {
+    // fast path: two plain Newton steps from the current value; accepted when
+    // the second step is at float32 resolution and the root is admissible
+    const float g0 = ((e + 3.0f) * e + c1) * e + c0, gp0 = (3.0f * e + 6.0f) * e + c1;
+    const float e1 = e - __fdividef(g0, gp0);
+    const float g1 = ((e1 + 3.0f) * e1 + c1) * e1 + c0, gp1 = (3.0f * e1 + 6.0f) * e1 + c1;
+    const float e2 = e1 - __fdividef(g1, gp1);
+    if (gp0 > 0.0f && gp1 > 0.0f && e2 > lo && fabsf(e2 - e1) <= 2e-7f * fabsf(e2) + 1e-12f) return e2;
+  }
   for (int it = 0; it < 30; ++it) {
     const float e2 = e * e;
     const float g = ((e + 3.0f) * e + c1) * e + c0;

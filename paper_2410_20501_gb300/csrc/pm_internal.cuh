@@ -31,8 +31,12 @@ inline pm_status launch_status() { return cuda_status(cudaGetLastError()); }
 inline int ilog2(int64_t v) { int l = 0; while ((int64_t(1) << (l + 1)) <= v) ++l; return l; }
 inline bool valid_n(int n) { return n >= 4 && n <= 1024 && (n & (n - 1)) == 0; }
 
-// Grid size for a grid-stride loop over `count` items with `threads` per block.
-inline unsigned grid_for(int64_t count, int threads, int64_t cap = 152 * 32) {
+// Grid size for a grid-stride loop over `count` items with `threads` per
+// block.  By default one item per thread: blocks are then scheduled roughly in
+// address order, which keeps the neighbouring-plane reuse of the stencil
+// kernels inside L2 (a capped grid makes every block jump ahead by the grid's
+// span on each iteration and defeats that reuse).  Reductions pass a cap.
+inline unsigned grid_for(int64_t count, int threads, int64_t cap = ((int64_t)1 << 30)) {
   int64_t b = (count + threads - 1) / threads;
   if (b < 1) b = 1;
   if (b > cap) b = cap;
