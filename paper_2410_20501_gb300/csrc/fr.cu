@@ -42,12 +42,18 @@ __device__ __forceinline__ float fr_root(float e, float c1, float c0, float q) {
   if (!(e > lo)) e = 0.0f;
   {
     // fast path: two plain Newton steps from the current value; accepted when
-    // the second step is at float32 resolution and the root is admissible
+    // the remaining error is at float32 resolution and the root is admissible
     const float g0 = ((e + 3.0f) * e + c1) * e + c0, gp0 = (3.0f * e + 6.0f) * e + c1;
     const float e1 = e - __fdividef(g0, gp0);
     const float g1 = ((e1 + 3.0f) * e1 + c1) * e1 + c0, gp1 = (3.0f * e1 + 6.0f) * e1 + c1;
     const float e2 = e1 - __fdividef(g1, gp1);
-    if (gp0 > 0.0f && gp1 > 0.0f && e2 > lo && fabsf(e2 - e1) <= 2e-7f * fabsf(e2) + 1e-12f) return e2;
+    // Newton's error after the second step is about K d^2, d = e2 - e1,
+    // K = g''/(2 g') = (3 e1 + 3) / g'(e1): accept when that is below float32
+    // resolution of e2
+    const float d = e2 - e1;
+    if (gp0 > 0.0f && gp1 > 0.0f && e2 > lo && d * d * (3.0f * e1 + 3.0f) <= (1e-7f * fabsf(e2) + 1e-20f) * gp1)
+      return e2;
+    if (gp1 > 0.0f && e2 > lo) e = e2;   // continue from the better point
   }
   for (int it = 0; it < 30; ++it) {
     const float e2 = e * e;
@@ -97,22 +103,22 @@ __device__ __forceinline__ float fr_update(float ec, const float nb[6], float bv
   return fr_root(ec, c1, c0, q);
 }
 
-__global__ void k_fr_sweep(float* __restrict__ e, Src b, int log2n, int colour, float beta, float kappa,
-                           float q) {
-  const int m = (1 << log2n) - 1, half = log2n - 1;
-  const float mean = load_mean(b);
-  const int64_t total = (int64_t)1 << (3 * log2n - 1);
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
-       t += (int64_t)gridDim.x * blockDim.x) {
-    const int kk = (int)(t & ((1 << half) - 1));
-    const int64_t rest = t >> half;
-    const int j = (int)(rest & m), i = (int)(rest >> log2n);
-    const int k = 2 * kk + ((colour + i + j) & 1);
-    const int64_t c = idx3(i, j, k, log2n);
-    float nb[6];
-    load_nb(e, i, j, k, log2n, nb);
-    e[c] = fr_update(e[c], nb, src_at(b, c, mean), beta, kappa, q);
-  }
+__global__ void __launch_bounds__(256) k_fr_sweep(float* __restrict__ e, Src b, int log2n, int colour, float beta,
+                                                  float kappa, float q) {
+  const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (1u << (3 * log2n - 1))) return;
+  const uint32_t m = (1u << log2n) - 1;
+  const uint32_t kk = t & ((1u << (log2n - 1)) - 1), row = t >> (log2n - 1);
+  const uint32_t j = row & m, i = row >> log2n;
+  const uint32_t k = 2 * kk + ((colour + i + j) & 1);
+  const uint32_t c = (row << log2n) | k;
+  uint32_t qi[6];
+  nb_index(c, i, j, k, log2n, qi);
+  float nb[6];
+#pragma unroll
+  for (int r = 0; r < 6; ++r) nb[r] = e[qi[r]];
+  const float bv = b.s * (__ldg(b.p + c) - load_mean(b));
+  e[c] = fr_update(e[c], nb, bv, beta, kappa, q);
 }
 
 // eH = rH = R eps, bH = R(b - N_h eps).

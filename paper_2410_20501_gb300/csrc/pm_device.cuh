@@ -68,6 +68,19 @@ __device__ __forceinline__ void block_sum_to(double* out, float sum, float comp,
   __syncthreads();
 }
 
+// Flat indices (32-bit: n <= 1024) of a cell's six periodic face neighbours in
+// the order x+, x-, y+, y-, z+, z-, for c = (i n + j) n + k.
+__device__ __forceinline__ void nb_index(uint32_t c, uint32_t i, uint32_t j, uint32_t k, int log2n,
+                                         uint32_t idx[6]) {
+  const uint32_t m = (1u << log2n) - 1, n = 1u << log2n, n2 = n << log2n;
+  idx[0] = i == m ? c - m * n2 : c + n2;
+  idx[1] = i == 0 ? c + m * n2 : c - n2;
+  idx[2] = j == m ? c - m * n : c + n;
+  idx[3] = j == 0 ? c + m * n : c - n;
+  idx[4] = k == m ? c - m : c + 1;
+  idx[5] = k == 0 ? c + m : c - 1;
+}
+
 // The 32 values of u that the 8 children of coarse cell (I, J, K) and their
 // face neighbours touch on the fine grid (n = 2^log2n), z pairs as float2:
 //   core[a][b][t]: x = 2I + a, y = 2J + b, z = 2K - 1 + t (t = 0..3)
