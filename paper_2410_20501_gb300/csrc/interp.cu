@@ -137,8 +137,8 @@ __global__ void __launch_bounds__(256) k_interp_kdk(const float* __restrict__ g,
                                                     float* __restrict__ acc, uint32_t* __restrict__ Xo,
                                                     float* __restrict__ Vo, uint32_t* __restrict__ ids_out,
                                                     float dt_kick, float drift_scale, int mode) {
-  const uint32_t m = (1u << log2n) - 1, sh = 32 - log2n;
-  const uint32_t N = 1u << (3 * log2n);
+  const int m = (1 << log2n) - 1, sh = 32 - log2n;
+  const int64_t N = (int64_t)1 << (3 * log2n);
   for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < np;
        p += (int64_t)gridDim.x * blockDim.x) {
     const uint32_t x = __ldg(Xs + p), y = __ldg(Xs + np + p), z = __ldg(Xs + 2 * np + p);
@@ -146,19 +146,18 @@ __global__ void __launch_bounds__(256) k_interp_kdk(const float* __restrict__ g,
     tsc_weights(cell_offset(x, log2n), wx);
     tsc_weights(cell_offset(y, log2n), wy);
     tsc_weights(cell_offset(z, log2n), wz);
-    const uint32_t ix = x >> sh, iy = y >> sh, iz = z >> sh;
-    const uint32_t zi[3] = {(iz - 1) & m, iz, (iz + 1) & m};
+    const int ix = (int)(x >> sh), iy = (int)(y >> sh), iz = (int)(z >> sh);
     float ax = 0.0f, ay = 0.0f, az = 0.0f;
 #pragma unroll
     for (int ox = 0; ox < 3; ++ox) {
-      const uint32_t ci = (ix + ox - 1) & m;
+      const int ci = (ix + ox - 1) & m;
 #pragma unroll
       for (int oy = 0; oy < 3; ++oy) {
-        const uint32_t rb = ((ci << log2n) | ((iy + oy - 1) & m)) << log2n;   // row base
+        const int cj = (iy + oy - 1) & m;
         const float wxy = wx[ox] * wy[oy];
 #pragma unroll
         for (int oz = 0; oz < 3; ++oz) {
-          const uint32_t c = rb | zi[oz];
+          const int64_t c = idx3(ci, cj, (iz + oz - 1) & m, log2n);
           const float w = wxy * wz[oz];
           if (VEC4) {
             const float4 v = __ldg(reinterpret_cast<const float4*>(g) + c);

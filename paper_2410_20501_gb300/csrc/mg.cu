@@ -69,26 +69,31 @@ __global__ void k_scale(float* __restrict__ u, int64_t count, float a) {
 // shared with the streaming smoother).  zero: the values of this level are
 // taken as 0 (the coarse-level error starts from zero): the red pass reads
 // nothing, the black pass ignores its own old value.
-__global__ void __launch_bounds__(256) k_rb_sweep(float* __restrict__ u, Src f, int log2n, int colour,
-                                                  PoissonUpdate upd, int nb_old, int own_old, int zero) {
-  const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (1u << (3 * log2n - 1))) return;
-  const uint32_t m = (1u << log2n) - 1;
-  const uint32_t kk = t & ((1u << (log2n - 1)) - 1), row = t >> (log2n - 1);
-  const uint32_t j = row & m, i = row >> log2n;
-  const uint32_t k = 2 * kk + ((colour + i + j) & 1);
-  const uint32_t c = (row << log2n) | k;
-  float nb[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
-  float old = 0.0f;
-  if (!(zero && colour == 0)) {
-    uint32_t q[6];
-    nb_index(c, i, j, k, log2n, q);
-#pragma unroll
-    for (int r = 0; r < 6; ++r) nb[r] = u[q[r]];
+__global__ void k_rb_sweep(float* __restrict__ u, Src f, int log2n, int colour, PoissonUpdate upd,
+                           int nb_old, int own_old, int zero) {
+  const int m = (1 << log2n) - 1, half = log2n - 1;
+  const float mean = load_mean(f);
+  const int64_t total = (int64_t)1 << (3 * log2n - 1);
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int kk = (int)(t & ((1 << half) - 1));
+    const int64_t rest = t >> half;
+    const int j = (int)(rest & m), i = (int)(rest >> log2n);
+    const int k = 2 * kk + ((colour + i + j) & 1);
+    const int64_t c = idx3(i, j, k, log2n);
+    float nb[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+    float old = 0.0f;
+    if (!(zero && colour == 0)) {
+      nb[0] = u[idx3((i + 1) & m, j, k, log2n)];
+      nb[1] = u[idx3((i - 1) & m, j, k, log2n)];
+      nb[2] = u[idx3(i, (j + 1) & m, k, log2n)];
+      nb[3] = u[idx3(i, (j - 1) & m, k, log2n)];
+      nb[4] = u[idx3(i, j, (k + 1) & m, log2n)];
+      nb[5] = u[idx3(i, j, (k - 1) & m, log2n)];
+    }
+    if (!zero) old = u[c];
+    u[c] = upd(old, nb, src_at(f, c, mean), 0, nb_old != 0, own_old != 0);
   }
-  if (!zero) old = u[c];
-  const float fv = f.s * (__ldg(f.p + c) - load_mean(f));
-  u[c] = upd(old, nb, fv, 0, nb_old != 0, own_old != 0);
 }
 
 // Coarse right-hand side fc = R(f - L u): residual of the 8 children, averaged.
