@@ -67,7 +67,8 @@ enum {
   PM_WS_MG = 2,        /* mg_solve                                             */
   PM_WS_FR = 4,        /* fr_solve                                             */
   PM_WS_STEP = 8,      /* pm_step, pm_step_host (includes all of the above)    */
-  PM_WS_IDS = 16       /* pm_step carries particle ids (pm_state.id != NULL)   */
+  PM_WS_IDS = 16,      /* pm_step carries particle ids (pm_state.id != NULL)   */
+  PM_WS_ADJ = 32       /* adjoint entry points (with PM_WS_SORT or PM_WS_STEP) */
 };
 
 /* Bytes of workspace needed for grids of n^3 cells and np particles.
@@ -269,6 +270,51 @@ pm_status pm_step(pm_state* s, const pm_step_params* prm, pm_stats* st, void* st
 pm_status pm_step_host(pm_state* s, const pm_step_params* prm, pm_stats* st,
                        const uint32_t* X_in, const float* V_in,
                        uint32_t* X_out, float* V_out, void* stream);
+
+/* -------------------------------------------------------------- adjoints --
+ * Reverse-mode derivatives of the Newtonian step, for gradients of losses
+ * with respect to particle positions and velocities (and, through the
+ * initial conditions, the white noise).  Position cotangents are float32
+ * [3][np] in box units (derivative with respect to x = X * 2^-32). */
+
+/* Deposit adjoint: with rho = pm_deposit(X), dX_bar[d][p] =
+ * sum_c d rho_c / d x_p,d * rho_bar[c] = (n^3/np) n sum_c dW_pc/d(offset_d) rho_bar[c]
+ * (W_TSC is C1, §3.4).  rho_bar [n^3], dX_bar [3][np] (written). */
+pm_status pm_deposit_adj(const uint32_t* X, int64_t np, int n, const float* rho_bar, float* dX_bar,
+                         void* stream);
+
+/* Interpolation adjoint: with acc = pm_interp(g, X), g_bar = sum_p W_pc acc_bar_p
+ * (a TSC deposit of acc_bar, deterministic like pm_deposit) and
+ * dX_bar[d][p] = n sum_c dW_pc/d(offset_d) (g_c . acc_bar_p).
+ *   g [3][n^3], acc_bar [3][np] (read); g_bar [3][n^3], dX_bar [3][np] (written).
+ * Workspace: pm_workspace_size(n, np, PM_WS_SORT | PM_WS_ADJ). */
+pm_status pm_interp_adj(const float* g, const uint32_t* X, int64_t np, int n, const float* acc_bar,
+                        float* g_bar, float* dX_bar, void* ws, size_t ws_bytes, void* stream);
+
+/* Gradient adjoint: with g = pm_gradient(phi, order) (g = -G phi, Table 1),
+ * phi_bar = -G^T g_bar = sum_d G_d g_bar_d (the stencil is antisymmetric).
+ * g_bar [3][n^3] (read), phi_bar [n^3] (written). */
+pm_status pm_gradient_adj(const float* g_bar, float* phi_bar, int n, int order, void* stream);
+
+/* Multigrid adjoint: the 7-point Laplacian is self-adjoint, so the cotangent of
+ * the right-hand side of mg_solve is the solution of the same problem with the
+ * cotangent of phi as right-hand side: this is mg_solve applied to phi_bar. */
+pm_status mg_solve_adj(const float* phi_bar, float* f_bar, int n, const mg_params* prm, mg_stats* st,
+                       void* ws, size_t ws_bytes, void* stream);
+
+/* Adjoint of one Newtonian pm_step taken from the state s (s->X, s->V are the
+ * step's INPUTS; nothing in s is modified).  X_bar_out, V_bar_out are the
+ * cotangents of the step's outputs, in the output order of pm_step (cell
+ * order); X_bar_in, V_bar_in receive the cotangents of the inputs, in the
+ * input order.  The forward force evaluation is recomputed (deposit, Poisson
+ * solve to prm->mg.tol from the Jacobi guess, gradient); then a_bar =
+ * dt_kick (V_bar' + dt_drift X_bar'), g_bar = deposit of a_bar,
+ * phi_bar = -G^T g_bar, rho_bar = 3/2 a Om A^+ phi_bar (a second solve), and
+ * X_bar = X_bar' + the interpolation and deposit position terms,
+ * V_bar = V_bar' + dt_drift X_bar'.  Workspace: PM_WS_STEP | PM_WS_ADJ
+ * (| PM_WS_IDS if s->id).  Newtonian gravity only (PM_EINVAL otherwise). */
+pm_status pm_step_adj(pm_state* s, const pm_step_params* prm, const float* X_bar_out, const float* V_bar_out,
+                      float* X_bar_in, float* V_bar_in, void* stream);
 
 /* ------------------------------------------------------ host utilities ---- */
 /* Supercomoving time between a0 and a1 (§3.1): integral of da/(a^3 E(a)),

@@ -11,9 +11,10 @@ namespace pmgb {
 
 const char* const kKernelClassNames[K_NCLASS] = {
     "cell_keys",   "radix_upsweep", "radix_scan",  "radix_downsweep", "cellstart",  "permute",
-    "tsc_deposit", "reduce",        "mg_guess",    "mg_smooth",       "mg_restrict", "mg_prolong",
-    "mg_coarse",   "mg_norm",       "fr_smooth",   "fr_restrict",     "fr_coarse_op", "fr_prolong",
-    "fr_coarse",   "fr_norm",       "gradient",    "interp_kdk",      "misc"};
+    "tsc_deposit", "reduce",        "mg_guess",    "mg_smooth_l0",    "mg_smooth",   "mg_restrict",
+    "mg_prolong",  "mg_coarse",     "mg_norm",     "fr_smooth_l0",    "fr_smooth",   "fr_restrict",
+    "fr_coarse_op", "fr_prolong",
+    "fr_coarse",   "fr_norm",       "gradient",    "interp_kdk",      "adjoint",     "misc"};
 
 namespace {
 
@@ -90,6 +91,12 @@ size_t layout_workspace(Workspace* w, void* base, int n, int64_t np, uint32_t fl
     if (flags & PM_WS_IDS) w->ids = (uint32_t*)take((size_t)np * 4);
     w->rho = (float*)take((size_t)N * 4);
     w->g = (float*)take((size_t)N * 16);   // three planes, or float4 per cell
+  }
+  if (flags & PM_WS_ADJ) {
+    w->adj_abar = (float*)take((size_t)np * 12);
+    w->adj_phi = (float*)take((size_t)N * 4);
+    w->adj_psi = (float*)take((size_t)N * 4);
+    w->adj_gbar = (float*)take((size_t)N * 12);
   }
   w->partials = (double*)take((size_t)2 * reduce_partials_capacity(n, np) * 8);
   w->scalars = (double*)take(64 * 8);
@@ -369,6 +376,87 @@ pm_status pm_step_host(pm_state* st_, const pm_step_params* prm, pm_stats* stats
   PM_TRY(cuda_status(cudaMemcpyAsync(V_out, st_->V, bytes, cudaMemcpyDeviceToHost, s)));
   PM_TRY(cuda_status(cudaStreamSynchronize(s)));
   return r;
+}
+
+pm_status pm_deposit_adj(const uint32_t* X, int64_t np, int n, const float* rho_bar, float* dX_bar, void* stream) {
+  if (!valid_n(n) || !valid_np(np) || (np > 0 && (!X || !dX_bar)) || !rho_bar) return PM_EINVAL;
+  const float s_rho = np > 0 ? (float)((double)n * n * n / (double)np) : 0.0f;
+  return pos_grad_launch(X, np, n, nullptr, nullptr, rho_bar, s_rho, nullptr, nullptr, 0.0f, nullptr, dX_bar,
+                         nullptr, as_stream(stream));
+}
+
+pm_status pm_interp_adj(const float* g, const uint32_t* X, int64_t np, int n, const float* acc_bar, float* g_bar,
+                        float* dX_bar, void* ws, size_t ws_bytes, void* stream) {
+  if (!valid_n(n) || !valid_np(np) || !g || !g_bar || (np > 0 && (!X || !acc_bar || !dX_bar))) return PM_EINVAL;
+  Workspace w;
+  PM_TRY(check_ws(w, ws, ws_bytes, n, np, PM_WS_SORT | PM_WS_ADJ));
+  cudaStream_t s = as_stream(stream);
+  const int64_t N = (int64_t)n * n * n;
+  uint32_t *perm, *skeys;
+  PM_TRY(sort_particles(X, np, n, w, s, &perm, &skeys));
+  PM_TRY(build_cellstart(skeys, np, n, w.cellstart, s));
+  // sorted positions and sorted acc_bar (the three planes permuted like X)
+  PM_TRY(permute_particles(perm, np, X, acc_bar, nullptr, w.Xs, w.adj_abar, nullptr, s));
+  for (int d = 0; d < 3; ++d)
+    PM_TRY(deposit_sorted_values(w.Xs, np, w.cellstart, n, w.adj_abar + d * np, 1.0f, g_bar + d * N, w.partials,
+                                 w.scalars + 12, s));
+  return pos_grad_launch(X, np, n, g, acc_bar, nullptr, 0.0f, nullptr, nullptr, 0.0f, nullptr, dX_bar, nullptr, s);
+}
+
+pm_status pm_gradient_adj(const float* g_bar, float* phi_bar, int n, int order, void* stream) {
+  if (!valid_n(n) || !g_bar || !phi_bar || (order != 3 && order != 5 && order != 7)) return PM_EINVAL;
+  return divergence_launch(g_bar, phi_bar, n, order, as_stream(stream));
+}
+
+pm_status mg_solve_adj(const float* phi_bar, float* f_bar, int n, const mg_params* prm, mg_stats* st, void* ws,
+                       size_t ws_bytes, void* stream) {
+  return mg_solve(phi_bar, f_bar, n, prm, st, ws, ws_bytes, stream);
+}
+
+pm_status pm_step_adj(pm_state* st_, const pm_step_params* prm, const float* X_bar_out, const float* V_bar_out,
+                      float* X_bar_in, float* V_bar_in, void* stream) {
+  if (!st_ || !prm || !X_bar_out || !V_bar_out || !X_bar_in || !V_bar_in) return PM_EINVAL;
+  pm_state& S = *st_;
+  const int n = S.n;
+  const int64_t np = S.np;
+  if (!valid_n(n) || !valid_np(np) || (np > 0 && !S.X) || prm->gravity != PM_GRAVITY_NEWTON) return PM_EINVAL;
+  if (prm->grad_order != 3 && prm->grad_order != 5 && prm->grad_order != 7) return PM_EINVAL;
+  if (!(prm->a > 0.0) || !valid_mg(&prm->mg)) return PM_EINVAL;
+  const uint32_t flags = PM_WS_STEP | PM_WS_ADJ | (S.id ? PM_WS_IDS : 0);
+  Workspace w;
+  PM_TRY(check_ws(w, S.ws, S.ws_bytes, n, np, flags));
+  cudaStream_t s = as_stream(stream);
+  // forward recomputation of the force field at the step's input positions
+  uint32_t *perm, *skeys;
+  PM_TRY(sort_particles(S.X, np, n, w, s, &perm, &skeys));
+  PM_TRY(build_cellstart(skeys, np, n, w.cellstart, s));
+  PM_TRY(permute_particles(perm, np, S.X, nullptr, nullptr, w.Xs, nullptr, nullptr, s));
+  PM_TRY(deposit_sorted(w.Xs, np, w.cellstart, n, w.rho, w.partials, w.scalars, s));
+  mg_params mp = prm->mg;
+  mp.first_guess = MG_GUESS_JACOBI;
+  mp.fixed_cycles = 0;
+  const float src_scale = (float)(1.5 * prm->a * prm->Om);
+  {
+    pm_status r = mg_solve_src(Src{w.rho, src_scale, w.scalars}, w.adj_phi, n, mp, nullptr, w, s);
+    if (r != PM_OK && r != PM_ENOCONV) return r;
+  }
+  PM_TRY(gradient_launch(w.adj_phi, nullptr, 0.0f, w.g, n, prm->grad_order, false, s));
+  // reverse sweep
+  PM_TRY(adj_accel_launch(X_bar_out, V_bar_out, np, (float)prm->dt_kick, (float)prm->dt_drift, w.adj_abar, s));
+  const int64_t N = (int64_t)n * n * n;
+  for (int d = 0; d < 3; ++d)
+    PM_TRY(deposit_sorted_values(w.Xs, np, w.cellstart, n, w.adj_abar + d * np, 1.0f, w.adj_gbar + d * N,
+                                 w.partials, w.scalars + 12, s));
+  PM_TRY(divergence_launch(w.adj_gbar, w.rho, n, prm->grad_order, s));   // phi_bar, in the rho buffer
+  PM_TRY(grid_mean(w.rho, N, w.partials, w.scalars + 13, s));
+  {
+    pm_status r = mg_solve_src(Src{w.rho, 1.0f, w.scalars + 13}, w.adj_psi, n, mp, nullptr, w, s);
+    if (r != PM_OK && r != PM_ENOCONV) return r;
+  }
+  const float s_rho = np > 0 ? (float)((double)src_scale * (double)n * n * n / (double)np) : 0.0f;
+  PM_TRY(pos_grad_launch(w.Xs, np, n, w.g, w.adj_abar, w.adj_psi, s_rho, X_bar_out, V_bar_out, (float)prm->dt_drift,
+                         perm, X_bar_in, V_bar_in, s));
+  return launch_status();
 }
 
 double pm_dt_supercomoving(double Om, double OL, double a0, double a1) {

@@ -17,8 +17,8 @@ namespace {
 template <int T>
 __global__ void __launch_bounds__(T * T * T) k_deposit(const uint32_t* __restrict__ Xs, int64_t np,
                                                        const uint32_t* __restrict__ cellstart, int n,
-                                                       int log2n, float scale, float* __restrict__ rho,
-                                                       double* __restrict__ partial) {
+                                                       int log2n, const float* __restrict__ vals, float scale,
+                                                       float* __restrict__ rho, double* __restrict__ partial) {
   constexpr int E = T + 2, S = E * E * E, NT = T * T * T;
   extern __shared__ float M[];  // [27][S]
   __shared__ double wsum[NT / 32];
@@ -42,6 +42,10 @@ __global__ void __launch_bounds__(T * T * T) k_deposit(const uint32_t* __restric
       tsc_weights(cell_offset(__ldg(Xs + p), log2n), wx);
       tsc_weights(cell_offset(__ldg(Xs + np + p), log2n), wy);
       tsc_weights(cell_offset(__ldg(Xs + 2 * np + p), log2n), wz);
+      if (vals) {
+        const float v = __ldg(vals + p);
+        wx[0] *= v; wx[1] *= v; wx[2] *= v;
+      }
 #pragma unroll
       for (int ox = 0; ox < 3; ++ox)
 #pragma unroll
@@ -94,8 +98,9 @@ static_assert(DEY * DEZ <= DTHREADS, "one source cell per thread");
 
 __global__ void __launch_bounds__(DTHREADS, 1) k_deposit_stream(const uint32_t* __restrict__ Xs, int64_t np,
                                                                 const uint32_t* __restrict__ cellstart, int log2n,
-                                                                int chunk, int nitems, float scale,
-                                                                float* __restrict__ rho, double* __restrict__ partial) {
+                                                                int chunk, int nitems, const float* __restrict__ vals,
+                                                                float scale, float* __restrict__ rho,
+                                                                double* __restrict__ partial) {
   extern __shared__ float sm[];
   float* Mom = sm;                      // [27][DEY * DEZ]
   float* Acc = sm + 27 * DEY * DEZ;     // [3][DNT]
@@ -142,6 +147,10 @@ __global__ void __launch_bounds__(DTHREADS, 1) k_deposit_stream(const uint32_t* 
           tsc_weights(cell_offset(px, log2n), wx);
           tsc_weights(cell_offset(py, log2n), wy);
           tsc_weights(cell_offset(pz, log2n), wz);
+          if (vals) {
+            const float v = __ldg(vals + p);
+            wx[0] *= v; wx[1] *= v; wx[2] *= v;
+          }
 #pragma unroll
           for (int ox = 0; ox < 3; ++ox)
 #pragma unroll
@@ -246,8 +255,8 @@ __global__ void __launch_bounds__(1024) k_reduce_partials(const double* __restri
 }
 
 template <int T>
-pm_status launch_deposit(const uint32_t* Xs, int64_t np, const uint32_t* cellstart, int n,
-                         float* rho, double* partials, double* mean_out, cudaStream_t s) {
+pm_status launch_deposit(const uint32_t* Xs, int64_t np, const uint32_t* cellstart, int n, const float* vals,
+                         float scale, float* rho, double* partials, double* mean_out, cudaStream_t s) {
   constexpr int E = T + 2;
   constexpr size_t smem = sizeof(float) * 27 * E * E * E;
   static bool attr = false;
@@ -258,9 +267,8 @@ pm_status launch_deposit(const uint32_t* Xs, int64_t np, const uint32_t* cellsta
   }
   const int tiles = n / T;
   const int64_t nblocks = (int64_t)tiles * tiles * tiles;
-  const float scale = np > 0 ? (float)((double)n * n * n / (double)np) : 0.0f;
-  PM_LAUNCH(K_DEPOSIT, 12.0 * np + 8.0 * n * n * (double)n + 4.0, k_deposit<T>, (unsigned)nblocks, T * T * T, smem, s, Xs, np, cellstart, n,
-            ilog2(n), scale, rho, partials);
+  PM_LAUNCH(K_DEPOSIT, (vals ? 16.0 : 12.0) * np + 8.0 * n * n * (double)n + 4.0, k_deposit<T>, (unsigned)nblocks,
+            T * T * T, smem, s, Xs, np, cellstart, n, ilog2(n), vals, scale, rho, partials);
   PM_LAUNCH(K_REDUCE, 8.0 * nblocks, k_reduce_partials, 1, 1024, 0, s, partials, nblocks, (int64_t)0, 1,
             1.0 / ((double)n * n * n), mean_out);
   return launch_status();
@@ -277,6 +285,12 @@ int64_t reduce_partials_capacity(int n, int64_t np) {
 
 pm_status deposit_sorted(const uint32_t* Xs, int64_t np, const uint32_t* cellstart, int n,
                          float* rho, double* partials, double* mean_out, cudaStream_t s) {
+  const float scale = np > 0 ? (float)((double)n * n * n / (double)np) : 0.0f;
+  return deposit_sorted_values(Xs, np, cellstart, n, nullptr, scale, rho, partials, mean_out, s);
+}
+
+pm_status deposit_sorted_values(const uint32_t* Xs, int64_t np, const uint32_t* cellstart, int n, const float* vals,
+                                float scale, float* rho, double* partials, double* mean_out, cudaStream_t s) {
   if (n >= 32) {
     static bool attr = false;
     if (!attr) {
@@ -286,16 +300,15 @@ pm_status deposit_sorted(const uint32_t* Xs, int64_t np, const uint32_t* cellsta
     }
     int chunk, nitems;
     deposit_stream_plan(n, &chunk, &nitems);
-    const float scale = np > 0 ? (float)((double)n * n * n / (double)np) : 0.0f;
     const unsigned grid = (unsigned)(nitems < 152 ? nitems : 152);   // one 1024-thread CTA per SM
-    PM_LAUNCH(K_DEPOSIT, 12.0 * np + 8.0 * n * n * (double)n + 4.0, k_deposit_stream, grid, DTHREADS, kDepositStreamSmem,
-              s, Xs, np, cellstart, ilog2(n), chunk, nitems, scale, rho, partials);
+    PM_LAUNCH(K_DEPOSIT, (vals ? 16.0 : 12.0) * np + 8.0 * n * n * (double)n + 4.0, k_deposit_stream, grid, DTHREADS,
+              kDepositStreamSmem, s, Xs, np, cellstart, ilog2(n), chunk, nitems, vals, scale, rho, partials);
     PM_LAUNCH(K_REDUCE, 8.0 * nitems, k_reduce_partials, 1, 1024, 0, s, partials, (int64_t)nitems, (int64_t)0, 1,
               1.0 / ((double)n * n * n), mean_out);
     return launch_status();
   }
-  if (n >= 8) return launch_deposit<8>(Xs, np, cellstart, n, rho, partials, mean_out, s);
-  return launch_deposit<4>(Xs, np, cellstart, n, rho, partials, mean_out, s);
+  if (n >= 8) return launch_deposit<8>(Xs, np, cellstart, n, vals, scale, rho, partials, mean_out, s);
+  return launch_deposit<4>(Xs, np, cellstart, n, vals, scale, rho, partials, mean_out, s);
 }
 
 pm_status grid_mean(const float* f, int64_t count, double* partials, double* mean_out,

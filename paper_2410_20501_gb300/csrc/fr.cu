@@ -310,10 +310,10 @@ pm_status fr_smooth(FR& f, int l, int count) {
     for (int done = 0; done < count;) {
       const int S = (count - done) >= 2 ? 2 : 1;
       if (S == 2)
-        PM_LAUNCH(K_FR_SMOOTH, 12.0 * N, (k_rb_stream<2, FRUpdate>), grid, kStreamThreads, StreamGeom<2>::smem_bytes,
+        PM_LAUNCH(l == 0 ? K_FR_SMOOTH0 : K_FR_SMOOTH, 12.0 * N, (k_rb_stream<2, FRUpdate>), grid, kStreamThreads, StreamGeom<2>::smem_bytes,
                   f.s, f.e[l], f.alt[l], f.b[l], c.log2n, chunk, nitems, 0, upd);
       else
-        PM_LAUNCH(K_FR_SMOOTH, 12.0 * N, (k_rb_stream<1, FRUpdate>), grid, kStreamThreads, StreamGeom<1>::smem_bytes,
+        PM_LAUNCH(l == 0 ? K_FR_SMOOTH0 : K_FR_SMOOTH, 12.0 * N, (k_rb_stream<1, FRUpdate>), grid, kStreamThreads, StreamGeom<1>::smem_bytes,
                   f.s, f.e[l], f.alt[l], f.b[l], c.log2n, chunk, nitems, 0, upd);
       float* t = f.e[l];
       f.e[l] = f.alt[l];
@@ -325,7 +325,7 @@ pm_status fr_smooth(FR& f, int l, int count) {
   const unsigned grid = grid_for(((int64_t)c.n * c.n * c.n) / 2, 256);
   for (int it = 0; it < count; ++it)
     for (int colour = 0; colour < 2; ++colour)
-      PM_LAUNCH(K_FR_SMOOTH, 8.0 * N, k_fr_sweep, grid, 256, 0, f.s, f.e[l], f.b[l], c.log2n, colour, c.beta, c.kappa,
+      PM_LAUNCH(l == 0 ? K_FR_SMOOTH0 : K_FR_SMOOTH, 8.0 * N, k_fr_sweep, grid, 256, 0, f.s, f.e[l], f.b[l], c.log2n, colour, c.beta, c.kappa,
                 c.q);
   return PM_OK;
 }

@@ -322,10 +322,10 @@ pm_status smooth(MG& g, int l, int count, const float* w, bool zero, float scale
       const int z = (done == 0 && zero) ? 1 : 0;
       const unsigned grid = (unsigned)(nitems < 152 * 2 ? nitems : 152 * 2);   // 2 CTAs/SM (shared memory)
       if (S == 2)
-        PM_LAUNCH(K_MG_SMOOTH, (z ? 8.0 : 12.0) * N, (k_rb_stream<2, PoissonUpdate>), grid, kStreamThreads,
+        PM_LAUNCH(l == 0 ? K_MG_SMOOTH0 : K_MG_SMOOTH, (z ? 8.0 : 12.0) * N, (k_rb_stream<2, PoissonUpdate>), grid, kStreamThreads,
                   StreamGeom<2>::smem_bytes, g.s, g.u[l], g.alt[l], g.f[l], log2n, chunk, nitems, z, upd);
       else
-        PM_LAUNCH(K_MG_SMOOTH, (z ? 8.0 : 12.0) * N, (k_rb_stream<1, PoissonUpdate>), grid, kStreamThreads,
+        PM_LAUNCH(l == 0 ? K_MG_SMOOTH0 : K_MG_SMOOTH, (z ? 8.0 : 12.0) * N, (k_rb_stream<1, PoissonUpdate>), grid, kStreamThreads,
                   StreamGeom<1>::smem_bytes, g.s, g.u[l], g.alt[l], g.f[l], log2n, chunk, nitems, z, upd);
       float* t = g.u[l];
       g.u[l] = g.alt[l];
@@ -339,9 +339,9 @@ pm_status smooth(MG& g, int l, int count, const float* w, bool zero, float scale
     PoissonUpdate upd{h2, {w[done], 1.0f}, done == 0 ? scale : 1.0f};
     const int z = (done == 0 && zero) ? 1 : 0;
     const int first = done == 0 ? 1 : 0;
-    PM_LAUNCH(K_MG_SMOOTH, (z ? 4.0 : 8.0) * N, k_rb_sweep, grid, 256, 0, g.s, g.u[l], g.f[l], log2n, 0, upd,
+    PM_LAUNCH(l == 0 ? K_MG_SMOOTH0 : K_MG_SMOOTH, (z ? 4.0 : 8.0) * N, k_rb_sweep, grid, 256, 0, g.s, g.u[l], g.f[l], log2n, 0, upd,
               first, first, z);
-    PM_LAUNCH(K_MG_SMOOTH, 8.0 * N, k_rb_sweep, grid, 256, 0, g.s, g.u[l], g.f[l], log2n, 1, upd, 0, first, z);
+    PM_LAUNCH(l == 0 ? K_MG_SMOOTH0 : K_MG_SMOOTH, 8.0 * N, k_rb_sweep, grid, 256, 0, g.s, g.u[l], g.f[l], log2n, 1, upd, 0, first, z);
   }
   return PM_OK;
 }

@@ -12,9 +12,9 @@ namespace pmgb {
 enum KernelClass {
   K_KEYS, K_SORT_UP, K_SORT_SCAN, K_SORT_DOWN, K_CELLSTART, K_PERMUTE,
   K_DEPOSIT, K_REDUCE,
-  K_MG_GUESS, K_MG_SMOOTH, K_MG_RESTRICT, K_MG_PROLONG, K_MG_COARSE, K_MG_NORM,
-  K_FR_SMOOTH, K_FR_RESTRICT, K_FR_COARSEOP, K_FR_PROLONG, K_FR_COARSE, K_FR_NORM,
-  K_GRADIENT, K_INTERP, K_MISC,
+  K_MG_GUESS, K_MG_SMOOTH0, K_MG_SMOOTH, K_MG_RESTRICT, K_MG_PROLONG, K_MG_COARSE, K_MG_NORM,
+  K_FR_SMOOTH0, K_FR_SMOOTH, K_FR_RESTRICT, K_FR_COARSEOP, K_FR_PROLONG, K_FR_COARSE, K_FR_NORM,
+  K_GRADIENT, K_INTERP, K_ADJOINT, K_MISC,
   K_NCLASS
 };
 
@@ -68,6 +68,8 @@ struct Workspace {
   // multigrid pyramids: level l >= 1 arrays (index 0 unused)
   float* mg_u[12]; float* mg_f[12]; float* mg_alt[12];
   float* fr_e[12]; float* fr_r[12]; float* fr_b[12]; float* fr_alt[12];
+  // adjoint buffers
+  float* adj_abar; float* adj_phi; float* adj_psi; float* adj_gbar;
   int64_t np; int n;
 };
 
@@ -90,6 +92,11 @@ pm_status permute_particles(const uint32_t* perm, int64_t np, const uint32_t* X,
 // rho = (n^3/np) TSC sum over cell-sorted particles; writes sum(rho)/n^3 to *mean_out.
 pm_status deposit_sorted(const uint32_t* Xs, int64_t np, const uint32_t* cellstart, int n,
                          float* rho, double* partials, double* mean_out, cudaStream_t s);
+// General form: rho[c] = scale * sum_p vals[p] W(x_p - x_c) (vals may be NULL
+// for 1); *mean_out = sum(rho)/n^3.
+pm_status deposit_sorted_values(const uint32_t* Xs, int64_t np, const uint32_t* cellstart, int n,
+                                const float* vals, float scale, float* rho, double* partials,
+                                double* mean_out, cudaStream_t s);
 // out[k] = scale * sum_{i < count} partials[k * stride + i] for k < nout (one block).
 pm_status reduce_partials(const double* partials, int64_t count, int64_t stride, int nout,
                           double scale, double* out, cudaStream_t s);
@@ -116,6 +123,15 @@ pm_status gradient_launch(const float* phi, const float* eps, float alpha, float
 pm_status interp_launch(const float* g, const uint32_t* Xs, const float* Vs, const uint32_t* ids_in,
                         int64_t np, int n, float* acc, uint32_t* Xo, float* Vo, uint32_t* ids_out,
                         float dt_kick, float dt_drift, int mode, bool vec4, cudaStream_t s);
+
+// Adjoint pieces (adjoint.cu).
+pm_status divergence_launch(const float* gbar, float* phibar, int n, int order, cudaStream_t s);
+pm_status adj_accel_launch(const float* xbar_out, const float* vbar_out, int64_t np, float dt_kick,
+                           float dt_drift, float* abar, cudaStream_t s);
+pm_status pos_grad_launch(const uint32_t* X, int64_t np, int n, const float* g, const float* abar,
+                          const float* psi, float s_rho, const float* xbar_out, const float* vbar_out,
+                          float dt_drift, const uint32_t* perm, float* xbar_in, float* vbar_in,
+                          cudaStream_t s);
 
 // Copies `count` doubles of device reduction results to host (synchronises).
 pm_status fetch_scalars(const double* dev, double* host, int count, cudaStream_t s);

@@ -224,3 +224,38 @@ def zeldovich_powerlaw_ics(n=32, seed=1, a_ini=0.02, rms_cells=0.2):
     X = to_fixed_point(lattice(n) + psi)
     V = psi * math.sqrt(a_ini)
     return X, V
+
+
+# ------------------------------------------------------ differentiable runs ---
+
+def lpt_amplitude(n, boxsize, Om=0.3, Ob=0.05, h=0.7, ns=0.96, sigma8=0.8):
+    """sqrt(P(k) n^3 / L^3) on the rfft grid [n, n, n//2+1] (float64 numpy),
+    zero at k = 0 and on the Nyquist planes: the factor that turns the FFT of
+    unit white noise into the z = 0 linear density contrast."""
+    pk = linear_power(Om, Ob, h, ns, sigma8)
+    kx, ky, kz, bad = _kgrid(n, "cpu")
+    kmag = torch.sqrt(kx * kx + ky * ky + kz * kz) / boxsize
+    kmag[0, 0, 0] = 1.0
+    amp = np.sqrt(pk(kmag.numpy()) * n ** 3 / boxsize ** 3)
+    amp[0, 0, 0] = 0.0
+    amp[bad.numpy()] = 0.0
+    return amp
+
+
+def lpt_growth(a_ini, Om, OL):
+    """(D(a)/D(1), a^2 E(a) D(a)/D(1) f(a)): the displacement and velocity
+    factors of first-order LPT at a_ini."""
+    D, _, f1, _ = growth([a_ini, 1.0], Om, OL)
+    d_ratio = D[0] / D[1]
+    return d_ratio, a_ini * a_ini * hubble_E(a_ini, Om, OL) * d_ratio * f1[0]
+
+
+def c4_workload(n, boxsize=200.0, Om=0.3, z_ini=20.0, steps=10, noise_seed=4, target_seed=5):
+    """The differentiable-PM workload: unit white noise (seed 4), the target
+    noise (seed 5), the spectrum amplitude, LPT factors and the scale factors
+    of ``steps`` leapfrog steps uniform in a from 1/(1+z_ini) to 1."""
+    a_ini = 1.0 / (1.0 + z_ini)
+    d_ratio, vfac = lpt_growth(a_ini, Om, 1.0 - Om)
+    return {"noise": white_noise(n, noise_seed), "target_noise": white_noise(n, target_seed),
+            "amp": lpt_amplitude(n, boxsize, Om), "d_ratio": d_ratio, "vfac": vfac,
+            "a_steps": list(np.linspace(a_ini, 1.0, steps + 1)), "Om": Om, "OL": 1.0 - Om, "boxsize": boxsize}

@@ -17,7 +17,7 @@ import torch
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_lib", "libpmgb.so")
 
-PM_WS_SORT, PM_WS_MG, PM_WS_FR, PM_WS_STEP, PM_WS_IDS = 1, 2, 4, 8, 16
+PM_WS_SORT, PM_WS_MG, PM_WS_FR, PM_WS_STEP, PM_WS_IDS, PM_WS_ADJ = 1, 2, 4, 8, 16, 32
 MG_GUESS_INPUT, MG_GUESS_JACOBI, MG_GUESS_SCALED = 0, 1, 2
 PM_GRAVITY_NEWTON, PM_GRAVITY_FR = 0, 1
 STATUS = {0: "PM_OK", 1: "PM_EINVAL", 2: "PM_ENOMEM", 3: "PM_ENOCONV", 4: "PM_ENAN", 5: "PM_ETIMEOUT",
@@ -103,6 +103,17 @@ _SIGS = {
     "pm_step_host": (ctypes.c_int, [ctypes.POINTER(pm_state), ctypes.POINTER(pm_step_params),
                                     ctypes.POINTER(pm_stats), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                     ctypes.c_void_p, ctypes.c_void_p]),
+    "pm_deposit_adj": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_void_p,
+                                      ctypes.c_void_p, ctypes.c_void_p]),
+    "pm_interp_adj": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int,
+                                     ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                     ctypes.c_size_t, ctypes.c_void_p]),
+    "pm_gradient_adj": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
+                                       ctypes.c_void_p]),
+    "mg_solve_adj": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(mg_params),
+                                    ctypes.POINTER(mg_stats), ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
+    "pm_step_adj": (ctypes.c_int, [ctypes.POINTER(pm_state), ctypes.POINTER(pm_step_params), ctypes.c_void_p,
+                                   ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "pm_dt_supercomoving": (ctypes.c_double, [ctypes.c_double] * 4),
     "pm_growth_D": (ctypes.c_double, [ctypes.c_double] * 3),
     "pm_launch_count": (ctypes.c_uint64, []),
@@ -247,6 +258,50 @@ def interp(g, X):
     return acc
 
 
+def deposit_adj(X, n, rho_bar):
+    """Position cotangent [3, np] of pm_deposit given rho_bar [n, n, n]."""
+    np_ = X.shape[1]
+    out = torch.empty((3, np_), dtype=torch.float32, device=X.device)
+    _check(lib().pm_deposit_adj(_p(X, torch.int32), np_, n, _p(rho_bar, torch.float32), _p(out), _stream()),
+           "pm_deposit_adj")
+    return out
+
+
+def interp_adj(g, X, acc_bar, ws=None):
+    """(g_bar [3, n, n, n], X cotangent [3, np]) of pm_interp given acc_bar."""
+    n = g.shape[1]
+    np_ = X.shape[1]
+    ws = ws if ws is not None else workspace(n, np_, PM_WS_SORT | PM_WS_ADJ, X.device)
+    g_bar = torch.empty_like(g)
+    dX = torch.empty((3, np_), dtype=torch.float32, device=X.device)
+    _check(lib().pm_interp_adj(_p(g, torch.float32), _p(X, torch.int32), np_, n, _p(acc_bar, torch.float32),
+                               _p(g_bar), _p(dX), _p(ws), ws.numel(), _stream()), "pm_interp_adj")
+    return g_bar, dX
+
+
+def mg_solve_adj(phi_bar, ws=None, **params):
+    """Cotangent of the source of a converged mg_solve given phi_bar: the
+    same solve (the 7-point Laplacian is symmetric), from the Jacobi guess."""
+    n = phi_bar.shape[0]
+    prm = default_mg(**params)
+    prm.first_guess = MG_GUESS_JACOBI
+    f_bar = torch.zeros_like(phi_bar, dtype=torch.float32)
+    ws = ws if ws is not None else workspace(n, 0, PM_WS_MG, phi_bar.device)
+    st = mg_stats()
+    code = lib().mg_solve_adj(_p(phi_bar, torch.float32), _p(f_bar), n, ctypes.byref(prm), ctypes.byref(st),
+                              _p(ws), ws.numel(), _stream())
+    if code not in (0, 3):
+        _check(code, "mg_solve_adj")
+    return f_bar
+
+
+def gradient_adj(g_bar, order=5):
+    n = g_bar.shape[1]
+    phi_bar = torch.empty((n, n, n), dtype=torch.float32, device=g_bar.device)
+    _check(lib().pm_gradient_adj(_p(g_bar, torch.float32), _p(phi_bar), n, order, _stream()), "pm_gradient_adj")
+    return phi_bar
+
+
 def dt_supercomoving(Om, OL, a0, a1):
     return lib().pm_dt_supercomoving(Om, OL, a0, a1)
 
@@ -282,7 +337,7 @@ class Simulation:
     track_ids."""
 
     def __init__(self, X, V, n, Om, OL, boxsize, gravity="newton", fR0=-1e-5, grad_order=5, mg=None, fr=None,
-                 track_ids=False, keep_acc=False, device="cuda"):
+                 track_ids=False, keep_acc=False, adjoint=False, device="cuda"):
         self.n = n
         self.np = X.shape[1]
         self.Om, self.OL, self.boxsize, self.fR0 = Om, OL, boxsize, fR0
@@ -294,7 +349,7 @@ class Simulation:
         self.phi = torch.zeros((n, n, n), dtype=torch.float32, device=device)
         self.eps = torch.zeros((n, n, n), dtype=torch.float32, device=device) if self.gravity else None
         self.acc = torch.empty((3, self.np), dtype=torch.float32, device=device) if keep_acc else None
-        flags = PM_WS_STEP | (PM_WS_IDS if track_ids else 0)
+        flags = PM_WS_STEP | (PM_WS_IDS if track_ids else 0) | (PM_WS_ADJ if adjoint else 0)
         self.ws = workspace(n, self.np, flags, device)
         self.mg = mg if mg is not None else default_mg()
         self.fr = fr if fr is not None else default_fr()
@@ -342,6 +397,17 @@ class Simulation:
             resc = (a * D[i]) / (a_steps[i - 1] * D[i - 1]) if (i > 0 and rescale_potential) else 1.0
             out.append(self.step(a, 0.5 * (prev + cur), cur, resc))
         return out
+
+    def step_adjoint(self, a, dt_kick, dt_drift, X_bar_out, V_bar_out):
+        """Cotangents of this step's inputs (the current self.X, self.V, which
+        are not modified) from the cotangents of its outputs (cell order of
+        pm_step's output).  Needs a workspace built with adjoint=True."""
+        xb = torch.empty((3, self.np), dtype=torch.float32, device=self.X.device)
+        vb = torch.empty_like(xb)
+        prm = self.params(a, dt_kick, dt_drift)
+        _check(lib().pm_step_adj(ctypes.byref(self.state), ctypes.byref(prm), _p(X_bar_out, torch.float32),
+                                 _p(V_bar_out, torch.float32), _p(xb), _p(vb), _stream()), "pm_step_adj")
+        return xb, vb
 
     def positions(self):
         return positions_to_host(self.X)
