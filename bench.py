@@ -213,6 +213,59 @@ def timed_steps(sim, coeffs, first, count, host_buffers=None):
     return start.elapsed_time(end), stats
 
 
+def run_adjoint(n=128, fd_dirs=16, reps=3, eps=1.0):
+    """The differentiable-PM workload: 128^3 white noise (seed 4) -> 1LPT at
+    z = 20 in a 200 Mpc/h box -> 10 fused-kick PM steps to a = 1 -> TSC
+    density; loss = sum (rho - rho_target)^2 with the target the same model
+    from seed 5.  Times the forward pass and the backward pass (pm_step_adj
+    per step, recomputing that step's forces) with CUDA events, and checks the
+    gradient against central differences along ``fd_dirs`` random unit
+    directions (seed 6)."""
+    import torch
+    from paper_2410_20501_gb300 import diffpm, inputs
+    w = inputs.c4_workload(n)
+    steps = diffpm.schedule_coefficients(w["a_steps"], w["Om"], w["OL"])
+    st = diffpm.Stepper(n, n ** 3, w["Om"], w["OL"], w["boxsize"])
+    args = (st, w["amp"], w["d_ratio"], w["vfac"], steps)
+    with torch.no_grad():
+        target = diffpm.forward_model(torch.from_numpy(w["target_noise"]).cuda(), *args).to(torch.float64)
+    noise0 = torch.from_numpy(w["noise"]).cuda()
+    s = torch.cuda.current_stream()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    fwd, bwd = [], []
+    for _ in range(reps + 1):
+        noise = noise0.clone().requires_grad_(True)
+        torch.cuda.synchronize()
+        ev[0].record(s)
+        loss = diffpm.density_loss(noise, target, *args)
+        ev[1].record(s)
+        loss.backward()
+        ev[2].record(s)
+        torch.cuda.synchronize()
+        fwd.append(ev[0].elapsed_time(ev[1]))
+        bwd.append(ev[1].elapsed_time(ev[2]))
+    fwd, bwd = statistics.median(fwd[1:]), statistics.median(bwd[1:])
+    grad = noise.grad.detach()
+    rng = np.random.Generator(np.random.PCG64(6))
+    errs = []
+
+    def L(x):
+        with torch.no_grad():
+            return float(diffpm.density_loss(x, target, *args))
+
+    for _ in range(fd_dirs):
+        u = torch.from_numpy(rng.standard_normal((n, n, n))).cuda()
+        u /= torch.linalg.vector_norm(u)
+        fd = (L(noise0 + eps * u) - L(noise0 - eps * u)) / (2 * eps)
+        an = float((grad * u).sum())
+        errs.append(abs(fd - an) / max(abs(an), 1e-30))
+    return {"workload": f"{n}^3 particles/grid, L=200 Mpc/h, 1LPT z=20 from white noise, 10 PM steps to z=0, "
+                        "density-difference loss", "forward_ms": fwd, "backward_ms": bwd,
+            "adjoint_over_forward": bwd / fwd, "loss": float(loss.detach()),
+            "fd_check": {"directions": fd_dirs, "eps": eps, "median_rel_err": statistics.median(errs) if errs else None,
+                         "max_rel_err": max(errs) if errs else None}}
+
+
 def run_gpu(args):
     import torch
     world, rank, local = dist_env()
@@ -315,6 +368,8 @@ def run_gpu(args):
         "kernels": per_kernel,
         "clocks": fr_res["clocks"],
     }
+    if world == 1 and not args.lean:
+        line["adjoint"] = run_adjoint()
     if world == 1 and not args.no_cpu_baseline and not args.lean:
         cv, secs, sample = oracle_sample(8)
         line["cpu_baseline"] = {"value": cv, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
@@ -387,11 +442,14 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--lean", action="store_true",
                     help="f(R) device-timed steps only (no Newtonian line, e2e or CPU baseline): for profilers")
-    ap.add_argument("--stage", choices=["sort", "deposit", "mg", "fr", "interp"],
+    ap.add_argument("--stage", choices=["sort", "deposit", "mg", "fr", "interp", "adjoint"],
                     help="time one stage alone on synthetic inputs (for profilers)")
     ap.add_argument("--n", type=int, default=256, help="grid size for --stage")
     ap.add_argument("--smoother", type=int, default=1, help="--stage mg/fr: 0 streaming, 1 colour passes")
     args = ap.parse_args()
+    if args.stage == "adjoint":
+        print(json.dumps(run_adjoint(args.n, fd_dirs=args.steps)))
+        return 0
     if args.stage:
         return run_stage(args)
     if args.warmup < 3:

@@ -141,6 +141,9 @@ typedef struct {
   int smoother;           /* 0: streaming red-black kernel (two sweeps per pass
                              over memory) on levels with n >= 128, colour
                              passes below; 1: colour passes everywhere         */
+  float coarse_omega;     /* SOR factor of the coarsest-level sweeps; 0: the
+                             optimal one for that grid, 2/(1 + sqrt(1 - mu^2)),
+                             mu = (2 + cos(2 pi/n))/3 (1.634 at 16^3)          */
 } mg_params;
 
 typedef struct {
@@ -156,13 +159,13 @@ typedef struct {
 /* Default parameters: npre = npost = 2, omega = 1.25, coarsest = 16,
  * coarse_max_sweeps = 200, coarse_drop = 1e-3, max_cycles = 30,
  * fixed_cycles = 0, tol = 1e-7, stall = 0.5, first_guess = MG_GUESS_INPUT,
- * smoother = 1. */
+ * smoother = 1, coarse_omega = 0. */
 void mg_default_params(mg_params* p);
 
 /* Solve the periodic Poisson problem (L(phi) - 6 phi)/h^2 = f - <f>, h = 1/n,
  * with red-black SOR V-cycles (§3.5, §3.6.1): restriction by 8-child average,
  * prolongation 27/9/3/1 over 64, zero initial guess for the coarse error,
- * Jacobi-type sweeps on the coarsest level.  Smoothing and transfers run in
+ * red-black SOR sweeps on the coarsest level (see coarse_drop / coarse_omega).  Smoothing and transfers run in
  * float32; the finest-level residual is evaluated with compensated float32
  * arithmetic and its norm accumulated in float64.
  *   f    [n^3] float32 right-hand side (read; its float64 mean is removed)
@@ -306,15 +309,18 @@ pm_status mg_solve_adj(const float* phi_bar, float* f_bar, int n, const mg_param
  * step's INPUTS; nothing in s is modified).  X_bar_out, V_bar_out are the
  * cotangents of the step's outputs, in the output order of pm_step (cell
  * order); X_bar_in, V_bar_in receive the cotangents of the inputs, in the
- * input order.  The forward force evaluation is recomputed (deposit, Poisson
- * solve to prm->mg.tol from the Jacobi guess, gradient); then a_bar =
+ * input order.  phi_fwd: the potential the forward step used (what pm_step
+ * left in s->phi, [n^3]), kept by the caller; NULL recomputes it here
+ * (deposit and a Poisson solve to prm->mg.tol from the Jacobi guess), which
+ * matches a forward step taken with s->have_prev = 0.  Then a_bar =
  * dt_kick (V_bar' + dt_drift X_bar'), g_bar = deposit of a_bar,
- * phi_bar = -G^T g_bar, rho_bar = 3/2 a Om A^+ phi_bar (a second solve), and
- * X_bar = X_bar' + the interpolation and deposit position terms,
- * V_bar = V_bar' + dt_drift X_bar'.  Workspace: PM_WS_STEP | PM_WS_ADJ
- * (| PM_WS_IDS if s->id).  Newtonian gravity only (PM_EINVAL otherwise). */
-pm_status pm_step_adj(pm_state* s, const pm_step_params* prm, const float* X_bar_out, const float* V_bar_out,
-                      float* X_bar_in, float* V_bar_in, void* stream);
+ * phi_bar = -G^T g_bar, rho_bar = 3/2 a Om A^+ phi_bar (a Poisson solve to
+ * prm->mg.tol from the Jacobi guess), and X_bar = X_bar' + the interpolation
+ * and deposit position terms, V_bar = V_bar' + dt_drift X_bar'.
+ * Workspace: PM_WS_STEP | PM_WS_ADJ (| PM_WS_IDS if s->id).  Newtonian
+ * gravity only (PM_EINVAL otherwise). */
+pm_status pm_step_adj(pm_state* s, const pm_step_params* prm, const float* phi_fwd, const float* X_bar_out,
+                      const float* V_bar_out, float* X_bar_in, float* V_bar_in, void* stream);
 
 /* ------------------------------------------------------ host utilities ---- */
 /* Supercomoving time between a0 and a1 (§3.1): integral of da/(a^3 E(a)),

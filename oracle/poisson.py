@@ -101,17 +101,30 @@ class MGParams:
     max_cycles: int = 60
     coarse_drop: float = 1e-3     # coarsest level: sweep until ||d|| drops by this
     coarse_max_sweeps: int = 200
+    coarse_omega: float = 0.0     # coarsest-level SOR factor; 0: optimal_sor_omega(coarsest)
+
+
+def optimal_sor_omega(n):
+    """Young's optimal SOR factor 2 / (1 + sqrt(1 - mu^2)) for red-black
+    ordering of the periodic 7-point Laplacian on n^3 cells, mu = (2 + cos(2 pi / n)) / 3
+    being the Jacobi iteration's largest eigenvalue below 1 (the constant mode,
+    mu = 1, is absent from a zero-mean problem)."""
+    mu = (2.0 + np.cos(2.0 * np.pi / n)) / 3.0
+    return 2.0 / (1.0 + np.sqrt(1.0 - mu * mu))
 
 
 def coarse_solve(u, f, h, prm):
-    """Coarsest level: red-black SOR sweeps until the level residual has dropped
-    by ``coarse_drop``, its running minimum has not improved by 0.1% for 5
-    sweeps (a plateau: the rounding floor), or ``coarse_max_sweeps`` sweeps (the paper does not state the coarsest-level method; this is the
-    reading used throughout)."""
+    """Coarsest level: red-black SOR sweeps (factor ``coarse_omega``, by default
+    the optimal one for this grid) until the level residual has dropped by
+    ``coarse_drop``, its running minimum has not improved by 0.1% for 5 sweeps
+    (a plateau: the rounding floor), or ``coarse_max_sweeps`` sweeps.  The
+    paper does not state the coarsest-level method; this is the reading used
+    throughout."""
     r0 = best = np.linalg.norm(residual(u, f, h))
     stale = 0
+    omega = prm.coarse_omega if prm.coarse_omega > 0 else optimal_sor_omega(u.shape[0])
     for _ in range(prm.coarse_max_sweeps):
-        rbgs_sweep(u, f, h, prm.omega)
+        rbgs_sweep(u, f, h, omega)
         r = np.linalg.norm(residual(u, f, h))
         if r <= prm.coarse_drop * r0:
             break

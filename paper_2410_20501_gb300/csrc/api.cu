@@ -152,7 +152,7 @@ bool valid_mg(const mg_params* p) {
   return p && p->npre >= 0 && p->npost >= 0 && p->npre + p->npost > 0 && p->coarsest >= 4 &&
          p->coarsest <= 16 && p->coarse_max_sweeps >= 0 && p->max_cycles >= 1 && p->omega > 0.0f &&
          p->omega < 2.0f && p->first_guess >= MG_GUESS_INPUT && p->first_guess <= MG_GUESS_SCALED &&
-         (p->smoother == 0 || p->smoother == 1);
+         (p->smoother == 0 || p->smoother == 1) && p->coarse_omega >= 0.0f && p->coarse_omega < 2.0f;
 }
 
 bool valid_fr(const fr_params* p) {
@@ -217,6 +217,7 @@ void mg_default_params(mg_params* p) {
   p->first_guess = MG_GUESS_INPUT;
   p->guess_scale = 1.0f;
   p->smoother = 1;
+  p->coarse_omega = 0.0f;
 }
 
 void fr_default_params(fr_params* p) {
@@ -413,8 +414,8 @@ pm_status mg_solve_adj(const float* phi_bar, float* f_bar, int n, const mg_param
   return mg_solve(phi_bar, f_bar, n, prm, st, ws, ws_bytes, stream);
 }
 
-pm_status pm_step_adj(pm_state* st_, const pm_step_params* prm, const float* X_bar_out, const float* V_bar_out,
-                      float* X_bar_in, float* V_bar_in, void* stream) {
+pm_status pm_step_adj(pm_state* st_, const pm_step_params* prm, const float* phi_fwd, const float* X_bar_out,
+                      const float* V_bar_out, float* X_bar_in, float* V_bar_in, void* stream) {
   if (!st_ || !prm || !X_bar_out || !V_bar_out || !X_bar_in || !V_bar_in) return PM_EINVAL;
   pm_state& S = *st_;
   const int n = S.n;
@@ -426,21 +427,24 @@ pm_status pm_step_adj(pm_state* st_, const pm_step_params* prm, const float* X_b
   Workspace w;
   PM_TRY(check_ws(w, S.ws, S.ws_bytes, n, np, flags));
   cudaStream_t s = as_stream(stream);
-  // forward recomputation of the force field at the step's input positions
+  // the step's sort (cotangent deposits gather in cell order) and, without
+  // phi_fwd, its force field recomputed at the input positions
   uint32_t *perm, *skeys;
   PM_TRY(sort_particles(S.X, np, n, w, s, &perm, &skeys));
   PM_TRY(build_cellstart(skeys, np, n, w.cellstart, s));
   PM_TRY(permute_particles(perm, np, S.X, nullptr, nullptr, w.Xs, nullptr, nullptr, s));
-  PM_TRY(deposit_sorted(w.Xs, np, w.cellstart, n, w.rho, w.partials, w.scalars, s));
   mg_params mp = prm->mg;
   mp.first_guess = MG_GUESS_JACOBI;
   mp.fixed_cycles = 0;
   const float src_scale = (float)(1.5 * prm->a * prm->Om);
-  {
+  const float* phi = phi_fwd;
+  if (!phi) {
+    PM_TRY(deposit_sorted(w.Xs, np, w.cellstart, n, w.rho, w.partials, w.scalars, s));
     pm_status r = mg_solve_src(Src{w.rho, src_scale, w.scalars}, w.adj_phi, n, mp, nullptr, w, s);
     if (r != PM_OK && r != PM_ENOCONV) return r;
+    phi = w.adj_phi;
   }
-  PM_TRY(gradient_launch(w.adj_phi, nullptr, 0.0f, w.g, n, prm->grad_order, false, s));
+  PM_TRY(gradient_launch(phi, nullptr, 0.0f, w.g, n, prm->grad_order, false, s));
   // reverse sweep
   PM_TRY(adj_accel_launch(X_bar_out, V_bar_out, np, (float)prm->dt_kick, (float)prm->dt_drift, w.adj_abar, s));
   const int64_t N = (int64_t)n * n * n;

@@ -216,61 +216,113 @@ __global__ void k_prolong_correct(float* __restrict__ u, const float* __restrict
   }
 }
 
-// Coarsest level (n <= 16) in one CTA: red-black SOR sweeps until the residual
-// norm dropped by `drop`, its running minimum stalls for 5 sweeps (float32 floor), or
-// `max_sweeps` sweeps.
+// Sum over the block of per-thread compensated pairs (sum, comp), returned to
+// every thread as the same float pair (hi, lo): warp shuffles with error-free
+// additions, then warp 0 over the per-warp pairs, whose result thread 0
+// publishes in scratch[32] (so every thread takes the same decision from it).
+// All threads call it; scratch holds 33 pairs.
+__device__ __forceinline__ float2 block_pair_sum(float sum, float comp, float2* scratch) {
+  float s = sum - comp, c = 0.0f;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float os = __shfl_down_sync(0xffffffffu, s, o), oc = __shfl_down_sync(0xffffffffu, c, o);
+    float t, e;
+    two_sum(s, os, t, e);
+    s = t;
+    c = c + oc + e;
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if (lane == 0) scratch[warp] = make_float2(s, c);
+  __syncthreads();
+  if (warp == 0) {
+    float2 v = lane < nw ? scratch[lane] : make_float2(0.0f, 0.0f);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const float os = __shfl_down_sync(0xffffffffu, v.x, o), oc = __shfl_down_sync(0xffffffffu, v.y, o);
+      float t, e;
+      two_sum(v.x, os, t, e);
+      v.x = t;
+      v.y = v.y + oc + e;
+    }
+    if (lane == 0) scratch[32] = v;
+  }
+  __syncthreads();
+  return scratch[32];
+}
+
+// Coarsest level (n <= 16) in one CTA: red-black SOR sweeps (factor omega)
+// until the residual norm dropped by `drop`, its running minimum stalls for 5
+// sweeps (float32 floor), or `max_sweeps` sweeps.  Thread t owns the cell
+// pairs (2P, 2P+1), P = t, t + blockDim, ... (same i, j; k even and odd), so
+// each colour pass gives every thread one cell per pair.  The residual of a
+// black cell is taken from its own update (its neighbours are red and do not
+// move during the black pass); red residuals are recomputed after it.
 __global__ void __launch_bounds__(1024) k_mg_coarse(float* __restrict__ u, Src f, int log2n, float h2,
                                                     float omega, int max_sweeps, float drop,
                                                     int zero_guess) {
   __shared__ float su[4096], sf[4096];
-  __shared__ double scratch[32];
-  __shared__ double r2;
-  const int n = 1 << log2n, m = n - 1, N = n * n * n;
+  __shared__ float2 scratch[33];
+  const int n = 1 << log2n, m = n - 1, N = n * n * n, npair = N >> 1;
   const float mean = load_mean(f);
+  const float inv_h2 = 1.0f / h2;
   for (int c = threadIdx.x; c < N; c += blockDim.x) {
     su[c] = zero_guess ? 0.0f : u[c];
     sf[c] = src_at(f, c, mean);
   }
   __syncthreads();
-  auto norm2 = [&]() -> double {
+  auto nbsum = [&](int c) -> float {
+    const int k = c & m, j = (c >> log2n) & m, i = c >> (2 * log2n);
+    return su[(((i + 1) & m) << (2 * log2n)) | (j << log2n) | k] +
+           su[(((i - 1) & m) << (2 * log2n)) | (j << log2n) | k] +
+           su[(i << (2 * log2n)) | (((j + 1) & m) << log2n) | k] +
+           su[(i << (2 * log2n)) | (((j - 1) & m) << log2n) | k] +
+           su[(i << (2 * log2n)) | (j << log2n) | ((k + 1) & m)] +
+           su[(i << (2 * log2n)) | (j << log2n) | ((k - 1) & m)];
+  };
+  // the cell of pair P with colour col: k of 2P is even, so its colour is (i + j) & 1
+  auto cell_of = [&](int P, int col) -> int {
+    const int c0 = P << 1;
+    return c0 + ((col ^ ((c0 >> log2n) + (c0 >> (2 * log2n)))) & 1);
+  };
+  float2 r2p;
+  {
     float s = 0.0f, cmp = 0.0f;
     for (int c = threadIdx.x; c < N; c += blockDim.x) {
-      const int k = c & m, j = (c >> log2n) & m, i = c >> (2 * log2n);
-      const float uc = su[c];
-      const float L = (su[(((i + 1) & m) << (2 * log2n)) | (j << log2n) | k] - uc) +
-                      (su[(((i - 1) & m) << (2 * log2n)) | (j << log2n) | k] - uc) +
-                      (su[(i << (2 * log2n)) | (((j + 1) & m) << log2n) | k] - uc) +
-                      (su[(i << (2 * log2n)) | (((j - 1) & m) << log2n) | k] - uc) +
-                      (su[(i << (2 * log2n)) | (j << log2n) | ((k + 1) & m)] - uc) +
-                      (su[(i << (2 * log2n)) | (j << log2n) | ((k - 1) & m)] - uc);
-      const float d = sf[c] - L / h2;
+      const float d = sf[c] - (nbsum(c) - 6.0f * su[c]) * inv_h2;
       kahan_add(s, cmp, d * d);
     }
-    block_sum_to(&r2, s, cmp, scratch);
-    return r2;
-  };
-  double best = norm2();
-  const double target = (double)drop * (double)drop * best;
+    r2p = block_pair_sum(s, cmp, scratch);
+  }
+  float best = r2p.x + r2p.y;
+  const float target = drop * drop * best;
   int stale = 0;
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
-    for (int colour = 0; colour < 2; ++colour) {
-      for (int c = threadIdx.x; c < N; c += blockDim.x) {
-        const int k = c & m, j = (c >> log2n) & m, i = c >> (2 * log2n);
-        if (((i + j + k) & 1) != colour) continue;
-        const float s = su[(((i + 1) & m) << (2 * log2n)) | (j << log2n) | k] +
-                        su[(((i - 1) & m) << (2 * log2n)) | (j << log2n) | k] +
-                        su[(i << (2 * log2n)) | (((j + 1) & m) << log2n) | k] +
-                        su[(i << (2 * log2n)) | (((j - 1) & m) << log2n) | k] +
-                        su[(i << (2 * log2n)) | (j << log2n) | ((k + 1) & m)] +
-                        su[(i << (2 * log2n)) | (j << log2n) | ((k - 1) & m)];
-        const float ugs = (s - h2 * sf[c]) * kSixth;
-        su[c] = (omega == 1.0f) ? ugs : omega * ugs + (1.0f - omega) * su[c];
-      }
-      __syncthreads();
+    for (int P = threadIdx.x; P < npair; P += blockDim.x) {      // red
+      const int c = cell_of(P, 0);
+      const float ugs = (nbsum(c) - h2 * sf[c]) * kSixth;
+      su[c] = (omega == 1.0f) ? ugs : omega * ugs + (1.0f - omega) * su[c];
     }
-    const double r = norm2();
+    __syncthreads();
+    float s = 0.0f, cmp = 0.0f;
+    for (int P = threadIdx.x; P < npair; P += blockDim.x) {      // black, with its residual
+      const int c = cell_of(P, 1);
+      const float nb = nbsum(c);
+      const float ugs = (nb - h2 * sf[c]) * kSixth;
+      const float un = (omega == 1.0f) ? ugs : omega * ugs + (1.0f - omega) * su[c];
+      su[c] = un;
+      const float d = sf[c] - (nb - 6.0f * un) * inv_h2;
+      kahan_add(s, cmp, d * d);
+    }
+    __syncthreads();
+    for (int P = threadIdx.x; P < npair; P += blockDim.x) {      // red residuals
+      const int c = cell_of(P, 0);
+      const float d = sf[c] - (nbsum(c) - 6.0f * su[c]) * inv_h2;
+      kahan_add(s, cmp, d * d);
+    }
+    r2p = block_pair_sum(s, cmp, scratch);
+    const float r = r2p.x + r2p.y;
     if (r <= target) break;
-    if (r < 0.998 * best) {   // squared norms: a 0.1% improvement of the norm
+    if (r < 0.998f * best) {   // squared norms: a 0.1% improvement of the norm
       best = r;
       stale = 0;
     } else if (++stale >= 5) {
@@ -278,6 +330,16 @@ __global__ void __launch_bounds__(1024) k_mg_coarse(float* __restrict__ u, Src f
     }
   }
   for (int c = threadIdx.x; c < N; c += blockDim.x) u[c] = su[c];
+}
+
+// SOR factor of the coarsest level: the caller's, else Young's optimum
+// 2 / (1 + sqrt(1 - mu^2)) for red-black ordering of the periodic 7-point
+// Laplacian on n^3 cells, mu = (2 + cos(2 pi / n)) / 3 the largest Jacobi
+// eigenvalue below 1 (the constant mode is absent from a zero-mean problem).
+float coarse_omega(const mg_params& p, int n) {
+  if (p.coarse_omega > 0.0f) return p.coarse_omega;
+  const double mu = (2.0 + cos(2.0 * M_PI / n)) / 3.0;
+  return (float)(2.0 / (1.0 + sqrt(1.0 - mu * mu)));
 }
 
 struct MG {
@@ -357,8 +419,8 @@ pm_status v_cycle(MG& g, int l, bool zero_guess) {
       const int64_t N = (int64_t)n * n * n;
       PM_LAUNCH(K_MG_GUESS, 8.0 * N, k_scale, grid_for(N, 256), 256, 0, g.s, u, N, g.gscale);
     }
-    PM_LAUNCH(K_MG_COARSE, 12.0 * n * n * n, k_mg_coarse, 1, 1024, 0, g.s, u, g.f[l], log2n, h2, p.omega,
-              p.coarse_max_sweeps, p.coarse_drop, zero_guess ? 1 : 0);
+    PM_LAUNCH(K_MG_COARSE, 12.0 * n * n * n, k_mg_coarse, 1, 1024, 0, g.s, u, g.f[l], log2n, h2,
+              coarse_omega(p, n), p.coarse_max_sweeps, p.coarse_drop, zero_guess ? 1 : 0);
     return PM_OK;
   }
   float w[64];

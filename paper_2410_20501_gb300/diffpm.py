@@ -6,8 +6,12 @@ x = q + D Psi, v~ = a^2 E(a) D f Psi) -> kick-drift-kick PM steps (pm_step)
 -> TSC density -> loss.  The LPT transform is written with torch.fft so autograd follows it;
 each PM step and the final deposit are autograd Functions whose backward calls
 the library's adjoint entry points (pm_step_adj, pm_deposit_adj).  Each step
-keeps only its inputs (positions as uint32 fixed point, velocities) and
-recomputes its force field in the backward pass (per-step checkpointing).
+keeps its inputs (positions as uint32 fixed point, velocities: 24 B per
+particle) and the potential it solved for (4 B per cell), so the backward pass
+re-sorts the particles but solves only the adjoint Poisson problem.  Within a
+forward pass each step's Poisson solve starts from the previous step's
+potential rescaled by a D(a) (the first from the Jacobi guess) and runs to
+the multigrid tolerance.
 
 Positions flow through autograd as float64 box coordinates [3, np]; the step
 converts them to uint32 fixed point (the rounding, 2^-32 of the box, is
@@ -54,27 +58,28 @@ class Stepper:
 
 class _StepFn(torch.autograd.Function):
     @staticmethod
-    def forward(ctx, x, v, stepper, a, dt_kick, dt_drift):
+    def forward(ctx, x, v, stepper, a, dt_kick, dt_drift, rescale, first):
         Xb = to_bits(x.detach())
         Vin = v.detach().to(torch.float32).contiguous()
         stepper.load(Xb, Vin)
-        stepper.sim.state.have_prev = 0          # cold start: forces to tolerance, as the adjoint recomputes
-        stepper.sim.step(a, dt_kick, dt_drift)
-        ctx.save_for_backward(Xb, Vin)
+        if first:
+            stepper.sim.state.have_prev = 0      # Jacobi first guess; later steps start from the last potential
+        stepper.sim.step(a, dt_kick, dt_drift, rescale)
+        ctx.save_for_backward(Xb, Vin, stepper.sim.phi.clone())
         ctx.stepper, ctx.coef = stepper, (a, dt_kick, dt_drift)
         return from_bits(stepper.sim.X.clone()), stepper.sim.V.clone().to(v.dtype)
 
     @staticmethod
     def backward(ctx, gx, gv):
-        Xb, Vin = ctx.saved_tensors
+        Xb, Vin, phi = ctx.saved_tensors
         st = ctx.stepper
         st.load(Xb, Vin)
         a, dtk, dtd = ctx.coef
         gx = torch.zeros((3, st.np), dtype=torch.float32, device=Xb.device) if gx is None else gx
         gv = torch.zeros((3, st.np), dtype=torch.float32, device=Xb.device) if gv is None else gv
         xb, vb = st.sim.step_adjoint(a, dtk, dtd, gx.to(torch.float32).contiguous(),
-                                     gv.to(torch.float32).contiguous())
-        return xb.to(torch.float64), vb.to(gv.dtype), None, None, None, None
+                                     gv.to(torch.float32).contiguous(), phi=phi)
+        return xb.to(torch.float64), vb.to(gv.dtype), None, None, None, None, None, None
 
 
 class _DepositFn(torch.autograd.Function):
@@ -91,8 +96,10 @@ class _DepositFn(torch.autograd.Function):
         return pm.deposit_adj(Xb, ctx.n, grho.to(torch.float32).contiguous()).to(torch.float64), None
 
 
-def pm_step(x, v, stepper, a, dt_kick, dt_drift):
-    return _StepFn.apply(x, v, stepper, a, dt_kick, dt_drift)
+def pm_step(x, v, stepper, a, dt_kick, dt_drift, rescale=1.0, first=True):
+    """One differentiable pm_step.  first: start the Poisson solve from the
+    Jacobi guess; otherwise from the stepper's last potential times rescale."""
+    return _StepFn.apply(x, v, stepper, a, dt_kick, dt_drift, rescale, first)
 
 
 def deposit(x, n):
@@ -117,21 +124,24 @@ def lpt1_from_noise(w, amp, d_ratio, vfac):
 
 
 def schedule_coefficients(a_steps, Om, OL):
-    """(a_i, dt_kick_i, dt_drift_i) of the fused-kick leapfrog through a_steps
-    that ends with the drift to a_steps[-1]: the force at a_i kicks by
-    (dt_{i-1} + dt_i)/2 (dt_{-1} = 0), then the particles drift by dt_i.  The
-    closing half kick at a_steps[-1] changes only velocities and is left out
-    (a density loss does not see it)."""
+    """(a_i, dt_kick_i, dt_drift_i, rescale_i) of the fused-kick leapfrog
+    through a_steps that ends with the drift to a_steps[-1]: the force at a_i
+    kicks by (dt_{i-1} + dt_i)/2 (dt_{-1} = 0), then the particles drift by
+    dt_i; rescale_i = a_i D_i / (a_{i-1} D_{i-1}) scales the previous
+    potential into the first guess.  The closing half kick at a_steps[-1]
+    changes only velocities and is left out (a density loss does not see it)."""
     dts = [pm.dt_supercomoving(Om, OL, a_steps[i], a_steps[i + 1]) for i in range(len(a_steps) - 1)]
-    return [(a_steps[i], 0.5 * ((dts[i - 1] if i > 0 else 0.0) + dts[i]), dts[i]) for i in range(len(dts))]
+    aD = [a * pm.growth_D(Om, OL, a) for a in a_steps]
+    return [(a_steps[i], 0.5 * ((dts[i - 1] if i > 0 else 0.0) + dts[i]), dts[i],
+             aD[i] / aD[i - 1] if i > 0 else 1.0) for i in range(len(dts))]
 
 
 def forward_model(w, stepper, amp, d_ratio, vfac, steps):
-    """White noise -> LPT -> ``steps`` [(a, dt_kick, dt_drift)] -> final TSC
-    density (differentiable in w)."""
+    """White noise -> LPT -> ``steps`` [(a, dt_kick, dt_drift, rescale)] ->
+    final TSC density (differentiable in w)."""
     x, v = lpt1_from_noise(w, amp, d_ratio, vfac)
-    for a, dtk, dtd in steps:
-        x, v = pm_step(x, v, stepper, a, dtk, dtd)
+    for i, (a, dtk, dtd, resc) in enumerate(steps):
+        x, v = pm_step(x, v, stepper, a, dtk, dtd, resc, first=(i == 0))
     return deposit(x, stepper.n)
 
 

@@ -38,7 +38,7 @@ class mg_params(ctypes.Structure):
                 ("coarsest", ctypes.c_int), ("coarse_max_sweeps", ctypes.c_int), ("coarse_drop", ctypes.c_float),
                 ("max_cycles", ctypes.c_int), ("fixed_cycles", ctypes.c_int), ("tol", ctypes.c_double),
                 ("stall", ctypes.c_double), ("first_guess", ctypes.c_int), ("guess_scale", ctypes.c_float),
-                ("smoother", ctypes.c_int)]
+                ("smoother", ctypes.c_int), ("coarse_omega", ctypes.c_float)]
 
 
 class mg_stats(ctypes.Structure):
@@ -113,7 +113,8 @@ _SIGS = {
     "mg_solve_adj": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(mg_params),
                                     ctypes.POINTER(mg_stats), ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
     "pm_step_adj": (ctypes.c_int, [ctypes.POINTER(pm_state), ctypes.POINTER(pm_step_params), ctypes.c_void_p,
-                                   ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+                                   ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                   ctypes.c_void_p]),
     "pm_dt_supercomoving": (ctypes.c_double, [ctypes.c_double] * 4),
     "pm_growth_D": (ctypes.c_double, [ctypes.c_double] * 3),
     "pm_launch_count": (ctypes.c_uint64, []),
@@ -398,14 +399,17 @@ class Simulation:
             out.append(self.step(a, 0.5 * (prev + cur), cur, resc))
         return out
 
-    def step_adjoint(self, a, dt_kick, dt_drift, X_bar_out, V_bar_out):
+    def step_adjoint(self, a, dt_kick, dt_drift, X_bar_out, V_bar_out, phi=None):
         """Cotangents of this step's inputs (the current self.X, self.V, which
         are not modified) from the cotangents of its outputs (cell order of
-        pm_step's output).  Needs a workspace built with adjoint=True."""
+        pm_step's output).  phi: the potential the forward step left in
+        self.phi (None: recomputed, as a cold-started forward step would).
+        Needs a workspace built with adjoint=True."""
         xb = torch.empty((3, self.np), dtype=torch.float32, device=self.X.device)
         vb = torch.empty_like(xb)
         prm = self.params(a, dt_kick, dt_drift)
-        _check(lib().pm_step_adj(ctypes.byref(self.state), ctypes.byref(prm), _p(X_bar_out, torch.float32),
+        _check(lib().pm_step_adj(ctypes.byref(self.state), ctypes.byref(prm),
+                                 None if phi is None else _p(phi, torch.float32), _p(X_bar_out, torch.float32),
                                  _p(V_bar_out, torch.float32), _p(xb), _p(vb), _stream()), "pm_step_adj")
         return xb, vb
 

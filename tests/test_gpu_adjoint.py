@@ -142,15 +142,22 @@ def test_mg_solve_adj_self_adjoint_and_exact(pm):
 
 # ----------------------------------------------------------------- step ---
 
-def step_case(pm, X, V, n, a, Om, OL, boxsize, dtk, dtd, seed, order=5):
+def step_case(pm, X, V, n, a, Om, OL, boxsize, dtk, dtd, seed, order=5, saved_phi=False):
     """GPU and oracle cotangents of one fused-kick step; returns
-    ((xbar_in_gpu, vbar_in_gpu), (xbar_in_ref, vbar_in_ref)) in input order."""
-    sim = pm.Simulation(X, V, n, Om=Om, OL=OL, boxsize=boxsize, grad_order=order, adjoint=True,
-                        mg=pm.default_mg(tol=1e-7))
+    ((xbar_in_gpu, vbar_in_gpu), (xbar_in_ref, vbar_in_ref)) in input order.
+    saved_phi: hand pm_step_adj the potential of a (cold-started) forward
+    step instead of letting it recompute the solve."""
+    mg = pm.default_mg(tol=1e-7)
+    phi = None
+    if saved_phi:
+        fwd = pm.Simulation(X, V, n, Om=Om, OL=OL, boxsize=boxsize, grad_order=order, mg=mg)
+        fwd.step(a, dtk, dtd)
+        phi = fwd.phi.clone()
+    sim = pm.Simulation(X, V, n, Om=Om, OL=OL, boxsize=boxsize, grad_order=order, adjoint=True, mg=mg)
     N = X.shape[1]
     xo32, xo = f32(rng_of(seed).standard_normal((3, N)))
     vo32, vo = f32(rng_of(seed + 1).standard_normal((3, N)))
-    xb, vb = sim.step_adjoint(a, dtk, dtd, torch.from_numpy(xo32).cuda(), torch.from_numpy(vo32).cuda())
+    xb, vb = sim.step_adjoint(a, dtk, dtd, torch.from_numpy(xo32).cuda(), torch.from_numpy(vo32).cuda(), phi=phi)
     # output slot p of the step holds input particle perm[p] (stable cell order)
     perm = mesh.stable_cell_order(X, n)
     xo_in, vo_in = np.empty_like(xo), np.empty_like(vo)
@@ -187,9 +194,19 @@ def test_step_adj_64_lcdm(pm, order):
     assert rel_l2(xb - xo, rx - xo) < 1e-4
 
 
+def test_step_adj_saved_potential_is_bitwise_the_recomputed_one(pm):
+    n = 32
+    X, V = inputs.zeldovich_powerlaw_ics(n, seed=2)
+    dt = cosmology.dt_supercomoving(0.02, 0.03, 1.0, 0.0)
+    (xb1, vb1), _ = step_case(pm, X, V, n, 0.02, 1.0, 0.0, 64.0, dt, dt, 50)
+    (xb2, vb2), _ = step_case(pm, X, V, n, 0.02, 1.0, 0.0, 64.0, dt, dt, 50, saved_phi=True)
+    assert np.array_equal(xb1, xb2) and np.array_equal(vb1, vb2)
+
+
 # ------------------------------------------------------- differentiable ---
 
 def schedule(a_steps, Om, OL):
+    """Oracle-side fused-kick leapfrog coefficients (a_i, (dt_{i-1} + dt_i)/2, dt_i)."""
     dts = [cosmology.dt_supercomoving(a0, a1, Om, OL) for a0, a1 in zip(a_steps[:-1], a_steps[1:])]
     return [(a_steps[i], 0.5 * ((dts[i - 1] if i else 0.0) + dts[i]), dts[i]) for i in range(len(dts))]
 
