@@ -23,7 +23,11 @@
  *  - Every pointer argument is caller-owned DEVICE memory unless the
  *    description says "host".  The library never allocates device memory: work
  *    buffers come from the caller as one workspace of pm_workspace_size() bytes,
- *    aligned to 256 bytes.  Arrays must not alias unless stated.
+ *    aligned to 256 bytes.  Every other device array must start on a 16-byte
+ *    boundary (cudaMalloc and PyTorch allocations start on 256 bytes; a view
+ *    at an odd float offset does not): kernels move grids as float2/float4.
+ *    A misaligned array is an argument error (PM_EINVAL).  Arrays must not
+ *    alias unless stated.
  *  - Work is enqueued asynchronously on `stream` (a cudaStream_t; NULL = the
  *    legacy default stream).  Argument errors are detected synchronously and
  *    nothing is enqueued.  Entry points that test convergence (mg_solve,
@@ -46,7 +50,7 @@ extern "C" {
 typedef int pm_status;
 enum {
   PM_OK = 0,
-  PM_EINVAL = 1,    /* bad size, null pointer or parameter                       */
+  PM_EINVAL = 1,    /* bad size, null or misaligned pointer, or bad parameter    */
   PM_ENOMEM = 2,    /* workspace smaller than pm_workspace_size()                 */
   PM_ENOCONV = 3,   /* solver hit max_cycles without meeting its tolerance        */
   PM_ENAN = 4,      /* a residual norm was not finite                             */
@@ -138,9 +142,12 @@ typedef struct {
                              MG_GUESS_SCALED: guess_scale * phi (the warm start
                              of Eq. rescaming_newtonian_potential)              */
   float guess_scale;
-  int smoother;           /* 0: streaming red-black kernel (two sweeps per pass
-                             over memory) on levels with n >= 128, colour
-                             passes below; 1: colour passes everywhere         */
+  int smoother;           /* 2: one fused red-black sweep per pass over memory
+                             on levels with n >= 128 (bitwise equal to the
+                             colour passes), colour passes below;
+                             1: colour passes (one kernel per colour)
+                             everywhere; 0: two sweeps per pass on levels with
+                             n >= 128 (streaming kernel)                       */
   float coarse_omega;     /* SOR factor of the coarsest-level sweeps; 0: the
                              optimal one for that grid, 2/(1 + sqrt(1 - mu^2)),
                              mu = (2 + cos(2 pi/n))/3 (1.634 at 16^3)          */
@@ -159,7 +166,7 @@ typedef struct {
 /* Default parameters: npre = npost = 2, omega = 1.25, coarsest = 16,
  * coarse_max_sweeps = 200, coarse_drop = 1e-3, max_cycles = 30,
  * fixed_cycles = 0, tol = 1e-7, stall = 0.5, first_guess = MG_GUESS_INPUT,
- * smoother = 1, coarse_omega = 0. */
+ * smoother = 2, coarse_omega = 0. */
 void mg_default_params(mg_params* p);
 
 /* Solve the periodic Poisson problem (L(phi) - 6 phi)/h^2 = f - <f>, h = 1/n,

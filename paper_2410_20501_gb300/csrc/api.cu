@@ -104,7 +104,7 @@ size_t layout_workspace(Workspace* w, void* base, int n, int64_t np, uint32_t fl
     const int nl = n >> l;
     if (nl < 4) break;
     const size_t bytes = (size_t)nl * nl * nl * 4;
-    const bool streamed = nl >= 128;   // levels smoothed by the streaming kernel need a ping-pong partner
+    const bool streamed = nl >= 64;   // levels smoothed out of place (fused or streaming sweeps) need a ping-pong partner
     if (mg) {
       if (l > 0) {
         w->mg_u[l] = (float*)take(bytes);
@@ -138,6 +138,12 @@ cudaStream_t as_stream(void* s) { return (cudaStream_t)s; }
 
 bool aligned(const void* p) { return ((uintptr_t)p & 255) == 0; }
 
+// Device arrays of the caller start on 16-byte boundaries (NULL passes: the
+// null checks are separate).
+bool a16(const void* p) { return ((uintptr_t)p & 15) == 0; }
+template <class... P>
+bool all_a16(const P*... p) { return (a16(p) && ...); }
+
 pm_status check_ws(Workspace& w, void* ws, size_t ws_bytes, int n, int64_t np, uint32_t flags) {
   const size_t need = layout_workspace(nullptr, nullptr, n, np, flags);
   if (!ws || !aligned(ws)) return PM_EINVAL;
@@ -152,13 +158,13 @@ bool valid_mg(const mg_params* p) {
   return p && p->npre >= 0 && p->npost >= 0 && p->npre + p->npost > 0 && p->coarsest >= 4 &&
          p->coarsest <= 16 && p->coarse_max_sweeps >= 0 && p->max_cycles >= 1 && p->omega > 0.0f &&
          p->omega < 2.0f && p->first_guess >= MG_GUESS_INPUT && p->first_guess <= MG_GUESS_SCALED &&
-         (p->smoother == 0 || p->smoother == 1) && p->coarse_omega >= 0.0f && p->coarse_omega < 2.0f;
+         p->smoother >= 0 && p->smoother <= 2 && p->coarse_omega >= 0.0f && p->coarse_omega < 2.0f;
 }
 
 bool valid_fr(const fr_params* p) {
   return p && p->a > 0.0 && p->Om > 0.0 && p->fR0 < 0.0 && p->boxsize > 0.0 && p->npre >= 0 && p->npost >= 0 &&
          p->coarsest >= 4 && p->coarsest <= 16 && p->coarse_max_sweeps >= 0 && (p->cycle == 0 || p->cycle == 1) &&
-         (p->tol > 0.0 ? p->max_cycles >= 1 : p->cycles >= 0) && (p->smoother == 0 || p->smoother == 1);
+         (p->tol > 0.0 ? p->max_cycles >= 1 : p->cycles >= 0) && p->smoother >= 0 && p->smoother <= 2;
 }
 
 // Adaptive Simpson quadrature of da / (a^3 E(a)).
@@ -216,7 +222,7 @@ void mg_default_params(mg_params* p) {
   p->stall = 0.5;
   p->first_guess = MG_GUESS_INPUT;
   p->guess_scale = 1.0f;
-  p->smoother = 1;
+  p->smoother = 2;
   p->coarse_omega = 0.0f;
 }
 
@@ -236,12 +242,12 @@ void fr_default_params(fr_params* p) {
   p->cycles = 1;
   p->tol = 0.0;
   p->max_cycles = 30;
-  p->smoother = 1;
+  p->smoother = 2;
 }
 
 pm_status pm_sort(const uint32_t* X, int64_t np, int n, uint32_t* perm, uint32_t* cellstart, void* ws,
                   size_t ws_bytes, void* stream) {
-  if (!valid_n(n) || !valid_np(np) || (np > 0 && !X)) return PM_EINVAL;
+  if (!valid_n(n) || !valid_np(np) || (np > 0 && !X) || !all_a16(X, perm, cellstart)) return PM_EINVAL;
   Workspace w;
   PM_TRY(check_ws(w, ws, ws_bytes, n, np, PM_WS_SORT));
   cudaStream_t s = as_stream(stream);
@@ -253,7 +259,7 @@ pm_status pm_sort(const uint32_t* X, int64_t np, int n, uint32_t* perm, uint32_t
 }
 
 pm_status pm_deposit(const uint32_t* X, int64_t np, int n, float* rho, void* ws, size_t ws_bytes, void* stream) {
-  if (!valid_n(n) || !valid_np(np) || (np > 0 && !X) || !rho) return PM_EINVAL;
+  if (!valid_n(n) || !valid_np(np) || (np > 0 && !X) || !rho || !all_a16(X, rho)) return PM_EINVAL;
   Workspace w;
   PM_TRY(check_ws(w, ws, ws_bytes, n, np, PM_WS_SORT));
   cudaStream_t s = as_stream(stream);
@@ -267,7 +273,7 @@ pm_status pm_deposit(const uint32_t* X, int64_t np, int n, float* rho, void* ws,
 
 pm_status mg_solve(const float* f, float* phi, int n, const mg_params* prm, mg_stats* st, void* ws,
                    size_t ws_bytes, void* stream) {
-  if (!valid_n(n) || !f || !phi || !valid_mg(prm)) return PM_EINVAL;
+  if (!valid_n(n) || !f || !phi || !valid_mg(prm) || !all_a16(f, phi)) return PM_EINVAL;
   Workspace w;
   PM_TRY(check_ws(w, ws, ws_bytes, n, 0, PM_WS_MG));
   cudaStream_t s = as_stream(stream);
@@ -277,7 +283,7 @@ pm_status mg_solve(const float* f, float* phi, int n, const mg_params* prm, mg_s
 
 pm_status fr_solve(const float* rho, float* eps, int n, const fr_params* prm, mg_stats* st, void* ws,
                    size_t ws_bytes, void* stream) {
-  if (!valid_n(n) || !rho || !eps || !valid_fr(prm)) return PM_EINVAL;
+  if (!valid_n(n) || !rho || !eps || !valid_fr(prm) || !all_a16(rho, eps)) return PM_EINVAL;
   Workspace w;
   PM_TRY(check_ws(w, ws, ws_bytes, n, 0, PM_WS_FR));
   cudaStream_t s = as_stream(stream);
@@ -289,12 +295,12 @@ pm_status fr_solve(const float* rho, float* eps, int n, const fr_params* prm, mg
 }
 
 pm_status pm_gradient(const float* phi, float* g, int n, int order, void* stream) {
-  if (!valid_n(n) || !phi || !g || (order != 3 && order != 5 && order != 7)) return PM_EINVAL;
+  if (!valid_n(n) || !phi || !g || (order != 3 && order != 5 && order != 7) || !all_a16(phi, g)) return PM_EINVAL;
   return gradient_launch(phi, nullptr, 0.0f, g, n, order, false, as_stream(stream));
 }
 
 pm_status pm_interp(const float* g, const uint32_t* X, int64_t np, int n, float* acc, void* stream) {
-  if (!valid_n(n) || !valid_np(np) || !g || (np > 0 && (!X || !acc))) return PM_EINVAL;
+  if (!valid_n(n) || !valid_np(np) || !g || (np > 0 && (!X || !acc)) || !all_a16(g, X, acc)) return PM_EINVAL;
   return interp_launch(g, X, nullptr, nullptr, np, n, acc, nullptr, nullptr, nullptr, 0.0f, 0.0f, 0, false,
                        as_stream(stream));
 }
@@ -305,6 +311,7 @@ pm_status pm_step(pm_state* st_, const pm_step_params* prm, pm_stats* stats, voi
   const int n = S.n;
   const int64_t np = S.np;
   if (!valid_n(n) || !valid_np(np) || (np > 0 && (!S.X || !S.V)) || !S.phi) return PM_EINVAL;
+  if (!all_a16(S.X, S.V, S.id, S.phi, S.eps, S.acc)) return PM_EINVAL;
   if (prm->gravity != PM_GRAVITY_NEWTON && prm->gravity != PM_GRAVITY_FR) return PM_EINVAL;
   if (prm->gravity == PM_GRAVITY_FR && !S.eps) return PM_EINVAL;
   if (prm->grad_order != 3 && prm->grad_order != 5 && prm->grad_order != 7) return PM_EINVAL;
@@ -380,7 +387,8 @@ pm_status pm_step_host(pm_state* st_, const pm_step_params* prm, pm_stats* stats
 }
 
 pm_status pm_deposit_adj(const uint32_t* X, int64_t np, int n, const float* rho_bar, float* dX_bar, void* stream) {
-  if (!valid_n(n) || !valid_np(np) || (np > 0 && (!X || !dX_bar)) || !rho_bar) return PM_EINVAL;
+  if (!valid_n(n) || !valid_np(np) || (np > 0 && (!X || !dX_bar)) || !rho_bar || !all_a16(X, rho_bar, dX_bar))
+    return PM_EINVAL;
   const float s_rho = np > 0 ? (float)((double)n * n * n / (double)np) : 0.0f;
   return pos_grad_launch(X, np, n, nullptr, nullptr, rho_bar, s_rho, nullptr, nullptr, 0.0f, nullptr, dX_bar,
                          nullptr, as_stream(stream));
@@ -389,6 +397,7 @@ pm_status pm_deposit_adj(const uint32_t* X, int64_t np, int n, const float* rho_
 pm_status pm_interp_adj(const float* g, const uint32_t* X, int64_t np, int n, const float* acc_bar, float* g_bar,
                         float* dX_bar, void* ws, size_t ws_bytes, void* stream) {
   if (!valid_n(n) || !valid_np(np) || !g || !g_bar || (np > 0 && (!X || !acc_bar || !dX_bar))) return PM_EINVAL;
+  if (!all_a16(g, X, acc_bar, g_bar, dX_bar)) return PM_EINVAL;
   Workspace w;
   PM_TRY(check_ws(w, ws, ws_bytes, n, np, PM_WS_SORT | PM_WS_ADJ));
   cudaStream_t s = as_stream(stream);
@@ -405,7 +414,8 @@ pm_status pm_interp_adj(const float* g, const uint32_t* X, int64_t np, int n, co
 }
 
 pm_status pm_gradient_adj(const float* g_bar, float* phi_bar, int n, int order, void* stream) {
-  if (!valid_n(n) || !g_bar || !phi_bar || (order != 3 && order != 5 && order != 7)) return PM_EINVAL;
+  if (!valid_n(n) || !g_bar || !phi_bar || (order != 3 && order != 5 && order != 7) || !all_a16(g_bar, phi_bar))
+    return PM_EINVAL;
   return divergence_launch(g_bar, phi_bar, n, order, as_stream(stream));
 }
 
@@ -417,6 +427,8 @@ pm_status mg_solve_adj(const float* phi_bar, float* f_bar, int n, const mg_param
 pm_status pm_step_adj(pm_state* st_, const pm_step_params* prm, const float* phi_fwd, const float* X_bar_out,
                       const float* V_bar_out, float* X_bar_in, float* V_bar_in, void* stream) {
   if (!st_ || !prm || !X_bar_out || !V_bar_out || !X_bar_in || !V_bar_in) return PM_EINVAL;
+  if (!all_a16(phi_fwd, X_bar_out, V_bar_out, X_bar_in, V_bar_in)) return PM_EINVAL;
+  if (!all_a16(st_->X, st_->V, st_->id, st_->phi, st_->eps, st_->acc)) return PM_EINVAL;
   pm_state& S = *st_;
   const int n = S.n;
   const int64_t np = S.np;

@@ -16,6 +16,7 @@
 
 #include "pm_device.cuh"
 #include "pm_internal.cuh"
+#include "rb_fused.cuh"
 #include "rb_stream.cuh"
 
 namespace pmgb {
@@ -294,6 +295,8 @@ pm_status stream_attributes() {
                                             (int)StreamGeom<2>::smem_bytes)));
     PM_TRY(cuda_status(cudaFuncSetAttribute(k_rb_stream<1, FRUpdate>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                             (int)StreamGeom<1>::smem_bytes)));
+    PM_TRY(cuda_status(cudaFuncSetAttribute((k_rb_fused<FRUpdate, 2, 1>), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)kFusedSmem)));
     done = true;
   }
   return PM_OK;
@@ -310,7 +313,7 @@ pm_status fr_smooth(FR& f, int l, int count) {
     for (int done = 0; done < count;) {
       const int S = (count - done) >= 2 ? 2 : 1;
       if (S == 2)
-        PM_LAUNCH(l == 0 ? K_FR_SMOOTH0 : K_FR_SMOOTH, 12.0 * N, (k_rb_stream<2, FRUpdate>), grid, kStreamThreads, StreamGeom<2>::smem_bytes,
+        PM_LAUNCH(l == 0 ? K_FR_SMOOTH0 : K_FR_SMOOTH, 24.0 * N, (k_rb_stream<2, FRUpdate>), grid, kStreamThreads, StreamGeom<2>::smem_bytes,
                   f.s, f.e[l], f.alt[l], f.b[l], c.log2n, chunk, nitems, 0, upd);
       else
         PM_LAUNCH(l == 0 ? K_FR_SMOOTH0 : K_FR_SMOOTH, 12.0 * N, (k_rb_stream<1, FRUpdate>), grid, kStreamThreads, StreamGeom<1>::smem_bytes,
@@ -322,10 +325,23 @@ pm_status fr_smooth(FR& f, int l, int count) {
     }
     return PM_OK;
   }
+  if (f.p->smoother == 2 && fused_ok(c.n) && f.alt[l] && fused_aligned(f.e[l], f.alt[l], f.b[l].p)) {
+    const int chunk = fused_chunk(c.n);
+    const unsigned grid = (unsigned)((c.n / kFusedT) * (c.n / kFusedT) * (c.n / chunk));
+    const FRUpdate upd{c.beta, c.kappa, c.q};
+    for (int it = 0; it < count; ++it) {
+      PM_LAUNCH(l == 0 ? K_FR_SMOOTH0 : K_FR_SMOOTH, 12.0 * N, (k_rb_fused<FRUpdate, 2, 1>), grid, kFusedThreads, kFusedSmem,
+                f.s, f.e[l], f.alt[l], f.b[l], c.log2n, chunk, 0, 0, upd);
+      float* t = f.e[l];
+      f.e[l] = f.alt[l];
+      f.alt[l] = t;
+    }
+    return PM_OK;
+  }
   const unsigned grid = grid_for(((int64_t)c.n * c.n * c.n) / 2, 256);
   for (int it = 0; it < count; ++it)
     for (int colour = 0; colour < 2; ++colour)
-      PM_LAUNCH(l == 0 ? K_FR_SMOOTH0 : K_FR_SMOOTH, 8.0 * N, k_fr_sweep, grid, 256, 0, f.s, f.e[l], f.b[l], c.log2n, colour, c.beta, c.kappa,
+      PM_LAUNCH(l == 0 ? K_FR_SMOOTH0 : K_FR_SMOOTH, 6.0 * N, k_fr_sweep, grid, 256, 0, f.s, f.e[l], f.b[l], c.log2n, colour, c.beta, c.kappa,
                 c.q);
   return PM_OK;
 }

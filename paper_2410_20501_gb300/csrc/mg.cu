@@ -11,6 +11,7 @@
 
 #include "pm_device.cuh"
 #include "pm_internal.cuh"
+#include "rb_fused.cuh"
 #include "rb_stream.cuh"
 
 namespace pmgb {
@@ -362,6 +363,8 @@ pm_status stream_attributes() {
     PM_TRY(cuda_status(cudaFuncSetAttribute(k_rb_stream<1, PoissonUpdate>,
                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
                                             (int)StreamGeom<1>::smem_bytes)));
+    PM_TRY(cuda_status(cudaFuncSetAttribute((k_rb_fused<PoissonUpdate, 2, 2>), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)kFusedSmem)));
     done = true;
   }
   return PM_OK;
@@ -384,7 +387,7 @@ pm_status smooth(MG& g, int l, int count, const float* w, bool zero, float scale
       const int z = (done == 0 && zero) ? 1 : 0;
       const unsigned grid = (unsigned)(nitems < 152 * 2 ? nitems : 152 * 2);   // 2 CTAs/SM (shared memory)
       if (S == 2)
-        PM_LAUNCH(l == 0 ? K_MG_SMOOTH0 : K_MG_SMOOTH, (z ? 8.0 : 12.0) * N, (k_rb_stream<2, PoissonUpdate>), grid, kStreamThreads,
+        PM_LAUNCH(l == 0 ? K_MG_SMOOTH0 : K_MG_SMOOTH, (z ? 20.0 : 24.0) * N, (k_rb_stream<2, PoissonUpdate>), grid, kStreamThreads,
                   StreamGeom<2>::smem_bytes, g.s, g.u[l], g.alt[l], g.f[l], log2n, chunk, nitems, z, upd);
       else
         PM_LAUNCH(l == 0 ? K_MG_SMOOTH0 : K_MG_SMOOTH, (z ? 8.0 : 12.0) * N, (k_rb_stream<1, PoissonUpdate>), grid, kStreamThreads,
@@ -396,14 +399,28 @@ pm_status smooth(MG& g, int l, int count, const float* w, bool zero, float scale
     }
     return PM_OK;
   }
+  if (g.p->smoother == 2 && fused_ok(n) && g.alt[l] && fused_aligned(g.u[l], g.alt[l], g.f[l].p)) {
+    const int chunk = fused_chunk(n);
+    const unsigned grid = (unsigned)((n / kFusedT) * (n / kFusedT) * (n / chunk));
+    for (; done < count; ++done) {
+      PoissonUpdate upd{h2, {w[done], 1.0f}, done == 0 ? scale : 1.0f};
+      const int z = (done == 0 && zero) ? 1 : 0;
+      PM_LAUNCH(l == 0 ? K_MG_SMOOTH0 : K_MG_SMOOTH, (z ? 8.0 : 12.0) * N, (k_rb_fused<PoissonUpdate, 2, 2>), grid,
+                kFusedThreads, kFusedSmem, g.s, g.u[l], g.alt[l], g.f[l], log2n, chunk, z, done == 0 ? 1 : 0, upd);
+      float* t = g.u[l];
+      g.u[l] = g.alt[l];
+      g.alt[l] = t;
+    }
+    return PM_OK;
+  }
   const unsigned grid = grid_for(N / 2, 256);
   for (; done < count; ++done) {
     PoissonUpdate upd{h2, {w[done], 1.0f}, done == 0 ? scale : 1.0f};
     const int z = (done == 0 && zero) ? 1 : 0;
     const int first = done == 0 ? 1 : 0;
-    PM_LAUNCH(l == 0 ? K_MG_SMOOTH0 : K_MG_SMOOTH, (z ? 4.0 : 8.0) * N, k_rb_sweep, grid, 256, 0, g.s, g.u[l], g.f[l], log2n, 0, upd,
+    PM_LAUNCH(l == 0 ? K_MG_SMOOTH0 : K_MG_SMOOTH, (z ? 4.0 : 6.0) * N, k_rb_sweep, grid, 256, 0, g.s, g.u[l], g.f[l], log2n, 0, upd,
               first, first, z);
-    PM_LAUNCH(l == 0 ? K_MG_SMOOTH0 : K_MG_SMOOTH, 8.0 * N, k_rb_sweep, grid, 256, 0, g.s, g.u[l], g.f[l], log2n, 1, upd, 0, first, z);
+    PM_LAUNCH(l == 0 ? K_MG_SMOOTH0 : K_MG_SMOOTH, (z ? 4.0 : 6.0) * N, k_rb_sweep, grid, 256, 0, g.s, g.u[l], g.f[l], log2n, 1, upd, 0, first, z);
   }
   return PM_OK;
 }

@@ -40,7 +40,8 @@ pm_status scratch_address(void** out) {
 using namespace pmgb;
 
 extern "C" pm_status pm_deposit_noalloc(const uint32_t* X, int64_t np, int n, float* rho, void* stream) {
-  if (!valid_n(n) || n > kNoallocMaxN || np < 0 || np > kNoallocMaxNp || (np > 0 && !X) || !rho)
+  if (!valid_n(n) || n > kNoallocMaxN || np < 0 || np > kNoallocMaxNp || (np > 0 && !X) || !rho ||
+      (((uintptr_t)X | (uintptr_t)rho) & 15) != 0)
     return PM_EINVAL;
   const size_t need = layout_workspace(nullptr, nullptr, n, np, PM_WS_SORT);
   if (need > kNoallocBytes) return PM_EINVAL;

@@ -57,6 +57,29 @@ def test_argument_errors_are_synchronous(L):
     assert L.fr_solve(fake, fake, 64, ctypes.byref(fr), None, fake, 1 << 30, None) == 1
 
 
+def test_misaligned_arrays_are_rejected_before_any_launch(L):
+    """Every device array must start on a 16-byte boundary (kernels move grids
+    as float2/float4): a view at an odd float offset is an argument error."""
+    from paper_2410_20501_gb300 import pm
+    ok, odd = ctypes.c_void_p(0x100000), ctypes.c_void_p(0x100004)
+    prm = pm.default_mg()
+    assert L.mg_solve(ok, odd, 64, ctypes.byref(prm), None, ok, 1 << 30, None) == 1
+    assert L.mg_solve(odd, ok, 64, ctypes.byref(prm), None, ok, 1 << 30, None) == 1
+    fr = pm.default_fr()
+    assert L.fr_solve(ok, odd, 64, ctypes.byref(fr), None, ok, 1 << 30, None) == 1
+    assert L.pm_deposit(odd, 10, 8, ok, ok, 1 << 30, None) == 1
+    assert L.pm_sort(ok, 10, 8, odd, ok, ok, 1 << 30, None) == 1
+    assert L.pm_gradient(ok, odd, 16, 5, None) == 1
+    assert L.pm_interp(ok, ok, 10, 16, odd, None) == 1
+    assert L.pm_deposit_adj(ok, 10, 16, ok, odd, None) == 1
+    assert L.pm_gradient_adj(odd, ok, 16, 5, None) == 1
+    assert L.pm_deposit_noalloc(ok, 10, 16, odd, None) == 1
+    st = pm.pm_state(n=16, np=10, X=ok.value, V=odd.value, phi=ok.value, ws=ok.value, ws_bytes=1 << 30)
+    sp = pm.pm_step_params(a=0.5, Om=0.3, OL=0.7, boxsize=16.0, grad_order=5, dt_kick=0.0, dt_drift=0.0,
+                           phi_rescale=1.0, mg=pm.default_mg(), fr=pm.default_fr())
+    assert L.pm_step(ctypes.byref(st), ctypes.byref(sp), None, None) == 1
+
+
 def test_workspace_size_monotone(L):
     from paper_2410_20501_gb300 import pm
     a = pm.workspace_size(32, 32 ** 3, pm.PM_WS_STEP)
