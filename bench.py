@@ -129,9 +129,32 @@ def load_peaks():
     return 6800.0, "fallback"
 
 
+def kernel_digest(relpath, kernel):
+    """Short sha256 of a kernel's definition text (from its __global__ line to
+    the closing brace at column 0)."""
+    import hashlib
+    src = open(os.path.join(ROOT, relpath)).read()
+    i = src.find(kernel + "(")
+    if i < 0:
+        return None
+    start, end = src.rfind("__global__", 0, i), src.find("\n}\n", i)
+    return hashlib.sha256(src[start:end].encode()).hexdigest()[:16]
+
+
 def load_ncu_traffic():
+    """Per timing class: DRAM bytes per launch from an ncu capture, kept only
+    while the captured kernel's source is unchanged (same digest)."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
-    return json.load(open(path)) if os.path.exists(path) else {}
+    if not os.path.exists(path):
+        return {}
+    out = {}
+    for cls, e in json.load(open(path)).items():
+        try:
+            if kernel_digest(e["source"], e["kernel"]) == e["digest"]:
+                out[cls] = e
+        except OSError:
+            pass
+    return out
 
 
 # --------------------------------------------------------------- oracle arm --
@@ -445,7 +468,8 @@ def main():
     ap.add_argument("--stage", choices=["sort", "deposit", "mg", "fr", "interp", "adjoint"],
                     help="time one stage alone on synthetic inputs (for profilers)")
     ap.add_argument("--n", type=int, default=256, help="grid size for --stage")
-    ap.add_argument("--smoother", type=int, default=1, help="--stage mg/fr: 0 streaming, 1 colour passes")
+    ap.add_argument("--smoother", type=int, default=2,
+                    help="--stage mg/fr: 2 fused sweeps, 1 colour passes, 0 two-sweep streaming")
     args = ap.parse_args()
     if args.stage == "adjoint":
         print(json.dumps(run_adjoint(args.n, fd_dirs=args.steps)))
