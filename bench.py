@@ -289,6 +289,42 @@ def run_adjoint(n=128, fd_dirs=16, reps=3, eps=1.0):
                          "max_rel_err": max(errs) if errs else None}}
 
 
+def run_ensemble(n=64, B=64, steps=50):
+    """The ensemble workload: 64 boxes of 64^3 particles on 64^3 grids,
+    L = 128 Mpc/h, Omega_m ~ U[0.25, 0.35], sigma8 ~ U[0.7, 0.9] (PCG64 seed 3),
+    box seeds 1000 + b, 2LPT at z = 30, 50 steps uniform in ln a, stepped
+    together by pm_step_batch (2 fixed V-cycles per warm step, 8 on the first).
+    Times the warm steps eagerly and as CUDA-graph replays."""
+    import torch
+    from paper_2410_20501_gb300 import inputs, pm
+    w = inputs.ensemble_workload(n=n, B=B, steps=steps, device="cuda")
+    s = torch.cuda.current_stream()
+    out = {}
+    for mode in ("eager", "graph"):
+        ens = pm.Ensemble(w["X"], w["V"], n, w["Om"], w["boxsize"], cold_cycles=8)
+        coef = ens.coefficients(w["a_steps"])
+        ens.step(coef[0])
+        ens.step(coef[1])
+        if mode == "graph":
+            ens.capture()
+        last = steps if mode == "graph" else 12
+        torch.cuda.synchronize()
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record(s)
+        for i in range(2, last):
+            if mode == "graph":
+                ens.replay_step(coef[i])
+            else:
+                ens.step(coef[i])
+        t1.record(s)
+        torch.cuda.synchronize()
+        ms = t0.elapsed_time(t1) / (last - 2)
+        out[mode] = {"ms_per_step": ms, "value": B * n ** 3 / (ms / 1e3), "steps_timed": last - 2}
+        del ens
+    return {"workload": f"{B} boxes x {n}^3 particles/grid, L=128 Mpc/h, Om~U[0.25,0.35], s8~U[0.7,0.9], "
+                        "2LPT z=30, 50 steps in ln a", "unit": "particle-steps/s", **out}
+
+
 def run_gpu(args):
     import torch
     world, rank, local = dist_env()
@@ -393,6 +429,7 @@ def run_gpu(args):
     }
     if world == 1 and not args.lean:
         line["adjoint"] = run_adjoint()
+        line["ensemble"] = run_ensemble()
     if world == 1 and not args.no_cpu_baseline and not args.lean:
         cv, secs, sample = oracle_sample(8)
         line["cpu_baseline"] = {"value": cv, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
@@ -465,7 +502,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--lean", action="store_true",
                     help="f(R) device-timed steps only (no Newtonian line, e2e or CPU baseline): for profilers")
-    ap.add_argument("--stage", choices=["sort", "deposit", "mg", "fr", "interp", "adjoint"],
+    ap.add_argument("--stage", choices=["sort", "deposit", "mg", "fr", "interp", "adjoint", "ensemble"],
                     help="time one stage alone on synthetic inputs (for profilers)")
     ap.add_argument("--n", type=int, default=256, help="grid size for --stage")
     ap.add_argument("--smoother", type=int, default=2,
@@ -473,6 +510,9 @@ def main():
     args = ap.parse_args()
     if args.stage == "adjoint":
         print(json.dumps(run_adjoint(args.n, fd_dirs=args.steps)))
+        return 0
+    if args.stage == "ensemble":
+        print(json.dumps(run_ensemble()))
         return 0
     if args.stage:
         return run_stage(args)

@@ -329,6 +329,53 @@ pm_status mg_solve_adj(const float* phi_bar, float* f_bar, int n, const mg_param
 pm_status pm_step_adj(pm_state* s, const pm_step_params* prm, const float* phi_fwd, const float* X_bar_out,
                       const float* V_bar_out, float* X_bar_in, float* V_bar_in, void* stream);
 
+/* ----------------------------------------------------- batched ensembles -- */
+/* B independent boxes of the same size advanced together: the ensembles of
+ * runs with different seeds and cosmologies that the paper's speed is meant
+ * for (§1, §5).  One launch of each kernel serves every box (the box is the
+ * third grid dimension), so small boxes fill the GPU and a step is a few dozen
+ * launches instead of B times as many.  The boxes do not interact: box b
+ * evolves bitwise as it would alone in a batch of one.  Newtonian gravity;
+ * the Poisson solve runs fixed cycle counts and nothing in a step waits on the
+ * host, so a step can be captured in a CUDA graph and replayed (the per-box
+ * coefficients are read from device memory at run time). */
+typedef struct {
+  int n;              /* cells per side of every box (power of two, 32..1024) */
+  int B;              /* boxes (3 log2 n + ceil(log2 B) <= 32)                 */
+  int64_t np_box;     /* particles per box                                      */
+  uint32_t* X;        /* [3][B np_box] positions; box b's particles at
+                         b np_box .. (b+1) np_box - 1 in every plane; in/out
+                         (reordered into cell order within each box)           */
+  float* V;           /* [3][B np_box] velocities (same order), in/out         */
+  float* phi;         /* [B][n^3] potentials, in/out (warm start)              */
+  void* ws;           /* workspace of pm_batch_workspace_size() bytes          */
+  size_t ws_bytes;
+  int have_prev;      /* 0: phi is not yet a potential (Jacobi first guess)    */
+} pm_batch_state;
+
+typedef struct {
+  int grad_order;             /* 3, 5 or 7 (Table 1)                             */
+  const float* src_scale;     /* [B] device: 3/2 a Om of each box (§3.1)         */
+  const float* dt_kick;       /* [B] device: kick interval of each box           */
+  const float* dt_drift;      /* [B] device: drift interval of each box          */
+  const float* phi_rescale;   /* [B] device: warm-start factor of each box
+                                 (a1 D1 / (a0 D0), used when have_prev)          */
+  mg_params mg;               /* fixed_cycles > 0: V-cycles of a warm step       */
+  int cold_cycles;            /* V-cycles of a step with have_prev = 0           */
+} pm_batch_params;
+
+/* Workspace bytes for B boxes of n^3 cells with np_box particles each. */
+pm_status pm_batch_workspace_size(int n, int B, int64_t np_box, size_t* bytes);
+
+/* One fused-kick leapfrog step of every box (pm_step's pipeline, batched):
+ * sort by (box, cell), deposit, per-box source 3/2 a Om_b (rho - <rho>_b),
+ * multigrid with fixed cycles (Jacobi guess, or phi_rescale[b] phi_b when
+ * have_prev), gradient, inverse TSC, kick by dt_kick[b], drift by
+ * dt_drift[b]; then have_prev = 1.  Per-box arrays are read on the device
+ * when the kernels run.  PM_EINVAL for bad sizes, pointers, parameters
+ * (mg.fixed_cycles < 1, cold_cycles < 1, smoother 0 is taken as 2). */
+pm_status pm_step_batch(pm_batch_state* s, const pm_batch_params* prm, void* stream);
+
 /* ------------------------------------------------------ host utilities ---- */
 /* Supercomoving time between a0 and a1 (§3.1): integral of da/(a^3 E(a)),
  * E(a) = sqrt(Om a^-3 + OL).  Host computation, float64. */

@@ -58,15 +58,15 @@ pm_status cuda_status(cudaError_t e) {
   return PM_ECUDA;
 }
 
-size_t layout_workspace(Workspace* w, void* base, int n, int64_t np, uint32_t flags) {
+size_t layout_workspace(Workspace* w, void* base, int n, int64_t np, uint32_t flags, int batch) {
   Workspace tmp;
   if (!w) w = &tmp;
   memset(w, 0, sizeof(*w));
   const bool step = flags & PM_WS_STEP;
   const bool sort = step || (flags & PM_WS_SORT);
   const bool mg = step || (flags & PM_WS_MG);
-  const bool fr = step || (flags & PM_WS_FR);
-  const int64_t N = (int64_t)n * n * n;
+  const bool fr = (step && batch == 1) || (flags & PM_WS_FR);   // batched steps are Newtonian
+  const int64_t N = (int64_t)n * n * n * batch;                  // cells of all boxes
   size_t off = 0;
   char* b = (char*)base;
   auto take = [&](size_t bytes) -> char* {
@@ -98,12 +98,13 @@ size_t layout_workspace(Workspace* w, void* base, int n, int64_t np, uint32_t fl
     w->adj_psi = (float*)take((size_t)N * 4);
     w->adj_gbar = (float*)take((size_t)N * 12);
   }
-  w->partials = (double*)take((size_t)2 * reduce_partials_capacity(n, np) * 8);
+  w->partials = (double*)take((size_t)2 * reduce_partials_capacity(n, np) * 8 * batch);
   w->scalars = (double*)take(64 * 8);
+  w->box_mean = (double*)take((size_t)batch * 8);
   for (int l = 0; l < 12; ++l) {
     const int nl = n >> l;
     if (nl < 4) break;
-    const size_t bytes = (size_t)nl * nl * nl * 4;
+    const size_t bytes = (size_t)nl * nl * nl * 4 * batch;
     const bool streamed = nl >= 64;   // levels smoothed out of place (fused or streaming sweeps) need a ping-pong partner
     if (mg) {
       if (l > 0) {
@@ -125,6 +126,7 @@ size_t layout_workspace(Workspace* w, void* base, int n, int64_t np, uint32_t fl
   w->total = align256(off);
   w->np = np;
   w->n = n;
+  w->batch = batch;
   return w->total;
 }
 
@@ -472,6 +474,56 @@ pm_status pm_step_adj(pm_state* st_, const pm_step_params* prm, const float* phi
   const float s_rho = np > 0 ? (float)((double)src_scale * (double)n * n * n / (double)np) : 0.0f;
   PM_TRY(pos_grad_launch(w.Xs, np, n, w.g, w.adj_abar, w.adj_psi, s_rho, X_bar_out, V_bar_out, (float)prm->dt_drift,
                          perm, X_bar_in, V_bar_in, s));
+  return launch_status();
+}
+
+bool valid_batch(int n, int B, int64_t np_box) {
+  if (!valid_n(n) || n < 32 || B < 1 || np_box < 0) return false;
+  if ((int64_t)B * np_box >= ((int64_t)1 << 31)) return false;
+  const int bbits = B > 1 ? ilog2(2 * (int64_t)B - 1) : 0;
+  return 3 * ilog2(n) + bbits <= 32;
+}
+
+pm_status pm_batch_workspace_size(int n, int B, int64_t np_box, size_t* bytes) {
+  if (!valid_batch(n, B, np_box) || !bytes) return PM_EINVAL;
+  *bytes = layout_workspace(nullptr, nullptr, n, (int64_t)B * np_box, PM_WS_STEP, B);
+  return PM_OK;
+}
+
+pm_status pm_step_batch(pm_batch_state* st_, const pm_batch_params* prm, void* stream) {
+  if (!st_ || !prm) return PM_EINVAL;
+  pm_batch_state& S = *st_;
+  const int n = S.n, B = S.B;
+  const int64_t np_box = S.np_box, np = (int64_t)B * np_box;
+  if (!valid_batch(n, B, np_box) || !S.phi || (np > 0 && (!S.X || !S.V))) return PM_EINVAL;
+  if (!prm->src_scale || !prm->dt_kick || !prm->dt_drift || !prm->phi_rescale) return PM_EINVAL;
+  if (!all_a16(S.X, S.V, S.phi) || !all_a16(prm->src_scale, prm->dt_kick, prm->dt_drift, prm->phi_rescale))
+    return PM_EINVAL;
+  if (prm->grad_order != 3 && prm->grad_order != 5 && prm->grad_order != 7) return PM_EINVAL;
+  if (!valid_mg(&prm->mg) || prm->mg.fixed_cycles < 1 || prm->cold_cycles < 1) return PM_EINVAL;
+  if (!S.ws || !aligned(S.ws)) return PM_EINVAL;
+  if (S.ws_bytes < layout_workspace(nullptr, nullptr, n, np, PM_WS_STEP, B)) return PM_ENOMEM;
+  Workspace w;
+  layout_workspace(&w, S.ws, n, np, PM_WS_STEP, B);
+  cudaStream_t s = as_stream(stream);
+  Batch bt;
+  bt.B = B;
+  bt.np_box = np_box;
+  bt.dt_kick = prm->dt_kick;
+  bt.dt_drift = prm->dt_drift;
+  uint32_t *perm, *skeys;
+  PM_TRY(sort_particles(S.X, np, n, w, s, &perm, &skeys, bt));
+  PM_TRY(build_cellstart(skeys, np, n, w.cellstart, s, B));
+  PM_TRY(permute_particles(perm, np, S.X, S.V, nullptr, w.Xs, w.Vs, nullptr, s));
+  PM_TRY(deposit_sorted_batch(w.Xs, np_box, B, w.cellstart, n, w.rho, w.partials, w.box_mean, s));
+  mg_params mp = prm->mg;
+  if (mp.smoother == 0) mp.smoother = 2;
+  mp.first_guess = S.have_prev ? MG_GUESS_SCALED : MG_GUESS_JACOBI;
+  if (!S.have_prev) mp.fixed_cycles = prm->cold_cycles;
+  PM_TRY(mg_solve_batch(Src{w.rho, 0.0f, w.box_mean, prm->src_scale}, S.phi, n, B, mp, prm->phi_rescale, w, s));
+  PM_TRY(gradient_launch(S.phi, nullptr, 0.0f, w.g, n, prm->grad_order, false, s, B));
+  PM_TRY(interp_launch(w.g, w.Xs, w.Vs, nullptr, np, n, nullptr, S.X, S.V, nullptr, 0.0f, 0.0f, 1, false, s, bt));
+  S.have_prev = 1;
   return launch_status();
 }
 

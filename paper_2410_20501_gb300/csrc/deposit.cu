@@ -102,6 +102,12 @@ __global__ void __launch_bounds__(DTHREADS, 1) k_deposit_stream(const uint32_t* 
                                                                 float scale, float* __restrict__ rho,
                                                                 double* __restrict__ partial) {
   extern __shared__ float sm[];
+  {   // the box of a batched launch: its cell starts (global particle indices), density, partials
+    const int64_t off = (int64_t)blockIdx.z << (3 * log2n);
+    cellstart += off;
+    rho += off;
+    partial += (int64_t)blockIdx.z * nitems;
+  }
   float* Mom = sm;                      // [27][DEY * DEZ]
   float* Acc = sm + 27 * DEY * DEZ;     // [3][DNT]
   __shared__ double wsum[DTHREADS / 32];
@@ -276,6 +282,12 @@ pm_status launch_deposit(const uint32_t* Xs, int64_t np, const uint32_t* cellsta
 
 }  // namespace
 
+int deposit_items(int n) {
+  int chunk, nitems;
+  deposit_stream_plan(n, &chunk, &nitems);
+  return nitems;
+}
+
 int64_t reduce_partials_capacity(int n, int64_t np) {
   (void)np;
   int64_t t = (int64_t)n / 4;
@@ -309,6 +321,30 @@ pm_status deposit_sorted_values(const uint32_t* Xs, int64_t np, const uint32_t* 
   }
   if (n >= 8) return launch_deposit<8>(Xs, np, cellstart, n, vals, scale, rho, partials, mean_out, s);
   return launch_deposit<4>(Xs, np, cellstart, n, vals, scale, rho, partials, mean_out, s);
+}
+
+pm_status deposit_sorted_batch(const uint32_t* Xs, int64_t np_box, int B, const uint32_t* cellstart, int n,
+                               float* rho, double* partials, double* mean_out, cudaStream_t s) {
+  if (n < 32 || B < 1) return PM_EINVAL;
+  static bool attr = false;
+  if (!attr) {
+    PM_TRY(cuda_status(cudaFuncSetAttribute(k_deposit_stream, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)kDepositStreamSmem)));
+    attr = true;
+  }
+  int chunk, nitems;
+  deposit_stream_plan(n, &chunk, &nitems);
+  const float scale = np_box > 0 ? (float)((double)n * n * n / (double)np_box) : 0.0f;
+  // one 1024-thread CTA per SM in all: the boxes share the SMs
+  int gx = (152 + B - 1) / B;
+  if (gx > nitems) gx = nitems;
+  const int64_t np = np_box * B;
+  PM_LAUNCH(K_DEPOSIT, 12.0 * np + 8.0 * n * n * (double)n * B + 4.0, k_deposit_stream, dim3(gx, 1, B), DTHREADS,
+            kDepositStreamSmem, s, Xs, np, cellstart, ilog2(n), chunk, nitems, (const float*)nullptr, scale, rho,
+            partials);
+  PM_LAUNCH(K_REDUCE, 8.0 * nitems * B, k_reduce_partials, 1, 1024, 0, s, partials, (int64_t)nitems,
+            (int64_t)nitems, B, 1.0 / ((double)n * n * n), mean_out);
+  return launch_status();
 }
 
 pm_status grid_mean(const float* f, int64_t count, double* partials, double* mean_out,

@@ -255,6 +255,7 @@ __global__ void __launch_bounds__(1024) k_fr_coarse(float* __restrict__ e, Src b
 // The non-linear Gauss-Seidel update as a functor for the streaming smoother.
 struct FRUpdate {
   float beta, kappa, q;
+  __device__ __forceinline__ FRUpdate box(int) const { return *this; }
   __device__ __forceinline__ float operator()(float old, const float nb[6], float bv, int, bool, bool) const {
     return fr_update(old, nb, bv, beta, kappa, q);
   }

@@ -46,6 +46,9 @@ __global__ void k_gradient(const float* __restrict__ phi, const float* __restric
                            float* __restrict__ g, int log2n, float inv_h) {
   const int m = (1 << log2n) - 1;
   const int64_t total = (int64_t)1 << (3 * log2n);
+  phi += (int64_t)blockIdx.z * total;          // the box of a batched launch
+  if (FR) eps += (int64_t)blockIdx.z * total;
+  g += (int64_t)blockIdx.z * 3 * total;
   for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < total;
        c += (int64_t)gridDim.x * blockDim.x) {
     const int k = (int)(c & m), j = (int)((c >> log2n) & m), i = (int)(c >> (2 * log2n));
@@ -85,6 +88,9 @@ __global__ void __launch_bounds__(GNT) k_gradient_stream(const float* __restrict
   const int tiles_z = n / GTZ, tiles = (n / GTY) * tiles_z;
   const int64_t N = (int64_t)1 << (3 * log2n);
   const int tid = threadIdx.x;
+  phi += (int64_t)blockIdx.z * N;              // the box of a batched launch
+  if (FR) eps += (int64_t)blockIdx.z * N;
+  g += (int64_t)blockIdx.z * (VEC4 ? 4 : 3) * N;
   for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
     const int tile = item % tiles, xc = item / tiles;
     const int y0 = (tile / tiles_z) * GTY, z0 = (tile % tiles_z) * GTZ;
@@ -136,10 +142,18 @@ __global__ void __launch_bounds__(256) k_interp_kdk(const float* __restrict__ g,
                                                     const uint32_t* __restrict__ ids_in, int64_t np, int log2n,
                                                     float* __restrict__ acc, uint32_t* __restrict__ Xo,
                                                     float* __restrict__ Vo, uint32_t* __restrict__ ids_out,
-                                                    float dt_kick, float drift_scale, int mode) {
+                                                    float dt_kick, float drift_scale, int mode, int64_t np_box,
+                                                    const float* __restrict__ dtk_box,
+                                                    const float* __restrict__ dtd_box) {
   const int m = (1 << log2n) - 1, sh = 32 - log2n;
   const int64_t N = (int64_t)1 << (3 * log2n);
-  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < np;
+  // the box of a batched launch: its grid and its particles p0 .. p0 + np_box
+  // (np stays the plane stride of the particle arrays)
+  const int64_t p0 = (int64_t)blockIdx.z * np_box, p1 = p0 + np_box;
+  g += (int64_t)blockIdx.z * (VEC4 ? 4 : 3) * N;
+  if (dtk_box) dt_kick = __ldg(dtk_box + blockIdx.z);
+  if (dtd_box) drift_scale = __ldg(dtd_box + blockIdx.z) * 4294967296.0f;
+  for (int64_t p = p0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < p1;
        p += (int64_t)gridDim.x * blockDim.x) {
     const uint32_t x = __ldg(Xs + p), y = __ldg(Xs + np + p), z = __ldg(Xs + 2 * np + p);
     float wx[3], wy[3], wz[3];
@@ -193,9 +207,10 @@ __global__ void __launch_bounds__(256) k_interp_kdk(const float* __restrict__ g,
 }
 
 template <int ORDER>
-pm_status launch_grad(const float* phi, const float* eps, float alpha, float* g, int n, bool vec4, cudaStream_t s) {
+pm_status launch_grad(const float* phi, const float* eps, float alpha, float* g, int n, bool vec4, cudaStream_t s,
+                      int B) {
   const int64_t N = (int64_t)n * n * n;
-  const double bytes = (eps ? 8.0 : 4.0) * N + (vec4 ? 16.0 : 12.0) * N;
+  const double bytes = ((eps ? 8.0 : 4.0) * N + (vec4 ? 16.0 : 12.0) * N) * B;
   if (n >= 64) {
     constexpr int R = Stencil<ORDER>::R;
     constexpr size_t smem = sizeof(float) * (2 * R + 1) * (GTY + 2 * R) * (GTZ + 2 * R);
@@ -203,7 +218,9 @@ pm_status launch_grad(const float* phi, const float* eps, float alpha, float* g,
     int chunk = n;
     while (chunk > 16 && (int64_t)tiles * (n / chunk) < 8 * 152) chunk >>= 1;
     const int nitems = tiles * (n / chunk);
-    const unsigned grid = (unsigned)(nitems < 152 * 4 ? nitems : 152 * 4);
+    unsigned gx = (unsigned)(nitems < 152 * 4 ? nitems : 152 * 4);
+    if (B > 1) gx = (unsigned)nitems;   // the boxes fill the GPU: one item per CTA
+    const dim3 grid(gx, 1, (unsigned)B);
 #define PM_GRAD_STREAM(FRB, V4)                                                                                    \
   PM_LAUNCH(K_GRADIENT, bytes, (k_gradient_stream<ORDER, FRB, V4>), grid, GNT, smem, s, phi, eps, alpha, g, ilog2(n), \
             (float)n, chunk, nitems)
@@ -216,7 +233,7 @@ pm_status launch_grad(const float* phi, const float* eps, float alpha, float* g,
     return launch_status();
   }
   if (vec4) return PM_EINVAL;
-  const unsigned grid = grid_for(N, 256);
+  const dim3 grid(grid_for(N, 256), 1, (unsigned)B);
   if (eps)
     PM_LAUNCH(K_GRADIENT, bytes, (k_gradient<ORDER, true>), grid, 256, 0, s, phi, eps, alpha, g, ilog2(n), (float)n);
   else
@@ -227,26 +244,28 @@ pm_status launch_grad(const float* phi, const float* eps, float alpha, float* g,
 }  // namespace
 
 pm_status gradient_launch(const float* phi, const float* eps, float alpha, float* g, int n, int order, bool vec4,
-                          cudaStream_t s) {
-  if (order == 3) return launch_grad<3>(phi, eps, alpha, g, n, vec4, s);
-  if (order == 5) return launch_grad<5>(phi, eps, alpha, g, n, vec4, s);
-  if (order == 7) return launch_grad<7>(phi, eps, alpha, g, n, vec4, s);
+                          cudaStream_t s, int batch) {
+  if (order == 3) return launch_grad<3>(phi, eps, alpha, g, n, vec4, s, batch);
+  if (order == 5) return launch_grad<5>(phi, eps, alpha, g, n, vec4, s, batch);
+  if (order == 7) return launch_grad<7>(phi, eps, alpha, g, n, vec4, s, batch);
   return PM_EINVAL;
 }
 
 pm_status interp_launch(const float* g, const uint32_t* Xs, const float* Vs, const uint32_t* ids_in, int64_t np,
                         int n, float* acc, uint32_t* Xo, float* Vo, uint32_t* ids_out, float dt_kick,
-                        float dt_drift, int mode, bool vec4, cudaStream_t s) {
+                        float dt_drift, int mode, bool vec4, cudaStream_t s, const Batch& bt) {
   if (np == 0) return PM_OK;
   const float drift_scale = (float)((double)dt_drift * 4294967296.0);
-  const double bytes = (vec4 ? 16.0 : 12.0) * n * n * (double)n +
+  const double bytes = (vec4 ? 16.0 : 12.0) * n * n * (double)n * bt.B +
                        np * (12.0 + (mode ? 36.0 : 0.0) + (acc ? 12.0 : 0.0) + (ids_out ? 8.0 : 0.0));
+  const int64_t np_box = bt.B > 1 ? bt.np_box : np;
+  const dim3 grid(grid_for(np_box, 256), 1, (unsigned)bt.B);
   if (vec4)
-    PM_LAUNCH(K_INTERP, bytes, k_interp_kdk<true>, grid_for(np, 256), 256, 0, s, g, Xs, Vs, ids_in, np, ilog2(n), acc,
-              Xo, Vo, ids_out, dt_kick, drift_scale, mode);
+    PM_LAUNCH(K_INTERP, bytes, k_interp_kdk<true>, grid, 256, 0, s, g, Xs, Vs, ids_in, np, ilog2(n), acc,
+              Xo, Vo, ids_out, dt_kick, drift_scale, mode, np_box, bt.dt_kick, bt.dt_drift);
   else
-    PM_LAUNCH(K_INTERP, bytes, k_interp_kdk<false>, grid_for(np, 256), 256, 0, s, g, Xs, Vs, ids_in, np, ilog2(n),
-              acc, Xo, Vo, ids_out, dt_kick, drift_scale, mode);
+    PM_LAUNCH(K_INTERP, bytes, k_interp_kdk<false>, grid, 256, 0, s, g, Xs, Vs, ids_in, np, ilog2(n),
+              acc, Xo, Vo, ids_out, dt_kick, drift_scale, mode, np_box, bt.dt_kick, bt.dt_drift);
   return launch_status();
 }
 

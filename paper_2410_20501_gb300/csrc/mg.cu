@@ -54,13 +54,18 @@ __device__ __forceinline__ void load_nb(const float* __restrict__ u, int i, int 
 
 // u = -h^2 f / 6 (Eq. multigrid_initial_guess).
 __global__ void k_jacobi_guess(float* __restrict__ u, Src f, int64_t count, float h2) {
+  u += (int64_t)blockIdx.z * count;
+  f = box_src(f, count);
   const float mean = load_mean(f);
   for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < count;
        c += (int64_t)gridDim.x * blockDim.x)
     u[c] = -h2 * src_at(f, c, mean) * kSixth;
 }
 
-__global__ void k_scale(float* __restrict__ u, int64_t count, float a) {
+// u *= a (per box: ab[box] if ab is set).
+__global__ void k_scale(float* __restrict__ u, int64_t count, float a, const float* __restrict__ ab) {
+  u += (int64_t)blockIdx.z * count;
+  if (ab) a = __ldg(ab + blockIdx.z);
   for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < count;
        c += (int64_t)gridDim.x * blockDim.x)
     u[c] *= a;
@@ -73,6 +78,9 @@ __global__ void k_scale(float* __restrict__ u, int64_t count, float a) {
 __global__ void k_rb_sweep(float* __restrict__ u, Src f, int log2n, int colour, PoissonUpdate upd,
                            int nb_old, int own_old, int zero) {
   const int m = (1 << log2n) - 1, half = log2n - 1;
+  u += (int64_t)blockIdx.z << (3 * log2n);
+  f = box_src(f, (int64_t)1 << (3 * log2n));
+  upd = upd.box(blockIdx.z);
   const float mean = load_mean(f);
   const int64_t total = (int64_t)1 << (3 * log2n - 1);
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
@@ -102,6 +110,9 @@ template <bool COMP>
 __global__ void k_resid_restrict(const float* __restrict__ u, Src f, int log2n, float inv_h2,
                                  float* __restrict__ fc) {
   const int lc = log2n - 1, mc = (1 << lc) - 1;
+  u += (int64_t)blockIdx.z << (3 * log2n);
+  f = box_src(f, (int64_t)1 << (3 * log2n));
+  fc += (int64_t)blockIdx.z << (3 * lc);
   const float mean = load_mean(f);
   const int64_t total = (int64_t)1 << (3 * lc);
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
@@ -172,6 +183,9 @@ __global__ void k_prolong_correct(float* __restrict__ u, const float* __restrict
                                   const float* __restrict__ uc2, int log2n) {
   const int lc = log2n - 1, mc = (1 << lc) - 1;
   const int64_t total = (int64_t)1 << (3 * lc);
+  u += (int64_t)blockIdx.z << (3 * log2n);
+  uc += (int64_t)blockIdx.z * total;
+  if (uc2) uc2 += (int64_t)blockIdx.z * total;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
        t += (int64_t)gridDim.x * blockDim.x) {
     const int K = (int)(t & mc), J = (int)((t >> lc) & mc), I = (int)(t >> (2 * lc));
@@ -264,6 +278,8 @@ __global__ void __launch_bounds__(1024) k_mg_coarse(float* __restrict__ u, Src f
   __shared__ float su[4096], sf[4096];
   __shared__ float2 scratch[33];
   const int n = 1 << log2n, m = n - 1, N = n * n * n, npair = N >> 1;
+  u += (int64_t)blockIdx.z * N;   // one CTA per box
+  f = box_src(f, N);
   const float mean = load_mean(f);
   const float inv_h2 = 1.0f / h2;
   for (int c = threadIdx.x; c < N; c += blockDim.x) {
@@ -352,6 +368,9 @@ struct MG {
   Src f[12];
   bool first_cycle;
   float gscale;
+  int B = 1;                    // boxes of a batched solve (blockIdx.z of every launch)
+  const float* gbox = nullptr;  // per-box warm-start factors (batched MG_GUESS_SCALED)
+  dim3 grid(unsigned gx) const { return dim3(gx, 1, (unsigned)B); }
 };
 
 pm_status stream_attributes() {
@@ -371,14 +390,14 @@ pm_status stream_attributes() {
 }
 
 // `count` smoothing sweeps on level l with SOR factors w[0..count-1].
-// zero: the level's values start at 0; scale: warm-start factor applied to the
-// values present before the first sweep.
-pm_status smooth(MG& g, int l, int count, const float* w, bool zero, float scale) {
+// zero: the level's values start at 0; scale (sbox: per box): warm-start
+// factor applied to the values present before the first sweep.
+pm_status smooth(MG& g, int l, int count, const float* w, bool zero, float scale, const float* sbox = nullptr) {
   const int n = g.n0 >> l, log2n = ilog2(n);
   const float h2 = 1.0f / ((float)n * (float)n);
   const int64_t N = (int64_t)n * n * n;
   int done = 0;
-  if (g.p->smoother == 0 && stream_ok(n) && g.alt[l]) {
+  if (g.p->smoother == 0 && stream_ok(n) && g.alt[l] && g.B == 1) {
     int chunk, nitems;
     stream_plan(n, &chunk, &nitems);
     while (done < count) {
@@ -403,10 +422,11 @@ pm_status smooth(MG& g, int l, int count, const float* w, bool zero, float scale
     const int chunk = fused_chunk(n);
     const unsigned grid = (unsigned)((n / kFusedT) * (n / kFusedT) * (n / chunk));
     for (; done < count; ++done) {
-      PoissonUpdate upd{h2, {w[done], 1.0f}, done == 0 ? scale : 1.0f};
+      PoissonUpdate upd{h2, {w[done], 1.0f}, done == 0 ? scale : 1.0f, done == 0 ? sbox : nullptr};
       const int z = (done == 0 && zero) ? 1 : 0;
-      PM_LAUNCH(l == 0 ? K_MG_SMOOTH0 : K_MG_SMOOTH, (z ? 8.0 : 12.0) * N, (k_rb_fused<PoissonUpdate, 2, 2>), grid,
-                kFusedThreads, kFusedSmem, g.s, g.u[l], g.alt[l], g.f[l], log2n, chunk, z, done == 0 ? 1 : 0, upd);
+      PM_LAUNCH(l == 0 ? K_MG_SMOOTH0 : K_MG_SMOOTH, (z ? 8.0 : 12.0) * N * g.B, (k_rb_fused<PoissonUpdate, 2, 2>),
+                g.grid(grid), kFusedThreads, kFusedSmem, g.s, g.u[l], g.alt[l], g.f[l], log2n, chunk, z,
+                done == 0 ? 1 : 0, upd);
       float* t = g.u[l];
       g.u[l] = g.alt[l];
       g.alt[l] = t;
@@ -415,12 +435,13 @@ pm_status smooth(MG& g, int l, int count, const float* w, bool zero, float scale
   }
   const unsigned grid = grid_for(N / 2, 256);
   for (; done < count; ++done) {
-    PoissonUpdate upd{h2, {w[done], 1.0f}, done == 0 ? scale : 1.0f};
+    PoissonUpdate upd{h2, {w[done], 1.0f}, done == 0 ? scale : 1.0f, done == 0 ? sbox : nullptr};
     const int z = (done == 0 && zero) ? 1 : 0;
     const int first = done == 0 ? 1 : 0;
-    PM_LAUNCH(l == 0 ? K_MG_SMOOTH0 : K_MG_SMOOTH, (z ? 4.0 : 6.0) * N, k_rb_sweep, grid, 256, 0, g.s, g.u[l], g.f[l], log2n, 0, upd,
-              first, first, z);
-    PM_LAUNCH(l == 0 ? K_MG_SMOOTH0 : K_MG_SMOOTH, (z ? 4.0 : 6.0) * N, k_rb_sweep, grid, 256, 0, g.s, g.u[l], g.f[l], log2n, 1, upd, 0, first, z);
+    PM_LAUNCH(l == 0 ? K_MG_SMOOTH0 : K_MG_SMOOTH, (z ? 4.0 : 6.0) * N * g.B, k_rb_sweep, g.grid(grid), 256, 0, g.s,
+              g.u[l], g.f[l], log2n, 0, upd, first, first, z);
+    PM_LAUNCH(l == 0 ? K_MG_SMOOTH0 : K_MG_SMOOTH, (z ? 4.0 : 6.0) * N * g.B, k_rb_sweep, g.grid(grid), 256, 0, g.s,
+              g.u[l], g.f[l], log2n, 1, upd, 0, first, z);
   }
   return PM_OK;
 }
@@ -429,37 +450,39 @@ pm_status v_cycle(MG& g, int l, bool zero_guess) {
   const int n = g.n0 >> l, log2n = ilog2(n);
   const mg_params& p = *g.p;
   const float h2 = 1.0f / ((float)n * (float)n);
-  const bool scaled = (l == 0 && g.first_cycle && g.gscale != 1.0f);
+  const bool scaled = (l == 0 && g.first_cycle && (g.gbox || g.gscale != 1.0f));
+  const float* sbox = scaled ? g.gbox : nullptr;
   if (n <= p.coarsest || n <= 4) {
     float* u = g.u[l];
     if (!zero_guess && scaled) {
       const int64_t N = (int64_t)n * n * n;
-      PM_LAUNCH(K_MG_GUESS, 8.0 * N, k_scale, grid_for(N, 256), 256, 0, g.s, u, N, g.gscale);
+      PM_LAUNCH(K_MG_GUESS, 8.0 * N * g.B, k_scale, g.grid(grid_for(N, 256)), 256, 0, g.s, u, N, g.gscale, sbox);
     }
-    PM_LAUNCH(K_MG_COARSE, 12.0 * n * n * n, k_mg_coarse, 1, 1024, 0, g.s, u, g.f[l], log2n, h2,
+    PM_LAUNCH(K_MG_COARSE, 12.0 * n * n * n * g.B, k_mg_coarse, g.grid(1), 1024, 0, g.s, u, g.f[l], log2n, h2,
               coarse_omega(p, n), p.coarse_max_sweeps, p.coarse_drop, zero_guess ? 1 : 0);
     return PM_OK;
   }
   float w[64];
   if (p.npre == 0) {
     const int64_t N = (int64_t)n * n * n;
-    if (zero_guess) PM_TRY(cuda_status(cudaMemsetAsync(g.u[l], 0, N * sizeof(float), g.s)));
-    else if (scaled) PM_LAUNCH(K_MG_GUESS, 8.0 * N, k_scale, grid_for(N, 256), 256, 0, g.s, g.u[l], N, g.gscale);
+    if (zero_guess) PM_TRY(cuda_status(cudaMemsetAsync(g.u[l], 0, N * g.B * sizeof(float), g.s)));
+    else if (scaled)
+      PM_LAUNCH(K_MG_GUESS, 8.0 * N * g.B, k_scale, g.grid(grid_for(N, 256)), 256, 0, g.s, g.u[l], N, g.gscale, sbox);
   } else {
     for (int si = 0; si < p.npre; ++si) w[si] = si == 0 ? 1.0f : p.omega;
-    PM_TRY(smooth(g, l, p.npre, w, zero_guess, scaled ? g.gscale : 1.0f));
+    PM_TRY(smooth(g, l, p.npre, w, zero_guess, scaled ? g.gscale : 1.0f, sbox));
   }
   const int64_t nc = ((int64_t)n * n * n) / 8;
   const unsigned grid = grid_for(nc, 256);
   if (l == 0)
-    PM_LAUNCH(K_MG_RESTRICT, 68.0 * nc, k_resid_restrict<true>, grid, 256, 0, g.s, g.u[l], g.f[l], log2n,
-              (float)n * (float)n, const_cast<float*>(g.f[l + 1].p));
+    PM_LAUNCH(K_MG_RESTRICT, 68.0 * nc * g.B, k_resid_restrict<true>, g.grid(grid), 256, 0, g.s, g.u[l], g.f[l],
+              log2n, (float)n * (float)n, const_cast<float*>(g.f[l + 1].p));
   else
-    PM_LAUNCH(K_MG_RESTRICT, 68.0 * nc, k_resid_restrict<false>, grid, 256, 0, g.s, g.u[l], g.f[l], log2n,
-              (float)n * (float)n, const_cast<float*>(g.f[l + 1].p));
+    PM_LAUNCH(K_MG_RESTRICT, 68.0 * nc * g.B, k_resid_restrict<false>, g.grid(grid), 256, 0, g.s, g.u[l], g.f[l],
+              log2n, (float)n * (float)n, const_cast<float*>(g.f[l + 1].p));
   PM_TRY(v_cycle(g, l + 1, true));
-  PM_LAUNCH(K_MG_PROLONG, 68.0 * nc, k_prolong_correct, grid_for(nc, 256), 256, 0, g.s, g.u[l], g.u[l + 1],
-            (const float*)nullptr, log2n);
+  PM_LAUNCH(K_MG_PROLONG, 68.0 * nc * g.B, k_prolong_correct, g.grid(grid_for(nc, 256)), 256, 0, g.s, g.u[l],
+            g.u[l + 1], (const float*)nullptr, log2n);
   if (p.npost > 0) {
     for (int si = 0; si < p.npost; ++si) w[si] = si == p.npost - 1 ? 1.0f : p.omega;
     PM_TRY(smooth(g, l, p.npost, w, false, 1.0f));
@@ -484,6 +507,43 @@ pm_status fetch_scalars(const double* dev, double* host, int count, cudaStream_t
   PM_TRY(cuda_status(cudaStreamSynchronize(s)));
   for (int i = 0; i < count; ++i) host[i] = pinned[i];
   return PM_OK;
+}
+
+pm_status mg_solve_batch(Src f, float* phi, int n, int B, const mg_params& prm, const float* gbox, Workspace& w,
+                         cudaStream_t s) {
+  if (B < 1 || prm.fixed_cycles < 1) return PM_EINVAL;
+  MG g;
+  g.n0 = n;
+  g.p = &prm;
+  g.s = s;
+  g.B = B;
+  g.u[0] = phi;
+  g.f[0] = f;
+  for (int l = 0; l < 12; ++l) {
+    if (l > 0) {
+      g.u[l] = w.mg_u[l];
+      g.f[l] = Src{w.mg_f[l], 1.0f, nullptr};
+    }
+    g.alt[l] = w.mg_alt[l];
+  }
+  PM_TRY(stream_attributes());
+  g.first_cycle = true;
+  g.gscale = 1.0f;
+  g.gbox = prm.first_guess == MG_GUESS_SCALED ? gbox : nullptr;
+  const int64_t N = (int64_t)n * n * n;
+  const float h2 = 1.0f / ((float)n * (float)n);
+  if (prm.first_guess == MG_GUESS_JACOBI)
+    PM_LAUNCH(K_MG_GUESS, 8.0 * N * B, k_jacobi_guess, g.grid(grid_for(N, 256)), 256, 0, s, phi, f, N, h2);
+  for (int c = 0; c < prm.fixed_cycles; ++c) {
+    PM_TRY(v_cycle(g, 0, false));
+    g.first_cycle = false;
+    if (g.u[0] != phi) {   // the iterate ended in the ping-pong partner: bring it home
+      PM_TRY(cuda_status(cudaMemcpyAsync(phi, g.u[0], N * B * sizeof(float), cudaMemcpyDeviceToDevice, s)));
+      g.alt[0] = g.u[0];
+      g.u[0] = phi;
+    }
+  }
+  return launch_status();
 }
 
 pm_status mg_solve_src(Src f, float* phi, int n, const mg_params& prm, mg_stats* st, Workspace& w,

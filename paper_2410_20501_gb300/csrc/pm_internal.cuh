@@ -44,12 +44,34 @@ inline unsigned grid_for(int64_t count, int threads, int64_t cap = ((int64_t)1 <
 }
 
 // A level-0 source term  s * (p[i] - mean)  with `mean` read from device
-// memory (float64), or a plain array (s = 1, mean = NULL).
+// memory (float64), or a plain array (s = 1, mean = NULL).  In a batched
+// launch (below) p covers all boxes, mean is per box and sb (if set) holds
+// the per-box s.
 struct Src {
   const float* p;
   float s;
   const double* mean;
+  const float* sb;
 };
+
+// Batched launches: B independent boxes stored back to back (grids
+// [B][n^3], vector grids [B][3][n^3]; particles [3][B * np_box] with box b's
+// particles, in cell order, at b * np_box ...).  Kernels take their box from
+// blockIdx.z; with B = 1 every launch is the single-box one.
+struct Batch {
+  int B = 1;
+  int64_t np_box = 0;                   // particles per box
+  const float* dt_kick = nullptr;       // per-box kick and drift (device, [B])
+  const float* dt_drift = nullptr;
+};
+
+#ifdef __CUDACC__
+// The source of the box of this block (blockIdx.z) on a level of N cells.
+__device__ __forceinline__ Src box_src(const Src& f, int64_t N) {
+  const int b = blockIdx.z;
+  return Src{f.p + (int64_t)b * N, f.sb ? __ldg(f.sb + b) : f.s, f.mean ? f.mean + b : nullptr, nullptr};
+}
+#endif
 
 // ------------------------------------------------------------ workspace --
 // Byte offsets of every buffer inside the caller's workspace.
@@ -70,22 +92,29 @@ struct Workspace {
   float* fr_e[12]; float* fr_r[12]; float* fr_b[12]; float* fr_alt[12];
   // adjoint buffers
   float* adj_abar; float* adj_phi; float* adj_psi; float* adj_gbar;
-  int64_t np; int n;
+  double* box_mean;   // per-box mean density of a batch
+  int64_t np; int n; int batch;
 };
 
-// Computes the layout for (n, np, flags); with base == NULL only sizes.
-size_t layout_workspace(Workspace* w, void* base, int n, int64_t np, uint32_t flags);
+// Computes the layout for (n, np, flags) and `batch` boxes of n^3 cells (np
+// counts the particles of all boxes); with base == NULL only sizes.
+size_t layout_workspace(Workspace* w, void* base, int n, int64_t np, uint32_t flags, int batch = 1);
 
 // Sizes of the scratch pieces.
 int64_t radix_tiles(int64_t np);
 int64_t radix_scan_blocks(int64_t np);
 int64_t reduce_partials_capacity(int n, int64_t np);
+// Work items of the streaming deposit for one box of n^3 cells (n >= 32).
+int deposit_items(int n);
 
 // ------------------------------------------------------ stage launchers --
+// Stable sort by cell key; with a batch the key is prefixed by the box
+// (particle index / np_box), so the order is by box, then cell.
 pm_status sort_particles(const uint32_t* X, int64_t np, int n, Workspace& w,
-                         cudaStream_t s, uint32_t** perm_out, uint32_t** skeys_out);
+                         cudaStream_t s, uint32_t** perm_out, uint32_t** skeys_out,
+                         const Batch& bt = Batch{});
 pm_status build_cellstart(const uint32_t* skeys, int64_t np, int n, uint32_t* cellstart,
-                          cudaStream_t s);
+                          cudaStream_t s, int batch = 1);
 pm_status permute_particles(const uint32_t* perm, int64_t np, const uint32_t* X, const float* V,
                             const uint32_t* id, uint32_t* Xs, float* Vs, uint32_t* ids,
                             cudaStream_t s);
@@ -97,6 +126,10 @@ pm_status deposit_sorted(const uint32_t* Xs, int64_t np, const uint32_t* cellsta
 pm_status deposit_sorted_values(const uint32_t* Xs, int64_t np, const uint32_t* cellstart, int n,
                                 const float* vals, float scale, float* rho, double* partials,
                                 double* mean_out, cudaStream_t s);
+// Batched deposit (n >= 32): box b's density [n^3] from its particles (the
+// cell starts cover all boxes); mean_out[b] = box b's mean.
+pm_status deposit_sorted_batch(const uint32_t* Xs, int64_t np_box, int B, const uint32_t* cellstart, int n,
+                               float* rho, double* partials, double* mean_out, cudaStream_t s);
 // out[k] = scale * sum_{i < count} partials[k * stride + i] for k < nout (one block).
 pm_status reduce_partials(const double* partials, int64_t count, int64_t stride, int nout,
                           double scale, double* out, cudaStream_t s);
@@ -106,6 +139,10 @@ pm_status grid_mean(const float* f, int64_t count, double* partials, double* mea
 
 pm_status mg_solve_src(Src f, float* phi, int n, const mg_params& prm, mg_stats* st,
                        Workspace& w, cudaStream_t s);
+// Batched multigrid: fixed cycles only (prm.fixed_cycles > 0); the warm start
+// MG_GUESS_SCALED takes the per-box factors gbox [B] (device).
+pm_status mg_solve_batch(Src f, float* phi, int n, int B, const mg_params& prm, const float* gbox,
+                         Workspace& w, cudaStream_t s);
 pm_status fr_solve_src(Src b, float* eps, int n, const fr_params& prm, mg_stats* st,
                        Workspace& w, cudaStream_t s);
 // u_fine += P(uc - uc2) (27/9/3/1 prolongation; uc2 may be NULL).
@@ -117,12 +154,13 @@ void fr_background(const fr_params& p, double* fbar, double* kappa, double* c2);
 // g = -grad(phi [+ alpha (2 eps + eps^2)]); vec4: g interleaved as float4
 // (gx, gy, gz, 0) per cell (n >= 64 only), else three planes.
 pm_status gradient_launch(const float* phi, const float* eps, float alpha, float* g, int n,
-                          int order, bool vec4, cudaStream_t s);
+                          int order, bool vec4, cudaStream_t s, int batch = 1);
 // mode 0: acc only; mode 1: kick + drift into Xo/Vo (and acc if non-NULL);
 // vec4: g interleaved as float4.
 pm_status interp_launch(const float* g, const uint32_t* Xs, const float* Vs, const uint32_t* ids_in,
                         int64_t np, int n, float* acc, uint32_t* Xo, float* Vo, uint32_t* ids_out,
-                        float dt_kick, float dt_drift, int mode, bool vec4, cudaStream_t s);
+                        float dt_kick, float dt_drift, int mode, bool vec4, cudaStream_t s,
+                        const Batch& bt = Batch{});
 
 // Adjoint pieces (adjoint.cu).
 pm_status divergence_launch(const float* gbar, float* phibar, int n, int order, cudaStream_t s);

@@ -54,6 +54,13 @@ __global__ void __launch_bounds__(kFusedThreads, MINB) k_rb_fused(const float* _
   const int n = 1 << log2n, m = n - 1;
   const int tiles_z = n / T, tiles = (n / T) * tiles_z;
   const int item = blockIdx.x;
+  {   // the box of a batched launch
+    const int64_t off = (int64_t)blockIdx.z << (3 * log2n);
+    uin += off;
+    uout += off;
+    f = box_src(f, (int64_t)1 << (3 * log2n));
+    upd = upd.box(blockIdx.z);
+  }
   const int tile = item % tiles, xc = item / tiles;
   const int y0 = (tile / tiles_z) * T, z0 = (tile % tiles_z) * T;
   const int x0 = xc * chunk, x1 = x0 + chunk;

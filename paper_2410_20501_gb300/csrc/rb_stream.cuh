@@ -58,6 +58,12 @@ struct PoissonUpdate {
   float h2;
   float omega[2];
   float gscale;     // warm-start rescale applied to never-updated values
+  const float* gbox = nullptr;   // per-box gscale of a batched launch (replaces gscale)
+  __device__ __forceinline__ PoissonUpdate box(int b) const {
+    PoissonUpdate u = *this;
+    if (gbox) u.gscale = __ldg(gbox + b);
+    return u;
+  }
   // Explicit rounding intrinsics (no contraction) so that the fused and the
   // colour-by-colour kernels produce bitwise identical updates.
   __device__ __forceinline__ float operator()(float old, const float nb[6], float fv, int sweep,

@@ -20,7 +20,9 @@ constexpr int RMAXBINS = 512;       // at most 9 bits per digit
 constexpr int SCAN_T = 1024;
 constexpr int SCAN_CHUNK = 4 * SCAN_T;
 
-__global__ void k_cell_keys(const uint32_t* __restrict__ X, int64_t np, int log2n,
+// key = (i n + j) n + k of the cell holding each particle; with np_box > 0
+// (a batch of boxes) prefixed by the box, i / np_box.
+__global__ void k_cell_keys(const uint32_t* __restrict__ X, int64_t np, int log2n, int64_t np_box,
                             uint32_t* __restrict__ keys) {
   const int sh = 32 - log2n;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < np;
@@ -28,7 +30,9 @@ __global__ void k_cell_keys(const uint32_t* __restrict__ X, int64_t np, int log2
     uint32_t ix = __ldg(X + i) >> sh;
     uint32_t iy = __ldg(X + np + i) >> sh;
     uint32_t iz = __ldg(X + 2 * np + i) >> sh;
-    keys[i] = (((ix << log2n) | iy) << log2n) | iz;
+    uint32_t key = (((ix << log2n) | iy) << log2n) | iz;
+    if (np_box > 0) key |= (uint32_t)(i / np_box) << (3 * log2n);
+    keys[i] = key;
   }
 }
 
@@ -289,7 +293,7 @@ int64_t radix_scan_blocks(int64_t np) {
 }
 
 pm_status sort_particles(const uint32_t* X, int64_t np, int n, Workspace& w, cudaStream_t s,
-                         uint32_t** perm_out, uint32_t** skeys_out) {
+                         uint32_t** perm_out, uint32_t** skeys_out, const Batch& bt) {
   static bool attr_done = false;
   if (!attr_done) {
     PM_TRY(cuda_status(cudaFuncSetAttribute(k_radix_down, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -300,8 +304,9 @@ pm_status sort_particles(const uint32_t* X, int64_t np, int n, Workspace& w, cud
   *perm_out = w.vals_a;
   *skeys_out = w.keys_a;
   if (np == 0) return PM_OK;
-  PM_LAUNCH(K_KEYS, 16.0 * np, k_cell_keys, grid_for(np, 256), 256, 0, s, X, np, log2n, w.keys_a);
-  const int keybits = 3 * log2n;
+  const int64_t np_box = bt.B > 1 ? bt.np_box : 0;
+  PM_LAUNCH(K_KEYS, 16.0 * np, k_cell_keys, grid_for(np, 256), 256, 0, s, X, np, log2n, np_box, w.keys_a);
+  const int keybits = 3 * log2n + (bt.B > 1 ? ilog2(2 * bt.B - 1) : 0);   // + ceil(log2 B) box bits
   const int passes = (keybits + 8) / 9;
   const int bpp = (keybits + passes - 1) / passes;
   const int64_t ntiles = radix_tiles(np);
@@ -325,8 +330,8 @@ pm_status sort_particles(const uint32_t* X, int64_t np, int n, Workspace& w, cud
 }
 
 pm_status build_cellstart(const uint32_t* skeys, int64_t np, int n, uint32_t* cellstart,
-                          cudaStream_t s) {
-  const uint32_t ncells = (uint32_t)((int64_t)n * n * n);
+                          cudaStream_t s, int batch) {
+  const uint32_t ncells = (uint32_t)((int64_t)n * n * n * batch);
   PM_LAUNCH(K_CELLSTART, 4.0 * np + 4.0 * (ncells + 1.0), k_cellstart, grid_for(np + 1, 256), 256, 0, s, skeys, np, ncells, cellstart);
   return launch_status();
 }

@@ -259,3 +259,23 @@ def c4_workload(n, boxsize=200.0, Om=0.3, z_ini=20.0, steps=10, noise_seed=4, ta
     return {"noise": white_noise(n, noise_seed), "target_noise": white_noise(n, target_seed),
             "amp": lpt_amplitude(n, boxsize, Om), "d_ratio": d_ratio, "vfac": vfac,
             "a_steps": list(np.linspace(a_ini, 1.0, steps + 1)), "Om": Om, "OL": 1.0 - Om, "boxsize": boxsize}
+
+
+def ensemble_workload(n=64, B=64, boxsize=128.0, z_ini=30.0, steps=50, param_seed=3, box_seed0=1000,
+                      device="cpu"):
+    """The ensemble workload: B boxes of n^3 particles (2LPT at z_ini), box b
+    from white-noise seed box_seed0 + b, with Omega_m ~ U[0.25, 0.35] and
+    sigma8 ~ U[0.7, 0.9] drawn from PCG64(param_seed), flat; scale factors of
+    ``steps`` steps uniform in ln a to a = 1.  Returns a dict with X uint32
+    [B, 3, n^3], V float32 [B, 3, n^3], Om [B], sigma8 [B], a_steps."""
+    rng = np.random.Generator(np.random.PCG64(param_seed))
+    Om = rng.uniform(0.25, 0.35, B)
+    s8 = rng.uniform(0.7, 0.9, B)
+    a_ini = 1.0 / (1.0 + z_ini)
+    X = np.empty((B, 3, n ** 3), dtype=np.uint32)
+    V = np.empty((B, 3, n ** 3), dtype=np.float32)
+    for b in range(B):
+        X[b], V[b] = lpt_ics(n, boxsize, float(Om[b]), 1.0 - float(Om[b]), a_ini, box_seed0 + b, order=2,
+                             sigma8=float(s8[b]), device=device)
+    a_steps = list(np.exp(np.linspace(math.log(a_ini), 0.0, steps + 1)))
+    return {"X": X, "V": V, "Om": Om, "sigma8": s8, "a_steps": a_steps, "n": n, "B": B, "boxsize": boxsize}

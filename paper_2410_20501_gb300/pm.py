@@ -75,6 +75,18 @@ class pm_stats(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int), ("mg", mg_stats), ("fr", mg_stats)]
 
 
+class pm_batch_state(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int), ("B", ctypes.c_int), ("np_box", ctypes.c_int64), ("X", ctypes.c_void_p),
+                ("V", ctypes.c_void_p), ("phi", ctypes.c_void_p), ("ws", ctypes.c_void_p),
+                ("ws_bytes", ctypes.c_size_t), ("have_prev", ctypes.c_int)]
+
+
+class pm_batch_params(ctypes.Structure):
+    _fields_ = [("grad_order", ctypes.c_int), ("src_scale", ctypes.c_void_p), ("dt_kick", ctypes.c_void_p),
+                ("dt_drift", ctypes.c_void_p), ("phi_rescale", ctypes.c_void_p), ("mg", mg_params),
+                ("cold_cycles", ctypes.c_int)]
+
+
 _lib = None
 
 _SIGS = {
@@ -112,6 +124,10 @@ _SIGS = {
                                        ctypes.c_void_p]),
     "mg_solve_adj": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(mg_params),
                                     ctypes.POINTER(mg_stats), ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
+    "pm_batch_workspace_size": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int64,
+                                               ctypes.POINTER(ctypes.c_size_t)]),
+    "pm_step_batch": (ctypes.c_int, [ctypes.POINTER(pm_batch_state), ctypes.POINTER(pm_batch_params),
+                                     ctypes.c_void_p]),
     "pm_step_adj": (ctypes.c_int, [ctypes.POINTER(pm_state), ctypes.POINTER(pm_step_params), ctypes.c_void_p,
                                    ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                    ctypes.c_void_p]),
@@ -421,3 +437,93 @@ class Simulation:
 
     def particle_ids(self):
         return None if self.ids is None else self.ids.cpu().numpy()
+
+
+def batch_workspace(n, B, np_box, device="cuda"):
+    size = ctypes.c_size_t()
+    _check(lib().pm_batch_workspace_size(n, B, np_box, ctypes.byref(size)), "pm_batch_workspace_size")
+    return torch.empty(size.value, dtype=torch.uint8, device=device)
+
+
+class Ensemble:
+    """B independent boxes of n^3 cells stepped together by pm_step_batch.
+
+    X: uint32 numpy [B, 3, np_box]; V: float [B, 3, np_box]; Om: [B] matter
+    densities (flat: OL = 1 - Om).  Box b's particles occupy b*np_box ... in
+    every plane of the device arrays and are kept in cell order within the box.
+    step() is eager; capture() records one warm step in a CUDA graph that
+    replay_step() then replays with the next coefficients."""
+
+    def __init__(self, X, V, n, Om, boxsize, grad_order=5, mg=None, cold_cycles=8, device="cuda"):
+        X = np.asarray(X, dtype=np.uint32)
+        self.B, _, self.np_box = X.shape
+        self.n, self.boxsize, self.grad_order, self.cold_cycles = n, boxsize, grad_order, cold_cycles
+        self.Om = np.asarray(Om, dtype=np.float64).reshape(self.B)
+        self.OL = 1.0 - self.Om
+        npt = self.B * self.np_box
+        self.X = torch.from_numpy(np.ascontiguousarray(X.transpose(1, 0, 2).reshape(3, npt)).view(np.int32)).to(device)
+        self.V = torch.from_numpy(np.ascontiguousarray(
+            np.asarray(V, dtype=np.float32).transpose(1, 0, 2).reshape(3, npt))).to(device)
+        self.phi = torch.zeros((self.B, n, n, n), dtype=torch.float32, device=device)
+        self.ws = batch_workspace(n, self.B, self.np_box, device)
+        bpad = (self.B + 3) // 4 * 4                    # 16-byte aligned rows
+        self.coef = torch.zeros((4, bpad), dtype=torch.float32, device=device)
+        self.mg = mg if mg is not None else default_mg(fixed_cycles=2)
+        self.state = pm_batch_state(n=n, B=self.B, np_box=self.np_box, X=_p(self.X).value, V=_p(self.V).value,
+                                    phi=_p(self.phi).value, ws=_p(self.ws).value, ws_bytes=self.ws.numel(),
+                                    have_prev=0)
+        self.graph = None
+
+    def coefficients(self, a_steps):
+        """float32 [steps, 4, B]: per fused-kick step i and box b the source
+        scale 3/2 a_i Om_b, the kick (dt_{i-1} + dt_i)/2, the drift dt_i and the
+        warm-start factor a_i D_b(a_i) / (a_{i-1} D_b(a_{i-1})), dt in each
+        box's supercomoving time."""
+        S, B = len(a_steps) - 1, self.B
+        out = np.zeros((S, 4, self.coef.shape[1]), dtype=np.float32)
+        for b in range(B):
+            Om, OL = float(self.Om[b]), float(self.OL[b])
+            dts = [dt_supercomoving(Om, OL, a_steps[i], a_steps[i + 1]) for i in range(S)]
+            aD = [a * growth_D(Om, OL, a) for a in a_steps]
+            for i in range(S):
+                out[i, 0, b] = 1.5 * a_steps[i] * Om
+                out[i, 1, b] = 0.5 * ((dts[i - 1] if i > 0 else 0.0) + dts[i])
+                out[i, 2, b] = dts[i]
+                out[i, 3, b] = aD[i] / aD[i - 1] if i > 0 else 1.0
+        return torch.from_numpy(out).to(self.coef.device)
+
+    def _params(self):
+        c = self.coef
+        return pm_batch_params(grad_order=self.grad_order, src_scale=_p(c[0]).value, dt_kick=_p(c[1]).value,
+                               dt_drift=_p(c[2]).value, phi_rescale=_p(c[3]).value, mg=self.mg,
+                               cold_cycles=self.cold_cycles)
+
+    def step(self, coef_row):
+        """One eager step with the coefficients coef_row [4, B] (device)."""
+        self.coef.copy_(coef_row)
+        prm = self._params()
+        _check(lib().pm_step_batch(ctypes.byref(self.state), ctypes.byref(prm), _stream()), "pm_step_batch")
+
+    def capture(self):
+        """Record one warm step (have_prev must be 1) in a CUDA graph."""
+        if not self.state.have_prev:
+            raise RuntimeError("capture a warm step: run one eager step first")
+        prm = self._params()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            _check(lib().pm_step_batch(ctypes.byref(self.state), ctypes.byref(prm), _stream()), "pm_step_batch")
+        self.graph = g
+
+    def replay_step(self, coef_row):
+        self.coef.copy_(coef_row)
+        self.graph.replay()
+
+    def positions(self):
+        """uint32 [B, 3, np_box] (cell order within each box)."""
+        X = positions_to_host(self.X).reshape(3, self.B, self.np_box)
+        return np.ascontiguousarray(X.transpose(1, 0, 2))
+
+    def velocities(self):
+        V = self.V.cpu().numpy().reshape(3, self.B, self.np_box)
+        return np.ascontiguousarray(V.transpose(1, 0, 2))
+

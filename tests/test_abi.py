@@ -99,3 +99,26 @@ def test_host_cosmology_matches_oracle(L):
         D = cosmology.growth_factors(a, Om, OL)[0]
         Dc = np.array([pm.growth_D(Om, OL, x) for x in a])
         assert Dc / Dc[-1] == pytest.approx(D / D[-1], rel=1e-7)
+
+
+def test_batch_arguments_are_checked(L):
+    from paper_2410_20501_gb300 import pm
+    ok = ctypes.c_void_p(0x100000)
+    size = ctypes.c_size_t()
+    assert L.pm_batch_workspace_size(64, 64, 64 ** 3, ctypes.byref(size)) == 0 and size.value > 0
+    big = ctypes.c_size_t()
+    assert L.pm_batch_workspace_size(64, 128, 64 ** 3, ctypes.byref(big)) == 0 and big.value > size.value
+    assert L.pm_batch_workspace_size(16, 4, 100, ctypes.byref(size)) == 1        # n < 32
+    assert L.pm_batch_workspace_size(512, 64, 10, ctypes.byref(size)) == 1       # key bits 27 + 6 > 32
+    st = pm.pm_batch_state(n=32, B=2, np_box=10, X=ok.value, V=ok.value, phi=ok.value, ws=ok.value,
+                           ws_bytes=1 << 30)
+    prm = pm.pm_batch_params(grad_order=5, src_scale=ok.value, dt_kick=ok.value, dt_drift=ok.value,
+                             phi_rescale=ok.value, mg=pm.default_mg(fixed_cycles=0), cold_cycles=8)
+    assert L.pm_step_batch(ctypes.byref(st), ctypes.byref(prm), None) == 1      # fixed cycles required
+    prm.mg = pm.default_mg(fixed_cycles=2)
+    prm.cold_cycles = 0
+    assert L.pm_step_batch(ctypes.byref(st), ctypes.byref(prm), None) == 1      # cold cycles required
+    prm.cold_cycles = 8
+    st.ws_bytes = 16
+    assert L.pm_step_batch(ctypes.byref(st), ctypes.byref(prm), None) == 2      # workspace too small
+
