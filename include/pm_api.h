@@ -72,7 +72,9 @@ enum {
   PM_WS_FR = 4,        /* fr_solve                                             */
   PM_WS_STEP = 8,      /* pm_step, pm_step_host (includes all of the above)    */
   PM_WS_IDS = 16,      /* pm_step carries particle ids (pm_state.id != NULL)   */
-  PM_WS_ADJ = 32       /* adjoint entry points (with PM_WS_SORT or PM_WS_STEP) */
+  PM_WS_ADJ = 32,      /* adjoint entry points (with PM_WS_SORT or PM_WS_STEP) */
+  PM_WS_FFT = 64       /* FFT Poisson solver (pm_poisson_fft, pm_step with
+                          poisson != PM_POISSON_MG): the half spectrum          */
 };
 
 /* Bytes of workspace needed for grids of n^3 cells and np particles.
@@ -181,6 +183,19 @@ void mg_default_params(mg_params* p);
 pm_status mg_solve(const float* f, float* phi, int n, const mg_params* prm,
                    mg_stats* st, void* ws, size_t ws_bytes, void* stream);
 
+/* Poisson solve by 3-D FFT (§3.7): phi = scale * G * (rho - <rho>), with the
+ * Green's function of kind PM_POISSON_FFT7 (FFT_7pt: 1 / the Fourier symbol
+ * -(4/h^2) sum_d sin^2(pi m_d / n) of the 7-point Laplacian, no mass-
+ * assignment compensation: the exact inverse that converged multigrid
+ * approaches) or PM_POISSON_FFT (-1 / (k^2 W_TSC(k)^2), k = 2 pi m,
+ * W_TSC = prod_d sinc(pi m_d / n)^3: the exact Laplacian with the TSC
+ * window deconvolved).  G(0) = 0, so phi has zero mean.  The FFTs are the
+ * library's own (shared-memory Stockham, float32).
+ *   rho [n^3] (read), phi [n^3] (written); 16 <= n <= 1024.
+ * Workspace: pm_workspace_size(n, 0, PM_WS_FFT). */
+pm_status pm_poisson_fft(const float* rho, float* phi, int n, int kind, double scale, void* ws, size_t ws_bytes,
+                         void* stream);
+
 /* ------------------------------------------------------------------ f(R) -- */
 typedef struct {
   double a;          /* scale factor                                          */
@@ -241,6 +256,7 @@ typedef struct {
 } pm_state;
 
 enum { PM_GRAVITY_NEWTON = 0, PM_GRAVITY_FR = 1 };
+enum { PM_POISSON_MG = 0, PM_POISSON_FFT7 = 1, PM_POISSON_FFT = 2 };
 
 typedef struct {
   double a;            /* scale factor of this force evaluation              */
@@ -257,6 +273,10 @@ typedef struct {
                           started steps only (have_prev = 1): the first step
                           always cycles to tol from the Jacobi guess         */
   fr_params fr;        /* f(R) solver (a, Om, OL, fR0, boxsize taken from above) */
+  int poisson;         /* PM_POISSON_MG (multigrid, mg above), PM_POISSON_FFT7
+                          or PM_POISSON_FFT (pm_poisson_fft; workspace with
+                          PM_WS_FFT); the f(R) scalaron always uses FAS
+                          multigrid                                           */
 } pm_step_params;
 
 typedef struct {

@@ -14,7 +14,8 @@ const char* const kKernelClassNames[K_NCLASS] = {
     "tsc_deposit", "reduce",        "mg_guess",    "mg_smooth_l0",    "mg_smooth",   "mg_restrict",
     "mg_prolong",  "mg_coarse",     "mg_norm",     "fr_smooth_l0",    "fr_smooth",   "fr_restrict",
     "fr_coarse_op", "fr_prolong",
-    "fr_coarse",   "fr_norm",       "gradient",    "interp_kdk",      "adjoint",     "misc"};
+    "fr_coarse",   "fr_norm",       "gradient",    "interp_kdk",      "adjoint",     "fft",
+    "misc"};
 
 namespace {
 
@@ -98,6 +99,7 @@ size_t layout_workspace(Workspace* w, void* base, int n, int64_t np, uint32_t fl
     w->adj_psi = (float*)take((size_t)N * 4);
     w->adj_gbar = (float*)take((size_t)N * 12);
   }
+  if (flags & PM_WS_FFT) w->spec = (float2*)take((size_t)n * n * (n / 2 + 1) * 8 * batch);
   w->partials = (double*)take((size_t)2 * reduce_partials_capacity(n, np) * 8 * batch);
   w->scalars = (double*)take(64 * 8);
   w->box_mean = (double*)take((size_t)batch * 8);
@@ -296,6 +298,17 @@ pm_status fr_solve(const float* rho, float* eps, int n, const fr_params* prm, mg
   return fr_solve_src(Src{rho, sb, w.scalars + 2}, eps, n, *prm, st, w, s);
 }
 
+pm_status pm_poisson_fft(const float* rho, float* phi, int n, int kind, double scale, void* ws, size_t ws_bytes,
+                         void* stream) {
+  if (!valid_n(n) || n < 16 || !rho || !phi || !all_a16(rho, phi)) return PM_EINVAL;
+  if (kind != PM_POISSON_FFT7 && kind != PM_POISSON_FFT) return PM_EINVAL;
+  Workspace w;
+  PM_TRY(check_ws(w, ws, ws_bytes, n, 0, PM_WS_FFT));
+  cudaStream_t s = as_stream(stream);
+  PM_TRY(grid_mean(rho, (int64_t)n * n * n, w.partials, w.scalars + 3, s));
+  return fft_poisson_launch(rho, w.scalars + 3, phi, w.spec, n, kind, scale, s);
+}
+
 pm_status pm_gradient(const float* phi, float* g, int n, int order, void* stream) {
   if (!valid_n(n) || !phi || !g || (order != 3 && order != 5 && order != 7) || !all_a16(phi, g)) return PM_EINVAL;
   return gradient_launch(phi, nullptr, 0.0f, g, n, order, false, as_stream(stream));
@@ -325,7 +338,10 @@ pm_status pm_step(pm_state* st_, const pm_step_params* prm, pm_stats* stats, voi
   frp.fR0 = prm->fR0;
   frp.boxsize = prm->boxsize;
   if (prm->gravity == PM_GRAVITY_FR && !valid_fr(&frp)) return PM_EINVAL;
-  const uint32_t flags = PM_WS_STEP | (S.id ? PM_WS_IDS : 0);
+  if (prm->poisson != PM_POISSON_MG && prm->poisson != PM_POISSON_FFT7 && prm->poisson != PM_POISSON_FFT)
+    return PM_EINVAL;
+  if (prm->poisson != PM_POISSON_MG && n < 16) return PM_EINVAL;
+  const uint32_t flags = PM_WS_STEP | (S.id ? PM_WS_IDS : 0) | (prm->poisson != PM_POISSON_MG ? PM_WS_FFT : 0);
   Workspace w;
   PM_TRY(check_ws(w, S.ws, S.ws_bytes, n, np, flags));
   cudaStream_t s = as_stream(stream);
@@ -353,7 +369,9 @@ pm_status pm_step(pm_state* st_, const pm_step_params* prm, pm_stats* stats, voi
   mp.first_guess = S.have_prev ? MG_GUESS_SCALED : MG_GUESS_JACOBI;
   mp.guess_scale = (float)prm->phi_rescale;
   if (!S.have_prev) mp.fixed_cycles = 0;   // a cold start always iterates to the tolerance
-  {
+  if (prm->poisson != PM_POISSON_MG) {
+    PM_TRY(fft_poisson_launch(w.rho, w.scalars, S.phi, w.spec, n, prm->poisson, 1.5 * prm->a * prm->Om, s));
+  } else {
     pm_status r = mg_solve_src(Src{w.rho, (float)(1.5 * prm->a * prm->Om), w.scalars}, S.phi, n, mp, &local.mg, w, s);
     if (r != PM_OK && r != PM_ENOCONV) return r;
     if (r != PM_OK) solve_status = r;

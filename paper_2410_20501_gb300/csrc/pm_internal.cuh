@@ -14,7 +14,7 @@ enum KernelClass {
   K_DEPOSIT, K_REDUCE,
   K_MG_GUESS, K_MG_SMOOTH0, K_MG_SMOOTH, K_MG_RESTRICT, K_MG_PROLONG, K_MG_COARSE, K_MG_NORM,
   K_FR_SMOOTH0, K_FR_SMOOTH, K_FR_RESTRICT, K_FR_COARSEOP, K_FR_PROLONG, K_FR_COARSE, K_FR_NORM,
-  K_GRADIENT, K_INTERP, K_ADJOINT, K_MISC,
+  K_GRADIENT, K_INTERP, K_ADJOINT, K_FFT, K_MISC,
   K_NCLASS
 };
 
@@ -93,6 +93,7 @@ struct Workspace {
   // adjoint buffers
   float* adj_abar; float* adj_phi; float* adj_psi; float* adj_gbar;
   double* box_mean;   // per-box mean density of a batch
+  float2* spec;       // half spectrum n^2 (n/2 + 1) of the FFT Poisson path
   int64_t np; int n; int batch;
 };
 
@@ -161,6 +162,12 @@ pm_status interp_launch(const float* g, const uint32_t* Xs, const float* Vs, con
                         int64_t np, int n, float* acc, uint32_t* Xo, float* Vo, uint32_t* ids_out,
                         float dt_kick, float dt_drift, int mode, bool vec4, cudaStream_t s,
                         const Batch& bt = Batch{});
+
+// phi = scale * IFFT[G FFT[rho - mean]], G(0) = 0; kind 1: FFT_7pt, 2: FFT
+// with the exact kernel and TSC deconvolution (§3.7); mean (device float64)
+// may be NULL.  C: n^2 (n/2 + 1) float2.
+pm_status fft_poisson_launch(const float* rho, const double* mean, float* phi, float2* C, int n, int kind,
+                             double scale, cudaStream_t s);
 
 // Adjoint pieces (adjoint.cu).
 pm_status divergence_launch(const float* gbar, float* phibar, int n, int order, cudaStream_t s);

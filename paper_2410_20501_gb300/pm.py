@@ -17,7 +17,8 @@ import torch
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_lib", "libpmgb.so")
 
-PM_WS_SORT, PM_WS_MG, PM_WS_FR, PM_WS_STEP, PM_WS_IDS, PM_WS_ADJ = 1, 2, 4, 8, 16, 32
+PM_WS_SORT, PM_WS_MG, PM_WS_FR, PM_WS_STEP, PM_WS_IDS, PM_WS_ADJ, PM_WS_FFT = 1, 2, 4, 8, 16, 32, 64
+PM_POISSON_MG, PM_POISSON_FFT7, PM_POISSON_FFT = 0, 1, 2
 MG_GUESS_INPUT, MG_GUESS_JACOBI, MG_GUESS_SCALED = 0, 1, 2
 PM_GRAVITY_NEWTON, PM_GRAVITY_FR = 0, 1
 STATUS = {0: "PM_OK", 1: "PM_EINVAL", 2: "PM_ENOMEM", 3: "PM_ENOCONV", 4: "PM_ENAN", 5: "PM_ETIMEOUT",
@@ -68,7 +69,7 @@ class pm_step_params(ctypes.Structure):
     _fields_ = [("a", ctypes.c_double), ("Om", ctypes.c_double), ("OL", ctypes.c_double),
                 ("boxsize", ctypes.c_double), ("gravity", ctypes.c_int), ("fR0", ctypes.c_double),
                 ("grad_order", ctypes.c_int), ("dt_kick", ctypes.c_double), ("dt_drift", ctypes.c_double),
-                ("phi_rescale", ctypes.c_double), ("mg", mg_params), ("fr", fr_params)]
+                ("phi_rescale", ctypes.c_double), ("mg", mg_params), ("fr", fr_params), ("poisson", ctypes.c_int)]
 
 
 class pm_stats(ctypes.Structure):
@@ -124,6 +125,8 @@ _SIGS = {
                                        ctypes.c_void_p]),
     "mg_solve_adj": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(mg_params),
                                     ctypes.POINTER(mg_stats), ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
+    "pm_poisson_fft": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                      ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
     "pm_batch_workspace_size": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int64,
                                                ctypes.POINTER(ctypes.c_size_t)]),
     "pm_step_batch": (ctypes.c_int, [ctypes.POINTER(pm_batch_state), ctypes.POINTER(pm_batch_params),
@@ -260,6 +263,17 @@ def fr_solve(rho, eps=None, ws=None, **params):
     return eps, st.as_dict()
 
 
+def poisson_fft(rho, scale=1.0, kind=PM_POISSON_FFT7, ws=None):
+    """phi = scale * G * (rho - <rho>) by the library's 3-D FFT (kind:
+    PM_POISSON_FFT7 or PM_POISSON_FFT)."""
+    n = rho.shape[0]
+    ws = ws if ws is not None else workspace(n, 0, PM_WS_FFT, rho.device)
+    phi = torch.empty_like(rho, dtype=torch.float32)
+    _check(lib().pm_poisson_fft(_p(rho, torch.float32), _p(phi), n, kind, scale, _p(ws), ws.numel(), _stream()),
+           "pm_poisson_fft")
+    return phi
+
+
 def gradient(phi, order=5):
     n = phi.shape[0]
     g = torch.empty((3, n, n, n), dtype=torch.float32, device=phi.device)
@@ -354,7 +368,7 @@ class Simulation:
     track_ids."""
 
     def __init__(self, X, V, n, Om, OL, boxsize, gravity="newton", fR0=-1e-5, grad_order=5, mg=None, fr=None,
-                 track_ids=False, keep_acc=False, adjoint=False, device="cuda"):
+                 track_ids=False, keep_acc=False, adjoint=False, poisson=0, device="cuda"):
         self.n = n
         self.np = X.shape[1]
         self.Om, self.OL, self.boxsize, self.fR0 = Om, OL, boxsize, fR0
@@ -366,7 +380,9 @@ class Simulation:
         self.phi = torch.zeros((n, n, n), dtype=torch.float32, device=device)
         self.eps = torch.zeros((n, n, n), dtype=torch.float32, device=device) if self.gravity else None
         self.acc = torch.empty((3, self.np), dtype=torch.float32, device=device) if keep_acc else None
-        flags = PM_WS_STEP | (PM_WS_IDS if track_ids else 0) | (PM_WS_ADJ if adjoint else 0)
+        self.poisson = poisson
+        flags = (PM_WS_STEP | (PM_WS_IDS if track_ids else 0) | (PM_WS_ADJ if adjoint else 0)
+                 | (PM_WS_FFT if poisson else 0))
         self.ws = workspace(n, self.np, flags, device)
         self.mg = mg if mg is not None else default_mg()
         self.fr = fr if fr is not None else default_fr()
@@ -379,7 +395,7 @@ class Simulation:
     def params(self, a, dt_kick, dt_drift, phi_rescale=1.0):
         return pm_step_params(a=a, Om=self.Om, OL=self.OL, boxsize=self.boxsize, gravity=self.gravity,
                               fR0=self.fR0, grad_order=self.grad_order, dt_kick=dt_kick, dt_drift=dt_drift,
-                              phi_rescale=phi_rescale, mg=self.mg, fr=self.fr)
+                              phi_rescale=phi_rescale, mg=self.mg, fr=self.fr, poisson=self.poisson)
 
     def step(self, a, dt_kick, dt_drift, phi_rescale=1.0):
         st = pm_stats()

@@ -99,3 +99,23 @@ def test_fullsize_fr_f_cycle_reduces_residual(pm, densities):
     r0 = np.linalg.norm(b - ofr.operator(np.ones_like(e), h, fbar, kappa))
     assert np.isfinite(e).all() and e.min() > -1.0
     assert r1 < r0 / 10.0
+
+
+def test_fullsize_fft7_accelerations_sampled(pm, densities):
+    """The FFT_7pt path at 512^3 against the oracle's exact 7-point inverse,
+    at 10^4 sampled particles."""
+    _, rho1 = densities
+    s = 1.5 * 0.5 * 0.3
+    phi = pm.poisson_fft(torch.from_numpy(rho1).cuda(), scale=s, kind=pm.PM_POISSON_FFT7)
+    g = pm.gradient(phi)
+    X = inputs.uniform_particles(10000, 53)
+    acc = pm.interp(g, pm.positions_to_device(X)).cpu().numpy()
+    del g, phi
+    torch.cuda.empty_cache()
+    f1_64 = s * rho1.astype(np.float64)
+    ref_phi = poisson.solve_fft7(f1_64 - f1_64.mean(), 1.0 / N)
+    ref_g = mesh.force_from_potential(ref_phi, 1.0 / N)
+    ref = mesh.interp_tsc(ref_g, mesh.positions_from_fixed_point(X)).T
+    err = np.linalg.norm(acc - ref) / np.linalg.norm(ref)
+    assert err < 1e-5, err
+

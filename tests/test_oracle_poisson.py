@@ -106,3 +106,25 @@ def test_truncation_error_of_smooth_field_is_second_order():
         u = np.broadcast_to(np.sin(2 * np.pi * x)[:, None, None], (n, n, n)).copy()
         errs.append(np.abs(poisson.truncation_error(u, mesh.laplacian7(u, h), h)).max())
     assert np.log2(errs[0] / errs[1]) == pytest.approx(2.0, abs=0.15)
+
+
+def test_fft_tsc_plane_wave_closed_form():
+    """A cosine source along y: phi = -f / (k^2 W(k)^2) with k = 2 pi m and
+    W = sinc(pi m / n)^3 (the other two axes contribute sinc(0) = 1)."""
+    n, m = 16, 3
+    c = (np.arange(n) + 0.5) / n
+    f = np.cos(2 * np.pi * m * c)[None, :, None] * np.ones((n, n, n))
+    phi = poisson.solve_fft_tsc(f, 1.0 / n)
+    x = np.pi * m / n
+    W = (np.sin(x) / x) ** 3
+    np.testing.assert_allclose(phi, -f / ((2 * np.pi * m) ** 2 * W * W), atol=1e-13)
+
+
+def test_fft_tsc_removes_the_mean_and_is_linear():
+    rng = np.random.Generator(np.random.PCG64(4))
+    f, g = rng.standard_normal((2, 8, 8, 8))
+    a = poisson.solve_fft_tsc(f + 3.0, 1.0 / 8)
+    assert abs(a.mean()) < 1e-14
+    np.testing.assert_allclose(poisson.solve_fft_tsc(2 * f - g, 1.0 / 8),
+                               2 * poisson.solve_fft_tsc(f, 1.0 / 8) - poisson.solve_fft_tsc(g, 1.0 / 8),
+                               atol=1e-12)
