@@ -347,8 +347,10 @@ def run_gpu(args):
     fr = pm.default_fr(cycle=1, cycles=1)
     W, K = args.warmup, args.steps
     results = {}
-    for gravity in (("fr",) if args.lean else ("fr", "newton")):
-        sim = pm.Simulation(X, V, n, OM, OL, BOX, gravity=gravity, fR0=FR0, mg=mg, fr=fr)
+    for variant in (("fr",) if args.lean else ("fr", "newton", "newton_fft7")):
+        gravity = "newton" if variant.startswith("newton") else "fr"
+        sim = pm.Simulation(X, V, n, OM, OL, BOX, gravity=gravity, fR0=FR0, mg=mg, fr=fr,
+                            poisson=pm.PM_POISSON_FFT7 if variant == "newton_fft7" else pm.PM_POISSON_MG)
         timed_steps(sim, coeffs, 0, W)
         barrier(world)
         torch.cuda.synchronize()
@@ -362,7 +364,7 @@ def run_gpu(args):
         if gravity == "fr":
             pm.timing_enable(False)
         ms = max_over_ranks(ms, world, "cuda")
-        results[gravity] = {"ms": ms, "stats": stats, "clocks": clk.summary(), "launches": launches,
+        results[variant] = {"ms": ms, "stats": stats, "clocks": clk.summary(), "launches": launches,
                             "kernels": kern}
         if gravity == "fr" and not args.lean:
             # end to end through the C ABI with host buffers: H2D of X, V and D2H of X, V every step
@@ -380,7 +382,7 @@ def run_gpu(args):
     if rank != 0:
         return 0
 
-    fr_res, nw_res = results["fr"], results.get("newton")
+    fr_res, nw_res, ft_res = results["fr"], results.get("newton"), results.get("newton_fft7")
     total = world * npart * K
     value = total / (fr_res["ms"] / 1e3)
     peak, peak_kind = load_peaks()
@@ -417,6 +419,10 @@ def run_gpu(args):
         "newton": None if nw_res is None else {
             "value": total / (nw_res["ms"] / 1e3), "ms_per_step": nw_res["ms"] / K,
             "gpu_launches": nw_res["launches"], "mg_cycles": [s["mg"]["cycles"] for s in nw_res["stats"]]},
+        "newton_fft7": None if ft_res is None else {
+            "value": total / (ft_res["ms"] / 1e3), "ms_per_step": ft_res["ms"] / K,
+            "gpu_launches": ft_res["launches"],
+            "what": "Newtonian step with the FFT_7pt Poisson solve (the exact 7-point inverse) instead of multigrid"},
         "mg_cycles": [s["mg"]["cycles"] for s in fr_res["stats"]],
         "e2e": None if "e2e_ms" not in results else {
             "value": total / (results["e2e_ms"] / 1e3), "unit": "particle-steps/s",
