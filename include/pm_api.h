@@ -255,14 +255,17 @@ typedef struct {
                       u = 1 for f(R); set to 1 by pm_step                     */
 } pm_state;
 
-enum { PM_GRAVITY_NEWTON = 0, PM_GRAVITY_FR = 1 };
+enum { PM_GRAVITY_NEWTON = 0, PM_GRAVITY_FR = 1, PM_GRAVITY_PARAM = 2 };
 enum { PM_POISSON_MG = 0, PM_POISSON_FFT7 = 1, PM_POISSON_FFT = 2 };
 
 typedef struct {
   double a;            /* scale factor of this force evaluation              */
   double Om, OL;       /* cosmology (flat)                                   */
   double boxsize;      /* Mpc/h                                              */
-  int gravity;         /* PM_GRAVITY_NEWTON or PM_GRAVITY_FR                 */
+  int gravity;         /* PM_GRAVITY_NEWTON, PM_GRAVITY_FR or PM_GRAVITY_PARAM
+                          (parametrised: the Poisson source times
+                          mu(a) = 1 + mu0 Omega_L(a)/Omega_L,0 = 1 + mu0/E(a)^2,
+                          §2.4, Eq. mu_parametrized_gravity)                  */
   double fR0;          /* for PM_GRAVITY_FR                                  */
   int grad_order;      /* 3, 5 or 7 (Table 1); 5 by default                  */
   double dt_kick;      /* v += acc * dt_kick (sum of the two half kicks of
@@ -277,12 +280,18 @@ typedef struct {
                           or PM_POISSON_FFT (pm_poisson_fft; workspace with
                           PM_WS_FFT); the f(R) scalaron always uses FAS
                           multigrid                                           */
+  double mu0;          /* PM_GRAVITY_PARAM: the coupling today minus one      */
+  int report_max;      /* 1: fill pm_stats.max_acc / max_vel (one 16-byte
+                          device-to-host read: the call synchronises)        */
 } pm_step_params;
 
 typedef struct {
   int status;
   mg_stats mg;         /* Poisson solve                                      */
   mg_stats fr;         /* f(R) solve                                         */
+  double max_acc;      /* with report_max: max |acceleration| of the step and */
+  double max_vel;      /* max |velocity| after its kick (the inputs of the
+                          free-fall and velocity time-step criteria, §3.4)   */
 } pm_stats;
 
 /* One PM step on the device-resident state (§3.4-§3.10): sort particles by

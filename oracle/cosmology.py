@@ -42,6 +42,12 @@ def omega_l_of_a(a, Om, OL):
     return OL / hubble_E(a, Om, OL) ** 2
 
 
+def mu_parametrised(a, Om, OL, mu0):
+    """Effective gravitational coupling of the parametrised model (§2.4,
+    Eq. mu_parametrized_gravity): mu(a) = 1 + mu0 Omega_Lambda(a) / Omega_Lambda,0."""
+    return 1.0 + mu0 * omega_l_of_a(a, Om, OL) / OL
+
+
 def growth_factors(a_eval, Om, OL, a_start=1e-5):
     """First and second order growth factors D, E and rates f1 = D'/D,
     f2 = E'/E (Appendix A, the ODEs in ln a):

@@ -4,7 +4,7 @@ from dataclasses import dataclass, field
 import numpy as np
 
 from . import fr as frmod
-from .cosmology import dt_supercomoving, growth_factors
+from .cosmology import dt_supercomoving, growth_factors, mu_parametrised
 from .mesh import deposit_tsc, force_from_potential, interp_tsc
 from .poisson import MGParams, mg_solve, solve_fft7
 
@@ -15,8 +15,9 @@ class PMParams:
     Om: float = 1.0
     OL: float = 0.0
     boxsize: float = 64.0
-    gravity: str = "newton"          # "newton" or "fr"
+    gravity: str = "newton"          # "newton", "fr" or "mu" (parametrised)
     fR0: float = -1e-5
+    mu0: float = 0.0                 # parametrised gravity: coupling today
     grad_order: int = 5
     solver: str = "fft7"             # "fft7" (exact discrete inverse) or "mg"
     mg: MGParams = field(default_factory=MGParams)
@@ -39,6 +40,8 @@ def accelerations(pos, a, prm, phi_guess=None, u_guess=None):
     h = 1.0 / n
     rho = deposit_tsc(pos, n)
     f = poisson_source(rho, a, prm.Om)
+    if prm.gravity == "mu":      # nabla^2 psi = 4 pi G mu(a) a^2 delta rho (Eq. parametrized_newtonian_equation)
+        f = f * mu_parametrised(a, prm.Om, prm.OL, prm.mu0)
     if prm.solver == "fft7":
         phi = solve_fft7(f, h)
     else:

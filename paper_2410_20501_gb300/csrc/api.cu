@@ -158,6 +158,14 @@ pm_status check_ws(Workspace& w, void* ws, size_t ws_bytes, int n, int64_t np, u
 
 bool valid_np(int64_t np) { return np >= 0 && np < ((int64_t)1 << 31); }
 
+// 3/2 a Om of the supercomoving Poisson equation (§3.1), times mu(a) =
+// 1 + mu0 Omega_L(a)/Omega_L,0 = 1 + mu0 / E(a)^2 for parametrised gravity.
+double poisson_scale(const pm_step_params& p) {
+  double s = 1.5 * p.a * p.Om;
+  if (p.gravity == PM_GRAVITY_PARAM) s *= 1.0 + p.mu0 / (p.Om / (p.a * p.a * p.a) + p.OL);
+  return s;
+}
+
 bool valid_mg(const mg_params* p) {
   return p && p->npre >= 0 && p->npost >= 0 && p->npre + p->npost > 0 && p->coarsest >= 4 &&
          p->coarsest <= 16 && p->coarse_max_sweeps >= 0 && p->max_cycles >= 1 && p->omega > 0.0f &&
@@ -327,7 +335,8 @@ pm_status pm_step(pm_state* st_, const pm_step_params* prm, pm_stats* stats, voi
   const int64_t np = S.np;
   if (!valid_n(n) || !valid_np(np) || (np > 0 && (!S.X || !S.V)) || !S.phi) return PM_EINVAL;
   if (!all_a16(S.X, S.V, S.id, S.phi, S.eps, S.acc)) return PM_EINVAL;
-  if (prm->gravity != PM_GRAVITY_NEWTON && prm->gravity != PM_GRAVITY_FR) return PM_EINVAL;
+  if (prm->gravity != PM_GRAVITY_NEWTON && prm->gravity != PM_GRAVITY_FR && prm->gravity != PM_GRAVITY_PARAM)
+    return PM_EINVAL;
   if (prm->gravity == PM_GRAVITY_FR && !S.eps) return PM_EINVAL;
   if (prm->grad_order != 3 && prm->grad_order != 5 && prm->grad_order != 7) return PM_EINVAL;
   if (!(prm->a > 0.0) || !valid_mg(&prm->mg)) return PM_EINVAL;
@@ -370,9 +379,9 @@ pm_status pm_step(pm_state* st_, const pm_step_params* prm, pm_stats* stats, voi
   mp.guess_scale = (float)prm->phi_rescale;
   if (!S.have_prev) mp.fixed_cycles = 0;   // a cold start always iterates to the tolerance
   if (prm->poisson != PM_POISSON_MG) {
-    PM_TRY(fft_poisson_launch(w.rho, w.scalars, S.phi, w.spec, n, prm->poisson, 1.5 * prm->a * prm->Om, s));
+    PM_TRY(fft_poisson_launch(w.rho, w.scalars, S.phi, w.spec, n, prm->poisson, poisson_scale(*prm), s));
   } else {
-    pm_status r = mg_solve_src(Src{w.rho, (float)(1.5 * prm->a * prm->Om), w.scalars}, S.phi, n, mp, &local.mg, w, s);
+    pm_status r = mg_solve_src(Src{w.rho, (float)poisson_scale(*prm), w.scalars}, S.phi, n, mp, &local.mg, w, s);
     if (r != PM_OK && r != PM_ENOCONV) return r;
     if (r != PM_OK) solve_status = r;
   }
@@ -382,8 +391,15 @@ pm_status pm_step(pm_state* st_, const pm_step_params* prm, pm_stats* stats, voi
   const bool vec4 = false;
   PM_TRY(gradient_launch(S.phi, prm->gravity == PM_GRAVITY_FR ? S.eps : nullptr, alpha, w.g, n, prm->grad_order,
                          vec4, s));
+  double* max_out = prm->report_max ? w.scalars + 24 : nullptr;   // largest |a|, |v| for the time step
   PM_TRY(interp_launch(w.g, w.Xs, w.Vs, w.ids, np, n, S.acc, S.X, S.V, S.id, (float)prm->dt_kick,
-                       (float)prm->dt_drift, 1, vec4, s));
+                       (float)prm->dt_drift, 1, vec4, s, Batch{}, reinterpret_cast<float2*>(w.partials), max_out));
+  if (max_out) {
+    double h[2] = {0.0, 0.0};
+    if (np > 0) PM_TRY(fetch_scalars(max_out, h, 2, s));
+    local.max_acc = h[0];
+    local.max_vel = h[1];
+  }
   S.have_prev = 1;
   local.status = solve_status;
   if (stats) *stats = local;
@@ -452,7 +468,8 @@ pm_status pm_step_adj(pm_state* st_, const pm_step_params* prm, const float* phi
   pm_state& S = *st_;
   const int n = S.n;
   const int64_t np = S.np;
-  if (!valid_n(n) || !valid_np(np) || (np > 0 && !S.X) || prm->gravity != PM_GRAVITY_NEWTON) return PM_EINVAL;
+  if (!valid_n(n) || !valid_np(np) || (np > 0 && !S.X)) return PM_EINVAL;
+  if (prm->gravity != PM_GRAVITY_NEWTON && prm->gravity != PM_GRAVITY_PARAM) return PM_EINVAL;
   if (prm->grad_order != 3 && prm->grad_order != 5 && prm->grad_order != 7) return PM_EINVAL;
   if (!(prm->a > 0.0) || !valid_mg(&prm->mg)) return PM_EINVAL;
   const uint32_t flags = PM_WS_STEP | PM_WS_ADJ | (S.id ? PM_WS_IDS : 0);
@@ -468,7 +485,7 @@ pm_status pm_step_adj(pm_state* st_, const pm_step_params* prm, const float* phi
   mg_params mp = prm->mg;
   mp.first_guess = MG_GUESS_JACOBI;
   mp.fixed_cycles = 0;
-  const float src_scale = (float)(1.5 * prm->a * prm->Om);
+  const float src_scale = (float)poisson_scale(*prm);
   const float* phi = phi_fwd;
   if (!phi) {
     PM_TRY(deposit_sorted(w.Xs, np, w.cellstart, n, w.rho, w.partials, w.scalars, s));

@@ -289,9 +289,10 @@ int deposit_items(int n) {
 }
 
 int64_t reduce_partials_capacity(int n, int64_t np) {
-  (void)np;
   int64_t t = (int64_t)n / 4;
   int64_t c = t * t * t;               // deposit blocks with 4^3 tiles (upper bound)
+  const int64_t b = np / 256 + 1;      // interpolation blocks (one float2 of maxima each)
+  if (b > c) c = b;
   return c > 152 * 64 ? c : 152 * 64;
 }
 

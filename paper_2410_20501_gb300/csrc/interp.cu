@@ -144,7 +144,8 @@ __global__ void __launch_bounds__(256) k_interp_kdk(const float* __restrict__ g,
                                                     float* __restrict__ Vo, uint32_t* __restrict__ ids_out,
                                                     float dt_kick, float drift_scale, int mode, int64_t np_box,
                                                     const float* __restrict__ dtk_box,
-                                                    const float* __restrict__ dtd_box) {
+                                                    const float* __restrict__ dtd_box,
+                                                    float2* __restrict__ blockmax) {
   const int m = (1 << log2n) - 1, sh = 32 - log2n;
   const int64_t N = (int64_t)1 << (3 * log2n);
   // the box of a batched launch: its grid and its particles p0 .. p0 + np_box
@@ -153,6 +154,7 @@ __global__ void __launch_bounds__(256) k_interp_kdk(const float* __restrict__ g,
   g += (int64_t)blockIdx.z * (VEC4 ? 4 : 3) * N;
   if (dtk_box) dt_kick = __ldg(dtk_box + blockIdx.z);
   if (dtd_box) drift_scale = __ldg(dtd_box + blockIdx.z) * 4294967296.0f;
+  float amax = 0.0f, vmax = 0.0f;   // largest |a| and |v after the kick| of this thread
   for (int64_t p = p0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < p1;
        p += (int64_t)gridDim.x * blockDim.x) {
     const uint32_t x = __ldg(Xs + p), y = __ldg(Xs + np + p), z = __ldg(Xs + 2 * np + p);
@@ -191,6 +193,7 @@ __global__ void __launch_bounds__(256) k_interp_kdk(const float* __restrict__ g,
       acc[np + p] = ay;
       acc[2 * np + p] = az;
     }
+    if (blockmax) amax = fmaxf(amax, sqrtf(fmaf(ax, ax, fmaf(ay, ay, az * az))));
     if (mode == 1) {
       const float vx = fmaf(ax, dt_kick, __ldg(Vs + p));
       const float vy = fmaf(ay, dt_kick, __ldg(Vs + np + p));
@@ -198,11 +201,58 @@ __global__ void __launch_bounds__(256) k_interp_kdk(const float* __restrict__ g,
       Vo[p] = vx;
       Vo[np + p] = vy;
       Vo[2 * np + p] = vz;
+      if (blockmax) vmax = fmaxf(vmax, sqrtf(fmaf(vx, vx, fmaf(vy, vy, vz * vz))));
       Xo[p] = x + (uint32_t)__float2int_rn(vx * drift_scale);
       Xo[np + p] = y + (uint32_t)__float2int_rn(vy * drift_scale);
       Xo[2 * np + p] = z + (uint32_t)__float2int_rn(vz * drift_scale);
       if (ids_out) ids_out[p] = __ldg(ids_in + p);
     }
+  }
+  if (blockmax) {   // block maxima (non-negative floats order like their bit patterns)
+    __shared__ unsigned wa[8], wv[8];
+    const unsigned ua = __reduce_max_sync(0xffffffffu, __float_as_uint(amax));
+    const unsigned uv = __reduce_max_sync(0xffffffffu, __float_as_uint(vmax));
+    if ((threadIdx.x & 31) == 0) {
+      wa[threadIdx.x >> 5] = ua;
+      wv[threadIdx.x >> 5] = uv;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      unsigned ma = 0, mv = 0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+        ma = max(ma, wa[w]);
+        mv = max(mv, wv[w]);
+      }
+      blockmax[(int64_t)blockIdx.z * gridDim.x + blockIdx.x] = make_float2(__uint_as_float(ma), __uint_as_float(mv));
+    }
+  }
+}
+
+// Maximum over count float2 pairs, per component, into out[0], out[1]
+// (float64); one block.
+__global__ void __launch_bounds__(1024) k_max_pairs(const float2* __restrict__ v, int64_t count,
+                                                    double* __restrict__ out) {
+  __shared__ unsigned wa[32], wv[32];
+  unsigned ma = 0, mv = 0;
+  for (int64_t i = threadIdx.x; i < count; i += blockDim.x) {
+    const float2 x = v[i];
+    ma = max(ma, __float_as_uint(x.x));
+    mv = max(mv, __float_as_uint(x.y));
+  }
+  ma = __reduce_max_sync(0xffffffffu, ma);
+  mv = __reduce_max_sync(0xffffffffu, mv);
+  if ((threadIdx.x & 31) == 0) {
+    wa[threadIdx.x >> 5] = ma;
+    wv[threadIdx.x >> 5] = mv;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      ma = max(ma, wa[w]);
+      mv = max(mv, wv[w]);
+    }
+    out[0] = __uint_as_float(ma);
+    out[1] = __uint_as_float(mv);
   }
 }
 
@@ -253,19 +303,25 @@ pm_status gradient_launch(const float* phi, const float* eps, float alpha, float
 
 pm_status interp_launch(const float* g, const uint32_t* Xs, const float* Vs, const uint32_t* ids_in, int64_t np,
                         int n, float* acc, uint32_t* Xo, float* Vo, uint32_t* ids_out, float dt_kick,
-                        float dt_drift, int mode, bool vec4, cudaStream_t s, const Batch& bt) {
+                        float dt_drift, int mode, bool vec4, cudaStream_t s, const Batch& bt,
+                        float2* blockmax, double* max_out) {
   if (np == 0) return PM_OK;
   const float drift_scale = (float)((double)dt_drift * 4294967296.0);
   const double bytes = (vec4 ? 16.0 : 12.0) * n * n * (double)n * bt.B +
                        np * (12.0 + (mode ? 36.0 : 0.0) + (acc ? 12.0 : 0.0) + (ids_out ? 8.0 : 0.0));
   const int64_t np_box = bt.B > 1 ? bt.np_box : np;
   const dim3 grid(grid_for(np_box, 256), 1, (unsigned)bt.B);
+  if (!max_out) blockmax = nullptr;
   if (vec4)
     PM_LAUNCH(K_INTERP, bytes, k_interp_kdk<true>, grid, 256, 0, s, g, Xs, Vs, ids_in, np, ilog2(n), acc,
-              Xo, Vo, ids_out, dt_kick, drift_scale, mode, np_box, bt.dt_kick, bt.dt_drift);
+              Xo, Vo, ids_out, dt_kick, drift_scale, mode, np_box, bt.dt_kick, bt.dt_drift, blockmax);
   else
     PM_LAUNCH(K_INTERP, bytes, k_interp_kdk<false>, grid, 256, 0, s, g, Xs, Vs, ids_in, np, ilog2(n),
-              acc, Xo, Vo, ids_out, dt_kick, drift_scale, mode, np_box, bt.dt_kick, bt.dt_drift);
+              acc, Xo, Vo, ids_out, dt_kick, drift_scale, mode, np_box, bt.dt_kick, bt.dt_drift, blockmax);
+  if (blockmax) {
+    const int64_t nb = (int64_t)grid.x * grid.z;
+    PM_LAUNCH(K_REDUCE, 8.0 * nb, k_max_pairs, 1, 1024, 0, s, blockmax, nb, max_out);
+  }
   return launch_status();
 }
 

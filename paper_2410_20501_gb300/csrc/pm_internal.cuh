@@ -157,11 +157,12 @@ void fr_background(const fr_params& p, double* fbar, double* kappa, double* c2);
 pm_status gradient_launch(const float* phi, const float* eps, float alpha, float* g, int n,
                           int order, bool vec4, cudaStream_t s, int batch = 1);
 // mode 0: acc only; mode 1: kick + drift into Xo/Vo (and acc if non-NULL);
-// vec4: g interleaved as float4.
+// vec4: g interleaved as float4.  With max_out (2 doubles, device) also the
+// largest |a| and |v after the kick| (blockmax: one float2 per block).
 pm_status interp_launch(const float* g, const uint32_t* Xs, const float* Vs, const uint32_t* ids_in,
                         int64_t np, int n, float* acc, uint32_t* Xo, float* Vo, uint32_t* ids_out,
                         float dt_kick, float dt_drift, int mode, bool vec4, cudaStream_t s,
-                        const Batch& bt = Batch{});
+                        const Batch& bt = Batch{}, float2* blockmax = nullptr, double* max_out = nullptr);
 
 // phi = scale * IFFT[G FFT[rho - mean]], G(0) = 0; kind 1: FFT_7pt, 2: FFT
 // with the exact kernel and TSC deconvolution (§3.7); mean (device float64)

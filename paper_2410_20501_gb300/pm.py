@@ -9,6 +9,7 @@ Layouts: positions are uint32 fixed point stored in int32 tensors [3, np]
 [n, n, n]; vector grids float32 [3, n, n, n].
 """
 import ctypes
+import math
 import os
 
 import numpy as np
@@ -20,7 +21,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libpmgb.so")
 PM_WS_SORT, PM_WS_MG, PM_WS_FR, PM_WS_STEP, PM_WS_IDS, PM_WS_ADJ, PM_WS_FFT = 1, 2, 4, 8, 16, 32, 64
 PM_POISSON_MG, PM_POISSON_FFT7, PM_POISSON_FFT = 0, 1, 2
 MG_GUESS_INPUT, MG_GUESS_JACOBI, MG_GUESS_SCALED = 0, 1, 2
-PM_GRAVITY_NEWTON, PM_GRAVITY_FR = 0, 1
+PM_GRAVITY_NEWTON, PM_GRAVITY_FR, PM_GRAVITY_PARAM = 0, 1, 2
 STATUS = {0: "PM_OK", 1: "PM_EINVAL", 2: "PM_ENOMEM", 3: "PM_ENOCONV", 4: "PM_ENAN", 5: "PM_ETIMEOUT",
           6: "PM_ECUDA"}
 
@@ -69,11 +70,13 @@ class pm_step_params(ctypes.Structure):
     _fields_ = [("a", ctypes.c_double), ("Om", ctypes.c_double), ("OL", ctypes.c_double),
                 ("boxsize", ctypes.c_double), ("gravity", ctypes.c_int), ("fR0", ctypes.c_double),
                 ("grad_order", ctypes.c_int), ("dt_kick", ctypes.c_double), ("dt_drift", ctypes.c_double),
-                ("phi_rescale", ctypes.c_double), ("mg", mg_params), ("fr", fr_params), ("poisson", ctypes.c_int)]
+                ("phi_rescale", ctypes.c_double), ("mg", mg_params), ("fr", fr_params), ("poisson", ctypes.c_int),
+                ("mu0", ctypes.c_double), ("report_max", ctypes.c_int)]
 
 
 class pm_stats(ctypes.Structure):
-    _fields_ = [("status", ctypes.c_int), ("mg", mg_stats), ("fr", mg_stats)]
+    _fields_ = [("status", ctypes.c_int), ("mg", mg_stats), ("fr", mg_stats), ("max_acc", ctypes.c_double),
+                ("max_vel", ctypes.c_double)]
 
 
 class pm_batch_state(ctypes.Structure):
@@ -333,6 +336,33 @@ def gradient_adj(g_bar, order=5):
     return phi_bar
 
 
+def next_timestep(a, Om, OL, n, max_acc, max_vel, courant=0.8, da_max=0.02, a_end=1.0):
+    """Time step of §3.4 (Integrator) in supercomoving time and the scale
+    factor it reaches: dt = courant * min(dt_cosmo, dt_ff, dt_vel) with
+    dt_cosmo the time for a to grow by the fraction da_max, dt_ff =
+    sqrt(h / max|a|), dt_vel = h / max|v| (h = 1/n; a criterion with a zero
+    maximum is absent), clipped so that a does not pass a_end.  Host code."""
+    h = 1.0 / n
+    dts = [dt_supercomoving(Om, OL, a, a * (1.0 + da_max))]
+    if max_acc > 0.0:
+        dts.append(math.sqrt(h / max_acc))
+    if max_vel > 0.0:
+        dts.append(h / max_vel)
+    dt = courant * min(dts)
+    if dt_supercomoving(Om, OL, a, a_end) <= dt:
+        return dt_supercomoving(Om, OL, a, a_end), a_end
+    lo, hi = a, a * (1.0 + da_max)       # dt <= dt_cosmo: the root lies in [a, a (1 + da_max)]
+    for _ in range(200):                  # bisection on the monotone t(a)
+        mid = 0.5 * (lo + hi)
+        if dt_supercomoving(Om, OL, a, mid) < dt:
+            lo = mid
+        else:
+            hi = mid
+        if hi - lo <= 1e-15 * hi:
+            break
+    return dt, 0.5 * (lo + hi)
+
+
 def dt_supercomoving(Om, OL, a0, a1):
     return lib().pm_dt_supercomoving(Om, OL, a0, a1)
 
@@ -368,17 +398,19 @@ class Simulation:
     track_ids."""
 
     def __init__(self, X, V, n, Om, OL, boxsize, gravity="newton", fR0=-1e-5, grad_order=5, mg=None, fr=None,
-                 track_ids=False, keep_acc=False, adjoint=False, poisson=0, device="cuda"):
+                 track_ids=False, keep_acc=False, adjoint=False, poisson=0, mu0=0.0, device="cuda"):
         self.n = n
         self.np = X.shape[1]
         self.Om, self.OL, self.boxsize, self.fR0 = Om, OL, boxsize, fR0
-        self.gravity = PM_GRAVITY_FR if gravity == "fr" else PM_GRAVITY_NEWTON
+        self.gravity = {"newton": PM_GRAVITY_NEWTON, "fr": PM_GRAVITY_FR, "mu": PM_GRAVITY_PARAM}[gravity]
+        self.mu0 = mu0
         self.grad_order = grad_order
         self.X = positions_to_device(X, device)
         self.V = torch.from_numpy(np.ascontiguousarray(V, dtype=np.float32)).to(device)
         self.ids = torch.arange(self.np, dtype=torch.int32, device=device) if track_ids else None
         self.phi = torch.zeros((n, n, n), dtype=torch.float32, device=device)
-        self.eps = torch.zeros((n, n, n), dtype=torch.float32, device=device) if self.gravity else None
+        self.eps = (torch.zeros((n, n, n), dtype=torch.float32, device=device)
+                    if self.gravity == PM_GRAVITY_FR else None)
         self.acc = torch.empty((3, self.np), dtype=torch.float32, device=device) if keep_acc else None
         self.poisson = poisson
         flags = (PM_WS_STEP | (PM_WS_IDS if track_ids else 0) | (PM_WS_ADJ if adjoint else 0)
@@ -392,18 +424,49 @@ class Simulation:
                               acc=_p(self.acc).value if keep_acc else None, ws=_p(self.ws).value,
                               ws_bytes=self.ws.numel(), have_prev=0)
 
-    def params(self, a, dt_kick, dt_drift, phi_rescale=1.0):
+    def params(self, a, dt_kick, dt_drift, phi_rescale=1.0, report_max=False):
         return pm_step_params(a=a, Om=self.Om, OL=self.OL, boxsize=self.boxsize, gravity=self.gravity,
                               fR0=self.fR0, grad_order=self.grad_order, dt_kick=dt_kick, dt_drift=dt_drift,
-                              phi_rescale=phi_rescale, mg=self.mg, fr=self.fr, poisson=self.poisson)
+                              phi_rescale=phi_rescale, mg=self.mg, fr=self.fr, poisson=self.poisson, mu0=self.mu0,
+                              report_max=1 if report_max else 0)
 
-    def step(self, a, dt_kick, dt_drift, phi_rescale=1.0):
+    def step(self, a, dt_kick, dt_drift, phi_rescale=1.0, report_max=False):
         st = pm_stats()
-        prm = self.params(a, dt_kick, dt_drift, phi_rescale)
+        prm = self.params(a, dt_kick, dt_drift, phi_rescale, report_max)
         code = lib().pm_step(ctypes.byref(self.state), ctypes.byref(prm), ctypes.byref(st), _stream())
         if code not in (0, 3):
             _check(code, "pm_step")
-        return {"status": st.status, "mg": st.mg.as_dict(), "fr": st.fr.as_dict()}
+        out = {"status": st.status, "mg": st.mg.as_dict(), "fr": st.fr.as_dict()}
+        if report_max:
+            out["max_acc"], out["max_vel"] = st.max_acc, st.max_vel
+        return out
+
+    def run_adaptive(self, a_start, a_end, courant=0.8, da_max=0.02, max_steps=100000):
+        """Kick-drift-kick from a_start to a_end with the time step of §3.4:
+        courant * min(the step that raises a by da_max, sqrt(h / max|a|),
+        h / max|v|), h = 1/n.  The fused kick of step i takes dt_i from the
+        accelerations and velocities of step i - 1 (the first step from the
+        initial velocities and the cosmological limit).  Returns the scale
+        factors of the force evaluations (the last one is a_end, reached by a
+        closing half kick)."""
+        a = a_start
+        v = self.V.float()
+        max_vel = float(torch.sqrt((v * v).sum(0)).max()) if self.np else 0.0
+        max_acc, dt_prev, phis, out = 0.0, 0.0, None, [a_start]
+        aD_prev = None
+        for _ in range(max_steps):
+            dt, a_next = next_timestep(a, self.Om, self.OL, self.n, max_acc, max_vel, courant, da_max, a_end)
+            aD = a * growth_D(self.Om, self.OL, a)
+            resc = aD / aD_prev if aD_prev is not None else 1.0
+            st = self.step(a, 0.5 * (dt_prev + dt), dt, resc, report_max=True)
+            max_acc, max_vel, dt_prev, aD_prev = st["max_acc"], st["max_vel"], dt, aD
+            a = a_next
+            out.append(a)
+            if a >= a_end:
+                break
+        aD = a * growth_D(self.Om, self.OL, a)
+        self.step(a, 0.5 * dt_prev, 0.0, aD / aD_prev)   # closing half kick at a_end
+        return out
 
     def step_host(self, a, dt_kick, dt_drift, X_in, V_in, X_out, V_out, phi_rescale=1.0):
         """pm_step_host with pinned host tensors (int32 [3,np], float32 [3,np])."""

@@ -122,3 +122,20 @@ def test_batch_arguments_are_checked(L):
     st.ws_bytes = 16
     assert L.pm_step_batch(ctypes.byref(st), ctypes.byref(prm), None) == 2      # workspace too small
 
+
+
+def test_adaptive_timestep_criteria(L):
+    """The §3.4 time-step rule on the host (EdS: t~(a) = -2 a^(-1/2), so the
+    scale factor a step reaches is known in closed form)."""
+    from paper_2410_20501_gb300 import pm
+    a, n = 0.05, 32
+    dt, a1 = pm.next_timestep(a, 1.0, 0.0, n, 0.0, 0.0, courant=1.0, da_max=0.02)
+    assert abs(a1 - 1.02 * a) < 1e-12 * a                                    # cosmological limit
+    assert abs(dt - 2 * (a ** -0.5 - (1.02 * a) ** -0.5)) < 1e-12 * dt
+    dt, a1 = pm.next_timestep(a, 1.0, 0.0, n, 1e6, 0.0, courant=0.5)
+    assert abs(dt - 0.5 * (1.0 / n / 1e6) ** 0.5) < 1e-15                     # free fall
+    assert abs(a1 - (a ** -0.5 - dt / 2) ** -2) < 1e-12 * a1
+    dt, a1 = pm.next_timestep(a, 1.0, 0.0, n, 1e-6, 1e4, courant=0.5)
+    assert abs(dt - 0.5 / n / 1e4) < 1e-18                                    # velocity
+    dt, a1 = pm.next_timestep(a, 1.0, 0.0, n, 0.0, 0.0, courant=1.0, da_max=0.5, a_end=0.06)
+    assert a1 == 0.06 and abs(dt - 2 * (a ** -0.5 - 0.06 ** -0.5)) < 1e-12 * dt   # clipped at a_end

@@ -255,3 +255,35 @@ def test_c1_twenty_steps_positions_and_power(pm):
     kr, Pr, _ = power.power_spectrum(mesh.deposit_tsc(pos_ref, n), 64.0)
     sel = k < 0.5 * np.pi * n / 64.0
     assert np.abs(P[sel] / Pr[sel] - 1.0).max() < 1e-3
+
+
+@pytest.mark.parametrize("mu0,poisson", [(0.5, 0), (-0.5, 0), (0.5, 1)])
+def test_step_accelerations_parametrised_gravity(pm, mu0, poisson):
+    """Parametrised gravity (mu(a) = 1 + mu0 Omega_L(a)/Omega_L,0) with the
+    multigrid and the FFT_7pt solvers."""
+    n = 64
+    X, V = inputs.lpt_ics(n, float(n), 0.3, 0.7, 0.8, seed=9, order=2)
+    mgp = pm.default_mg(tol=1e-9)
+    acc, _ = gpu_accelerations(pm, X, V, n, 0.8, gravity="mu", boxsize=float(n), Om=0.3, OL=0.7, mg=mgp,
+                               mu0=mu0, poisson=poisson)
+    prm = step.PMParams(n=n, Om=0.3, OL=0.7, boxsize=float(n), gravity="mu", mu0=mu0)
+    ref, _, _ = step.accelerations(mesh.positions_from_fixed_point(X), 0.8, prm)
+    assert rel_l2(acc.T, ref) < 1e-5
+
+
+def test_adaptive_steps_match_oracle_on_their_schedule(pm):
+    """C1 with the §3.4 adaptive time step (free fall, velocity, 2% in a;
+    Courant factor 0.8) on the FFT_7pt solver: the final positions after the
+    GPU-chosen schedule against the oracle's KDK on the same schedule."""
+    n = 32
+    X, V = inputs.zeldovich_powerlaw_ics(n, seed=1)
+    sim = pm.Simulation(X, V, n, Om=1.0, OL=0.0, boxsize=64.0, track_ids=True, poisson=pm.PM_POISSON_FFT7)
+    a_steps = sim.run_adaptive(0.02, 0.2, courant=0.8, da_max=0.02)
+    assert len(a_steps) > 20 and a_steps[-1] == 0.2
+    assert all(a1 <= 1.02 * a0 * (1 + 1e-12) for a0, a1 in zip(a_steps[:-1], a_steps[1:]))
+    out = np.empty((3, n ** 3))
+    out[:, sim.particle_ids()] = mesh.positions_from_fixed_point(sim.positions()).T
+    ref, _ = step.run_kdk(mesh.positions_from_fixed_point(X), np.asarray(V, dtype=np.float32).T.astype(np.float64),
+                          a_steps, step.PMParams(n=n, Om=1.0, OL=0.0, boxsize=64.0), warm_start=False)
+    d = (out.T - ref + 0.5) % 1.0 - 0.5
+    assert np.sqrt((d ** 2).sum(1).mean()) * n < 1e-4

@@ -89,3 +89,25 @@ def test_power_spectrum_plane_wave_total():
     assert total[m - 1] == pytest.approx(L ** 3 * A ** 2 / 2, rel=1e-12)
     assert np.abs(np.delete(total, m - 1)).max() < 1e-20
     assert abs(k[m - 1] - 2 * np.pi * m / L) < 0.5 * 2 * np.pi / L   # mode-averaged shell wavenumber
+
+
+def test_parametrised_coupling_closed_forms():
+    from oracle.cosmology import mu_parametrised
+    # today mu = 1 + mu0 (Omega_Lambda(1) = Omega_Lambda,0); early times mu -> 1
+    assert abs(mu_parametrised(1.0, 0.3, 0.7, 0.4) - 1.4) < 1e-14
+    assert abs(mu_parametrised(1e-3, 0.3, 0.7, 0.4) - 1.0) < 1e-8
+    # Omega_Lambda(a) / Omega_Lambda,0 = 1 / E(a)^2
+    a = 0.5
+    assert abs(mu_parametrised(a, 0.3, 0.7, -0.5) - (1.0 - 0.5 / (0.3 / a ** 3 + 0.7))) < 1e-14
+
+
+def test_parametrised_accelerations_scale_with_mu():
+    """The parametrised source only rescales the Poisson equation, so the
+    accelerations are mu(a) times the Newtonian ones."""
+    from oracle.cosmology import mu_parametrised
+    rng = np.random.Generator(np.random.PCG64(7))
+    pos = rng.random((500, 3))
+    base = step.PMParams(n=16, Om=0.3, OL=0.7)
+    acc_n, _, _ = step.accelerations(pos, 0.6, base)
+    acc_m, _, _ = step.accelerations(pos, 0.6, step.PMParams(n=16, Om=0.3, OL=0.7, gravity="mu", mu0=0.3))
+    np.testing.assert_allclose(acc_m, mu_parametrised(0.6, 0.3, 0.7, 0.3) * acc_n, rtol=1e-12, atol=1e-15)
