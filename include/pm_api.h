@@ -200,7 +200,7 @@ pm_status pm_poisson_fft(const float* rho, float* phi, int n, int kind, double s
 typedef struct {
   double a;          /* scale factor                                          */
   double Om, OL;     /* density parameters today (flat)                       */
-  double fR0;        /* f_R0 < 0 (Hu-Sawicki, n = 1)                          */
+  double fR0;        /* f_R0 < 0 (Hu-Sawicki)                                  */
   double boxsize;    /* box size in Mpc/h (sets c~ = c / (H0 L))              */
   int cycle;         /* 0 = V-cycle, 1 = F-cycle (default: one F-cycle, §3.10) */
   int npre, npost, coarsest, coarse_max_sweeps;
@@ -209,6 +209,8 @@ typedef struct {
   double tol;        /* > 0: cycle until ||b - N(u)|| <= tol ||b|| (synchronises) */
   int max_cycles;
   int smoother;      /* as mg_params.smoother                                   */
+  int nhs;           /* Hu-Sawicki exponent n: 1 (cubic per cell) or 2 (quartic,
+                        §3.10); 0 is taken as 1                                 */
 } fr_params;
 
 void fr_default_params(fr_params* p);

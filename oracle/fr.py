@@ -1,17 +1,20 @@
-"""Hu-Sawicki f(R) scalaron (n = 1) in supercomoving units (oracle; test infrastructure only).
+"""Hu-Sawicki f(R) scalaron (n = 1 and n = 2) in supercomoving units (oracle; test infrastructure only).
 
 Units (§3.1, §3.10): f~_R = a^2 f_R; the background curvature in simulation units
 is R~ = 3 Omega_m (a^-3 + 4 Omega_L / Omega_m) (the 3 m^2 (...) of §2.x with
 m^2 L^2 = Omega_m / c~^2, the 1/c~^2 written explicitly in the equations); the
-background scalaron is f~_R = a^2 (R0/R)^(n+1) f_R0.  With u = (f~_R / fbar)^(1/2)
+background scalaron is f~_R = a^2 (R0/R)^(n+1) f_R0.  With u = (f~_R / fbar)^(1/(n+1))
 the field equation Eq. fr_sim_2 discretised with the 7-point Laplacian is
 
-    N_h(u) = (fbar / h^2) (L(u^2) - 6 u^2) - kappa (1/u - 1) = b,
+    N_h(u) = (fbar / h^2) (L(u^(n+1)) - 6 u^(n+1)) - kappa (1/u - 1) = b,
     kappa = a^4 R~ / (3 c~^2),   b = -(Omega_m a / c~^2) (rho~ - <rho~>)
 
-whose per-cell Gauss-Seidel update is the depressed cubic u^3 + p u + q = 0 of
-Eq. fr_depressed_equation with p = h^2 (b - kappa) / (6 fbar) - L(u^2)/6 and
-q = h^2 kappa / (6 fbar) (for b as above these are the paper's p and q).
+whose per-cell Gauss-Seidel update (multiply by h^2 u / (6 fbar)) is
+u^(n+2) + p u + q = 0 with p = h^2 (b - kappa) / (6 fbar) - L(u^(n+1))/6 and
+q = h^2 kappa / (6 fbar): the depressed cubic for n = 1 (Eq. cubic_equation)
+and the quartic for n = 2 (§3.10).  Eq. fr_depressed_equation prints the
+exponent as n + 1; both special cases the paper then solves have n + 2, which
+is what the algebra gives, and that is the reading used here.
 """
 from dataclasses import dataclass
 
@@ -28,14 +31,15 @@ class FRModel:
     OL: float = 0.7
     fR0: float = -1e-5
     boxsize: float = 512.0   # Mpc/h
+    n: int = 1               # Hu-Sawicki exponent (1 or 2)
 
 
 def background(a, model):
-    """(fbar, kappa, c~^2) at scale factor a (§2.x R-bar and f_R-bar with n = 1;
-    §3.10 units).  fbar < 0."""
+    """(fbar, kappa, c~^2) at scale factor a (§2.x R-bar and f_R-bar; §3.10
+    units).  fbar < 0."""
     Rbar = 3.0 * model.Om * (a ** -3.0 + 4.0 * model.OL / model.Om)
     Rbar0 = 3.0 * model.Om * (1.0 + 4.0 * model.OL / model.Om)
-    fbar = a * a * model.fR0 * (Rbar0 / Rbar) ** 2
+    fbar = a * a * model.fR0 * (Rbar0 / Rbar) ** (model.n + 1)
     c2 = c_tilde(model.boxsize) ** 2
     kappa = a ** 4 * Rbar / (3.0 * c2)
     return fbar, kappa, c2
@@ -66,23 +70,59 @@ def depressed_cubic_root(p, q):
     return out
 
 
-def operator(u, h, fbar, kappa):
+def depressed_quartic_root(p, q):
+    """Root of u^4 + p u + q = 0 by the closed form of §3.10 (n = 2):
+    Delta_0 = 12 q, Delta_1 = 27 p^2, Q = [(Delta_1 + sqrt(Delta_1^2 - 4 Delta_0^3))/2]^(1/3),
+    S = (1/2) sqrt((Q + Delta_0/Q)/3); u = -S + sqrt(-4S^2 + p/S)/2 for p > 0,
+    S + sqrt(-4S^2 - p/S)/2 for p < 0, (-q)^(1/4) for p = 0 and wherever
+    Delta_1^2 - 4 Delta_0^3 < 0 or Q + Delta_0/Q <= 0 (the paper's rule).
+    For q < 0 the root is the unique positive one.  Q + Delta_0/Q is formed as
+    (Q^3 - |Delta_0|^(3/2)) (Q + |Delta_0|^(1/2)) / (Q (Q^2 + Q |Delta_0|^(1/2) + |Delta_0|))
+    with Q^3 - |Delta_0|^(3/2) = (Delta_1 + Delta_1^2 / (sqrt(Delta_1^2 + 4|Delta_0|^3)
+    + 2 |Delta_0|^(3/2))) / 2: algebraically the printed expression, without the
+    cancellation it suffers for small p when Delta_0 < 0."""
+    p, q = np.broadcast_arrays(np.asarray(p, dtype=np.float64), np.asarray(q, dtype=np.float64))
+    out = np.power(-np.minimum(q, 0.0), 0.25)
+    d0 = 12.0 * q
+    d1 = 27.0 * p * p
+    disc = d1 * d1 - 4.0 * d0 ** 3
+    ok = (p != 0.0) & (disc >= 0.0) & (q < 0.0)
+    A = -d0[ok]                                              # |Delta_0| (Delta_0 < 0 for q < 0)
+    sq = np.sqrt(disc[ok])
+    Q3 = 0.5 * (d1[ok] + sq)
+    Q = np.cbrt(Q3)
+    rA = np.sqrt(A)
+    diff3 = 0.5 * (d1[ok] + d1[ok] ** 2 / (sq + 2.0 * A * rA))    # Q^3 - A^(3/2)
+    s_arg = diff3 * (Q + rA) / (Q * (Q * Q + Q * rA + A))         # Q + Delta_0 / Q
+    good = s_arg > 0.0
+    S = 0.5 * np.sqrt(np.where(good, s_arg, 1.0) / 3.0)
+    pp = p[ok]
+    r = np.where(pp > 0.0, -S + 0.5 * np.sqrt(np.maximum(-4.0 * S * S + pp / S, 0.0)),
+                 S + 0.5 * np.sqrt(np.maximum(-4.0 * S * S - pp / S, 0.0)))
+    sub = out[ok]
+    sub[good] = r[good]
+    out[ok] = sub
+    return out
+
+
+def operator(u, h, fbar, kappa, n=1):
     """N_h(u) (module docstring)."""
-    u2 = u * u
-    return (fbar / (h * h)) * (neighbour_sum(u2) - 6.0 * u2) - kappa * (1.0 / u - 1.0)
+    un = u ** (n + 1)
+    return (fbar / (h * h)) * (neighbour_sum(un) - 6.0 * un) - kappa * (1.0 / u - 1.0)
 
 
-def gs_sweep(u, b, h, fbar, kappa):
+def gs_sweep(u, b, h, fbar, kappa, n=1):
     """One red-black non-linear Gauss-Seidel sweep: each cell takes the root of
-    its cubic given its neighbours (§3.10; no over-relaxation for the
-    non-linear solver, Appendix C).  In place."""
+    its cubic (n = 1) or quartic (n = 2) given its neighbours (§3.10; no
+    over-relaxation for the non-linear solver, Appendix C).  In place."""
     par = parity(u.shape[0])
     beta = h * h / (6.0 * fbar)
     q = beta * kappa
+    root = depressed_cubic_root if n == 1 else depressed_quartic_root
     for colour in (0, 1):
-        p = beta * (b - kappa) - neighbour_sum(u * u) / 6.0
+        p = beta * (b - kappa) - neighbour_sum(u ** (n + 1)) / 6.0
         m = par == colour
-        u[m] = depressed_cubic_root(p[m], q)
+        u[m] = root(p[m], q)
     return u
 
 
@@ -95,15 +135,15 @@ class FASParams:
     coarse_max_sweeps: int = 200
 
 
-def _coarse(u, b, h, fbar, kappa, prm):
+def _coarse(u, b, h, fbar, kappa, prm, n=1):
     """Coarsest level: non-linear sweeps until the residual dropped by
     ``coarse_drop``, its running minimum stalls (no 0.1% gain in 5 sweeps),
     or ``coarse_max_sweeps``."""
-    r0 = best = np.linalg.norm(b - operator(u, h, fbar, kappa))
+    r0 = best = np.linalg.norm(b - operator(u, h, fbar, kappa, n))
     stale = 0
     for _ in range(prm.coarse_max_sweeps):
-        gs_sweep(u, b, h, fbar, kappa)
-        r = np.linalg.norm(b - operator(u, h, fbar, kappa))
+        gs_sweep(u, b, h, fbar, kappa, n)
+        r = np.linalg.norm(b - operator(u, h, fbar, kappa, n))
         if r <= prm.coarse_drop * r0:
             break
         if r < 0.999 * best:
@@ -115,40 +155,40 @@ def _coarse(u, b, h, fbar, kappa, prm):
     return u
 
 
-def _to_coarse(u, b, h, fbar, kappa, prm):
+def _to_coarse(u, b, h, fbar, kappa, prm, n=1):
     """Pre-smooth, then the FAS coarse problem (§3.6.2):
     u_H = R u_h, b_H = N_H(R u_h) + R d_h."""
     for _ in range(prm.npre):
-        gs_sweep(u, b, h, fbar, kappa)
-    d = b - operator(u, h, fbar, kappa)
+        gs_sweep(u, b, h, fbar, kappa, n)
+    d = b - operator(u, h, fbar, kappa, n)
     uH = restrict(u)
-    bH = operator(uH, 2.0 * h, fbar, kappa) + restrict(d)
+    bH = operator(uH, 2.0 * h, fbar, kappa, n) + restrict(d)
     return uH, uH.copy(), bH
 
 
-def fas_v_cycle(u, b, h, fbar, kappa, prm):
+def fas_v_cycle(u, b, h, fbar, kappa, prm, n=1):
     """FAS V-cycle (§3.6.2): coarse problem as in _to_coarse, recurse,
     u_h += P(u_H - R u_h), post-smooth.  In place."""
     if u.shape[0] <= prm.coarsest:
-        return _coarse(u, b, h, fbar, kappa, prm)
-    uH, RuH, bH = _to_coarse(u, b, h, fbar, kappa, prm)
-    fas_v_cycle(uH, bH, 2.0 * h, fbar, kappa, prm)
+        return _coarse(u, b, h, fbar, kappa, prm, n)
+    uH, RuH, bH = _to_coarse(u, b, h, fbar, kappa, prm, n)
+    fas_v_cycle(uH, bH, 2.0 * h, fbar, kappa, prm, n)
     u += prolong(uH - RuH)
     for _ in range(prm.npost):
-        gs_sweep(u, b, h, fbar, kappa)
+        gs_sweep(u, b, h, fbar, kappa, n)
     return u
 
 
-def fas_f_cycle(u, b, h, fbar, kappa, prm):
+def fas_f_cycle(u, b, h, fbar, kappa, prm, n=1):
     """FAS F-cycle: pre-smooth, restrict, F-cycle on the coarse level, prolong
     and correct, then one V-cycle on this level (the paper names F-cycles
     without defining them; this is the reading used throughout).  In place."""
     if u.shape[0] <= prm.coarsest:
-        return _coarse(u, b, h, fbar, kappa, prm)
-    uH, RuH, bH = _to_coarse(u, b, h, fbar, kappa, prm)
-    fas_f_cycle(uH, bH, 2.0 * h, fbar, kappa, prm)
+        return _coarse(u, b, h, fbar, kappa, prm, n)
+    uH, RuH, bH = _to_coarse(u, b, h, fbar, kappa, prm, n)
+    fas_f_cycle(uH, bH, 2.0 * h, fbar, kappa, prm, n)
     u += prolong(uH - RuH)
-    return fas_v_cycle(u, b, h, fbar, kappa, prm)
+    return fas_v_cycle(u, b, h, fbar, kappa, prm, n)
 
 
 def source(rho, a, model):
@@ -169,19 +209,20 @@ def fr_solve(rho, a, model, u0=None, prm=None, cycles=1, cycle="F", tol=None, ma
     b = source(rho, a, model)
     u = np.ones_like(rho) if u0 is None else np.array(u0, dtype=np.float64)
     step = fas_f_cycle if cycle == "F" else fas_v_cycle
-    hist = [np.linalg.norm(b - operator(u, h, fbar, kappa))]
+    nh = model.n
+    hist = [np.linalg.norm(b - operator(u, h, fbar, kappa, nh))]
     nb = np.linalg.norm(b)
     ncyc = max_cycles if tol is not None else cycles
     for _ in range(ncyc):
         if tol is not None and hist[-1] <= tol * nb:
             break
-        step(u, b, h, fbar, kappa, prm)
-        hist.append(np.linalg.norm(b - operator(u, h, fbar, kappa)))
+        step(u, b, h, fbar, kappa, prm, nh)
+        hist.append(np.linalg.norm(b - operator(u, h, fbar, kappa, nh)))
     return u, hist
 
 
 def scalaron_potential(u, a, model):
-    """-(c~^2/2) f~_R with f~_R = fbar u^2: the term that, added to the
+    """-(c~^2/2) f~_R with f~_R = fbar u^(n+1): the term that, added to the
     Newtonian potential, gives F = F_N + (c~^2/2) grad f~_R (§3.10)."""
     fbar, _, c2 = background(a, model)
-    return -0.5 * c2 * fbar * u * u
+    return -0.5 * c2 * fbar * u ** (model.n + 1)

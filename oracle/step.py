@@ -18,6 +18,7 @@ class PMParams:
     gravity: str = "newton"          # "newton", "fr" or "mu" (parametrised)
     fR0: float = -1e-5
     mu0: float = 0.0                 # parametrised gravity: coupling today
+    fr_n: int = 1                    # Hu-Sawicki exponent (1 or 2)
     grad_order: int = 5
     solver: str = "fft7"             # "fft7" (exact discrete inverse) or "mg"
     mg: MGParams = field(default_factory=MGParams)
@@ -49,7 +50,7 @@ def accelerations(pos, a, prm, phi_guess=None, u_guess=None):
     Phi = phi
     u = None
     if prm.gravity == "fr":
-        model = frmod.FRModel(Om=prm.Om, OL=prm.OL, fR0=prm.fR0, boxsize=prm.boxsize)
+        model = frmod.FRModel(Om=prm.Om, OL=prm.OL, fR0=prm.fR0, boxsize=prm.boxsize, n=prm.fr_n)
         u, _ = frmod.fr_solve(rho, a, model, u0=u_guess, cycles=prm.fr_cycles)
         Phi = phi + frmod.scalaron_potential(u, a, model)
     g = force_from_potential(Phi, h, prm.grad_order)

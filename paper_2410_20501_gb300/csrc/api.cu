@@ -176,7 +176,8 @@ bool valid_mg(const mg_params* p) {
 bool valid_fr(const fr_params* p) {
   return p && p->a > 0.0 && p->Om > 0.0 && p->fR0 < 0.0 && p->boxsize > 0.0 && p->npre >= 0 && p->npost >= 0 &&
          p->coarsest >= 4 && p->coarsest <= 16 && p->coarse_max_sweeps >= 0 && (p->cycle == 0 || p->cycle == 1) &&
-         (p->tol > 0.0 ? p->max_cycles >= 1 : p->cycles >= 0) && p->smoother >= 0 && p->smoother <= 2;
+         (p->tol > 0.0 ? p->max_cycles >= 1 : p->cycles >= 0) && p->smoother >= 0 && p->smoother <= 2 &&
+         p->nhs >= 0 && p->nhs <= 2;
 }
 
 // Adaptive Simpson quadrature of da / (a^3 E(a)).
@@ -255,6 +256,7 @@ void fr_default_params(fr_params* p) {
   p->tol = 0.0;
   p->max_cycles = 30;
   p->smoother = 2;
+  p->nhs = 1;
 }
 
 pm_status pm_sort(const uint32_t* X, int64_t np, int n, uint32_t* perm, uint32_t* cellstart, void* ws,
@@ -390,7 +392,7 @@ pm_status pm_step(pm_state* st_, const pm_step_params* prm, pm_stats* stats, voi
   // gathers of an interleaved float4 layout measured slower than three 4-byte ones
   const bool vec4 = false;
   PM_TRY(gradient_launch(S.phi, prm->gravity == PM_GRAVITY_FR ? S.eps : nullptr, alpha, w.g, n, prm->grad_order,
-                         vec4, s));
+                         vec4, s, 1, frp.nhs == 2 ? 2 : 1));
   double* max_out = prm->report_max ? w.scalars + 24 : nullptr;   // largest |a|, |v| for the time step
   PM_TRY(interp_launch(w.g, w.Xs, w.Vs, w.ids, np, n, S.acc, S.X, S.V, S.id, (float)prm->dt_kick,
                        (float)prm->dt_drift, 1, vec4, s, Batch{}, reinterpret_cast<float2*>(w.partials), max_out));

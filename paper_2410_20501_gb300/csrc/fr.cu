@@ -1,4 +1,11 @@
-// Hu-Sawicki f(R) scalaron (n = 1) by non-linear FAS multigrid (§3.6.2, §3.10).
+// Hu-Sawicki f(R) scalaron (n = 1 and n = 2) by non-linear FAS multigrid
+// (§3.6.2, §3.10).  The kernels are templates on the exponent NH; the text
+// below is for n = 1, and n = 2 follows the same pattern with u^3:
+//   N_h(eps) = (fbar/h^2) sum_nb (eps_nb - eps)(3 + 3 eps_nb + 3 eps + eps_nb^2
+//              + eps_nb eps + eps^2) + kappa eps/(1 + eps),
+//   eps^4 + 4 eps^3 + 6 eps^2 + c1 eps + c0 = 0, c1 = 3 + beta (b - kappa) - T/6,
+//   c0 = beta b - T/6, T = sum_nb eps_nb (3 + 3 eps_nb + eps_nb^2)
+// (u^4 + p u + q = 0, the quartic of §3.10, with u = 1 + eps).
 //
 // Unknown: eps = u - 1 with u = (f~_R / fbar)^(1/2).  Discrete operator
 //   N_h(eps) = (fbar/h^2) sum_nb (eps_nb - eps)(2 + eps_nb + eps) + kappa eps/(1 + eps)
@@ -38,36 +45,65 @@ __device__ __forceinline__ int64_t idx3(int i, int j, int k, int log2n) {
 // upper end is set from the bound u* <= sqrt(max(-p, 0)) + (-q)^(1/3),
 // p = c1 - 3, and the step falls back to bisection.  Stops when g is at its
 // float32 rounding level or the step is below 2e-7 relative.
+// g(e) of the cell equation in eps = u - 1 (NH = 1: cubic, NH = 2: quartic),
+// its derivative, half its second derivative, the float32 rounding level of
+// its evaluation, and an upper bound of the root (from u* <= sqrt(max(-p, 0))
+// + (-q)^(1/3) for the cubic, u* <= max(1, (|p| + |q|)^(1/3)) for the quartic).
+template <int NH> struct CellPoly;
+template <> struct CellPoly<1> {
+  __device__ static float g(float e, float c1, float c0) { return ((e + 3.0f) * e + c1) * e + c0; }
+  __device__ static float gp(float e, float c1) { return (3.0f * e + 6.0f) * e + c1; }
+  __device__ static float half_gpp(float e) { return 3.0f * e + 3.0f; }
+  __device__ static float noise(float e, float c1, float c0) {
+    const float e2 = e * e;
+    return 1.5e-7f * (fabsf(c0) + fabsf(c1 * e) + 3.0f * e2 + fabsf(e2 * e));
+  }
+  __device__ static float upper(float c1, float q, float lo) {
+    return fmaxf(sqrtf(fmaxf(3.0f - c1, 0.0f)) + cbrtf(-q) - 1.0f, lo);
+  }
+};
+template <> struct CellPoly<2> {
+  __device__ static float g(float e, float c1, float c0) { return (((e + 4.0f) * e + 6.0f) * e + c1) * e + c0; }
+  __device__ static float gp(float e, float c1) { return ((4.0f * e + 12.0f) * e + 12.0f) * e + c1; }
+  __device__ static float half_gpp(float e) { const float u = e + 1.0f; return 6.0f * u * u; }
+  __device__ static float noise(float e, float c1, float c0) {
+    const float e2 = e * e;
+    return 1.5e-7f * (fabsf(c0) + fabsf(c1 * e) + 6.0f * e2 + 4.0f * fabsf(e2 * e) + e2 * e2);
+  }
+  __device__ static float upper(float c1, float q, float lo) {
+    return fmaxf(fmaxf(cbrtf(fabsf(c1 - 4.0f) + fabsf(q)), 1.0f) - 1.0f, lo);
+  }
+};
+
+template <int NH>
 __device__ __forceinline__ float fr_root(float e, float c1, float c0, float q) {
+  using P = CellPoly<NH>;
   float lo = -1.0f, hi = __int_as_float(0x7f800000);  // +inf until needed
   if (!(e > lo)) e = 0.0f;
   {
     // fast path: two plain Newton steps from the current value; accepted when
     // the remaining error is at float32 resolution and the root is admissible
-    const float g0 = ((e + 3.0f) * e + c1) * e + c0, gp0 = (3.0f * e + 6.0f) * e + c1;
+    const float g0 = P::g(e, c1, c0), gp0 = P::gp(e, c1);
     const float e1 = e - __fdividef(g0, gp0);
-    const float g1 = ((e1 + 3.0f) * e1 + c1) * e1 + c0, gp1 = (3.0f * e1 + 6.0f) * e1 + c1;
+    const float g1 = P::g(e1, c1, c0), gp1 = P::gp(e1, c1);
     const float e2 = e1 - __fdividef(g1, gp1);
     // Newton's error after the second step is about K d^2, d = e2 - e1,
-    // K = g''/(2 g') = (3 e1 + 3) / g'(e1): accept when that is below float32
-    // resolution of e2
+    // K = g''/(2 g'): accept when that is below float32 resolution of e2
     const float d = e2 - e1;
-    if (gp0 > 0.0f && gp1 > 0.0f && e2 > lo && d * d * (3.0f * e1 + 3.0f) <= (1e-7f * fabsf(e2) + 1e-20f) * gp1)
+    if (gp0 > 0.0f && gp1 > 0.0f && e2 > lo && d * d * P::half_gpp(e1) <= (1e-7f * fabsf(e2) + 1e-20f) * gp1)
       return e2;
     if (gp1 > 0.0f && e2 > lo) e = e2;   // continue from the better point
   }
   for (int it = 0; it < 30; ++it) {
-    const float e2 = e * e;
-    const float g = ((e + 3.0f) * e + c1) * e + c0;
-    const float gp = (3.0f * e + 6.0f) * e + c1;
+    const float g = P::g(e, c1, c0);
+    const float gp = P::gp(e, c1);
     if (g > 0.0f) hi = fminf(hi, e);
     else if (g < 0.0f) lo = fmaxf(lo, e);
     else return e;
-    const float noise = 1.5e-7f * (fabsf(c0) + fabsf(c1 * e) + 3.0f * e2 + fabsf(e2 * e));
-    if (fabsf(g) <= noise) return e;
+    if (fabsf(g) <= P::noise(e, c1, c0)) return e;
     float en = gp > 0.0f ? e - __fdividef(g, gp) : lo;
     if (!(en > lo && en < hi)) {
-      if (isinf(hi)) hi = fmaxf(sqrtf(fmaxf(3.0f - c1, 0.0f)) + cbrtf(-q) - 1.0f, lo);
+      if (isinf(hi)) hi = P::upper(c1, q, lo);
       en = 0.5f * (lo + hi);
     }
     if (fabsf(en - e) <= 2e-7f * fabsf(en) + 1e-12f) return en;
@@ -86,24 +122,37 @@ __device__ __forceinline__ void load_nb(const float* u, int i, int j, int k, int
   nb[5] = u[idx3(i, j, (k - 1) & m, log2n)];
 }
 
+// N_h(eps) at one cell: (fbar/h^2) sum_nb (u_nb^(n+1) - u^(n+1)) written in
+// differences, plus kappa eps/(1 + eps).
+template <int NH>
 __device__ __forceinline__ float fr_op(float ec, const float nb[6], float alpha, float kappa) {
   float L = 0.0f;
 #pragma unroll
-  for (int q = 0; q < 6; ++q) L = fmaf(nb[q] - ec, 2.0f + nb[q] + ec, L);
+  for (int q = 0; q < 6; ++q) {
+    if (NH == 1) {
+      L = fmaf(nb[q] - ec, 2.0f + nb[q] + ec, L);
+    } else {   // u_nb^3 - u^3 = (e_nb - e)(3 + 3 (e_nb + e) + e_nb^2 + e_nb e + e^2)
+      const float s = nb[q] + ec;
+      L = fmaf(nb[q] - ec, fmaf(3.0f, s, 3.0f) + fmaf(nb[q], s, ec * ec), L);
+    }
+  }
   return alpha * L + kappa * ec / (1.0f + ec);
 }
 
+template <int NH>
 __device__ __forceinline__ float fr_update(float ec, const float nb[6], float bv, float beta, float kappa,
                                            float q) {
   float S = 0.0f;
 #pragma unroll
-  for (int t = 0; t < 6; ++t) S = fmaf(nb[t], 2.0f + nb[t], S);
+  for (int t = 0; t < 6; ++t)
+    S = NH == 1 ? fmaf(nb[t], 2.0f + nb[t], S) : fmaf(nb[t], fmaf(nb[t], 3.0f + nb[t], 3.0f), S);
   const float S6 = S * (1.0f / 6.0f);
-  const float c1 = 2.0f + beta * (bv - kappa) - S6;
+  const float c1 = (NH == 1 ? 2.0f : 3.0f) + beta * (bv - kappa) - S6;
   const float c0 = beta * bv - S6;
-  return fr_root(ec, c1, c0, q);
+  return fr_root<NH>(ec, c1, c0, q);
 }
 
+template <int NH>
 __global__ void __launch_bounds__(256) k_fr_sweep(float* __restrict__ e, Src b, int log2n, int colour, float beta,
                                                   float kappa, float q) {
   const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -119,10 +168,11 @@ __global__ void __launch_bounds__(256) k_fr_sweep(float* __restrict__ e, Src b, 
 #pragma unroll
   for (int r = 0; r < 6; ++r) nb[r] = e[qi[r]];
   const float bv = b.s * (__ldg(b.p + c) - load_mean(b));
-  e[c] = fr_update(e[c], nb, bv, beta, kappa, q);
+  e[c] = fr_update<NH>(e[c], nb, bv, beta, kappa, q);
 }
 
 // eH = rH = R eps, bH = R(b - N_h eps).
+template <int NH>
 __global__ void k_fr_restrict(const float* __restrict__ e, Src b, int log2n, float alpha, float kappa,
                               float* __restrict__ eH, float* __restrict__ rH, float* __restrict__ bH) {
   const int lc = log2n - 1, mc = (1 << lc) - 1;
@@ -146,7 +196,7 @@ __global__ void k_fr_restrict(const float* __restrict__ e, Src b, int log2n, flo
           child_nb(core, xf, yf, a, bb, cc, nb);
           const float ec = core[a][bb][cc + 1];
           se += ec;
-          sd += bz[cc] - fr_op(ec, nb, alpha, kappa);
+          sd += bz[cc] - fr_op<NH>(ec, nb, alpha, kappa);
         }
       }
     eH[t] = 0.125f * se;
@@ -156,6 +206,7 @@ __global__ void k_fr_restrict(const float* __restrict__ e, Src b, int log2n, flo
 }
 
 // bH += N_H(eH).
+template <int NH>
 __global__ void k_fr_coarse_op(const float* __restrict__ eH, float* __restrict__ bH, int log2n, float alpha,
                                float kappa) {
   const int m = (1 << log2n) - 1;
@@ -165,10 +216,11 @@ __global__ void k_fr_coarse_op(const float* __restrict__ eH, float* __restrict__
     const int k = (int)(c & m), j = (int)((c >> log2n) & m), i = (int)(c >> (2 * log2n));
     float nb[6];
     load_nb(eH, i, j, k, log2n, nb);
-    bH[c] += fr_op(eH[c], nb, alpha, kappa);
+    bH[c] += fr_op<NH>(eH[c], nb, alpha, kappa);
   }
 }
 
+template <int NH>
 __global__ void __launch_bounds__(256) k_fr_norm(const float* __restrict__ e, Src b, int log2n, float alpha,
                                                  float kappa, double* __restrict__ partial) {
   __shared__ double scratch[32];
@@ -182,7 +234,7 @@ __global__ void __launch_bounds__(256) k_fr_norm(const float* __restrict__ e, Sr
     float nb[6];
     load_nb(e, i, j, k, log2n, nb);
     const float bv = src_at(b, c, mean);
-    const float d = bv - fr_op(e[c], nb, alpha, kappa);
+    const float d = bv - fr_op<NH>(e[c], nb, alpha, kappa);
     kahan_add(sd, cd, d * d);
     kahan_add(sb, cb, bv * bv);
   }
@@ -193,6 +245,7 @@ __global__ void __launch_bounds__(256) k_fr_norm(const float* __restrict__ e, Sr
 // Coarsest level (n <= 16) in one CTA: non-linear sweeps until the residual
 // dropped by `drop`, its running minimum stalls for 5 sweeps (float32 floor), or
 // `max_sweeps` sweeps.
+template <int NH>
 __global__ void __launch_bounds__(1024) k_fr_coarse(float* __restrict__ e, Src b, int log2n, float alpha,
                                                     float beta, float kappa, float q, int max_sweeps,
                                                     float drop) {
@@ -220,7 +273,7 @@ __global__ void __launch_bounds__(1024) k_fr_coarse(float* __restrict__ e, Src b
     for (int c = threadIdx.x; c < N; c += blockDim.x) {
       float nb[6];
       nbs(c, nb);
-      const float d = sbv[c] - fr_op(se[c], nb, alpha, kappa);
+      const float d = sbv[c] - fr_op<NH>(se[c], nb, alpha, kappa);
       kahan_add(s, cmp, d * d);
     }
     block_sum_to(&r2, s, cmp, scratch);
@@ -236,7 +289,7 @@ __global__ void __launch_bounds__(1024) k_fr_coarse(float* __restrict__ e, Src b
         if (((i + j + k) & 1) != colour) continue;
         float nb[6];
         nbs(c, nb);
-        se[c] = fr_update(se[c], nb, sbv[c], beta, kappa, q);
+        se[c] = fr_update<NH>(se[c], nb, sbv[c], beta, kappa, q);
       }
       __syncthreads();
     }
@@ -253,11 +306,12 @@ __global__ void __launch_bounds__(1024) k_fr_coarse(float* __restrict__ e, Src b
 }
 
 // The non-linear Gauss-Seidel update as a functor for the streaming smoother.
+template <int NH>
 struct FRUpdate {
   float beta, kappa, q;
   __device__ __forceinline__ FRUpdate box(int) const { return *this; }
   __device__ __forceinline__ float operator()(float old, const float nb[6], float bv, int, bool, bool) const {
-    return fr_update(old, nb, bv, beta, kappa, q);
+    return fr_update<NH>(old, nb, bv, beta, kappa, q);
   }
 };
 
@@ -270,7 +324,20 @@ struct FR {
   float* r[12];
   Src b[12];
   double fbar, kappa;
+  int nh;           // Hu-Sawicki exponent (1 or 2)
 };
+
+// Runs the statement with the compile-time exponent NH of f.
+#define FR_NH(f, ...)                      \
+  do {                                     \
+    if ((f).nh == 2) {                     \
+      constexpr int NH = 2;                \
+      __VA_ARGS__;                         \
+    } else {                               \
+      constexpr int NH = 1;                \
+      __VA_ARGS__;                         \
+    }                                      \
+  } while (0)
 
 struct LevelConst {
   int n, log2n;
@@ -289,21 +356,28 @@ LevelConst level_const(const FR& f, int l) {
   return c;
 }
 
-pm_status stream_attributes() {
+template <int NH>
+pm_status stream_attributes_nh() {
   static bool done = false;
   if (!done) {
-    PM_TRY(cuda_status(cudaFuncSetAttribute(k_rb_stream<2, FRUpdate>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    PM_TRY(cuda_status(cudaFuncSetAttribute(k_rb_stream<2, FRUpdate<NH>>,
+                                            cudaFuncAttributeMaxDynamicSharedMemorySize,
                                             (int)StreamGeom<2>::smem_bytes)));
-    PM_TRY(cuda_status(cudaFuncSetAttribute(k_rb_stream<1, FRUpdate>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    PM_TRY(cuda_status(cudaFuncSetAttribute(k_rb_stream<1, FRUpdate<NH>>,
+                                            cudaFuncAttributeMaxDynamicSharedMemorySize,
                                             (int)StreamGeom<1>::smem_bytes)));
-    PM_TRY(cuda_status(cudaFuncSetAttribute((k_rb_fused<FRUpdate, 2, 1>), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                            (int)kFusedSmem)));
+    PM_TRY(cuda_status(cudaFuncSetAttribute((k_rb_fused<FRUpdate<NH>, 2, 1>),
+                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFusedSmem)));
     done = true;
   }
   return PM_OK;
 }
 
-pm_status fr_smooth(FR& f, int l, int count) {
+pm_status stream_attributes(int nh) { return nh == 2 ? stream_attributes_nh<2>() : stream_attributes_nh<1>(); }
+
+template <int NH>
+pm_status fr_smooth_nh(FR& f, int l, int count) {
+  using FRUpdate = ::pmgb::FRUpdate<NH>;
   const LevelConst c = level_const(f, l);
   const double N = (double)c.n * c.n * c.n;
   if (f.p->smoother == 0 && stream_ok(c.n) && f.alt[l]) {
@@ -342,9 +416,13 @@ pm_status fr_smooth(FR& f, int l, int count) {
   const unsigned grid = grid_for(((int64_t)c.n * c.n * c.n) / 2, 256);
   for (int it = 0; it < count; ++it)
     for (int colour = 0; colour < 2; ++colour)
-      PM_LAUNCH(l == 0 ? K_FR_SMOOTH0 : K_FR_SMOOTH, 6.0 * N, k_fr_sweep, grid, 256, 0, f.s, f.e[l], f.b[l], c.log2n, colour, c.beta, c.kappa,
-                c.q);
+      PM_LAUNCH(l == 0 ? K_FR_SMOOTH0 : K_FR_SMOOTH, 6.0 * N, k_fr_sweep<NH>, grid, 256, 0, f.s, f.e[l], f.b[l],
+                c.log2n, colour, c.beta, c.kappa, c.q);
   return PM_OK;
+}
+
+pm_status fr_smooth(FR& f, int l, int count) {
+  return f.nh == 2 ? fr_smooth_nh<2>(f, l, count) : fr_smooth_nh<1>(f, l, count);
 }
 
 bool is_coarsest(const FR& f, int l) {
@@ -354,8 +432,8 @@ bool is_coarsest(const FR& f, int l) {
 
 pm_status fr_coarse(FR& f, int l) {
   const LevelConst c = level_const(f, l);
-  PM_LAUNCH(K_FR_COARSE, 12.0 * c.n * c.n * (double)c.n, k_fr_coarse, 1, 1024, 0, f.s, f.e[l], f.b[l], c.log2n, c.alpha, c.beta, c.kappa,
-            c.q, f.p->coarse_max_sweeps, f.p->coarse_drop);
+  FR_NH(f, PM_LAUNCH(K_FR_COARSE, 12.0 * c.n * c.n * (double)c.n, k_fr_coarse<NH>, 1, 1024, 0, f.s, f.e[l], f.b[l],
+                     c.log2n, c.alpha, c.beta, c.kappa, c.q, f.p->coarse_max_sweeps, f.p->coarse_drop));
   return PM_OK;
 }
 
@@ -364,10 +442,10 @@ pm_status fr_to_coarse(FR& f, int l) {
   PM_TRY(fr_smooth(f, l, f.p->npre));
   const LevelConst c = level_const(f, l), cH = level_const(f, l + 1);
   const int64_t nc = (int64_t)cH.n * cH.n * cH.n;
-  PM_LAUNCH(K_FR_RESTRICT, 76.0 * nc, k_fr_restrict, grid_for(nc, 256), 256, 0, f.s, f.e[l], f.b[l], c.log2n, c.alpha,
-            c.kappa, f.e[l + 1], f.r[l + 1], const_cast<float*>(f.b[l + 1].p));
-  PM_LAUNCH(K_FR_COARSEOP, 12.0 * nc, k_fr_coarse_op, grid_for(nc, 256), 256, 0, f.s, f.e[l + 1],
-            const_cast<float*>(f.b[l + 1].p), cH.log2n, cH.alpha, cH.kappa);
+  FR_NH(f, PM_LAUNCH(K_FR_RESTRICT, 76.0 * nc, k_fr_restrict<NH>, grid_for(nc, 256), 256, 0, f.s, f.e[l], f.b[l],
+                     c.log2n, c.alpha, c.kappa, f.e[l + 1], f.r[l + 1], const_cast<float*>(f.b[l + 1].p)));
+  FR_NH(f, PM_LAUNCH(K_FR_COARSEOP, 12.0 * nc, k_fr_coarse_op<NH>, grid_for(nc, 256), 256, 0, f.s, f.e[l + 1],
+                     const_cast<float*>(f.b[l + 1].p), cH.log2n, cH.alpha, cH.kappa));
   return PM_OK;
 }
 
@@ -394,7 +472,7 @@ void fr_background(const fr_params& p, double* fbar, double* kappa, double* c2) 
   const double Rbar = 3.0 * p.Om * (1.0 / (a * a * a) + 4.0 * p.OL / p.Om);
   const double Rbar0 = 3.0 * p.Om * (1.0 + 4.0 * p.OL / p.Om);
   const double ratio = Rbar0 / Rbar;
-  *fbar = a * a * p.fR0 * ratio * ratio;
+  *fbar = a * a * p.fR0 * (p.nhs == 2 ? ratio * ratio * ratio : ratio * ratio);   // (R0/R)^(n+1)
   const double ct = 299792.458 / (100.0 * p.boxsize);
   *c2 = ct * ct;
   *kappa = a * a * a * a * Rbar / (3.0 * *c2);
@@ -417,7 +495,8 @@ pm_status fr_solve_src(Src b, float* eps, int n, const fr_params& prm, mg_stats*
     }
     f.alt[l] = w.fr_alt[l];
   }
-  PM_TRY(stream_attributes());
+  f.nh = prm.nhs == 2 ? 2 : 1;
+  PM_TRY(stream_attributes(f.nh));
   double c2;
   fr_background(prm, &f.fbar, &f.kappa, &c2);
   mg_stats local{PM_OK, 0, -1.0, -1.0, -1.0};
@@ -444,7 +523,8 @@ pm_status fr_solve_src(Src b, float* eps, int n, const fr_params& prm, mg_stats*
   for (int c = 0; c < prm.max_cycles; ++c) {
     PM_TRY(one());
     local.cycles = c + 1;
-    PM_LAUNCH(K_FR_NORM, 8.0 * N, k_fr_norm, nb, 256, 0, s, eps, b, c0.log2n, c0.alpha, c0.kappa, w.partials);
+    FR_NH(f, PM_LAUNCH(K_FR_NORM, 8.0 * N, k_fr_norm<NH>, nb, 256, 0, s, eps, b, c0.log2n, c0.alpha, c0.kappa,
+                       w.partials));
     PM_TRY(reduce_partials(w.partials, nb, nb, 2, 1.0, w.scalars + 8, s));
     double h[2];
     PM_TRY(fetch_scalars(w.scalars + 8, h, 2, s));

@@ -17,13 +17,15 @@ __device__ __forceinline__ int64_t idx3(int i, int j, int k, int log2n) {
   return ((int64_t)i << (2 * log2n)) | ((int64_t)j << log2n) | k;
 }
 
+// phi + alpha (u^(n+1) - 1), u = 1 + eps: the combined potential up to a
+// constant (alpha = -(c~^2/2) fbar; n = nh, 1 or 2).
 template <bool FR>
 __device__ __forceinline__ float pot(const float* __restrict__ phi, const float* __restrict__ eps, float alpha,
-                                     int64_t c) {
+                                     int64_t c, int nh) {
   float v = __ldg(phi + c);
   if (FR) {
     const float e = __ldg(eps + c);
-    v = fmaf(alpha, e * (2.0f + e), v);
+    v = fmaf(alpha, nh == 2 ? e * fmaf(e, 3.0f + e, 3.0f) : e * (2.0f + e), v);
   }
   return v;
 }
@@ -43,7 +45,7 @@ template <> struct Stencil<7> {
 
 template <int ORDER, bool FR>
 __global__ void k_gradient(const float* __restrict__ phi, const float* __restrict__ eps, float alpha,
-                           float* __restrict__ g, int log2n, float inv_h) {
+                           float* __restrict__ g, int log2n, float inv_h, int nh) {
   const int m = (1 << log2n) - 1;
   const int64_t total = (int64_t)1 << (3 * log2n);
   phi += (int64_t)blockIdx.z * total;          // the box of a batched launch
@@ -56,12 +58,12 @@ __global__ void k_gradient(const float* __restrict__ phi, const float* __restric
 #pragma unroll
     for (int q = Stencil<ORDER>::R; q >= 1; --q) {
       const float w = Stencil<ORDER>::c(q);
-      gx = fmaf(w, pot<FR>(phi, eps, alpha, idx3((i + q) & m, j, k, log2n)) -
-                       pot<FR>(phi, eps, alpha, idx3((i - q) & m, j, k, log2n)), gx);
-      gy = fmaf(w, pot<FR>(phi, eps, alpha, idx3(i, (j + q) & m, k, log2n)) -
-                       pot<FR>(phi, eps, alpha, idx3(i, (j - q) & m, k, log2n)), gy);
-      gz = fmaf(w, pot<FR>(phi, eps, alpha, idx3(i, j, (k + q) & m, log2n)) -
-                       pot<FR>(phi, eps, alpha, idx3(i, j, (k - q) & m, log2n)), gz);
+      gx = fmaf(w, pot<FR>(phi, eps, alpha, idx3((i + q) & m, j, k, log2n), nh) -
+                       pot<FR>(phi, eps, alpha, idx3((i - q) & m, j, k, log2n), nh), gx);
+      gy = fmaf(w, pot<FR>(phi, eps, alpha, idx3(i, (j + q) & m, k, log2n), nh) -
+                       pot<FR>(phi, eps, alpha, idx3(i, (j - q) & m, k, log2n), nh), gy);
+      gz = fmaf(w, pot<FR>(phi, eps, alpha, idx3(i, j, (k + q) & m, log2n), nh) -
+                       pot<FR>(phi, eps, alpha, idx3(i, j, (k - q) & m, log2n), nh), gz);
     }
     const int64_t N = total;
     g[c] = -gx * inv_h;
@@ -81,7 +83,7 @@ template <int ORDER, bool FR, bool VEC4>
 __global__ void __launch_bounds__(GNT) k_gradient_stream(const float* __restrict__ phi,
                                                         const float* __restrict__ eps, float alpha,
                                                         float* __restrict__ g, int log2n, float inv_h,
-                                                        int chunk, int nitems) {
+                                                        int chunk, int nitems, int nh) {
   constexpr int R = Stencil<ORDER>::R, W = 2 * R + 1, EY = GTY + 2 * R, EZ = GTZ + 2 * R, PL = EY * EZ;
   extern __shared__ float P[];   // [W][EY][EZ]
   const int n = 1 << log2n, m = n - 1;
@@ -100,7 +102,7 @@ __global__ void __launch_bounds__(GNT) k_gradient_stream(const float* __restrict
       const int64_t pb = (int64_t)(t & m) << (2 * log2n);
       for (int e = tid; e < PL; e += GNT) {
         const int ly = e / EZ, lz = e - ly * EZ;
-        Pt[e] = pot<FR>(phi, eps, alpha, pb | ((int64_t)((y0 - R + ly) & m) << log2n) | ((z0 - R + lz) & m));
+        Pt[e] = pot<FR>(phi, eps, alpha, pb | ((int64_t)((y0 - R + ly) & m) << log2n) | ((z0 - R + lz) & m), nh);
       }
       __syncthreads();
       const int xo = t - R;
@@ -136,7 +138,7 @@ __global__ void __launch_bounds__(GNT) k_gradient_stream(const float* __restrict
 
 // Inverse TSC; mode 1 also kicks and drifts.  Particles are read in cell
 // order (Xs, Vs) and written in the same order (Xo, Vo).
-template <bool VEC4>
+template <bool VEC4, bool MAXES>
 __global__ void __launch_bounds__(256) k_interp_kdk(const float* __restrict__ g, const uint32_t* __restrict__ Xs,
                                                     const float* __restrict__ Vs,
                                                     const uint32_t* __restrict__ ids_in, int64_t np, int log2n,
@@ -193,7 +195,7 @@ __global__ void __launch_bounds__(256) k_interp_kdk(const float* __restrict__ g,
       acc[np + p] = ay;
       acc[2 * np + p] = az;
     }
-    if (blockmax) amax = fmaxf(amax, sqrtf(fmaf(ax, ax, fmaf(ay, ay, az * az))));
+    if (MAXES) amax = fmaxf(amax, sqrtf(fmaf(ax, ax, fmaf(ay, ay, az * az))));
     if (mode == 1) {
       const float vx = fmaf(ax, dt_kick, __ldg(Vs + p));
       const float vy = fmaf(ay, dt_kick, __ldg(Vs + np + p));
@@ -201,14 +203,14 @@ __global__ void __launch_bounds__(256) k_interp_kdk(const float* __restrict__ g,
       Vo[p] = vx;
       Vo[np + p] = vy;
       Vo[2 * np + p] = vz;
-      if (blockmax) vmax = fmaxf(vmax, sqrtf(fmaf(vx, vx, fmaf(vy, vy, vz * vz))));
+      if (MAXES) vmax = fmaxf(vmax, sqrtf(fmaf(vx, vx, fmaf(vy, vy, vz * vz))));
       Xo[p] = x + (uint32_t)__float2int_rn(vx * drift_scale);
       Xo[np + p] = y + (uint32_t)__float2int_rn(vy * drift_scale);
       Xo[2 * np + p] = z + (uint32_t)__float2int_rn(vz * drift_scale);
       if (ids_out) ids_out[p] = __ldg(ids_in + p);
     }
   }
-  if (blockmax) {   // block maxima (non-negative floats order like their bit patterns)
+  if (MAXES) {   // block maxima (non-negative floats order like their bit patterns)
     __shared__ unsigned wa[8], wv[8];
     const unsigned ua = __reduce_max_sync(0xffffffffu, __float_as_uint(amax));
     const unsigned uv = __reduce_max_sync(0xffffffffu, __float_as_uint(vmax));
@@ -258,7 +260,7 @@ __global__ void __launch_bounds__(1024) k_max_pairs(const float2* __restrict__ v
 
 template <int ORDER>
 pm_status launch_grad(const float* phi, const float* eps, float alpha, float* g, int n, bool vec4, cudaStream_t s,
-                      int B) {
+                      int B, int nh) {
   const int64_t N = (int64_t)n * n * n;
   const double bytes = ((eps ? 8.0 : 4.0) * N + (vec4 ? 16.0 : 12.0) * N) * B;
   if (n >= 64) {
@@ -273,7 +275,7 @@ pm_status launch_grad(const float* phi, const float* eps, float alpha, float* g,
     const dim3 grid(gx, 1, (unsigned)B);
 #define PM_GRAD_STREAM(FRB, V4)                                                                                    \
   PM_LAUNCH(K_GRADIENT, bytes, (k_gradient_stream<ORDER, FRB, V4>), grid, GNT, smem, s, phi, eps, alpha, g, ilog2(n), \
-            (float)n, chunk, nitems)
+            (float)n, chunk, nitems, nh)
     if (eps) {
       if (vec4) PM_GRAD_STREAM(true, true); else PM_GRAD_STREAM(true, false);
     } else {
@@ -285,19 +287,21 @@ pm_status launch_grad(const float* phi, const float* eps, float alpha, float* g,
   if (vec4) return PM_EINVAL;
   const dim3 grid(grid_for(N, 256), 1, (unsigned)B);
   if (eps)
-    PM_LAUNCH(K_GRADIENT, bytes, (k_gradient<ORDER, true>), grid, 256, 0, s, phi, eps, alpha, g, ilog2(n), (float)n);
+    PM_LAUNCH(K_GRADIENT, bytes, (k_gradient<ORDER, true>), grid, 256, 0, s, phi, eps, alpha, g, ilog2(n), (float)n,
+              nh);
   else
-    PM_LAUNCH(K_GRADIENT, bytes, (k_gradient<ORDER, false>), grid, 256, 0, s, phi, eps, alpha, g, ilog2(n), (float)n);
+    PM_LAUNCH(K_GRADIENT, bytes, (k_gradient<ORDER, false>), grid, 256, 0, s, phi, eps, alpha, g, ilog2(n), (float)n,
+              nh);
   return launch_status();
 }
 
 }  // namespace
 
 pm_status gradient_launch(const float* phi, const float* eps, float alpha, float* g, int n, int order, bool vec4,
-                          cudaStream_t s, int batch) {
-  if (order == 3) return launch_grad<3>(phi, eps, alpha, g, n, vec4, s, batch);
-  if (order == 5) return launch_grad<5>(phi, eps, alpha, g, n, vec4, s, batch);
-  if (order == 7) return launch_grad<7>(phi, eps, alpha, g, n, vec4, s, batch);
+                          cudaStream_t s, int batch, int nh) {
+  if (order == 3) return launch_grad<3>(phi, eps, alpha, g, n, vec4, s, batch, nh);
+  if (order == 5) return launch_grad<5>(phi, eps, alpha, g, n, vec4, s, batch, nh);
+  if (order == 7) return launch_grad<7>(phi, eps, alpha, g, n, vec4, s, batch, nh);
   return PM_EINVAL;
 }
 
@@ -312,12 +316,15 @@ pm_status interp_launch(const float* g, const uint32_t* Xs, const float* Vs, con
   const int64_t np_box = bt.B > 1 ? bt.np_box : np;
   const dim3 grid(grid_for(np_box, 256), 1, (unsigned)bt.B);
   if (!max_out) blockmax = nullptr;
-  if (vec4)
-    PM_LAUNCH(K_INTERP, bytes, k_interp_kdk<true>, grid, 256, 0, s, g, Xs, Vs, ids_in, np, ilog2(n), acc,
-              Xo, Vo, ids_out, dt_kick, drift_scale, mode, np_box, bt.dt_kick, bt.dt_drift, blockmax);
-  else
-    PM_LAUNCH(K_INTERP, bytes, k_interp_kdk<false>, grid, 256, 0, s, g, Xs, Vs, ids_in, np, ilog2(n),
-              acc, Xo, Vo, ids_out, dt_kick, drift_scale, mode, np_box, bt.dt_kick, bt.dt_drift, blockmax);
+#define PM_INTERP(V4, MX)                                                                                       \
+  PM_LAUNCH(K_INTERP, bytes, (k_interp_kdk<V4, MX>), grid, 256, 0, s, g, Xs, Vs, ids_in, np, ilog2(n), acc, Xo, Vo, \
+            ids_out, dt_kick, drift_scale, mode, np_box, bt.dt_kick, bt.dt_drift, blockmax)
+  if (vec4) {
+    if (blockmax) PM_INTERP(true, true); else PM_INTERP(true, false);
+  } else {
+    if (blockmax) PM_INTERP(false, true); else PM_INTERP(false, false);
+  }
+#undef PM_INTERP
   if (blockmax) {
     const int64_t nb = (int64_t)grid.x * grid.z;
     PM_LAUNCH(K_REDUCE, 8.0 * nb, k_max_pairs, 1, 1024, 0, s, blockmax, nb, max_out);

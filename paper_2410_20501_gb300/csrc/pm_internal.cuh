@@ -152,10 +152,10 @@ pm_status prolong_correct_launch(float* u, const float* uc, const float* uc2, in
 // Background constants of the f(R) equation (host, float64).
 void fr_background(const fr_params& p, double* fbar, double* kappa, double* c2);
 
-// g = -grad(phi [+ alpha (2 eps + eps^2)]); vec4: g interleaved as float4
+// g = -grad(phi [+ alpha ((1 + eps)^(nh+1) - 1)]); vec4: g interleaved as float4
 // (gx, gy, gz, 0) per cell (n >= 64 only), else three planes.
 pm_status gradient_launch(const float* phi, const float* eps, float alpha, float* g, int n,
-                          int order, bool vec4, cudaStream_t s, int batch = 1);
+                          int order, bool vec4, cudaStream_t s, int batch = 1, int nh = 1);
 // mode 0: acc only; mode 1: kick + drift into Xo/Vo (and acc if non-NULL);
 // vec4: g interleaved as float4.  With max_out (2 doubles, device) also the
 // largest |a| and |v after the kick| (blockmax: one float2 per block).

@@ -56,7 +56,8 @@ class fr_params(ctypes.Structure):
                 ("fR0", ctypes.c_double), ("boxsize", ctypes.c_double), ("cycle", ctypes.c_int),
                 ("npre", ctypes.c_int), ("npost", ctypes.c_int), ("coarsest", ctypes.c_int),
                 ("coarse_max_sweeps", ctypes.c_int), ("coarse_drop", ctypes.c_float), ("cycles", ctypes.c_int),
-                ("tol", ctypes.c_double), ("max_cycles", ctypes.c_int), ("smoother", ctypes.c_int)]
+                ("tol", ctypes.c_double), ("max_cycles", ctypes.c_int), ("smoother", ctypes.c_int),
+                ("nhs", ctypes.c_int)]
 
 
 class pm_state(ctypes.Structure):

@@ -287,3 +287,40 @@ def test_adaptive_steps_match_oracle_on_their_schedule(pm):
                           a_steps, step.PMParams(n=n, Om=1.0, OL=0.0, boxsize=64.0), warm_start=False)
     d = (out.T - ref + 0.5) % 1.0 - 0.5
     assert np.sqrt((d ** 2).sum(1).mean()) * n < 1e-4
+
+
+# ---------------------------------------------------------- f(R), n = 2 ---
+
+@pytest.mark.parametrize("a", [0.3, 1.0])
+def test_fr_n2_one_f_cycle_matches_oracle(pm, a):
+    """Hu-Sawicki n = 2 (the quartic per cell, §3.10): one F-cycle from u = 1."""
+    n = 32
+    rho = lognormal_density(n, 8).astype(np.float32).astype(np.float64)
+    model = ofr.FRModel(Om=0.3, OL=0.7, fR0=-1e-5, boxsize=float(n), n=2)
+    eps, _ = pm.fr_solve(torch.from_numpy(rho.astype(np.float32)).cuda(), a=a, Om=0.3, OL=0.7, fR0=-1e-5,
+                         boxsize=float(n), coarsest=16, cycles=1, nhs=2)
+    u, _ = ofr.fr_solve(rho, a, model, prm=ofr.FASParams(coarsest=16), cycles=1)
+    assert rel_l2(eps.cpu().numpy(), u - 1.0) < 1e-4
+
+
+def test_fr_n2_converged_matches_oracle(pm):
+    n = 32
+    rho = lognormal_density(n, 12, 1.2).astype(np.float32).astype(np.float64)
+    model = ofr.FRModel(Om=0.3, OL=0.7, fR0=-1e-5, boxsize=float(n), n=2)
+    eps, st = pm.fr_solve(torch.from_numpy(rho.astype(np.float32)).cuda(), a=0.8, Om=0.3, OL=0.7, fR0=-1e-5,
+                          boxsize=float(n), coarsest=8, tol=1e-6, max_cycles=20, nhs=2)
+    u, _ = ofr.fr_solve(rho, 0.8, model, prm=ofr.FASParams(coarsest=8), tol=1e-10)
+    assert st["status"] == 0
+    assert rel_l2(eps.cpu().numpy(), u - 1.0) < 2e-5
+
+
+def test_step_accelerations_fr_n2(pm):
+    n = 32
+    X = displaced_lattice(n, 13, amp=0.45)
+    V = np.zeros((3, n ** 3))
+    mgp = pm.default_mg(tol=1e-9)
+    frp = pm.default_fr(coarsest=16, cycles=1, nhs=2)
+    acc, _ = gpu_accelerations(pm, X, V, n, 0.7, gravity="fr", boxsize=float(n), Om=0.3, OL=0.7, mg=mgp, fr=frp)
+    prm = step.PMParams(n=n, Om=0.3, OL=0.7, boxsize=float(n), gravity="fr", fR0=-1e-5, fr_n=2)
+    ref, _, _ = step.accelerations(mesh.positions_from_fixed_point(X), 0.7, prm)
+    assert rel_l2(acc.T, ref) < 1e-5

@@ -118,3 +118,69 @@ def test_fas_f_cycle_rate(golden):
     rate = (hist[0] / hist[-1]) ** (1 / 3)
     assert rate > golden["multigrid_convergence"]["f_cycle"] / 2
     assert u.min() > 0
+
+
+# ------------------------------------------------------------------ n = 2 --
+
+def test_quartic_root_vs_numpy_roots():
+    """u^4 + p u + q = 0, q < 0: the closed form of §3.10 gives the unique
+    positive root for either sign of p, tiny |p| included."""
+    rng = np.random.default_rng(2)
+    p = np.concatenate([[0.0], rng.uniform(0.01, 3, 60), rng.uniform(-3, -0.01, 60), rng.uniform(-1e-4, 1e-4, 30),
+                        -1.0 + rng.uniform(-0.05, 0.05, 30)])
+    q = -rng.uniform(1e-6, 2.0, p.size)
+    u = fr.depressed_quartic_root(p, q)
+    for pi, qi, ui in zip(p, q, u):
+        r = np.roots([1.0, 0.0, 0.0, pi, qi])
+        pos = r[(np.abs(r.imag) < 1e-7) & (r.real > 0)].real
+        assert pos.size == 1
+        assert ui == pytest.approx(pos[0], rel=1e-9, abs=1e-12), (pi, qi)
+
+
+def test_quartic_root_vs_bisection_operating_range():
+    rng = np.random.default_rng(3)
+    p = -1.0 + rng.uniform(-0.05, 0.05, 100)
+    q = -rng.uniform(1e-4, 1e-2, 100)
+    u = fr.depressed_quartic_root(p, q)
+    lo, hi = np.zeros_like(p), np.full_like(p, 10.0)
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        neg = mid ** 4 + p * mid + q < 0
+        lo = np.where(neg, mid, lo)
+        hi = np.where(neg, hi, mid)
+    assert np.abs(u - 0.5 * (lo + hi)).max() < 1e-13
+
+
+def test_n2_background_and_fixed_point():
+    m = fr.FRModel(fR0=-1e-5, n=2, boxsize=8.0)
+    assert fr.background(1.0, m)[0] == pytest.approx(-1e-5, rel=1e-15)
+    Rb = 3 * 0.3 * (0.5 ** -3 + 4 * 0.7 / 0.3)
+    R0 = 3 * 0.3 * (1 + 4 * 0.7 / 0.3)
+    assert fr.background(0.5, m)[0] == pytest.approx(0.25 * -1e-5 * (R0 / Rb) ** 3, rel=1e-14)
+    fbar, kappa, _ = fr.background(0.5, m)
+    u = np.ones((8, 8, 8))
+    assert np.abs(fr.operator(u, 1.0 / 8, fbar, kappa, 2)).max() == 0.0
+    fr.gs_sweep(u, np.zeros_like(u), 1.0 / 8, fbar, kappa, 2)
+    assert np.abs(u - 1.0).max() < 1e-13
+
+
+def test_n2_linear_regime_matches_yukawa_closed_form():
+    """Linearised with f~_R = fbar (1 + x): (1 + x)^(-1/3) - 1 ~ -x/3, so the
+    mass term is mu^2 = a^4 R~ / (9 c~^2 |fbar|) for n = 2."""
+    n, a = 16, 0.6
+    model = fr.FRModel(boxsize=16.0, n=2)
+    i = np.arange(n)
+    delta = 1e-4 * (np.cos(2 * np.pi * 2 * i / n)[:, None, None] + np.sin(2 * np.pi * 5 * i / n)[None, None, :])
+    delta = np.broadcast_to(delta, (n, n, n)).copy()
+    u, _ = fr.fr_solve(1.0 + delta, a, model, prm=fr.FASParams(coarsest=4), tol=1e-11)
+    h = 1.0 / n
+    fbar, _, c2 = fr.background(a, model)
+    Rbar = 3 * model.Om * (a ** -3 + 4 * model.OL / model.Om)
+    mu2 = a ** 4 * Rbar / (9 * c2 * abs(fbar))
+    m = np.fft.fftfreq(n) * n
+    mz = np.fft.rfftfreq(n) * n
+    lam = -(4 / h ** 2) * (np.sin(np.pi * m / n)[:, None, None] ** 2 + np.sin(np.pi * m / n)[None, :, None] ** 2
+                            + np.sin(np.pi * mz / n)[None, None, :] ** 2)
+    pred = np.fft.irfftn(-(model.Om * a / c2) * np.fft.rfftn(delta) / (lam - mu2), s=delta.shape, axes=(0, 1, 2))
+    df = fbar * (u ** 3 - 1.0)
+    assert np.abs(df - pred).max() < 2e-3 * np.abs(pred).max()
