@@ -246,7 +246,7 @@ __global__ void __launch_bounds__(1024) k_reduce_partials(const double* __restri
                                                           int64_t count, int64_t stride, int nout,
                                                           double scale, double* __restrict__ out) {
   __shared__ double red[1024];
-  for (int k = 0; k < nout; ++k) {
+  for (int k = blockIdx.x; k < nout; k += gridDim.x) {   // one output per block (fixed order within it)
     double t = 0.0;
     for (int64_t i = threadIdx.x; i < count; i += blockDim.x) t += partial[k * stride + i];
     red[threadIdx.x] = t;
@@ -336,14 +336,13 @@ pm_status deposit_sorted_batch(const uint32_t* Xs, int64_t np_box, int B, const 
   int chunk, nitems;
   deposit_stream_plan(n, &chunk, &nitems);
   const float scale = np_box > 0 ? (float)((double)n * n * n / (double)np_box) : 0.0f;
-  // one 1024-thread CTA per SM in all: the boxes share the SMs
-  int gx = (152 + B - 1) / B;
-  if (gx > nitems) gx = nitems;
+  // one item per CTA: B x nitems CTAs balance over the SMs (one resident each)
+  const int gx = nitems;
   const int64_t np = np_box * B;
   PM_LAUNCH(K_DEPOSIT, 12.0 * np + 8.0 * n * n * (double)n * B + 4.0, k_deposit_stream, dim3(gx, 1, B), DTHREADS,
             kDepositStreamSmem, s, Xs, np, cellstart, ilog2(n), chunk, nitems, (const float*)nullptr, scale, rho,
             partials);
-  PM_LAUNCH(K_REDUCE, 8.0 * nitems * B, k_reduce_partials, 1, 1024, 0, s, partials, (int64_t)nitems,
+  PM_LAUNCH(K_REDUCE, 8.0 * nitems * B, k_reduce_partials, B, 1024, 0, s, partials, (int64_t)nitems,
             (int64_t)nitems, B, 1.0 / ((double)n * n * n), mean_out);
   return launch_status();
 }
@@ -359,7 +358,8 @@ pm_status grid_mean(const float* f, int64_t count, double* partials, double* mea
 
 pm_status reduce_partials(const double* partials, int64_t count, int64_t stride, int nout,
                           double scale, double* out, cudaStream_t s) {
-  PM_LAUNCH(K_REDUCE, 8.0 * count * nout, k_reduce_partials, 1, 1024, 0, s, partials, count, stride, nout, scale, out);
+  PM_LAUNCH(K_REDUCE, 8.0 * count * nout, k_reduce_partials, nout, 1024, 0, s, partials, count, stride, nout, scale,
+            out);
   return launch_status();
 }
 

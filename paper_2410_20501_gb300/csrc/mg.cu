@@ -418,7 +418,7 @@ pm_status smooth(MG& g, int l, int count, const float* w, bool zero, float scale
     }
     return PM_OK;
   }
-  if (g.p->smoother == 2 && fused_ok(n) && g.alt[l] && fused_aligned(g.u[l], g.alt[l], g.f[l].p)) {
+  if (g.p->smoother == 2 && fused_ok(n, g.B) && g.alt[l] && fused_aligned(g.u[l], g.alt[l], g.f[l].p)) {
     const int chunk = fused_chunk(n);
     const unsigned grid = (unsigned)((n / kFusedT) * (n / kFusedT) * (n / chunk));
     for (; done < count; ++done) {

@@ -203,7 +203,9 @@ inline int fused_chunk(int n) {
   return c;
 }
 
-inline bool fused_ok(int n) { return n >= 128; }
+// Levels the fused kernel takes: n >= 128, or n = 64 in a batch of at least 8
+// boxes (enough CTAs to fill the GPU).
+inline bool fused_ok(int n, int B = 1) { return n >= 128 || (n >= 64 && B >= 8); }
 
 // float4 plane loads, float2 source loads and pair stores need 16- and 8-byte
 // aligned level arrays (workspace levels always are; caller arrays may not be).

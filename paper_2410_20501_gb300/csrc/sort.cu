@@ -22,6 +22,7 @@ constexpr int SCAN_CHUNK = 4 * SCAN_T;
 
 // key = (i n + j) n + k of the cell holding each particle; with np_box > 0
 // (a batch of boxes) prefixed by the box, i / np_box.
+template <bool BOX>
 __global__ void k_cell_keys(const uint32_t* __restrict__ X, int64_t np, int log2n, int64_t np_box,
                             uint32_t* __restrict__ keys) {
   const int sh = 32 - log2n;
@@ -31,7 +32,7 @@ __global__ void k_cell_keys(const uint32_t* __restrict__ X, int64_t np, int log2
     uint32_t iy = __ldg(X + np + i) >> sh;
     uint32_t iz = __ldg(X + 2 * np + i) >> sh;
     uint32_t key = (((ix << log2n) | iy) << log2n) | iz;
-    if (np_box > 0) key |= (uint32_t)(i / np_box) << (3 * log2n);
+    if (BOX) key |= (uint32_t)(i / np_box) << (3 * log2n);
     keys[i] = key;
   }
 }
@@ -305,7 +306,10 @@ pm_status sort_particles(const uint32_t* X, int64_t np, int n, Workspace& w, cud
   *skeys_out = w.keys_a;
   if (np == 0) return PM_OK;
   const int64_t np_box = bt.B > 1 ? bt.np_box : 0;
-  PM_LAUNCH(K_KEYS, 16.0 * np, k_cell_keys, grid_for(np, 256), 256, 0, s, X, np, log2n, np_box, w.keys_a);
+  if (np_box > 0)
+    PM_LAUNCH(K_KEYS, 16.0 * np, k_cell_keys<true>, grid_for(np, 256), 256, 0, s, X, np, log2n, np_box, w.keys_a);
+  else
+    PM_LAUNCH(K_KEYS, 16.0 * np, k_cell_keys<false>, grid_for(np, 256), 256, 0, s, X, np, log2n, np_box, w.keys_a);
   const int keybits = 3 * log2n + (bt.B > 1 ? ilog2(2 * bt.B - 1) : 0);   // + ceil(log2 B) box bits
   const int passes = (keybits + 8) / 9;
   const int bpp = (keybits + passes - 1) / passes;

@@ -83,3 +83,13 @@ def test_batched_accelerations_match_the_oracle(pm, small):
     Xo = ens.positions()
     for b in range(B):
         assert np.array_equal(Xo[b], X[b][:, mesh.stable_cell_order(X[b], n)])
+
+
+def test_batch_of_eight_64cubed_is_bitwise_the_boxes_run_alone(pm):
+    """With 8 or more boxes the 64^3 levels take the fused sweep (a single
+    box takes the colour passes): still bitwise the boxes run alone."""
+    w = inputs.ensemble_workload(n=64, B=8, boxsize=128.0, steps=3)
+    Xb, Vb = run(pm, w, list(range(8)), 3)
+    for b in (0, 5):
+        Xs, Vs = run(pm, w, [b], 3)
+        assert np.array_equal(Xb[b], Xs[0]) and np.array_equal(Vb[b], Vs[0]), b
