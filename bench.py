@@ -325,6 +325,29 @@ def run_ensemble(n=64, B=64, steps=50):
                         "2LPT z=30, 50 steps in ln a", "unit": "particle-steps/s", **out}
 
 
+def run_lpt(n, reps=3):
+    """2LPT initial conditions of n^3 particles (L = n Mpc/h, z = 30) by
+    pm_lpt2: device time per generation."""
+    import torch
+    from paper_2410_20501_gb300 import inputs, pm
+    a = 1.0 / (1.0 + Z_INI)
+    D, E, f1, f2 = inputs.growth([a, 1.0], OM, OL)
+    vfac = a * a * inputs.hubble_E(a, OM, OL)
+    d1, e2 = D[0] / D[1], E[0] / D[1] ** 2
+    noise = torch.from_numpy(inputs.white_noise(n, SEED).astype(np.float32)).cuda()
+    amp = torch.from_numpy(inputs.lpt_amplitude(n, float(n), OM).astype(np.float32)).cuda()
+    ws = pm.workspace(n, 0, pm.PM_WS_LPT)
+    pm.lpt2(noise, amp, d1, e2, vfac * d1 * f1[0], vfac * e2 * f2[0], ws)
+    s = torch.cuda.current_stream()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record(s)
+    for _ in range(reps):
+        pm.lpt2(noise, amp, d1, e2, vfac * d1 * f1[0], vfac * e2 * f2[0], ws)
+    t1.record(s)
+    torch.cuda.synchronize()
+    return {"stage": "lpt", "n": n, "ms_per_generation": t0.elapsed_time(t1) / reps}
+
+
 def run_gpu(args):
     import torch
     world, rank, local = dist_env()
@@ -508,7 +531,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--lean", action="store_true",
                     help="f(R) device-timed steps only (no Newtonian line, e2e or CPU baseline): for profilers")
-    ap.add_argument("--stage", choices=["sort", "deposit", "mg", "fr", "interp", "adjoint", "ensemble"],
+    ap.add_argument("--stage", choices=["sort", "deposit", "mg", "fr", "interp", "adjoint", "ensemble", "lpt"],
                     help="time one stage alone on synthetic inputs (for profilers)")
     ap.add_argument("--n", type=int, default=256, help="grid size for --stage")
     ap.add_argument("--smoother", type=int, default=2,
@@ -519,6 +542,9 @@ def main():
         return 0
     if args.stage == "ensemble":
         print(json.dumps(run_ensemble()))
+        return 0
+    if args.stage == "lpt":
+        print(json.dumps(run_lpt(args.n, args.steps)))
         return 0
     if args.stage:
         return run_stage(args)

@@ -73,8 +73,9 @@ enum {
   PM_WS_STEP = 8,      /* pm_step, pm_step_host (includes all of the above)    */
   PM_WS_IDS = 16,      /* pm_step carries particle ids (pm_state.id != NULL)   */
   PM_WS_ADJ = 32,      /* adjoint entry points (with PM_WS_SORT or PM_WS_STEP) */
-  PM_WS_FFT = 64       /* FFT Poisson solver (pm_poisson_fft, pm_step with
+  PM_WS_FFT = 64,      /* FFT Poisson solver (pm_poisson_fft, pm_step with
                           poisson != PM_POISSON_MG): the half spectrum          */
+  PM_WS_LPT = 128      /* pm_lpt2: two half spectra and five grids             */
 };
 
 /* Bytes of workspace needed for grids of n^3 cells and np particles.
@@ -195,6 +196,21 @@ pm_status mg_solve(const float* f, float* phi, int n, const mg_params* prm,
  * Workspace: pm_workspace_size(n, 0, PM_WS_FFT). */
 pm_status pm_poisson_fft(const float* rho, float* phi, int n, int kind, double scale, void* ws, size_t ws_bytes,
                          void* stream);
+
+/* Initial conditions by Lagrangian perturbation theory (§3.3): one particle
+ * per cell centre q of the n^3 lattice (lattice order, index (i n + j) n + k),
+ * moved to X = q + d1 Psi1 + e2 Psi2 with velocity V = v1 Psi1 + v2 Psi2,
+ * where delta_k = amp_k FFT(noise)_k, phi1 = grad^-2 delta, Psi1 = -grad phi1,
+ * phi2 = (1/2) grad^-2 [phi1_ii phi1_jj - phi1_ij phi1_ij], Psi2 = grad phi2
+ * (spectral derivatives, k = 2 pi m in box units, modes on Nyquist planes set
+ * to zero).  e2 = v2 = 0 gives first order (no second-order work).  The
+ * factors are the caller's: d1 = D(a)/D(1), e2 the second-order growth
+ * factor, v1 = a^2 E(a) d1 f1, v2 = a^2 E(a) e2 f2 (§3.1 velocity units).
+ *   noise [n^3] real white noise, amp [n][n][n/2+1] = sqrt(P(k) n^3 / L^3)
+ *   (read); X [3][n^3] uint32 fixed point, V [3][n^3] (written); n >= 16.
+ * Workspace: pm_workspace_size(n, 0, PM_WS_LPT). */
+pm_status pm_lpt2(const float* noise, const float* amp, int n, double d1, double e2, double v1, double v2,
+                  uint32_t* X, float* V, void* ws, size_t ws_bytes, void* stream);
 
 /* ------------------------------------------------------------------ f(R) -- */
 typedef struct {

@@ -100,6 +100,11 @@ size_t layout_workspace(Workspace* w, void* base, int n, int64_t np, uint32_t fl
     w->adj_gbar = (float*)take((size_t)N * 12);
   }
   if (flags & PM_WS_FFT) w->spec = (float2*)take((size_t)n * n * (n / 2 + 1) * 8 * batch);
+  if (flags & PM_WS_LPT) {
+    w->lpt_a = (float2*)take((size_t)n * n * (n / 2 + 1) * 8);
+    w->lpt_b = (float2*)take((size_t)n * n * (n / 2 + 1) * 8);
+    w->lpt_r = (float*)take((size_t)N * 4 * 5);
+  }
   w->partials = (double*)take((size_t)2 * reduce_partials_capacity(n, np) * 8 * batch);
   w->scalars = (double*)take(64 * 8);
   w->box_mean = (double*)take((size_t)batch * 8);
@@ -317,6 +322,14 @@ pm_status pm_poisson_fft(const float* rho, float* phi, int n, int kind, double s
   cudaStream_t s = as_stream(stream);
   PM_TRY(grid_mean(rho, (int64_t)n * n * n, w.partials, w.scalars + 3, s));
   return fft_poisson_launch(rho, w.scalars + 3, phi, w.spec, n, kind, scale, s);
+}
+
+pm_status pm_lpt2(const float* noise, const float* amp, int n, double d1, double e2, double v1, double v2,
+                  uint32_t* X, float* V, void* ws, size_t ws_bytes, void* stream) {
+  if (!valid_n(n) || n < 16 || !noise || !amp || !X || !V || !all_a16(noise, amp, X, V)) return PM_EINVAL;
+  Workspace w;
+  PM_TRY(check_ws(w, ws, ws_bytes, n, 0, PM_WS_LPT));
+  return lpt2_launch(noise, amp, n, d1, e2, v1, v2, X, V, w.lpt_a, w.lpt_b, w.lpt_r, as_stream(stream));
 }
 
 pm_status pm_gradient(const float* phi, float* g, int n, int order, void* stream) {

@@ -233,17 +233,36 @@ __global__ void __launch_bounds__(lines_per_block<M>() * (M / 8)) k_fft_z_c2r(co
 // one y (AXIS 0: lines along x); for AXIS 0 with SOLVE the block multiplies by
 // scale G(k) (times the normalisation) between the forward and the inverse
 // transform.
-struct Green {
-  int kind;        // 1: FFT_7pt, 2: FFT (exact, TSC-deconvolved)
-  float scale;     // includes the 2 / n^3 of the unnormalised transforms
+// Spectral multiplier applied on the x pass (kz = kz0 + line, kx index i,
+// ky index `other`; m = index for index < n/2, else index - n; k = 2 pi m):
+//   GREEN7   -scale / ((4/h^2) sum_d sin^2(pi m_d / n))      (FFT_7pt)
+//   GREENTSC -scale / (k^2 W_TSC^2), W_TSC = prod_d sinc(pi m_d / n)^3   (FFT)
+//   AMPLAP   -scale amp(kx, ky, kz) / k^2   (first-order LPT potential)
+//   INVLAP   -scale / k^2
+//   DERIV    scale i k_d1
+//   HESS     -scale k_d1 k_d2
+// All are 0 at k = 0; the LPT kinds (AMPLAP .. HESS) also on every Nyquist
+// plane (|m_d| = n/2 on any axis).
+enum MultKind { GREEN7 = 1, GREENTSC = 2, AMPLAP = 3, INVLAP = 4, DERIV = 5, HESS = 6 };
+struct Mult {
+  int kind;
+  int d1, d2;            // axes of DERIV / HESS (0 = x, 1 = y, 2 = z)
+  float scale;           // includes the 2 / n^3 of an inverse transform
+  const float* amp;      // AMPLAP: [n][n][n/2 + 1]
 };
 
-template <int L, int AXIS, bool INV, bool SOLVE>
-__global__ void __launch_bounds__(lines_per_block<L>() * (L / 8)) k_fft_cols(float2* __restrict__ C, int ntiles,
-                                                                             Green gr) {
+// Column-pass modes: forward or inverse transform in place; FWDMUL: forward,
+// then multiply (x pass, in place); MULINV: multiply the lines read from `in`,
+// inverse, write `out` (x pass); SOLVE: forward, multiply, inverse (x pass).
+enum ColMode { FWD = 0, INVT = 1, FWDMUL = 2, MULINV = 3, SOLVE = 4 };
+
+template <int L, int AXIS, int MODE>
+__global__ void __launch_bounds__(lines_per_block<L>() * (L / 8)) k_fft_cols(const float2* in, float2* out,
+                                                                             int ntiles, Mult mu) {
+  constexpr bool MUL = MODE == FWDMUL || MODE == MULINV || MODE == SOLVE;
   constexpr int TW = lines_per_block<L>(), TPL = L / 8, LP = L + 1, n = L, H = n / 2 + 1;
   __shared__ float2 s[TW * LP];
-  __shared__ float ax2[SOLVE ? n : 1], axw[SOLVE ? n : 1];
+  __shared__ float ta[MUL ? n : 1], tb[MUL ? n : 1];
   const int tile = blockIdx.x % ntiles, other = blockIdx.x / ntiles;   // other: x (AXIS 1) or y (AXIS 0)
   const int kz0 = tile * TW;
   const int tw = (H - kz0) < TW ? (H - kz0) : TW;
@@ -251,69 +270,213 @@ __global__ void __launch_bounds__(lines_per_block<L>() * (L / 8)) k_fft_cols(flo
   const int64_t base = (AXIS == 1 ? (int64_t)other * n * H : (int64_t)other * H) + kz0;
   for (int e = threadIdx.x; e < tw * L; e += blockDim.x) {
     const int i = e / tw, l = e - i * tw;
-    s[l * LP + i] = C[base + i * stride + l];
+    s[l * LP + i] = in[base + i * stride + l];
   }
-  if (SOLVE) {
-    // per-axis factors: sin^2(pi m / n) (FFT_7pt) or (2 pi m)^2 and sinc^6 (FFT)
+  if (MUL) {
+    // per-axis tables: GREEN7: sin^2(pi m/n); GREENTSC: k^2 and sinc^6;
+    // LPT kinds: k (0 on the Nyquist index, which also flags it in tb)
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
       const int m = i < n / 2 ? i : i - n;
       const float sp = sinpif((float)m / (float)n);
-      ax2[i] = gr.kind == 1 ? sp * sp : 39.47841760435743f * (float)m * (float)m;
-      const float sc = m == 0 ? 1.0f : sp / (3.14159265358979f * (float)m / (float)n);
-      const float s2 = sc * sc;
-      axw[i] = s2 * s2 * s2;
+      if (mu.kind == GREEN7) {
+        ta[i] = sp * sp;
+      } else if (mu.kind == GREENTSC) {
+        ta[i] = 39.47841760435743f * (float)m * (float)m;
+        const float sc = m == 0 ? 1.0f : sp / (3.14159265358979f * (float)m / (float)n);
+        const float s2 = sc * sc;
+        tb[i] = s2 * s2 * s2;
+      } else {
+        const bool nyq = 2 * i == n;
+        ta[i] = nyq ? 0.0f : 6.283185307179586f * (float)m;
+        tb[i] = nyq ? 1.0f : 0.0f;
+      }
     }
   }
   __syncthreads();
   const int line = threadIdx.x / TPL, t = threadIdx.x - line * TPL;
-  fft_line<L, INV>(s + line * LP, t);
-  if (SOLVE) {
+  if (MODE == FWD || MODE == FWDMUL || MODE == SOLVE) fft_line<L, false>(s + line * LP, t);
+  if (MODE == INVT) fft_line<L, true>(s + line * LP, t);
+  if (MUL) {
     for (int e = threadIdx.x; e < tw * L; e += blockDim.x) {
       const int l = e / L, i = e - l * L;          // kx index i, kz = kz0 + l
       const int kz = kz0 + l;
-      float g;
-      if (gr.kind == 1) {
-        const float lam = ax2[i] + ax2[other] + ax2[kz];
-        g = lam > 0.0f ? -gr.scale / (4.0f * (float)n * (float)n * lam) : 0.0f;
-      } else {
-        const float k2 = ax2[i] + ax2[other] + ax2[kz];
-        const float w2 = axw[i] * axw[other] * axw[kz];
-        g = k2 > 0.0f ? -gr.scale / (k2 * w2) : 0.0f;
-      }
       float2& v = s[l * LP + i];
-      v = make_float2(v.x * g, v.y * g);
+      const int ix[3] = {i, other, kz};
+      if (mu.kind == GREEN7) {
+        const float lam = ta[i] + ta[other] + ta[kz];
+        const float g = lam > 0.0f ? -mu.scale / (4.0f * (float)n * (float)n * lam) : 0.0f;
+        v = make_float2(v.x * g, v.y * g);
+      } else if (mu.kind == GREENTSC) {
+        const float k2 = ta[i] + ta[other] + ta[kz];
+        const float g = k2 > 0.0f ? -mu.scale / (k2 * tb[i] * tb[other] * tb[kz]) : 0.0f;
+        v = make_float2(v.x * g, v.y * g);
+      } else {
+        const bool zero = tb[i] + tb[other] + tb[kz] > 0.0f || (i == 0 && other == 0 && kz == 0);
+        if (zero) {
+          v = make_float2(0.0f, 0.0f);
+        } else if (mu.kind == DERIV) {
+          const float k = mu.scale * ta[ix[mu.d1]];
+          v = make_float2(-k * v.y, k * v.x);                 // i k v
+        } else {
+          float g;
+          if (mu.kind == HESS) {
+            g = -mu.scale * ta[ix[mu.d1]] * ta[ix[mu.d2]];
+          } else {
+            const float k2 = ta[i] * ta[i] + ta[other] * ta[other] + ta[kz] * ta[kz];
+            g = -mu.scale / k2;
+            if (mu.kind == AMPLAP) g *= __ldg(mu.amp + ((int64_t)i * n + other) * H + kz);
+          }
+          v = make_float2(v.x * g, v.y * g);
+        }
+      }
     }
     __syncthreads();
-    fft_line<L, true>(s + line * LP, t);
+    if (MODE == MULINV || MODE == SOLVE) fft_line<L, true>(s + line * LP, t);
   }
   for (int e = threadIdx.x; e < tw * L; e += blockDim.x) {
     const int i = e / tw, l = e - i * tw;
-    C[base + i * stride + l] = s[l * LP + i];
+    out[base + i * stride + l] = s[l * LP + i];
   }
+}
+
+// Launch geometry of the transforms of an n^3 grid.
+template <int N>
+struct FftPlan {
+  static constexpr int M = N / 2, H = M + 1, LBz = lines_per_block<M>(), LBc = lines_per_block<N>();
+  static constexpr int64_t rows = (int64_t)N * N;
+  static constexpr double cells = (double)N * N * N, spec = (double)N * N * H * 8.0;
+  static unsigned zblocks() { return (unsigned)((rows + LBz - 1) / LBz); }
+  static int ntiles() { return (H + LBc - 1) / LBc; }
+  static unsigned cblocks() { return (unsigned)(ntiles() * N); }
+};
+
+// spec = M(k) FFT[real]  (unnormalised forward transform, then the multiplier)
+template <int N>
+pm_status fft_forward_mul(const float* real, const double* mean, float2* spec, const Mult& mu, cudaStream_t s) {
+  using P = FftPlan<N>;
+  PM_LAUNCH(K_FFT, 4.0 * P::cells + P::spec, k_fft_z_r2c<P::M>, P::zblocks(), P::LBz * (P::M / 8), 0, s, real, mean,
+            spec, P::rows);
+  PM_LAUNCH(K_FFT, 2.0 * P::spec, (k_fft_cols<N, 1, FWD>), P::cblocks(), P::LBc * (N / 8), 0, s, spec, spec,
+            P::ntiles(), mu);
+  PM_LAUNCH(K_FFT, 2.0 * P::spec, (k_fft_cols<N, 0, FWDMUL>), P::cblocks(), P::LBc * (N / 8), 0, s, spec, spec,
+            P::ntiles(), mu);
+  return launch_status();
+}
+
+// real = IFFT[M(k) spec]  (spec is read only; tmp receives the intermediate
+// spectrum; mu.scale carries the 2 / n^3 normalisation)
+template <int N>
+pm_status fft_mul_inverse(const float2* spec, float2* tmp, float* real, const Mult& mu, cudaStream_t s) {
+  using P = FftPlan<N>;
+  PM_LAUNCH(K_FFT, 2.0 * P::spec, (k_fft_cols<N, 0, MULINV>), P::cblocks(), P::LBc * (N / 8), 0, s, spec, tmp,
+            P::ntiles(), mu);
+  PM_LAUNCH(K_FFT, 2.0 * P::spec, (k_fft_cols<N, 1, INVT>), P::cblocks(), P::LBc * (N / 8), 0, s, tmp, tmp,
+            P::ntiles(), mu);
+  PM_LAUNCH(K_FFT, P::spec + 4.0 * P::cells, k_fft_z_c2r<P::M>, P::zblocks(), P::LBz * (P::M / 8), 0, s, tmp, real,
+            P::rows);
+  return launch_status();
 }
 
 template <int N>
 pm_status launch_fft_poisson(const float* rho, const double* mean, float* phi, float2* C, int kind, double scale,
                              cudaStream_t s) {
-  constexpr int M = N / 2, H = M + 1;
-  const int64_t rows = (int64_t)N * N;
-  const double cells = (double)N * N * N, spec = (double)N * N * H * 8.0;
-  constexpr int LBz = lines_per_block<M>(), LBc = lines_per_block<N>();
-  const unsigned zblocks = (unsigned)((rows + LBz - 1) / LBz);
-  const int ntiles = (H + LBc - 1) / LBc;
-  const unsigned cblocks = (unsigned)(ntiles * N);
+  using P = FftPlan<N>;
   // the y and x transform pairs scale by n each, the z pair by n/2 (the
   // inverse runs an n/2-point transform of the packed pairs): divide by n^3/2
-  const Green gr{kind, (float)(2.0 * scale / cells)};
-  PM_LAUNCH(K_FFT, 4.0 * cells + spec, k_fft_z_r2c<M>, zblocks, LBz * (M / 8), 0, s, rho, mean, C, rows);
-  PM_LAUNCH(K_FFT, 2.0 * spec, (k_fft_cols<N, 1, false, false>), cblocks, LBc * (N / 8), 0, s, C, ntiles, gr);
-  PM_LAUNCH(K_FFT, 2.0 * spec, (k_fft_cols<N, 0, false, true>), cblocks, LBc * (N / 8), 0, s, C, ntiles, gr);
-  PM_LAUNCH(K_FFT, 2.0 * spec, (k_fft_cols<N, 1, true, false>), cblocks, LBc * (N / 8), 0, s, C, ntiles, gr);
-  PM_LAUNCH(K_FFT, spec + 4.0 * cells, k_fft_z_c2r<M>, zblocks, LBz * (M / 8), 0, s, C, phi, rows);
+  const Mult mu{kind == 1 ? GREEN7 : GREENTSC, 0, 0, (float)(2.0 * scale / P::cells), nullptr};
+  PM_LAUNCH(K_FFT, 4.0 * P::cells + P::spec, k_fft_z_r2c<P::M>, P::zblocks(), P::LBz * (P::M / 8), 0, s, rho, mean,
+            C, P::rows);
+  PM_LAUNCH(K_FFT, 2.0 * P::spec, (k_fft_cols<N, 1, FWD>), P::cblocks(), P::LBc * (N / 8), 0, s, C, C, P::ntiles(),
+            mu);
+  PM_LAUNCH(K_FFT, 2.0 * P::spec, (k_fft_cols<N, 0, SOLVE>), P::cblocks(), P::LBc * (N / 8), 0, s, C, C,
+            P::ntiles(), mu);
+  PM_LAUNCH(K_FFT, 2.0 * P::spec, (k_fft_cols<N, 1, INVT>), P::cblocks(), P::LBc * (N / 8), 0, s, C, C,
+            P::ntiles(), mu);
+  PM_LAUNCH(K_FFT, P::spec + 4.0 * P::cells, k_fft_z_c2r<P::M>, P::zblocks(), P::LBz * (P::M / 8), 0, s, C, phi,
+            P::rows);
+  return launch_status();
+}
+
+// S = phi_xx phi_yy + phi_xx phi_zz + phi_yy phi_zz (H: the three diagonal
+// second derivatives, planes of N), then S -= T^2 for each mixed derivative T.
+__global__ void k_lpt_diag(const float* __restrict__ H, float* __restrict__ S, int64_t N) {
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < N; c += (int64_t)gridDim.x * blockDim.x) {
+    const float a = H[c], b = H[N + c], d = H[2 * N + c];
+    S[c] = fmaf(a, b, fmaf(a, d, b * d));
+  }
+}
+
+__global__ void k_lpt_sub_sq(const float* __restrict__ T, float* __restrict__ S, int64_t N) {
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < N; c += (int64_t)gridDim.x * blockDim.x)
+    S[c] = fmaf(-T[c], T[c], S[c]);
+}
+
+// Particle p on cell centre q_p (lattice order): component d of
+// X = q + d1 Psi1 + e2 Psi2 (fixed point: the displacement rounded to units
+// of 2^-32 of the box and added to the exact centre, modulo 2^32) and
+// V = v1 Psi1 + v2 Psi2.  V holds Psi1_d on entry; psi2 may be NULL (1LPT).
+__global__ void k_lpt_combine(const float* __restrict__ psi2, float* __restrict__ V, uint32_t* __restrict__ X,
+                              int d, int log2n, float d1, float e2, float v1, float v2) {
+  const int64_t N = (int64_t)1 << (3 * log2n);
+  const int m = (1 << log2n) - 1;
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < N; p += (int64_t)gridDim.x * blockDim.x) {
+    const int cell = (int)((p >> ((2 - d) * log2n)) & m);                 // i, j or k of the particle
+    const uint32_t q = (uint32_t)(2 * cell + 1) << (31 - log2n);          // (cell + 1/2)/n in units of 2^-32
+    const float p1 = V[p], p2 = psi2 ? psi2[p] : 0.0f;
+    const float disp = fmaf(d1, p1, e2 * p2);
+    X[p] = q + (uint32_t)__float2int_rn(disp * 4294967296.0f);
+    V[p] = fmaf(v1, p1, v2 * p2);
+  }
+}
+
+template <int N>
+pm_status launch_lpt2(const float* noise, const float* amp, float d1, float e2, float v1, float v2, uint32_t* X,
+                      float* V, float2* A, float2* B, float* R, cudaStream_t s) {
+  using P = FftPlan<N>;
+  const int64_t NC = (int64_t)N * N * N;
+  const float inv = (float)(2.0 / P::cells);
+  float *H = R, *S = R + 3 * NC, *T = R + 4 * NC;
+  const unsigned g = grid_for(NC, 256);
+  PM_TRY(fft_forward_mul<N>(noise, nullptr, A, Mult{AMPLAP, 0, 0, 1.0f, amp}, s));       // phi1
+  for (int d = 0; d < 3; ++d)                                                             // Psi1 = -grad phi1
+    PM_TRY(fft_mul_inverse<N>(A, B, V + d * NC, Mult{DERIV, d, 0, -inv, nullptr}, s));
+  const bool second = e2 != 0.0f || v2 != 0.0f;
+  if (second) {
+    for (int d = 0; d < 3; ++d)
+      PM_TRY(fft_mul_inverse<N>(A, B, H + d * NC, Mult{HESS, d, d, inv, nullptr}, s));
+    PM_LAUNCH(K_MISC, 16.0 * NC, k_lpt_diag, g, 256, 0, s, H, S, NC);
+    const int pairs[3][2] = {{0, 1}, {0, 2}, {1, 2}};
+    for (const auto& pr : pairs) {
+      PM_TRY(fft_mul_inverse<N>(A, B, T, Mult{HESS, pr[0], pr[1], inv, nullptr}, s));
+      PM_LAUNCH(K_MISC, 12.0 * NC, k_lpt_sub_sq, g, 256, 0, s, T, S, NC);
+    }
+    PM_TRY(fft_forward_mul<N>(S, nullptr, A, Mult{INVLAP, 0, 0, 1.0f, nullptr}, s));      // phi2
+  }
+  for (int d = 0; d < 3; ++d) {
+    if (second) PM_TRY(fft_mul_inverse<N>(A, B, T, Mult{DERIV, d, 0, inv, nullptr}, s));  // Psi2 = grad phi2
+    PM_LAUNCH(K_MISC, 20.0 * NC, k_lpt_combine, g, 256, 0, s, second ? T : nullptr, V + d * NC, X + d * NC, d,
+              ilog2(N), d1, e2, v1, v2);
+  }
   return launch_status();
 }
 
 }  // namespace
+
+pm_status lpt2_launch(const float* noise, const float* amp, int n, double d1, double e2, double v1, double v2,
+                      uint32_t* X, float* V, float2* A, float2* B, float* R, cudaStream_t s) {
+  PM_TRY(twiddles_ready());
+  const float f[4] = {(float)d1, (float)e2, (float)v1, (float)v2};
+  switch (n) {
+    case 16: return launch_lpt2<16>(noise, amp, f[0], f[1], f[2], f[3], X, V, A, B, R, s);
+    case 32: return launch_lpt2<32>(noise, amp, f[0], f[1], f[2], f[3], X, V, A, B, R, s);
+    case 64: return launch_lpt2<64>(noise, amp, f[0], f[1], f[2], f[3], X, V, A, B, R, s);
+    case 128: return launch_lpt2<128>(noise, amp, f[0], f[1], f[2], f[3], X, V, A, B, R, s);
+    case 256: return launch_lpt2<256>(noise, amp, f[0], f[1], f[2], f[3], X, V, A, B, R, s);
+    case 512: return launch_lpt2<512>(noise, amp, f[0], f[1], f[2], f[3], X, V, A, B, R, s);
+    case 1024: return launch_lpt2<1024>(noise, amp, f[0], f[1], f[2], f[3], X, V, A, B, R, s);
+    default: return PM_EINVAL;
+  }
+}
 
 pm_status fft_poisson_launch(const float* rho, const double* mean, float* phi, float2* C, int n, int kind,
                              double scale, cudaStream_t s) {

@@ -94,6 +94,7 @@ struct Workspace {
   float* adj_abar; float* adj_phi; float* adj_psi; float* adj_gbar;
   double* box_mean;   // per-box mean density of a batch
   float2* spec;       // half spectrum n^2 (n/2 + 1) of the FFT Poisson path
+  float2* lpt_a; float2* lpt_b; float* lpt_r;   // LPT: two half spectra, five real grids
   int64_t np; int n; int batch;
 };
 
@@ -169,6 +170,12 @@ pm_status interp_launch(const float* g, const uint32_t* Xs, const float* Vs, con
 // may be NULL.  C: n^2 (n/2 + 1) float2.
 pm_status fft_poisson_launch(const float* rho, const double* mean, float* phi, float2* C, int n, int kind,
                              double scale, cudaStream_t s);
+
+// 2LPT (1LPT when e2 = v2 = 0) particles on the n^3 lattice from real white
+// noise and the spectrum amplitude amp [n][n][n/2+1]: X = q + d1 Psi1 + e2 Psi2,
+// V = v1 Psi1 + v2 Psi2 (§3.3).  A, B: half spectra; R: 5 n^3 floats.
+pm_status lpt2_launch(const float* noise, const float* amp, int n, double d1, double e2, double v1, double v2,
+                      uint32_t* X, float* V, float2* A, float2* B, float* R, cudaStream_t s);
 
 // Adjoint pieces (adjoint.cu).
 pm_status divergence_launch(const float* gbar, float* phibar, int n, int order, cudaStream_t s);

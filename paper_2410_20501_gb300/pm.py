@@ -18,7 +18,7 @@ import torch
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_lib", "libpmgb.so")
 
-PM_WS_SORT, PM_WS_MG, PM_WS_FR, PM_WS_STEP, PM_WS_IDS, PM_WS_ADJ, PM_WS_FFT = 1, 2, 4, 8, 16, 32, 64
+PM_WS_SORT, PM_WS_MG, PM_WS_FR, PM_WS_STEP, PM_WS_IDS, PM_WS_ADJ, PM_WS_FFT, PM_WS_LPT = 1, 2, 4, 8, 16, 32, 64, 128
 PM_POISSON_MG, PM_POISSON_FFT7, PM_POISSON_FFT = 0, 1, 2
 MG_GUESS_INPUT, MG_GUESS_JACOBI, MG_GUESS_SCALED = 0, 1, 2
 PM_GRAVITY_NEWTON, PM_GRAVITY_FR, PM_GRAVITY_PARAM = 0, 1, 2
@@ -131,6 +131,9 @@ _SIGS = {
                                     ctypes.POINTER(mg_stats), ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
     "pm_poisson_fft": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                       ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
+    "pm_lpt2": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                               ctypes.c_double, ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                               ctypes.c_size_t, ctypes.c_void_p]),
     "pm_batch_workspace_size": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int64,
                                                ctypes.POINTER(ctypes.c_size_t)]),
     "pm_step_batch": (ctypes.c_int, [ctypes.POINTER(pm_batch_state), ctypes.POINTER(pm_batch_params),
@@ -276,6 +279,19 @@ def poisson_fft(rho, scale=1.0, kind=PM_POISSON_FFT7, ws=None):
     _check(lib().pm_poisson_fft(_p(rho, torch.float32), _p(phi), n, kind, scale, _p(ws), ws.numel(), _stream()),
            "pm_poisson_fft")
     return phi
+
+
+def lpt2(noise, amp, d1, e2, v1, v2, ws=None):
+    """2LPT particles on the lattice from real white noise [n, n, n] and the
+    amplitude grid [n, n, n//2+1] (device float32): returns (X int32 bits
+    [3, n^3], V [3, n^3])."""
+    n = noise.shape[0]
+    ws = ws if ws is not None else workspace(n, 0, PM_WS_LPT, noise.device)
+    X = torch.empty((3, n ** 3), dtype=torch.int32, device=noise.device)
+    V = torch.empty((3, n ** 3), dtype=torch.float32, device=noise.device)
+    _check(lib().pm_lpt2(_p(noise, torch.float32), _p(amp, torch.float32), n, d1, e2, v1, v2, _p(X), _p(V), _p(ws),
+                         ws.numel(), _stream()), "pm_lpt2")
+    return X, V
 
 
 def gradient(phi, order=5):
