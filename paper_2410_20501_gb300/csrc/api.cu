@@ -10,7 +10,7 @@
 namespace pmgb {
 
 const char* const kKernelClassNames[K_NCLASS] = {
-    "cell_keys",   "radix_upsweep", "radix_scan",  "radix_downsweep", "cellstart",  "permute",
+    "cell_count",  "cell_scan",     "cell_scatter", "cell_order",     "permute",
     "tsc_deposit", "reduce",        "mg_guess",    "mg_smooth_l0",    "mg_smooth",   "mg_restrict",
     "mg_prolong",  "mg_coarse",     "mg_norm",     "fr_smooth_l0",    "fr_smooth",   "fr_restrict",
     "fr_coarse_op", "fr_prolong",
@@ -78,12 +78,10 @@ size_t layout_workspace(Workspace* w, void* base, int n, int64_t np, uint32_t fl
   };
   if (sort) {
     const size_t kb = (size_t)np * 4;
-    w->keys_a = (uint32_t*)take(kb);
-    w->keys_b = (uint32_t*)take(kb);
-    w->vals_a = (uint32_t*)take(kb);
-    w->vals_b = (uint32_t*)take(kb);
-    w->counts = (uint32_t*)take((size_t)512 * radix_tiles(np) * 4 + 4);
-    w->scan_blocks = (uint32_t*)take((size_t)radix_scan_blocks(np) * 4 + 4);
+    w->keyrank = (uint2*)take(2 * kb);
+    w->perm = (uint32_t*)take(kb);
+    w->runs = (uint32_t*)take((size_t)sort_runs_capacity(np) * 4);
+    w->scan_blocks = (uint32_t*)take((size_t)sort_scan_blocks(N) * 4);
     w->cellstart = (uint32_t*)take((size_t)(N + 1) * 4);
     w->Xs = (uint32_t*)take(3 * kb);
   }
@@ -270,10 +268,9 @@ pm_status pm_sort(const uint32_t* X, int64_t np, int n, uint32_t* perm, uint32_t
   Workspace w;
   PM_TRY(check_ws(w, ws, ws_bytes, n, np, PM_WS_SORT));
   cudaStream_t s = as_stream(stream);
-  uint32_t *p, *k;
-  PM_TRY(sort_particles(X, np, n, w, s, &p, &k));
+  uint32_t* p;
+  PM_TRY(sort_cells(X, np, n, w, s, cellstart ? cellstart : w.cellstart, &p));
   if (perm && np > 0) PM_TRY(cuda_status(cudaMemcpyAsync(perm, p, np * 4, cudaMemcpyDeviceToDevice, s)));
-  if (cellstart) PM_TRY(build_cellstart(k, np, n, cellstart, s));
   return launch_status();
 }
 
@@ -282,9 +279,8 @@ pm_status pm_deposit(const uint32_t* X, int64_t np, int n, float* rho, void* ws,
   Workspace w;
   PM_TRY(check_ws(w, ws, ws_bytes, n, np, PM_WS_SORT));
   cudaStream_t s = as_stream(stream);
-  uint32_t *p, *k;
-  PM_TRY(sort_particles(X, np, n, w, s, &p, &k));
-  PM_TRY(build_cellstart(k, np, n, w.cellstart, s));
+  uint32_t* p;
+  PM_TRY(sort_cells(X, np, n, w, s, w.cellstart, &p));
   PM_TRY(permute_particles(p, np, X, nullptr, nullptr, w.Xs, nullptr, nullptr, s));
   PM_TRY(deposit_sorted(w.Xs, np, w.cellstart, n, rho, w.partials, w.scalars, s));
   return launch_status();
@@ -373,9 +369,8 @@ pm_status pm_step(pm_state* st_, const pm_step_params* prm, pm_stats* stats, voi
   pm_stats local;
   memset(&local, 0, sizeof(local));
 
-  uint32_t *perm, *skeys;
-  PM_TRY(sort_particles(S.X, np, n, w, s, &perm, &skeys));
-  PM_TRY(build_cellstart(skeys, np, n, w.cellstart, s));
+  uint32_t* perm;
+  PM_TRY(sort_cells(S.X, np, n, w, s, w.cellstart, &perm));
   PM_TRY(permute_particles(perm, np, S.X, S.V, S.id, w.Xs, w.Vs, w.ids, s));
   PM_TRY(deposit_sorted(w.Xs, np, w.cellstart, n, w.rho, w.partials, w.scalars, s));
 
@@ -453,9 +448,8 @@ pm_status pm_interp_adj(const float* g, const uint32_t* X, int64_t np, int n, co
   PM_TRY(check_ws(w, ws, ws_bytes, n, np, PM_WS_SORT | PM_WS_ADJ));
   cudaStream_t s = as_stream(stream);
   const int64_t N = (int64_t)n * n * n;
-  uint32_t *perm, *skeys;
-  PM_TRY(sort_particles(X, np, n, w, s, &perm, &skeys));
-  PM_TRY(build_cellstart(skeys, np, n, w.cellstart, s));
+  uint32_t* perm;
+  PM_TRY(sort_cells(X, np, n, w, s, w.cellstart, &perm));
   // sorted positions and sorted acc_bar (the three planes permuted like X)
   PM_TRY(permute_particles(perm, np, X, acc_bar, nullptr, w.Xs, w.adj_abar, nullptr, s));
   for (int d = 0; d < 3; ++d)
@@ -493,9 +487,8 @@ pm_status pm_step_adj(pm_state* st_, const pm_step_params* prm, const float* phi
   cudaStream_t s = as_stream(stream);
   // the step's sort (cotangent deposits gather in cell order) and, without
   // phi_fwd, its force field recomputed at the input positions
-  uint32_t *perm, *skeys;
-  PM_TRY(sort_particles(S.X, np, n, w, s, &perm, &skeys));
-  PM_TRY(build_cellstart(skeys, np, n, w.cellstart, s));
+  uint32_t* perm;
+  PM_TRY(sort_cells(S.X, np, n, w, s, w.cellstart, &perm));
   PM_TRY(permute_particles(perm, np, S.X, nullptr, nullptr, w.Xs, nullptr, nullptr, s));
   mg_params mp = prm->mg;
   mp.first_guess = MG_GUESS_JACOBI;
@@ -561,9 +554,8 @@ pm_status pm_step_batch(pm_batch_state* st_, const pm_batch_params* prm, void* s
   bt.np_box = np_box;
   bt.dt_kick = prm->dt_kick;
   bt.dt_drift = prm->dt_drift;
-  uint32_t *perm, *skeys;
-  PM_TRY(sort_particles(S.X, np, n, w, s, &perm, &skeys, bt));
-  PM_TRY(build_cellstart(skeys, np, n, w.cellstart, s, B));
+  uint32_t* perm;
+  PM_TRY(sort_cells(S.X, np, n, w, s, w.cellstart, &perm, bt));
   PM_TRY(permute_particles(perm, np, S.X, S.V, nullptr, w.Xs, w.Vs, nullptr, s));
   PM_TRY(deposit_sorted_batch(w.Xs, np_box, B, w.cellstart, n, w.rho, w.partials, w.box_mean, s));
   mg_params mp = prm->mg;

@@ -50,12 +50,11 @@ extern "C" pm_status pm_deposit_noalloc(const uint32_t* X, int64_t np, int n, fl
   Workspace w;
   layout_workspace(&w, base, n, np, PM_WS_SORT);
   // Nothing in the scratch has to start at zero: every buffer the deposit
-  // reads (radix counts and offsets, cell starts, sorted positions, block
+  // reads (cell starts, keys, the permutation, sorted positions, block
   // partials) is fully written earlier in the same call.
   cudaStream_t s = (cudaStream_t)stream;
-  uint32_t *perm, *skeys;
-  PM_TRY(sort_particles(X, np, n, w, s, &perm, &skeys));
-  PM_TRY(build_cellstart(skeys, np, n, w.cellstart, s));
+  uint32_t* perm;
+  PM_TRY(sort_cells(X, np, n, w, s, w.cellstart, &perm));
   PM_TRY(permute_particles(perm, np, X, nullptr, nullptr, w.Xs, nullptr, nullptr, s));
   PM_TRY(deposit_sorted(w.Xs, np, w.cellstart, n, rho, w.partials, w.scalars, s));
   return launch_status();

@@ -10,7 +10,7 @@ namespace pmgb {
 
 // Kernel classes for launch counting and CUDA-event timing.
 enum KernelClass {
-  K_KEYS, K_SORT_UP, K_SORT_SCAN, K_SORT_DOWN, K_CELLSTART, K_PERMUTE,
+  K_KEYS, K_SORT_SCAN, K_SCATTER, K_ORDER, K_PERMUTE,
   K_DEPOSIT, K_REDUCE,
   K_MG_GUESS, K_MG_SMOOTH0, K_MG_SMOOTH, K_MG_RESTRICT, K_MG_PROLONG, K_MG_COARSE, K_MG_NORM,
   K_FR_SMOOTH0, K_FR_SMOOTH, K_FR_RESTRICT, K_FR_COARSEOP, K_FR_PROLONG, K_FR_COARSE, K_FR_NORM,
@@ -79,8 +79,7 @@ struct Workspace {
   char* base;
   size_t total;
   // sort
-  uint32_t* keys_a; uint32_t* keys_b; uint32_t* vals_a; uint32_t* vals_b;
-  uint32_t* counts; uint32_t* scan_blocks; uint32_t* cellstart;
+  uint2* keyrank; uint32_t* perm; uint32_t* runs; uint32_t* scan_blocks; uint32_t* cellstart;
   // particles in cell order
   uint32_t* Xs; float* Vs; uint32_t* ids;
   // grids
@@ -103,20 +102,20 @@ struct Workspace {
 size_t layout_workspace(Workspace* w, void* base, int n, int64_t np, uint32_t flags, int batch = 1);
 
 // Sizes of the scratch pieces.
-int64_t radix_tiles(int64_t np);
-int64_t radix_scan_blocks(int64_t np);
+int64_t sort_scan_blocks(int64_t ncells);
+int64_t sort_runs_capacity(int64_t np);
 int64_t reduce_partials_capacity(int n, int64_t np);
 // Work items of the streaming deposit for one box of n^3 cells (n >= 32).
 int deposit_items(int n);
 
 // ------------------------------------------------------ stage launchers --
-// Stable sort by cell key; with a batch the key is prefixed by the box
-// (particle index / np_box), so the order is by box, then cell.
-pm_status sort_particles(const uint32_t* X, int64_t np, int n, Workspace& w,
-                         cudaStream_t s, uint32_t** perm_out, uint32_t** skeys_out,
-                         const Batch& bt = Batch{});
-pm_status build_cellstart(const uint32_t* skeys, int64_t np, int n, uint32_t* cellstart,
-                          cudaStream_t s, int batch = 1);
+// Stable sort by cell key: *perm_out (in the workspace) lists the particles
+// in cell order, ties in input order, and cellstart[c] .. cellstart[c+1]-1 are
+// the ranks of cell c (cellstart [ncells + 1], cellstart[ncells] = np).  With
+// a batch the key is prefixed by the box (particle index / np_box), so the
+// order is by box, then cell, and ncells = B n^3.
+pm_status sort_cells(const uint32_t* X, int64_t np, int n, Workspace& w, cudaStream_t s, uint32_t* cellstart,
+                     uint32_t** perm_out, const Batch& bt = Batch{});
 pm_status permute_particles(const uint32_t* perm, int64_t np, const uint32_t* X, const float* V,
                             const uint32_t* id, uint32_t* Xs, float* Vs, uint32_t* ids,
                             cudaStream_t s);

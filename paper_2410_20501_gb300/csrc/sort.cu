@@ -1,80 +1,181 @@
-// Cell keys, stable LSD radix sort, cell start offsets and the particle
-// permutation: the cell ordering that replaces PySCo's periodic Morton
-// reordering (§3.2, Appendix E) and that the deterministic TSC gather needs.
+// Cell keys, the stable counting sort by cell, cell start offsets and the
+// particle permutation: the cell ordering that replaces PySCo's periodic
+// Morton reordering (§3.2, Appendix E) and that the deterministic TSC gather
+// needs.
 //
-// The radix sort is stable by construction: each tile ranks its keys with
-// warp-level __match_any_sync in (warp, round, lane) order, which is the input
-// order, so ties keep their input order and the permutation is bit-exact.
+// With about one particle per cell the cell index itself is the natural
+// bucket: one pass counts the particles of each cell with atomics into the
+// cell-start array, keeping each particle's rank among its cell's particles
+// (the value its atomic returned); an in-place exclusive scan turns the counts
+// into cell starts; one pass writes each particle to its cell's start plus its
+// rank.  The atomics leave the order of equal keys to the hardware, so a last
+// pass restores the stable order (ascending input index) inside every cell:
+// one thread per cell for short runs, one block per cell (bitonic chunks in
+// shared memory, then merges) for long ones.  The permutation is therefore
+// bit-exact and deterministic, equal to a stable sort by key.
+//
+// The step writes particles back in cell order, so the input of the next
+// step is nearly sorted: the counts and scatters then touch neighbouring
+// words and the per-cell runs are already in order.
 #include "pm_internal.cuh"
 
 namespace pmgb {
 
 namespace {
 
-constexpr int RT = 256;             // threads per radix block
-constexpr int RI = 16;              // keys per thread
-constexpr int RTILE = RT * RI;      // keys per tile
-constexpr int RWARPS = RT / 32;
-constexpr int RMAXBINS = 512;       // at most 9 bits per digit
-
 constexpr int SCAN_T = 1024;
 constexpr int SCAN_CHUNK = 4 * SCAN_T;
+constexpr int KT = 256;             // threads of the key, scatter and order kernels
+constexpr uint32_t SHORT_RUN = 32;  // runs up to this length are ordered by one thread
+constexpr int LT = 512;             // threads of a long-run block
+constexpr int LCH = 4096;           // elements sorted in shared memory at once
+constexpr int LONG_BLOCKS = 2 * 152;
+
+__device__ __forceinline__ uint32_t lanemask_lt() { return (1u << (threadIdx.x & 31)) - 1u; }
 
 // key = (i n + j) n + k of the cell holding each particle; with np_box > 0
-// (a batch of boxes) prefixed by the box, i / np_box.
+// (a batch of boxes) prefixed by the box, i / np_box.  Counts the particles of
+// each cell into cnt[key] (zeroed) with one atomic per run of equal keys in a
+// warp and stores kr[i] = (key, rank of i among its cell's particles).
 template <bool BOX>
-__global__ void k_cell_keys(const uint32_t* __restrict__ X, int64_t np, int log2n, int64_t np_box,
-                            uint32_t* __restrict__ keys) {
-  const int sh = 32 - log2n;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < np;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    uint32_t ix = __ldg(X + i) >> sh;
-    uint32_t iy = __ldg(X + np + i) >> sh;
-    uint32_t iz = __ldg(X + 2 * np + i) >> sh;
-    uint32_t key = (((ix << log2n) | iy) << log2n) | iz;
+__global__ void __launch_bounds__(KT) k_cell_count(const uint32_t* __restrict__ X, int64_t np, int log2n,
+                                                   int64_t np_box, uint2* __restrict__ kr,
+                                                   uint32_t* __restrict__ cnt) {
+  const int64_t i = blockIdx.x * (int64_t)KT + threadIdx.x;
+  const bool valid = i < np;
+  uint32_t key = 0xffffffffu;
+  if (valid) {
+    const int sh = 32 - log2n;
+    const uint32_t ix = __ldg(X + i) >> sh;
+    const uint32_t iy = __ldg(X + np + i) >> sh;
+    const uint32_t iz = __ldg(X + 2 * np + i) >> sh;
+    key = (((ix << log2n) | iy) << log2n) | iz;
     if (BOX) key |= (uint32_t)(i / np_box) << (3 * log2n);
-    keys[i] = key;
+  }
+  const uint32_t peers = __match_any_sync(0xffffffffu, key);
+  const int leader = __ffs(peers) - 1;
+  uint32_t r = 0;
+  if (valid && (int)(threadIdx.x & 31) == leader) r = atomicAdd(cnt + key, (uint32_t)__popc(peers));
+  r = __shfl_sync(0xffffffffu, r, leader);
+  if (valid) kr[i] = make_uint2(key, r + __popc(peers & lanemask_lt()));
+}
+
+// perm[cellstart[key] + rank] = i.
+__global__ void __launch_bounds__(KT) k_cell_scatter(const uint2* __restrict__ kr, int64_t np,
+                                                     const uint32_t* __restrict__ cellstart,
+                                                     uint32_t* __restrict__ perm) {
+  const int64_t i = blockIdx.x * (int64_t)KT + threadIdx.x;
+  if (i >= np) return;
+  const uint2 t = __ldg(kr + i);
+  perm[__ldg(cellstart + t.x) + t.y] = (uint32_t)i;
+}
+
+// Stable order inside each cell: the ranks of cell c, cellstart[c] ..
+// cellstart[c+1]-1, in ascending particle index.  Runs of at most SHORT_RUN
+// are insertion-sorted here; longer ones are listed in runs[1 ..] (runs[0]
+// counts them, zeroed) for k_cell_order_long.
+__global__ void __launch_bounds__(KT) k_cell_order(const uint32_t* __restrict__ cellstart, int64_t ncells,
+                                                   uint32_t* __restrict__ perm, uint32_t* __restrict__ runs) {
+  const int64_t c = blockIdx.x * (int64_t)KT + threadIdx.x;
+  if (c >= ncells) return;
+  const uint32_t a = __ldg(cellstart + c), b = __ldg(cellstart + c + 1);
+  if (b - a < 2) return;
+  if (b - a > SHORT_RUN) {
+    runs[1 + atomicAdd(runs, 1u)] = (uint32_t)c;
+    return;
+  }
+  for (uint32_t p = a + 1; p < b; ++p) {
+    const uint32_t v = perm[p];
+    uint32_t q = p;
+    for (; q > a; --q) {
+      const uint32_t u = perm[q - 1];
+      if (u < v) break;
+      perm[q] = u;
+    }
+    perm[q] = v;
   }
 }
 
-// Per-tile digit histogram, written digit-major: counts[d * ntiles + tile].
-// Each thread counts RI consecutive keys and adds runs of equal digits with
-// one shared atomic (cell-ordered input has long runs in the high digits).
-__global__ void __launch_bounds__(RT) k_radix_up(const uint32_t* __restrict__ keys, int64_t np,
-                                                 int shift, int rbits,
-                                                 uint32_t* __restrict__ counts, int64_t ntiles) {
-  __shared__ uint32_t hist[RMAXBINS];
-  const int R = 1 << rbits;
-  for (int d = threadIdx.x; d < R; d += RT) hist[d] = 0;
-  __syncthreads();
-  const int64_t base = (int64_t)blockIdx.x * RTILE + (int64_t)threadIdx.x * RI;
-  uint32_t k[RI];
-  if (base + RI <= np) {
-    const uint4* v = reinterpret_cast<const uint4*>(keys + base);
-#pragma unroll
-    for (int q = 0; q < RI / 4; ++q) {
-      const uint4 t = __ldg(v + q);
-      k[4 * q] = t.x; k[4 * q + 1] = t.y; k[4 * q + 2] = t.z; k[4 * q + 3] = t.w;
+// Ascending bitonic sort of s[0 .. p2) (p2 a power of two) by the block.
+__device__ void block_bitonic(uint32_t* s, int p2) {
+  for (int k = 2; k <= p2; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int t = threadIdx.x; t < (p2 >> 1); t += LT) {
+        const int i = 2 * t - (t & (j - 1)), l = i + j;
+        const uint32_t x = s[i], y = s[l];
+        if ((x > y) == ((i & k) == 0)) {
+          s[i] = y;
+          s[l] = x;
+        }
+      }
+      __syncthreads();
     }
-  } else {
-#pragma unroll
-    for (int r = 0; r < RI; ++r) k[r] = base + r < np ? __ldg(keys + base + r) : 0xffffffffu;
   }
-  uint32_t cur = 0xffffffffu, run = 0;
-#pragma unroll
-  for (int r = 0; r < RI; ++r) {
-    if (base + r >= np) break;
-    const uint32_t d = (k[r] >> shift) & (R - 1);
-    if (d != cur) {
-      if (run) atomicAdd(&hist[cur], run);
-      cur = d;
-      run = 0;
+}
+
+// out[0 .. la+lb) = merge of the ascending runs A[0 .. la) and B[0 .. lb),
+// split evenly over the block's threads along the merge path.
+__device__ void block_merge(const uint32_t* A, int64_t la, const uint32_t* B, int64_t lb, uint32_t* out) {
+  const int64_t L = la + lb;
+  const int64_t d0 = L * threadIdx.x / LT, d1 = L * (threadIdx.x + 1) / LT;
+  int64_t lo = d0 > lb ? d0 - lb : 0, hi = d0 < la ? d0 : la;
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) >> 1;
+    if (A[mid] < B[d0 - 1 - mid]) lo = mid + 1;
+    else hi = mid;
+  }
+  int64_t ia = lo, ib = d0 - lo;
+  for (int64_t d = d0; d < d1; ++d) {
+    const bool take_a = ib >= lb || (ia < la && A[ia] < B[ib]);
+    out[d] = take_a ? A[ia++] : B[ib++];
+  }
+}
+
+// The long runs listed by k_cell_order, one block each: LCH-element chunks
+// sorted in shared memory, then pairwise merges between the run and the same
+// ranks of `scratch`.  Runs already in order are left as they are.
+__global__ void __launch_bounds__(LT) k_cell_order_long(const uint32_t* __restrict__ cellstart,
+                                                        const uint32_t* __restrict__ runs,
+                                                        uint32_t* __restrict__ perm,
+                                                        uint32_t* __restrict__ scratch) {
+  __shared__ uint32_t sv[LCH];
+  const uint32_t nruns = runs[0];
+  for (uint32_t q = blockIdx.x; q < nruns; q += gridDim.x) {
+    const uint32_t c = runs[1 + q];
+    const uint32_t a = cellstart[c];
+    const int64_t m = (int64_t)cellstart[c + 1] - a;
+    uint32_t* seg = perm + a;
+    int unsorted = 0;
+    for (int64_t t = threadIdx.x; t + 1 < m; t += LT) unsorted |= seg[t] > seg[t + 1];
+    if (!__syncthreads_or(unsorted)) continue;
+    for (int64_t c0 = 0; c0 < m; c0 += LCH) {
+      const int len = (int)(m - c0 < LCH ? m - c0 : LCH);
+      int p2 = 1;
+      while (p2 < len) p2 <<= 1;
+      for (int t = threadIdx.x; t < p2; t += LT) sv[t] = t < len ? seg[c0 + t] : 0xffffffffu;
+      __syncthreads();
+      block_bitonic(sv, p2);
+      for (int t = threadIdx.x; t < len; t += LT) seg[c0 + t] = sv[t];
+      __syncthreads();
     }
-    ++run;
+    uint32_t* in = seg;
+    uint32_t* out = scratch + a;
+    for (int64_t w = LCH; w < m; w *= 2) {
+      for (int64_t lo = 0; lo < m; lo += 2 * w) {
+        const int64_t la = m - lo < w ? m - lo : w;
+        const int64_t rest = m - lo - la;
+        block_merge(in + lo, la, in + lo + la, rest < w ? rest : w, out + lo);
+      }
+      __syncthreads();
+      uint32_t* t = in;
+      in = out;
+      out = t;
+    }
+    if (in != seg) {
+      for (int64_t t = threadIdx.x; t < m; t += LT) seg[t] = in[t];
+    }
+    __syncthreads();
   }
-  if (run) atomicAdd(&hist[cur], run);
-  __syncthreads();
-  for (int d = threadIdx.x; d < R; d += RT) counts[(int64_t)d * ntiles + blockIdx.x] = hist[d];
 }
 
 // ---- exclusive scan of a uint32 array (three kernels) ----
@@ -113,8 +214,13 @@ __global__ void __launch_bounds__(SCAN_T) k_scan_reduce(const uint32_t* __restri
   __shared__ uint32_t tot;
   const int64_t base = (int64_t)blockIdx.x * SCAN_CHUNK + (int64_t)threadIdx.x * 4;
   uint32_t v = 0;
-  for (int k = 0; k < 4; ++k)
-    if (base + k < len) v += a[base + k];
+  if (base + 4 <= len && ((uintptr_t)a & 15) == 0) {
+    const uint4 t = __ldg(reinterpret_cast<const uint4*>(a + base));
+    v = t.x + t.y + t.z + t.w;
+  } else {
+    for (int k = 0; k < 4; ++k)
+      if (base + k < len) v += a[base + k];
+  }
   block_exclusive_scan(v, wt, &tot);
   if (threadIdx.x == 0) sums[blockIdx.x] = tot;
 }
@@ -138,124 +244,23 @@ __global__ void __launch_bounds__(SCAN_T) k_scan_apply(uint32_t* __restrict__ a,
   __shared__ uint32_t wt[32];
   __shared__ uint32_t tot;
   const int64_t base = (int64_t)blockIdx.x * SCAN_CHUNK + (int64_t)threadIdx.x * 4;
+  const bool vec = base + 4 <= len && ((uintptr_t)a & 15) == 0;
   uint32_t v[4], s = 0;
-  for (int k = 0; k < 4; ++k) {
-    v[k] = base + k < len ? a[base + k] : 0;
-    s += v[k];
+  if (vec) {
+    const uint4 t = *reinterpret_cast<const uint4*>(a + base);
+    v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+  } else {
+    for (int k = 0; k < 4; ++k) v[k] = base + k < len ? a[base + k] : 0;
   }
+  for (int k = 0; k < 4; ++k) s += v[k];
   uint32_t e = block_exclusive_scan(s, wt, &tot) + sums[blockIdx.x];
-  for (int k = 0; k < 4; ++k) {
-    if (base + k < len) a[base + k] = e;
-    e += v[k];
-  }
-}
-
-// Stable scatter of one digit pass.  offsets[d * ntiles + tile] is the global
-// rank of the first key of digit d in this tile.
-__global__ void __launch_bounds__(RT) k_radix_down(const uint32_t* __restrict__ keys_in,
-                                                   const uint32_t* __restrict__ vals_in,
-                                                   int64_t np, int shift, int rbits,
-                                                   const uint32_t* __restrict__ offsets,
-                                                   int64_t ntiles,
-                                                   uint32_t* __restrict__ keys_out,
-                                                   uint32_t* __restrict__ vals_out) {
-  extern __shared__ uint32_t smem[];
-  uint32_t* whist = smem;                          // [RWARPS][RMAXBINS]
-  uint32_t* tprefix = whist + RWARPS * RMAXBINS;   // [RMAXBINS]
-  uint32_t* goff = tprefix + RMAXBINS;             // [RMAXBINS]
-  uint32_t* skeys = goff + RMAXBINS;               // [RTILE]
-  uint32_t* svals = skeys + RTILE;                 // [RTILE]
-  __shared__ uint32_t wt[32];
-  __shared__ uint32_t tot;
-
-  const int R = 1 << rbits;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  for (int i = tid; i < RWARPS * RMAXBINS; i += RT) whist[i] = 0;
-  __syncthreads();
-
-  const int64_t base = (int64_t)blockIdx.x * RTILE;
-  const int64_t wbase = base + (int64_t)warp * (RI * 32);
-  const uint32_t lt = (1u << lane) - 1u;
-  uint32_t k[RI], v[RI], rk[RI];
-  // issue every load of the tile before the ranking rounds
-#pragma unroll
-  for (int r = 0; r < RI; ++r) {
-    const int64_t i = wbase + r * 32 + lane;
-    k[r] = i < np ? __ldg(keys_in + i) : 0u;
-  }
-#pragma unroll
-  for (int r = 0; r < RI; ++r) {
-    const int64_t i = wbase + r * 32 + lane;
-    v[r] = i < np ? (vals_in ? __ldg(vals_in + i) : (uint32_t)i) : 0u;
-  }
-#pragma unroll
-  for (int r = 0; r < RI; ++r) {
-    int64_t i = wbase + r * 32 + lane;
-    bool valid = i < np;
-    uint32_t key = k[r];
-    uint32_t d = valid ? ((key >> shift) & (R - 1)) : (uint32_t)R;
-    uint32_t peers = __match_any_sync(0xffffffffu, d);
-    int leader = __ffs(peers) - 1;
-    uint32_t b = (valid && lane == leader) ? whist[warp * RMAXBINS + d] : 0u;
-    b = __shfl_sync(0xffffffffu, b, leader);
-    __syncwarp();
-    if (valid && lane == leader) whist[warp * RMAXBINS + d] = b + __popc(peers);
-    __syncwarp();
-    rk[r] = valid ? b + __popc(peers & lt) : 0xffffffffu;
-  }
-  __syncthreads();
-  for (int d = tid; d < RMAXBINS; d += RT) {
-    uint32_t run = 0;
-    if (d < R) {
-      for (int w = 0; w < RWARPS; ++w) {
-        uint32_t t = whist[w * RMAXBINS + d];
-        whist[w * RMAXBINS + d] = run;
-        run += t;
-      }
-      goff[d] = offsets[(int64_t)d * ntiles + blockIdx.x];
+  if (vec) {
+    *reinterpret_cast<uint4*>(a + base) = make_uint4(e, e + v[0], e + v[0] + v[1], e + v[0] + v[1] + v[2]);
+  } else {
+    for (int k = 0; k < 4; ++k) {
+      if (base + k < len) a[base + k] = e;
+      e += v[k];
     }
-    tprefix[d] = run;
-  }
-  __syncthreads();
-  // exclusive scan of tprefix[0..511], two digits per thread
-  {
-    uint32_t a0 = tprefix[2 * tid], a1 = tprefix[2 * tid + 1];
-    uint32_t e = block_exclusive_scan(a0 + a1, wt, &tot);
-    tprefix[2 * tid] = e;
-    tprefix[2 * tid + 1] = e + a0;
-  }
-  __syncthreads();
-#pragma unroll
-  for (int r = 0; r < RI; ++r) {
-    if (rk[r] != 0xffffffffu) {
-      uint32_t d = (k[r] >> shift) & (R - 1);
-      uint32_t lp = tprefix[d] + whist[warp * RMAXBINS + d] + rk[r];
-      skeys[lp] = k[r];
-      svals[lp] = v[r];
-    }
-  }
-  __syncthreads();
-  const int64_t rem = np - base;
-  const int tile_n = rem < RTILE ? (int)rem : RTILE;
-  for (int i = tid; i < tile_n; i += RT) {
-    uint32_t key = skeys[i];
-    uint32_t d = (key >> shift) & (R - 1);
-    uint32_t pos = goff[d] + (uint32_t)(i - (int)tprefix[d]);
-    keys_out[pos] = key;
-    vals_out[pos] = svals[i];
-  }
-}
-
-constexpr size_t kDownSmem = sizeof(uint32_t) * (RWARPS * RMAXBINS + 2 * RMAXBINS + 2 * RTILE);
-
-// cellstart[c] = first rank whose key is >= c; cellstart[ncells] = np.
-__global__ void k_cellstart(const uint32_t* __restrict__ skeys, int64_t np, uint32_t ncells,
-                            uint32_t* __restrict__ cellstart) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i <= np;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    uint32_t lo = i == 0 ? 0u : skeys[i - 1] + 1u;
-    uint32_t hi = i == np ? ncells : skeys[i];
-    for (uint32_t c = lo; c <= hi && c <= ncells; ++c) cellstart[c] = (uint32_t)i;
   }
 }
 
@@ -285,58 +290,33 @@ pm_status scan_u32(uint32_t* a, int64_t len, uint32_t* sums, cudaStream_t s) {
   return PM_OK;
 }
 
+
 }  // namespace
 
-int64_t radix_tiles(int64_t np) { return (np + RTILE - 1) / RTILE; }
+int64_t sort_scan_blocks(int64_t ncells) { return (ncells + 1 + SCAN_CHUNK - 1) / SCAN_CHUNK + 1; }
 
-int64_t radix_scan_blocks(int64_t np) {
-  return (radix_tiles(np) * RMAXBINS + SCAN_CHUNK - 1) / SCAN_CHUNK + 1;
-}
+int64_t sort_runs_capacity(int64_t np) { return np / (SHORT_RUN + 1) + 2; }
 
-pm_status sort_particles(const uint32_t* X, int64_t np, int n, Workspace& w, cudaStream_t s,
-                         uint32_t** perm_out, uint32_t** skeys_out, const Batch& bt) {
-  static bool attr_done = false;
-  if (!attr_done) {
-    PM_TRY(cuda_status(cudaFuncSetAttribute(k_radix_down, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                            (int)kDownSmem)));
-    attr_done = true;
-  }
+pm_status sort_cells(const uint32_t* X, int64_t np, int n, Workspace& w, cudaStream_t s, uint32_t* cellstart,
+                     uint32_t** perm_out, const Batch& bt) {
   const int log2n = ilog2(n);
-  *perm_out = w.vals_a;
-  *skeys_out = w.keys_a;
+  const int64_t ncells = (int64_t)n * n * n * bt.B;
+  *perm_out = w.perm;
+  PM_TRY(cuda_status(cudaMemsetAsync(cellstart, 0, (size_t)(ncells + 1) * 4, s)));
   if (np == 0) return PM_OK;
   const int64_t np_box = bt.B > 1 ? bt.np_box : 0;
+  const unsigned gp = grid_for(np, KT);
   if (np_box > 0)
-    PM_LAUNCH(K_KEYS, 16.0 * np, k_cell_keys<true>, grid_for(np, 256), 256, 0, s, X, np, log2n, np_box, w.keys_a);
+    PM_LAUNCH(K_KEYS, 28.0 * np, k_cell_count<true>, gp, KT, 0, s, X, np, log2n, np_box, w.keyrank, cellstart);
   else
-    PM_LAUNCH(K_KEYS, 16.0 * np, k_cell_keys<false>, grid_for(np, 256), 256, 0, s, X, np, log2n, np_box, w.keys_a);
-  const int keybits = 3 * log2n + (bt.B > 1 ? ilog2(2 * bt.B - 1) : 0);   // + ceil(log2 B) box bits
-  const int passes = (keybits + 8) / 9;
-  const int bpp = (keybits + passes - 1) / passes;
-  const int64_t ntiles = radix_tiles(np);
-  uint32_t *kin = w.keys_a, *vin = nullptr;
-  for (int p = 0; p < passes; ++p) {
-    const int shift = p * bpp;
-    const int rb = (keybits - shift) < bpp ? (keybits - shift) : bpp;
-    const int64_t len = ((int64_t)1 << rb) * ntiles;
-    uint32_t* kout = (kin == w.keys_a) ? w.keys_b : w.keys_a;
-    uint32_t* vout = (vin == w.vals_b) ? w.vals_a : w.vals_b;
-    PM_LAUNCH(K_SORT_UP, 4.0 * np, k_radix_up, (unsigned)ntiles, RT, 0, s, kin, np, shift, rb, w.counts, ntiles);
-    PM_TRY(scan_u32(w.counts, len, w.scan_blocks, s));
-    PM_LAUNCH(K_SORT_DOWN, (vin ? 16.0 : 12.0) * np, k_radix_down, (unsigned)ntiles, RT, kDownSmem, s, kin, vin, np, shift, rb,
-              w.counts, ntiles, kout, vout);
-    kin = kout;
-    vin = vout;
-  }
-  *perm_out = vin;
-  *skeys_out = kin;
-  return launch_status();
-}
-
-pm_status build_cellstart(const uint32_t* skeys, int64_t np, int n, uint32_t* cellstart,
-                          cudaStream_t s, int batch) {
-  const uint32_t ncells = (uint32_t)((int64_t)n * n * n * batch);
-  PM_LAUNCH(K_CELLSTART, 4.0 * np + 4.0 * (ncells + 1.0), k_cellstart, grid_for(np + 1, 256), 256, 0, s, skeys, np, ncells, cellstart);
+    PM_LAUNCH(K_KEYS, 28.0 * np, k_cell_count<false>, gp, KT, 0, s, X, np, log2n, np_box, w.keyrank, cellstart);
+  PM_TRY(scan_u32(cellstart, ncells + 1, w.scan_blocks, s));
+  PM_LAUNCH(K_SCATTER, 16.0 * np, k_cell_scatter, gp, KT, 0, s, w.keyrank, np, cellstart, w.perm);
+  PM_TRY(cuda_status(cudaMemsetAsync(w.runs, 0, 4, s)));
+  PM_LAUNCH(K_ORDER, 4.0 * ncells + 8.0 * np, k_cell_order, grid_for(ncells, KT), KT, 0, s, cellstart, ncells,
+            w.perm, w.runs);
+  PM_LAUNCH(K_ORDER, 0.0, k_cell_order_long, LONG_BLOCKS, LT, 0, s, cellstart, w.runs, w.perm,
+            reinterpret_cast<uint32_t*>(w.keyrank));
   return launch_status();
 }
 

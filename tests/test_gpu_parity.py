@@ -56,6 +56,47 @@ def test_sort_nearly_sorted_with_many_ties(pm):
     assert np.array_equal(perm.cpu().numpy().view(np.uint32), mesh.stable_cell_order(X, n))
 
 
+def clustered(n, counts, seed, background=0):
+    """Particles piled into a few cells: counts[q] particles uniformly inside
+    cell q * 37 % n^3 (plus `background` uniform ones), in seeded random order."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    pos = [rng.uniform(0.0, 1.0, (3, background))]
+    for q, m in enumerate(counts):
+        c = (q * 37) % n ** 3
+        ijk = np.array([c // (n * n), (c // n) % n, c % n], dtype=np.float64)[:, None]
+        pos.append((ijk + rng.uniform(0.0, 1.0, (3, m))) / n)
+    pos = np.concatenate(pos, axis=1)
+    return inputs.to_fixed_point(pos[:, rng.permutation(pos.shape[1])])
+
+
+@pytest.mark.parametrize("counts,background", [
+    ([32, 33, 34, 64, 100], 3000),              # around the one-thread limit
+    ([4095, 4096, 4097, 8193], 20000),          # one and several shared-memory chunks
+    ([150000, 999, 2], 50000),                  # a long run merged over several passes
+])
+def test_sort_long_runs(pm, counts, background):
+    """Cells holding long runs of particles in shuffled order: the stable
+    order (ties by input index) is restored inside every cell."""
+    n = 16
+    X = clustered(n, counts, 5 + len(counts), background)
+    perm, cs = pm.sort(pm.positions_to_device(X), n)
+    ref = mesh.stable_cell_order(X, n)
+    assert np.array_equal(perm.cpu().numpy().view(np.uint32), ref)
+    keys = mesh.cell_key(X, n)[ref]
+    ref_cs = np.searchsorted(keys, np.arange(n ** 3 + 1), side="left").astype(np.uint32)
+    assert np.array_equal(cs.cpu().numpy().view(np.uint32), ref_cs)
+
+
+def test_sort_of_sorted_input_is_identity(pm):
+    """Particles already in stable cell order (as the step leaves them) sort to
+    the identity, long runs included."""
+    n = 16
+    X = clustered(n, [5000, 40, 3], 11, 30000)
+    X = np.ascontiguousarray(X[:, mesh.stable_cell_order(X, n)])
+    perm, _ = pm.sort(pm.positions_to_device(X), n)
+    assert np.array_equal(perm.cpu().numpy().view(np.uint32), np.arange(X.shape[1], dtype=np.uint32))
+
+
 # --------------------------------------------------------------- deposit ---
 
 @pytest.mark.parametrize("n,kind", [(8, "lattice"), (32, "lattice"), (64, "lattice"), (32, "random"),
