@@ -478,7 +478,10 @@ def run_stage(args):
     n = args.n
     X = None
     if args.stage in ("sort", "deposit"):
-        X = pm.positions_to_device(inputs.uniform_particles(n ** 3, 61))
+        # nearly cell-ordered, as a step receives the particles the previous
+        # step wrote back: lattice order, displaced by up to 0.7 cells
+        rng = np.random.Generator(np.random.PCG64(61))
+        X = pm.positions_to_device(inputs.to_fixed_point(inputs.lattice(n) + rng.uniform(-0.7, 0.7, (3, n ** 3)) / n))
     elif args.stage == "interp":   # cell-ordered particles, as pm_step interpolates them
         rng = np.random.Generator(np.random.PCG64(61))
         X = pm.positions_to_device(inputs.to_fixed_point(inputs.lattice(n) + rng.uniform(-0.45, 0.45, (3, n ** 3)) / n))

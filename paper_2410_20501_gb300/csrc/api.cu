@@ -524,7 +524,7 @@ bool valid_batch(int n, int B, int64_t np_box) {
   if (!valid_n(n) || n < 32 || B < 1 || np_box < 0) return false;
   if ((int64_t)B * np_box >= ((int64_t)1 << 31)) return false;
   const int bbits = B > 1 ? ilog2(2 * (int64_t)B - 1) : 0;
-  return 3 * ilog2(n) + bbits <= 32;
+  return 3 * ilog2(n) + bbits <= 31;   // (box, cell) keys below 2^31: the all-ones key is the sort's sentinel
 }
 
 pm_status pm_batch_workspace_size(int n, int B, int64_t np_box, size_t* bytes) {

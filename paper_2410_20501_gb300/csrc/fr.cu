@@ -171,7 +171,18 @@ __global__ void __launch_bounds__(256) k_fr_sweep(float* __restrict__ e, Src b, 
   e[c] = fr_update<NH>(e[c], nb, bv, beta, kappa, q);
 }
 
-// eH = rH = R eps, bH = R(b - N_h eps).
+// The non-linear flux of N_h through one face, (u_nb^(n+1) - u^(n+1)) in
+// eps differences; it changes sign with the face's orientation.
+template <int NH>
+__device__ __forceinline__ float fr_flux(float enb, float ec) {
+  if (NH == 1) return (enb - ec) * (2.0f + enb + ec);
+  const float s = enb + ec;
+  return (enb - ec) * (fmaf(3.0f, s, 3.0f) + fmaf(enb, s, ec * ec));
+}
+
+// eH = rH = R eps, bH = R(b - N_h eps).  Summed over the 2x2x2 block the
+// fluxes through the 12 inner faces cancel pairwise, so only the 24 outer
+// faces enter the restricted operator.
 template <int NH>
 __global__ void k_fr_restrict(const float* __restrict__ e, Src b, int log2n, float alpha, float kappa,
                               float* __restrict__ eH, float* __restrict__ rH, float* __restrict__ bH) {
@@ -183,25 +194,35 @@ __global__ void k_fr_restrict(const float* __restrict__ e, Src b, int log2n, flo
     const int K = (int)(t & mc), J = (int)((t >> lc) & mc), I = (int)(t >> (2 * lc));
     float core[2][2][4], xf[2][2][2], yf[2][2][2];
     load_children_block(e, I, J, K, log2n, core, xf, yf);
-    float se = 0.0f, sd = 0.0f;
+    float se = 0.0f, sb = 0.0f, sk = 0.0f;
 #pragma unroll
     for (int a = 0; a < 2; ++a)
 #pragma unroll
       for (int bb = 0; bb < 2; ++bb) {
         const float2 br = __ldg(reinterpret_cast<const float2*>(b.p + idx3(2 * I + a, 2 * J + bb, 2 * K, log2n)));
-        const float bz[2] = {b.s * (br.x - mean), b.s * (br.y - mean)};
+        sb += b.s * (br.x - mean) + b.s * (br.y - mean);
 #pragma unroll
         for (int cc = 0; cc < 2; ++cc) {
-          float nb[6];
-          child_nb(core, xf, yf, a, bb, cc, nb);
           const float ec = core[a][bb][cc + 1];
           se += ec;
-          sd += bz[cc] - fr_op<NH>(ec, nb, alpha, kappa);
+          sk += ec / (1.0f + ec);
         }
       }
+    float L[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+    for (int p = 0; p < 2; ++p)
+#pragma unroll
+      for (int c = 0; c < 2; ++c)
+#pragma unroll
+        for (int side = 0; side < 2; ++side) {
+          L[0] += fr_flux<NH>(xf[side][p][c], core[side][p][c + 1]);       // x faces of children (side, p, c)
+          L[1] += fr_flux<NH>(yf[p][side][c], core[p][side][c + 1]);       // y faces of children (p, side, c)
+          L[2] += fr_flux<NH>(core[p][c][side ? 3 : 0], core[p][c][side ? 2 : 1]);   // z faces of (p, c, side)
+        }
+    const float ops = fmaf(alpha, (L[0] + L[1]) + L[2], kappa * sk);
     eH[t] = 0.125f * se;
     rH[t] = 0.125f * se;
-    bH[t] = 0.125f * sd;
+    bH[t] = 0.125f * (sb - ops);
   }
 }
 

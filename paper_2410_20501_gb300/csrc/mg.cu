@@ -105,7 +105,13 @@ __global__ void k_rb_sweep(float* __restrict__ u, Src f, int log2n, int colour, 
   }
 }
 
-// Coarse right-hand side fc = R(f - L u): residual of the 8 children, averaged.
+// Coarse right-hand side fc = R(f - L u): residual of the 8 children,
+// averaged.  Summed over the 2x2x2 block the Laplacian fluxes through the 12
+// inner faces cancel pairwise, so  h^2 sum_c L u_c  is the sum of
+// (u_nb - u_c) over the 24 outer faces only.  With COMP the differences are
+// exact (TwoSum) and summed with compensation, as is the sum of the sources,
+// and the one cancelling subtraction is a single rounding (fused
+// multiply-add).
 template <bool COMP>
 __global__ void k_resid_restrict(const float* __restrict__ u, Src f, int log2n, float inv_h2,
                                  float* __restrict__ fc) {
@@ -120,32 +126,57 @@ __global__ void k_resid_restrict(const float* __restrict__ u, Src f, int log2n, 
     const int K = (int)(t & mc), J = (int)((t >> lc) & mc), I = (int)(t >> (2 * lc));
     float core[2][2][4], xf[2][2][2], yf[2][2][2];
     load_children_block(u, I, J, K, log2n, core, xf, yf);
-    float sum = 0.0f;
+    float fz[8];
 #pragma unroll
     for (int a = 0; a < 2; ++a)
 #pragma unroll
       for (int b = 0; b < 2; ++b) {
         const float2 fr = __ldg(reinterpret_cast<const float2*>(f.p + idx3(2 * I + a, 2 * J + b, 2 * K, log2n)));
-        const float fz[2] = {f.s * (fr.x - mean), f.s * (fr.y - mean)};
-#pragma unroll
-        for (int cc = 0; cc < 2; ++cc) {
-          float nb[6];
-          child_nb(core, xf, yf, a, b, cc, nb);
-          const float uc = core[a][b][cc + 1], fv = fz[cc];
-          float d;
-          if (COMP) {
-            float S, E;
-            lap_diff_comp(uc, nb, S, E);
-            d = fmaf(-inv_h2, S, fv) - inv_h2 * E;
-          } else {
-            const float L = ((nb[0] - uc) + (nb[1] - uc)) + ((nb[2] - uc) + (nb[3] - uc)) +
-                            ((nb[4] - uc) + (nb[5] - uc));
-            d = fv - inv_h2 * L;
-          }
-          sum += d;
-        }
+        fz[(a * 2 + b) * 2] = f.s * (fr.x - mean);
+        fz[(a * 2 + b) * 2 + 1] = f.s * (fr.y - mean);
       }
-    fc[t] = 0.125f * sum;
+    // outer faces (neighbour, child): x-, x+ for each (b, c); y-, y+ for each
+    // (a, c); z-, z+ for each (a, b)
+    float nbv[24], chv[24];
+#pragma unroll
+    for (int b = 0; b < 2; ++b)
+#pragma unroll
+      for (int c = 0; c < 2; ++c)
+#pragma unroll
+        for (int side = 0; side < 2; ++side) {
+          const int q = (b * 2 + c) * 2 + side;
+          nbv[q] = xf[side][b][c];
+          chv[q] = core[side][b][c + 1];
+          nbv[8 + q] = yf[b][side][c];          // here b plays a (x offset)
+          chv[8 + q] = core[b][side][c + 1];
+          nbv[16 + q] = core[b][c][side ? 3 : 0];   // here (b, c) play (a, b)
+          chv[16 + q] = core[b][c][side ? 2 : 1];
+        }
+    float d;
+    if (COMP) {
+      float S, E, sq, eq, tq;
+      two_sum(nbv[0], -chv[0], S, E);
+#pragma unroll
+      for (int q = 1; q < 24; ++q) {
+        two_sum(nbv[q], -chv[q], sq, eq);
+        two_sum(S, sq, S, tq);
+        E += tq + eq;
+      }
+      float F = fz[0], Fe = 0.0f;
+#pragma unroll
+      for (int q = 1; q < 8; ++q) {
+        two_sum(F, fz[q], F, tq);
+        Fe += tq;
+      }
+      d = fmaf(-inv_h2, S, F) + (Fe - inv_h2 * E);
+    } else {
+      float L[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+      for (int q = 0; q < 24; ++q) L[q & 3] += nbv[q] - chv[q];
+      const float F = ((fz[0] + fz[1]) + (fz[2] + fz[3])) + ((fz[4] + fz[5]) + (fz[6] + fz[7]));
+      d = fmaf(-inv_h2, (L[0] + L[1]) + (L[2] + L[3]), F);
+    }
+    fc[t] = 0.125f * d;
   }
 }
 
@@ -175,10 +206,11 @@ __global__ void __launch_bounds__(256) k_resid_norm(const float* __restrict__ u,
 }
 
 // u += P(uc - uc2): cell-centred trilinear prolongation, weights 27/9/3/1 over
-// 64 (§3.6.1); uc2 may be NULL.  One thread per coarse cell: it reads the
-// 3x3x3 coarse neighbourhood once and corrects its 8 children (pairs along z
-// as float2).  Per child the interpolation runs z, then y, then x, parent
-// (weight 3/4) before neighbour (1/4), in fused multiply-adds.
+// 64 (§3.6.1); uc2 may be NULL.  One thread per two coarse cells along z
+// (K = 2G, 2G + 1): it reads their 3x3x4 coarse neighbourhood once (a float2
+// and two scalars per coarse row) and corrects their 16 children (runs of
+// four along z as float4).  Per child the interpolation runs z, then y, then
+// x, parent (weight 3/4) before neighbour (1/4), in fused multiply-adds.
 __global__ void k_prolong_correct(float* __restrict__ u, const float* __restrict__ uc,
                                   const float* __restrict__ uc2, int log2n) {
   const int lc = log2n - 1, mc = (1 << lc) - 1;
@@ -186,45 +218,54 @@ __global__ void k_prolong_correct(float* __restrict__ u, const float* __restrict
   u += (int64_t)blockIdx.z << (3 * log2n);
   uc += (int64_t)blockIdx.z * total;
   if (uc2) uc2 += (int64_t)blockIdx.z * total;
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+  const int hz = lc - 1;   // log2 of the pairs per coarse row
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < (total >> 1);
        t += (int64_t)gridDim.x * blockDim.x) {
-    const int K = (int)(t & mc), J = (int)((t >> lc) & mc), I = (int)(t >> (2 * lc));
-    float c[3][3][3];   // [x][y][z], index 1 = this coarse cell
+    const int K = 2 * (int)(t & ((1 << hz) - 1));
+    const int64_t row = t >> hz;
+    const int J = (int)(row & mc), I = (int)(row >> lc);
+    float c[3][3][4];   // [x][y][z]: x, y = I-1 .. I+1, J-1 .. J+1; z = K-1 .. K+2
 #pragma unroll
     for (int a = 0; a < 3; ++a)
 #pragma unroll
-      for (int b = 0; b < 3; ++b)
-#pragma unroll
-        for (int cc = 0; cc < 3; ++cc) {
-          const int64_t q = idx3((I + a - 1) & mc, (J + b - 1) & mc, (K + cc - 1) & mc, lc);
-          float x = __ldg(uc + q);
-          if (uc2) x -= __ldg(uc2 + q);
-          c[a][b][cc] = x;
-        }
-    // z then y contractions: vy[x][b][cz] for child offsets b (y) and cz (z)
-    float vy[3][2][2];
-#pragma unroll
-    for (int a = 0; a < 3; ++a)
-#pragma unroll
-      for (int b = 0; b < 2; ++b)
-#pragma unroll
-        for (int cz = 0; cz < 2; ++cz) {
-          const int jn = b ? 2 : 0, kn = cz ? 2 : 0;
-          const float vz0 = fmaf(0.25f, c[a][1][kn], fmaf(0.75f, c[a][1][1], 0.0f));
-          const float vz1 = fmaf(0.25f, c[a][jn][kn], fmaf(0.75f, c[a][jn][1], 0.0f));
-          vy[a][b][cz] = fmaf(0.25f, vz1, fmaf(0.75f, vz0, 0.0f));
+      for (int b = 0; b < 3; ++b) {
+        const int64_t base = idx3((I + a - 1) & mc, (J + b - 1) & mc, 0, lc);
+        const float2 mid = __ldg(reinterpret_cast<const float2*>(uc + base + K));
+        float v[4] = {__ldg(uc + base + ((K - 1) & mc)), mid.x, mid.y, __ldg(uc + base + ((K + 2) & mc))};
+        if (uc2) {
+          const float2 m2 = __ldg(reinterpret_cast<const float2*>(uc2 + base + K));
+          v[0] -= __ldg(uc2 + base + ((K - 1) & mc));
+          v[1] -= m2.x;
+          v[2] -= m2.y;
+          v[3] -= __ldg(uc2 + base + ((K + 2) & mc));
         }
 #pragma unroll
-    for (int ax = 0; ax < 2; ++ax) {
-      const int in = ax ? 2 : 0;
+        for (int z = 0; z < 4; ++z) c[a][b][z] = v[z];
+      }
 #pragma unroll
-      for (int b = 0; b < 2; ++b) {
-        const float v0 = fmaf(0.25f, vy[in][b][0], fmaf(0.75f, vy[1][b][0], 0.0f));
-        const float v1 = fmaf(0.25f, vy[in][b][1], fmaf(0.75f, vy[1][b][1], 0.0f));
-        float2* dst = reinterpret_cast<float2*>(u + idx3(2 * I + ax, 2 * J + b, 2 * K, log2n));
-        float2 w = *dst;
-        w.x += v0;
-        w.y += v1;
+    for (int b = 0; b < 2; ++b) {
+      const int jn = b ? 2 : 0;
+      // z then y contractions: vy[x][q] for the fine z offsets q = 0..3 (coarse
+      // cell q / 2 at column q / 2 + 1, child q & 1)
+      float vy[3][4];
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int kc = (q >> 1) + 1, kn = (q & 1) ? kc + 1 : kc - 1;
+          const float vz0 = fmaf(0.25f, c[a][1][kn], fmaf(0.75f, c[a][1][kc], 0.0f));
+          const float vz1 = fmaf(0.25f, c[a][jn][kn], fmaf(0.75f, c[a][jn][kc], 0.0f));
+          vy[a][q] = fmaf(0.25f, vz1, fmaf(0.75f, vz0, 0.0f));
+        }
+#pragma unroll
+      for (int ax = 0; ax < 2; ++ax) {
+        const int in = ax ? 2 : 0;
+        float4* dst = reinterpret_cast<float4*>(u + idx3(2 * I + ax, 2 * J + b, 2 * K, log2n));
+        float4 w = *dst;
+        w.x += fmaf(0.25f, vy[in][0], fmaf(0.75f, vy[1][0], 0.0f));
+        w.y += fmaf(0.25f, vy[in][1], fmaf(0.75f, vy[1][1], 0.0f));
+        w.z += fmaf(0.25f, vy[in][2], fmaf(0.75f, vy[1][2], 0.0f));
+        w.w += fmaf(0.25f, vy[in][3], fmaf(0.75f, vy[1][3], 0.0f));
         *dst = w;
       }
     }
@@ -481,7 +522,7 @@ pm_status v_cycle(MG& g, int l, bool zero_guess) {
     PM_LAUNCH(K_MG_RESTRICT, 68.0 * nc * g.B, k_resid_restrict<false>, g.grid(grid), 256, 0, g.s, g.u[l], g.f[l],
               log2n, (float)n * (float)n, const_cast<float*>(g.f[l + 1].p));
   PM_TRY(v_cycle(g, l + 1, true));
-  PM_LAUNCH(K_MG_PROLONG, 68.0 * nc * g.B, k_prolong_correct, g.grid(grid_for(nc, 256)), 256, 0, g.s, g.u[l],
+  PM_LAUNCH(K_MG_PROLONG, 68.0 * nc * g.B, k_prolong_correct, g.grid(grid_for(nc / 2, 256)), 256, 0, g.s, g.u[l],
             g.u[l + 1], (const float*)nullptr, log2n);
   if (p.npost > 0) {
     for (int si = 0; si < p.npost; ++si) w[si] = si == p.npost - 1 ? 1.0f : p.omega;
@@ -495,7 +536,7 @@ pm_status v_cycle(MG& g, int l, bool zero_guess) {
 pm_status prolong_correct_launch(float* u, const float* uc, const float* uc2, int n_fine, int cls,
                                  cudaStream_t s) {
   const int64_t N = (int64_t)n_fine * n_fine * n_fine;
-  PM_LAUNCH(cls, 8.0 * N + (uc2 ? 1.0 : 0.5) * N, k_prolong_correct, grid_for(N / 8, 256), 256, 0, s, u, uc, uc2,
+  PM_LAUNCH(cls, 8.0 * N + (uc2 ? 1.0 : 0.5) * N, k_prolong_correct, grid_for(N / 16, 256), 256, 0, s, u, uc, uc2,
             ilog2(n_fine));
   return PM_OK;
 }

@@ -26,38 +26,56 @@ namespace {
 constexpr int SCAN_T = 1024;
 constexpr int SCAN_CHUNK = 4 * SCAN_T;
 constexpr int KT = 256;             // threads of the key, scatter and order kernels
+constexpr int CI = 4;               // particles per thread of the counting kernel
 constexpr uint32_t SHORT_RUN = 32;  // runs up to this length are ordered by one thread
 constexpr int LT = 512;             // threads of a long-run block
 constexpr int LCH = 4096;           // elements sorted in shared memory at once
 constexpr int LONG_BLOCKS = 2 * 152;
 
-__device__ __forceinline__ uint32_t lanemask_lt() { return (1u << (threadIdx.x & 31)) - 1u; }
 
 // key = (i n + j) n + k of the cell holding each particle; with np_box > 0
 // (a batch of boxes) prefixed by the box, i / np_box.  Counts the particles of
-// each cell into cnt[key] (zeroed) with one atomic per run of equal keys in a
-// warp and stores kr[i] = (key, rank of i among its cell's particles).
+// each cell into cnt[key] (zeroed) and stores kr[i] = (key, rank of i among
+// its cell's particles).  A thread takes CI particles, KT apart (coalesced),
+// with their loads and atomics all in flight together; a run of equal keys
+// in adjacent lanes takes one atomic (its head's) and ranks in lane order.
 template <bool BOX>
 __global__ void __launch_bounds__(KT) k_cell_count(const uint32_t* __restrict__ X, int64_t np, int log2n,
                                                    int64_t np_box, uint2* __restrict__ kr,
                                                    uint32_t* __restrict__ cnt) {
-  const int64_t i = blockIdx.x * (int64_t)KT + threadIdx.x;
-  const bool valid = i < np;
-  uint32_t key = 0xffffffffu;
-  if (valid) {
-    const int sh = 32 - log2n;
-    const uint32_t ix = __ldg(X + i) >> sh;
-    const uint32_t iy = __ldg(X + np + i) >> sh;
-    const uint32_t iz = __ldg(X + 2 * np + i) >> sh;
-    key = (((ix << log2n) | iy) << log2n) | iz;
-    if (BOX) key |= (uint32_t)(i / np_box) << (3 * log2n);
+  const int64_t i0 = blockIdx.x * (int64_t)(KT * CI) + threadIdx.x;
+  const int sh = 32 - log2n;
+  const uint32_t lane = threadIdx.x & 31;
+  const uint32_t upto = (2u << lane) - 1u;       // lanes 0 .. lane
+  uint32_t key[CI], r[CI], start[CI];
+#pragma unroll
+  for (int k = 0; k < CI; ++k) {
+    const int64_t i = i0 + k * KT;
+    key[k] = 0xffffffffu;
+    if (i < np) {
+      const uint32_t ix = __ldg(X + i) >> sh;
+      const uint32_t iy = __ldg(X + np + i) >> sh;
+      const uint32_t iz = __ldg(X + 2 * np + i) >> sh;
+      key[k] = (((ix << log2n) | iy) << log2n) | iz;
+      if (BOX) key[k] |= (uint32_t)(i / np_box) << (3 * log2n);
+    }
   }
-  const uint32_t peers = __match_any_sync(0xffffffffu, key);
-  const int leader = __ffs(peers) - 1;
-  uint32_t r = 0;
-  if (valid && (int)(threadIdx.x & 31) == leader) r = atomicAdd(cnt + key, (uint32_t)__popc(peers));
-  r = __shfl_sync(0xffffffffu, r, leader);
-  if (valid) kr[i] = make_uint2(key, r + __popc(peers & lanemask_lt()));
+#pragma unroll
+  for (int k = 0; k < CI; ++k) {
+    const uint32_t prev = __shfl_up_sync(0xffffffffu, key[k], 1);
+    const uint32_t heads = __ballot_sync(0xffffffffu, lane == 0 || key[k] != prev);
+    start[k] = 31 - __clz(heads & upto);
+    const uint32_t after = heads & ~upto;
+    const uint32_t end = after ? (uint32_t)__ffs(after) - 1 : 32u;
+    r[k] = 0;
+    if (key[k] != 0xffffffffu && start[k] == lane) r[k] = atomicAdd(cnt + key[k], end - lane);
+  }
+#pragma unroll
+  for (int k = 0; k < CI; ++k) {
+    const uint32_t base = __shfl_sync(0xffffffffu, r[k], start[k]);
+    const int64_t i = i0 + k * KT;
+    if (i < np) kr[i] = make_uint2(key[k], base + lane - start[k]);
+  }
 }
 
 // perm[cellstart[key] + rank] = i.
@@ -71,28 +89,34 @@ __global__ void __launch_bounds__(KT) k_cell_scatter(const uint2* __restrict__ k
 }
 
 // Stable order inside each cell: the ranks of cell c, cellstart[c] ..
-// cellstart[c+1]-1, in ascending particle index.  Runs of at most SHORT_RUN
-// are insertion-sorted here; longer ones are listed in runs[1 ..] (runs[0]
-// counts them, zeroed) for k_cell_order_long.
+// cellstart[c+1]-1, in ascending particle index.  A thread takes four
+// consecutive cells (one 16-byte load of their starts).  Runs of at most
+// SHORT_RUN are insertion-sorted here; longer ones are listed in runs[1 ..]
+// (runs[0] counts them, zeroed) for k_cell_order_long.
 __global__ void __launch_bounds__(KT) k_cell_order(const uint32_t* __restrict__ cellstart, int64_t ncells,
                                                    uint32_t* __restrict__ perm, uint32_t* __restrict__ runs) {
-  const int64_t c = blockIdx.x * (int64_t)KT + threadIdx.x;
-  if (c >= ncells) return;
-  const uint32_t a = __ldg(cellstart + c), b = __ldg(cellstart + c + 1);
-  if (b - a < 2) return;
-  if (b - a > SHORT_RUN) {
-    runs[1 + atomicAdd(runs, 1u)] = (uint32_t)c;
-    return;
-  }
-  for (uint32_t p = a + 1; p < b; ++p) {
-    const uint32_t v = perm[p];
-    uint32_t q = p;
-    for (; q > a; --q) {
-      const uint32_t u = perm[q - 1];
-      if (u < v) break;
-      perm[q] = u;
+  const int64_t c0 = (blockIdx.x * (int64_t)KT + threadIdx.x) * 4;
+  if (c0 >= ncells) return;
+  const uint4 s4 = __ldg(reinterpret_cast<const uint4*>(cellstart + c0));
+  const uint32_t st[5] = {s4.x, s4.y, s4.z, s4.w, __ldg(cellstart + c0 + 4)};
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const uint32_t a = st[k], b = st[k + 1];
+    if (b - a < 2) continue;
+    if (b - a > SHORT_RUN) {
+      runs[1 + atomicAdd(runs, 1u)] = (uint32_t)(c0 + k);
+      continue;
     }
-    perm[q] = v;
+    for (uint32_t p = a + 1; p < b; ++p) {
+      const uint32_t v = perm[p];
+      uint32_t q = p;
+      for (; q > a; --q) {
+        const uint32_t u = perm[q - 1];
+        if (u < v) break;
+        perm[q] = u;
+      }
+      if (q != p) perm[q] = v;
+    }
   }
 }
 
@@ -305,15 +329,15 @@ pm_status sort_cells(const uint32_t* X, int64_t np, int n, Workspace& w, cudaStr
   PM_TRY(cuda_status(cudaMemsetAsync(cellstart, 0, (size_t)(ncells + 1) * 4, s)));
   if (np == 0) return PM_OK;
   const int64_t np_box = bt.B > 1 ? bt.np_box : 0;
-  const unsigned gp = grid_for(np, KT);
+  const unsigned gp = grid_for(np, KT), gc = grid_for(np, KT * CI);
   if (np_box > 0)
-    PM_LAUNCH(K_KEYS, 28.0 * np, k_cell_count<true>, gp, KT, 0, s, X, np, log2n, np_box, w.keyrank, cellstart);
+    PM_LAUNCH(K_KEYS, 28.0 * np, k_cell_count<true>, gc, KT, 0, s, X, np, log2n, np_box, w.keyrank, cellstart);
   else
-    PM_LAUNCH(K_KEYS, 28.0 * np, k_cell_count<false>, gp, KT, 0, s, X, np, log2n, np_box, w.keyrank, cellstart);
+    PM_LAUNCH(K_KEYS, 28.0 * np, k_cell_count<false>, gc, KT, 0, s, X, np, log2n, np_box, w.keyrank, cellstart);
   PM_TRY(scan_u32(cellstart, ncells + 1, w.scan_blocks, s));
   PM_LAUNCH(K_SCATTER, 16.0 * np, k_cell_scatter, gp, KT, 0, s, w.keyrank, np, cellstart, w.perm);
   PM_TRY(cuda_status(cudaMemsetAsync(w.runs, 0, 4, s)));
-  PM_LAUNCH(K_ORDER, 4.0 * ncells + 8.0 * np, k_cell_order, grid_for(ncells, KT), KT, 0, s, cellstart, ncells,
+  PM_LAUNCH(K_ORDER, 4.0 * ncells + 8.0 * np, k_cell_order, grid_for(ncells / 4, KT), KT, 0, s, cellstart, ncells,
             w.perm, w.runs);
   PM_LAUNCH(K_ORDER, 0.0, k_cell_order_long, LONG_BLOCKS, LT, 0, s, cellstart, w.runs, w.perm,
             reinterpret_cast<uint32_t*>(w.keyrank));
