@@ -403,7 +403,8 @@ pm_status pm_step(pm_state* st_, const pm_step_params* prm, pm_stats* stats, voi
                          vec4, s, 1, frp.nhs == 2 ? 2 : 1));
   double* max_out = prm->report_max ? w.scalars + 24 : nullptr;   // largest |a|, |v| for the time step
   PM_TRY(interp_launch(w.g, w.Xs, w.Vs, w.ids, np, n, S.acc, S.X, S.V, S.id, (float)prm->dt_kick,
-                       (float)prm->dt_drift, 1, vec4, s, Batch{}, reinterpret_cast<float2*>(w.partials), max_out));
+                       (float)prm->dt_drift, 1, vec4, s, Batch{}, reinterpret_cast<float2*>(w.partials), max_out,
+                       w.cellstart));
   if (max_out) {
     double h[2] = {0.0, 0.0};
     if (np > 0) PM_TRY(fetch_scalars(max_out, h, 2, s));
@@ -564,7 +565,8 @@ pm_status pm_step_batch(pm_batch_state* st_, const pm_batch_params* prm, void* s
   if (!S.have_prev) mp.fixed_cycles = prm->cold_cycles;
   PM_TRY(mg_solve_batch(Src{w.rho, 0.0f, w.box_mean, prm->src_scale}, S.phi, n, B, mp, prm->phi_rescale, w, s));
   PM_TRY(gradient_launch(S.phi, nullptr, 0.0f, w.g, n, prm->grad_order, false, s, B));
-  PM_TRY(interp_launch(w.g, w.Xs, w.Vs, nullptr, np, n, nullptr, S.X, S.V, nullptr, 0.0f, 0.0f, 1, false, s, bt));
+  PM_TRY(interp_launch(w.g, w.Xs, w.Vs, nullptr, np, n, nullptr, S.X, S.V, nullptr, 0.0f, 0.0f, 1, false, s, bt,
+                       nullptr, nullptr, w.cellstart));
   S.have_prev = 1;
   return launch_status();
 }

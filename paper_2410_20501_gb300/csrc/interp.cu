@@ -230,6 +230,169 @@ __global__ void __launch_bounds__(256) k_interp_kdk(const float* __restrict__ g,
   }
 }
 
+// Streaming inverse TSC + kick-drift-kick for cell-sorted particles (n >= 32):
+// a CTA owns a IT_Y x IT_Z column of cells and a chunk of x planes and walks
+// the planes in order.  The three force planes around plane x (with a
+// one-cell halo in y and z) sit in a ring of shared-memory slots filled by
+// asynchronous 4-byte copies two planes ahead; the particles of the column's
+// cells on plane x are IT_Y contiguous runs of the sorted arrays (one per
+// row), which the threads take in flat order.  Every particle then reads its
+// 27 x 3 force values from shared memory at fixed offsets from its cell, in
+// the same order and with the same operations as k_interp_kdk (bitwise the
+// same result).
+constexpr int IT_Y = 16, IT_Z = 32, IE_Y = IT_Y + 2, IE_Z = IT_Z + 2, I_PL = IE_Y * IE_Z, I_SLOTS = 5,
+              I_THREADS = 256;
+constexpr size_t kInterpStreamSmem = sizeof(float) * I_SLOTS * 3 * I_PL;
+
+__device__ __forceinline__ void cp_async4(float* dst, const float* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all_but_one() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+
+template <bool MAXES>
+__global__ void __launch_bounds__(I_THREADS) k_interp_stream(
+    const float* __restrict__ g, const uint32_t* __restrict__ cellstart, const uint32_t* __restrict__ Xs,
+    const float* __restrict__ Vs, const uint32_t* __restrict__ ids_in, int64_t np, int log2n, int chunk, int nitems,
+    float* __restrict__ acc, uint32_t* __restrict__ Xo, float* __restrict__ Vo, uint32_t* __restrict__ ids_out,
+    float dt_kick, float drift_scale, int mode, const float* __restrict__ dtk_box,
+    const float* __restrict__ dtd_box, float2* __restrict__ blockmax) {
+  extern __shared__ float gsm[];   // [I_SLOTS][3][IE_Y][IE_Z]
+  __shared__ uint32_t s_start[2][IT_Y], s_pre[2][IT_Y + 1];
+  const int n = 1 << log2n, m = n - 1, sh = 32 - log2n;
+  const int64_t N = (int64_t)1 << (3 * log2n);
+  g += (int64_t)blockIdx.z * 3 * N;   // the box of a batched launch
+  cellstart += (int64_t)blockIdx.z * N;
+  if (dtk_box) dt_kick = __ldg(dtk_box + blockIdx.z);
+  if (dtd_box) drift_scale = __ldg(dtd_box + blockIdx.z) * 4294967296.0f;
+  const int tiles_z = n / IT_Z, tiles = (n / IT_Y) * tiles_z;
+  const int tid = threadIdx.x;
+  float amax = 0.0f, vmax = 0.0f;
+  for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
+    const int tile = item % tiles, xc = item / tiles;
+    const int y0 = (tile / tiles_z) * IT_Y, z0 = (tile % tiles_z) * IT_Z;
+    const int x0 = xc * chunk, x1 = x0 + chunk;
+    // plane q (x0 - 1 .. x1) into slot (q - x0 + 1) mod I_SLOTS, one copy group
+    auto load_plane = [&](int q) {
+      if (q <= x1) {
+        float* dst = gsm + ((q - x0 + 1) % I_SLOTS) * 3 * I_PL;
+        const int64_t gp = (int64_t)(q & m) << (2 * log2n);
+        for (int i = tid; i < 3 * I_PL; i += I_THREADS) {
+          const int comp = i / I_PL, rem = i - comp * I_PL, r = rem / IE_Z, c = rem - r * IE_Z;
+          cp_async4(dst + i, g + comp * N + (gp | ((int64_t)((y0 - 1 + r) & m) << log2n) | ((z0 - 1 + c) & m)));
+        }
+      }
+      cp_async_commit();
+    };
+    // runs of plane q (warp 0): start of each row's particles and the flat
+    // prefix of the run lengths, into buffer q & 1
+    auto runs = [&](int q) {
+      if (tid < 32) {
+        const int j = tid & (IT_Y - 1);
+        const int64_t row = ((int64_t)(q & m) << (2 * log2n)) | ((int64_t)(y0 + j) << log2n);
+        const uint32_t v = __ldg(cellstart + row + z0 + (tid < IT_Y ? 0 : IT_Z));
+        const uint32_t end = __shfl_down_sync(0xffffffffu, v, IT_Y);
+        uint32_t cnt = tid < IT_Y ? end - v : 0u, incl = cnt;
+#pragma unroll
+        for (int o = 1; o < IT_Y; o <<= 1) {
+          const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+          if (j >= o) incl += y;
+        }
+        if (tid < IT_Y) {
+          s_start[q & 1][j] = v;
+          s_pre[q & 1][j + 1] = incl;
+          if (j == 0) s_pre[q & 1][0] = 0;
+        }
+      }
+    };
+    load_plane(x0 - 1);
+    load_plane(x0);
+    load_plane(x0 + 1);
+    runs(x0);
+    for (int t = x0; t < x1; ++t) {
+      load_plane(t + 2);
+      cp_async_wait_all_but_one();   // planes up to t + 1 have landed (this thread's copies)
+      __syncthreads();
+      if (t + 1 < x1) runs(t + 1);
+      const uint32_t* st = s_start[t & 1];
+      const uint32_t* pre = s_pre[t & 1];
+      const uint32_t total = pre[IT_Y];
+      const float* S[3];
+#pragma unroll
+      for (int ox = 0; ox < 3; ++ox) S[ox] = gsm + ((t + ox - x0) % I_SLOTS) * 3 * I_PL;
+      for (uint32_t i = tid; i < total; i += I_THREADS) {
+        int j = 0;   // the run holding flat index i
+#pragma unroll
+        for (int b = IT_Y / 2; b > 0; b >>= 1)
+          if (pre[j + b] <= i) j += b;
+        const int64_t p = (int64_t)st[j] + (i - pre[j]);
+        const uint32_t x = __ldg(Xs + p), y = __ldg(Xs + np + p), z = __ldg(Xs + 2 * np + p);
+        float wx[3], wy[3], wz[3];
+        tsc_weights(cell_offset(x, log2n), wx);
+        tsc_weights(cell_offset(y, log2n), wy);
+        tsc_weights(cell_offset(z, log2n), wz);
+        const int c = ((int)(y >> sh) - y0 + 1) * IE_Z + ((int)(z >> sh) - z0 + 1);
+        float ax = 0.0f, ay = 0.0f, az = 0.0f;
+#pragma unroll
+        for (int ox = 0; ox < 3; ++ox) {
+#pragma unroll
+          for (int oy = 0; oy < 3; ++oy) {
+            const float wxy = wx[ox] * wy[oy];
+            const float* r = S[ox] + c + (oy - 1) * IE_Z;
+#pragma unroll
+            for (int oz = 0; oz < 3; ++oz) {
+              const float w = wxy * wz[oz];
+              ax = fmaf(w, r[oz - 1], ax);
+              ay = fmaf(w, r[I_PL + oz - 1], ay);
+              az = fmaf(w, r[2 * I_PL + oz - 1], az);
+            }
+          }
+        }
+        if (acc) {
+          acc[p] = ax;
+          acc[np + p] = ay;
+          acc[2 * np + p] = az;
+        }
+        if (MAXES) amax = fmaxf(amax, sqrtf(fmaf(ax, ax, fmaf(ay, ay, az * az))));
+        if (mode == 1) {
+          const float vx = fmaf(ax, dt_kick, __ldg(Vs + p));
+          const float vy = fmaf(ay, dt_kick, __ldg(Vs + np + p));
+          const float vz = fmaf(az, dt_kick, __ldg(Vs + 2 * np + p));
+          Vo[p] = vx;
+          Vo[np + p] = vy;
+          Vo[2 * np + p] = vz;
+          if (MAXES) vmax = fmaxf(vmax, sqrtf(fmaf(vx, vx, fmaf(vy, vy, vz * vz))));
+          Xo[p] = x + (uint32_t)__float2int_rn(vx * drift_scale);
+          Xo[np + p] = y + (uint32_t)__float2int_rn(vy * drift_scale);
+          Xo[2 * np + p] = z + (uint32_t)__float2int_rn(vz * drift_scale);
+          if (ids_out) ids_out[p] = __ldg(ids_in + p);
+        }
+      }
+    }
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    __syncthreads();   // the slots and run buffers are reused by the next item
+  }
+  if (MAXES) {   // block maxima (non-negative floats order like their bit patterns)
+    __shared__ unsigned wa[I_THREADS / 32], wv[I_THREADS / 32];
+    const unsigned ua = __reduce_max_sync(0xffffffffu, __float_as_uint(amax));
+    const unsigned uv = __reduce_max_sync(0xffffffffu, __float_as_uint(vmax));
+    if ((tid & 31) == 0) {
+      wa[tid >> 5] = ua;
+      wv[tid >> 5] = uv;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      unsigned ma = 0, mv = 0;
+      for (int w = 0; w < I_THREADS / 32; ++w) {
+        ma = max(ma, wa[w]);
+        mv = max(mv, wv[w]);
+      }
+      blockmax[(int64_t)blockIdx.z * gridDim.x + blockIdx.x] = make_float2(__uint_as_float(ma), __uint_as_float(mv));
+    }
+  }
+}
+
 // Maximum over count float2 pairs, per component, into out[0], out[1]
 // (float64); one block.
 __global__ void __launch_bounds__(1024) k_max_pairs(const float2* __restrict__ v, int64_t count,
@@ -308,27 +471,49 @@ pm_status gradient_launch(const float* phi, const float* eps, float alpha, float
 pm_status interp_launch(const float* g, const uint32_t* Xs, const float* Vs, const uint32_t* ids_in, int64_t np,
                         int n, float* acc, uint32_t* Xo, float* Vo, uint32_t* ids_out, float dt_kick,
                         float dt_drift, int mode, bool vec4, cudaStream_t s, const Batch& bt,
-                        float2* blockmax, double* max_out) {
+                        float2* blockmax, double* max_out, const uint32_t* cellstart) {
   if (np == 0) return PM_OK;
   const float drift_scale = (float)((double)dt_drift * 4294967296.0);
   const double bytes = (vec4 ? 16.0 : 12.0) * n * n * (double)n * bt.B +
                        np * (12.0 + (mode ? 36.0 : 0.0) + (acc ? 12.0 : 0.0) + (ids_out ? 8.0 : 0.0));
   const int64_t np_box = bt.B > 1 ? bt.np_box : np;
-  const dim3 grid(grid_for(np_box, 256), 1, (unsigned)bt.B);
   if (!max_out) blockmax = nullptr;
+  int64_t nblocks;
+  if (cellstart && !vec4 && n >= 32) {
+    static bool attr = false;
+    if (!attr) {
+      PM_TRY(cuda_status(cudaFuncSetAttribute(k_interp_stream<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)kInterpStreamSmem)));
+      PM_TRY(cuda_status(cudaFuncSetAttribute(k_interp_stream<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)kInterpStreamSmem)));
+      attr = true;
+    }
+    const int tiles = (n / IT_Y) * (n / IT_Z);
+    int chunk = n;
+    while (chunk > 8 && (int64_t)tiles * (n / chunk) * bt.B < 16 * 152) chunk >>= 1;
+    const int nitems = tiles * (n / chunk);
+    const dim3 grid((unsigned)nitems, 1, (unsigned)bt.B);
+    nblocks = (int64_t)grid.x * grid.z;
+#define PM_INTERP_S(MX)                                                                                       \
+  PM_LAUNCH(K_INTERP, bytes, (k_interp_stream<MX>), grid, I_THREADS, kInterpStreamSmem, s, g, cellstart, Xs, Vs,  \
+            ids_in, np, ilog2(n), chunk, nitems, acc, Xo, Vo, ids_out, dt_kick, drift_scale, mode, bt.dt_kick,     \
+            bt.dt_drift, blockmax)
+    if (blockmax) PM_INTERP_S(true); else PM_INTERP_S(false);
+#undef PM_INTERP_S
+  } else {
+    const dim3 grid(grid_for(np_box, 256), 1, (unsigned)bt.B);
+    nblocks = (int64_t)grid.x * grid.z;
 #define PM_INTERP(V4, MX)                                                                                       \
   PM_LAUNCH(K_INTERP, bytes, (k_interp_kdk<V4, MX>), grid, 256, 0, s, g, Xs, Vs, ids_in, np, ilog2(n), acc, Xo, Vo, \
             ids_out, dt_kick, drift_scale, mode, np_box, bt.dt_kick, bt.dt_drift, blockmax)
-  if (vec4) {
-    if (blockmax) PM_INTERP(true, true); else PM_INTERP(true, false);
-  } else {
-    if (blockmax) PM_INTERP(false, true); else PM_INTERP(false, false);
-  }
+    if (vec4) {
+      if (blockmax) PM_INTERP(true, true); else PM_INTERP(true, false);
+    } else {
+      if (blockmax) PM_INTERP(false, true); else PM_INTERP(false, false);
+    }
 #undef PM_INTERP
-  if (blockmax) {
-    const int64_t nb = (int64_t)grid.x * grid.z;
-    PM_LAUNCH(K_REDUCE, 8.0 * nb, k_max_pairs, 1, 1024, 0, s, blockmax, nb, max_out);
   }
+  if (blockmax) PM_LAUNCH(K_REDUCE, 8.0 * nblocks, k_max_pairs, 1, 1024, 0, s, blockmax, nblocks, max_out);
   return launch_status();
 }
 
