@@ -396,15 +396,19 @@ pm_status pm_step(pm_state* st_, const pm_step_params* prm, pm_stats* stats, voi
     if (r != PM_OK) solve_status = r;
   }
   const float alpha = (float)(-0.5 * c2 * fbar);
-  // three planes: the interpolation is bound by L1 wavefronts, and 16-byte
-  // gathers of an interleaved float4 layout measured slower than three 4-byte ones
-  const bool vec4 = false;
-  PM_TRY(gradient_launch(S.phi, prm->gravity == PM_GRAVITY_FR ? S.eps : nullptr, alpha, w.g, n, prm->grad_order,
-                         vec4, s, 1, frp.nhs == 2 ? 2 : 1));
+  const float* eps_force = prm->gravity == PM_GRAVITY_FR ? S.eps : nullptr;
+  const int nh = frp.nhs == 2 ? 2 : 1;
   double* max_out = prm->report_max ? w.scalars + 24 : nullptr;   // largest |a|, |v| for the time step
-  PM_TRY(interp_launch(w.g, w.Xs, w.Vs, w.ids, np, n, S.acc, S.X, S.V, S.id, (float)prm->dt_kick,
-                       (float)prm->dt_drift, 1, vec4, s, Batch{}, reinterpret_cast<float2*>(w.partials), max_out,
-                       w.cellstart));
+  float2* blockmax = reinterpret_cast<float2*>(w.partials);
+  if (n >= 32) {   // force computed in shared memory next to the particles
+    PM_TRY(force_interp_launch(S.phi, eps_force, alpha, nh, prm->grad_order, w.cellstart, w.Xs, w.Vs, w.ids, np, n,
+                               S.acc, S.X, S.V, S.id, (float)prm->dt_kick, (float)prm->dt_drift, 1, s, Batch{},
+                               blockmax, max_out));
+  } else {
+    PM_TRY(gradient_launch(S.phi, eps_force, alpha, w.g, n, prm->grad_order, false, s, 1, nh));
+    PM_TRY(interp_launch(w.g, w.Xs, w.Vs, w.ids, np, n, S.acc, S.X, S.V, S.id, (float)prm->dt_kick,
+                         (float)prm->dt_drift, 1, false, s, Batch{}, blockmax, max_out));
+  }
   if (max_out) {
     double h[2] = {0.0, 0.0};
     if (np > 0) PM_TRY(fetch_scalars(max_out, h, 2, s));
@@ -564,9 +568,8 @@ pm_status pm_step_batch(pm_batch_state* st_, const pm_batch_params* prm, void* s
   mp.first_guess = S.have_prev ? MG_GUESS_SCALED : MG_GUESS_JACOBI;
   if (!S.have_prev) mp.fixed_cycles = prm->cold_cycles;
   PM_TRY(mg_solve_batch(Src{w.rho, 0.0f, w.box_mean, prm->src_scale}, S.phi, n, B, mp, prm->phi_rescale, w, s));
-  PM_TRY(gradient_launch(S.phi, nullptr, 0.0f, w.g, n, prm->grad_order, false, s, B));
-  PM_TRY(interp_launch(w.g, w.Xs, w.Vs, nullptr, np, n, nullptr, S.X, S.V, nullptr, 0.0f, 0.0f, 1, false, s, bt,
-                       nullptr, nullptr, w.cellstart));
+  PM_TRY(force_interp_launch(S.phi, nullptr, 0.0f, 1, prm->grad_order, w.cellstart, w.Xs, w.Vs, nullptr, np, n,
+                             nullptr, S.X, S.V, nullptr, 0.0f, 0.0f, 1, s, bt));
   S.have_prev = 1;
   return launch_status();
 }

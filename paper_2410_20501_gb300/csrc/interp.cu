@@ -230,39 +230,148 @@ __global__ void __launch_bounds__(256) k_interp_kdk(const float* __restrict__ g,
   }
 }
 
-// Streaming inverse TSC + kick-drift-kick for cell-sorted particles (n >= 32):
-// a CTA owns a IT_Y x IT_Z column of cells and a chunk of x planes and walks
-// the planes in order.  The three force planes around plane x (with a
-// one-cell halo in y and z) sit in a ring of shared-memory slots filled by
-// asynchronous 4-byte copies two planes ahead; the particles of the column's
-// cells on plane x are IT_Y contiguous runs of the sorted arrays (one per
-// row), which the threads take in flat order.  Every particle then reads its
-// 27 x 3 force values from shared memory at fixed offsets from its cell, in
-// the same order and with the same operations as k_interp_kdk (bitwise the
-// same result).
-constexpr int IT_Y = 16, IT_Z = 32, IE_Y = IT_Y + 2, IE_Z = IT_Z + 2, I_PL = IE_Y * IE_Z, I_SLOTS = 5,
-              I_THREADS = 256;
-constexpr size_t kInterpStreamSmem = sizeof(float) * I_SLOTS * 3 * I_PL;
-
-__device__ __forceinline__ void cp_async4(float* dst, const float* src) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
-               : "memory");
+// Force and inverse TSC + kick-drift-kick in one pass for cell-sorted
+// particles (n >= 32): a CTA owns a IT_Y x IT_Z column of cells and a chunk
+// of x planes and walks the planes in order.  The force planes around plane
+// x (with a one-cell halo in y and z) are computed in shared memory from the
+// potential (the gradient of k_gradient, same arithmetic), so the force field
+// never goes through HBM; the particles of the column's cells on plane x are
+// IT_Y contiguous runs of the sorted arrays (one per row), which the threads
+// take in flat order.  Every particle then reads its 27 x 3 force values
+// from shared memory at fixed offsets from its cell, in the same order and
+// with the same operations as k_interp_kdk (bitwise the same result).
+constexpr int IT_Y = 16, IT_Z = 32, IE_Y = IT_Y + 2, IE_Z = IT_Z + 2, I_PL = IE_Y * IE_Z, I_THREADS = 256;
+// Warp 0: the runs of the column's rows on plane q (start of each row's
+// particles, flat prefix of the run lengths).
+__device__ __forceinline__ void column_runs(const uint32_t* __restrict__ cellstart, int q, int y0, int z0,
+                                            int log2n, uint32_t* start, uint32_t* pre) {
+  const int tid = threadIdx.x;
+  if (tid >= 32) return;
+  const int m = (1 << log2n) - 1, j = tid & (IT_Y - 1);
+  const int64_t row = ((int64_t)(q & m) << (2 * log2n)) | ((int64_t)(y0 + j) << log2n);
+  const uint32_t v = __ldg(cellstart + row + z0 + (tid < IT_Y ? 0 : IT_Z));
+  const uint32_t end = __shfl_down_sync(0xffffffffu, v, IT_Y);
+  uint32_t incl = tid < IT_Y ? end - v : 0u;
+#pragma unroll
+  for (int o = 1; o < IT_Y; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (j >= o) incl += y;
+  }
+  if (tid < IT_Y) {
+    start[j] = v;
+    pre[j + 1] = incl;
+    if (j == 0) pre[0] = 0;
+  }
 }
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all_but_one() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 
+// Inverse TSC (+ kick and drift) of the particles of one plane of a column,
+// force planes x-1, x, x+1 at S[0..2] (each [3][IE_Y][IE_Z]).
 template <bool MAXES>
-__global__ void __launch_bounds__(I_THREADS) k_interp_stream(
-    const float* __restrict__ g, const uint32_t* __restrict__ cellstart, const uint32_t* __restrict__ Xs,
-    const float* __restrict__ Vs, const uint32_t* __restrict__ ids_in, int64_t np, int log2n, int chunk, int nitems,
-    float* __restrict__ acc, uint32_t* __restrict__ Xo, float* __restrict__ Vo, uint32_t* __restrict__ ids_out,
-    float dt_kick, float drift_scale, int mode, const float* __restrict__ dtk_box,
-    const float* __restrict__ dtd_box, float2* __restrict__ blockmax) {
-  extern __shared__ float gsm[];   // [I_SLOTS][3][IE_Y][IE_Z]
-  __shared__ uint32_t s_start[2][IT_Y], s_pre[2][IT_Y + 1];
-  const int n = 1 << log2n, m = n - 1, sh = 32 - log2n;
+__device__ __forceinline__ void column_particles(const float* const S[3], const uint32_t* st, const uint32_t* pre,
+                                                 int y0, int z0, const uint32_t* __restrict__ Xs,
+                                                 const float* __restrict__ Vs, const uint32_t* __restrict__ ids_in,
+                                                 int64_t np, int log2n, float* __restrict__ acc,
+                                                 uint32_t* __restrict__ Xo, float* __restrict__ Vo,
+                                                 uint32_t* __restrict__ ids_out, float dt_kick, float drift_scale,
+                                                 int mode, float& amax, float& vmax) {
+  const int sh = 32 - log2n;
+  const uint32_t total = pre[IT_Y];
+  for (uint32_t i = threadIdx.x; i < total; i += I_THREADS) {
+    int j = 0;   // the run holding flat index i
+#pragma unroll
+    for (int b = IT_Y / 2; b > 0; b >>= 1)
+      if (pre[j + b] <= i) j += b;
+    const int64_t p = (int64_t)st[j] + (i - pre[j]);
+    const uint32_t x = __ldg(Xs + p), y = __ldg(Xs + np + p), z = __ldg(Xs + 2 * np + p);
+    float wx[3], wy[3], wz[3];
+    tsc_weights(cell_offset(x, log2n), wx);
+    tsc_weights(cell_offset(y, log2n), wy);
+    tsc_weights(cell_offset(z, log2n), wz);
+    const int c = ((int)(y >> sh) - y0 + 1) * IE_Z + ((int)(z >> sh) - z0 + 1);
+    float ax = 0.0f, ay = 0.0f, az = 0.0f;
+#pragma unroll
+    for (int ox = 0; ox < 3; ++ox) {
+#pragma unroll
+      for (int oy = 0; oy < 3; ++oy) {
+        const float wxy = wx[ox] * wy[oy];
+        const float* r = S[ox] + c + (oy - 1) * IE_Z;
+#pragma unroll
+        for (int oz = 0; oz < 3; ++oz) {
+          const float w = wxy * wz[oz];
+          ax = fmaf(w, r[oz - 1], ax);
+          ay = fmaf(w, r[I_PL + oz - 1], ay);
+          az = fmaf(w, r[2 * I_PL + oz - 1], az);
+        }
+      }
+    }
+    if (acc) {
+      acc[p] = ax;
+      acc[np + p] = ay;
+      acc[2 * np + p] = az;
+    }
+    if (MAXES) amax = fmaxf(amax, sqrtf(fmaf(ax, ax, fmaf(ay, ay, az * az))));
+    if (mode == 1) {
+      const float vx = fmaf(ax, dt_kick, __ldg(Vs + p));
+      const float vy = fmaf(ay, dt_kick, __ldg(Vs + np + p));
+      const float vz = fmaf(az, dt_kick, __ldg(Vs + 2 * np + p));
+      Vo[p] = vx;
+      Vo[np + p] = vy;
+      Vo[2 * np + p] = vz;
+      if (MAXES) vmax = fmaxf(vmax, sqrtf(fmaf(vx, vx, fmaf(vy, vy, vz * vz))));
+      Xo[p] = x + (uint32_t)__float2int_rn(vx * drift_scale);
+      Xo[np + p] = y + (uint32_t)__float2int_rn(vy * drift_scale);
+      Xo[2 * np + p] = z + (uint32_t)__float2int_rn(vz * drift_scale);
+      if (ids_out) ids_out[p] = __ldg(ids_in + p);
+    }
+  }
+}
+
+// Block maxima of |a| and |v| (non-negative floats order like their bit
+// patterns), one float2 per block.
+__device__ __forceinline__ void block_maxima(float amax, float vmax, float2* __restrict__ blockmax) {
+  __shared__ unsigned wa[I_THREADS / 32], wv[I_THREADS / 32];
+  const int tid = threadIdx.x;
+  const unsigned ua = __reduce_max_sync(0xffffffffu, __float_as_uint(amax));
+  const unsigned uv = __reduce_max_sync(0xffffffffu, __float_as_uint(vmax));
+  if ((tid & 31) == 0) {
+    wa[tid >> 5] = ua;
+    wv[tid >> 5] = uv;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    unsigned ma = 0, mv = 0;
+    for (int w = 0; w < I_THREADS / 32; ++w) {
+      ma = max(ma, wa[w]);
+      mv = max(mv, wv[w]);
+    }
+    blockmax[(int64_t)blockIdx.z * gridDim.x + blockIdx.x] = make_float2(__uint_as_float(ma), __uint_as_float(mv));
+  }
+}
+
+// The force planes from the potential in shared memory, then the particles.
+// Per plane step u: the potential plane u (with a halo of R + 1 in y and z;
+// loaded into registers one step ahead, combined with eps for f(R)) goes to a
+// ring of 2R + 1 slots; after a barrier the force plane u - R (with a
+// one-cell halo) is computed into a ring of 4 slots; after a second barrier
+// the particles of plane u - R - 1 are interpolated.
+template <int ORDER, bool FR, bool MAXES>
+__global__ void __launch_bounds__(I_THREADS) k_force_interp_stream(
+    const float* __restrict__ phi, const float* __restrict__ eps, float alpha, int nh, float inv_h,
+    const uint32_t* __restrict__ cellstart, const uint32_t* __restrict__ Xs, const float* __restrict__ Vs,
+    const uint32_t* __restrict__ ids_in, int64_t np, int log2n, int chunk, int nitems, float* __restrict__ acc,
+    uint32_t* __restrict__ Xo, float* __restrict__ Vo, uint32_t* __restrict__ ids_out, float dt_kick,
+    float drift_scale, int mode, const float* __restrict__ dtk_box, const float* __restrict__ dtd_box,
+    float2* __restrict__ blockmax) {
+  constexpr int R = Stencil<ORDER>::R, H = R + 1, PEY = IT_Y + 2 * H, PEZ = IT_Z + 2 * H, PPL = PEY * PEZ,
+                PS = 2 * R + 1, PL_T = (PPL + I_THREADS - 1) / I_THREADS;
+  extern __shared__ float fsm[];
+  float* Gs = fsm;                   // [4][3][IE_Y][IE_Z]
+  float* Ps = Gs + 4 * 3 * I_PL;     // [PS][PEY][PEZ]
+  __shared__ uint32_t s_start[IT_Y], s_pre[IT_Y + 1];
+  const int n = 1 << log2n, m = n - 1;
   const int64_t N = (int64_t)1 << (3 * log2n);
-  g += (int64_t)blockIdx.z * 3 * N;   // the box of a batched launch
+  phi += (int64_t)blockIdx.z * N;   // the box of a batched launch
+  if (FR) eps += (int64_t)blockIdx.z * N;
   cellstart += (int64_t)blockIdx.z * N;
   if (dtk_box) dt_kick = __ldg(dtk_box + blockIdx.z);
   if (dtd_box) drift_scale = __ldg(dtd_box + blockIdx.z) * 4294967296.0f;
@@ -273,124 +382,84 @@ __global__ void __launch_bounds__(I_THREADS) k_interp_stream(
     const int tile = item % tiles, xc = item / tiles;
     const int y0 = (tile / tiles_z) * IT_Y, z0 = (tile % tiles_z) * IT_Z;
     const int x0 = xc * chunk, x1 = x0 + chunk;
-    // plane q (x0 - 1 .. x1) into slot (q - x0 + 1) mod I_SLOTS, one copy group
-    auto load_plane = [&](int q) {
-      if (q <= x1) {
-        float* dst = gsm + ((q - x0 + 1) % I_SLOTS) * 3 * I_PL;
-        const int64_t gp = (int64_t)(q & m) << (2 * log2n);
-        for (int i = tid; i < 3 * I_PL; i += I_THREADS) {
-          const int comp = i / I_PL, rem = i - comp * I_PL, r = rem / IE_Z, c = rem - r * IE_Z;
-          cp_async4(dst + i, g + comp * N + (gp | ((int64_t)((y0 - 1 + r) & m) << log2n) | ((z0 - 1 + c) & m)));
-        }
-      }
-      cp_async_commit();
-    };
-    // runs of plane q (warp 0): start of each row's particles and the flat
-    // prefix of the run lengths, into buffer q & 1
-    auto runs = [&](int q) {
-      if (tid < 32) {
-        const int j = tid & (IT_Y - 1);
-        const int64_t row = ((int64_t)(q & m) << (2 * log2n)) | ((int64_t)(y0 + j) << log2n);
-        const uint32_t v = __ldg(cellstart + row + z0 + (tid < IT_Y ? 0 : IT_Z));
-        const uint32_t end = __shfl_down_sync(0xffffffffu, v, IT_Y);
-        uint32_t cnt = tid < IT_Y ? end - v : 0u, incl = cnt;
+    // raw potential (and eps) of plane q at this thread's positions
+    float rp[PL_T], re[PL_T];
+    auto fetch = [&](int q) {
+      const int64_t pb = (int64_t)(q & m) << (2 * log2n);
 #pragma unroll
-        for (int o = 1; o < IT_Y; o <<= 1) {
-          const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
-          if (j >= o) incl += y;
-        }
-        if (tid < IT_Y) {
-          s_start[q & 1][j] = v;
-          s_pre[q & 1][j + 1] = incl;
-          if (j == 0) s_pre[q & 1][0] = 0;
+      for (int k = 0; k < PL_T; ++k) {
+        const int e = tid + k * I_THREADS;
+        if (e < PPL) {
+          const int ly = e / PEZ, lz = e - ly * PEZ;
+          const int64_t c = pb | ((int64_t)((y0 - H + ly) & m) << log2n) | ((z0 - H + lz) & m);
+          rp[k] = __ldg(phi + c);
+          if (FR) re[k] = __ldg(eps + c);
         }
       }
     };
-    load_plane(x0 - 1);
-    load_plane(x0);
-    load_plane(x0 + 1);
-    runs(x0);
-    for (int t = x0; t < x1; ++t) {
-      load_plane(t + 2);
-      cp_async_wait_all_but_one();   // planes up to t + 1 have landed (this thread's copies)
-      __syncthreads();
-      if (t + 1 < x1) runs(t + 1);
-      const uint32_t* st = s_start[t & 1];
-      const uint32_t* pre = s_pre[t & 1];
-      const uint32_t total = pre[IT_Y];
-      const float* S[3];
+    auto store = [&](int q) {
+      float* P = Ps + (((q % PS) + PS) % PS) * PPL;
 #pragma unroll
-      for (int ox = 0; ox < 3; ++ox) S[ox] = gsm + ((t + ox - x0) % I_SLOTS) * 3 * I_PL;
-      for (uint32_t i = tid; i < total; i += I_THREADS) {
-        int j = 0;   // the run holding flat index i
-#pragma unroll
-        for (int b = IT_Y / 2; b > 0; b >>= 1)
-          if (pre[j + b] <= i) j += b;
-        const int64_t p = (int64_t)st[j] + (i - pre[j]);
-        const uint32_t x = __ldg(Xs + p), y = __ldg(Xs + np + p), z = __ldg(Xs + 2 * np + p);
-        float wx[3], wy[3], wz[3];
-        tsc_weights(cell_offset(x, log2n), wx);
-        tsc_weights(cell_offset(y, log2n), wy);
-        tsc_weights(cell_offset(z, log2n), wz);
-        const int c = ((int)(y >> sh) - y0 + 1) * IE_Z + ((int)(z >> sh) - z0 + 1);
-        float ax = 0.0f, ay = 0.0f, az = 0.0f;
-#pragma unroll
-        for (int ox = 0; ox < 3; ++ox) {
-#pragma unroll
-          for (int oy = 0; oy < 3; ++oy) {
-            const float wxy = wx[ox] * wy[oy];
-            const float* r = S[ox] + c + (oy - 1) * IE_Z;
-#pragma unroll
-            for (int oz = 0; oz < 3; ++oz) {
-              const float w = wxy * wz[oz];
-              ax = fmaf(w, r[oz - 1], ax);
-              ay = fmaf(w, r[I_PL + oz - 1], ay);
-              az = fmaf(w, r[2 * I_PL + oz - 1], az);
-            }
+      for (int k = 0; k < PL_T; ++k) {
+        const int e = tid + k * I_THREADS;
+        if (e < PPL) {
+          float v = rp[k];
+          if (FR) {
+            const float ev = re[k];
+            v = fmaf(alpha, nh == 2 ? ev * fmaf(ev, 3.0f + ev, 3.0f) : ev * (2.0f + ev), v);
           }
-        }
-        if (acc) {
-          acc[p] = ax;
-          acc[np + p] = ay;
-          acc[2 * np + p] = az;
-        }
-        if (MAXES) amax = fmaxf(amax, sqrtf(fmaf(ax, ax, fmaf(ay, ay, az * az))));
-        if (mode == 1) {
-          const float vx = fmaf(ax, dt_kick, __ldg(Vs + p));
-          const float vy = fmaf(ay, dt_kick, __ldg(Vs + np + p));
-          const float vz = fmaf(az, dt_kick, __ldg(Vs + 2 * np + p));
-          Vo[p] = vx;
-          Vo[np + p] = vy;
-          Vo[2 * np + p] = vz;
-          if (MAXES) vmax = fmaxf(vmax, sqrtf(fmaf(vx, vx, fmaf(vy, vy, vz * vz))));
-          Xo[p] = x + (uint32_t)__float2int_rn(vx * drift_scale);
-          Xo[np + p] = y + (uint32_t)__float2int_rn(vy * drift_scale);
-          Xo[2 * np + p] = z + (uint32_t)__float2int_rn(vz * drift_scale);
-          if (ids_out) ids_out[p] = __ldg(ids_in + p);
+          P[e] = v;
         }
       }
-    }
-    asm volatile("cp.async.wait_all;" ::: "memory");
-    __syncthreads();   // the slots and run buffers are reused by the next item
-  }
-  if (MAXES) {   // block maxima (non-negative floats order like their bit patterns)
-    __shared__ unsigned wa[I_THREADS / 32], wv[I_THREADS / 32];
-    const unsigned ua = __reduce_max_sync(0xffffffffu, __float_as_uint(amax));
-    const unsigned uv = __reduce_max_sync(0xffffffffu, __float_as_uint(vmax));
-    if ((tid & 31) == 0) {
-      wa[tid >> 5] = ua;
-      wv[tid >> 5] = uv;
-    }
-    __syncthreads();
-    if (tid == 0) {
-      unsigned ma = 0, mv = 0;
-      for (int w = 0; w < I_THREADS / 32; ++w) {
-        ma = max(ma, wa[w]);
-        mv = max(mv, wv[w]);
+    };
+    const int u0 = x0 - 1 - R, u1 = x1 + R;   // potential planes of the chunk
+    fetch(u0);
+    for (int u = u0; u <= u1; ++u) {
+      store(u);
+      if (u < u1) fetch(u + 1);
+      __syncthreads();
+      const int qg = u - R;                    // force plane computed this step
+      if (qg >= x0 - 1) {
+        float* G = Gs + (qg & 3) * 3 * I_PL;
+        const float* Pc = Ps + (((qg % PS) + PS) % PS) * PPL;
+        for (int e = tid; e < I_PL; e += I_THREADS) {
+          const int ly = e / IE_Z, lz = e - ly * IE_Z;
+          const int c = (ly + R) * PEZ + lz + R;   // potential position of force cell (ly - 1, lz - 1)
+          float gx = 0.0f, gy = 0.0f, gz = 0.0f;
+#pragma unroll
+          for (int q = R; q >= 1; --q) {
+            const float w = Stencil<ORDER>::c(q);
+            const float* Pp = Ps + ((((qg + q) % PS) + PS) % PS) * PPL;
+            const float* Pm = Ps + ((((qg - q) % PS) + PS) % PS) * PPL;
+            gx = fmaf(w, Pp[c] - Pm[c], gx);
+            gy = fmaf(w, Pc[c + q * PEZ] - Pc[c - q * PEZ], gy);
+            gz = fmaf(w, Pc[c + q] - Pc[c - q], gz);
+          }
+          G[e] = -gx * inv_h;
+          G[I_PL + e] = -gy * inv_h;
+          G[2 * I_PL + e] = -gz * inv_h;
+        }
       }
-      blockmax[(int64_t)blockIdx.z * gridDim.x + blockIdx.x] = make_float2(__uint_as_float(ma), __uint_as_float(mv));
+      const int t = qg - 1;                    // particle plane of this step
+      if (t >= x0 && t < x1) column_runs(cellstart, t, y0, z0, log2n, s_start, s_pre);
+      __syncthreads();
+      if (t >= x0 && t < x1) {
+        const float* S[3];
+#pragma unroll
+        for (int ox = 0; ox < 3; ++ox) S[ox] = Gs + ((t + ox - 1) & 3) * 3 * I_PL;
+        column_particles<MAXES>(S, s_start, s_pre, y0, z0, Xs, Vs, ids_in, np, log2n, acc, Xo, Vo, ids_out, dt_kick,
+                                drift_scale, mode, amax, vmax);
+      }
     }
+    __syncthreads();   // the rings and run buffers are reused by the next item
   }
+  if (MAXES) block_maxima(amax, vmax, blockmax);
+}
+
+template <int ORDER>
+constexpr size_t force_interp_smem() {
+  return sizeof(float) * (4 * 3 * I_PL + (2 * Stencil<ORDER>::R + 1) * (IT_Y + 2 * Stencil<ORDER>::R + 2) *
+                                             (IT_Z + 2 * Stencil<ORDER>::R + 2));
 }
 
 // Maximum over count float2 pairs, per component, into out[0], out[1]
@@ -468,52 +537,96 @@ pm_status gradient_launch(const float* phi, const float* eps, float alpha, float
   return PM_EINVAL;
 }
 
+template <int ORDER>
+pm_status launch_force_interp(const float* phi, const float* eps, float alpha, int nh, const uint32_t* cellstart,
+                              const uint32_t* Xs, const float* Vs, const uint32_t* ids_in, int64_t np, int n,
+                              float* acc, uint32_t* Xo, float* Vo, uint32_t* ids_out, float dt_kick,
+                              float drift_scale, int mode, cudaStream_t s, const Batch& bt, float2* blockmax,
+                              int64_t* nblocks) {
+  constexpr size_t smem = force_interp_smem<ORDER>();
+  static bool attr = false;
+  if (!attr) {
+    PM_TRY(cuda_status(cudaFuncSetAttribute(k_force_interp_stream<ORDER, false, false>,
+                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)));
+    PM_TRY(cuda_status(cudaFuncSetAttribute(k_force_interp_stream<ORDER, false, true>,
+                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)));
+    PM_TRY(cuda_status(cudaFuncSetAttribute(k_force_interp_stream<ORDER, true, false>,
+                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)));
+    PM_TRY(cuda_status(cudaFuncSetAttribute(k_force_interp_stream<ORDER, true, true>,
+                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)));
+    attr = true;
+  }
+  const int tiles = (n / IT_Y) * (n / IT_Z);
+  int chunk = n;
+  while (chunk > 16 && (int64_t)tiles * (n / chunk) * bt.B < 16 * 152) chunk >>= 1;
+  const int nitems = tiles * (n / chunk);
+  const dim3 grid((unsigned)nitems, 1, (unsigned)bt.B);
+  *nblocks = (int64_t)grid.x * grid.z;
+  const double N = (double)n * n * n * bt.B;
+  const double bytes = (eps ? 8.0 : 4.0) * N + np * (12.0 + (mode ? 36.0 : 0.0) + (acc ? 12.0 : 0.0) +
+                                                      (ids_out ? 8.0 : 0.0));
+#define PM_FI(FRB, MX)                                                                                          \
+  PM_LAUNCH(K_INTERP, bytes, (k_force_interp_stream<ORDER, FRB, MX>), grid, I_THREADS, smem, s, phi, eps, alpha, nh, \
+            (float)n, cellstart, Xs, Vs, ids_in, np, ilog2(n), chunk, nitems, acc, Xo, Vo, ids_out, dt_kick,       \
+            drift_scale, mode, bt.dt_kick, bt.dt_drift, blockmax)
+  if (eps) {
+    if (blockmax) PM_FI(true, true); else PM_FI(true, false);
+  } else {
+    if (blockmax) PM_FI(false, true); else PM_FI(false, false);
+  }
+#undef PM_FI
+  return launch_status();
+}
+
+pm_status force_interp_launch(const float* phi, const float* eps, float alpha, int nh, int order,
+                              const uint32_t* cellstart, const uint32_t* Xs, const float* Vs, const uint32_t* ids_in,
+                              int64_t np, int n, float* acc, uint32_t* Xo, float* Vo, uint32_t* ids_out,
+                              float dt_kick, float dt_drift, int mode, cudaStream_t s, const Batch& bt,
+                              float2* blockmax, double* max_out) {
+  if (np == 0) return PM_OK;
+  if (n < 32 || !cellstart) return PM_EINVAL;
+  const float drift_scale = (float)((double)dt_drift * 4294967296.0);
+  if (!max_out) blockmax = nullptr;
+  int64_t nblocks = 0;
+  pm_status r = PM_EINVAL;
+  if (order == 3)
+    r = launch_force_interp<3>(phi, eps, alpha, nh, cellstart, Xs, Vs, ids_in, np, n, acc, Xo, Vo, ids_out, dt_kick,
+                               drift_scale, mode, s, bt, blockmax, &nblocks);
+  else if (order == 5)
+    r = launch_force_interp<5>(phi, eps, alpha, nh, cellstart, Xs, Vs, ids_in, np, n, acc, Xo, Vo, ids_out, dt_kick,
+                               drift_scale, mode, s, bt, blockmax, &nblocks);
+  else if (order == 7)
+    r = launch_force_interp<7>(phi, eps, alpha, nh, cellstart, Xs, Vs, ids_in, np, n, acc, Xo, Vo, ids_out, dt_kick,
+                               drift_scale, mode, s, bt, blockmax, &nblocks);
+  if (r != PM_OK) return r;
+  if (blockmax) PM_LAUNCH(K_REDUCE, 8.0 * nblocks, k_max_pairs, 1, 1024, 0, s, blockmax, nblocks, max_out);
+  return launch_status();
+}
+
 pm_status interp_launch(const float* g, const uint32_t* Xs, const float* Vs, const uint32_t* ids_in, int64_t np,
                         int n, float* acc, uint32_t* Xo, float* Vo, uint32_t* ids_out, float dt_kick,
                         float dt_drift, int mode, bool vec4, cudaStream_t s, const Batch& bt,
-                        float2* blockmax, double* max_out, const uint32_t* cellstart) {
+                        float2* blockmax, double* max_out) {
   if (np == 0) return PM_OK;
   const float drift_scale = (float)((double)dt_drift * 4294967296.0);
   const double bytes = (vec4 ? 16.0 : 12.0) * n * n * (double)n * bt.B +
                        np * (12.0 + (mode ? 36.0 : 0.0) + (acc ? 12.0 : 0.0) + (ids_out ? 8.0 : 0.0));
   const int64_t np_box = bt.B > 1 ? bt.np_box : np;
+  const dim3 grid(grid_for(np_box, 256), 1, (unsigned)bt.B);
   if (!max_out) blockmax = nullptr;
-  int64_t nblocks;
-  if (cellstart && !vec4 && n >= 32) {
-    static bool attr = false;
-    if (!attr) {
-      PM_TRY(cuda_status(cudaFuncSetAttribute(k_interp_stream<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                              (int)kInterpStreamSmem)));
-      PM_TRY(cuda_status(cudaFuncSetAttribute(k_interp_stream<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                              (int)kInterpStreamSmem)));
-      attr = true;
-    }
-    const int tiles = (n / IT_Y) * (n / IT_Z);
-    int chunk = n;
-    while (chunk > 8 && (int64_t)tiles * (n / chunk) * bt.B < 16 * 152) chunk >>= 1;
-    const int nitems = tiles * (n / chunk);
-    const dim3 grid((unsigned)nitems, 1, (unsigned)bt.B);
-    nblocks = (int64_t)grid.x * grid.z;
-#define PM_INTERP_S(MX)                                                                                       \
-  PM_LAUNCH(K_INTERP, bytes, (k_interp_stream<MX>), grid, I_THREADS, kInterpStreamSmem, s, g, cellstart, Xs, Vs,  \
-            ids_in, np, ilog2(n), chunk, nitems, acc, Xo, Vo, ids_out, dt_kick, drift_scale, mode, bt.dt_kick,     \
-            bt.dt_drift, blockmax)
-    if (blockmax) PM_INTERP_S(true); else PM_INTERP_S(false);
-#undef PM_INTERP_S
-  } else {
-    const dim3 grid(grid_for(np_box, 256), 1, (unsigned)bt.B);
-    nblocks = (int64_t)grid.x * grid.z;
 #define PM_INTERP(V4, MX)                                                                                       \
   PM_LAUNCH(K_INTERP, bytes, (k_interp_kdk<V4, MX>), grid, 256, 0, s, g, Xs, Vs, ids_in, np, ilog2(n), acc, Xo, Vo, \
             ids_out, dt_kick, drift_scale, mode, np_box, bt.dt_kick, bt.dt_drift, blockmax)
-    if (vec4) {
-      if (blockmax) PM_INTERP(true, true); else PM_INTERP(true, false);
-    } else {
-      if (blockmax) PM_INTERP(false, true); else PM_INTERP(false, false);
-    }
-#undef PM_INTERP
+  if (vec4) {
+    if (blockmax) PM_INTERP(true, true); else PM_INTERP(true, false);
+  } else {
+    if (blockmax) PM_INTERP(false, true); else PM_INTERP(false, false);
   }
-  if (blockmax) PM_LAUNCH(K_REDUCE, 8.0 * nblocks, k_max_pairs, 1, 1024, 0, s, blockmax, nblocks, max_out);
+#undef PM_INTERP
+  if (blockmax) {
+    const int64_t nb = (int64_t)grid.x * grid.z;
+    PM_LAUNCH(K_REDUCE, 8.0 * nb, k_max_pairs, 1, 1024, 0, s, blockmax, nb, max_out);
+  }
   return launch_status();
 }
 

@@ -158,14 +158,21 @@ pm_status gradient_launch(const float* phi, const float* eps, float alpha, float
                           int order, bool vec4, cudaStream_t s, int batch = 1, int nh = 1);
 // mode 0: acc only; mode 1: kick + drift into Xo/Vo (and acc if non-NULL);
 // vec4: g interleaved as float4.  With max_out (2 doubles, device) also the
-// largest |a| and |v after the kick| (blockmax: one float2 per block).  With
-// the cell starts of the (cell-sorted) Xs and n >= 32, the streaming kernel
-// that stages the force planes in shared memory.
+// largest |a| and |v after the kick| (blockmax: one float2 per block).
 pm_status interp_launch(const float* g, const uint32_t* Xs, const float* Vs, const uint32_t* ids_in,
                         int64_t np, int n, float* acc, uint32_t* Xo, float* Vo, uint32_t* ids_out,
                         float dt_kick, float dt_drift, int mode, bool vec4, cudaStream_t s,
-                        const Batch& bt = Batch{}, float2* blockmax = nullptr, double* max_out = nullptr,
-                        const uint32_t* cellstart = nullptr);
+                        const Batch& bt = Batch{}, float2* blockmax = nullptr, double* max_out = nullptr);
+
+// The force g = -grad(phi [+ alpha ((1 + eps)^(nh+1) - 1)]) (order 3, 5 or
+// 7) computed in shared memory and interpolated at the cell-sorted particles
+// (with their cell starts; n >= 32) in one pass, as gradient_launch followed
+// by interp_launch (same arithmetic), without the force field in HBM.
+pm_status force_interp_launch(const float* phi, const float* eps, float alpha, int nh, int order,
+                              const uint32_t* cellstart, const uint32_t* Xs, const float* Vs, const uint32_t* ids_in,
+                              int64_t np, int n, float* acc, uint32_t* Xo, float* Vo, uint32_t* ids_out,
+                              float dt_kick, float dt_drift, int mode, cudaStream_t s, const Batch& bt = Batch{},
+                              float2* blockmax = nullptr, double* max_out = nullptr);
 
 // phi = scale * IFFT[G FFT[rho - mean]], G(0) = 0; kind 1: FFT_7pt, 2: FFT
 // with the exact kernel and TSC deconvolution (§3.7); mean (device float64)

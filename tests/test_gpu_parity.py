@@ -262,6 +262,20 @@ def test_step_accelerations_64_lcdm(pm, gravity):
     assert rel_l2(acc.T, ref) < 1e-5
 
 
+@pytest.mark.parametrize("order", [3, 5, 7])
+def test_step_force_in_shared_memory_equals_gradient_then_interpolation(pm, order):
+    """For n >= 32 the step computes the force next to the particles (shared
+    memory); it equals, bitwise, the force field of pm_gradient interpolated
+    by pm_interp at the same positions."""
+    n = 64
+    X, V = inputs.lpt_ics(n, float(n), 0.3, 0.7, 0.25, seed=5, order=2)
+    acc, sim = gpu_accelerations(pm, X, V, n, 0.25, boxsize=float(n), Om=0.3, OL=0.7, grad_order=order,
+                                 mg=pm.default_mg(tol=1e-7))
+    g = pm.gradient(sim.phi, order=order)
+    ref = pm.interp(g, pm.positions_to_device(X)).cpu().numpy()
+    assert np.array_equal(acc.astype(np.float32), ref)
+
+
 def test_step_is_deterministic(pm):
     n = 32
     X, V = inputs.zeldovich_powerlaw_ics(n, seed=2)
