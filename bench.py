@@ -159,9 +159,12 @@ def load_ncu_traffic():
 
 # --------------------------------------------------------------- oracle arm --
 
-def oracle_sample(steps):
-    """The FP64 oracle, unchanged, on a bounded sample of the workload: 32^3
-    particles on a 32^3 grid in a 32 Mpc/h box (the 1 Mpc/h cells of the
+ORACLE_N = 64   # oracle sample: 64^3 particles on a 64^3 grid (a few seconds of one core per step)
+
+
+def oracle_sample(steps, n=ORACLE_N):
+    """The FP64 oracle, unchanged, on a bounded sample of the workload: n^3
+    particles on an n^3 grid in an n Mpc/h box (the 1 Mpc/h cells of the
     512^3 run), same cosmology, f_R0 and 2LPT start at z = 30, advanced through
     the first ``steps`` steps of the same schedule with f(R) forces (exact
     discrete Poisson inverse, one FAS F-cycle) and kick-drift-kick.  Returns
@@ -170,7 +173,6 @@ def oracle_sample(steps):
         os.environ.setdefault(v, "1")
     from oracle import mesh, step
     from paper_2410_20501_gb300 import inputs
-    n = 32
     X, V = inputs.lpt_ics(n, float(n), OM, OL, 1.0 / (1.0 + Z_INI), SEED, order=2)
     prm = step.PMParams(n=n, Om=OM, OL=OL, boxsize=float(n), gravity="fr", fR0=FR0)
     a = schedule()[:steps + 1]
@@ -178,8 +180,8 @@ def oracle_sample(steps):
     step.run_kdk(mesh.positions_from_fixed_point(X), V.T, a, prm, warm_start=False)
     dt = time.perf_counter() - t0
     return n ** 3 * steps / dt, dt, (f"FP64 oracle, {steps} f(R) PM steps (deposit, exact 7-point Poisson "
-                                     f"inverse, one FAS F-cycle, 5-point gradient, inverse TSC, KDK) of 32^3 "
-                                     f"particles on a 32^3 grid with the 1 Mpc/h cells of the 512^3 run")
+                                     f"inverse, one FAS F-cycle, 5-point gradient, inverse TSC, KDK) of {n}^3 "
+                                     f"particles on a {n}^3 grid with the 1 Mpc/h cells of the 512^3 run")
 
 
 def run_reference(args):
@@ -193,7 +195,7 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / max(1, args.steps),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "impl": "reference",
-            "config": {"workload": "hu-sawicki f(R) pm step, bounded oracle sample", "n": 32},
+            "config": {"workload": "hu-sawicki f(R) pm step, bounded oracle sample", "n": ORACLE_N},
             "cpu_baseline": {"value": value, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": "particle-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -467,6 +469,27 @@ def run_gpu(args):
     return 0
 
 
+def run_step_stage(n, steps, warmup):
+    """The f(R) step of the bench workload at n^3 particles on an n^3 grid
+    (same 1 Mpc/h cells, cosmology, schedule and solver settings): a small
+    case of every step kernel for profilers.  Returns the device time per
+    step."""
+    import torch
+    from paper_2410_20501_gb300 import build, inputs, pm
+    if not os.path.exists(pm.LIB_PATH):
+        build.build()
+    box = BOX * n / N_GRID
+    a = schedule()
+    coeffs = step_coefficients(OM, OL, a)
+    X, V = inputs.lpt_ics(n, box, OM, OL, a[0], SEED, order=2, device="cuda")
+    sim = pm.Simulation(X, V, n, OM, OL, box, gravity="fr", fR0=FR0,
+                        mg=pm.default_mg(tol=1e-7, stall=0.5, max_cycles=12, fixed_cycles=2),
+                        fr=pm.default_fr(cycle=1, cycles=1))
+    timed_steps(sim, coeffs, 0, warmup)
+    ms, _ = timed_steps(sim, coeffs, warmup, steps)
+    return {"stage": "step", "n": n, "steps": steps, "ms_per_step": ms}
+
+
 def run_stage(args):
     """One stage alone on seeded synthetic inputs at size n (for profilers:
     a few GB on the device at most).  Prints one JSON line with the
@@ -534,7 +557,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--lean", action="store_true",
                     help="f(R) device-timed steps only (no Newtonian line, e2e or CPU baseline): for profilers")
-    ap.add_argument("--stage", choices=["sort", "deposit", "mg", "fr", "interp", "adjoint", "ensemble", "lpt"],
+    ap.add_argument("--stage", choices=["sort", "deposit", "mg", "fr", "interp", "adjoint", "ensemble", "lpt", "step"],
                     help="time one stage alone on synthetic inputs (for profilers)")
     ap.add_argument("--n", type=int, default=256, help="grid size for --stage")
     ap.add_argument("--smoother", type=int, default=2,
@@ -548,6 +571,9 @@ def main():
         return 0
     if args.stage == "lpt":
         print(json.dumps(run_lpt(args.n, args.steps)))
+        return 0
+    if args.stage == "step":
+        print(json.dumps(run_step_stage(args.n, args.steps, args.warmup)))
         return 0
     if args.stage:
         return run_stage(args)
