@@ -78,14 +78,21 @@ __global__ void __launch_bounds__(KT) k_cell_count(const uint32_t* __restrict__ 
   }
 }
 
-// perm[cellstart[key] + rank] = i.
+// perm[cellstart[key] + rank] = i; a thread takes CI particles, KT apart, with
+// their loads in flight together.
 __global__ void __launch_bounds__(KT) k_cell_scatter(const uint2* __restrict__ kr, int64_t np,
                                                      const uint32_t* __restrict__ cellstart,
                                                      uint32_t* __restrict__ perm) {
-  const int64_t i = blockIdx.x * (int64_t)KT + threadIdx.x;
-  if (i >= np) return;
-  const uint2 t = __ldg(kr + i);
-  perm[__ldg(cellstart + t.x) + t.y] = (uint32_t)i;
+  const int64_t i0 = blockIdx.x * (int64_t)(KT * CI) + threadIdx.x;
+  uint2 t[CI];
+  uint32_t base[CI];
+#pragma unroll
+  for (int k = 0; k < CI; ++k) t[k] = i0 + k * KT < np ? __ldg(kr + i0 + k * KT) : make_uint2(0u, 0u);
+#pragma unroll
+  for (int k = 0; k < CI; ++k) base[k] = i0 + k * KT < np ? __ldg(cellstart + t[k].x) : 0u;
+#pragma unroll
+  for (int k = 0; k < CI; ++k)
+    if (i0 + k * KT < np) perm[base[k] + t[k].y] = (uint32_t)(i0 + k * KT);
 }
 
 // Stable order inside each cell: the ranks of cell c, cellstart[c] ..
@@ -329,13 +336,13 @@ pm_status sort_cells(const uint32_t* X, int64_t np, int n, Workspace& w, cudaStr
   PM_TRY(cuda_status(cudaMemsetAsync(cellstart, 0, (size_t)(ncells + 1) * 4, s)));
   if (np == 0) return PM_OK;
   const int64_t np_box = bt.B > 1 ? bt.np_box : 0;
-  const unsigned gp = grid_for(np, KT), gc = grid_for(np, KT * CI);
+  const unsigned gc = grid_for(np, KT * CI);
   if (np_box > 0)
     PM_LAUNCH(K_KEYS, 28.0 * np, k_cell_count<true>, gc, KT, 0, s, X, np, log2n, np_box, w.keyrank, cellstart);
   else
     PM_LAUNCH(K_KEYS, 28.0 * np, k_cell_count<false>, gc, KT, 0, s, X, np, log2n, np_box, w.keyrank, cellstart);
   PM_TRY(scan_u32(cellstart, ncells + 1, w.scan_blocks, s));
-  PM_LAUNCH(K_SCATTER, 16.0 * np, k_cell_scatter, gp, KT, 0, s, w.keyrank, np, cellstart, w.perm);
+  PM_LAUNCH(K_SCATTER, 16.0 * np, k_cell_scatter, gc, KT, 0, s, w.keyrank, np, cellstart, w.perm);
   PM_TRY(cuda_status(cudaMemsetAsync(w.runs, 0, 4, s)));
   PM_LAUNCH(K_ORDER, 4.0 * ncells + 8.0 * np, k_cell_order, grid_for(ncells / 4, KT), KT, 0, s, cellstart, ncells,
             w.perm, w.runs);
