@@ -487,7 +487,7 @@ def run_step_stage(n, steps, warmup):
                         fr=pm.default_fr(cycle=1, cycles=1))
     timed_steps(sim, coeffs, 0, warmup)
     ms, _ = timed_steps(sim, coeffs, warmup, steps)
-    return {"stage": "step", "n": n, "steps": steps, "ms_per_step": ms}
+    return {"stage": "step", "n": n, "steps": steps, "ms_per_step": ms / steps}
 
 
 def run_stage(args):
