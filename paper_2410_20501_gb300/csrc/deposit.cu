@@ -92,11 +92,11 @@ __global__ void __launch_bounds__(T * T * T) k_deposit(const uint32_t* __restric
 // accumulators.  A destination plane is complete (and written) once the
 // source plane after it has been added.  The cell starts of plane x + 2 and
 // the first particle of plane x + 1 are loaded while plane x is processed.
-constexpr int DTY = 16, DTZ = 32, DEY = DTY + 2, DEZ = DTZ + 2, DNT = DTY * DTZ, DTHREADS = 1024;
+constexpr int DTY = 16, DTZ = 16, DEY = DTY + 2, DEZ = DTZ + 2, DNT = DTY * DTZ, DTHREADS = 512;
 constexpr size_t kDepositStreamSmem = sizeof(float) * (27 * DEY * DEZ + 3 * DNT);
 static_assert(DEY * DEZ <= DTHREADS, "one source cell per thread");
 
-__global__ void __launch_bounds__(DTHREADS, 1) k_deposit_stream(const uint32_t* __restrict__ Xs, int64_t np,
+__global__ void __launch_bounds__(DTHREADS, 2) k_deposit_stream(const uint32_t* __restrict__ Xs, int64_t np,
                                                                 const uint32_t* __restrict__ cellstart, int log2n,
                                                                 int chunk, int nitems, const float* __restrict__ vals,
                                                                 float scale, float* __restrict__ rho,
@@ -313,7 +313,7 @@ pm_status deposit_sorted_values(const uint32_t* Xs, int64_t np, const uint32_t* 
     }
     int chunk, nitems;
     deposit_stream_plan(n, &chunk, &nitems);
-    const unsigned grid = (unsigned)(nitems < 152 ? nitems : 152);   // one 1024-thread CTA per SM
+    const unsigned grid = (unsigned)nitems;   // one item per CTA, two 512-thread CTAs per SM
     PM_LAUNCH(K_DEPOSIT, (vals ? 16.0 : 12.0) * np + 8.0 * n * n * (double)n + 4.0, k_deposit_stream, grid, DTHREADS,
               kDepositStreamSmem, s, Xs, np, cellstart, ilog2(n), chunk, nitems, vals, scale, rho, partials);
     PM_LAUNCH(K_REDUCE, 8.0 * nitems, k_reduce_partials, 1, 1024, 0, s, partials, (int64_t)nitems, (int64_t)0, 1,
@@ -336,7 +336,7 @@ pm_status deposit_sorted_batch(const uint32_t* Xs, int64_t np_box, int B, const 
   int chunk, nitems;
   deposit_stream_plan(n, &chunk, &nitems);
   const float scale = np_box > 0 ? (float)((double)n * n * n / (double)np_box) : 0.0f;
-  // one item per CTA: B x nitems CTAs balance over the SMs (one resident each)
+  // one item per CTA: B x nitems CTAs balance over the SMs (two resident each)
   const int gx = nitems;
   const int64_t np = np_box * B;
   PM_LAUNCH(K_DEPOSIT, 12.0 * np + 8.0 * n * n * (double)n * B + 4.0, k_deposit_stream, dim3(gx, 1, B), DTHREADS,
