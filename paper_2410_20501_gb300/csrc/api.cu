@@ -143,6 +143,32 @@ namespace {
 
 cudaStream_t as_stream(void* s) { return (cudaStream_t)s; }
 
+// A second stream (and fork / join events) per device for work that runs
+// beside the caller's stream inside one call.
+struct SideStream {
+  cudaStream_t s = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
+};
+SideStream g_side[64];
+
+pm_status side_stream(SideStream** out) {
+  int dev = 0;
+  PM_TRY(cuda_status(cudaGetDevice(&dev)));
+  if (dev < 0 || dev >= 64) return PM_EINVAL;
+  SideStream& ss = g_side[dev];
+  if (!ss.s) {
+    PM_TRY(cuda_status(cudaStreamCreateWithFlags(&ss.s, cudaStreamNonBlocking)));
+    PM_TRY(cuda_status(cudaEventCreateWithFlags(&ss.fork, cudaEventDisableTiming)));
+    PM_TRY(cuda_status(cudaEventCreateWithFlags(&ss.join, cudaEventDisableTiming)));
+  }
+  *out = &ss;
+  return PM_OK;
+}
+
+// Offset (in doubles) of the side stream's share of the partials: past the
+// 2 x (152 x 8) block sums of a residual norm on the main stream, twice.
+constexpr int64_t kSidePartials = 4 * 152 * 8;
+
 bool aligned(const void* p) { return ((uintptr_t)p & 255) == 0; }
 
 // Device arrays of the caller start on 16-byte boundaries (NULL passes: the
@@ -376,25 +402,43 @@ pm_status pm_step(pm_state* st_, const pm_step_params* prm, pm_stats* stats, voi
 
   double fbar = 0.0, kappa = 0.0, c2 = 0.0;
   pm_status solve_status = PM_OK;
+  // The scalaron (FAS) and the Newtonian potential (multigrid or FFT) both
+  // depend on the density only: the scalaron runs on a side stream, forked
+  // after the deposit and joined before the force, so the two solvers' many
+  // small-level launches overlap.  It reduces its norms in its own part of
+  // the partials.
+  SideStream* side = nullptr;
+  pm_status fr_status = PM_OK;
   if (prm->gravity == PM_GRAVITY_FR) {
     fr_background(frp, &fbar, &kappa, &c2);
     if (!S.have_prev) PM_TRY(cuda_status(cudaMemsetAsync(S.eps, 0, N * sizeof(float), s)));
+    PM_TRY(side_stream(&side));
+    PM_TRY(cuda_status(cudaEventRecord(side->fork, s)));
+    PM_TRY(cuda_status(cudaStreamWaitEvent(side->s, side->fork, 0)));
+    Workspace wf = w;
+    wf.partials = w.partials + kSidePartials;
     const float sb = (float)(-prm->Om * prm->a / c2);
-    pm_status r = fr_solve_src(Src{w.rho, sb, w.scalars}, S.eps, n, frp, &local.fr, w, s);
-    if (r != PM_OK && r != PM_ENOCONV) return r;
-    if (r != PM_OK) solve_status = r;
+    fr_status = fr_solve_src(Src{w.rho, sb, w.scalars}, S.eps, n, frp, &local.fr, wf, side->s);
+    PM_TRY(cuda_status(cudaEventRecord(side->join, side->s)));
+    if (fr_status != PM_OK && fr_status != PM_ENOCONV) {
+      PM_TRY(cuda_status(cudaStreamWaitEvent(s, side->join, 0)));
+      return fr_status;
+    }
+    if (fr_status != PM_OK) solve_status = fr_status;
   }
   mg_params mp = prm->mg;
   mp.first_guess = S.have_prev ? MG_GUESS_SCALED : MG_GUESS_JACOBI;
   mp.guess_scale = (float)prm->phi_rescale;
   if (!S.have_prev) mp.fixed_cycles = 0;   // a cold start always iterates to the tolerance
+  pm_status mg_status = PM_OK;
   if (prm->poisson != PM_POISSON_MG) {
-    PM_TRY(fft_poisson_launch(w.rho, w.scalars, S.phi, w.spec, n, prm->poisson, poisson_scale(*prm), s));
+    mg_status = fft_poisson_launch(w.rho, w.scalars, S.phi, w.spec, n, prm->poisson, poisson_scale(*prm), s);
   } else {
-    pm_status r = mg_solve_src(Src{w.rho, (float)poisson_scale(*prm), w.scalars}, S.phi, n, mp, &local.mg, w, s);
-    if (r != PM_OK && r != PM_ENOCONV) return r;
-    if (r != PM_OK) solve_status = r;
+    mg_status = mg_solve_src(Src{w.rho, (float)poisson_scale(*prm), w.scalars}, S.phi, n, mp, &local.mg, w, s);
   }
+  if (side) PM_TRY(cuda_status(cudaStreamWaitEvent(s, side->join, 0)));   // the scalaron is done
+  if (mg_status != PM_OK && mg_status != PM_ENOCONV) return mg_status;
+  if (mg_status != PM_OK) solve_status = mg_status;
   const float alpha = (float)(-0.5 * c2 * fbar);
   const float* eps_force = prm->gravity == PM_GRAVITY_FR ? S.eps : nullptr;
   const int nh = frp.nhs == 2 ? 2 : 1;
