@@ -249,6 +249,28 @@ def test_step_accelerations_fr(pm):
     assert rel_l2(acc.T, ref) < 1e-5
 
 
+def test_step_fr_and_poisson_to_tolerance_together(pm):
+    """Both solvers iterating to a tolerance in one step (the scalaron on its
+    side stream, each reducing its residual norms in its own buffer): the
+    step reports both converged and the forces match the oracle."""
+    n = 32
+    X = displaced_lattice(n, 17, amp=0.45)
+    V = np.zeros((3, n ** 3))
+    mgp = pm.default_mg(tol=1e-9)
+    frp = pm.default_fr(coarsest=16, tol=1e-4, max_cycles=20)
+    sim = pm.Simulation(X, V, n, Om=0.3, OL=0.7, boxsize=float(n), gravity="fr", track_ids=True, keep_acc=True,
+                        mg=mgp, fr=frp)
+    st = sim.step(a=0.7, dt_kick=0.0, dt_drift=0.0)
+    acc = np.empty((3, X.shape[1]))
+    acc[:, sim.particle_ids()] = sim.acc.cpu().numpy()
+    assert st["fr"]["status"] == 0 and st["fr"]["cycles"] > 1
+    assert st["mg"]["status"] == 0 and st["mg"]["cycles"] > 1
+    # the oracle's scalaron from ten F-cycles (converged far below 1e-4)
+    prm = step.PMParams(n=n, Om=0.3, OL=0.7, boxsize=float(n), gravity="fr", fR0=-1e-5, fr_cycles=10)
+    ref, _, _ = step.accelerations(mesh.positions_from_fixed_point(X), 0.7, prm)
+    assert rel_l2(acc.T, ref) < 1e-4
+
+
 @pytest.mark.parametrize("gravity", ["newton", "fr"])
 def test_step_accelerations_64_lcdm(pm, gravity):
     """64^3 LCDM 2LPT particles (the float4 gradient / interpolation path of
