@@ -148,7 +148,9 @@ __global__ void __launch_bounds__(DTHREADS, 2) k_deposit_stream(const uint32_t* 
         for (int o = 0; o < 27; ++o) m[o] = 0.0f;
         uint32_t px = fx, py = fy, pz = fz;
         for (uint32_t p = b0; p < e0; ++p) {
-          if (p > b0) { px = __ldg(Xs + p); py = __ldg(Xs + np + p); pz = __ldg(Xs + 2 * np + p); }
+          // the next particle of the cell is loaded while this one is weighed
+          uint32_t qx = 0, qy = 0, qz = 0;
+          if (p + 1 < e0) { qx = __ldg(Xs + p + 1); qy = __ldg(Xs + np + p + 1); qz = __ldg(Xs + 2 * np + p + 1); }
           float wx[3], wy[3], wz[3];
           tsc_weights(cell_offset(px, log2n), wx);
           tsc_weights(cell_offset(py, log2n), wy);
@@ -165,6 +167,9 @@ __global__ void __launch_bounds__(DTHREADS, 2) k_deposit_stream(const uint32_t* 
 #pragma unroll
               for (int oz = 0; oz < 3; ++oz) m[(ox * 3 + oy) * 3 + oz] = fmaf(wxy, wz[oz], m[(ox * 3 + oy) * 3 + oz]);
             }
+          px = qx;
+          py = qy;
+          pz = qz;
         }
 #pragma unroll
         for (int o = 0; o < 27; ++o) Mom[o * PL + tid] = m[o];

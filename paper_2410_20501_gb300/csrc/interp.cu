@@ -283,6 +283,13 @@ __device__ __forceinline__ void column_particles(const float* const S[3], const 
       if (pre[j + b] <= i) j += b;
     const int64_t p = (int64_t)st[j] + (i - pre[j]);
     const uint32_t x = __ldg(Xs + p), y = __ldg(Xs + np + p), z = __ldg(Xs + 2 * np + p);
+    // velocities in flight while the force is summed
+    float v0x = 0.0f, v0y = 0.0f, v0z = 0.0f;
+    if (mode == 1) {
+      v0x = __ldg(Vs + p);
+      v0y = __ldg(Vs + np + p);
+      v0z = __ldg(Vs + 2 * np + p);
+    }
     float wx[3], wy[3], wz[3];
     tsc_weights(cell_offset(x, log2n), wx);
     tsc_weights(cell_offset(y, log2n), wy);
@@ -311,9 +318,9 @@ __device__ __forceinline__ void column_particles(const float* const S[3], const 
     }
     if (MAXES) amax = fmaxf(amax, sqrtf(fmaf(ax, ax, fmaf(ay, ay, az * az))));
     if (mode == 1) {
-      const float vx = fmaf(ax, dt_kick, __ldg(Vs + p));
-      const float vy = fmaf(ay, dt_kick, __ldg(Vs + np + p));
-      const float vz = fmaf(az, dt_kick, __ldg(Vs + 2 * np + p));
+      const float vx = fmaf(ax, dt_kick, v0x);
+      const float vy = fmaf(ay, dt_kick, v0y);
+      const float vz = fmaf(az, dt_kick, v0z);
       Vo[p] = vx;
       Vo[np + p] = vy;
       Vo[2 * np + p] = vz;
