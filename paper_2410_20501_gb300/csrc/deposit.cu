@@ -90,10 +90,12 @@ __global__ void __launch_bounds__(T * T * T) k_deposit(const uint32_t* __restric
 // and lets every destination cell of the column add, in a fixed order, the
 // moments that point at it into a ring of three destination-plane
 // accumulators.  A destination plane is complete (and written) once the
-// source plane after it has been added.  The cell starts of plane x + 2 and
-// the first particle of plane x + 1 are loaded while plane x is processed.
+// source plane after it has been added.  The moments are double-buffered:
+// the sources of plane x are computed while the destinations add plane x - 1
+// (one barrier per plane).  The cell starts of plane x + 2 and the first
+// particle of plane x + 1 are loaded while plane x is processed.
 constexpr int DTY = 16, DTZ = 16, DEY = DTY + 2, DEZ = DTZ + 2, DNT = DTY * DTZ, DTHREADS = 512;
-constexpr size_t kDepositStreamSmem = sizeof(float) * (27 * DEY * DEZ + 3 * DNT);
+constexpr size_t kDepositStreamSmem = sizeof(float) * (2 * 27 * DEY * DEZ + 3 * DNT);
 static_assert(DEY * DEZ <= DTHREADS, "one source cell per thread");
 
 __global__ void __launch_bounds__(DTHREADS, 2) k_deposit_stream(const uint32_t* __restrict__ Xs, int64_t np,
@@ -108,8 +110,8 @@ __global__ void __launch_bounds__(DTHREADS, 2) k_deposit_stream(const uint32_t* 
     rho += off;
     partial += (int64_t)blockIdx.z * nitems;
   }
-  float* Mom = sm;                      // [27][DEY * DEZ]
-  float* Acc = sm + 27 * DEY * DEZ;     // [3][DNT]
+  float* Mom = sm;                      // [2][27][DEY * DEZ]
+  float* Acc = sm + 2 * 27 * DEY * DEZ; // [3][DNT]
   __shared__ double wsum[DTHREADS / 32];
   constexpr int PL = DEY * DEZ;
   const int n = 1 << log2n, mask = n - 1;
@@ -135,9 +137,14 @@ __global__ void __launch_bounds__(DTHREADS, 2) k_deposit_stream(const uint32_t* 
       b1 = __ldg(cellstart + c1); e1 = __ldg(cellstart + c1 + 1);
       if (b0 < e0) { fx = __ldg(Xs + b0); fy = __ldg(Xs + np + b0); fz = __ldg(Xs + 2 * np + b0); }
     }
-    for (int xs = x0 - 1; xs <= x1; ++xs) {
+    for (int xs = x0 - 1; xs <= x1 + 1; ++xs) {
+      // the moments of source plane xs go to one buffer while the
+      // destinations add those of plane xs - 1 from the other: one barrier
+      // per step
+      float* MomW = Mom + (xs & 1) * 27 * PL;
+      const float* MomR = Mom + ((xs - 1) & 1) * 27 * PL;
       uint32_t nfx = 0, nfy = 0, nfz = 0, b2 = 0, e2 = 0;
-      if (src) {
+      if (src && xs <= x1) {
         if (b1 < e1) { nfx = __ldg(Xs + b1); nfy = __ldg(Xs + np + b1); nfz = __ldg(Xs + 2 * np + b1); }
         if (xs + 2 <= x1) {
           const uint32_t c2 = cell_of(xs + 2);
@@ -172,25 +179,25 @@ __global__ void __launch_bounds__(DTHREADS, 2) k_deposit_stream(const uint32_t* 
           pz = qz;
         }
 #pragma unroll
-        for (int o = 0; o < 27; ++o) Mom[o * PL + tid] = m[o];
+        for (int o = 0; o < 27; ++o) MomW[o * PL + tid] = m[o];
       }
-      __syncthreads();
-      if (dst) {
-        // destination plane xs + ox - 1 receives the moments with x offset ox - 1
+      const int xr = xs - 1;   // the source plane whose moments the destinations add now
+      if (dst && xr >= x0 - 1) {
+        // destination plane xr + ox - 1 receives the moments with x offset ox - 1
 #pragma unroll
         for (int ox = 0; ox < 3; ++ox) {
-          const int d = xs + ox - 1;
+          const int d = xr + ox - 1;
           if (d < x0 || d >= x1) continue;
           float a = 0.0f;
 #pragma unroll
           for (int oy = 0; oy < 3; ++oy)
 #pragma unroll
             for (int oz = 0; oz < 3; ++oz)
-              a += Mom[((ox * 3 + oy) * 3 + oz) * PL + (ty + 2 - oy) * DEZ + (tz + 2 - oz)];
+              a += MomR[((ox * 3 + oy) * 3 + oz) * PL + (ty + 2 - oy) * DEZ + (tz + 2 - oz)];
           Acc[(d % 3) * DNT + tid] += a;
         }
-        // plane xs - 1 has now received its three source planes
-        const int done = xs - 1;
+        // plane xr - 1 has now received its three source planes
+        const int done = xr - 1;
         if (done >= x0 && done < x1) {
           float* slot = Acc + (done % 3) * DNT;
           const float r = slot[tid] * scale;
