@@ -358,9 +358,10 @@ __device__ __forceinline__ void block_maxima(float amax, float vmax, float2* __r
 // The force planes from the potential in shared memory, then the particles.
 // Per plane step u: the potential plane u (with a halo of R + 1 in y and z;
 // loaded into registers one step ahead, combined with eps for f(R)) goes to a
-// ring of 2R + 1 slots; after a barrier the force plane u - R (with a
-// one-cell halo) is computed into a ring of 4 slots; after a second barrier
-// the particles of plane u - R - 1 are interpolated.
+// ring of 2R + 2 slots; after the step's one barrier the force plane u - R
+// (with a one-cell halo) is computed into a ring of 4 slots while the
+// particles of plane u - R - 2 are interpolated from the three force planes
+// computed in the steps before.
 template <int ORDER, bool FR, bool MAXES>
 __global__ void __launch_bounds__(I_THREADS) k_force_interp_stream(
     const float* __restrict__ phi, const float* __restrict__ eps, float alpha, int nh, float inv_h,
@@ -370,11 +371,11 @@ __global__ void __launch_bounds__(I_THREADS) k_force_interp_stream(
     float drift_scale, int mode, const float* __restrict__ dtk_box, const float* __restrict__ dtd_box,
     float2* __restrict__ blockmax) {
   constexpr int R = Stencil<ORDER>::R, H = R + 1, PEY = IT_Y + 2 * H, PEZ = IT_Z + 2 * H, PPL = PEY * PEZ,
-                PS = 2 * R + 1, PL_T = (PPL + I_THREADS - 1) / I_THREADS;
+                PS = 2 * R + 2, PL_T = (PPL + I_THREADS - 1) / I_THREADS;
   extern __shared__ float fsm[];
   float* Gs = fsm;                   // [4][3][IE_Y][IE_Z]
   float* Ps = Gs + 4 * 3 * I_PL;     // [PS][PEY][PEZ]
-  __shared__ uint32_t s_start[IT_Y], s_pre[IT_Y + 1];
+  __shared__ uint32_t s_start[2][IT_Y], s_pre[2][IT_Y + 1];
   const int n = 1 << log2n, m = n - 1;
   const int64_t N = (int64_t)1 << (3 * log2n);
   phi += (int64_t)blockIdx.z * N;   // the box of a batched launch
@@ -419,14 +420,17 @@ __global__ void __launch_bounds__(I_THREADS) k_force_interp_stream(
         }
       }
     };
-    const int u0 = x0 - 1 - R, u1 = x1 + R;   // potential planes of the chunk
+    // step u: potential plane u stored, force plane u - R computed, particles
+    // of plane u - R - 2 interpolated (their force planes were computed in
+    // the three steps before): one barrier per step
+    const int u0 = x0 - 1 - R, ulast = x1 + R + 1;
     fetch(u0);
-    for (int u = u0; u <= u1; ++u) {
-      store(u);
-      if (u < u1) fetch(u + 1);
+    for (int u = u0; u <= ulast; ++u) {
+      if (u <= x1 + R) store(u);
+      if (u < x1 + R) fetch(u + 1);
       __syncthreads();
-      const int qg = u - R;                    // force plane computed this step
-      if (qg >= x0 - 1) {
+      const int qg = u - R;
+      if (qg >= x0 - 1 && qg <= x1) {
         float* G = Gs + (qg & 3) * 3 * I_PL;
         const float* Pc = Ps + (((qg % PS) + PS) % PS) * PPL;
         for (int e = tid; e < I_PL; e += I_THREADS) {
@@ -447,15 +451,15 @@ __global__ void __launch_bounds__(I_THREADS) k_force_interp_stream(
           G[2 * I_PL + e] = -gz * inv_h;
         }
       }
-      const int t = qg - 1;                    // particle plane of this step
-      if (t >= x0 && t < x1) column_runs(cellstart, t, y0, z0, log2n, s_start, s_pre);
-      __syncthreads();
+      const int t = qg - 2;   // particle plane of this step
+      if (t + 1 >= x0 && t + 1 < x1)
+        column_runs(cellstart, t + 1, y0, z0, log2n, s_start[(t + 1) & 1], s_pre[(t + 1) & 1]);
       if (t >= x0 && t < x1) {
         const float* S[3];
 #pragma unroll
         for (int ox = 0; ox < 3; ++ox) S[ox] = Gs + ((t + ox - 1) & 3) * 3 * I_PL;
-        column_particles<MAXES>(S, s_start, s_pre, y0, z0, Xs, Vs, ids_in, np, log2n, acc, Xo, Vo, ids_out, dt_kick,
-                                drift_scale, mode, amax, vmax);
+        column_particles<MAXES>(S, s_start[t & 1], s_pre[t & 1], y0, z0, Xs, Vs, ids_in, np, log2n, acc, Xo, Vo,
+                                ids_out, dt_kick, drift_scale, mode, amax, vmax);
       }
     }
     __syncthreads();   // the rings and run buffers are reused by the next item
@@ -465,7 +469,7 @@ __global__ void __launch_bounds__(I_THREADS) k_force_interp_stream(
 
 template <int ORDER>
 constexpr size_t force_interp_smem() {
-  return sizeof(float) * (4 * 3 * I_PL + (2 * Stencil<ORDER>::R + 1) * (IT_Y + 2 * Stencil<ORDER>::R + 2) *
+  return sizeof(float) * (4 * 3 * I_PL + (2 * Stencil<ORDER>::R + 2) * (IT_Y + 2 * Stencil<ORDER>::R + 2) *
                                              (IT_Z + 2 * Stencil<ORDER>::R + 2));
 }
 
