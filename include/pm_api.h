@@ -301,6 +301,11 @@ typedef struct {
   double mu0;          /* PM_GRAVITY_PARAM: the coupling today minus one      */
   int report_max;      /* 1: fill pm_stats.max_acc / max_vel (one 16-byte
                           device-to-host read: the call synchronises)        */
+  int serial;          /* f(R): 0 (default) runs the scalaron solve on a
+                          second stream beside the Newtonian Poisson solve
+                          (both depend on the density only); 1 runs it on
+                          `stream` before the Poisson solve (same results;
+                          per-kernel timing without overlap)                 */
 } pm_step_params;
 
 typedef struct {

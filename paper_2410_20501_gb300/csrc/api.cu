@@ -412,16 +412,20 @@ pm_status pm_step(pm_state* st_, const pm_step_params* prm, pm_stats* stats, voi
   if (prm->gravity == PM_GRAVITY_FR) {
     fr_background(frp, &fbar, &kappa, &c2);
     if (!S.have_prev) PM_TRY(cuda_status(cudaMemsetAsync(S.eps, 0, N * sizeof(float), s)));
-    PM_TRY(side_stream(&side));
-    PM_TRY(cuda_status(cudaEventRecord(side->fork, s)));
-    PM_TRY(cuda_status(cudaStreamWaitEvent(side->s, side->fork, 0)));
-    Workspace wf = w;
-    wf.partials = w.partials + kSidePartials;
     const float sb = (float)(-prm->Om * prm->a / c2);
-    fr_status = fr_solve_src(Src{w.rho, sb, w.scalars}, S.eps, n, frp, &local.fr, wf, side->s);
-    PM_TRY(cuda_status(cudaEventRecord(side->join, side->s)));
+    if (prm->serial) {
+      fr_status = fr_solve_src(Src{w.rho, sb, w.scalars}, S.eps, n, frp, &local.fr, w, s);
+    } else {
+      PM_TRY(side_stream(&side));
+      PM_TRY(cuda_status(cudaEventRecord(side->fork, s)));
+      PM_TRY(cuda_status(cudaStreamWaitEvent(side->s, side->fork, 0)));
+      Workspace wf = w;
+      wf.partials = w.partials + kSidePartials;
+      fr_status = fr_solve_src(Src{w.rho, sb, w.scalars}, S.eps, n, frp, &local.fr, wf, side->s);
+      PM_TRY(cuda_status(cudaEventRecord(side->join, side->s)));
+    }
     if (fr_status != PM_OK && fr_status != PM_ENOCONV) {
-      PM_TRY(cuda_status(cudaStreamWaitEvent(s, side->join, 0)));
+      if (side) PM_TRY(cuda_status(cudaStreamWaitEvent(s, side->join, 0)));
       return fr_status;
     }
     if (fr_status != PM_OK) solve_status = fr_status;

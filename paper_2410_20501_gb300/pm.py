@@ -72,7 +72,7 @@ class pm_step_params(ctypes.Structure):
                 ("boxsize", ctypes.c_double), ("gravity", ctypes.c_int), ("fR0", ctypes.c_double),
                 ("grad_order", ctypes.c_int), ("dt_kick", ctypes.c_double), ("dt_drift", ctypes.c_double),
                 ("phi_rescale", ctypes.c_double), ("mg", mg_params), ("fr", fr_params), ("poisson", ctypes.c_int),
-                ("mu0", ctypes.c_double), ("report_max", ctypes.c_int)]
+                ("mu0", ctypes.c_double), ("report_max", ctypes.c_int), ("serial", ctypes.c_int)]
 
 
 class pm_stats(ctypes.Structure):
@@ -430,6 +430,7 @@ class Simulation:
                     if self.gravity == PM_GRAVITY_FR else None)
         self.acc = torch.empty((3, self.np), dtype=torch.float32, device=device) if keep_acc else None
         self.poisson = poisson
+        self.serial = False   # True: scalaron solve on the caller's stream (per-kernel timing without overlap)
         flags = (PM_WS_STEP | (PM_WS_IDS if track_ids else 0) | (PM_WS_ADJ if adjoint else 0)
                  | (PM_WS_FFT if poisson else 0))
         self.ws = workspace(n, self.np, flags, device)
@@ -445,7 +446,7 @@ class Simulation:
         return pm_step_params(a=a, Om=self.Om, OL=self.OL, boxsize=self.boxsize, gravity=self.gravity,
                               fR0=self.fR0, grad_order=self.grad_order, dt_kick=dt_kick, dt_drift=dt_drift,
                               phi_rescale=phi_rescale, mg=self.mg, fr=self.fr, poisson=self.poisson, mu0=self.mu0,
-                              report_max=1 if report_max else 0)
+                              report_max=1 if report_max else 0, serial=1 if self.serial else 0)
 
     def step(self, a, dt_kick, dt_drift, phi_rescale=1.0, report_max=False):
         st = pm_stats()

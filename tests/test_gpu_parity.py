@@ -271,6 +271,31 @@ def test_step_fr_and_poisson_to_tolerance_together(pm):
     assert rel_l2(acc.T, ref) < 1e-4
 
 
+def test_step_fr_serial_equals_side_stream(pm):
+    """The scalaron solve on the caller's stream (serial) and on the side
+    stream beside the Poisson solve give bitwise-equal particles over three
+    kick-drift-kick steps (same kernels, same reductions, own norm buffers)."""
+    import torch
+    n = 64
+    X, V = inputs.lpt_ics(n, float(n), 0.3, 0.7, 0.25, seed=21, order=2)
+    out = []
+    for serial in (False, True):
+        sim = pm.Simulation(X, V, n, Om=0.3, OL=0.7, boxsize=float(n), gravity="fr", track_ids=True,
+                            mg=pm.default_mg(tol=1e-7), fr=pm.default_fr(tol=1e-3, max_cycles=4))
+        sim.serial = serial
+        for a in (0.25, 0.26, 0.27):
+            sim.step(a=a, dt_kick=0.02, dt_drift=0.02)
+        torch.cuda.synchronize()
+        ids = sim.particle_ids()
+        Xs = np.empty((3, n ** 3), dtype=np.int64)
+        Vs = np.empty((3, n ** 3), dtype=np.float32)
+        Xs[:, ids] = sim.X.cpu().numpy()
+        Vs[:, ids] = sim.V.cpu().numpy()
+        out.append((Xs, Vs))
+    assert np.array_equal(out[0][0], out[1][0])
+    assert np.array_equal(out[0][1], out[1][1])
+
+
 @pytest.mark.parametrize("gravity", ["newton", "fr"])
 def test_step_accelerations_64_lcdm(pm, gravity):
     """64^3 LCDM 2LPT particles (the float4 gradient / interpolation path of
