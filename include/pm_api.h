@@ -327,8 +327,12 @@ pm_status pm_step(pm_state* s, const pm_step_params* prm, pm_stats* st, void* st
 
 /* pm_step with HOST particle buffers: copies X_in, V_in (host, ideally pinned)
  * into s->X, s->V, runs pm_step and copies the new X, V back into X_out, V_out
- * (host).  The copies are enqueued on `stream`; the call returns after the
- * device-to-host copies have completed. */
+ * (host); same results as the copies around pm_step.  X travels on `stream`
+ * before the sort; V travels on a second, library-owned stream while the
+ * positions are sorted and the potentials solved (V enters only the force
+ * pass), and on the way back V and X travel on the two streams at once.  The
+ * call returns after all copies have completed, also on error (the host
+ * arrays are then free).  X_in may equal X_out and V_in V_out. */
 pm_status pm_step_host(pm_state* s, const pm_step_params* prm, pm_stats* st,
                        const uint32_t* X_in, const float* V_in,
                        uint32_t* X_out, float* V_out, void* stream);

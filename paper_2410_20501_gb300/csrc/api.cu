@@ -149,13 +149,14 @@ struct SideStream {
   cudaStream_t s = nullptr;
   cudaEvent_t fork = nullptr, join = nullptr;
 };
-SideStream g_side[64];
+SideStream g_side[64];   // the scalaron solve of an f(R) step
+SideStream g_copy[64];   // the velocity copies of pm_step_host
 
-pm_status side_stream(SideStream** out) {
+pm_status lib_stream(SideStream* table, SideStream** out) {
   int dev = 0;
   PM_TRY(cuda_status(cudaGetDevice(&dev)));
   if (dev < 0 || dev >= 64) return PM_EINVAL;
-  SideStream& ss = g_side[dev];
+  SideStream& ss = table[dev];
   if (!ss.s) {
     PM_TRY(cuda_status(cudaStreamCreateWithFlags(&ss.s, cudaStreamNonBlocking)));
     PM_TRY(cuda_status(cudaEventCreateWithFlags(&ss.fork, cudaEventDisableTiming)));
@@ -164,6 +165,8 @@ pm_status side_stream(SideStream** out) {
   *out = &ss;
   return PM_OK;
 }
+
+pm_status side_stream(SideStream** out) { return lib_stream(g_side, out); }
 
 // Offset (in doubles) of the side stream's share of the partials: past the
 // 2 x (152 x 8) block sums of a residual norm on the main stream, twice.
@@ -365,7 +368,11 @@ pm_status pm_interp(const float* g, const uint32_t* X, int64_t np, int n, float*
                        as_stream(stream));
 }
 
-pm_status pm_step(pm_state* st_, const pm_step_params* prm, pm_stats* stats, void* stream) {
+// The step; with V_host, the velocities are copied from that host array on
+// the copy stream cp while the positions are sorted and the potentials solved
+// (the velocities enter only the force pass, after their own permutation).
+pm_status step_impl(pm_state* st_, const pm_step_params* prm, pm_stats* stats, void* stream, const float* V_host,
+                    SideStream* cp) {
   if (!st_ || !prm) return PM_EINVAL;
   pm_state& S = *st_;
   const int n = S.n;
@@ -395,9 +402,15 @@ pm_status pm_step(pm_state* st_, const pm_step_params* prm, pm_stats* stats, voi
   pm_stats local;
   memset(&local, 0, sizeof(local));
 
+  if (V_host) {
+    PM_TRY(cuda_status(cudaEventRecord(cp->fork, s)));
+    PM_TRY(cuda_status(cudaStreamWaitEvent(cp->s, cp->fork, 0)));
+    PM_TRY(cuda_status(cudaMemcpyAsync(S.V, V_host, (size_t)np * 12, cudaMemcpyHostToDevice, cp->s)));
+    PM_TRY(cuda_status(cudaEventRecord(cp->join, cp->s)));
+  }
   uint32_t* perm;
   PM_TRY(sort_cells(S.X, np, n, w, s, w.cellstart, &perm));
-  PM_TRY(permute_particles(perm, np, S.X, S.V, S.id, w.Xs, w.Vs, w.ids, s));
+  PM_TRY(permute_particles(perm, np, S.X, V_host ? nullptr : S.V, S.id, w.Xs, V_host ? nullptr : w.Vs, w.ids, s));
   PM_TRY(deposit_sorted(w.Xs, np, w.cellstart, n, w.rho, w.partials, w.scalars, s));
 
   double fbar = 0.0, kappa = 0.0, c2 = 0.0;
@@ -443,6 +456,10 @@ pm_status pm_step(pm_state* st_, const pm_step_params* prm, pm_stats* stats, voi
   if (side) PM_TRY(cuda_status(cudaStreamWaitEvent(s, side->join, 0)));   // the scalaron is done
   if (mg_status != PM_OK && mg_status != PM_ENOCONV) return mg_status;
   if (mg_status != PM_OK) solve_status = mg_status;
+  if (V_host) {   // the velocities have arrived: into cell order
+    PM_TRY(cuda_status(cudaStreamWaitEvent(s, cp->join, 0)));
+    PM_TRY(permute_particles(perm, np, nullptr, S.V, nullptr, nullptr, w.Vs, nullptr, s));
+  }
   const float alpha = (float)(-0.5 * c2 * fbar);
   const float* eps_force = prm->gravity == PM_GRAVITY_FR ? S.eps : nullptr;
   const int nh = frp.nhs == 2 ? 2 : 1;
@@ -470,17 +487,33 @@ pm_status pm_step(pm_state* st_, const pm_step_params* prm, pm_stats* stats, voi
   return solve_status;
 }
 
+pm_status pm_step(pm_state* st_, const pm_step_params* prm, pm_stats* stats, void* stream) {
+  return step_impl(st_, prm, stats, stream, nullptr, nullptr);
+}
+
+// Positions in on the caller's stream, velocities in on the copy stream
+// beside the sort and the solvers; after the force pass, positions out on the
+// caller's stream and velocities out on the copy stream (two copy engines).
 pm_status pm_step_host(pm_state* st_, const pm_step_params* prm, pm_stats* stats, const uint32_t* X_in,
                        const float* V_in, uint32_t* X_out, float* V_out, void* stream) {
   if (!st_ || !X_in || !V_in || !X_out || !V_out) return PM_EINVAL;
   cudaStream_t s = as_stream(stream);
   const size_t bytes = (size_t)st_->np * 12;
+  SideStream* cp = nullptr;
+  PM_TRY(lib_stream(g_copy, &cp));
   PM_TRY(cuda_status(cudaMemcpyAsync(st_->X, X_in, bytes, cudaMemcpyHostToDevice, s)));
-  PM_TRY(cuda_status(cudaMemcpyAsync(st_->V, V_in, bytes, cudaMemcpyHostToDevice, s)));
-  pm_status r = pm_step(st_, prm, stats, stream);
-  if (r != PM_OK && r != PM_ENOCONV) return r;
+  pm_status r = step_impl(st_, prm, stats, stream, V_in, cp);
+  if (r != PM_OK && r != PM_ENOCONV) {   // nothing may still read the caller's host arrays
+    cudaStreamSynchronize(cp->s);
+    cudaStreamSynchronize(s);
+    return r;
+  }
+  PM_TRY(cuda_status(cudaEventRecord(cp->fork, s)));
+  PM_TRY(cuda_status(cudaStreamWaitEvent(cp->s, cp->fork, 0)));
+  PM_TRY(cuda_status(cudaMemcpyAsync(V_out, st_->V, bytes, cudaMemcpyDeviceToHost, cp->s)));
   PM_TRY(cuda_status(cudaMemcpyAsync(X_out, st_->X, bytes, cudaMemcpyDeviceToHost, s)));
-  PM_TRY(cuda_status(cudaMemcpyAsync(V_out, st_->V, bytes, cudaMemcpyDeviceToHost, s)));
+  PM_TRY(cuda_status(cudaEventRecord(cp->join, cp->s)));
+  PM_TRY(cuda_status(cudaStreamWaitEvent(s, cp->join, 0)));
   PM_TRY(cuda_status(cudaStreamSynchronize(s)));
   return r;
 }

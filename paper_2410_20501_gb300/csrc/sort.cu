@@ -302,8 +302,10 @@ __global__ void k_permute(const uint32_t* __restrict__ perm, int64_t np,
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < np;
        j += (int64_t)gridDim.x * blockDim.x) {
     uint32_t p = __ldg(perm + j);
+    if (X) {
 #pragma unroll
-    for (int d = 0; d < 3; ++d) Xs[d * np + j] = __ldg(X + d * np + p);
+      for (int d = 0; d < 3; ++d) Xs[d * np + j] = __ldg(X + d * np + p);
+    }
     if (V) {
 #pragma unroll
       for (int d = 0; d < 3; ++d) Vs[d * np + j] = __ldg(V + d * np + p);
@@ -355,7 +357,7 @@ pm_status permute_particles(const uint32_t* perm, int64_t np, const uint32_t* X,
                             const uint32_t* id, uint32_t* Xs, float* Vs, uint32_t* ids,
                             cudaStream_t s) {
   if (np == 0) return PM_OK;
-  PM_LAUNCH(K_PERMUTE, (28.0 + (V ? 24.0 : 0.0) + (id ? 8.0 : 0.0)) * np, k_permute, grid_for(np, 256), 256, 0, s, perm, np, X, V, id, Xs, Vs, ids);
+  PM_LAUNCH(K_PERMUTE, (4.0 + (X ? 24.0 : 0.0) + (V ? 24.0 : 0.0) + (id ? 8.0 : 0.0)) * np, k_permute, grid_for(np, 256), 256, 0, s, perm, np, X, V, id, Xs, Vs, ids);
   return launch_status();
 }
 

@@ -426,3 +426,30 @@ def test_step_accelerations_fr_n2(pm):
     prm = step.PMParams(n=n, Om=0.3, OL=0.7, boxsize=float(n), gravity="fr", fR0=-1e-5, fr_n=2)
     ref, _, _ = step.accelerations(mesh.positions_from_fixed_point(X), 0.7, prm)
     assert rel_l2(acc.T, ref) < 1e-5
+
+
+@pytest.mark.parametrize("gravity", ["newton", "fr"])
+def test_step_host_equals_device_step(pm, gravity):
+    """pm_step_host (positions in before the sort, velocities in on a second
+    stream beside the sort and the solvers, both out on two streams) gives
+    bitwise the particles of pm_step on device-resident arrays, over three
+    steps, with in-place host buffers."""
+    import torch
+    n = 64
+    X, V = inputs.lpt_ics(n, float(n), 0.3, 0.7, 0.25, seed=23, order=2)
+    mk = lambda: pm.Simulation(X, V, n, Om=0.3, OL=0.7, boxsize=float(n), gravity=gravity,
+                               mg=pm.default_mg(tol=1e-7), fr=pm.default_fr(tol=1e-3, max_cycles=4))
+    steps = [(0.25, 0.02, 0.02), (0.26, 0.02, 0.02), (0.27, 0.02, 0.02)]
+    dev = mk()
+    for a, k, d in steps:
+        dev.step(a=a, dt_kick=k, dt_drift=d)
+    torch.cuda.synchronize()
+    host = mk()
+    Xh = torch.empty((3, n ** 3), dtype=torch.int32).pin_memory()
+    Vh = torch.empty((3, n ** 3), dtype=torch.float32).pin_memory()
+    Xh.copy_(host.X)
+    Vh.copy_(host.V)
+    for a, k, d in steps:
+        host.step_host(a, k, d, Xh, Vh, Xh, Vh)
+    assert torch.equal(Xh, dev.X.cpu())
+    assert torch.equal(Vh, dev.V.cpu())
