@@ -40,7 +40,8 @@ __device__ __forceinline__ int64_t idx3(int i, int j, int k, int log2n) {
 
 // Root eps > -1 of g(e) = e^3 + 3e^2 + c1 e + c0 (g(-1) = q < 0, g convex on
 // e > -1, so the root is unique).  Two plain Newton steps from the current
-// value usually reach float32 resolution; otherwise Newton continues inside a
+// value usually reach float32 resolution (one suffices when the value moved
+// little since the last sweep); otherwise Newton continues inside a
 // shrinking bracket [lo, hi]; when a step leaves the bracket (or g' <= 0) the
 // upper end is set from the bound u* <= sqrt(max(-p, 0)) + (-q)^(1/3),
 // p = c1 - 3, and the step falls back to bisection.  Stops when g is at its
@@ -81,14 +82,19 @@ __device__ __forceinline__ float fr_root(float e, float c1, float c0, float q) {
   float lo = -1.0f, hi = __int_as_float(0x7f800000);  // +inf until needed
   if (!(e > lo)) e = 0.0f;
   {
-    // fast path: two plain Newton steps from the current value; accepted when
-    // the remaining error is at float32 resolution and the root is admissible
+    // fast path: one or two plain Newton steps from the current value;
+    // accepted when the remaining error is at float32 resolution and the root
+    // is admissible.  Newton's error after a step of length d is about K d^2,
+    // K = g''/(2 g')
     const float g0 = P::g(e, c1, c0), gp0 = P::gp(e, c1);
     const float e1 = e - __fdividef(g0, gp0);
+    {
+      const float d0 = e1 - e;
+      if (gp0 > 0.0f && e1 > lo && d0 * d0 * P::half_gpp(e) <= (1e-7f * fabsf(e1) + 1e-20f) * gp0) return e1;
+    }
     const float g1 = P::g(e1, c1, c0), gp1 = P::gp(e1, c1);
     const float e2 = e1 - __fdividef(g1, gp1);
-    // Newton's error after the second step is about K d^2, d = e2 - e1,
-    // K = g''/(2 g'): accept when that is below float32 resolution of e2
+    // the same test for the second step, d = e2 - e1
     const float d = e2 - e1;
     if (gp0 > 0.0f && gp1 > 0.0f && e2 > lo && d * d * P::half_gpp(e1) <= (1e-7f * fabsf(e2) + 1e-20f) * gp1)
       return e2;
