@@ -393,7 +393,7 @@ pm_status stream_attributes_nh() {
     PM_TRY(cuda_status(cudaFuncSetAttribute(k_rb_stream<1, FRUpdate<NH>>,
                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
                                             (int)StreamGeom<1>::smem_bytes)));
-    PM_TRY(cuda_status(cudaFuncSetAttribute((k_rb_fused<FRUpdate<NH>, 2, 1>),
+    PM_TRY(cuda_status(cudaFuncSetAttribute((k_rb_fused<FRUpdate<NH>, 2, 2>),
                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFusedSmem)));
     done = true;
   }
@@ -432,7 +432,7 @@ pm_status fr_smooth_nh(FR& f, int l, int count) {
     const unsigned grid = (unsigned)((c.n / kFusedT) * (c.n / kFusedT) * (c.n / chunk));
     const FRUpdate upd{c.beta, c.kappa, c.q};
     for (int it = 0; it < count; ++it) {
-      PM_LAUNCH(l == 0 ? K_FR_SMOOTH0 : K_FR_SMOOTH, 12.0 * N, (k_rb_fused<FRUpdate, 2, 1>), grid, kFusedThreads, kFusedSmem,
+      PM_LAUNCH(l == 0 ? K_FR_SMOOTH0 : K_FR_SMOOTH, 12.0 * N, (k_rb_fused<FRUpdate, 2, 2>), grid, kFusedThreads, kFusedSmem,
                 f.s, f.e[l], f.alt[l], f.b[l], c.log2n, chunk, 0, 0, upd);
       float* t = f.e[l];
       f.e[l] = f.alt[l];
