@@ -141,16 +141,27 @@ def kernel_digest(relpath, kernel):
     return hashlib.sha256(src[start:end].encode()).hexdigest()[:16]
 
 
+def files_digest(relpaths):
+    """Short sha256 of the concatenated text of source files."""
+    import hashlib
+    h = hashlib.sha256()
+    for r in relpaths:
+        h.update(open(os.path.join(ROOT, r), "rb").read())
+    return h.hexdigest()[:16]
+
+
 def load_ncu_traffic():
     """Per timing class: DRAM bytes per launch from an ncu capture, kept only
-    while the captured kernel's source is unchanged (same digest)."""
+    while the captured kernel's source is unchanged (same digest: of the
+    kernel's definition text, or of every file its launch depends on)."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     if not os.path.exists(path):
         return {}
     out = {}
     for cls, e in json.load(open(path)).items():
         try:
-            if kernel_digest(e["source"], e["kernel"]) == e["digest"]:
+            d = files_digest(e["sources"]) if "sources" in e else kernel_digest(e["source"], e["kernel"])
+            if d == e["digest"]:
                 out[cls] = e
         except OSError:
             pass
