@@ -452,6 +452,26 @@ pm_status pm_timing_enable(int on);
  * names[i] are static strings. */
 int pm_timing_collect(const char** names, double* ms, int64_t* launches, double* bytes, int cap);
 
+/* ------------------------------------------------------------ autotuning --
+ * Batched launches (pm_step_batch) tune how they tile their work, online: for
+ * each launch site and shape (n, B) the candidate values of one parameter
+ * (the x chunk of the force pass and of the fused multigrid sweep; colour
+ * passes or fused sweeps on 64^3 levels) take turns on successive real
+ * launches, timed with CUDA events on the launch stream and read back
+ * without synchronising; after two timings each the fastest is kept for the
+ * rest of the process.  Every candidate computes bitwise the same result, so
+ * tuning never changes a result, only when it is ready.  Nothing is timed
+ * while a stream is captured into a CUDA graph.  Single-box launches use
+ * fixed tilings. */
+/* mode 0: fixed default tilings; 1 (the default): tune; 2: forget every
+ * choice and timing, then tune.  PM_EINVAL for another mode. */
+pm_status pm_autotune(int mode);
+/* Reports the tuned sites, five ints each: site (0 force-pass chunk, 1 fused
+ * multigrid sweep chunk, 2 multigrid smoother form: 0 colour passes, 1 fused),
+ * n, B, the chosen value (-1 while undecided) and the timings read so far.
+ * out (host, 5 * cap ints) may be NULL; returns the number of sites. */
+int pm_autotune_report(int* out, int cap);
+
 #ifdef __cplusplus
 }
 #endif

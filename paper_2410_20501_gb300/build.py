@@ -13,7 +13,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 OUT = os.path.join(PKG, "_lib")
 LIB = os.path.join(OUT, "libpmgb.so")
-SOURCES = ["sort.cu", "deposit.cu", "mg.cu", "fr.cu", "interp.cu", "api.cu", "noalloc.cu", "adjoint.cu", "fft.cu"]
+SOURCES = ["sort.cu", "deposit.cu", "mg.cu", "fr.cu", "interp.cu", "api.cu", "noalloc.cu", "adjoint.cu", "fft.cu", "tune.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I", os.path.join(ROOT, "include"), "-I", CSRC]

@@ -570,6 +570,11 @@ pm_status launch_force_interp(const float* phi, const float* eps, float alpha, i
   const int tiles = (n / IT_Y) * (n / IT_Z);
   int chunk = n;
   while (chunk > 16 && (int64_t)tiles * (n / chunk) * bt.B < 16 * 152) chunk >>= 1;
+  if (bt.B > 1) {   // batches: the x chunk is tuned (each particle's force is chunk-independent)
+    int cand[3], nc = 0;
+    for (int c = 16; c <= 64 && c <= n; c *= 2) cand[nc++] = c;
+    chunk = tune_begin(TUNE_FORCE_CHUNK, n, bt.B, cand, nc, chunk, s);
+  }
   const int nitems = tiles * (n / chunk);
   const dim3 grid((unsigned)nitems, 1, (unsigned)bt.B);
   *nblocks = (int64_t)grid.x * grid.z;
@@ -586,6 +591,7 @@ pm_status launch_force_interp(const float* phi, const float* eps, float alpha, i
     if (blockmax) PM_FI(false, true); else PM_FI(false, false);
   }
 #undef PM_FI
+  if (bt.B > 1) tune_end(s);
   return launch_status();
 }
 

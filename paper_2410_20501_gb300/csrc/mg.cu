@@ -459,31 +459,50 @@ pm_status smooth(MG& g, int l, int count, const float* w, bool zero, float scale
     }
     return PM_OK;
   }
-  if (g.p->smoother == 2 && fused_ok(n, g.B) && g.alt[l] && fused_aligned(g.u[l], g.alt[l], g.f[l].p)) {
-    const int chunk = fused_chunk(n);
-    const unsigned grid = (unsigned)((n / kFusedT) * (n / kFusedT) * (n / chunk));
+  // fused sweeps (one pass per sweep) or colour passes (two per sweep), bitwise
+  // the same result; on 64^3 levels of a batch the form is tuned, and the
+  // fused sweep's x chunk is tuned on every batched level
+  const bool fused_valid = g.p->smoother == 2 && n >= 64 && g.alt[l] && fused_aligned(g.u[l], g.alt[l], g.f[l].p);
+  bool fused = fused_valid && fused_ok(n, g.B);
+  const bool tune_form = fused_valid && g.B > 1 && n < 128;
+  if (tune_form) {
+    static const int forms[2] = {0, 1};
+    fused = tune_begin(TUNE_MG_SMOOTHER, n, g.B, forms, 2, fused ? 1 : 0, g.s) == 1;
+  }
+  const bool form_timed = tune_form && tune_active();
+  if (fused) {
     for (; done < count; ++done) {
+      int chunk = fused_chunk(n);
+      const bool tune_chunk = g.B > 1 && !form_timed;   // one timing at a time
+      if (tune_chunk) {
+        int cand[3], nc = 0;
+        for (int c = 16; c <= 64 && c <= n; c *= 2) cand[nc++] = c;
+        chunk = tune_begin(TUNE_MG_FUSED_CHUNK, n, g.B, cand, nc, chunk, g.s);
+      }
+      const unsigned grid = (unsigned)((n / kFusedT) * (n / kFusedT) * (n / chunk));
       PoissonUpdate upd{h2, {w[done], 1.0f}, done == 0 ? scale : 1.0f, done == 0 ? sbox : nullptr};
       const int z = (done == 0 && zero) ? 1 : 0;
       PM_LAUNCH(l == 0 ? K_MG_SMOOTH0 : K_MG_SMOOTH, (z ? 8.0 : 12.0) * N * g.B, (k_rb_fused<PoissonUpdate, 2, 2>),
                 g.grid(grid), kFusedThreads, kFusedSmem, g.s, g.u[l], g.alt[l], g.f[l], log2n, chunk, z,
                 done == 0 ? 1 : 0, upd);
+      if (tune_chunk) tune_end(g.s);
       float* t = g.u[l];
       g.u[l] = g.alt[l];
       g.alt[l] = t;
     }
-    return PM_OK;
+  } else {
+    const unsigned grid = grid_for(N / 2, 256);
+    for (; done < count; ++done) {
+      PoissonUpdate upd{h2, {w[done], 1.0f}, done == 0 ? scale : 1.0f, done == 0 ? sbox : nullptr};
+      const int z = (done == 0 && zero) ? 1 : 0;
+      const int first = done == 0 ? 1 : 0;
+      PM_LAUNCH(l == 0 ? K_MG_SMOOTH0 : K_MG_SMOOTH, (z ? 4.0 : 6.0) * N * g.B, k_rb_sweep, g.grid(grid), 256, 0,
+                g.s, g.u[l], g.f[l], log2n, 0, upd, first, first, z);
+      PM_LAUNCH(l == 0 ? K_MG_SMOOTH0 : K_MG_SMOOTH, (z ? 4.0 : 6.0) * N * g.B, k_rb_sweep, g.grid(grid), 256, 0,
+                g.s, g.u[l], g.f[l], log2n, 1, upd, 0, first, z);
+    }
   }
-  const unsigned grid = grid_for(N / 2, 256);
-  for (; done < count; ++done) {
-    PoissonUpdate upd{h2, {w[done], 1.0f}, done == 0 ? scale : 1.0f, done == 0 ? sbox : nullptr};
-    const int z = (done == 0 && zero) ? 1 : 0;
-    const int first = done == 0 ? 1 : 0;
-    PM_LAUNCH(l == 0 ? K_MG_SMOOTH0 : K_MG_SMOOTH, (z ? 4.0 : 6.0) * N * g.B, k_rb_sweep, g.grid(grid), 256, 0, g.s,
-              g.u[l], g.f[l], log2n, 0, upd, first, first, z);
-    PM_LAUNCH(l == 0 ? K_MG_SMOOTH0 : K_MG_SMOOTH, (z ? 4.0 : 6.0) * N * g.B, k_rb_sweep, g.grid(grid), 256, 0, g.s,
-              g.u[l], g.f[l], log2n, 1, upd, 0, first, z);
-  }
+  if (form_timed) tune_end(g.s);
   return PM_OK;
 }
 

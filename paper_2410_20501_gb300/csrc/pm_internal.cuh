@@ -20,6 +20,15 @@ enum KernelClass {
 
 extern const char* const kKernelClassNames[K_NCLASS];
 
+// Online autotuner of batched launch tiling (tune.cu).  A site calls
+// tune_begin before its launch(es) with candidate values that compute bitwise
+// the same result, uses the value returned, and calls tune_end after them on
+// the same stream; tune_active() says whether this call is being timed.
+enum TuneSite { TUNE_FORCE_CHUNK, TUNE_MG_FUSED_CHUNK, TUNE_MG_SMOOTHER };
+int tune_begin(int site, int n, int B, const int* cand, int ncand, int dflt, cudaStream_t s);
+void tune_end(cudaStream_t s);
+bool tune_active();
+
 void launch_begin(int cls, double bytes, cudaStream_t s);
 void launch_end(int cls, cudaStream_t s);
 

@@ -148,6 +148,8 @@ _SIGS = {
     "pm_timing_collect": (ctypes.c_int, [ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_double),
                                          ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double),
                                          ctypes.c_int]),
+    "pm_autotune": (ctypes.c_int, [ctypes.c_int]),
+    "pm_autotune_report": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int), ctypes.c_int]),
 }
 
 
@@ -394,6 +396,24 @@ def launch_count():
 
 def timing_enable(on=True):
     _check(lib().pm_timing_enable(1 if on else 0), "pm_timing_enable")
+
+
+TUNE_SITES = ("force_chunk", "mg_fused_chunk", "mg_smoother")
+
+
+def autotune(mode):
+    """pm_autotune: 0 fixed tilings, 1 tune batched launches (default), 2 forget and retune."""
+    _check(lib().pm_autotune(int(mode)), "pm_autotune")
+
+
+def autotune_report():
+    """The tuned launch sites: [{site, n, B, chosen (None while undecided), samples}]."""
+    cap = 64
+    out = (ctypes.c_int * (5 * cap))()
+    m = min(lib().pm_autotune_report(out, cap), cap)
+    return [{"site": TUNE_SITES[out[5 * i]], "n": out[5 * i + 1], "B": out[5 * i + 2],
+             "chosen": None if out[5 * i + 3] < 0 else out[5 * i + 3], "samples": out[5 * i + 4]}
+            for i in range(m)]
 
 
 def timing_collect():

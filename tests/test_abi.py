@@ -139,3 +139,11 @@ def test_adaptive_timestep_criteria(L):
     assert abs(dt - 0.5 / n / 1e4) < 1e-18                                    # velocity
     dt, a1 = pm.next_timestep(a, 1.0, 0.0, n, 0.0, 0.0, courant=1.0, da_max=0.5, a_end=0.06)
     assert a1 == 0.06 and abs(dt - 2 * (a ** -0.5 - 0.06 ** -0.5)) < 1e-12 * dt   # clipped at a_end
+
+
+def test_autotune_mode_is_checked_on_the_host(L):
+    """pm_autotune rejects unknown modes before touching any device state; the
+    report of a tuner that has seen no batched launch is empty."""
+    assert L.pm_autotune(3) == 1 and L.pm_autotune(-1) == 1
+    assert L.pm_autotune_report(None, 0) == 0
+    assert L.pm_autotune(1) == 0

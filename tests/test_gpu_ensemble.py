@@ -93,3 +93,26 @@ def test_batch_of_eight_64cubed_is_bitwise_the_boxes_run_alone(pm):
     for b in (0, 5):
         Xs, Vs = run(pm, w, [b], 3)
         assert np.array_equal(Xb[b], Xs[0]) and np.array_equal(Vb[b], Vs[0]), b
+
+
+def test_autotuned_tilings_are_bitwise_the_fixed_ones(pm):
+    """The online autotuner tries each candidate tiling of the batched force
+    pass (x chunk) and of the 64^3 smoothing (colour passes or fused sweeps,
+    and the fused sweep's x chunk) on real steps and keeps the fastest: the
+    particles are bitwise those of the fixed default tilings, and after ten
+    steps every site it opened for this shape has chosen."""
+    w = inputs.ensemble_workload(n=64, B=4, boxsize=128.0, steps=10)
+    try:
+        pm.autotune(0)
+        Xf, Vf = run(pm, w, list(range(4)), 10)
+        pm.autotune(2)
+        Xt, Vt = run(pm, w, list(range(4)), 10)
+        rep = [r for r in pm.autotune_report() if r["n"] == 64 and r["B"] == 4]
+    finally:
+        pm.autotune(1)
+    assert np.array_equal(Xf, Xt) and np.array_equal(Vf, Vt)
+    sites = {r["site"]: r for r in rep}
+    assert "force_chunk" in sites and "mg_smoother" in sites, rep
+    assert all(r["chosen"] is not None and r["samples"] >= 4 for r in rep), rep
+    assert sites["force_chunk"]["chosen"] in (16, 32, 64)
+    assert sites["mg_smoother"]["chosen"] in (0, 1)
