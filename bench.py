@@ -334,8 +334,11 @@ def run_ensemble(n=64, B=64, steps=50):
         ms = t0.elapsed_time(t1) / (last - 2)
         out[mode] = {"ms_per_step": ms, "value": B * n ** 3 / (ms / 1e3), "steps_timed": last - 2}
         del ens
+    tuned = [{k: r[k] for k in ("site", "n", "chosen", "samples")} for r in pm.autotune_report() if r["B"] == B]
     return {"workload": f"{B} boxes x {n}^3 particles/grid, L=128 Mpc/h, Om~U[0.25,0.35], s8~U[0.7,0.9], "
-                        "2LPT z=30, 50 steps in ln a", "unit": "particle-steps/s", **out}
+                        "2LPT z=30, 50 steps in ln a", "unit": "particle-steps/s", **out,
+            "autotune": {"what": "tilings the online tuner chose for this batch (eager steps; the graph "
+                                 "replays the choices)", "sites": tuned}}
 
 
 def run_lpt(n, reps=3):
