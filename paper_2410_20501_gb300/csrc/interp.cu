@@ -267,7 +267,8 @@ __device__ __forceinline__ void column_runs(const uint32_t* __restrict__ cellsta
 // Inverse TSC (+ kick and drift) of the particles of one plane of a column,
 // force planes x-1, x, x+1 at S[0..2] (each [3][IE_Y][IE_Z]).
 template <bool MAXES>
-__device__ __forceinline__ void column_particles(const float* const S[3], const uint32_t* st, const uint32_t* pre,
+__device__ __forceinline__ void column_particles(const float2* const S2[3], const float* const Sz[3],
+                                                 const uint32_t* st, const uint32_t* pre,
                                                  int y0, int z0, const uint32_t* __restrict__ Xs,
                                                  const float* __restrict__ Vs, const uint32_t* __restrict__ ids_in,
                                                  int64_t np, int log2n, float* __restrict__ acc,
@@ -301,13 +302,15 @@ __device__ __forceinline__ void column_particles(const float* const S[3], const 
 #pragma unroll
       for (int oy = 0; oy < 3; ++oy) {
         const float wxy = wx[ox] * wy[oy];
-        const float* r = S[ox] + c + (oy - 1) * IE_Z;
+        const float2* r2 = S2[ox] + c + (oy - 1) * IE_Z;
+        const float* rz = Sz[ox] + c + (oy - 1) * IE_Z;
 #pragma unroll
         for (int oz = 0; oz < 3; ++oz) {
           const float w = wxy * wz[oz];
-          ax = fmaf(w, r[oz - 1], ax);
-          ay = fmaf(w, r[I_PL + oz - 1], ay);
-          az = fmaf(w, r[2 * I_PL + oz - 1], az);
+          const float2 fxy = r2[oz - 1];
+          ax = fmaf(w, fxy.x, ax);
+          ay = fmaf(w, fxy.y, ay);
+          az = fmaf(w, rz[oz - 1], az);
         }
       }
     }
@@ -373,8 +376,9 @@ __global__ void __launch_bounds__(I_THREADS) k_force_interp_stream(
   constexpr int R = Stencil<ORDER>::R, H = R + 1, PEY = IT_Y + 2 * H, PEZ = IT_Z + 2 * H, PPL = PEY * PEZ,
                 PS = 2 * R + 2, PL_T = (PPL + I_THREADS - 1) / I_THREADS;
   extern __shared__ float fsm[];
-  float* Gs = fsm;                   // [4][3][IE_Y][IE_Z]
-  float* Ps = Gs + 4 * 3 * I_PL;     // [PS][PEY][PEZ]
+  float2* Gxy = reinterpret_cast<float2*>(fsm);   // [4][IE_Y][IE_Z] (g_x, g_y)
+  float* Gz = fsm + 4 * 2 * I_PL;                  // [4][IE_Y][IE_Z] g_z
+  float* Ps = fsm + 4 * 3 * I_PL;                  // [PS][PEY][PEZ]
   __shared__ uint32_t s_start[2][IT_Y], s_pre[2][IT_Y + 1];
   const int n = 1 << log2n, m = n - 1;
   const int64_t N = (int64_t)1 << (3 * log2n);
@@ -431,7 +435,8 @@ __global__ void __launch_bounds__(I_THREADS) k_force_interp_stream(
       __syncthreads();
       const int qg = u - R;
       if (qg >= x0 - 1 && qg <= x1) {
-        float* G = Gs + (qg & 3) * 3 * I_PL;
+        float2* G2 = Gxy + (qg & 3) * I_PL;
+        float* G1 = Gz + (qg & 3) * I_PL;
         const float* Pc = Ps + (((qg % PS) + PS) % PS) * PPL;
         for (int e = tid; e < I_PL; e += I_THREADS) {
           const int ly = e / IE_Z, lz = e - ly * IE_Z;
@@ -446,19 +451,22 @@ __global__ void __launch_bounds__(I_THREADS) k_force_interp_stream(
             gy = fmaf(w, Pc[c + q * PEZ] - Pc[c - q * PEZ], gy);
             gz = fmaf(w, Pc[c + q] - Pc[c - q], gz);
           }
-          G[e] = -gx * inv_h;
-          G[I_PL + e] = -gy * inv_h;
-          G[2 * I_PL + e] = -gz * inv_h;
+          G2[e] = make_float2(-gx * inv_h, -gy * inv_h);
+          G1[e] = -gz * inv_h;
         }
       }
       const int t = qg - 2;   // particle plane of this step
       if (t + 1 >= x0 && t + 1 < x1)
         column_runs(cellstart, t + 1, y0, z0, log2n, s_start[(t + 1) & 1], s_pre[(t + 1) & 1]);
       if (t >= x0 && t < x1) {
-        const float* S[3];
+        const float2* S2[3];
+        const float* Sz[3];
 #pragma unroll
-        for (int ox = 0; ox < 3; ++ox) S[ox] = Gs + ((t + ox - 1) & 3) * 3 * I_PL;
-        column_particles<MAXES>(S, s_start[t & 1], s_pre[t & 1], y0, z0, Xs, Vs, ids_in, np, log2n, acc, Xo, Vo,
+        for (int ox = 0; ox < 3; ++ox) {
+          S2[ox] = Gxy + ((t + ox - 1) & 3) * I_PL;
+          Sz[ox] = Gz + ((t + ox - 1) & 3) * I_PL;
+        }
+        column_particles<MAXES>(S2, Sz, s_start[t & 1], s_pre[t & 1], y0, z0, Xs, Vs, ids_in, np, log2n, acc, Xo, Vo,
                                 ids_out, dt_kick, drift_scale, mode, amax, vmax);
       }
     }
