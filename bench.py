@@ -141,26 +141,34 @@ def kernel_digest(relpath, kernel):
     return hashlib.sha256(src[start:end].encode()).hexdigest()[:16]
 
 
-def files_digest(relpaths):
-    """Short sha256 of the concatenated text of source files."""
+def parts_digest(parts):
+    """Short sha256 of source excerpts: for each [file, begin, end], the text
+    from the first occurrence of ``begin`` to the next ``end`` after it (the
+    kernel, its update functor, the instantiation that is launched).  None if
+    an excerpt is missing."""
     import hashlib
     h = hashlib.sha256()
-    for r in relpaths:
-        h.update(open(os.path.join(ROOT, r), "rb").read())
+    for rel, begin, end in parts:
+        src = open(os.path.join(ROOT, rel)).read()
+        i = src.find(begin)
+        j = src.find(end, i + len(begin)) if i >= 0 else -1
+        if i < 0 or j < 0:
+            return None
+        h.update(src[i:j + len(end)].encode())
     return h.hexdigest()[:16]
 
 
 def load_ncu_traffic():
     """Per timing class: DRAM bytes per launch from an ncu capture, kept only
     while the captured kernel's source is unchanged (same digest: of the
-    kernel's definition text, or of every file its launch depends on)."""
+    kernel's definition text, or of the source excerpts its launch depends on)."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     if not os.path.exists(path):
         return {}
     out = {}
     for cls, e in json.load(open(path)).items():
         try:
-            d = files_digest(e["sources"]) if "sources" in e else kernel_digest(e["source"], e["kernel"])
+            d = parts_digest(e["parts"]) if "parts" in e else kernel_digest(e["source"], e["kernel"])
             if d == e["digest"]:
                 out[cls] = e
         except OSError:
