@@ -21,7 +21,7 @@ namespace {
 constexpr int kMaxCand = 4, kSamples = 2, kSlots = 8, kEntries = 64;
 
 struct Entry {
-  int site = -1, n = 0, B = 0;
+  int site = -1, n = 0, B = 0, dev = 0;   // key (events belong to device dev)
   int ncand = 0, cand[kMaxCand] = {};
   int chosen = -1;                    // index into cand once decided
   float best[kMaxCand] = {};          // minimum sample per candidate
@@ -83,14 +83,15 @@ void harvest(Entry& e) {
   }
 }
 
-Entry* find(int site, int n, int B, const int* cand, int ncand) {
+Entry* find(int site, int n, int B, int dev, const int* cand, int ncand) {
   for (int i = 0; i < g_used; ++i)
-    if (g_tab[i].site == site && g_tab[i].n == n && g_tab[i].B == B) return &g_tab[i];
+    if (g_tab[i].site == site && g_tab[i].n == n && g_tab[i].B == B && g_tab[i].dev == dev) return &g_tab[i];
   if (g_used == kEntries) return nullptr;
   Entry& e = g_tab[g_used++];
   e.site = site;
   e.n = n;
   e.B = B;
+  e.dev = dev;
   e.ncand = ncand;
   for (int c = 0; c < ncand; ++c) e.cand[c] = cand[c];
   for (int k = 0; k < kSlots; ++k) e.slot_cand[k] = -1;
@@ -104,7 +105,12 @@ int tune_begin(int site, int n, int B, const int* cand, int ncand, int dflt, cud
   if (ncand <= 1 || ncand > kMaxCand) return ncand == 1 ? cand[0] : dflt;
   std::lock_guard<std::mutex> lock(g_mu);
   if (g_mode == 0) return dflt;
-  Entry* e = find(site, n, B, cand, ncand);
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return dflt;
+  }
+  Entry* e = find(site, n, B, dev, cand, ncand);
   if (!e) return dflt;
   if (e->chosen >= 0) return e->cand[e->chosen];
   const bool cap = capturing(s);
@@ -184,7 +190,10 @@ pm_status pm_autotune(int mode) {
 
 int pm_autotune_report(int* out, int cap) {
   std::lock_guard<std::mutex> lock(g_mu);
-  for (int i = 0; i < g_used; ++i) harvest(g_tab[i]);
+  int dev = -1;
+  if (g_used > 0 && cudaGetDevice(&dev) != cudaSuccess) cudaGetLastError();
+  for (int i = 0; i < g_used; ++i)
+    if (g_tab[i].dev == dev) harvest(g_tab[i]);
   const int m = g_used < cap ? g_used : cap;
   for (int i = 0; out && i < m; ++i) {
     const Entry& e = g_tab[i];
