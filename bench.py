@@ -31,6 +31,7 @@ N_GRID = 512
 BOX = 512.0
 OM, OL = 0.3, 0.7
 FR0 = -1e-5
+MU0 = -0.2      # parametrised-gravity amplitude of the variant line (mu(a) = 1 + mu0 Omega_L(a)/Omega_L0)
 Z_INI = 30.0
 SEED = 5
 N_STEPS_RUN = 100
@@ -394,10 +395,12 @@ def run_gpu(args):
     fr = pm.default_fr(cycle=1, cycles=1)
     W, K = args.warmup, args.steps
     results = {}
-    for variant in (("fr",) if args.lean else ("fr", "newton", "newton_fft7")):
-        gravity = "newton" if variant.startswith("newton") else "fr"
-        sim = pm.Simulation(X, V, n, OM, OL, BOX, gravity=gravity, fR0=FR0, mg=mg, fr=fr,
-                            poisson=pm.PM_POISSON_FFT7 if variant == "newton_fft7" else pm.PM_POISSON_MG)
+    for variant in (("fr",) if args.lean else ("fr", "newton", "newton_fft7", "fr_n2", "mu")):
+        gravity = {"fr": "fr", "fr_n2": "fr", "mu": "mu"}.get(variant, "newton")
+        sim = pm.Simulation(X, V, n, OM, OL, BOX, gravity=gravity, fR0=FR0, mg=mg,
+                            fr=pm.default_fr(cycle=1, cycles=1, nhs=2) if variant == "fr_n2" else fr,
+                            poisson=pm.PM_POISSON_FFT7 if variant == "newton_fft7" else pm.PM_POISSON_MG,
+                            mu0=MU0 if variant == "mu" else 0.0)
         timed_steps(sim, coeffs, 0, W)
         barrier(world)
         torch.cuda.synchronize()
@@ -408,7 +411,7 @@ def run_gpu(args):
         ms = max_over_ranks(ms, world, "cuda")
         results[variant] = {"ms": ms, "stats": stats, "clocks": clk.summary(), "launches": launches}
         next_step = W + K
-        if gravity == "fr" and not args.lean:
+        if variant == "fr" and not args.lean:
             # end to end through the C ABI with host buffers: H2D of X, V and D2H of X, V every step
             Xh = torch.empty((3, npart), dtype=torch.int32).pin_memory()
             Vh = torch.empty((3, npart), dtype=torch.float32).pin_memory()
@@ -420,7 +423,7 @@ def run_gpu(args):
             results["e2e_bytes"] = int(Xh.numel() * 4 + Vh.numel() * 4)
             del Xh, Vh
             next_step = W + 2 * K
-        if gravity == "fr":
+        if variant == "fr":
             # per-kernel classes timed alone: the next K steps with both solvers
             # on one stream (the timed steps above run the scalaron beside the
             # Poisson solve, where CUDA events would time kernels sharing the GPU)
@@ -437,6 +440,7 @@ def run_gpu(args):
         return 0
 
     fr_res, nw_res, ft_res = results["fr"], results.get("newton"), results.get("newton_fft7")
+    n2_res, mu_res = results.get("fr_n2"), results.get("mu")
     total = world * npart * K
     value = total / (fr_res["ms"] / 1e3)
     peak, peak_kind = load_peaks()
@@ -477,6 +481,14 @@ def run_gpu(args):
             "value": total / (ft_res["ms"] / 1e3), "ms_per_step": ft_res["ms"] / K,
             "gpu_launches": ft_res["launches"],
             "what": "Newtonian step with the FFT_7pt Poisson solve (the exact 7-point inverse) instead of multigrid"},
+        "fr_n2": None if n2_res is None else {
+            "value": total / (n2_res["ms"] / 1e3), "ms_per_step": n2_res["ms"] / K,
+            "gpu_launches": n2_res["launches"],
+            "what": "the same step with the Hu-Sawicki n = 2 scalaron (quartic per cell)"},
+        "mu": None if mu_res is None else {
+            "value": total / (mu_res["ms"] / 1e3), "ms_per_step": mu_res["ms"] / K,
+            "gpu_launches": mu_res["launches"],
+            "what": f"the Newtonian step with parametrised gravity, mu0 = {MU0}"},
         "mg_cycles": [s["mg"]["cycles"] for s in fr_res["stats"]],
         "serial_ms_per_step": fr_res["ms_serial"] / K,
         "e2e": None if "e2e_ms" not in results else {
