@@ -2,9 +2,14 @@
 configuration: 512^3 particles on a 512^3 grid, L = 512 Mpc/h, Omega_m = 0.3,
 sigma8 = 0.8, f_R0 = -1e-5, 2LPT initial conditions at z = 30 (seed 5), steps
 uniform in ln a.  One step = cell sort, TSC deposit, one FAS F-cycle for the
-scalaron, Poisson V-cycles to the float32 floor, gradient of the combined
-potential, inverse TSC, kick and drift.  The Newtonian step on the same
-particles is reported beside it.
+scalaron beside two warm-started Poisson V-cycles (the cold first step
+iterates to a relative residual of 1e-7), gradient of the combined potential,
+inverse TSC, kick and drift.  Beside it: the same step through the C ABI with
+host buffers (e2e), per-kernel-class CUDA-event times from further steps with
+both solvers on one stream (the roofline of the dominant class), the
+Newtonian, FFT_7pt, n = 2 and parametrised-gravity steps on the same
+particles, the differentiable 128^3 run, the 64-box ensemble and the FP64
+oracle on a bounded sample.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
