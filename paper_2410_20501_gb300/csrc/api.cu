@@ -371,10 +371,12 @@ pm_status pm_interp(const float* g, const uint32_t* X, int64_t np, int n, float*
 // The step; with V_host, the velocities are copied from that host array on
 // the copy stream cp while the positions are sorted and the potentials solved
 // (the velocities enter only the force pass, after their own permutation).
-pm_status step_impl(pm_state* st_, const pm_step_params* prm, pm_stats* stats, void* stream, const float* V_host,
-                    SideStream* cp) {
+// Host-side checks of a step's arguments (nothing is enqueued), with the
+// effective f(R) parameters and the workspace carve-up: PM_EINVAL / PM_ENOMEM
+// exactly as the step returns them.
+pm_status step_args(const pm_state* st_, const pm_step_params* prm, fr_params* frp, Workspace* w) {
   if (!st_ || !prm) return PM_EINVAL;
-  pm_state& S = *st_;
+  const pm_state& S = *st_;
   const int n = S.n;
   const int64_t np = S.np;
   if (!valid_n(n) || !valid_np(np) || (np > 0 && (!S.X || !S.V)) || !S.phi) return PM_EINVAL;
@@ -384,19 +386,28 @@ pm_status step_impl(pm_state* st_, const pm_step_params* prm, pm_stats* stats, v
   if (prm->gravity == PM_GRAVITY_FR && !S.eps) return PM_EINVAL;
   if (prm->grad_order != 3 && prm->grad_order != 5 && prm->grad_order != 7) return PM_EINVAL;
   if (!(prm->a > 0.0) || !valid_mg(&prm->mg)) return PM_EINVAL;
-  fr_params frp = prm->fr;
-  frp.a = prm->a;
-  frp.Om = prm->Om;
-  frp.OL = prm->OL;
-  frp.fR0 = prm->fR0;
-  frp.boxsize = prm->boxsize;
-  if (prm->gravity == PM_GRAVITY_FR && !valid_fr(&frp)) return PM_EINVAL;
+  *frp = prm->fr;
+  frp->a = prm->a;
+  frp->Om = prm->Om;
+  frp->OL = prm->OL;
+  frp->fR0 = prm->fR0;
+  frp->boxsize = prm->boxsize;
+  if (prm->gravity == PM_GRAVITY_FR && !valid_fr(frp)) return PM_EINVAL;
   if (prm->poisson != PM_POISSON_MG && prm->poisson != PM_POISSON_FFT7 && prm->poisson != PM_POISSON_FFT)
     return PM_EINVAL;
   if (prm->poisson != PM_POISSON_MG && n < 16) return PM_EINVAL;
   const uint32_t flags = PM_WS_STEP | (S.id ? PM_WS_IDS : 0) | (prm->poisson != PM_POISSON_MG ? PM_WS_FFT : 0);
+  return check_ws(*w, S.ws, S.ws_bytes, n, np, flags);
+}
+
+pm_status step_impl(pm_state* st_, const pm_step_params* prm, pm_stats* stats, void* stream, const float* V_host,
+                    SideStream* cp) {
+  fr_params frp;
   Workspace w;
-  PM_TRY(check_ws(w, S.ws, S.ws_bytes, n, np, flags));
+  PM_TRY(step_args(st_, prm, &frp, &w));
+  pm_state& S = *st_;
+  const int n = S.n;
+  const int64_t np = S.np;
   cudaStream_t s = as_stream(stream);
   const int64_t N = (int64_t)n * n * n;
   pm_stats local;
@@ -497,6 +508,11 @@ pm_status pm_step(pm_state* st_, const pm_step_params* prm, pm_stats* stats, voi
 pm_status pm_step_host(pm_state* st_, const pm_step_params* prm, pm_stats* stats, const uint32_t* X_in,
                        const float* V_in, uint32_t* X_out, float* V_out, void* stream) {
   if (!st_ || !X_in || !V_in || !X_out || !V_out) return PM_EINVAL;
+  {   // argument errors before any copy is enqueued
+    fr_params frp;
+    Workspace w;
+    PM_TRY(step_args(st_, prm, &frp, &w));
+  }
   cudaStream_t s = as_stream(stream);
   const size_t bytes = (size_t)st_->np * 12;
   SideStream* cp = nullptr;

@@ -78,6 +78,12 @@ def test_misaligned_arrays_are_rejected_before_any_launch(L):
     sp = pm.pm_step_params(a=0.5, Om=0.3, OL=0.7, boxsize=16.0, grad_order=5, dt_kick=0.0, dt_drift=0.0,
                            phi_rescale=1.0, mg=pm.default_mg(), fr=pm.default_fr())
     assert L.pm_step(ctypes.byref(st), ctypes.byref(sp), None, None) == 1
+    # the host-buffer step checks the same arguments before enqueuing any copy
+    host = ctypes.c_void_p(0x200000)
+    assert L.pm_step_host(ctypes.byref(st), ctypes.byref(sp), None, host, host, host, host, None) == 1
+    st.V = ok.value
+    st.ws_bytes = 1024
+    assert L.pm_step_host(ctypes.byref(st), ctypes.byref(sp), None, host, host, host, host, None) == 2
 
 
 def test_workspace_size_monotone(L):
