@@ -35,7 +35,10 @@
  *    read an 8-byte residual norm; with fixed cycle counts they never sync.
  *  - Results are deterministic: no floating-point atomics are used anywhere,
  *    every reduction has a fixed order, so reruns are bitwise identical.
- *  - Not thread-safe: calls must come from one host thread at a time.
+ *  - Not thread-safe: calls must come from one host thread at a time.  The
+ *    library's per-device state (kernel shared-memory limits, its second
+ *    streams, the scratch address of pm_deposit_noalloc) is kept per device,
+ *    so one process may drive several GPUs, one call at a time.
  */
 #ifndef PM_API_H
 #define PM_API_H
@@ -115,9 +118,12 @@ pm_status pm_deposit(const uint32_t* X, int64_t np, int n, float* rho,
  *   Limits: n <= 64 and np <= 262144 (2^18); larger sizes return PM_EINVAL.
  *   The caller still passes X (device, [3][np] uint32) and rho (device,
  *   [n^3] float32).
- *   The first call on a device looks up the array's device address with
- *   cudaGetSymbolAddress (with that device current); make that first call
- *   before any stream capture.
+ *   Each call made outside stream capture looks up the array's device
+ *   address with cudaGetSymbolAddress (with the calling device current); a
+ *   call captured into a CUDA graph uses the address found by the last
+ *   uncaptured call on that device.  So make the first call on a device, and
+ *   the first call after a device reset, before any stream capture (a
+ *   captured call with no address on record returns PM_EINVAL).
  *   Every call shares the array: calls that overlap on the GPU (different
  *   streams, or different host threads) race on it and give wrong results. */
 pm_status pm_deposit_noalloc(const uint32_t* X, int64_t np, int n, float* rho, void* stream);

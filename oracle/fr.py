@@ -136,22 +136,15 @@ class FASParams:
 
 
 def _coarse(u, b, h, fbar, kappa, prm, n=1):
-    """Coarsest level: non-linear sweeps until the residual dropped by
-    ``coarse_drop``, its running minimum stalls (no 0.1% gain in 5 sweeps),
-    or ``coarse_max_sweeps``."""
-    r0 = best = np.linalg.norm(b - operator(u, h, fbar, kappa, n))
-    stale = 0
+    """Coarsest level: non-linear Gauss-Seidel sweeps until the residual has
+    dropped by ``coarse_drop`` or ``coarse_max_sweeps`` sweeps have run (the
+    paper leaves the coarsest-level method open; same reading as the linear
+    solver's)."""
+    r0 = np.linalg.norm(b - operator(u, h, fbar, kappa, n))
     for _ in range(prm.coarse_max_sweeps):
         gs_sweep(u, b, h, fbar, kappa, n)
-        r = np.linalg.norm(b - operator(u, h, fbar, kappa, n))
-        if r <= prm.coarse_drop * r0:
+        if np.linalg.norm(b - operator(u, h, fbar, kappa, n)) <= prm.coarse_drop * r0:
             break
-        if r < 0.999 * best:
-            best, stale = r, 0
-        else:
-            stale += 1
-            if stale >= 5:
-                break
     return u
 
 

@@ -3,6 +3,8 @@
 #include <math.h>
 #include <string.h>
 
+#include <mutex>
+#include <utility>
 #include <vector>
 
 #include "pm_internal.cuh"
@@ -51,6 +53,19 @@ void launch_end(int cls, cudaStream_t s) {
     cudaEventRecord(g_timing.stop[g_timing.used], s);
     ++g_timing.used;
   }
+}
+
+pm_status smem_attr_fn(const void* fn, size_t bytes) {
+  static std::mutex mu;
+  static std::vector<std::pair<int, const void*>> done;   // (device, kernel) pairs already raised
+  int dev = 0;
+  PM_TRY(cuda_status(cudaGetDevice(&dev)));
+  std::lock_guard<std::mutex> lock(mu);
+  for (const auto& d : done)
+    if (d.first == dev && d.second == fn) return PM_OK;
+  PM_TRY(cuda_status(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes)));
+  done.emplace_back(dev, fn);
+  return PM_OK;
 }
 
 pm_status cuda_status(cudaError_t e) {

@@ -277,12 +277,7 @@ pm_status launch_deposit(const uint32_t* Xs, int64_t np, const uint32_t* cellsta
                          float scale, float* rho, double* partials, double* mean_out, cudaStream_t s) {
   constexpr int E = T + 2;
   constexpr size_t smem = sizeof(float) * 27 * E * E * E;
-  static bool attr = false;
-  if (!attr) {
-    PM_TRY(cuda_status(cudaFuncSetAttribute(k_deposit<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                            (int)smem)));
-    attr = true;
-  }
+  PM_TRY(smem_attr(k_deposit<T>, smem));
   const int tiles = n / T;
   const int64_t nblocks = (int64_t)tiles * tiles * tiles;
   PM_LAUNCH(K_DEPOSIT, (vals ? 16.0 : 12.0) * np + 8.0 * n * n * (double)n + 4.0, k_deposit<T>, (unsigned)nblocks,
@@ -317,12 +312,7 @@ pm_status deposit_sorted(const uint32_t* Xs, int64_t np, const uint32_t* cellsta
 pm_status deposit_sorted_values(const uint32_t* Xs, int64_t np, const uint32_t* cellstart, int n, const float* vals,
                                 float scale, float* rho, double* partials, double* mean_out, cudaStream_t s) {
   if (n >= 32) {
-    static bool attr = false;
-    if (!attr) {
-      PM_TRY(cuda_status(cudaFuncSetAttribute(k_deposit_stream, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                              (int)kDepositStreamSmem)));
-      attr = true;
-    }
+    PM_TRY(smem_attr(k_deposit_stream, kDepositStreamSmem));
     int chunk, nitems;
     deposit_stream_plan(n, &chunk, &nitems);
     const unsigned grid = (unsigned)nitems;   // one item per CTA, two 512-thread CTAs per SM
@@ -339,12 +329,7 @@ pm_status deposit_sorted_values(const uint32_t* Xs, int64_t np, const uint32_t* 
 pm_status deposit_sorted_batch(const uint32_t* Xs, int64_t np_box, int B, const uint32_t* cellstart, int n,
                                float* rho, double* partials, double* mean_out, cudaStream_t s) {
   if (n < 32 || B < 1) return PM_EINVAL;
-  static bool attr = false;
-  if (!attr) {
-    PM_TRY(cuda_status(cudaFuncSetAttribute(k_deposit_stream, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                            (int)kDepositStreamSmem)));
-    attr = true;
-  }
+  PM_TRY(smem_attr(k_deposit_stream, kDepositStreamSmem));
   int chunk, nitems;
   deposit_stream_plan(n, &chunk, &nitems);
   const float scale = np_box > 0 ? (float)((double)n * n * n / (double)np_box) : 0.0f;

@@ -385,18 +385,9 @@ LevelConst level_const(const FR& f, int l) {
 
 template <int NH>
 pm_status stream_attributes_nh() {
-  static bool done = false;
-  if (!done) {
-    PM_TRY(cuda_status(cudaFuncSetAttribute(k_rb_stream<2, FRUpdate<NH>>,
-                                            cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                            (int)StreamGeom<2>::smem_bytes)));
-    PM_TRY(cuda_status(cudaFuncSetAttribute(k_rb_stream<1, FRUpdate<NH>>,
-                                            cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                            (int)StreamGeom<1>::smem_bytes)));
-    PM_TRY(cuda_status(cudaFuncSetAttribute((k_rb_fused<FRUpdate<NH>, 2, 2>),
-                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFusedSmem)));
-    done = true;
-  }
+  PM_TRY(smem_attr(k_rb_stream<2, FRUpdate<NH>>, StreamGeom<2>::smem_bytes));
+  PM_TRY(smem_attr(k_rb_stream<1, FRUpdate<NH>>, StreamGeom<1>::smem_bytes));
+  PM_TRY(smem_attr(k_rb_fused<FRUpdate<NH>, 2, 2>, kFusedSmem));
   return PM_OK;
 }
 

@@ -563,18 +563,10 @@ pm_status launch_force_interp(const float* phi, const float* eps, float alpha, i
                               float drift_scale, int mode, cudaStream_t s, const Batch& bt, float2* blockmax,
                               int64_t* nblocks) {
   constexpr size_t smem = force_interp_smem<ORDER>();
-  static bool attr = false;
-  if (!attr) {
-    PM_TRY(cuda_status(cudaFuncSetAttribute(k_force_interp_stream<ORDER, false, false>,
-                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)));
-    PM_TRY(cuda_status(cudaFuncSetAttribute(k_force_interp_stream<ORDER, false, true>,
-                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)));
-    PM_TRY(cuda_status(cudaFuncSetAttribute(k_force_interp_stream<ORDER, true, false>,
-                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)));
-    PM_TRY(cuda_status(cudaFuncSetAttribute(k_force_interp_stream<ORDER, true, true>,
-                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)));
-    attr = true;
-  }
+  PM_TRY(smem_attr(k_force_interp_stream<ORDER, false, false>, smem));
+  PM_TRY(smem_attr(k_force_interp_stream<ORDER, false, true>, smem));
+  PM_TRY(smem_attr(k_force_interp_stream<ORDER, true, false>, smem));
+  PM_TRY(smem_attr(k_force_interp_stream<ORDER, true, true>, smem));
   const int tiles = (n / IT_Y) * (n / IT_Z);
   int chunk = n;
   while (chunk > 16 && (int64_t)tiles * (n / chunk) * bt.B < 16 * 152) chunk >>= 1;

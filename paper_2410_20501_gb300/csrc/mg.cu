@@ -415,18 +415,9 @@ struct MG {
 };
 
 pm_status stream_attributes() {
-  static bool done = false;
-  if (!done) {
-    PM_TRY(cuda_status(cudaFuncSetAttribute(k_rb_stream<2, PoissonUpdate>,
-                                            cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                            (int)StreamGeom<2>::smem_bytes)));
-    PM_TRY(cuda_status(cudaFuncSetAttribute(k_rb_stream<1, PoissonUpdate>,
-                                            cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                            (int)StreamGeom<1>::smem_bytes)));
-    PM_TRY(cuda_status(cudaFuncSetAttribute((k_rb_fused<PoissonUpdate, 2, 2>), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                            (int)kFusedSmem)));
-    done = true;
-  }
+  PM_TRY(smem_attr(k_rb_stream<2, PoissonUpdate>, StreamGeom<2>::smem_bytes));
+  PM_TRY(smem_attr(k_rb_stream<1, PoissonUpdate>, StreamGeom<1>::smem_bytes));
+  PM_TRY(smem_attr(k_rb_fused<PoissonUpdate, 2, 2>, kFusedSmem));
   return PM_OK;
 }
 
@@ -562,7 +553,7 @@ pm_status prolong_correct_launch(float* u, const float* uc, const float* uc2, in
 
 pm_status fetch_scalars(const double* dev, double* host, int count, cudaStream_t s) {
   static double* pinned = nullptr;
-  if (!pinned) PM_TRY(cuda_status(cudaHostAlloc((void**)&pinned, 64 * sizeof(double), cudaHostAllocDefault)));
+  if (!pinned) PM_TRY(cuda_status(cudaHostAlloc((void**)&pinned, 64 * sizeof(double), cudaHostAllocPortable)));
   PM_TRY(cuda_status(cudaMemcpyAsync(pinned, dev, count * sizeof(double), cudaMemcpyDeviceToHost, s)));
   PM_TRY(cuda_status(cudaStreamSynchronize(s)));
   for (int i = 0; i < count; ++i) host[i] = pinned[i];

@@ -2,6 +2,8 @@
 // memory.  Instead of a caller workspace it uses one file-scope device array.
 #include <string.h>
 
+#include <mutex>
+
 #include "pm_internal.cuh"
 
 namespace pmgb {
@@ -17,18 +19,27 @@ constexpr int kMaxDevices = 64;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
 
 void* g_scratch_addr[kMaxDevices] = {nullptr};
+std::mutex g_scratch_mu;
 
 // Device address of the scratch array on the current device (host code must
-// not use the symbol itself: on the host it is only a stand-in).
-pm_status scratch_address(void** out) {
+// not use the symbol itself: on the host it is only a stand-in).  Outside
+// stream capture the address is looked up again on every call, so a device
+// reset (after which the module is loaded anew and the array may move) is
+// followed; during capture the address recorded by the last uncaptured call
+// on this device is used, and a call that has none returns PM_EINVAL.
+pm_status scratch_address(cudaStream_t s, void** out) {
   int dev = 0;
   PM_TRY(cuda_status(cudaGetDevice(&dev)));
   if (dev < 0 || dev >= kMaxDevices) return PM_EINVAL;
-  if (!g_scratch_addr[dev]) {
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  PM_TRY(cuda_status(cudaStreamIsCapturing(s, &cap)));
+  std::lock_guard<std::mutex> lock(g_scratch_mu);
+  if (cap == cudaStreamCaptureStatusNone) {
     void* p = nullptr;
     PM_TRY(cuda_status(cudaGetSymbolAddress(&p, g_noalloc_scratch)));
     g_scratch_addr[dev] = p;
   }
+  if (!g_scratch_addr[dev]) return PM_EINVAL;
   *out = g_scratch_addr[dev];
   return PM_OK;
 }
@@ -45,14 +56,14 @@ extern "C" pm_status pm_deposit_noalloc(const uint32_t* X, int64_t np, int n, fl
     return PM_EINVAL;
   const size_t need = layout_workspace(nullptr, nullptr, n, np, PM_WS_SORT);
   if (need > kNoallocBytes) return PM_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
   void* base = nullptr;
-  PM_TRY(scratch_address(&base));
+  PM_TRY(scratch_address(s, &base));
   Workspace w;
   layout_workspace(&w, base, n, np, PM_WS_SORT);
   // Nothing in the scratch has to start at zero: every buffer the deposit
   // reads (cell starts, keys, the permutation, sorted positions, block
   // partials) is fully written earlier in the same call.
-  cudaStream_t s = (cudaStream_t)stream;
   uint32_t* perm;
   PM_TRY(sort_cells(X, np, n, w, s, w.cellstart, &perm));
   PM_TRY(permute_particles(perm, np, X, nullptr, nullptr, w.Xs, nullptr, nullptr, s));

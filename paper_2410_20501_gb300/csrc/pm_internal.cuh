@@ -37,6 +37,16 @@ pm_status cuda_status(cudaError_t e);
 // cudaGetLastError() after a batch of launches.
 inline pm_status launch_status() { return cuda_status(cudaGetLastError()); }
 
+// Raises the dynamic shared-memory limit of kernel `fn` to `bytes` on the
+// current device.  The attribute belongs to the device that is current when
+// it is set, so it is set once per (device, kernel) pair; the record is
+// guarded by a mutex.
+pm_status smem_attr_fn(const void* fn, size_t bytes);
+template <class K>
+inline pm_status smem_attr(K* fn, size_t bytes) {
+  return smem_attr_fn(reinterpret_cast<const void*>(fn), bytes);
+}
+
 inline int ilog2(int64_t v) { int l = 0; while ((int64_t(1) << (l + 1)) <= v) ++l; return l; }
 inline bool valid_n(int n) { return n >= 4 && n <= 1024 && (n & (n - 1)) == 0; }
 

@@ -184,3 +184,71 @@ def test_n2_linear_regime_matches_yukawa_closed_form():
     pred = np.fft.irfftn(-(model.Om * a / c2) * np.fft.rfftn(delta) / (lam - mu2), s=delta.shape, axes=(0, 1, 2))
     df = fbar * (u ** 3 - 1.0)
     assert np.abs(df - pred).max() < 2e-3 * np.abs(pred).max()
+
+
+def _fas_problem(n, seed, a=0.7):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    g = rng.standard_normal((n, n, n))
+    rho = np.exp(0.5 * g)
+    rho /= rho.mean()
+    model = fr.FRModel(Om=0.3, OL=0.7, fR0=-1e-5, boxsize=float(n))
+    fbar, kappa, _ = fr.background(a, model)
+    return fr.source(rho, a, model), fbar, kappa
+
+
+def test_f_cycle_is_its_steps_in_order():
+    """A three-level FAS F-cycle (16^3 over 8^3 over a 4^3 coarsest level)
+    equals, bit for bit, the sequence written out here (§3.6.2 for the FAS
+    coarse problem; the F-cycle reading: pre-smooth, FAS coarse problem,
+    F-cycle on it, correction, then a V-cycle on this level).  Running the
+    V-cycle first instead changes the result."""
+    n, h = 16, 1.0 / 16
+    b, fbar, kappa = _fas_problem(n, 41)
+    prm = fr.FASParams(coarsest=4)
+    got = fr.fas_f_cycle(np.ones((n, n, n)), b, h, fbar, kappa, prm)
+
+    def smooth(u, bb, hh, k):
+        for _ in range(k):
+            fr.gs_sweep(u, bb, hh, fbar, kappa)
+
+    def coarse_problem(u, bb, hh):
+        smooth(u, bb, hh, 2)                                  # pre-smooth
+        d = bb - fr.operator(u, hh, fbar, kappa)
+        uH = poisson.restrict(u)
+        return uH, uH.copy(), fr.operator(uH, 2 * hh, fbar, kappa) + poisson.restrict(d)
+
+    def v8(u, bb):                                           # V-cycle on the 8^3 level
+        u4, r4, b4 = coarse_problem(u, bb, 2 * h)
+        fr._coarse(u4, b4, 4 * h, fbar, kappa, prm)
+        u += poisson.prolong(u4 - r4)
+        smooth(u, bb, 2 * h, 2)
+
+    u = np.ones((n, n, n))
+    u8, r8, b8 = coarse_problem(u, b, h)                     # 16: pre-smooth, FAS problem on 8
+    u4, r4, b4 = coarse_problem(u8, b8, 2 * h)               # F-cycle on 8: FAS problem on 4,
+    fr._coarse(u4, b4, 4 * h, fbar, kappa, prm)              # solved (coarsest),
+    u8 += poisson.prolong(u4 - r4)                           # corrected,
+    v8(u8, b8)                                               # then a V-cycle on 8
+    u += poisson.prolong(u8 - r8)                            # correct 16
+    v_u8, v_r8, v_b8 = coarse_problem(u, b, h)               # V-cycle on 16: FAS problem on 8,
+    v8(v_u8, v_b8)                                           # V-cycle there,
+    u += poisson.prolong(v_u8 - v_r8)                        # correct,
+    smooth(u, b, h, 2)                                       # post-smooth
+    assert np.array_equal(got, u)
+
+    alt = np.ones((n, n, n))
+    fr.fas_v_cycle(alt, b, h, fbar, kappa, prm)
+    fr.fas_f_cycle(alt, b, h, fbar, kappa, fr.FASParams(coarsest=16))   # V first, then the smoother
+    assert not np.allclose(got, alt, rtol=0, atol=1e-12)
+
+
+def test_fas_coarsest_solve_reaches_its_drop_in_fp64():
+    """The non-linear coarsest-level solve stops on the 1e-3 drop inside its
+    sweep cap in float64, from the background u = 1."""
+    n, h = 16, 1.0 / 16
+    for seed in (1, 2):
+        b, fbar, kappa = _fas_problem(n, seed)
+        u = np.ones((n, n, n))
+        r0 = np.linalg.norm(b - fr.operator(u, h, fbar, kappa))
+        fr._coarse(u, b, h, fbar, kappa, fr.FASParams(coarse_max_sweeps=150))
+        assert np.linalg.norm(b - fr.operator(u, h, fbar, kappa)) <= 1e-3 * r0

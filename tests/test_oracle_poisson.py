@@ -128,3 +128,108 @@ def test_fft_tsc_removes_the_mean_and_is_linear():
     np.testing.assert_allclose(poisson.solve_fft_tsc(2 * f - g, 1.0 / 8),
                                2 * poisson.solve_fft_tsc(f, 1.0 / 8) - poisson.solve_fft_tsc(g, 1.0 / 8),
                                atol=1e-12)
+
+
+def test_rbgs_sweep_point_source_by_hand():
+    """One sweep from u = 0 with a unit source in red cell (0, 0, 0), h = 1 on a
+    4^3 grid, worked by hand from Eq. jacobi_sweep_laplacian with SOR: the red
+    pass sets u_000 = -omega/6 (its neighbours are still 0); the black pass then
+    gives each of the six neighbours omega (u_000 / 6) and leaves the other
+    black cells at 0.  A black-first sweep would leave the neighbours at 0."""
+    for omega in (1.0, 1.25):
+        f = np.zeros((4, 4, 4))
+        f[0, 0, 0] = 1.0
+        u = poisson.rbgs_sweep(np.zeros((4, 4, 4)), f, 1.0, omega)
+        expect = np.zeros((4, 4, 4))
+        expect[0, 0, 0] = -omega / 6.0
+        for d in ((1, 0, 0), (3, 0, 0), (0, 1, 0), (0, 3, 0), (0, 0, 1), (0, 0, 3)):
+            expect[d] = omega * (-omega / 6.0) / 6.0
+        assert np.abs(u - expect).max() < 1e-15
+    # a source in a black cell: the red pass sees only zeros, so only that cell moves
+    f = np.zeros((4, 4, 4))
+    f[1, 0, 0] = 1.0
+    u = poisson.rbgs_sweep(np.zeros((4, 4, 4)), f, 1.0, 1.25)
+    expect = np.zeros((4, 4, 4))
+    expect[1, 0, 0] = -1.25 / 6.0
+    assert np.abs(u - expect).max() < 1e-15
+
+
+def test_sweep_omegas_reading():
+    """§3.6.1 "omit SOR on the first and last iterations", read per level visit:
+    omega = 1 on the first pre-sweep and on the last post-sweep only."""
+    assert poisson.sweep_omegas(2, 1.25, True, False) == [1.0, 1.25]
+    assert poisson.sweep_omegas(2, 1.25, False, True) == [1.25, 1.0]
+    assert poisson.sweep_omegas(3, 1.25, True, False) == [1.0, 1.25, 1.25]
+    assert poisson.sweep_omegas(1, 1.25, False, True) == [1.0]
+    assert poisson.sweep_omegas(0, 1.25, True, False) == []
+
+
+def test_v_cycle_is_its_steps_in_order():
+    """A two-level V-cycle (8^3 over a 4^3 coarsest level) equals, bit for bit,
+    the sequence written out here: sweeps with omega 1 then 1.25, residual,
+    restriction, coarsest solve of the error from zero, prolongation and
+    correction, sweeps with omega 1.25 then 1.  Swapping the SOR factors of the
+    pre-sweeps changes the result."""
+    n, h = 8, 1.0 / 8
+    rng = np.random.Generator(np.random.PCG64(31))
+    f = rng.standard_normal((n, n, n))
+    f -= f.mean()
+    u0 = 1e-3 * rng.standard_normal((n, n, n))
+    prm = poisson.MGParams(coarsest=4)
+    got = poisson.v_cycle(u0.copy(), f, h, prm)
+
+    def written_out(w_pre):
+        u = u0.copy()
+        for w in w_pre:
+            poisson.rbgs_sweep(u, f, h, w)
+        fH = poisson.restrict(f - mesh.laplacian7(u, h))
+        vH = poisson.coarse_solve(np.zeros_like(fH), fH, 2 * h, prm)
+        u += poisson.prolong(vH)
+        poisson.rbgs_sweep(u, f, h, 1.25)
+        poisson.rbgs_sweep(u, f, h, 1.0)
+        return u
+
+    assert np.array_equal(got, written_out((1.0, 1.25)))
+    assert not np.allclose(got, written_out((1.25, 1.0)), rtol=0, atol=1e-12)
+
+
+def test_coarsest_solve_rate_is_youngs_optimum():
+    """With Young's optimal factor the asymptotic residual reduction per
+    red-black SOR sweep is omega_opt - 1 (0.634 at 16^3); a wrong Jacobi
+    eigenvalue in the factor's formula moves the measured rate off it."""
+    n = 16
+    h = 1.0 / n
+    w = poisson.optimal_sor_omega(n)
+    assert w == pytest.approx(1.634, abs=5e-4)
+    rng = np.random.Generator(np.random.PCG64(32))
+    f = rng.standard_normal((n, n, n))
+    f -= f.mean()
+    u = np.zeros((n, n, n))
+    r = []
+    for _ in range(80):
+        poisson.rbgs_sweep(u, f, h, w)
+        u -= u.mean()
+        r.append(np.linalg.norm(poisson.residual(u, f, h)))
+    rate = (r[-1] / r[-21]) ** (1.0 / 20)
+    assert rate == pytest.approx(w - 1.0, rel=0.1)
+    for other in (1.25, 1.9):      # both converge more slowly
+        v = np.zeros((n, n, n))
+        for _ in range(40):
+            poisson.rbgs_sweep(v, f, h, other)
+        assert np.linalg.norm(poisson.residual(v, f, h)) > r[39]
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_coarsest_solve_reaches_its_drop_in_fp64(seed):
+    """The coarsest-level solve stops on the 1e-3 drop well inside its
+    200-sweep cap on 16^3 levels in float64 (no other stopping rule is
+    needed at this precision)."""
+    n = 16
+    h = 1.0 / 16
+    rng = np.random.Generator(np.random.PCG64(seed))
+    f = rng.standard_normal((n, n, n))
+    f -= f.mean()
+    r0 = np.linalg.norm(f)
+    prm = poisson.MGParams(coarse_max_sweeps=60)
+    u = poisson.coarse_solve(np.zeros((n, n, n)), f, h, prm)
+    assert np.linalg.norm(poisson.residual(u, f, h)) <= 1e-3 * r0

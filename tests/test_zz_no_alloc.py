@@ -39,13 +39,19 @@ def _noalloc(pm, X, n):
 
 
 def test_noalloc_deposit_matches_pm_deposit_twice(pm):
-    cases = [(64, inputs.uniform_particles(200000, 41)),
+    """Both entry points run the same sort, permutation and deposit kernels on
+    the same buffer layout, so their densities agree bit for bit.  The cases
+    run back to back: the first (n = 64, np = 2^18, the largest accepted
+    layout) fills the shared array, the later smaller ones run over what it
+    left there."""
+    cases = [(64, inputs.uniform_particles(1 << 18, 40)),
+             (64, inputs.uniform_particles(200000, 41)),
              (32, inputs.to_fixed_point(inputs.lattice(32) + 0.004 * inputs.random_field(32, 2).reshape(1, -1)))]
     for n, Xh in cases:
         X = pm.positions_to_device(Xh)
         got = _noalloc(pm, X, n)
         ref = pm.deposit(X, n).cpu().numpy()
-        assert np.abs(got - ref).max() <= 2e-6 * np.abs(ref).max()
+        assert np.array_equal(got, ref)
 
 
 def test_noalloc_rejects_sizes_beyond_the_limit(pm):
