@@ -92,17 +92,41 @@ __global__ void __launch_bounds__(T * T * T) k_deposit(const uint32_t* __restric
 // accumulators.  A destination plane is complete (and written) once the
 // source plane after it has been added.  The moments are double-buffered:
 // the sources of plane x are computed while the destinations add plane x - 1
-// (one barrier per plane).  The cell starts of plane x + 2 and the first
-// particle of plane x + 1 are loaded while plane x is processed.
+// (one barrier per plane).
+//
+// Particle loads: a source thread copies the first KP particles of its cell
+// on the next plane into its own shared-memory slots with asynchronous copies
+// (cp.async, 4 bytes each) while it weighs the particles of this plane, so a
+// cell with up to KP particles is weighed without waiting on global memory;
+// particles beyond KP are loaded in the walk, the next one while the current
+// one is weighed.  The slots of a thread are written and read by that thread
+// only, so they need no barrier.  The cell starts of plane x + 2 are loaded
+// while plane x is processed.  The particles of a cell are weighed in the
+// same order (ascending index) either way.
 constexpr int DTY = 16, DTZ = 16, DEY = DTY + 2, DEZ = DTZ + 2, DNT = DTY * DTZ, DTHREADS = 512;
-constexpr size_t kDepositStreamSmem = sizeof(float) * (2 * 27 * DEY * DEZ + 3 * DNT);
-static_assert(DEY * DEZ <= DTHREADS, "one source cell per thread");
+constexpr int DPL = DEY * DEZ;   // source cells of a plane (one per thread)
+static_assert(DPL <= DTHREADS, "one source cell per thread");
+// Staged particles per cell and words per particle (x, y, z [, value]).
+template <bool VALS> struct DepositStage {
+  static constexpr int KP = VALS ? 3 : 4, NC = VALS ? 4 : 3;
+  static constexpr size_t smem = sizeof(float) * (2 * 27 * DPL + 3 * DNT + 2 * KP * NC * DPL);
+};
 
+__device__ __forceinline__ void cp_async4(void* smem_dst, const void* gsrc) {
+  const uint32_t d = (uint32_t)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+
+template <bool VALS>
 __global__ void __launch_bounds__(DTHREADS, 2) k_deposit_stream(const uint32_t* __restrict__ Xs, int64_t np,
                                                                 const uint32_t* __restrict__ cellstart, int log2n,
                                                                 int chunk, int nitems, const float* __restrict__ vals,
                                                                 float scale, float* __restrict__ rho,
                                                                 double* __restrict__ partial) {
+  using G = DepositStage<VALS>;
+  constexpr int KP = G::KP, NC = G::NC, PL = DPL;
   extern __shared__ float sm[];
   {   // the box of a batched launch: its cell starts (global particle indices), density, partials
     const int64_t off = (int64_t)blockIdx.z << (3 * log2n);
@@ -110,16 +134,28 @@ __global__ void __launch_bounds__(DTHREADS, 2) k_deposit_stream(const uint32_t* 
     rho += off;
     partial += (int64_t)blockIdx.z * nitems;
   }
-  float* Mom = sm;                      // [2][27][DEY * DEZ]
-  float* Acc = sm + 2 * 27 * DEY * DEZ; // [3][DNT]
+  float* Mom = sm;                                   // [2][27][PL]
+  float* Acc = sm + 2 * 27 * PL;                     // [3][DNT]
+  uint32_t* Slot = reinterpret_cast<uint32_t*>(Acc + 3 * DNT);   // [2][KP][NC][PL]
   __shared__ double wsum[DTHREADS / 32];
-  constexpr int PL = DEY * DEZ;
   const int n = 1 << log2n, mask = n - 1;
   const int tiles_z = n / DTZ, tiles = (n / DTY) * tiles_z;
   const int tid = threadIdx.x;
   const bool src = tid < PL, dst = tid < DNT;
   const int sly = tid / DEZ, slz = tid - sly * DEZ;            // source cell of this thread (if src)
   const int ty = tid / DTZ, tz = tid - ty * DTZ;               // destination cell (if dst)
+  // copies the first KP particles [b, min(e, b + KP)) into slot buffer `buf`
+  auto stage = [&](int buf, uint32_t b, uint32_t e) {
+    uint32_t* s0 = Slot + buf * KP * NC * PL + tid;
+#pragma unroll
+    for (int k = 0; k < KP; ++k) {
+      if (b + k < e) {
+#pragma unroll
+        for (int d = 0; d < 3; ++d) cp_async4(s0 + (k * NC + d) * PL, Xs + d * np + b + k);
+        if (VALS) cp_async4(s0 + (k * NC + 3) * PL, vals + b + k);
+      }
+    }
+  };
   for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
     const int tile = item % tiles, xc = item / tiles;
     const int y0 = (tile / tiles_z) * DTY, z0 = (tile % tiles_z) * DTZ;
@@ -129,13 +165,14 @@ __global__ void __launch_bounds__(DTHREADS, 2) k_deposit_stream(const uint32_t* 
     if (dst)
       for (int q = 0; q < 3; ++q) Acc[q * DNT + tid] = 0.0f;
     float wsum_s = 0.0f, wsum_c = 0.0f;
-    // pipeline registers: cell starts of planes xs and xs + 1, first particle of plane xs
-    uint32_t b0 = 0, e0 = 0, b1 = 0, e1 = 0, fx = 0, fy = 0, fz = 0;
+    // pipeline registers: cell starts of planes xs and xs + 1
+    uint32_t b0 = 0, e0 = 0, b1 = 0, e1 = 0;
     if (src) {
       const uint32_t c0 = cell_of(x0 - 1), c1 = cell_of(x0);
       b0 = __ldg(cellstart + c0); e0 = __ldg(cellstart + c0 + 1);
       b1 = __ldg(cellstart + c1); e1 = __ldg(cellstart + c1 + 1);
-      if (b0 < e0) { fx = __ldg(Xs + b0); fy = __ldg(Xs + np + b0); fz = __ldg(Xs + 2 * np + b0); }
+      stage((x0 - 1) & 1, b0, e0);
+      cp_async_commit();
     }
     for (int xs = x0 - 1; xs <= x1 + 1; ++xs) {
       // the moments of source plane xs go to one buffer while the
@@ -143,27 +180,24 @@ __global__ void __launch_bounds__(DTHREADS, 2) k_deposit_stream(const uint32_t* 
       // per step
       float* MomW = Mom + (xs & 1) * 27 * PL;
       const float* MomR = Mom + ((xs - 1) & 1) * 27 * PL;
-      uint32_t nfx = 0, nfy = 0, nfz = 0, b2 = 0, e2 = 0;
+      uint32_t b2 = 0, e2 = 0;
       if (src && xs <= x1) {
-        if (b1 < e1) { nfx = __ldg(Xs + b1); nfy = __ldg(Xs + np + b1); nfz = __ldg(Xs + 2 * np + b1); }
+        if (xs + 1 <= x1) stage((xs + 1) & 1, b1, e1);   // the next plane's particles, in flight
+        cp_async_commit();
         if (xs + 2 <= x1) {
           const uint32_t c2 = cell_of(xs + 2);
           b2 = __ldg(cellstart + c2); e2 = __ldg(cellstart + c2 + 1);
         }
+        cp_async_wait1();                                  // this plane's particles have arrived
         float m[27];
 #pragma unroll
         for (int o = 0; o < 27; ++o) m[o] = 0.0f;
-        uint32_t px = fx, py = fy, pz = fz;
-        for (uint32_t p = b0; p < e0; ++p) {
-          // the next particle of the cell is loaded while this one is weighed
-          uint32_t qx = 0, qy = 0, qz = 0;
-          if (p + 1 < e0) { qx = __ldg(Xs + p + 1); qy = __ldg(Xs + np + p + 1); qz = __ldg(Xs + 2 * np + p + 1); }
+        auto weigh = [&](uint32_t px, uint32_t py, uint32_t pz, float v) {
           float wx[3], wy[3], wz[3];
           tsc_weights(cell_offset(px, log2n), wx);
           tsc_weights(cell_offset(py, log2n), wy);
           tsc_weights(cell_offset(pz, log2n), wz);
-          if (vals) {
-            const float v = __ldg(vals + p);
+          if (VALS) {
             wx[0] *= v; wx[1] *= v; wx[2] *= v;
           }
 #pragma unroll
@@ -174,9 +208,26 @@ __global__ void __launch_bounds__(DTHREADS, 2) k_deposit_stream(const uint32_t* 
 #pragma unroll
               for (int oz = 0; oz < 3; ++oz) m[(ox * 3 + oy) * 3 + oz] = fmaf(wxy, wz[oz], m[(ox * 3 + oy) * 3 + oz]);
             }
-          px = qx;
-          py = qy;
-          pz = qz;
+        };
+        const uint32_t* s0 = Slot + (xs & 1) * KP * NC * PL + tid;
+        const uint32_t cnt = e0 - b0;
+#pragma unroll
+        for (int k = 0; k < KP; ++k)
+          if ((uint32_t)k < cnt)
+            weigh(s0[(k * NC) * PL], s0[(k * NC + 1) * PL], s0[(k * NC + 2) * PL],
+                  VALS ? __uint_as_float(s0[(k * NC + 3) * PL]) : 1.0f);
+        if (cnt > (uint32_t)KP) {   // a crowded cell: the rest from global memory
+          uint32_t p = b0 + KP;
+          uint32_t px = __ldg(Xs + p), py = __ldg(Xs + np + p), pz = __ldg(Xs + 2 * np + p);
+          for (; p < e0; ++p) {
+            // the next particle of the cell is loaded while this one is weighed
+            uint32_t qx = 0, qy = 0, qz = 0;
+            if (p + 1 < e0) { qx = __ldg(Xs + p + 1); qy = __ldg(Xs + np + p + 1); qz = __ldg(Xs + 2 * np + p + 1); }
+            weigh(px, py, pz, VALS ? __ldg(vals + p) : 1.0f);
+            px = qx;
+            py = qy;
+            pz = qz;
+          }
         }
 #pragma unroll
         for (int o = 0; o < 27; ++o) MomW[o * PL + tid] = m[o];
@@ -208,7 +259,6 @@ __global__ void __launch_bounds__(DTHREADS, 2) k_deposit_stream(const uint32_t* 
       }
       __syncthreads();
       b0 = b1; e0 = e1; b1 = b2; e1 = e2;
-      fx = nfx; fy = nfy; fz = nfz;
     }
     const double ws = warp_sum_comp(wsum_s - wsum_c);
     if ((tid & 31) == 0) wsum[tid >> 5] = ws;
@@ -312,12 +362,19 @@ pm_status deposit_sorted(const uint32_t* Xs, int64_t np, const uint32_t* cellsta
 pm_status deposit_sorted_values(const uint32_t* Xs, int64_t np, const uint32_t* cellstart, int n, const float* vals,
                                 float scale, float* rho, double* partials, double* mean_out, cudaStream_t s) {
   if (n >= 32) {
-    PM_TRY(smem_attr(k_deposit_stream, kDepositStreamSmem));
     int chunk, nitems;
     deposit_stream_plan(n, &chunk, &nitems);
     const unsigned grid = (unsigned)nitems;   // one item per CTA, two 512-thread CTAs per SM
-    PM_LAUNCH(K_DEPOSIT, (vals ? 16.0 : 12.0) * np + 8.0 * n * n * (double)n + 4.0, k_deposit_stream, grid, DTHREADS,
-              kDepositStreamSmem, s, Xs, np, cellstart, ilog2(n), chunk, nitems, vals, scale, rho, partials);
+    const double bytes = (vals ? 16.0 : 12.0) * np + 8.0 * n * n * (double)n + 4.0;
+    if (vals) {
+      PM_TRY(smem_attr(k_deposit_stream<true>, DepositStage<true>::smem));
+      PM_LAUNCH(K_DEPOSIT, bytes, k_deposit_stream<true>, grid, DTHREADS, DepositStage<true>::smem, s, Xs, np,
+                cellstart, ilog2(n), chunk, nitems, vals, scale, rho, partials);
+    } else {
+      PM_TRY(smem_attr(k_deposit_stream<false>, DepositStage<false>::smem));
+      PM_LAUNCH(K_DEPOSIT, bytes, k_deposit_stream<false>, grid, DTHREADS, DepositStage<false>::smem, s, Xs, np,
+                cellstart, ilog2(n), chunk, nitems, vals, scale, rho, partials);
+    }
     PM_LAUNCH(K_REDUCE, 8.0 * nitems, k_reduce_partials, 1, 1024, 0, s, partials, (int64_t)nitems, (int64_t)0, 1,
               1.0 / ((double)n * n * n), mean_out);
     return launch_status();
@@ -329,15 +386,15 @@ pm_status deposit_sorted_values(const uint32_t* Xs, int64_t np, const uint32_t* 
 pm_status deposit_sorted_batch(const uint32_t* Xs, int64_t np_box, int B, const uint32_t* cellstart, int n,
                                float* rho, double* partials, double* mean_out, cudaStream_t s) {
   if (n < 32 || B < 1) return PM_EINVAL;
-  PM_TRY(smem_attr(k_deposit_stream, kDepositStreamSmem));
+  PM_TRY(smem_attr(k_deposit_stream<false>, DepositStage<false>::smem));
   int chunk, nitems;
   deposit_stream_plan(n, &chunk, &nitems);
   const float scale = np_box > 0 ? (float)((double)n * n * n / (double)np_box) : 0.0f;
   // one item per CTA: B x nitems CTAs balance over the SMs (two resident each)
   const int gx = nitems;
   const int64_t np = np_box * B;
-  PM_LAUNCH(K_DEPOSIT, 12.0 * np + 8.0 * n * n * (double)n * B + 4.0, k_deposit_stream, dim3(gx, 1, B), DTHREADS,
-            kDepositStreamSmem, s, Xs, np, cellstart, ilog2(n), chunk, nitems, (const float*)nullptr, scale, rho,
+  PM_LAUNCH(K_DEPOSIT, 12.0 * np + 8.0 * n * n * (double)n * B + 4.0, k_deposit_stream<false>, dim3(gx, 1, B),
+            DTHREADS, DepositStage<false>::smem, s, Xs, np, cellstart, ilog2(n), chunk, nitems, (const float*)nullptr, scale, rho,
             partials);
   PM_LAUNCH(K_REDUCE, 8.0 * nitems * B, k_reduce_partials, B, 1024, 0, s, partials, (int64_t)nitems,
             (int64_t)nitems, B, 1.0 / ((double)n * n * n), mean_out);

@@ -39,22 +39,25 @@ __device__ __forceinline__ int64_t idx3(int i, int j, int k, int log2n) {
 }
 
 // Root eps > -1 of g(e) = e^3 + 3e^2 + c1 e + c0 (g(-1) = q < 0, g convex on
-// e > -1, so the root is unique).  Two plain Newton steps from the current
-// value usually reach float32 resolution (one suffices when the value moved
-// little since the last sweep); otherwise Newton continues inside a
-// shrinking bracket [lo, hi]; when a step leaves the bracket (or g' <= 0) the
-// upper end is set from the bound u* <= sqrt(max(-p, 0)) + (-q)^(1/3),
-// p = c1 - 3, and the step falls back to bisection.  Stops when g is at its
-// float32 rounding level or the step is below 2e-7 relative.
+// e > -1, so the root is unique).  One Halley step from the current value
+// reaches float32 resolution in a warm sweep (the value moved little since
+// the last one); otherwise up to two plain Newton steps from the Halley
+// point, then Newton inside a shrinking bracket [lo, hi]; when a step leaves
+// the bracket (or g' <= 0) the upper end is set from the bound
+// u* <= sqrt(max(-p, 0)) + (-q)^(1/3), p = c1 - 3, and the step falls back to
+// bisection.  Stops when g is at its float32 rounding level or the step is
+// below 2e-7 relative.
 // g(e) of the cell equation in eps = u - 1 (NH = 1: cubic, NH = 2: quartic),
-// its derivative, half its second derivative, the float32 rounding level of
-// its evaluation, and an upper bound of the root (from u* <= sqrt(max(-p, 0))
-// + (-q)^(1/3) for the cubic, u* <= max(1, (|p| + |q|)^(1/3)) for the quartic).
+// its derivative, half its second and a sixth of its third derivative, the
+// float32 rounding level of its evaluation, and an upper bound of the root
+// (from u* <= sqrt(max(-p, 0)) + (-q)^(1/3) for the cubic,
+// u* <= max(1, (|p| + |q|)^(1/3)) for the quartic).
 template <int NH> struct CellPoly;
 template <> struct CellPoly<1> {
   __device__ static float g(float e, float c1, float c0) { return ((e + 3.0f) * e + c1) * e + c0; }
   __device__ static float gp(float e, float c1) { return (3.0f * e + 6.0f) * e + c1; }
   __device__ static float half_gpp(float e) { return 3.0f * e + 3.0f; }
+  __device__ static float sixth_gppp(float) { return 1.0f; }
   __device__ static float noise(float e, float c1, float c0) {
     const float e2 = e * e;
     return 1.5e-7f * (fabsf(c0) + fabsf(c1 * e) + 3.0f * e2 + fabsf(e2 * e));
@@ -67,6 +70,7 @@ template <> struct CellPoly<2> {
   __device__ static float g(float e, float c1, float c0) { return (((e + 4.0f) * e + 6.0f) * e + c1) * e + c0; }
   __device__ static float gp(float e, float c1) { return ((4.0f * e + 12.0f) * e + 12.0f) * e + c1; }
   __device__ static float half_gpp(float e) { const float u = e + 1.0f; return 6.0f * u * u; }
+  __device__ static float sixth_gppp(float e) { return 4.0f * (e + 1.0f); }
   __device__ static float noise(float e, float c1, float c0) {
     const float e2 = e * e;
     return 1.5e-7f * (fabsf(c0) + fabsf(c1 * e) + 6.0f * e2 + 4.0f * fabsf(e2 * e) + e2 * e2);
@@ -82,7 +86,21 @@ __device__ __forceinline__ float fr_root(float e, float c1, float c0, float q) {
   float lo = -1.0f, hi = __int_as_float(0x7f800000);  // +inf until needed
   if (!(e > lo)) e = 0.0f;
   {
-    // fast path: one or two plain Newton steps from the current value;
+    // Halley: e1 = e - g g' / (g'^2 - g g''/2); its remaining error is about
+    // C d^3 for a step d, C = (g''/2g')^2 - g'''/(6 g') (Halley's cubic error
+    // constant), tested without a division
+    const float g0 = P::g(e, c1, c0), gp0 = P::gp(e, c1), hg = P::half_gpp(e);
+    const float den = gp0 * gp0 - g0 * hg;
+    const float e1 = e - __fdividef(g0 * gp0, den);
+    if (gp0 > 0.0f && den > 0.0f && e1 > lo) {
+      const float d = e1 - e;
+      if (fabsf(hg * hg - P::sixth_gppp(e) * gp0) * fabsf(d * d * d) <= (1e-7f * fabsf(e1) + 1e-20f) * (gp0 * gp0))
+        return e1;
+      e = e1;   // not yet at resolution: the Newton steps start from here
+    }
+  }
+  {
+    // one or two plain Newton steps;
     // accepted when the remaining error is at float32 resolution and the root
     // is admissible.  Newton's error after a step of length d is about K d^2,
     // K = g''/(2 g')
@@ -383,11 +401,15 @@ LevelConst level_const(const FR& f, int l) {
   return c;
 }
 
+// Resident CTAs per SM that the four-cell fused f(R) sweep's registers are
+// sized for.
+constexpr int kFrRunsMinBlocks = 3;
+
 template <int NH>
 pm_status stream_attributes_nh() {
   PM_TRY(smem_attr(k_rb_stream<2, FRUpdate<NH>>, StreamGeom<2>::smem_bytes));
   PM_TRY(smem_attr(k_rb_stream<1, FRUpdate<NH>>, StreamGeom<1>::smem_bytes));
-  PM_TRY(smem_attr(k_rb_fused<FRUpdate<NH>, 2, 2>, kFusedSmem));
+  PM_TRY(smem_attr(k_rb_fused4<FRUpdate<NH>, kFrRunsMinBlocks>, kFusedSmem));
   return PM_OK;
 }
 
@@ -423,8 +445,8 @@ pm_status fr_smooth_nh(FR& f, int l, int count) {
     const unsigned grid = (unsigned)((c.n / kFusedT) * (c.n / kFusedT) * (c.n / chunk));
     const FRUpdate upd{c.beta, c.kappa, c.q};
     for (int it = 0; it < count; ++it) {
-      PM_LAUNCH(l == 0 ? K_FR_SMOOTH0 : K_FR_SMOOTH, 12.0 * N, (k_rb_fused<FRUpdate, 2, 2>), grid, kFusedThreads, kFusedSmem,
-                f.s, f.e[l], f.alt[l], f.b[l], c.log2n, chunk, 0, 0, upd);
+      PM_LAUNCH(l == 0 ? K_FR_SMOOTH0 : K_FR_SMOOTH, 12.0 * N, (k_rb_fused4<FRUpdate, kFrRunsMinBlocks>), grid,
+                kQuadThreads, kFusedSmem, f.s, f.e[l], f.alt[l], f.b[l], c.log2n, chunk, 0, 0, upd);
       float* t = f.e[l];
       f.e[l] = f.alt[l];
       f.alt[l] = t;

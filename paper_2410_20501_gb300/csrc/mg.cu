@@ -417,7 +417,7 @@ struct MG {
 pm_status stream_attributes() {
   PM_TRY(smem_attr(k_rb_stream<2, PoissonUpdate>, StreamGeom<2>::smem_bytes));
   PM_TRY(smem_attr(k_rb_stream<1, PoissonUpdate>, StreamGeom<1>::smem_bytes));
-  PM_TRY(smem_attr(k_rb_fused<PoissonUpdate, 2, 2>, kFusedSmem));
+  PM_TRY(smem_attr(k_rb_fused4<PoissonUpdate, 3>, kFusedSmem));
   return PM_OK;
 }
 
@@ -473,8 +473,8 @@ pm_status smooth(MG& g, int l, int count, const float* w, bool zero, float scale
       const unsigned grid = (unsigned)((n / kFusedT) * (n / kFusedT) * (n / chunk));
       PoissonUpdate upd{h2, {w[done], 1.0f}, done == 0 ? scale : 1.0f, done == 0 ? sbox : nullptr};
       const int z = (done == 0 && zero) ? 1 : 0;
-      PM_LAUNCH(l == 0 ? K_MG_SMOOTH0 : K_MG_SMOOTH, (z ? 8.0 : 12.0) * N * g.B, (k_rb_fused<PoissonUpdate, 2, 2>),
-                g.grid(grid), kFusedThreads, kFusedSmem, g.s, g.u[l], g.alt[l], g.f[l], log2n, chunk, z,
+      PM_LAUNCH(l == 0 ? K_MG_SMOOTH0 : K_MG_SMOOTH, (z ? 8.0 : 12.0) * N * g.B, (k_rb_fused4<PoissonUpdate, 3>),
+                g.grid(grid), kQuadThreads, kFusedSmem, g.s, g.u[l], g.alt[l], g.f[l], log2n, chunk, z,
                 done == 0 ? 1 : 0, upd);
       if (tune_chunk) tune_end(g.s);
       float* t = g.u[l];

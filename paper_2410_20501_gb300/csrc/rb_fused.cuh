@@ -7,20 +7,29 @@
 // has moved yet), and the black cells of plane t - 2 on the column, from the
 // new red values of planes t - 3, t - 2, t - 1 computed in earlier steps (all
 // in shared memory: the ring supplies the in-plane neighbours owned by the
-// next columns).  Every update therefore sees exactly the neighbour values of the
-// plain red pass followed by the black pass, and with the same update functor
-// the result is bitwise that of the two colour passes.  Old values come from
-// `uin`, the result goes to `uout` (ping-pong), so neighbouring CTAs never
-// see each other's new values.  Each cell's old value and source are read
-// from HBM once and its new value written once: 12 bytes per cell and sweep.
+// next columns).  Every update therefore sees exactly the neighbour values of
+// the plain red pass followed by the black pass, in the functor's order x+,
+// x-, y+, y-, z+, z-, and with the same update functor the result is bitwise
+// that of the two colour passes.  Old values come from `uin`, the result goes
+// to `uout` (ping-pong), so neighbouring CTAs never see each other's new
+// values.  Each cell's old value and source are read from HBM once and its
+// new value written once: 12 bytes per cell and sweep.
 //
 // Shared memory holds rings of 8 planes of old values (rows y0-2 .. y0+33,
-// columns z0-4 .. z0+35, stored as float4) and 4 planes of new red values
-// (same layout); with these depths one barrier per plane suffices.  Old
-// values and sources are fetched into registers two planes ahead.  Threads 0..511 own the red-black pair (z = 2kp, 2kp + 1) of row
-// y = tid / 16 (one red update and one black update per plane); threads
-// 512..575 update the 64 red cells of the ring (rows y0-1 and y0+32,
-// columns z0-1 and z0+32).
+// columns z0-4 .. z0+35) and 4 planes of new red values (same layout); with
+// these depths one barrier per plane suffices.  The old-value planes arrive
+// by per-thread asynchronous copies (cp.async, 16 bytes each) issued three
+// planes ahead, so no registers hold them in flight; the sources are fetched
+// into registers two planes ahead.
+//
+// 320 threads: threads 0..255 each own a run of four consecutive z cells of
+// one row (two red and two black cells on every plane), threads 256..319
+// update the 64 red cells of the ring (rows y0-1 and y0+32, columns z0-1 and
+// z0+32).  A run's neighbours come in 16-byte shared-memory loads (x+, x-,
+// y+, y- and its own row) plus one scalar for the z neighbour outside the
+// run, and its result leaves in one 16-byte store.  Warp w owns the rows
+// (w / 2) * 8 + (w & 1) + {0, 2, 4, 6}, all of one parity, so which cells of
+// a run are red is the same for the whole warp.
 #pragma once
 
 #include "pm_internal.cuh"
@@ -28,174 +37,19 @@
 namespace pmgb {
 
 constexpr int kFusedT = 32;                        // tile edge (y and z)
-constexpr int kFusedThreads = 16 * kFusedT + 64;   // 512 pair owners + 64 ring cells
 constexpr int kFusedER = kFusedT + 4;              // stored rows: y0-2 .. y0+33
 constexpr int kFusedEC = kFusedT + 8;              // stored columns: z0-4 .. z0+35
 constexpr int kFusedPL = kFusedER * kFusedEC;      // floats per stored plane
-constexpr int kFusedRingOld = 8;   // old values: planes t - 7 .. t + 1 (a store may run ahead of
-                                   // the previous step's readers: no barrier between them)
+constexpr int kFusedRingOld = 8;   // old values: planes t - 3 .. t + 3 (copies run three planes
+                                   // ahead while warps finishing step t - 1 still read plane t - 3)
 constexpr int kFusedRing = 4;      // new red values: planes t - 3 .. t
 constexpr size_t kFusedSmem = sizeof(float) * (kFusedRingOld + kFusedRing) * kFusedPL;
 constexpr int kFusedLoads = kFusedER * (kFusedEC / 4);   // float4 loads per plane (360)
-static_assert(kFusedLoads <= kFusedThreads, "one float4 per thread per plane");
-
-// Update functor interface: upd(old, nb[6] (x+, x-, y+, y-, z+, z-), source,
-// sweep index (0 here), neighbours-never-updated, own-never-updated).  MINB:
-// resident CTAs per SM the register allocation is sized for.  LAG: planes
-// between the red and the black update of a step (1 or 2, below).
-template <class Upd, int MINB, int LAG>
-__global__ void __launch_bounds__(kFusedThreads, MINB) k_rb_fused(const float* __restrict__ uin,
-                                                               float* __restrict__ uout, Src f, int log2n, int chunk,
-                                                               int zero, int first, Upd upd) {
-  constexpr int T = kFusedT, EC = kFusedEC, PL = kFusedPL, R = kFusedRing, RO = kFusedRingOld;
-  extern __shared__ float4 fsm4[];
-  float* Old = reinterpret_cast<float*>(fsm4);   // [RO][ER][EC]
-  float* Red = Old + RO * PL;                    // [R][ER][EC]
-  const int n = 1 << log2n, m = n - 1;
-  const int tiles_z = n / T, tiles = (n / T) * tiles_z;
-  const int item = blockIdx.x;
-  {   // the box of a batched launch
-    const int64_t off = (int64_t)blockIdx.z << (3 * log2n);
-    uin += off;
-    uout += off;
-    f = box_src(f, (int64_t)1 << (3 * log2n));
-    upd = upd.box(blockIdx.z);
-  }
-  const int tile = item % tiles, xc = item / tiles;
-  const int y0 = (tile / tiles_z) * T, z0 = (tile % tiles_z) * T;
-  const int x0 = xc * chunk, x1 = x0 + chunk;
-  const float mean = f.mean ? (float)*f.mean : 0.0f;
-  const int tid = threadIdx.x;
-  const bool nb_old_red = first != 0, own_old = first != 0;
-  // stored position of local (y, z): row y + 2, column z + 4
-
-  // plane loads: thread tid < 360 moves one float4 (row lr, column group lc)
-  const int lr = tid / (EC / 4), lc4 = tid - lr * (EC / 4);
-  const bool loader = tid < kFusedLoads;
-  const int64_t goff = loader ? (((int64_t)((y0 - 2 + lr) & m) << log2n) | ((z0 - 4 + 4 * lc4) & m)) : 0;
-  auto fetch = [&](int t) -> float4 {
-    return __ldg(reinterpret_cast<const float4*>(uin + (((int64_t)(t & m) << (2 * log2n)) | goff)));
-  };
-  auto store = [&](int t, float4 v) {
-    *reinterpret_cast<float4*>(Old + (t & (RO - 1)) * PL + lr * EC + 4 * lc4) = v;
-  };
-
-  if (zero) {
-    for (int i = tid; i < RO * PL; i += kFusedThreads) Old[i] = 0.0f;
-  } else if (loader) {
-    store(x0 - 2, fetch(x0 - 2));
-    store(x0 - 1, fetch(x0 - 1));
-  }
-  // old values of planes t + 1 and t + 2 in flight (two planes ahead)
-  float4 pre0 = make_float4(0.0f, 0.0f, 0.0f, 0.0f), pre1 = pre0;
-  if (!zero && loader) {
-    pre0 = fetch(x0);
-    pre1 = fetch(x0 + 1);
-  }
-
-  // pair owners: row py, pair kp; ring workers: task h
-  const bool owner = tid < 16 * T;
-  const int py = tid >> 4, kp = tid & 15, h = tid - 16 * T;
-  // the red cell (local y, z) this thread updates on plane t
-  auto red_cell = [&](int t, int& y, int& z) {
-    if (owner) {
-      y = py;
-      z = 2 * kp + ((t + y0 + y) & 1);
-    } else if (h < 32) {                       // rows y0 - 1 and y0 + 32
-      y = h < 16 ? -1 : T;
-      z = 2 * (h & 15) + ((t + y0 + y) & 1);
-    } else {                                   // columns z0 - 1 and z0 + 32
-      z = h < 48 ? -1 : T;
-      y = 2 * (h & 15) + ((t + y0 + z0 + z) & 1);
-    }
-  };
-  // source values of plane t, fetched one step ahead: owners read their pair
-  // (red and black cell), ring workers their red cell
-  auto fetch_f = [&](int t) -> float2 {
-    const int64_t gplane = (int64_t)(t & m) << (2 * log2n);
-    if (owner)
-      return __ldg(reinterpret_cast<const float2*>(f.p + (gplane | ((int64_t)((y0 + py) & m) << log2n) |
-                                                         (z0 + 2 * kp))));
-    int y, z;
-    red_cell(t, y, z);
-    return make_float2(__ldg(f.p + (gplane | ((int64_t)((y0 + y) & m) << log2n) | ((z0 + z) & m))), 0.0f);
-  };
-  float2 f0 = fetch_f(x0 - 1), f1 = fetch_f(x0);   // sources of planes t and t + 1
-
-  // One plane step t: store the old values of plane t + 1, a barrier, then
-  // the red cells of plane t and the black cells of plane p = t - LAG, whose
-  // red neighbours on planes p - 1 .. p + 1 are complete: with LAG = 2 they
-  // were all computed in earlier steps (one barrier per step); with LAG = 1
-  // plane t is among them and a second barrier separates the two updates.
-  // The prefetch registers alternate between even and odd steps (no register
-  // copies, which would wait for the loads in flight): pa holds plane t + 1
-  // and is refilled with plane t + 3, fa the sources of plane t, refilled
-  // with plane t + 2; fb_t receives the black source of plane t, fb_p holds
-  // that of plane p (the same register as fb_t when LAG = 2).
-  auto black = [&](int p, float fbp) {
-    if (!(owner && p >= x0 && p < x1)) return;
-    const float* Op = Old + (p & (RO - 1)) * PL;
-    const float* Rp = Red + (p & (R - 1)) * PL;      // new red values, planes p - 1, p, p + 1
-    const float* Rm = Red + ((p - 1) & (R - 1)) * PL;
-    const float* Rq = Red + ((p + 1) & (R - 1)) * PL;
-    const int y = py;
-    const int o = (p + y0 + y) & 1;                  // red cell of the pair at z = 2 kp + o
-    const int qr = (y + 2) * EC + 2 * kp + 4;        // first cell of the pair
-    const int q = qr + 1 - o;                        // black cell
-    const float nb[6] = {Rq[q], Rm[q], Rp[q + EC], Rp[q - EC], Rp[q + 1], Rp[q - 1]};
-    const float vb = upd(Op[q], nb, fbp, 0, false, own_old);
-    const float vr = Rp[qr + o];
-    const float2 out = o ? make_float2(vb, vr) : make_float2(vr, vb);
-    *reinterpret_cast<float2*>(uout + (((int64_t)(p & m) << (2 * log2n)) | ((int64_t)((y0 + y) & m) << log2n) |
-                                       (z0 + 2 * kp))) = out;
-  };
-  auto red = [&](int t, float2 f_t, float& fb_t) {
-    if (t > x1) return;
-    const float* Om = Old + ((t - 1) & (RO - 1)) * PL;   // old values, planes t - 1, t, t + 1
-    const float* O0 = Old + (t & (RO - 1)) * PL;
-    const float* Oq = Old + ((t + 1) & (RO - 1)) * PL;
-    int y, z;
-    red_cell(t, y, z);
-    const int q = (y + 2) * EC + z + 4;
-    const float nb[6] = {Oq[q], Om[q], O0[q + EC], O0[q - EC], O0[q + 1], O0[q - 1]};
-    float fv;
-    if (owner) {
-      const bool red_first = ((t + y0 + y) & 1) == 0;
-      fv = f.s * ((red_first ? f_t.x : f_t.y) - mean);
-      fb_t = f.s * ((red_first ? f_t.y : f_t.x) - mean);
-    } else {
-      fv = f.s * (f_t.x - mean);
-    }
-    Red[(t & (R - 1)) * PL + q] = upd(O0[q], nb, fv, 0, nb_old_red, own_old);
-  };
-  auto step = [&](int t, float4& pa, float2& fa, float& fb_t, float& fb_p) {
-    if (!zero && loader && t + 1 <= x1 + 1) {
-      store(t + 1, pa);
-      if (t + 3 <= x1 + 1) pa = fetch(t + 3);
-    }
-    const float2 f_t = fa;
-    if (t + 2 <= x1) fa = fetch_f(t + 2);
-    __syncthreads();
-    if constexpr (LAG == 2) {
-      black(t - 2, fb_p);       // fb_p is fb_t: read before red() replaces it
-      red(t, f_t, fb_t);
-    } else {
-      red(t, f_t, fb_t);
-      __syncthreads();
-      black(t - 1, fb_p);
-    }
-  };
-  float fb0 = 0.0f, fb1 = 0.0f;
-  for (int t = x0 - 1; t <= x1 + LAG - 1; t += 2) {
-    step(t, pre0, f0, fb0, LAG == 2 ? fb0 : fb1);
-    if (t + 1 <= x1 + LAG - 1) step(t + 1, pre1, f1, fb1, LAG == 2 ? fb1 : fb0);
-  }
-}
 
 // Work decomposition: x chunk for a level of size n (n >= 128): enough CTAs
-// for about eight waves of two resident CTAs per SM (the tail wave is then a
-// small part of the sweep), chunks of at least 16 planes (each chunk
-// recomputes two red planes at its ends).
+// for about eight waves of two CTAs per SM (the tail wave is then a small
+// part of the sweep), chunks of at least 16 planes (each chunk recomputes two
+// red planes at its ends).
 inline int fused_chunk(int n) {
   const int tiles = (n / kFusedT) * (n / kFusedT);
   int c = n;
@@ -207,10 +61,207 @@ inline int fused_chunk(int n) {
 // boxes (enough CTAs to fill the GPU).
 inline bool fused_ok(int n, int B = 1) { return n >= 128 || (n >= 64 && B >= 8); }
 
-// float4 plane loads, float2 source loads and pair stores need 16- and 8-byte
-// aligned level arrays (workspace levels always are; caller arrays may not be).
+// float4 plane, source and run loads and stores need 16-byte aligned level
+// arrays (workspace levels always are; caller arrays are checked on entry).
 inline bool fused_aligned(const float* u, const float* alt, const float* f) {
-  return (((uintptr_t)u | (uintptr_t)alt) & 15) == 0 && ((uintptr_t)f & 7) == 0;
+  return (((uintptr_t)u | (uintptr_t)alt | (uintptr_t)f) & 15) == 0;
+}
+
+}  // namespace pmgb
+
+namespace pmgb {
+
+constexpr int kQuadRuns = 8 * kFusedT;                 // 256 run owners
+constexpr int kQuadThreads = kQuadRuns + 64;           // + 64 ring cells
+constexpr int kQuadExtra = kFusedLoads - kQuadThreads; // plane loads taken by a second thread set
+static_assert(kQuadExtra > 0 && kQuadExtra <= kQuadThreads, "two float4 plane loads per thread at most");
+
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc) {
+  const uint32_t d = (uint32_t)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit_group() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_group2() { asm volatile("cp.async.wait_group 2;\n" ::: "memory"); }
+
+// Update functor interface: upd(old, nb[6] (x+, x-, y+, y-, z+, z-), source,
+// sweep index (0 here), neighbours-never-updated, own-never-updated).  first:
+// this is the first sweep of the level in the cycle (values never updated
+// yet take the functor's warm-start factor); zero: the level's values are
+// taken as 0 (nothing is loaded).  MINB: resident CTAs per SM the register
+// allocation is sized for.
+template <class Upd, int MINB>
+__global__ void __launch_bounds__(kQuadThreads, MINB) k_rb_fused4(const float* __restrict__ uin,
+                                                                 float* __restrict__ uout, Src f, int log2n,
+                                                                 int chunk, int zero, int first, Upd upd) {
+  constexpr int T = kFusedT, EC = kFusedEC, PL = kFusedPL, R = kFusedRing, RO = kFusedRingOld;
+  extern __shared__ float4 fsm4[];
+  float* Old = reinterpret_cast<float*>(fsm4);   // [RO][ER][EC]
+  float* Red = Old + RO * PL;                    // [R][ER][EC]
+  const uint32_t n = 1u << log2n, m = n - 1;
+  const uint32_t tiles_z = n / T, tiles = (n / T) * tiles_z;
+  const uint32_t item = blockIdx.x;
+  {   // the box of a batched launch
+    const int64_t off = (int64_t)blockIdx.z << (3 * log2n);
+    uin += off;
+    uout += off;
+    f = box_src(f, (int64_t)1 << (3 * log2n));
+    upd = upd.box(blockIdx.z);
+  }
+  const uint32_t tile = item % tiles, xc = item / tiles;
+  const uint32_t y0 = (tile / tiles_z) * T, z0 = (tile % tiles_z) * T;
+  const int x0 = (int)(xc * chunk), x1 = x0 + chunk;
+  const float mean = f.mean ? (float)*f.mean : 0.0f;
+  const int tid = threadIdx.x;
+  const int sh2 = 2 * log2n;
+  // offsets inside one box are below 2^30 (n <= 1024): 32-bit arithmetic
+  auto plane = [&](int t) -> uint32_t { return ((uint32_t)t & m) << sh2; };
+
+  // plane loads: float4 number tid, and tid + kQuadExtra for the last
+  // kQuadExtra threads (rows y0-2 .. y0+33, columns z0-4 .. z0+35)
+  const bool two = tid >= kQuadThreads - kQuadExtra;
+  auto goff = [&](int idx) -> uint32_t {
+    const int lr = idx / (EC / 4), lc4 = idx - lr * (EC / 4);
+    return (((y0 - 2 + lr) & m) << log2n) | ((z0 - 4 + 4 * lc4) & m);
+  };
+  auto soff = [&](int idx) -> int {
+    const int lr = idx / (EC / 4), lc4 = idx - lr * (EC / 4);
+    return lr * EC + 4 * lc4;
+  };
+  const uint32_t g1 = goff(tid), g2 = two ? goff(tid + kQuadExtra) : 0u;
+  const int s1 = soff(tid), s2 = two ? soff(tid + kQuadExtra) : 0;
+  auto issue = [&](int t) {   // asynchronous copy of old plane t into its ring slot
+    const uint32_t pt = plane(t);
+    float* sp = Old + (t & (RO - 1)) * PL;
+    cp_async16(sp + s1, uin + (pt | g1));
+    if (two) cp_async16(sp + s2, uin + (pt | g2));
+  };
+
+  if (zero) {
+    for (int i = tid; i < RO * PL; i += kQuadThreads) Old[i] = 0.0f;
+  } else {
+    for (int t = x0 - 2; t <= x0 + 1; ++t) {
+      if (t <= x1 + 1) issue(t);
+      cp_async_commit_group();
+    }
+  }
+
+  // run owners: row qy, first column qz (local); ring workers: task h
+  const bool run = tid < kQuadRuns;
+  const int lane = tid & 31, warp = tid >> 5;
+  const int qy = (warp >> 1) * 8 + 2 * (lane >> 3) + (warp & 1), qz = 4 * (lane & 7);
+  const int qs = (qy + 2) * EC + qz + 4;                        // stored position of the run
+  const uint32_t ro = (((y0 + qy) & m) << log2n) | (z0 + qz);   // its offset inside a plane
+  const int h = tid - kQuadRuns;
+  // the red ring cell (local y, z) of worker h on plane t
+  auto ring_cell = [&](int t, int& y, int& z) {
+    if (h < 32) {                              // rows y0 - 1 and y0 + 32
+      y = h < 16 ? -1 : T;
+      z = 2 * (h & 15) + ((t + y0 + y) & 1);
+    } else {                                   // columns z0 - 1 and z0 + 32
+      z = h < 48 ? -1 : T;
+      y = 2 * (h & 15) + ((t + y0 + z0 + z) & 1);
+    }
+  };
+  // sources of plane t: a run's four cells, a ring worker's red cell
+  auto fetch_f = [&](int t) -> float4 {
+    if (run) return __ldg(reinterpret_cast<const float4*>(f.p + (plane(t) | ro)));
+    int y, z;
+    ring_cell(t, y, z);
+    return make_float4(__ldg(f.p + (plane(t) | (((y0 + y) & m) << log2n) | ((z0 + z) & m))), 0.0f, 0.0f, 0.0f);
+  };
+  auto src = [&](float v) { return f.s * (v - mean); };
+  const bool own_old = first != 0;
+  auto upd_red = [&](float old, const float nb[6], float fv) -> float {
+    return upd(old, nb, fv, 0, own_old, own_old);   // red neighbours are old values too
+  };
+  auto upd_black = [&](float old, const float nb[6], float fv) -> float {
+    return upd(old, nb, fv, 0, false, own_old);     // black neighbours are new red values
+  };
+
+  // black cells of plane p on the run, from the new red values of planes
+  // p - 1 .. p + 1; fb: the raw sources of the two black cells
+  auto black = [&](int p, float2 fb) {
+    if (!(run && p >= x0 && p < x1)) return;
+    const float* Rp = Red + (p & (R - 1)) * PL + qs;
+    const float4 A = *reinterpret_cast<const float4*>(Red + ((p + 1) & (R - 1)) * PL + qs);
+    const float4 B = *reinterpret_cast<const float4*>(Red + ((p - 1) & (R - 1)) * PL + qs);
+    const float4 C = *reinterpret_cast<const float4*>(Rp + EC);
+    const float4 D = *reinterpret_cast<const float4*>(Rp - EC);
+    const float4 E = *reinterpret_cast<const float4*>(Rp);
+    const float4 O = *reinterpret_cast<const float4*>(Old + (p & (RO - 1)) * PL + qs);
+    float4 out;
+    if (((p + y0 + qy) & 1) == 0) {            // black cells z + 1, z + 3
+      const float nb1[6] = {A.y, B.y, C.y, D.y, E.z, E.x};
+      const float nb3[6] = {A.w, B.w, C.w, D.w, Rp[4], E.z};
+      out = make_float4(E.x, upd_black(O.y, nb1, src(fb.x)), E.z,
+                        upd_black(O.w, nb3, src(fb.y)));
+    } else {                                   // black cells z, z + 2
+      const float nb0[6] = {A.x, B.x, C.x, D.x, E.y, Rp[-1]};
+      const float nb2[6] = {A.z, B.z, C.z, D.z, E.w, E.y};
+      out = make_float4(upd_black(O.x, nb0, src(fb.x)), E.y,
+                        upd_black(O.z, nb2, src(fb.y)), E.w);
+    }
+    *reinterpret_cast<float4*>(uout + (plane(p) | ro)) = out;
+  };
+  // red cells of plane t (run or ring cell) from the old values of planes
+  // t - 1 .. t + 1; fb receives the raw sources of the run's black cells
+  auto red = [&](int t, float4 F, float2& fb) {
+    if (t > x1) return;
+    const float* Om = Old + ((t - 1) & (RO - 1)) * PL;
+    const float* O0 = Old + (t & (RO - 1)) * PL;
+    const float* Oq = Old + ((t + 1) & (RO - 1)) * PL;
+    float* Rt = Red + (t & (R - 1)) * PL;
+    if (run) {
+      const float4 A = *reinterpret_cast<const float4*>(Oq + qs);
+      const float4 B = *reinterpret_cast<const float4*>(Om + qs);
+      const float4 C = *reinterpret_cast<const float4*>(O0 + qs + EC);
+      const float4 D = *reinterpret_cast<const float4*>(O0 + qs - EC);
+      const float4 E = *reinterpret_cast<const float4*>(O0 + qs);
+      float4 out;
+      if (((t + y0 + qy) & 1) == 0) {          // red cells z, z + 2
+        const float nb0[6] = {A.x, B.x, C.x, D.x, E.y, O0[qs - 1]};
+        const float nb2[6] = {A.z, B.z, C.z, D.z, E.w, E.y};
+        out = make_float4(upd_red(E.x, nb0, src(F.x)), E.y,
+                          upd_red(E.z, nb2, src(F.z)), E.w);
+        fb = make_float2(F.y, F.w);
+      } else {                                 // red cells z + 1, z + 3
+        const float nb1[6] = {A.y, B.y, C.y, D.y, E.z, E.x};
+        const float nb3[6] = {A.w, B.w, C.w, D.w, O0[qs + 4], E.z};
+        out = make_float4(E.x, upd_red(E.y, nb1, src(F.y)), E.z,
+                          upd_red(E.w, nb3, src(F.w)));
+        fb = make_float2(F.x, F.z);
+      }
+      *reinterpret_cast<float4*>(Rt + qs) = out;
+    } else {
+      int y, z;
+      ring_cell(t, y, z);
+      const int q = (y + 2) * EC + z + 4;
+      const float nb[6] = {Oq[q], Om[q], O0[q + EC], O0[q - EC], O0[q + 1], O0[q - 1]};
+      Rt[q] = upd_red(O0[q], nb, src(F.x));
+    }
+  };
+  // One plane step t: the old plane t + 3 is put in flight, plane t + 1 has
+  // landed (at most the two newest copy groups pending), a barrier, then the
+  // black cells of plane t - 2 (their red neighbours on planes t - 3 .. t - 1
+  // were computed in earlier steps) and the red cells of plane t.
+  auto step = [&](int t, float4& Fa, float2& fb) {
+    if (!zero) {
+      if (t + 3 <= x1 + 1) issue(t + 3);
+      cp_async_commit_group();
+      cp_async_wait_group2();
+    }
+    const float4 F_t = Fa;
+    if (t + 2 <= x1) Fa = fetch_f(t + 2);
+    __syncthreads();
+    black(t - 2, fb);   // fb holds plane t - 2's black sources: read before red() replaces it
+    red(t, F_t, fb);
+  };
+  float4 F0 = fetch_f(x0 - 1), F1 = fetch_f(x0);
+  float2 fb0 = make_float2(0.0f, 0.0f), fb1 = fb0;
+  for (int t = x0 - 1; t <= x1 + 1; t += 2) {
+    step(t, F0, fb0);
+    if (t + 1 <= x1 + 1) step(t + 1, F1, fb1);
+  }
 }
 
 }  // namespace pmgb
