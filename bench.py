@@ -1,15 +1,21 @@
 """Throughput of the PM step (particle-steps/s) on the 512^3 Hu-Sawicki f(R)
 configuration: 512^3 particles on a 512^3 grid, L = 512 Mpc/h, Omega_m = 0.3,
-sigma8 = 0.8, f_R0 = -1e-5, 2LPT initial conditions at z = 30 (seed 5), steps
-uniform in ln a.  One step = cell sort, TSC deposit, one FAS F-cycle for the
-scalaron beside two warm-started Poisson V-cycles (the cold first step
-iterates to a relative residual of 1e-7), gradient of the combined potential,
-inverse TSC, kick and drift.  Beside it: the same step through the C ABI with
-host buffers (e2e), per-kernel-class CUDA-event times from further steps with
-both solvers on one stream (the roofline of the dominant class), the
-Newtonian, FFT_7pt, n = 2 and parametrised-gravity steps on the same
-particles, the differentiable 128^3 run, the 64-box ensemble and the FP64
-oracle on a bounded sample.
+sigma8 = 0.8, f_R0 = -1e-5, 2LPT initial conditions at z = 30 (seed 5), 100
+steps uniform in ln a to z = 0.  One step = cell sort, TSC deposit, one FAS
+F-cycle for the scalaron beside two warm-started Poisson V-cycles (the cold
+first step iterates to a relative residual of 1e-7), gradient of the combined
+potential, inverse TSC, kick and drift.
+
+The headline times steps W .. W+K-1 (--warmup W, --steps K) of one run of the
+whole schedule, which is timed in segments: the line also gives the late
+window (steps 90-99, z < 0.1) and the mean over all 100 steps.  Beside it,
+each from a fresh start over the same window: per-kernel-class CUDA-event
+times with both solvers on one stream (the roofline of the dominant class),
+the same step through the C ABI with host buffers (e2e), and the Newtonian,
+FFT_7pt, n = 2 and parametrised-gravity steps; then the differentiable 128^3
+run, the 64-box ensemble (eager and graph replay over the same steps), and
+the CPU leg: the FP64 oracle on a bounded sample (median of 5 single-core
+runs and an all-core run) and the error of the GPU results against it.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
@@ -187,13 +193,7 @@ def load_ncu_traffic():
 ORACLE_N = 64   # oracle sample: 64^3 particles on a 64^3 grid (a few seconds of one core per step)
 
 
-def oracle_sample(steps, n=ORACLE_N):
-    """The FP64 oracle, unchanged, on a bounded sample of the workload: n^3
-    particles on an n^3 grid in an n Mpc/h box (the 1 Mpc/h cells of the
-    512^3 run), same cosmology, f_R0 and 2LPT start at z = 30, advanced through
-    the first ``steps`` steps of the same schedule with f(R) forces (exact
-    discrete Poisson inverse, one FAS F-cycle) and kick-drift-kick.  Returns
-    (particle-steps/s, seconds, sample description)."""
+def _oracle_setup(steps, n=ORACLE_N):
     for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
         os.environ.setdefault(v, "1")
     from oracle import mesh, step
@@ -201,12 +201,124 @@ def oracle_sample(steps, n=ORACLE_N):
     X, V = inputs.lpt_ics(n, float(n), OM, OL, 1.0 / (1.0 + Z_INI), SEED, order=2)
     prm = step.PMParams(n=n, Om=OM, OL=OL, boxsize=float(n), gravity="fr", fR0=FR0)
     a = schedule()[:steps + 1]
+    return lambda: step.run_kdk(mesh.positions_from_fixed_point(X), V.T, a, prm, warm_start=False)
+
+
+def oracle_sample(steps, n=ORACLE_N):
+    """The FP64 oracle, unchanged, on a bounded sample of the workload: n^3
+    particles on an n^3 grid in an n Mpc/h box (the 1 Mpc/h cells of the
+    512^3 run), same cosmology, f_R0 and 2LPT start at z = 30, advanced through
+    the first ``steps`` steps of the same schedule with f(R) forces (exact
+    discrete Poisson inverse, one FAS F-cycle) and kick-drift-kick.  Returns
+    (particle-steps/s, seconds, sample description)."""
+    run = _oracle_setup(steps, n)
     t0 = time.perf_counter()
-    step.run_kdk(mesh.positions_from_fixed_point(X), V.T, a, prm, warm_start=False)
+    run()
     dt = time.perf_counter() - t0
     return n ** 3 * steps / dt, dt, (f"FP64 oracle, {steps} f(R) PM steps (deposit, exact 7-point Poisson "
                                      f"inverse, one FAS F-cycle, 5-point gradient, inverse TSC, KDK) of {n}^3 "
                                      f"particles on a {n}^3 grid with the 1 Mpc/h cells of the 512^3 run")
+
+
+def _oracle_core(steps, start, queue):
+    """One core of the all-core baseline: set up, wait for the others, run."""
+    run = _oracle_setup(steps)
+    start.wait()
+    t0 = time.time()
+    run()
+    queue.put((t0, time.time()))
+
+
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else platform)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def cpu_baseline(steps=6, runs=5):
+    """The oracle on the host cores: the median of ``runs`` single-core runs of
+    the bounded sample, and one all-core run (one independent sample per core,
+    in spawned processes that set up, meet at a barrier and then run; timed
+    from the first start to the last finish).  Returns the cpu_baseline
+    object."""
+    single = [oracle_sample(steps) for _ in range(runs)]
+    secs = sorted(r[1] for r in single)
+    med = secs[len(secs) // 2]
+    ncores = os.cpu_count() or 1
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    start, queue = ctx.Barrier(ncores), ctx.Queue()
+    procs = [ctx.Process(target=_oracle_core, args=(steps, start, queue)) for _ in range(ncores)]
+    for p in procs:
+        p.start()
+    spans = [queue.get() for _ in procs]
+    for p in procs:
+        p.join()
+    wall = max(t1 for _, t1 in spans) - min(t0 for t0, _ in spans)
+    per = ORACLE_N ** 3 * steps
+    return {"value": per / med, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
+            "sample": single[0][2], "runs": runs, "seconds_median": med, "seconds_all_runs": secs,
+            "all_cores": {"value": ncores * per / wall, "cores": ncores, "seconds": wall,
+                          "what": f"{ncores} independent samples at once, one per core (spawned processes)"},
+            "nproc": ncores, "cpu_model": cpu_model()}
+
+
+def oracle_errors(probes):
+    """Error of the GPU results against the FP64 oracle, from the probes the
+    GPU passes saved (plain arrays): sampled accelerations of the 512^3 steps
+    (the oracle's Table 1 gradient and inverse TSC of the GPU's own phi and
+    eps on the 7^3 cells around each sampled particle), and the accelerations
+    of two ensemble boxes in a warm batched step (the oracle's exact-Poisson
+    accelerations at the same positions)."""
+    from oracle import fr as ofr
+    from oracle import mesh, step
+    out = {}
+    for name, p in probes.items():
+        if p["kind"] == "patch":
+            n = p["n"]
+            Phi = p["phi"]
+            if p["eps"] is not None:
+                model = ofr.FRModel(Om=OM, OL=OL, fR0=FR0, boxsize=BOX)
+                Phi = Phi + ofr.scalaron_potential(1.0 + p["eps"], p["a"], model)
+            h = 1.0 / n
+            g = [-mesh.derivative(Phi, ax + 1, h, 5) for ax in range(3)]
+            pos = p["pos"]
+            i0 = np.floor(pos * n)
+            off = pos * n - 0.5 - i0
+            w = [np.stack([mesh.w_tsc(off[:, ax] - o) for o in (-1, 0, 1)], axis=1) for ax in range(3)]
+            ref = np.zeros_like(p["acc"])
+            for ox in range(3):
+                for oy in range(3):
+                    for oz in range(3):
+                        wt = w[0][:, ox] * w[1][:, oy] * w[2][:, oz]
+                        for ax in range(3):
+                            ref[:, ax] += wt * g[ax][:, 2 + ox, 2 + oy, 2 + oz]
+            out[name] = {"rel_l2_acc": float(np.linalg.norm(p["acc"] - ref) / np.linalg.norm(ref)),
+                         "what": f"{p['acc'].shape[0]} sampled particles of step {p['step']}, oracle gradient and "
+                                 "inverse TSC of the GPU's own potential(s)"}
+        elif p["kind"] == "boxes":
+            errs = []
+            for b, (pos, acc, Om_b) in enumerate(zip(p["pos"], p["acc"], p["Om"])):
+                ref, _, _ = step.accelerations(pos, p["a"], step.PMParams(n=p["n"], Om=Om_b, OL=1.0 - Om_b,
+                                                                         boxsize=p["boxsize"]))
+                errs.append(float(np.linalg.norm(acc - ref) / np.linalg.norm(ref)))
+            out[name] = {"rel_l2_acc": errs, "boxes": p["boxes"],
+                         "what": "accelerations of a warm batched step (2 V-cycles) against the exact-Poisson "
+                                 "oracle at the same positions"}
+    return out
 
 
 def run_reference(args):
@@ -230,6 +342,9 @@ def run_reference(args):
 
 # ------------------------------------------------------------------ GPU arm --
 
+LATE = 90   # the late window: steps 90-99 of the schedule (z < 0.1)
+
+
 def step_coefficients(Om, OL, a):
     """Per step i of the schedule: (a_i, kick, drift, potential rescale), with
     the two half kicks around a_i merged: kick_i = (dt_{i-1} + dt_i)/2."""
@@ -244,12 +359,16 @@ def step_coefficients(Om, OL, a):
     return out
 
 
-def timed_steps(sim, coeffs, first, count, host_buffers=None):
-    """Runs steps first .. first+count-1; returns (device ms, per-step stats)."""
+def timed_steps(sim, coeffs, first, count, host_buffers=None, world=1):
+    """Runs steps first .. first+count-1 between a barrier and a device
+    synchronisation on both sides; returns (device ms from CUDA events on the
+    launching stream, per-step stats)."""
     import torch
     s = torch.cuda.current_stream()
     start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     stats = []
+    torch.cuda.synchronize()
+    barrier(world)
     start.record(s)
     for i in range(first, first + count):
         a, kick, drift, resc = coeffs[i]
@@ -260,7 +379,50 @@ def timed_steps(sim, coeffs, first, count, host_buffers=None):
             stats.append(sim.step_host(a, kick, drift, Xh, Vh, Xh, Vh, resc))
     end.record(s)
     torch.cuda.synchronize()
+    barrier(world)
     return start.elapsed_time(end), stats
+
+
+def make_sim(pm, X, V, variant, **kw):
+    n = N_GRID
+    mg = pm.default_mg(tol=1e-7, stall=0.5, max_cycles=12, fixed_cycles=2)
+    fr = pm.default_fr(cycle=1, cycles=1, nhs=2 if variant == "fr_n2" else 1)
+    gravity = {"fr": "fr", "fr_n2": "fr", "mu": "mu"}.get(variant, "newton")
+    return pm.Simulation(X, V, n, OM, OL, BOX, gravity=gravity, fR0=FR0, mg=mg, fr=fr,
+                         poisson=pm.PM_POISSON_FFT7 if variant == "newton_fft7" else pm.PM_POISSON_MG,
+                         mu0=MU0 if variant == "mu" else 0.0, **kw)
+
+
+def patch_probe(pm, X, V, variant, coeffs, at, count=10000):
+    """A fresh run of ``variant`` to step ``at`` (untimed), keeping ids and
+    accelerations: the accelerations of step ``at`` at ``count`` sampled
+    particles, their positions, and the 7^3 cells of phi (and eps) around each
+    (plain arrays for the oracle comparison of the CPU leg)."""
+    import torch
+    n = N_GRID
+    sim = make_sim(pm, X, V, variant, track_ids=True, keep_acc=True)
+    for i in range(at):
+        sim.step(*coeffs[i])
+    X_in, id_in = sim.X.clone(), sim.ids.clone().long()
+    sim.step(*coeffs[at])
+    torch.cuda.synchronize()
+    rng = np.random.Generator(np.random.PCG64(91))
+    ranks = torch.from_numpy(rng.choice(n ** 3, count, replace=False)).cuda()
+    where_in = torch.empty_like(id_in)
+    where_in[id_in] = torch.arange(id_in.numel(), device="cuda")
+    src = where_in[sim.ids[ranks].long()]
+    acc = sim.acc[:, ranks].double().cpu().numpy().T
+    pos = (X_in[:, src].cpu().numpy().view(np.uint32).astype(np.float64) * 2.0 ** -32).T
+    i0 = np.floor(pos * n).astype(np.int64)
+    d = np.arange(-3, 4)
+    ii, jj, kk = ((i0[:, ax, None] + d) % n for ax in range(3))
+    flat = (ii[:, :, None, None] * n + jj[:, None, :, None]) * n + kk[:, None, None, :]
+    ft = torch.from_numpy(flat.reshape(-1)).cuda()
+    phi = sim.phi.reshape(-1)[ft].double().cpu().numpy().reshape(flat.shape)
+    eps = None if sim.eps is None else sim.eps.reshape(-1)[ft].double().cpu().numpy().reshape(flat.shape)
+    del sim, X_in, id_in, where_in
+    torch.cuda.empty_cache()
+    return {"kind": "patch", "n": n, "a": coeffs[at][0], "step": at, "acc": acc, "pos": pos, "phi": phi, "eps": eps}
 
 
 def run_adjoint(n=128, fd_dirs=16, reps=3, eps=1.0):
@@ -321,7 +483,10 @@ def run_ensemble(n=64, B=64, steps=50):
     L = 128 Mpc/h, Omega_m ~ U[0.25, 0.35], sigma8 ~ U[0.7, 0.9] (PCG64 seed 3),
     box seeds 1000 + b, 2LPT at z = 30, 50 steps uniform in ln a, stepped
     together by pm_step_batch (2 fixed V-cycles per warm step, 8 on the first).
-    Times the warm steps eagerly and as CUDA-graph replays."""
+    Times the warm steps 2..49 eagerly and, from a fresh start, as CUDA-graph
+    replays of one captured warm step (the same window); then a probe step 4
+    (positions unchanged, velocities zeroed, so V = acc dt_kick) whose
+    accelerations of two boxes the CPU leg compares with the oracle."""
     import torch
     from paper_2410_20501_gb300 import inputs, pm
     w = inputs.ensemble_workload(n=n, B=B, steps=steps, device="cuda")
@@ -334,25 +499,43 @@ def run_ensemble(n=64, B=64, steps=50):
         ens.step(coef[1])
         if mode == "graph":
             ens.capture()
-        last = steps if mode == "graph" else 12
         torch.cuda.synchronize()
         t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         t0.record(s)
-        for i in range(2, last):
+        for i in range(2, steps):
             if mode == "graph":
                 ens.replay_step(coef[i])
             else:
                 ens.step(coef[i])
         t1.record(s)
         torch.cuda.synchronize()
-        ms = t0.elapsed_time(t1) / (last - 2)
-        out[mode] = {"ms_per_step": ms, "value": B * n ** 3 / (ms / 1e3), "steps_timed": last - 2}
+        ms = t0.elapsed_time(t1) / (steps - 2)
+        out[mode] = {"ms_per_step": ms, "value": B * n ** 3 / (ms / 1e3), "steps_timed": f"2..{steps - 1}"}
         del ens
     tuned = [{k: r[k] for k in ("site", "n", "chosen", "samples")} for r in pm.autotune_report() if r["B"] == B]
-    return {"workload": f"{B} boxes x {n}^3 particles/grid, L=128 Mpc/h, Om~U[0.25,0.35], s8~U[0.7,0.9], "
-                        "2LPT z=30, 50 steps in ln a", "unit": "particle-steps/s", **out,
-            "autotune": {"what": "tilings the online tuner chose for this batch (eager steps; the graph "
-                                 "replays the choices)", "sites": tuned}}
+    # probe: steps 0..3, then step 4 with no drift from zeroed velocities
+    ens = pm.Ensemble(w["X"], w["V"], n, w["Om"], w["boxsize"], cold_cycles=8)
+    coef = ens.coefficients(w["a_steps"])
+    for i in range(4):
+        ens.step(coef[i])
+    dtk = 1e-2
+    row = coef[4].clone()
+    row[1, :B] = dtk
+    row[2, :B] = 0.0
+    ens.V.zero_()
+    ens.step(row)
+    Xp, Vp = ens.positions(), ens.velocities()
+    boxes = [0, B - 1]
+    probe = {"kind": "boxes", "n": n, "a": float(w["a_steps"][4]), "boxsize": w["boxsize"], "boxes": boxes,
+             "Om": [float(w["Om"][b]) for b in boxes],
+             "pos": [(Xp[b].astype(np.float64) * 2.0 ** -32).T for b in boxes],
+             "acc": [(Vp[b].astype(np.float64) / np.float32(dtk)).T for b in boxes]}
+    del ens
+    return ({"workload": f"{B} boxes x {n}^3 particles/grid, L=128 Mpc/h, Om~U[0.25,0.35], s8~U[0.7,0.9], "
+                         "2LPT z=30, 50 steps in ln a", "unit": "particle-steps/s", **out,
+             "graph_over_eager": out["graph"]["ms_per_step"] / out["eager"]["ms_per_step"],
+             "autotune": {"what": "tilings the online tuner chose for this batch (eager steps; the graph "
+                                  "replays the choices)", "sites": tuned}}, probe)
 
 
 def run_lpt(n, reps=3):
@@ -394,72 +577,87 @@ def run_gpu(args):
     n = N_GRID
     X, V = inputs.lpt_ics(n, BOX, OM, OL, a[0], SEED + rank, order=2, device="cuda")
     npart = X.shape[1]
-    # warm-started steps: two V-cycles (tests/test_gpu_fullsize.py shows they meet
-    # the 1e-5 acceleration bar at 512^3); the cold first step cycles to tol
-    mg = pm.default_mg(tol=1e-7, stall=0.5, max_cycles=12, fixed_cycles=2)
-    fr = pm.default_fr(cycle=1, cycles=1)
     W, K = args.warmup, args.steps
-    results = {}
-    for variant in (("fr",) if args.lean else ("fr", "newton", "newton_fft7", "fr_n2", "mu")):
-        gravity = {"fr": "fr", "fr_n2": "fr", "mu": "mu"}.get(variant, "newton")
-        sim = pm.Simulation(X, V, n, OM, OL, BOX, gravity=gravity, fR0=FR0, mg=mg,
-                            fr=pm.default_fr(cycle=1, cycles=1, nhs=2) if variant == "fr_n2" else fr,
-                            poisson=pm.PM_POISSON_FFT7 if variant == "newton_fft7" else pm.PM_POISSON_MG,
-                            mu0=MU0 if variant == "mu" else 0.0)
-        timed_steps(sim, coeffs, 0, W)
-        barrier(world)
-        torch.cuda.synchronize()
-        launches0 = pm.launch_count()
-        with ClockSampler(local) as clk:
-            ms, stats = timed_steps(sim, coeffs, W, K)
-        launches = pm.launch_count() - launches0
-        ms = max_over_ranks(ms, world, "cuda")
-        results[variant] = {"ms": ms, "stats": stats, "clocks": clk.summary(), "launches": launches}
-        next_step = W + K
-        if variant == "fr" and not args.lean:
-            # end to end through the C ABI with host buffers: H2D of X, V and D2H of X, V every step
-            Xh = torch.empty((3, npart), dtype=torch.int32).pin_memory()
-            Vh = torch.empty((3, npart), dtype=torch.float32).pin_memory()
-            Xh.copy_(sim.X)
-            Vh.copy_(sim.V)
-            barrier(world)
-            ms_e2e, _ = timed_steps(sim, coeffs, W + K, K, host_buffers=(Xh, Vh))
-            results["e2e_ms"] = max_over_ranks(ms_e2e, world, "cuda")
-            results["e2e_bytes"] = int(Xh.numel() * 4 + Vh.numel() * 4)
-            del Xh, Vh
-            next_step = W + 2 * K
-        if variant == "fr":
-            # per-kernel classes timed alone: the next K steps with both solvers
-            # on one stream (the timed steps above run the scalaron beside the
-            # Poisson solve, where CUDA events would time kernels sharing the GPU)
-            sim.serial = True
-            pm.timing_enable(True)
-            ms_serial, _ = timed_steps(sim, coeffs, next_step, K)
-            results[variant]["kernels"] = pm.timing_collect()
-            results[variant]["ms_serial"] = ms_serial
-            pm.timing_enable(False)
-            sim.serial = False
-        del sim
+    probes = {}
+
+    # f(R), the headline: the whole 100-step schedule in timed segments --
+    # warm-up [0, W), the headline window [W, W+K), the middle and the late
+    # window [90, 100) -- each between barriers and synchronisations
+    sim = make_sim(pm, X, V, "fr")
+    seg = {}
+    seg["warmup"], _ = timed_steps(sim, coeffs, 0, W, world=world)
+    launches0 = pm.launch_count()
+    with ClockSampler(local) as clk:
+        seg["window"], fr_stats = timed_steps(sim, coeffs, W, K, world=world)
+    launches = pm.launch_count() - launches0
+    fr_clocks = clk.summary()
+    seg["middle"], _ = timed_steps(sim, coeffs, W + K, LATE - W - K, world=world)
+    with ClockSampler(local) as clk_late:
+        seg["late"], _ = timed_steps(sim, coeffs, LATE, N_STEPS_RUN - LATE, world=world)
+    seg = {k: max_over_ranks(v, world, "cuda") for k, v in seg.items()}
+    del sim
+    torch.cuda.empty_cache()
+
+    # per-kernel classes on the same window, from a fresh start, with both
+    # solvers on one stream (CUDA events would time kernels sharing the GPU)
+    sim = make_sim(pm, X, V, "fr")
+    sim.serial = True
+    timed_steps(sim, coeffs, 0, W, world=world)
+    pm.timing_enable(True)
+    ms_serial, _ = timed_steps(sim, coeffs, W, K, world=world)
+    kern = pm.timing_collect()
+    pm.timing_enable(False)
+    del sim
+    torch.cuda.empty_cache()
+
+    # end to end through the C ABI with host buffers, same window: H2D of X, V
+    # and D2H of X, V every step
+    e2e_ms, e2e_bytes = None, None
+    if not args.lean:
+        sim = make_sim(pm, X, V, "fr")
+        timed_steps(sim, coeffs, 0, W, world=world)
+        Xh = torch.empty((3, npart), dtype=torch.int32).pin_memory()
+        Vh = torch.empty((3, npart), dtype=torch.float32).pin_memory()
+        Xh.copy_(sim.X)
+        Vh.copy_(sim.V)
+        e2e_ms, _ = timed_steps(sim, coeffs, W, K, host_buffers=(Xh, Vh), world=world)
+        e2e_ms = max_over_ranks(e2e_ms, world, "cuda")
+        e2e_bytes = int(Xh.numel() * 4 + Vh.numel() * 4)
+        del sim, Xh, Vh
         torch.cuda.empty_cache()
+
+    # the other gravity and solver forms on the same window
+    variants = {}
+    if not args.lean:
+        for variant in ("newton", "newton_fft7", "fr_n2", "mu"):
+            sim = make_sim(pm, X, V, variant)
+            timed_steps(sim, coeffs, 0, W, world=world)
+            l0 = pm.launch_count()
+            ms, st = timed_steps(sim, coeffs, W, K, world=world)
+            variants[variant] = {"ms": max_over_ranks(ms, world, "cuda"), "stats": st,
+                                 "launches": pm.launch_count() - l0}
+            del sim
+            torch.cuda.empty_cache()
+    if rank == 0 and not args.lean and not args.no_cpu_baseline:
+        for variant in ("fr", "newton", "newton_fft7"):
+            probes[variant] = patch_probe(pm, X, V, variant, coeffs, W)
     if rank != 0:
         return 0
 
-    fr_res, nw_res, ft_res = results["fr"], results.get("newton"), results.get("newton_fft7")
-    n2_res, mu_res = results.get("fr_n2"), results.get("mu")
     total = world * npart * K
-    value = total / (fr_res["ms"] / 1e3)
+    value = total / (seg["window"] / 1e3)
     peak, peak_kind = load_peaks()
-    kern = fr_res["kernels"]
     dom = max(kern.items(), key=lambda kv: kv[1][0])
     dname, (dms, dcount, dbytes) = dom
     traffic = load_ncu_traffic().get(dname)
     achieved = (dbytes / dcount) / (dms / dcount / 1e3) / 1e9 if dcount else None
-    roof = {"bound": "hbm", "kernel": dname, "timed": "per-class CUDA events, both solvers on one stream", "achieved": achieved, "peak": peak, "unit": "GB/s",
+    roof = {"bound": "hbm", "kernel": dname, "timed": f"per-class CUDA events, steps {W}..{W + K - 1} with both "
+            "solvers on one stream", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak if achieved else None,
             "traffic": traffic.get("bytes_per_launch") if traffic else None,
             "peak_source": peak_kind,
             "launches": dcount, "avg_launch_ms": dms / dcount if dcount else None,
-            "share_of_step": dms / fr_res["ms_serial"] if fr_res["ms_serial"] else None}
+            "share_of_step": dms / ms_serial if ms_serial else None}
     mg_classes = [k for k in kern if k.startswith("mg_")]
     mg_ms = sum(kern[k][0] for k in mg_classes)
     mg_bytes = sum(kern[k][2] for k in mg_classes)
@@ -468,50 +666,62 @@ def run_gpu(args):
               "what": "algorithmic bytes of every Poisson multigrid kernel (all levels, smoothing, transfers, "
                       "coarsest solve) / their CUDA-event time, 512^3"}
     per_kernel = {k: {"ms": round(v[0], 4), "launches": v[1],
-                      "GB/s": round(v[2] / (v[0] / 1e3) / 1e9, 1) if v[0] > 0 else None}
+                      "GB/s": round(v[2] / (v[0] / 1e3) / 1e9, 1) if v[0] > 0 else None,
+                      "share_of_step": round(v[0] / ms_serial, 4) if ms_serial else None}
                   for k, v in kern.items() if v[1] > 0}
+
+    def vline(key, what):
+        r = variants.get(key)
+        if r is None:
+            return None
+        out = {"value": total / (r["ms"] / 1e3), "ms_per_step": r["ms"] / K, "gpu_launches": r["launches"],
+               "what": what}
+        if key == "newton":
+            out["mg_cycles"] = [s["mg"]["cycles"] for s in r["stats"]]
+        return out
+
+    late_n = N_STEPS_RUN - LATE
+    full_ms = sum(seg.values())
     line = {
         "metric": METRIC, "value": value, "unit": "particle-steps/s", "n_gpus": world, "steps": K,
-        "warmup": W, "ms_per_step": fr_res["ms"] / K, "higher_is_better": True, "scaling": "weak",
+        "warmup": W, "ms_per_step": seg["window"] / K, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": "hu-sawicki f(R) n=1 pm step, 512^3 particles, 512^3 grid, L=512 Mpc/h, "
                                "2LPT z=30", "global_batch": world * npart, "n_grid": n, "boxsize_mpc_h": BOX,
                    "fR0": FR0, "parallelism": f"replicas{world}", "l2": "inputs larger than L2 (every array "
                    ">= 537 MB)", "poisson": "2 warm-started V-cycles per step (first step: to relative residual 1e-7)",
                    "fr": "one FAS F-cycle per step"},
-        "newton": None if nw_res is None else {
-            "value": total / (nw_res["ms"] / 1e3), "ms_per_step": nw_res["ms"] / K,
-            "gpu_launches": nw_res["launches"], "mg_cycles": [s["mg"]["cycles"] for s in nw_res["stats"]]},
-        "newton_fft7": None if ft_res is None else {
-            "value": total / (ft_res["ms"] / 1e3), "ms_per_step": ft_res["ms"] / K,
-            "gpu_launches": ft_res["launches"],
-            "what": "Newtonian step with the FFT_7pt Poisson solve (the exact 7-point inverse) instead of multigrid"},
-        "fr_n2": None if n2_res is None else {
-            "value": total / (n2_res["ms"] / 1e3), "ms_per_step": n2_res["ms"] / K,
-            "gpu_launches": n2_res["launches"],
-            "what": "the same step with the Hu-Sawicki n = 2 scalaron (quartic per cell)"},
-        "mu": None if mu_res is None else {
-            "value": total / (mu_res["ms"] / 1e3), "ms_per_step": mu_res["ms"] / K,
-            "gpu_launches": mu_res["launches"],
-            "what": f"the Newtonian step with parametrised gravity, mu0 = {MU0}"},
-        "mg_cycles": [s["mg"]["cycles"] for s in fr_res["stats"]],
-        "serial_ms_per_step": fr_res["ms_serial"] / K,
-        "e2e": None if "e2e_ms" not in results else {
-            "value": total / (results["e2e_ms"] / 1e3), "unit": "particle-steps/s",
-            "h2d_bytes_per_step": results["e2e_bytes"], "d2h_bytes_per_step": results["e2e_bytes"]},
-        "gpu_launches": fr_res["launches"],
+        "window": {"steps": f"{W}..{W + K - 1}", "z": [1.0 / a[W] - 1.0, 1.0 / a[W + K - 1] - 1.0],
+                   "what": "the headline's steps of the 100-step schedule uniform in ln a from z = 30"},
+        "late": {"steps": f"{LATE}..{N_STEPS_RUN - 1}", "z": [1.0 / a[LATE] - 1.0, 1.0 / a[N_STEPS_RUN - 1] - 1.0],
+                 "ms_per_step": seg["late"] / late_n, "value": world * npart * late_n / (seg["late"] / 1e3),
+                 "clocks": clk_late.summary()},
+        "full_run_ms_per_step": full_ms / N_STEPS_RUN,
+        "full_run": {"value": world * npart * N_STEPS_RUN / (full_ms / 1e3), "seconds": full_ms / 1e3,
+                     "what": "all 100 steps of the schedule (the first iterates the Poisson solve to 1e-7 from "
+                             "the Jacobi guess)"},
+        "newton": vline("newton", "Newtonian step, multigrid, same window"),
+        "newton_fft7": vline("newton_fft7", "Newtonian step with the FFT_7pt Poisson solve (the exact 7-point "
+                                            "inverse) instead of multigrid, same window"),
+        "fr_n2": vline("fr_n2", "the same step with the Hu-Sawicki n = 2 scalaron (quartic per cell)"),
+        "mu": vline("mu", f"the Newtonian step with parametrised gravity, mu0 = {MU0}"),
+        "mg_cycles": [s["mg"]["cycles"] for s in fr_stats],
+        "serial_ms_per_step": ms_serial / K,
+        "e2e": None if e2e_ms is None else {
+            "value": total / (e2e_ms / 1e3), "unit": "particle-steps/s",
+            "h2d_bytes_per_step": e2e_bytes, "d2h_bytes_per_step": e2e_bytes},
+        "gpu_launches": launches,
         "roofline": roof,
         "vcycle_hbm": vcycle,
         "kernels": per_kernel,
-        "clocks": fr_res["clocks"],
+        "clocks": fr_clocks,
     }
     if world == 1 and not args.lean:
         line["adjoint"] = run_adjoint()
-        line["ensemble"] = run_ensemble()
+        line["ensemble"], probes["ensemble"] = run_ensemble()
     if world == 1 and not args.no_cpu_baseline and not args.lean:
-        cv, secs, sample = oracle_sample(16)
-        line["cpu_baseline"] = {"value": cv, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
-                                "sample": sample, "seconds": secs}
+        line["cpu_baseline"] = cpu_baseline()
+        line["oracle_error"] = oracle_errors(probes)
     print(json.dumps(line))
     return 0
 
@@ -626,8 +836,8 @@ def main():
         return run_stage(args)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
-    if args.warmup + 3 * args.steps > N_STEPS_RUN:
-        ap.error(f"--warmup + 3 * --steps must be <= {N_STEPS_RUN} (the step schedule's length)")
+    if args.warmup + args.steps > LATE:
+        ap.error(f"--warmup + --steps must be <= {LATE} (the late window is steps {LATE}..{N_STEPS_RUN - 1})")
     if args.impl == "reference":
         return run_reference(args)
     return run_gpu(args)
