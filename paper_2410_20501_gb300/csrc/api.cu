@@ -96,6 +96,7 @@ size_t layout_workspace(Workspace* w, void* base, int n, int64_t np, uint32_t fl
     w->keyrank = (uint2*)take(2 * kb);
     w->perm = (uint32_t*)take(kb);
     w->runs = (uint32_t*)take((size_t)sort_runs_capacity(np) * 4);
+    w->meds = (uint32_t*)take((size_t)sort_meds_capacity(np) * 4);
     w->scan_blocks = (uint32_t*)take((size_t)sort_scan_blocks(N) * 4);
     w->cellstart = (uint32_t*)take((size_t)(N + 1) * 4);
     w->Xs = (uint32_t*)take(3 * kb);
@@ -204,6 +205,11 @@ pm_status check_ws(Workspace& w, void* ws, size_t ws_bytes, int n, int64_t np, u
 }
 
 bool valid_np(int64_t np) { return np >= 0 && np < ((int64_t)1 << 31); }
+
+// The crowded cells of the workspace's last cell sort, with the sort's key
+// buffer (8 bytes per particle, unused until the next sort) as the moment
+// scratch.
+Crowded crowded(const Workspace& w) { return Crowded{w.runs, w.meds, reinterpret_cast<float*>(w.keyrank)}; }
 
 // 3/2 a Om of the supercomoving Poisson equation (§3.1), times mu(a) =
 // 1 + mu0 Omega_L(a)/Omega_L,0 = 1 + mu0 / E(a)^2 for parametrised gravity.
@@ -326,7 +332,7 @@ pm_status pm_deposit(const uint32_t* X, int64_t np, int n, float* rho, void* ws,
   uint32_t* p;
   PM_TRY(sort_cells(X, np, n, w, s, w.cellstart, &p));
   PM_TRY(permute_particles(p, np, X, nullptr, nullptr, w.Xs, nullptr, nullptr, s));
-  PM_TRY(deposit_sorted(w.Xs, np, w.cellstart, n, rho, w.partials, w.scalars, s));
+  PM_TRY(deposit_sorted(w.Xs, np, w.cellstart, n, rho, w.partials, w.scalars, s, crowded(w)));
   return launch_status();
 }
 
@@ -437,7 +443,7 @@ pm_status step_impl(pm_state* st_, const pm_step_params* prm, pm_stats* stats, v
   uint32_t* perm;
   PM_TRY(sort_cells(S.X, np, n, w, s, w.cellstart, &perm));
   PM_TRY(permute_particles(perm, np, S.X, V_host ? nullptr : S.V, S.id, w.Xs, V_host ? nullptr : w.Vs, w.ids, s));
-  PM_TRY(deposit_sorted(w.Xs, np, w.cellstart, n, w.rho, w.partials, w.scalars, s));
+  PM_TRY(deposit_sorted(w.Xs, np, w.cellstart, n, w.rho, w.partials, w.scalars, s, crowded(w)));
 
   double fbar = 0.0, kappa = 0.0, c2 = 0.0;
   pm_status solve_status = PM_OK;
@@ -571,7 +577,7 @@ pm_status pm_interp_adj(const float* g, const uint32_t* X, int64_t np, int n, co
   PM_TRY(permute_particles(perm, np, X, acc_bar, nullptr, w.Xs, w.adj_abar, nullptr, s));
   for (int d = 0; d < 3; ++d)
     PM_TRY(deposit_sorted_values(w.Xs, np, w.cellstart, n, w.adj_abar + d * np, 1.0f, g_bar + d * N, w.partials,
-                                 w.scalars + 12, s));
+                                 w.scalars + 12, s, crowded(w)));
   return pos_grad_launch(X, np, n, g, acc_bar, nullptr, 0.0f, nullptr, nullptr, 0.0f, nullptr, dX_bar, nullptr, s);
 }
 
@@ -613,7 +619,7 @@ pm_status pm_step_adj(pm_state* st_, const pm_step_params* prm, const float* phi
   const float src_scale = (float)poisson_scale(*prm);
   const float* phi = phi_fwd;
   if (!phi) {
-    PM_TRY(deposit_sorted(w.Xs, np, w.cellstart, n, w.rho, w.partials, w.scalars, s));
+    PM_TRY(deposit_sorted(w.Xs, np, w.cellstart, n, w.rho, w.partials, w.scalars, s, crowded(w)));
     pm_status r = mg_solve_src(Src{w.rho, src_scale, w.scalars}, w.adj_phi, n, mp, nullptr, w, s);
     if (r != PM_OK && r != PM_ENOCONV) return r;
     phi = w.adj_phi;
@@ -624,7 +630,7 @@ pm_status pm_step_adj(pm_state* st_, const pm_step_params* prm, const float* phi
   const int64_t N = (int64_t)n * n * n;
   for (int d = 0; d < 3; ++d)
     PM_TRY(deposit_sorted_values(w.Xs, np, w.cellstart, n, w.adj_abar + d * np, 1.0f, w.adj_gbar + d * N,
-                                 w.partials, w.scalars + 12, s));
+                                 w.partials, w.scalars + 12, s, crowded(w)));
   PM_TRY(divergence_launch(w.adj_gbar, w.rho, n, prm->grad_order, s));   // phi_bar, in the rho buffer
   PM_TRY(grid_mean(w.rho, N, w.partials, w.scalars + 13, s));
   {
@@ -674,7 +680,7 @@ pm_status pm_step_batch(pm_batch_state* st_, const pm_batch_params* prm, void* s
   uint32_t* perm;
   PM_TRY(sort_cells(S.X, np, n, w, s, w.cellstart, &perm, bt));
   PM_TRY(permute_particles(perm, np, S.X, S.V, nullptr, w.Xs, w.Vs, nullptr, s));
-  PM_TRY(deposit_sorted_batch(w.Xs, np_box, B, w.cellstart, n, w.rho, w.partials, w.box_mean, s));
+  PM_TRY(deposit_sorted_batch(w.Xs, np_box, B, w.cellstart, n, w.rho, w.partials, w.box_mean, s, crowded(w)));
   mg_params mp = prm->mg;
   if (mp.smoother == 0) mp.smoother = 2;
   mp.first_guess = S.have_prev ? MG_GUESS_SCALED : MG_GUESS_JACOBI;

@@ -103,6 +103,11 @@ __global__ void __launch_bounds__(T * T * T) k_deposit(const uint32_t* __restric
 // only, so they need no barrier.  The cell starts of plane x + 2 are loaded
 // while plane x is processed.  The particles of a cell are weighed in the
 // same order (ascending index) either way.
+//
+// Medium and crowded cells (more than kMedRun particles) are not walked here:
+// one warp or one block per cell summed their moments beforehand
+// (k_medium_moments, k_crowded_moments), and the cell's thread reads the 27
+// sums.
 constexpr int DTY = 16, DTZ = 16, DEY = DTY + 2, DEZ = DTZ + 2, DNT = DTY * DTZ, DTHREADS = 512;
 constexpr int DPL = DEY * DEZ;   // source cells of a plane (one per thread)
 static_assert(DPL <= DTHREADS, "one source cell per thread");
@@ -124,7 +129,8 @@ __global__ void __launch_bounds__(DTHREADS, 2) k_deposit_stream(const uint32_t* 
                                                                 const uint32_t* __restrict__ cellstart, int log2n,
                                                                 int chunk, int nitems, const float* __restrict__ vals,
                                                                 float scale, float* __restrict__ rho,
-                                                                double* __restrict__ partial) {
+                                                                double* __restrict__ partial,
+                                                                const float* __restrict__ crowd) {
   using G = DepositStage<VALS>;
   constexpr int KP = G::KP, NC = G::NC, PL = DPL;
   extern __shared__ float sm[];
@@ -145,7 +151,9 @@ __global__ void __launch_bounds__(DTHREADS, 2) k_deposit_stream(const uint32_t* 
   const int sly = tid / DEZ, slz = tid - sly * DEZ;            // source cell of this thread (if src)
   const int ty = tid / DTZ, tz = tid - ty * DTZ;               // destination cell (if dst)
   // copies the first KP particles [b, min(e, b + KP)) into slot buffer `buf`
+  // (none for a crowded cell, whose moments are ready in `crowd`)
   auto stage = [&](int buf, uint32_t b, uint32_t e) {
+    if (crowd && e - b > kMedRun) return;
     uint32_t* s0 = Slot + buf * KP * NC * PL + tid;
 #pragma unroll
     for (int k = 0; k < KP; ++k) {
@@ -211,12 +219,16 @@ __global__ void __launch_bounds__(DTHREADS, 2) k_deposit_stream(const uint32_t* 
         };
         const uint32_t* s0 = Slot + (xs & 1) * KP * NC * PL + tid;
         const uint32_t cnt = e0 - b0;
+        if (crowd && cnt > kMedRun) {   // a medium or crowded cell: its moments were summed already
+#pragma unroll
+          for (int o = 0; o < 27; ++o) m[o] = __ldg(crowd + 2 * (int64_t)b0 + o);
+        } else {
 #pragma unroll
         for (int k = 0; k < KP; ++k)
           if ((uint32_t)k < cnt)
             weigh(s0[(k * NC) * PL], s0[(k * NC + 1) * PL], s0[(k * NC + 2) * PL],
                   VALS ? __uint_as_float(s0[(k * NC + 3) * PL]) : 1.0f);
-        if (cnt > (uint32_t)KP) {   // a crowded cell: the rest from global memory
+        if (cnt > (uint32_t)KP) {   // the rest from global memory
           uint32_t p = b0 + KP;
           uint32_t px = __ldg(Xs + p), py = __ldg(Xs + np + p), pz = __ldg(Xs + 2 * np + p);
           for (; p < e0; ++p) {
@@ -228,6 +240,7 @@ __global__ void __launch_bounds__(DTHREADS, 2) k_deposit_stream(const uint32_t* 
             py = qy;
             pz = qz;
           }
+        }
         }
 #pragma unroll
         for (int o = 0; o < 27; ++o) MomW[o * PL + tid] = m[o];
@@ -267,6 +280,103 @@ __global__ void __launch_bounds__(DTHREADS, 2) k_deposit_stream(const uint32_t* 
       double t = 0.0;
       for (int w = 0; w < DTHREADS / 32; ++w) t += wsum[w];
       partial[item] = t;
+    }
+    __syncthreads();
+  }
+}
+
+// The 27 moments of one particle (TSC weight products), added into m.
+template <bool VALS>
+__device__ __forceinline__ void add_moments(const uint32_t* __restrict__ Xs, int64_t np, uint32_t p, int log2n,
+                                            const float* __restrict__ vals, float m[27]) {
+  float wx[3], wy[3], wz[3];
+  tsc_weights(cell_offset(__ldg(Xs + p), log2n), wx);
+  tsc_weights(cell_offset(__ldg(Xs + np + p), log2n), wy);
+  tsc_weights(cell_offset(__ldg(Xs + 2 * np + p), log2n), wz);
+  if (VALS) {
+    const float v = __ldg(vals + p);
+    wx[0] *= v; wx[1] *= v; wx[2] *= v;
+  }
+#pragma unroll
+  for (int ox = 0; ox < 3; ++ox)
+#pragma unroll
+    for (int oy = 0; oy < 3; ++oy) {
+      const float wxy = wx[ox] * wy[oy];
+#pragma unroll
+      for (int oz = 0; oz < 3; ++oz) m[(ox * 3 + oy) * 3 + oz] = fmaf(wxy, wz[oz], m[(ox * 3 + oy) * 3 + oz]);
+    }
+}
+
+// The 27 moments of each medium cell (kMedRun < particles <= kLongRun; the
+// cell sort's meds list), one warp per cell: lane i weighs the cell's i-th
+// particle, then the warp adds them in a fixed shuffle tree.  The moments go
+// to crowd[2a .. 2a + 26] (a = the cell's first rank: a medium cell owns at
+// least 28 floats there, so cells never share slots).
+template <bool VALS>
+__global__ void __launch_bounds__(256) k_medium_moments(const uint32_t* __restrict__ Xs, int64_t np,
+                                                        const uint32_t* __restrict__ cellstart,
+                                                        const uint32_t* __restrict__ meds, int log2n,
+                                                        const float* __restrict__ vals, float* __restrict__ crowd) {
+  const uint32_t nmeds = meds[0];
+  const uint32_t lane = threadIdx.x & 31;
+  const uint32_t warps = gridDim.x * 8;
+  for (uint32_t q = blockIdx.x * 8 + (threadIdx.x >> 5); q < nmeds; q += warps) {
+    const uint32_t c = meds[1 + q];
+    const uint32_t a = cellstart[c], b = cellstart[c + 1];
+    float m[27];
+#pragma unroll
+    for (int o = 0; o < 27; ++o) m[o] = 0.0f;
+    if (a + lane < b) add_moments<VALS>(Xs, np, a + lane, log2n, vals, m);
+#pragma unroll
+    for (int o = 0; o < 27; ++o) {
+#pragma unroll
+      for (int d = 16; d > 0; d >>= 1) m[o] += __shfl_down_sync(0xffffffffu, m[o], d);
+    }
+    // lane 0 holds the sums; lanes 0..26 write one each
+    float out = 0.0f;
+#pragma unroll
+    for (int o = 0; o < 27; ++o) {
+      const float v = __shfl_sync(0xffffffffu, m[o], 0);
+      if (lane == (uint32_t)o) out = v;
+    }
+    if (lane < 27) crowd[2 * (int64_t)a + lane] = out;
+  }
+}
+
+// The 27 moments of each crowded cell (more than kLongRun particles; the
+// cell sort's runs list), one block per cell: thread t weighs particles
+// a + t, a + t + CT, ... of the cell in that order, then the block adds the
+// per-thread sums in a fixed tree (warp shuffles, then the warps in order), so
+// the result does not depend on scheduling.  The moments go to
+// crowd[2a .. 2a + 26], as for medium cells.
+constexpr int CT = 256;
+template <bool VALS>
+__global__ void __launch_bounds__(CT) k_crowded_moments(const uint32_t* __restrict__ Xs, int64_t np,
+                                                        const uint32_t* __restrict__ cellstart,
+                                                        const uint32_t* __restrict__ runs, int log2n,
+                                                        const float* __restrict__ vals, float* __restrict__ crowd) {
+  __shared__ float part[CT / 32][27];
+  const uint32_t nruns = runs[0];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (uint32_t q = blockIdx.x; q < nruns; q += gridDim.x) {
+    const uint32_t c = runs[1 + q];
+    const uint32_t a = cellstart[c], b = cellstart[c + 1];
+    float m[27];
+#pragma unroll
+    for (int o = 0; o < 27; ++o) m[o] = 0.0f;
+    for (uint32_t p = a + threadIdx.x; p < b; p += CT) add_moments<VALS>(Xs, np, p, log2n, vals, m);
+#pragma unroll
+    for (int o = 0; o < 27; ++o) {
+#pragma unroll
+      for (int d = 16; d > 0; d >>= 1) m[o] += __shfl_down_sync(0xffffffffu, m[o], d);
+      if (lane == 0) part[warp][o] = m[o];
+    }
+    __syncthreads();
+    if (threadIdx.x < 27) {
+      float t = 0.0f;
+#pragma unroll
+      for (int w = 0; w < CT / 32; ++w) t += part[w][threadIdx.x];
+      crowd[2 * (int64_t)a + threadIdx.x] = t;
     }
     __syncthreads();
   }
@@ -354,14 +464,40 @@ int64_t reduce_partials_capacity(int n, int64_t np) {
 }
 
 pm_status deposit_sorted(const uint32_t* Xs, int64_t np, const uint32_t* cellstart, int n,
-                         float* rho, double* partials, double* mean_out, cudaStream_t s) {
+                         float* rho, double* partials, double* mean_out, cudaStream_t s, const Crowded& cr) {
   const float scale = np > 0 ? (float)((double)n * n * n / (double)np) : 0.0f;
-  return deposit_sorted_values(Xs, np, cellstart, n, nullptr, scale, rho, partials, mean_out, s);
+  return deposit_sorted_values(Xs, np, cellstart, n, nullptr, scale, rho, partials, mean_out, s, cr);
 }
 
+namespace {
+// Moments of the crowded cells into cr.moments (a no-op launch when there are
+// none); the caller's streaming deposit then reads them.
+pm_status crowded_moments(const uint32_t* Xs, int64_t np, const uint32_t* cellstart, int n, const float* vals,
+                          const Crowded& cr, cudaStream_t s) {
+  if (!cr.runs || np == 0) return PM_OK;
+  if (vals)
+    PM_LAUNCH(K_DEPOSIT, 0.0, k_medium_moments<true>, 8 * 152, 256, 0, s, Xs, np, cellstart, cr.meds, ilog2(n), vals,
+              cr.moments);
+  else
+    PM_LAUNCH(K_DEPOSIT, 0.0, k_medium_moments<false>, 8 * 152, 256, 0, s, Xs, np, cellstart, cr.meds, ilog2(n),
+              vals, cr.moments);
+  const unsigned grid = 4 * 152;
+  if (vals)
+    PM_LAUNCH(K_DEPOSIT, 0.0, k_crowded_moments<true>, grid, CT, 0, s, Xs, np, cellstart, cr.runs, ilog2(n), vals,
+              cr.moments);
+  else
+    PM_LAUNCH(K_DEPOSIT, 0.0, k_crowded_moments<false>, grid, CT, 0, s, Xs, np, cellstart, cr.runs, ilog2(n), vals,
+              cr.moments);
+  return PM_OK;
+}
+}  // namespace
+
 pm_status deposit_sorted_values(const uint32_t* Xs, int64_t np, const uint32_t* cellstart, int n, const float* vals,
-                                float scale, float* rho, double* partials, double* mean_out, cudaStream_t s) {
+                                float scale, float* rho, double* partials, double* mean_out, cudaStream_t s,
+                                const Crowded& cr) {
   if (n >= 32) {
+    PM_TRY(crowded_moments(Xs, np, cellstart, n, vals, cr, s));
+    const float* crowd = cr.runs && np > 0 ? cr.moments : nullptr;
     int chunk, nitems;
     deposit_stream_plan(n, &chunk, &nitems);
     const unsigned grid = (unsigned)nitems;   // one item per CTA, two 512-thread CTAs per SM
@@ -369,11 +505,11 @@ pm_status deposit_sorted_values(const uint32_t* Xs, int64_t np, const uint32_t* 
     if (vals) {
       PM_TRY(smem_attr(k_deposit_stream<true>, DepositStage<true>::smem));
       PM_LAUNCH(K_DEPOSIT, bytes, k_deposit_stream<true>, grid, DTHREADS, DepositStage<true>::smem, s, Xs, np,
-                cellstart, ilog2(n), chunk, nitems, vals, scale, rho, partials);
+                cellstart, ilog2(n), chunk, nitems, vals, scale, rho, partials, crowd);
     } else {
       PM_TRY(smem_attr(k_deposit_stream<false>, DepositStage<false>::smem));
       PM_LAUNCH(K_DEPOSIT, bytes, k_deposit_stream<false>, grid, DTHREADS, DepositStage<false>::smem, s, Xs, np,
-                cellstart, ilog2(n), chunk, nitems, vals, scale, rho, partials);
+                cellstart, ilog2(n), chunk, nitems, vals, scale, rho, partials, crowd);
     }
     PM_LAUNCH(K_REDUCE, 8.0 * nitems, k_reduce_partials, 1, 1024, 0, s, partials, (int64_t)nitems, (int64_t)0, 1,
               1.0 / ((double)n * n * n), mean_out);
@@ -384,8 +520,9 @@ pm_status deposit_sorted_values(const uint32_t* Xs, int64_t np, const uint32_t* 
 }
 
 pm_status deposit_sorted_batch(const uint32_t* Xs, int64_t np_box, int B, const uint32_t* cellstart, int n,
-                               float* rho, double* partials, double* mean_out, cudaStream_t s) {
+                               float* rho, double* partials, double* mean_out, cudaStream_t s, const Crowded& cr) {
   if (n < 32 || B < 1) return PM_EINVAL;
+  PM_TRY(crowded_moments(Xs, np_box * B, cellstart, n, nullptr, cr, s));
   PM_TRY(smem_attr(k_deposit_stream<false>, DepositStage<false>::smem));
   int chunk, nitems;
   deposit_stream_plan(n, &chunk, &nitems);
@@ -395,7 +532,7 @@ pm_status deposit_sorted_batch(const uint32_t* Xs, int64_t np_box, int B, const 
   const int64_t np = np_box * B;
   PM_LAUNCH(K_DEPOSIT, 12.0 * np + 8.0 * n * n * (double)n * B + 4.0, k_deposit_stream<false>, dim3(gx, 1, B),
             DTHREADS, DepositStage<false>::smem, s, Xs, np, cellstart, ilog2(n), chunk, nitems, (const float*)nullptr, scale, rho,
-            partials);
+            partials, cr.runs && np > 0 ? (const float*)cr.moments : nullptr);
   PM_LAUNCH(K_REDUCE, 8.0 * nitems * B, k_reduce_partials, B, 1024, 0, s, partials, (int64_t)nitems,
             (int64_t)nitems, B, 1.0 / ((double)n * n * n), mean_out);
   return launch_status();

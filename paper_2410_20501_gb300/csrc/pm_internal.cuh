@@ -47,6 +47,18 @@ inline pm_status smem_attr(K* fn, size_t bytes) {
   return smem_attr_fn(reinterpret_cast<const void*>(fn), bytes);
 }
 
+// Cells holding more particles than this are "crowded": the cell sort lists
+// them (runs[0] = their number, runs[1 ..] = their cells, in no fixed order)
+// and orders their particles with a block each; the deposit takes their 27
+// TSC moments from a block each as well.
+constexpr uint32_t kLongRun = 32;
+// Cells holding more than kMedRun and at most kLongRun particles are
+// "medium": listed apart (meds[0] = their number, meds[1 ..] = their cells)
+// and ordered, and their moments summed, by a warp each.  A cell of more than
+// kMedRun particles owns at least 28 floats of the sort's 8-byte-per-rank key
+// buffer, at twice its first rank: room for its 27 moments.
+constexpr uint32_t kMedRun = 13;
+
 inline int ilog2(int64_t v) { int l = 0; while ((int64_t(1) << (l + 1)) <= v) ++l; return l; }
 inline bool valid_n(int n) { return n >= 4 && n <= 1024 && (n & (n - 1)) == 0; }
 
@@ -98,7 +110,7 @@ struct Workspace {
   char* base;
   size_t total;
   // sort
-  uint2* keyrank; uint32_t* perm; uint32_t* runs; uint32_t* scan_blocks; uint32_t* cellstart;
+  uint2* keyrank; uint32_t* perm; uint32_t* runs; uint32_t* meds; uint32_t* scan_blocks; uint32_t* cellstart;
   // particles in cell order
   uint32_t* Xs; float* Vs; uint32_t* ids;
   // grids
@@ -123,6 +135,7 @@ size_t layout_workspace(Workspace* w, void* base, int n, int64_t np, uint32_t fl
 // Sizes of the scratch pieces.
 int64_t sort_scan_blocks(int64_t ncells);
 int64_t sort_runs_capacity(int64_t np);
+int64_t sort_meds_capacity(int64_t np);
 int64_t reduce_partials_capacity(int n, int64_t np);
 // Work items of the streaming deposit for one box of n^3 cells (n >= 32).
 int deposit_items(int n);
@@ -138,18 +151,29 @@ pm_status sort_cells(const uint32_t* X, int64_t np, int n, Workspace& w, cudaStr
 pm_status permute_particles(const uint32_t* perm, int64_t np, const uint32_t* X, const float* V,
                             const uint32_t* id, uint32_t* Xs, float* Vs, uint32_t* ids,
                             cudaStream_t s);
+// The crowded cells of the last cell sort (its runs list) and np floats of
+// scratch that nothing reads between the sort and the deposit (the sort's key
+// buffer): the deposit stores each crowded cell's 27 moments at the ranks of
+// its first particles.  runs == NULL: every cell is walked by one thread.
+struct Crowded {
+  const uint32_t* runs = nullptr;
+  const uint32_t* meds = nullptr;
+  float* moments = nullptr;
+};
 // rho = (n^3/np) TSC sum over cell-sorted particles; writes sum(rho)/n^3 to *mean_out.
 pm_status deposit_sorted(const uint32_t* Xs, int64_t np, const uint32_t* cellstart, int n,
-                         float* rho, double* partials, double* mean_out, cudaStream_t s);
+                         float* rho, double* partials, double* mean_out, cudaStream_t s,
+                         const Crowded& cr = Crowded{});
 // General form: rho[c] = scale * sum_p vals[p] W(x_p - x_c) (vals may be NULL
 // for 1); *mean_out = sum(rho)/n^3.
 pm_status deposit_sorted_values(const uint32_t* Xs, int64_t np, const uint32_t* cellstart, int n,
                                 const float* vals, float scale, float* rho, double* partials,
-                                double* mean_out, cudaStream_t s);
+                                double* mean_out, cudaStream_t s, const Crowded& cr = Crowded{});
 // Batched deposit (n >= 32): box b's density [n^3] from its particles (the
 // cell starts cover all boxes); mean_out[b] = box b's mean.
 pm_status deposit_sorted_batch(const uint32_t* Xs, int64_t np_box, int B, const uint32_t* cellstart, int n,
-                               float* rho, double* partials, double* mean_out, cudaStream_t s);
+                               float* rho, double* partials, double* mean_out, cudaStream_t s,
+                               const Crowded& cr = Crowded{});
 // out[k] = scale * sum_{i < count} partials[k * stride + i] for k < nout (one block).
 pm_status reduce_partials(const double* partials, int64_t count, int64_t stride, int nout,
                           double scale, double* out, cudaStream_t s);

@@ -27,7 +27,7 @@ constexpr int SCAN_T = 1024;
 constexpr int SCAN_CHUNK = 4 * SCAN_T;
 constexpr int KT = 256;             // threads of the key, scatter and order kernels
 constexpr int CI = 4;               // particles per thread of the counting kernel
-constexpr uint32_t SHORT_RUN = 32;  // runs up to this length are ordered by one thread
+constexpr uint32_t SHORT_RUN = kLongRun;  // runs up to this length are ordered by one thread
 constexpr int LT = 512;             // threads of a long-run block
 constexpr int LCH = 4096;           // elements sorted in shared memory at once
 constexpr int LONG_BLOCKS = 2 * 152;
@@ -98,10 +98,12 @@ __global__ void __launch_bounds__(KT) k_cell_scatter(const uint2* __restrict__ k
 // Stable order inside each cell: the ranks of cell c, cellstart[c] ..
 // cellstart[c+1]-1, in ascending particle index.  A thread takes four
 // consecutive cells (one 16-byte load of their starts).  Runs of at most
-// SHORT_RUN are insertion-sorted here; longer ones are listed in runs[1 ..]
-// (runs[0] counts them, zeroed) for k_cell_order_long.
+// kMedRun are insertion-sorted here; runs of at most SHORT_RUN are listed in
+// meds[1 ..] for k_cell_order_med, longer ones in runs[1 ..] for
+// k_cell_order_long (meds[0], runs[0] count them, zeroed).
 __global__ void __launch_bounds__(KT) k_cell_order(const uint32_t* __restrict__ cellstart, int64_t ncells,
-                                                   uint32_t* __restrict__ perm, uint32_t* __restrict__ runs) {
+                                                   uint32_t* __restrict__ perm, uint32_t* __restrict__ runs,
+                                                   uint32_t* __restrict__ meds) {
   const int64_t c0 = (blockIdx.x * (int64_t)KT + threadIdx.x) * 4;
   if (c0 >= ncells) return;
   const uint4 s4 = __ldg(reinterpret_cast<const uint4*>(cellstart + c0));
@@ -114,6 +116,10 @@ __global__ void __launch_bounds__(KT) k_cell_order(const uint32_t* __restrict__ 
       runs[1 + atomicAdd(runs, 1u)] = (uint32_t)(c0 + k);
       continue;
     }
+    if (b - a > kMedRun) {
+      meds[1 + atomicAdd(meds, 1u)] = (uint32_t)(c0 + k);
+      continue;
+    }
     for (uint32_t p = a + 1; p < b; ++p) {
       const uint32_t v = perm[p];
       uint32_t q = p;
@@ -124,6 +130,26 @@ __global__ void __launch_bounds__(KT) k_cell_order(const uint32_t* __restrict__ 
       }
       if (q != p) perm[q] = v;
     }
+  }
+}
+
+// The medium runs listed by k_cell_order, one warp each: lane i holds the
+// run's i-th particle index and moves it to its rank among the run's
+// (distinct) indices, counted over the warp by shuffles.
+__global__ void __launch_bounds__(KT) k_cell_order_med(const uint32_t* __restrict__ cellstart,
+                                                       const uint32_t* __restrict__ meds,
+                                                       uint32_t* __restrict__ perm) {
+  const uint32_t nmeds = meds[0];
+  const uint32_t lane = threadIdx.x & 31;
+  const uint32_t warps = gridDim.x * (KT / 32);
+  for (uint32_t q = blockIdx.x * (KT / 32) + (threadIdx.x >> 5); q < nmeds; q += warps) {
+    const uint32_t c = meds[1 + q];
+    const uint32_t a = cellstart[c], m = cellstart[c + 1] - a;
+    const uint32_t v = lane < m ? perm[a + lane] : 0xffffffffu;
+    uint32_t rank = 0;
+    for (uint32_t j = 0; j < m; ++j) rank += __shfl_sync(0xffffffffu, v, j) < v;
+    __syncwarp();
+    if (lane < m) perm[a + rank] = v;
   }
 }
 
@@ -329,6 +355,7 @@ pm_status scan_u32(uint32_t* a, int64_t len, uint32_t* sums, cudaStream_t s) {
 int64_t sort_scan_blocks(int64_t ncells) { return (ncells + 1 + SCAN_CHUNK - 1) / SCAN_CHUNK + 1; }
 
 int64_t sort_runs_capacity(int64_t np) { return np / (SHORT_RUN + 1) + 2; }
+int64_t sort_meds_capacity(int64_t np) { return np / (kMedRun + 1) + 2; }
 
 pm_status sort_cells(const uint32_t* X, int64_t np, int n, Workspace& w, cudaStream_t s, uint32_t* cellstart,
                      uint32_t** perm_out, const Batch& bt) {
@@ -336,6 +363,8 @@ pm_status sort_cells(const uint32_t* X, int64_t np, int n, Workspace& w, cudaStr
   const int64_t ncells = (int64_t)n * n * n * bt.B;
   *perm_out = w.perm;
   PM_TRY(cuda_status(cudaMemsetAsync(cellstart, 0, (size_t)(ncells + 1) * 4, s)));
+  PM_TRY(cuda_status(cudaMemsetAsync(w.runs, 0, 4, s)));   // no crowded or medium cells yet
+  PM_TRY(cuda_status(cudaMemsetAsync(w.meds, 0, 4, s)));
   if (np == 0) return PM_OK;
   const int64_t np_box = bt.B > 1 ? bt.np_box : 0;
   const unsigned gc = grid_for(np, KT * CI);
@@ -345,9 +374,9 @@ pm_status sort_cells(const uint32_t* X, int64_t np, int n, Workspace& w, cudaStr
     PM_LAUNCH(K_KEYS, 28.0 * np, k_cell_count<false>, gc, KT, 0, s, X, np, log2n, np_box, w.keyrank, cellstart);
   PM_TRY(scan_u32(cellstart, ncells + 1, w.scan_blocks, s));
   PM_LAUNCH(K_SCATTER, 16.0 * np, k_cell_scatter, gc, KT, 0, s, w.keyrank, np, cellstart, w.perm);
-  PM_TRY(cuda_status(cudaMemsetAsync(w.runs, 0, 4, s)));
   PM_LAUNCH(K_ORDER, 4.0 * ncells + 8.0 * np, k_cell_order, grid_for(ncells / 4, KT), KT, 0, s, cellstart, ncells,
-            w.perm, w.runs);
+            w.perm, w.runs, w.meds);
+  PM_LAUNCH(K_ORDER, 0.0, k_cell_order_med, 8 * 152, KT, 0, s, cellstart, w.meds, w.perm);
   PM_LAUNCH(K_ORDER, 0.0, k_cell_order_long, LONG_BLOCKS, LT, 0, s, cellstart, w.runs, w.perm,
             reinterpret_cast<uint32_t*>(w.keyrank));
   return launch_status();

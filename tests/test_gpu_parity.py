@@ -70,7 +70,8 @@ def clustered(n, counts, seed, background=0):
 
 
 @pytest.mark.parametrize("counts,background", [
-    ([32, 33, 34, 64, 100], 3000),              # around the one-thread limit
+    ([12, 13, 14, 15, 20, 31, 32, 33], 3000),   # around the one-thread and one-warp limits
+    ([32, 33, 34, 64, 100], 3000),              # around the one-warp limit
     ([4095, 4096, 4097, 8193], 20000),          # one and several shared-memory chunks
     ([150000, 999, 2], 50000),                  # a long run merged over several passes
 ])

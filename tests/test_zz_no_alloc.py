@@ -38,6 +38,17 @@ def _noalloc(pm, X, n):
     return rho.cpu().numpy()
 
 
+def _crowded(n, seed):
+    """Uniform particles plus clumps of 100 to 20000 inside single cells: the
+    cells whose moments a block sums."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    pos = [rng.uniform(0.0, 1.0, (3, 100000))]
+    for q, m in enumerate((100, 1000, 20000)):
+        c = rng.integers(0, n, 3).astype(np.float64)[:, None]
+        pos.append((c + rng.uniform(0.0, 1.0, (3, m))) / n)
+    return inputs.to_fixed_point(np.concatenate(pos, axis=1))
+
+
 def test_noalloc_deposit_matches_pm_deposit_twice(pm):
     """Both entry points run the same sort, permutation and deposit kernels on
     the same buffer layout, so their densities agree bit for bit.  The cases
@@ -46,7 +57,8 @@ def test_noalloc_deposit_matches_pm_deposit_twice(pm):
     left there."""
     cases = [(64, inputs.uniform_particles(1 << 18, 40)),
              (64, inputs.uniform_particles(200000, 41)),
-             (32, inputs.to_fixed_point(inputs.lattice(32) + 0.004 * inputs.random_field(32, 2).reshape(1, -1)))]
+             (32, inputs.to_fixed_point(inputs.lattice(32) + 0.004 * inputs.random_field(32, 2).reshape(1, -1))),
+             (64, _crowded(64, 42))]
     for n, Xh in cases:
         X = pm.positions_to_device(Xh)
         got = _noalloc(pm, X, n)
