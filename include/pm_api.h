@@ -445,6 +445,30 @@ double pm_dt_supercomoving(double Om, double OL, double a0, double a1);
 /* Linear growth factor D(a) (Appendix A, growing mode, D ~ a early on). */
 double pm_growth_D(double Om, double OL, double a);
 
+/* Adaptive time step of the integrator (§3.4, "Integrator"): the
+ * supercomoving step dt = courant * min(dt_a, dt_ff, dt_v), where dt_a lets
+ * the scale factor grow by the fraction da_max, dt_ff = sqrt(h / max_acc) is
+ * the free-fall time over one cell and dt_v = h / max_vel the time to cross
+ * one cell at the largest speed (h = 1/n; a criterion whose maximum is 0 is
+ * left out); if the step would pass a_end it ends there instead.  Writes the
+ * step (*dt) and the scale factor it reaches (*a_next, by bisection on the
+ * monotone t(a)).  Host computation in float64; max_acc and max_vel are the
+ * host values pm_step reports with report_max (and pm_max_speed).
+ * PM_EINVAL for a <= 0, a_end <= a, negative maxima, courant or da_max <= 0,
+ * or NULL outputs. */
+pm_status pm_next_timestep(double a, double Om, double OL, int n, double max_acc, double max_vel, double courant,
+                           double da_max, double a_end, double* dt, double* a_next);
+
+/* Largest particle speed |v| of V [3][np] (device, float32 planes; computed
+ * in float32, returned as float64 in *max_vel, host): the velocity criterion's
+ * input before the first step, when no step has reported one yet.
+ * Synchronises `stream` (one 16-byte read).  ws: a workspace of
+ * pm_workspace_size(n, np, flags) bytes for any flags (its reduction
+ * buffers are used; nothing else in it is touched).  PM_EINVAL for bad sizes
+ * or pointers, PM_ENOMEM for a short workspace. */
+pm_status pm_max_speed(const float* V, int64_t np, int n, uint32_t flags, double* max_vel, void* ws,
+                       size_t ws_bytes, void* stream);
+
 /* --------------------------------------------------------- instrumentation */
 /* Number of kernels this library has launched since load. */
 uint64_t pm_launch_count(void);

@@ -77,3 +77,26 @@ def run_kdk(pos, vel, a_steps, prm, warm_start=True):
         acc, phi, u = accelerations(pos, a1, prm, phi_guess=guess, u_guess=u)
         vel += 0.5 * dt * acc
     return pos, vel
+
+
+def next_timestep(a, Om, OL, n, max_acc, max_vel, courant=0.8, da_max=0.02, a_end=1.0):
+    """The adaptive time step of §3.4 (Integrator), in supercomoving time:
+    the smallest of (i) the time over which a grows by the fraction da_max,
+    (ii) the free-fall time sqrt(h / max|a|) and (iii) the cell-crossing time
+    h / max|v| (h = 1/n; a criterion with a zero maximum does not apply),
+    times the Courant factor; a step that would pass a_end stops there.
+    Returns (dt, a reached after dt), the latter by root finding on the
+    monotone t(a)."""
+    from scipy.optimize import brentq
+    h = 1.0 / n
+    limits = [dt_supercomoving(a, a * (1.0 + da_max), Om, OL)]
+    if max_acc > 0.0:
+        limits.append(np.sqrt(h / max_acc))
+    if max_vel > 0.0:
+        limits.append(h / max_vel)
+    dt = courant * min(limits)
+    to_end = dt_supercomoving(a, a_end, Om, OL)
+    if to_end <= dt:
+        return to_end, a_end
+    a_next = brentq(lambda x: dt_supercomoving(a, x, Om, OL) - dt, a, a_end, xtol=1e-16, rtol=1e-15, maxiter=500)
+    return dt, a_next

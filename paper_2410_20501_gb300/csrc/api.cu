@@ -702,6 +702,49 @@ double pm_dt_supercomoving(double Om, double OL, double a0, double a1) {
   return sign * simpson(Om, OL, lo, hi, fa, fm, fb, whole, 1e-15 * fabs(whole), 50);
 }
 
+pm_status pm_max_speed(const float* V, int64_t np, int n, uint32_t flags, double* max_vel, void* ws,
+                       size_t ws_bytes, void* stream) {
+  if (!valid_n(n) || !valid_np(np) || (np > 0 && !V) || !max_vel || !all_a16(V)) return PM_EINVAL;
+  Workspace w;
+  PM_TRY(check_ws(w, ws, ws_bytes, n, np, flags));
+  *max_vel = 0.0;
+  if (np == 0) return PM_OK;
+  cudaStream_t s = as_stream(stream);
+  PM_TRY(max_speed_launch(V, np, reinterpret_cast<float2*>(w.partials), w.scalars + 28, s));
+  double h[2];
+  PM_TRY(fetch_scalars(w.scalars + 28, h, 2, s));
+  *max_vel = h[1];
+  return PM_OK;
+}
+
+pm_status pm_next_timestep(double a, double Om, double OL, int n, double max_acc, double max_vel, double courant,
+                           double da_max, double a_end, double* dt, double* a_next) {
+  if (!(a > 0.0) || !(a_end > a) || n < 1 || !(max_acc >= 0.0) || !(max_vel >= 0.0) || !(courant > 0.0) ||
+      !(da_max > 0.0) || !dt || !a_next)
+    return PM_EINVAL;
+  const double h = 1.0 / n;
+  double lim = pm_dt_supercomoving(Om, OL, a, a * (1.0 + da_max));   // a grows by the fraction da_max
+  if (max_acc > 0.0) lim = fmin(lim, sqrt(h / max_acc));            // free fall over one cell
+  if (max_vel > 0.0) lim = fmin(lim, h / max_vel);                  // one cell at the largest speed
+  const double step = courant * lim;
+  const double to_end = pm_dt_supercomoving(Om, OL, a, a_end);
+  if (to_end <= step) {
+    *dt = to_end;
+    *a_next = a_end;
+    return PM_OK;
+  }
+  // t(a) grows monotonically: bisection for the scale factor a step later
+  double lo = a, hi = a_end;
+  for (int it = 0; it < 200 && hi - lo > 1e-15 * hi; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (pm_dt_supercomoving(Om, OL, a, mid) < step) lo = mid;
+    else hi = mid;
+  }
+  *dt = step;
+  *a_next = 0.5 * (lo + hi);
+  return PM_OK;
+}
+
 double pm_growth_D(double Om, double OL, double a) {
   if (!(a > 0.0)) return NAN;
   // D'' = -gamma D' + beta D in x = ln a (Appendix A), RK4 from the

@@ -483,6 +483,25 @@ constexpr size_t force_interp_smem() {
 
 // Maximum over count float2 pairs, per component, into out[0], out[1]
 // (float64); one block.
+// Largest |v| of the velocity planes V [3][np]: one float2 (0, max) per block
+// (float bits of non-negative values order like unsigned integers).
+__global__ void __launch_bounds__(256) k_speed_max(const float* __restrict__ V, int64_t np,
+                                                   float2* __restrict__ blockmax) {
+  __shared__ unsigned wv[8];
+  unsigned mv = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < np; i += (int64_t)gridDim.x * blockDim.x) {
+    const float vx = __ldg(V + i), vy = __ldg(V + np + i), vz = __ldg(V + 2 * np + i);
+    mv = max(mv, __float_as_uint(sqrtf(vx * vx + vy * vy + vz * vz)));
+  }
+  mv = __reduce_max_sync(0xffffffffu, mv);
+  if ((threadIdx.x & 31) == 0) wv[threadIdx.x >> 5] = mv;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 0; w < 8; ++w) mv = max(mv, wv[w]);
+    blockmax[blockIdx.x] = make_float2(0.0f, __uint_as_float(mv));
+  }
+}
+
 __global__ void __launch_bounds__(1024) k_max_pairs(const float2* __restrict__ v, int64_t count,
                                                     double* __restrict__ out) {
   __shared__ unsigned wa[32], wv[32];
@@ -592,6 +611,13 @@ pm_status launch_force_interp(const float* phi, const float* eps, float alpha, i
   }
 #undef PM_FI
   if (bt.B > 1) tune_end(s);
+  return launch_status();
+}
+
+pm_status max_speed_launch(const float* V, int64_t np, float2* blockmax, double* max_out, cudaStream_t s) {
+  const unsigned nb = grid_for(np, 256, 152 * 16);
+  PM_LAUNCH(K_REDUCE, 12.0 * np, k_speed_max, nb, 256, 0, s, V, np, blockmax);
+  PM_LAUNCH(K_REDUCE, 8.0 * nb, k_max_pairs, 1, 1024, 0, s, blockmax, (int64_t)nb, max_out);
   return launch_status();
 }
 

@@ -229,6 +229,10 @@ pm_status fft_poisson_launch(const float* rho, const double* mean, float* phi, f
 pm_status lpt2_launch(const float* noise, const float* amp, int n, double d1, double e2, double v1, double v2,
                       uint32_t* X, float* V, float2* A, float2* B, float* R, cudaStream_t s);
 
+// max_out[1] = the largest |v| of V [3][np] (max_out[0] = 0); blockmax:
+// at most 152 * 16 float2.
+pm_status max_speed_launch(const float* V, int64_t np, float2* blockmax, double* max_out, cudaStream_t s);
+
 // Adjoint pieces (adjoint.cu).
 pm_status divergence_launch(const float* gbar, float* phibar, int n, int order, cudaStream_t s);
 pm_status adj_accel_launch(const float* xbar_out, const float* vbar_out, int64_t np, float dt_kick,

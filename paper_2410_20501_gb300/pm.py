@@ -143,6 +143,13 @@ _SIGS = {
                                    ctypes.c_void_p]),
     "pm_dt_supercomoving": (ctypes.c_double, [ctypes.c_double] * 4),
     "pm_growth_D": (ctypes.c_double, [ctypes.c_double] * 3),
+    "pm_next_timestep": (ctypes.c_int, [ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                        ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                        ctypes.c_double, ctypes.POINTER(ctypes.c_double),
+                                        ctypes.POINTER(ctypes.c_double)]),
+    "pm_max_speed": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_uint32,
+                                    ctypes.POINTER(ctypes.c_double), ctypes.c_void_p, ctypes.c_size_t,
+                                    ctypes.c_void_p]),
     "pm_launch_count": (ctypes.c_uint64, []),
     "pm_timing_enable": (ctypes.c_int, [ctypes.c_int]),
     "pm_timing_collect": (ctypes.c_int, [ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_double),
@@ -356,30 +363,21 @@ def gradient_adj(g_bar, order=5):
 
 
 def next_timestep(a, Om, OL, n, max_acc, max_vel, courant=0.8, da_max=0.02, a_end=1.0):
-    """Time step of §3.4 (Integrator) in supercomoving time and the scale
-    factor it reaches: dt = courant * min(dt_cosmo, dt_ff, dt_vel) with
-    dt_cosmo the time for a to grow by the fraction da_max, dt_ff =
-    sqrt(h / max|a|), dt_vel = h / max|v| (h = 1/n; a criterion with a zero
-    maximum is absent), clipped so that a does not pass a_end.  Host code."""
-    h = 1.0 / n
-    dts = [dt_supercomoving(Om, OL, a, a * (1.0 + da_max))]
-    if max_acc > 0.0:
-        dts.append(math.sqrt(h / max_acc))
-    if max_vel > 0.0:
-        dts.append(h / max_vel)
-    dt = courant * min(dts)
-    if dt_supercomoving(Om, OL, a, a_end) <= dt:
-        return dt_supercomoving(Om, OL, a, a_end), a_end
-    lo, hi = a, a * (1.0 + da_max)       # dt <= dt_cosmo: the root lies in [a, a (1 + da_max)]
-    for _ in range(200):                  # bisection on the monotone t(a)
-        mid = 0.5 * (lo + hi)
-        if dt_supercomoving(Om, OL, a, mid) < dt:
-            lo = mid
-        else:
-            hi = mid
-        if hi - lo <= 1e-15 * hi:
-            break
-    return dt, 0.5 * (lo + hi)
+    """pm_next_timestep: the §3.4 time step and the scale factor it reaches,
+    (dt, a_next)."""
+    dt, an = ctypes.c_double(), ctypes.c_double()
+    _check(lib().pm_next_timestep(a, Om, OL, n, max_acc, max_vel, courant, da_max, a_end, ctypes.byref(dt),
+                                  ctypes.byref(an)), "pm_next_timestep")
+    return dt.value, an.value
+
+
+def max_speed(V, n, ws, flags):
+    """pm_max_speed: the largest |v| of V [3, np] (device), with a workspace
+    sized by pm_workspace_size(n, np, flags)."""
+    out = ctypes.c_double()
+    _check(lib().pm_max_speed(_p(V, torch.float32), V.shape[1], n, flags, ctypes.byref(out), _p(ws), ws.numel(),
+                              _stream()), "pm_max_speed")
+    return out.value
 
 
 def dt_supercomoving(Om, OL, a0, a1):
@@ -454,6 +452,7 @@ class Simulation:
         flags = (PM_WS_STEP | (PM_WS_IDS if track_ids else 0) | (PM_WS_ADJ if adjoint else 0)
                  | (PM_WS_FFT if poisson else 0))
         self.ws = workspace(n, self.np, flags, device)
+        self.ws_flags = flags
         self.mg = mg if mg is not None else default_mg()
         self.fr = fr if fr is not None else default_fr()
         self.state = pm_state(n=n, np=self.np, X=_p(self.X).value, V=_p(self.V).value,
@@ -488,9 +487,8 @@ class Simulation:
         factors of the force evaluations (the last one is a_end, reached by a
         closing half kick)."""
         a = a_start
-        v = self.V.float()
-        max_vel = float(torch.sqrt((v * v).sum(0)).max()) if self.np else 0.0
-        max_acc, dt_prev, phis, out = 0.0, 0.0, None, [a_start]
+        max_vel = max_speed(self.V, self.n, self.ws, self.ws_flags)
+        max_acc, dt_prev, out = 0.0, 0.0, [a_start]
         aD_prev = None
         for _ in range(max_steps):
             dt, a_next = next_timestep(a, self.Om, self.OL, self.n, max_acc, max_vel, courant, da_max, a_end)

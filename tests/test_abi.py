@@ -153,3 +153,24 @@ def test_autotune_mode_is_checked_on_the_host(L):
     assert L.pm_autotune(3) == 1 and L.pm_autotune(-1) == 1
     assert L.pm_autotune_report(None, 0) == 0
     assert L.pm_autotune(1) == 0
+
+
+def test_next_timestep_matches_oracle(L):
+    """pm_next_timestep (host code of the library) against the oracle's
+    restatement of §3.4 on LCDM and EdS cases where each criterion wins."""
+    from oracle.step import next_timestep as oracle_dt
+    from paper_2410_20501_gb300 import pm
+    cases = [(0.05, 0.3, 0.7, 512, 0.0, 0.0), (0.3, 0.3, 0.7, 512, 5e3, 0.0), (0.6, 0.3, 0.7, 256, 1e2, 40.0),
+             (0.9, 0.3, 0.7, 64, 0.0, 1e3), (0.1, 1.0, 0.0, 32, 3.0, 0.5), (0.999, 0.3, 0.7, 512, 0.0, 0.0)]
+    for a, Om, OL, n, acc, vel in cases:
+        dt, an = pm.next_timestep(a, Om, OL, n, acc, vel, 0.8, 0.02, 1.0)
+        rdt, ran = oracle_dt(a, Om, OL, n, acc, vel, 0.8, 0.02, 1.0)
+        assert dt == pytest.approx(rdt, rel=1e-10) and an == pytest.approx(ran, rel=1e-12), (a, n, acc, vel)
+
+
+def test_next_timestep_rejects_bad_arguments(L):
+    out = ctypes.c_double()
+    bad = [(0.0, 0.3, 0.7, 32, 0.0, 0.0, 0.8, 0.02, 1.0), (0.5, 0.3, 0.7, 32, 0.0, 0.0, 0.8, 0.02, 0.5),
+           (0.5, 0.3, 0.7, 32, -1.0, 0.0, 0.8, 0.02, 1.0), (0.5, 0.3, 0.7, 32, 0.0, 0.0, 0.0, 0.02, 1.0)]
+    for args in bad:
+        assert L.pm_next_timestep(*args, ctypes.byref(out), ctypes.byref(out)) == 1

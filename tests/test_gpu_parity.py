@@ -454,3 +454,16 @@ def test_step_host_equals_device_step(pm, gravity):
         host.step_host(a, k, d, Xh, Vh, Xh, Vh)
     assert torch.equal(Xh, dev.X.cpu())
     assert torch.equal(Vh, dev.V.cpu())
+
+
+@pytest.mark.parametrize("N", [0, 1, 1000, 300001])
+def test_max_speed_matches_host(pm, N):
+    """pm_max_speed: the largest |v| over the particles (the velocity
+    criterion's input before the first step), against numpy."""
+    rng = np.random.Generator(np.random.PCG64(N + 3))
+    V = rng.standard_normal((3, N)).astype(np.float32)
+    n = 32
+    ws = pm.workspace(n, N, pm.PM_WS_STEP)
+    got = pm.max_speed(torch.from_numpy(V).cuda(), n, ws, pm.PM_WS_STEP)
+    ref = float(np.sqrt((V.astype(np.float64) ** 2).sum(0)).max()) if N else 0.0
+    assert got == pytest.approx(ref, rel=1e-6, abs=0.0)

@@ -111,3 +111,30 @@ def test_parametrised_accelerations_scale_with_mu():
     acc_n, _, _ = step.accelerations(pos, 0.6, base)
     acc_m, _, _ = step.accelerations(pos, 0.6, step.PMParams(n=16, Om=0.3, OL=0.7, gravity="mu", mu0=0.3))
     np.testing.assert_allclose(acc_m, mu_parametrised(0.6, 0.3, 0.7, 0.3) * acc_n, rtol=1e-12, atol=1e-15)
+
+
+def _eds_a_after(a, dt):
+    """EdS: t~(a) = -2 a^(-1/2) + const, so a after dt is (a^(-1/2) - dt/2)^(-2)."""
+    return (a ** -0.5 - 0.5 * dt) ** -2
+
+
+def test_next_timestep_eds_closed_forms():
+    """Each §3.4 criterion alone, in Einstein-de Sitter where the supercomoving
+    time has the closed form t~ = -2 a^(-1/2): the 2% growth of a, the free
+    fall over one cell and the cell crossing, times the Courant factor, and
+    the clip at a_end."""
+    from oracle.step import next_timestep
+    a, n, C, da = 0.1, 32, 0.8, 0.02
+    dt_a = 2.0 * (a ** -0.5 - (a * (1 + da)) ** -0.5)
+    dt, an = next_timestep(a, 1.0, 0.0, n, 0.0, 0.0, C, da)               # growth of a only
+    assert dt == pytest.approx(C * dt_a, rel=1e-12)
+    assert an == pytest.approx(_eds_a_after(a, dt), rel=1e-12)
+    big_acc = 10.0 / (n * dt_a ** 2)                                      # free fall: sqrt(h / acc) < dt_a
+    dt, an = next_timestep(a, 1.0, 0.0, n, big_acc, 0.0, C, da)
+    assert dt == pytest.approx(C * np.sqrt(1.0 / n / big_acc), rel=1e-12)
+    assert an == pytest.approx(_eds_a_after(a, dt), rel=1e-12)
+    big_v = 10.0 / (n * dt_a)                                             # crossing: h / v < dt_a
+    dt, an = next_timestep(a, 1.0, 0.0, n, big_acc * 1e-6, big_v, C, da)
+    assert dt == pytest.approx(C / (n * big_v), rel=1e-12)
+    dt, an = next_timestep(0.995, 1.0, 0.0, n, 0.0, 0.0, C, da, a_end=1.0)  # clipped at a_end
+    assert an == 1.0 and dt == pytest.approx(2.0 * (0.995 ** -0.5 - 1.0), rel=1e-12)
