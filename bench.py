@@ -309,6 +309,22 @@ def oracle_errors(probes):
             out[name] = {"rel_l2_acc": float(np.linalg.norm(p["acc"] - ref) / np.linalg.norm(ref)),
                          "what": f"{p['acc'].shape[0]} sampled particles of step {p['step']}, oracle gradient and "
                                  "inverse TSC of the GPU's own potential(s)"}
+        elif p["kind"] == "adjoint":
+            import torch
+            from oracle import adjoint as oadj
+            from oracle import cosmology
+            from paper_2410_20501_gb300 import inputs
+            w = inputs.c4_workload(p["n"], boxsize=50.0)
+            a = w["a_steps"]
+            dts = [cosmology.dt_supercomoving(a0, a1, w["Om"], w["OL"]) for a0, a1 in zip(a[:-1], a[1:])]
+            steps = [(a[i], 0.5 * ((dts[i - 1] if i else 0.0) + dts[i]), dts[i]) for i in range(len(dts))]
+            loss_ref, grad_ref = oadj.density_loss_grad(w["noise"], torch.from_numpy(p["target"]), w["amp"],
+                                                        w["d_ratio"], w["vfac"], steps, w["Om"], p["n"])
+            g = grad_ref.numpy()
+            out[name] = {"rel_l2_grad": float(np.linalg.norm(p["grad"] - g) / np.linalg.norm(g)),
+                         "rel_loss": abs(p["loss"] - loss_ref) / abs(loss_ref),
+                         "what": "d loss / d noise of the 10-step density loss at 32^3 (L = 50 Mpc/h) against "
+                                 "the FP64 autograd oracle, same target"}
         elif p["kind"] == "boxes":
             errs = []
             for b, (pos, acc, Om_b) in enumerate(zip(p["pos"], p["acc"], p["Om"])):
@@ -471,11 +487,25 @@ def run_adjoint(n=128, fd_dirs=16, reps=3, eps=1.0):
         fd = (L(noise0 + eps * u) - L(noise0 - eps * u)) / (2 * eps)
         an = float((grad * u).sum())
         errs.append(abs(fd - an) / max(abs(an), 1e-30))
-    return {"workload": f"{n}^3 particles/grid, L=200 Mpc/h, 1LPT z=20 from white noise, 10 PM steps to z=0, "
-                        "density-difference loss", "forward_ms": fwd, "backward_ms": bwd,
-            "adjoint_over_forward": bwd / fwd, "loss": float(loss.detach()),
-            "fd_check": {"directions": fd_dirs, "eps": eps, "median_rel_err": statistics.median(errs) if errs else None,
-                         "max_rel_err": max(errs) if errs else None}}
+    # the same chain at 32^3 (the 200 Mpc/h / 128 resolution: L = 50 Mpc/h),
+    # kept for the CPU leg's comparison with the FP64 autograd oracle
+    ws = inputs.c4_workload(32, boxsize=50.0)
+    st32 = diffpm.Stepper(32, 32 ** 3, ws["Om"], ws["OL"], ws["boxsize"])
+    steps32 = diffpm.schedule_coefficients(ws["a_steps"], ws["Om"], ws["OL"])
+    args32 = (st32, ws["amp"], ws["d_ratio"], ws["vfac"], steps32)
+    with torch.no_grad():
+        target32 = diffpm.forward_model(torch.from_numpy(ws["target_noise"]).cuda(), *args32).to(torch.float64)
+    noise32 = torch.from_numpy(ws["noise"]).cuda().requires_grad_(True)
+    loss32 = diffpm.density_loss(noise32, target32, *args32)
+    loss32.backward()
+    probe = {"kind": "adjoint", "n": 32, "target": target32.cpu().numpy(), "grad": noise32.grad.cpu().numpy(),
+             "loss": float(loss32.detach())}
+    return ({"workload": f"{n}^3 particles/grid, L=200 Mpc/h, 1LPT z=20 from white noise, 10 PM steps to z=0, "
+                         "density-difference loss", "forward_ms": fwd, "backward_ms": bwd,
+             "adjoint_over_forward": bwd / fwd, "loss": float(loss.detach()),
+             "fd_check": {"directions": fd_dirs, "eps": eps,
+                          "median_rel_err": statistics.median(errs) if errs else None,
+                          "max_rel_err": max(errs) if errs else None}}, probe)
 
 
 def run_ensemble(n=64, B=64, steps=50):
@@ -717,7 +747,7 @@ def run_gpu(args):
         "clocks": fr_clocks,
     }
     if world == 1 and not args.lean:
-        line["adjoint"] = run_adjoint()
+        line["adjoint"], probes["adjoint"] = run_adjoint()
         line["ensemble"], probes["ensemble"] = run_ensemble()
     if world == 1 and not args.no_cpu_baseline and not args.lean:
         line["cpu_baseline"] = cpu_baseline()
@@ -821,10 +851,10 @@ def main():
                     help="--stage mg/fr: 2 fused sweeps, 1 colour passes, 0 two-sweep streaming")
     args = ap.parse_args()
     if args.stage == "adjoint":
-        print(json.dumps(run_adjoint(args.n, fd_dirs=args.steps)))
+        print(json.dumps(run_adjoint(args.n, fd_dirs=args.steps)[0]))
         return 0
     if args.stage == "ensemble":
-        print(json.dumps(run_ensemble()))
+        print(json.dumps(run_ensemble()[0]))
         return 0
     if args.stage == "lpt":
         print(json.dumps(run_lpt(args.n, args.steps)))
