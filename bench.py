@@ -796,7 +796,7 @@ def run_stage(args):
         rng = np.random.Generator(np.random.PCG64(61))
         X = pm.positions_to_device(inputs.to_fixed_point(inputs.lattice(n) + rng.uniform(-0.45, 0.45, (3, n ** 3)) / n))
     rho = None
-    if args.stage in ("mg", "fr"):
+    if args.stage in ("mg", "fr", "fft"):
         g = inputs.random_field(n, 62)
         r = np.exp(0.7 * g)
         rho = torch.from_numpy((r / r.mean()).astype(np.float32)).cuda()
@@ -820,6 +820,9 @@ def run_stage(args):
         elif args.stage == "interp":
             gr = torch.randn((3, n, n, n), device="cuda")
             pm.interp(gr, X)
+        elif args.stage == "fft":
+            ws = ws if ws is not None else pm.workspace(n, 0, pm.PM_WS_FFT)
+            pm.poisson_fft(rho, scale=0.45, kind=pm.PM_POISSON_FFT7, ws=ws)
 
     for _ in range(args.warmup):
         once()
@@ -844,7 +847,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--lean", action="store_true",
                     help="f(R) device-timed steps only (no Newtonian line, e2e or CPU baseline): for profilers")
-    ap.add_argument("--stage", choices=["sort", "deposit", "mg", "fr", "interp", "adjoint", "ensemble", "lpt", "step"],
+    ap.add_argument("--stage", choices=["sort", "deposit", "mg", "fr", "fft", "interp", "adjoint", "ensemble", "lpt",
+                                        "step"],
                     help="time one stage alone on synthetic inputs (for profilers)")
     ap.add_argument("--n", type=int, default=256, help="grid size for --stage")
     ap.add_argument("--smoother", type=int, default=2,
