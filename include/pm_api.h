@@ -58,7 +58,8 @@ enum {
   PM_ENOCONV = 3,   /* solver hit max_cycles without meeting its tolerance        */
   PM_ENAN = 4,      /* a residual norm was not finite                             */
   PM_ETIMEOUT = 5,  /* a device-side bounded wait gave up                         */
-  PM_ECUDA = 6      /* a CUDA runtime call failed (see pm_last_cuda_error)        */
+  PM_ECUDA = 6,     /* a CUDA runtime call failed (see pm_last_cuda_error)        */
+  PM_EIO = 7        /* a checkpoint file could not be written, read or matched    */
 };
 
 /* Human-readable name of a status code (static string). */
@@ -343,6 +344,24 @@ pm_status pm_step_host(pm_state* s, const pm_step_params* prm, pm_stats* st,
                        const uint32_t* X_in, const float* V_in,
                        uint32_t* X_out, float* V_out, void* stream);
 
+/* --------------------------------------------------------- checkpointing --
+ * Checkpoint and resume of a device-resident state (not part of the paper's
+ * method: a run of many steps can stop and continue).  The file holds a
+ * header (magic "PMGBCKP1", n, np, which optional arrays are present,
+ * have_prev) and then X [3][np] uint32, V [3][np] float32, id [np] (if
+ * s->id), phi [n^3] and eps [n^3] (if s->eps), in the host's byte order,
+ * copied through a host staging buffer of at most 64 MiB (host memory, freed
+ * before return).  Both calls synchronise `stream` first and are
+ * synchronous.  A step continued from a loaded state is bitwise the step the
+ * saved run would have taken (same library, same GPU model). */
+/* Writes s to the file at `path` (host string).  PM_EINVAL for bad
+ * arguments, PM_EIO if the file cannot be written. */
+pm_status pm_state_save(const pm_state* s, const char* path, void* stream);
+/* Reads the file at `path` into s, whose n, np and optional arrays (id,
+ * eps) must match the file's; sets s->have_prev from the file.  PM_EIO if
+ * the file cannot be read or does not match. */
+pm_status pm_state_load(pm_state* s, const char* path, void* stream);
+
 /* -------------------------------------------------------------- adjoints --
  * Reverse-mode derivatives of the Newtonian step, for gradients of losses
  * with respect to particle positions and velocities (and, through the
@@ -428,6 +447,25 @@ typedef struct {
 
 /* Workspace bytes for B boxes of n^3 cells with np_box particles each. */
 pm_status pm_batch_workspace_size(int n, int B, int64_t np_box, size_t* bytes);
+
+/* The stages of the step, one launch per kernel for B boxes (the `batch`
+ * argument of the boundary): box b's particles at b np_box .. (b+1) np_box - 1
+ * of every plane, its grids at b n^3 (scalar) and 3 b n^3 (vector); every box
+ * gives bitwise the result of the single-box call on it.  32 <= n for the
+ * deposit and the multigrid; the f(R) solver is single-box only.
+ *   pm_deposit_batch: rho [B][n^3] of X [3][B np_box]; workspace
+ *     pm_batch_workspace_size(n, B, np_box).
+ *   mg_solve_batch: exactly prm->fixed_cycles V-cycles per box, each box's
+ *     float64 mean of f removed (first_guess MG_GUESS_INPUT or
+ *     MG_GUESS_JACOBI); workspace pm_batch_workspace_size(n, B, 0).
+ *   pm_gradient_batch: g [B][3][n^3] of phi [B][n^3].
+ *   pm_interp_batch: acc [3][B np_box] of g [B][3][n^3] at X [3][B np_box]. */
+pm_status pm_deposit_batch(const uint32_t* X, int64_t np_box, int n, int B, float* rho, void* ws, size_t ws_bytes,
+                           void* stream);
+pm_status mg_solve_batch(const float* f, float* phi, int n, int B, const mg_params* prm, void* ws, size_t ws_bytes,
+                         void* stream);
+pm_status pm_gradient_batch(const float* phi, float* g, int n, int B, int order, void* stream);
+pm_status pm_interp_batch(const float* g, const uint32_t* X, int64_t np_box, int n, int B, float* acc, void* stream);
 
 /* One fused-kick leapfrog step of every box (pm_step's pipeline, batched):
  * sort by (box, cell), deposit, per-box source 3/2 a Om_b (rho - <rho>_b),

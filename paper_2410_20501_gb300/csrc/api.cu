@@ -1,6 +1,8 @@
 // C ABI of libpmgb: argument checks, workspace layout, the step pipeline,
 // host-side cosmology utilities and launch instrumentation.
 #include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <mutex>
@@ -260,6 +262,7 @@ const char* pm_status_string(pm_status s) {
     case PM_ENAN: return "PM_ENAN: non-finite residual";
     case PM_ETIMEOUT: return "PM_ETIMEOUT: device wait timed out";
     case PM_ECUDA: return "PM_ECUDA: CUDA error";
+    case PM_EIO: return "PM_EIO: checkpoint file error";
     default: return "unknown status";
   }
 }
@@ -555,6 +558,91 @@ pm_status pm_step_host(pm_state* st_, const pm_step_params* prm, pm_stats* stats
   return r;
 }
 
+namespace {
+
+const char kCkptMagic[8] = {'P', 'M', 'G', 'B', 'C', 'K', 'P', '1'};
+struct CkptHeader {
+  char magic[8];
+  int32_t n;
+  int32_t have_prev;
+  int64_t np;
+  int32_t has_id, has_eps;
+};
+
+// Copies `bytes` between device memory and a file through a host staging
+// buffer (dir 0: device -> file, 1: file -> device).
+pm_status ckpt_stream(FILE* f, void* dev, size_t bytes, int dir, char* stage, size_t cap) {
+  char* d = static_cast<char*>(dev);
+  for (size_t off = 0; off < bytes; off += cap) {
+    const size_t len = bytes - off < cap ? bytes - off : cap;
+    if (dir == 0) {
+      PM_TRY(cuda_status(cudaMemcpy(stage, d + off, len, cudaMemcpyDeviceToHost)));
+      if (fwrite(stage, 1, len, f) != len) return PM_EIO;
+    } else {
+      if (fread(stage, 1, len, f) != len) return PM_EIO;
+      PM_TRY(cuda_status(cudaMemcpy(d + off, stage, len, cudaMemcpyHostToDevice)));
+    }
+  }
+  return PM_OK;
+}
+
+pm_status ckpt_arrays(const pm_state& S, FILE* f, int dir) {
+  const size_t cap = (size_t)64 << 20;
+  const int64_t N = (int64_t)S.n * S.n * S.n;
+  const size_t total = (size_t)S.np * 24 + (S.id ? (size_t)S.np * 4 : 0) + (size_t)N * 4 * (S.eps ? 2 : 1);
+  const size_t sz = total < cap ? (total > 0 ? total : 1) : cap;
+  char* stage = static_cast<char*>(malloc(sz));
+  if (!stage) return PM_EIO;
+  pm_status r = ckpt_stream(f, S.X, (size_t)S.np * 12, dir, stage, sz);
+  if (r == PM_OK) r = ckpt_stream(f, S.V, (size_t)S.np * 12, dir, stage, sz);
+  if (r == PM_OK && S.id) r = ckpt_stream(f, S.id, (size_t)S.np * 4, dir, stage, sz);
+  if (r == PM_OK) r = ckpt_stream(f, S.phi, (size_t)N * 4, dir, stage, sz);
+  if (r == PM_OK && S.eps) r = ckpt_stream(f, S.eps, (size_t)N * 4, dir, stage, sz);
+  free(stage);
+  return r;
+}
+
+bool ckpt_args(const pm_state* s, const char* path) {
+  return s && path && valid_n(s->n) && valid_np(s->np) && (s->np == 0 || (s->X && s->V)) && s->phi;
+}
+
+}  // namespace
+
+pm_status pm_state_save(const pm_state* s, const char* path, void* stream) {
+  if (!ckpt_args(s, path)) return PM_EINVAL;
+  PM_TRY(cuda_status(cudaStreamSynchronize(as_stream(stream))));
+  FILE* f = fopen(path, "wb");
+  if (!f) return PM_EIO;
+  CkptHeader h;
+  memset(&h, 0, sizeof(h));
+  memcpy(h.magic, kCkptMagic, 8);
+  h.n = s->n;
+  h.have_prev = s->have_prev;
+  h.np = s->np;
+  h.has_id = s->id != nullptr;
+  h.has_eps = s->eps != nullptr;
+  pm_status r = fwrite(&h, sizeof(h), 1, f) == 1 ? PM_OK : PM_EIO;
+  if (r == PM_OK) r = ckpt_arrays(*s, f, 0);
+  if (fclose(f) != 0 && r == PM_OK) r = PM_EIO;
+  return r;
+}
+
+pm_status pm_state_load(pm_state* s, const char* path, void* stream) {
+  if (!ckpt_args(s, path)) return PM_EINVAL;
+  PM_TRY(cuda_status(cudaStreamSynchronize(as_stream(stream))));
+  FILE* f = fopen(path, "rb");
+  if (!f) return PM_EIO;
+  CkptHeader h;
+  pm_status r = fread(&h, sizeof(h), 1, f) == 1 ? PM_OK : PM_EIO;
+  if (r == PM_OK && (memcmp(h.magic, kCkptMagic, 8) != 0 || h.n != s->n || h.np != s->np ||
+                     h.has_id != (s->id != nullptr) || h.has_eps != (s->eps != nullptr)))
+    r = PM_EIO;
+  if (r == PM_OK) r = ckpt_arrays(*s, f, 1);
+  fclose(f);
+  if (r == PM_OK) s->have_prev = h.have_prev;
+  return r;
+}
+
 pm_status pm_deposit_adj(const uint32_t* X, int64_t np, int n, const float* rho_bar, float* dX_bar, void* stream) {
   if (!valid_n(n) || !valid_np(np) || (np > 0 && (!X || !dX_bar)) || !rho_bar || !all_a16(X, rho_bar, dX_bar))
     return PM_EINVAL;
@@ -685,11 +773,66 @@ pm_status pm_step_batch(pm_batch_state* st_, const pm_batch_params* prm, void* s
   if (mp.smoother == 0) mp.smoother = 2;
   mp.first_guess = S.have_prev ? MG_GUESS_SCALED : MG_GUESS_JACOBI;
   if (!S.have_prev) mp.fixed_cycles = prm->cold_cycles;
-  PM_TRY(mg_solve_batch(Src{w.rho, 0.0f, w.box_mean, prm->src_scale}, S.phi, n, B, mp, prm->phi_rescale, w, s));
+  PM_TRY(mg_solve_batch_src(Src{w.rho, 0.0f, w.box_mean, prm->src_scale}, S.phi, n, B, mp, prm->phi_rescale, w, s));
   PM_TRY(force_interp_launch(S.phi, nullptr, 0.0f, 1, prm->grad_order, w.cellstart, w.Xs, w.Vs, nullptr, np, n,
                              nullptr, S.X, S.V, nullptr, 0.0f, 0.0f, 1, s, bt));
   S.have_prev = 1;
   return launch_status();
+}
+
+pm_status pm_deposit_batch(const uint32_t* X, int64_t np_box, int n, int B, float* rho, void* ws, size_t ws_bytes,
+                           void* stream) {
+  const int64_t np = (int64_t)B * np_box;
+  if (!valid_batch(n, B, np_box) || (np > 0 && !X) || !rho || !all_a16(X, rho)) return PM_EINVAL;
+  if (!ws || !aligned(ws)) return PM_EINVAL;
+  if (ws_bytes < layout_workspace(nullptr, nullptr, n, np, PM_WS_STEP, B)) return PM_ENOMEM;
+  Workspace w;
+  layout_workspace(&w, ws, n, np, PM_WS_STEP, B);
+  cudaStream_t s = as_stream(stream);
+  Batch bt;
+  bt.B = B;
+  bt.np_box = np_box;
+  uint32_t* perm;
+  PM_TRY(sort_cells(X, np, n, w, s, w.cellstart, &perm, bt));
+  PM_TRY(permute_particles(perm, np, X, nullptr, nullptr, w.Xs, nullptr, nullptr, s));
+  PM_TRY(deposit_sorted_batch(w.Xs, np_box, B, w.cellstart, n, rho, w.partials, w.box_mean, s, crowded(w)));
+  return launch_status();
+}
+
+pm_status mg_solve_batch(const float* f, float* phi, int n, int B, const mg_params* prm, void* ws, size_t ws_bytes,
+                         void* stream) {
+  if (!valid_batch(n, B, 0) || !f || !phi || !valid_mg(prm) || prm->fixed_cycles < 1 || !all_a16(f, phi))
+    return PM_EINVAL;
+  if (prm->first_guess == MG_GUESS_SCALED) return PM_EINVAL;   // a per-box factor is pm_step_batch's business
+  if (!ws || !aligned(ws)) return PM_EINVAL;
+  if (ws_bytes < layout_workspace(nullptr, nullptr, n, 0, PM_WS_MG, B)) return PM_ENOMEM;
+  Workspace w;
+  layout_workspace(&w, ws, n, 0, PM_WS_MG, B);
+  cudaStream_t s = as_stream(stream);
+  const int64_t N = (int64_t)n * n * n;
+  for (int b = 0; b < B; ++b) PM_TRY(grid_mean(f + b * N, N, w.partials, w.box_mean + b, s));
+  mg_params mp = *prm;
+  if (mp.smoother == 0) mp.smoother = 2;
+  return mg_solve_batch_src(Src{f, 1.0f, w.box_mean, nullptr}, phi, n, B, mp, nullptr, w, s);
+}
+
+pm_status pm_gradient_batch(const float* phi, float* g, int n, int B, int order, void* stream) {
+  if (!valid_n(n) || B < 1 || !phi || !g || (order != 3 && order != 5 && order != 7) || !all_a16(phi, g))
+    return PM_EINVAL;
+  return gradient_launch(phi, nullptr, 0.0f, g, n, order, false, as_stream(stream), B);
+}
+
+pm_status pm_interp_batch(const float* g, const uint32_t* X, int64_t np_box, int n, int B, float* acc,
+                          void* stream) {
+  const int64_t np = (int64_t)B * np_box;
+  if (!valid_n(n) || B < 1 || np_box < 0 || np >= ((int64_t)1 << 31) || !g || (np > 0 && (!X || !acc)) ||
+      !all_a16(g, X, acc))
+    return PM_EINVAL;
+  Batch bt;
+  bt.B = B;
+  bt.np_box = np_box;
+  return interp_launch(g, X, nullptr, nullptr, np, n, acc, nullptr, nullptr, nullptr, 0.0f, 0.0f, 0, false,
+                       as_stream(stream), bt);
 }
 
 double pm_dt_supercomoving(double Om, double OL, double a0, double a1) {

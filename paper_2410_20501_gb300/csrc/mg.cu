@@ -560,7 +560,7 @@ pm_status fetch_scalars(const double* dev, double* host, int count, cudaStream_t
   return PM_OK;
 }
 
-pm_status mg_solve_batch(Src f, float* phi, int n, int B, const mg_params& prm, const float* gbox, Workspace& w,
+pm_status mg_solve_batch_src(Src f, float* phi, int n, int B, const mg_params& prm, const float* gbox, Workspace& w,
                          cudaStream_t s) {
   if (B < 1 || prm.fixed_cycles < 1) return PM_EINVAL;
   MG g;

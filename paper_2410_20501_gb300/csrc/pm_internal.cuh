@@ -185,7 +185,7 @@ pm_status mg_solve_src(Src f, float* phi, int n, const mg_params& prm, mg_stats*
                        Workspace& w, cudaStream_t s);
 // Batched multigrid: fixed cycles only (prm.fixed_cycles > 0); the warm start
 // MG_GUESS_SCALED takes the per-box factors gbox [B] (device).
-pm_status mg_solve_batch(Src f, float* phi, int n, int B, const mg_params& prm, const float* gbox,
+pm_status mg_solve_batch_src(Src f, float* phi, int n, int B, const mg_params& prm, const float* gbox,
                          Workspace& w, cudaStream_t s);
 pm_status fr_solve_src(Src b, float* eps, int n, const fr_params& prm, mg_stats* st,
                        Workspace& w, cudaStream_t s);

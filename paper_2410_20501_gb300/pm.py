@@ -23,7 +23,7 @@ PM_POISSON_MG, PM_POISSON_FFT7, PM_POISSON_FFT = 0, 1, 2
 MG_GUESS_INPUT, MG_GUESS_JACOBI, MG_GUESS_SCALED = 0, 1, 2
 PM_GRAVITY_NEWTON, PM_GRAVITY_FR, PM_GRAVITY_PARAM = 0, 1, 2
 STATUS = {0: "PM_OK", 1: "PM_EINVAL", 2: "PM_ENOMEM", 3: "PM_ENOCONV", 4: "PM_ENAN", 5: "PM_ETIMEOUT",
-          6: "PM_ECUDA"}
+          6: "PM_ECUDA", 7: "PM_EIO"}
 
 
 class PMError(RuntimeError):
@@ -138,9 +138,19 @@ _SIGS = {
                                                ctypes.POINTER(ctypes.c_size_t)]),
     "pm_step_batch": (ctypes.c_int, [ctypes.POINTER(pm_batch_state), ctypes.POINTER(pm_batch_params),
                                      ctypes.c_void_p]),
+    "pm_deposit_batch": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_int,
+                                        ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
+    "mg_solve_batch": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
+                                      ctypes.POINTER(mg_params), ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
+    "pm_gradient_batch": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                         ctypes.c_void_p]),
+    "pm_interp_batch": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_int,
+                                       ctypes.c_void_p, ctypes.c_void_p]),
     "pm_step_adj": (ctypes.c_int, [ctypes.POINTER(pm_state), ctypes.POINTER(pm_step_params), ctypes.c_void_p,
                                    ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                    ctypes.c_void_p]),
+    "pm_state_save": (ctypes.c_int, [ctypes.POINTER(pm_state), ctypes.c_char_p, ctypes.c_void_p]),
+    "pm_state_load": (ctypes.c_int, [ctypes.POINTER(pm_state), ctypes.c_char_p, ctypes.c_void_p]),
     "pm_dt_supercomoving": (ctypes.c_double, [ctypes.c_double] * 4),
     "pm_growth_D": (ctypes.c_double, [ctypes.c_double] * 3),
     "pm_next_timestep": (ctypes.c_int, [ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int,
@@ -544,6 +554,15 @@ class Simulation:
                                  _p(V_bar_out, torch.float32), _p(xb), _p(vb), _stream()), "pm_step_adj")
         return xb, vb
 
+    def save(self, path):
+        """pm_state_save: checkpoint the particles, potentials and warm-start
+        flag to a file."""
+        _check(lib().pm_state_save(ctypes.byref(self.state), os.fsencode(path), _stream()), "pm_state_save")
+
+    def load(self, path):
+        """pm_state_load: resume from a checkpoint of a state of the same sizes."""
+        _check(lib().pm_state_load(ctypes.byref(self.state), os.fsencode(path), _stream()), "pm_state_load")
+
     def positions(self):
         return positions_to_host(self.X)
 
@@ -558,6 +577,46 @@ def batch_workspace(n, B, np_box, device="cuda"):
     size = ctypes.c_size_t()
     _check(lib().pm_batch_workspace_size(n, B, np_box, ctypes.byref(size)), "pm_batch_workspace_size")
     return torch.empty(size.value, dtype=torch.uint8, device=device)
+
+
+def deposit_batch(X, n, B, ws=None):
+    """pm_deposit_batch: densities [B, n, n, n] of B boxes, X int32 bits [3, B * np_box]."""
+    np_box = X.shape[1] // B
+    ws = ws if ws is not None else batch_workspace(n, B, np_box, X.device)
+    rho = torch.empty((B, n, n, n), dtype=torch.float32, device=X.device)
+    _check(lib().pm_deposit_batch(_p(X, torch.int32), np_box, n, B, _p(rho), _p(ws), ws.numel(), _stream()),
+           "pm_deposit_batch")
+    return rho
+
+
+def mg_solve_batch(f, phi=None, ws=None, **params):
+    """mg_solve_batch: fixed V-cycles on B boxes, f [B, n, n, n]; returns phi."""
+    B, n = f.shape[0], f.shape[1]
+    prm = default_mg(**params)
+    if phi is None:
+        phi = torch.zeros_like(f)
+        if "first_guess" not in params:
+            prm.first_guess = MG_GUESS_JACOBI
+    ws = ws if ws is not None else batch_workspace(n, B, 0, f.device)
+    _check(lib().mg_solve_batch(_p(f, torch.float32), _p(phi, torch.float32), n, B, ctypes.byref(prm), _p(ws),
+                                ws.numel(), _stream()), "mg_solve_batch")
+    return phi
+
+
+def gradient_batch(phi, order=5):
+    B, n = phi.shape[0], phi.shape[1]
+    g = torch.empty((B, 3, n, n, n), dtype=torch.float32, device=phi.device)
+    _check(lib().pm_gradient_batch(_p(phi, torch.float32), _p(g), n, B, order, _stream()), "pm_gradient_batch")
+    return g
+
+
+def interp_batch(g, X):
+    B, n = g.shape[0], g.shape[2]
+    np_box = X.shape[1] // B
+    acc = torch.empty((3, X.shape[1]), dtype=torch.float32, device=X.device)
+    _check(lib().pm_interp_batch(_p(g, torch.float32), _p(X, torch.int32), np_box, n, B, _p(acc), _stream()),
+           "pm_interp_batch")
+    return acc
 
 
 class Ensemble:

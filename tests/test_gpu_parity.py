@@ -467,3 +467,49 @@ def test_max_speed_matches_host(pm, N):
     got = pm.max_speed(torch.from_numpy(V).cuda(), n, ws, pm.PM_WS_STEP)
     ref = float(np.sqrt((V.astype(np.float64) ** 2).sum(0)).max()) if N else 0.0
     assert got == pytest.approx(ref, rel=1e-6, abs=0.0)
+
+
+@pytest.mark.parametrize("gravity", ["newton", "fr"])
+def test_checkpoint_resume_is_bitwise_the_uninterrupted_run(pm, tmp_path, gravity):
+    """pm_state_save after three steps, pm_state_load into a fresh state, two
+    more steps: bitwise the particles (and ids, potentials) of five steps
+    without the interruption."""
+    n = 32
+    X, V = inputs.lpt_ics(n, float(n), 0.3, 0.7, 0.2, seed=31, order=2)
+    mk = lambda: pm.Simulation(X, V, n, Om=0.3, OL=0.7, boxsize=float(n), gravity=gravity, track_ids=True,
+                               mg=pm.default_mg(tol=1e-7, fixed_cycles=2), fr=pm.default_fr(cycles=1))
+    steps = [(0.2 + 0.01 * i, 0.01, 0.01) for i in range(5)]
+    ref = mk()
+    for s in steps:
+        ref.step(*s)
+    first = mk()
+    for s in steps[:3]:
+        first.step(*s)
+    path = str(tmp_path / "state.ckpt")
+    first.save(path)
+    resumed = mk()
+    resumed.load(path)
+    assert resumed.state.have_prev == 1
+    for s in steps[3:]:
+        resumed.step(*s)
+    assert np.array_equal(resumed.positions(), ref.positions())
+    assert np.array_equal(resumed.velocities(), ref.velocities())
+    assert np.array_equal(resumed.particle_ids(), ref.particle_ids())
+    assert torch.equal(resumed.phi, ref.phi)
+    if gravity == "fr":
+        assert torch.equal(resumed.eps, ref.eps)
+
+
+def test_checkpoint_mismatch_is_an_io_error(pm, tmp_path):
+    n = 16
+    X = inputs.uniform_particles(1000, 5)
+    a = pm.Simulation(X, np.zeros((3, 1000)), n, Om=1.0, OL=0.0, boxsize=16.0)
+    path = str(tmp_path / "a.ckpt")
+    a.save(path)
+    b = pm.Simulation(X[:, :999], np.zeros((3, 999)), n, Om=1.0, OL=0.0, boxsize=16.0)
+    with pytest.raises(pm.PMError) as e:
+        b.load(path)
+    assert e.value.code == 7
+    with pytest.raises(pm.PMError) as e:
+        a.load(str(tmp_path / "missing.ckpt"))
+    assert e.value.code == 7
