@@ -481,8 +481,6 @@ constexpr size_t force_interp_smem() {
                                              (IT_Z + 2 * Stencil<ORDER>::R + 2));
 }
 
-// Maximum over count float2 pairs, per component, into out[0], out[1]
-// (float64); one block.
 // Largest |v| of the velocity planes V [3][np]: one float2 (0, max) per block
 // (float bits of non-negative values order like unsigned integers).
 __global__ void __launch_bounds__(256) k_speed_max(const float* __restrict__ V, int64_t np,
@@ -502,6 +500,8 @@ __global__ void __launch_bounds__(256) k_speed_max(const float* __restrict__ V, 
   }
 }
 
+// Maximum over count float2 pairs, per component, into out[0], out[1]
+// (float64); one block.
 __global__ void __launch_bounds__(1024) k_max_pairs(const float2* __restrict__ v, int64_t count,
                                                     double* __restrict__ out) {
   __shared__ unsigned wa[32], wv[32];
