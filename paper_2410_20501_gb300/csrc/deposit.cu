@@ -85,14 +85,16 @@ __global__ void __launch_bounds__(T * T * T) k_deposit(const uint32_t* __restric
 
 // Streaming variant for n >= 32: a CTA owns a DTY x DTZ column of
 // destination cells and a chunk of x planes; it walks the source planes in
-// order, computes the 27 moments of each source cell of the plane (column
-// plus a one-cell halo in y and z: one cell per thread) into shared memory,
-// and lets every destination cell of the column add, in a fixed order, the
-// moments that point at it into a ring of three destination-plane
-// accumulators.  A destination plane is complete (and written) once the
-// source plane after it has been added.  The moments are double-buffered:
-// the sources of plane x are computed while the destinations add plane x - 1
-// (one barrier per plane).
+// order.  Source warps compute the 27 moments of each source cell of the plane
+// (column plus a one-cell halo in y and z: one cell per thread) into shared
+// memory; destination warps (two cells per thread, rows ty and ty + DTY / 2)
+// add, in a fixed order, the moments that point at each of their cells and
+// keep the three destination planes a source plane reaches in registers.  A
+// destination plane is complete (and written) once the source plane after it
+// has been added.  The moments are double-buffered: the sources of plane x are
+// computed while the destinations add plane x - 1 (one barrier per plane), and
+// the two roles run on different warps, so a plane step lasts as long as the
+// slower of them rather than their sum.
 //
 // Particle loads: a source thread copies the first KP particles of its cell
 // on the next plane into its own shared-memory slots with asynchronous copies
@@ -108,13 +110,16 @@ __global__ void __launch_bounds__(T * T * T) k_deposit(const uint32_t* __restric
 // one warp or one block per cell summed their moments beforehand
 // (k_medium_moments, k_crowded_moments), and the cell's thread reads the 27
 // sums.
-constexpr int DTY = 16, DTZ = 16, DEY = DTY + 2, DEZ = DTZ + 2, DNT = DTY * DTZ, DTHREADS = 512;
-constexpr int DPL = DEY * DEZ;   // source cells of a plane (one per thread)
-static_assert(DPL <= DTHREADS, "one source cell per thread");
+constexpr int DTY = 16, DTZ = 16, DEY = DTY + 2, DEZ = DTZ + 2, DNT = DTY * DTZ;
+constexpr int DPL = DEY * DEZ;                     // source cells of a plane (one per source thread)
+constexpr int DSRC_T = (DPL + 31) / 32 * 32;       // source warps
+constexpr int DDST_T = DNT / 2;                    // destination threads (two cells each)
+constexpr int DTHREADS = DSRC_T + DDST_T;
+static_assert(DDST_T % 32 == 0 && DTY % 2 == 0, "whole destination warps, two rows per thread");
 // Staged particles per cell and words per particle (x, y, z [, value]).
 template <bool VALS> struct DepositStage {
   static constexpr int KP = VALS ? 3 : 4, NC = VALS ? 4 : 3;
-  static constexpr size_t smem = sizeof(float) * (2 * 27 * DPL + 3 * DNT + 2 * KP * NC * DPL);
+  static constexpr size_t smem = sizeof(float) * (2 * 27 * DPL + 2 * KP * NC * DPL);
 };
 
 __device__ __forceinline__ void cp_async4(void* smem_dst, const void* gsrc) {
@@ -140,16 +145,16 @@ __global__ void __launch_bounds__(DTHREADS, 2) k_deposit_stream(const uint32_t* 
     rho += off;
     partial += (int64_t)blockIdx.z * nitems;
   }
-  float* Mom = sm;                                   // [2][27][PL]
-  float* Acc = sm + 2 * 27 * PL;                     // [3][DNT]
-  uint32_t* Slot = reinterpret_cast<uint32_t*>(Acc + 3 * DNT);   // [2][KP][NC][PL]
+  float* Mom = sm;                                                  // [2][27][PL]
+  uint32_t* Slot = reinterpret_cast<uint32_t*>(sm + 2 * 27 * PL);   // [2][KP][NC][PL]
   __shared__ double wsum[DTHREADS / 32];
   const int n = 1 << log2n, mask = n - 1;
   const int tiles_z = n / DTZ, tiles = (n / DTY) * tiles_z;
   const int tid = threadIdx.x;
-  const bool src = tid < PL, dst = tid < DNT;
+  const bool src = tid < PL, dst = tid >= DSRC_T;
   const int sly = tid / DEZ, slz = tid - sly * DEZ;            // source cell of this thread (if src)
-  const int ty = tid / DTZ, tz = tid - ty * DTZ;               // destination cell (if dst)
+  const int dt = tid - DSRC_T;
+  const int ty = dt / DTZ, tz = dt - ty * DTZ;                 // destination cells (ty, tz), (ty + DTY / 2, tz) (if dst)
   // copies the first KP particles [b, min(e, b + KP)) into slot buffer `buf`
   // (none for a crowded cell, whose moments are ready in `crowd`)
   auto stage = [&](int buf, uint32_t b, uint32_t e) {
@@ -170,8 +175,8 @@ __global__ void __launch_bounds__(DTHREADS, 2) k_deposit_stream(const uint32_t* 
     const int x0 = xc * chunk, x1 = x0 + chunk;
     const uint32_t cy = (uint32_t)((y0 - 1 + sly) & mask), cz = (uint32_t)((z0 - 1 + slz) & mask);
     auto cell_of = [&](int x) -> uint32_t { return ((((uint32_t)(x & mask)) << log2n | cy) << log2n) | cz; };
-    if (dst)
-      for (int q = 0; q < 3; ++q) Acc[q * DNT + tid] = 0.0f;
+    // destination ring per cell h: partial sums of planes xr - 1 (P) and xr (Q)
+    float P[2] = {0.0f, 0.0f}, Q[2] = {0.0f, 0.0f};
     float wsum_s = 0.0f, wsum_c = 0.0f;
     // pipeline registers: cell starts of planes xs and xs + 1
     uint32_t b0 = 0, e0 = 0, b1 = 0, e1 = 0;
@@ -247,27 +252,30 @@ __global__ void __launch_bounds__(DTHREADS, 2) k_deposit_stream(const uint32_t* 
       }
       const int xr = xs - 1;   // the source plane whose moments the destinations add now
       if (dst && xr >= x0 - 1) {
-        // destination plane xr + ox - 1 receives the moments with x offset ox - 1
+        // destination plane xr + ox - 1 receives the moments with x offset
+        // ox - 1; each plane sums its three source planes in the order they
+        // come (xr + 1, xr, xr - 1 for ox = 2, 1, 0)
+        const int done = xr - 1;   // complete after this source plane
 #pragma unroll
-        for (int ox = 0; ox < 3; ++ox) {
-          const int d = xr + ox - 1;
-          if (d < x0 || d >= x1) continue;
-          float a = 0.0f;
+        for (int h = 0; h < 2; ++h) {
+          const int cy = ty + h * (DTY / 2);
+          float a[3];
 #pragma unroll
-          for (int oy = 0; oy < 3; ++oy)
+          for (int ox = 0; ox < 3; ++ox) {
+            a[ox] = 0.0f;
 #pragma unroll
-            for (int oz = 0; oz < 3; ++oz)
-              a += MomR[((ox * 3 + oy) * 3 + oz) * PL + (ty + 2 - oy) * DEZ + (tz + 2 - oz)];
-          Acc[(d % 3) * DNT + tid] += a;
-        }
-        // plane xr - 1 has now received its three source planes
-        const int done = xr - 1;
-        if (done >= x0 && done < x1) {
-          float* slot = Acc + (done % 3) * DNT;
-          const float r = slot[tid] * scale;
-          rho[((((int64_t)done << log2n) | (y0 + ty)) << log2n) | (z0 + tz)] = r;
-          kahan_add(wsum_s, wsum_c, r);
-          slot[tid] = 0.0f;
+            for (int oy = 0; oy < 3; ++oy)
+#pragma unroll
+              for (int oz = 0; oz < 3; ++oz)
+                a[ox] += MomR[((ox * 3 + oy) * 3 + oz) * PL + (cy + 2 - oy) * DEZ + (tz + 2 - oz)];
+          }
+          const float r = (P[h] + a[0]) * scale;
+          P[h] = Q[h] + a[1];
+          Q[h] = 0.0f + a[2];
+          if (done >= x0 && done < x1) {
+            rho[((((int64_t)done << log2n) | (y0 + cy)) << log2n) | (z0 + tz)] = r;
+            kahan_add(wsum_s, wsum_c, r);
+          }
         }
       }
       __syncthreads();
