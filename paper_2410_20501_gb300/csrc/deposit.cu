@@ -316,25 +316,30 @@ __device__ __forceinline__ void add_moments(const uint32_t* __restrict__ Xs, int
 }
 
 // The 27 moments of each medium cell (kMedRun < particles <= kLongRun; the
-// cell sort's meds list), one warp per cell: lane i weighs the cell's i-th
-// particle, then the warp adds them in a fixed shuffle tree.  The moments go
-// to crowd[2a .. 2a + 26] (a = the cell's first rank: a medium cell owns at
-// least 28 floats there, so cells never share slots).
+// cell sort's meds list) and of each crowded cell of at most kWarpRun
+// particles (its runs list, longer runs skipped), one warp per cell: lane i
+// weighs the cell's particles i, i + 32, ... in that order, then the warp adds
+// the lanes' sums in a fixed shuffle tree.  The moments go to
+// crowd[2a .. 2a + 26] (a = the cell's first rank: a cell of more than
+// kMedRun particles owns at least 28 floats there, so cells never share
+// slots).
 template <bool VALS>
 __global__ void __launch_bounds__(256) k_medium_moments(const uint32_t* __restrict__ Xs, int64_t np,
                                                         const uint32_t* __restrict__ cellstart,
-                                                        const uint32_t* __restrict__ meds, int log2n,
+                                                        const uint32_t* __restrict__ meds,
+                                                        const uint32_t* __restrict__ runs, int log2n,
                                                         const float* __restrict__ vals, float* __restrict__ crowd) {
-  const uint32_t nmeds = meds[0];
+  const uint32_t nmeds = meds[0], ntot = nmeds + runs[0];
   const uint32_t lane = threadIdx.x & 31;
   const uint32_t warps = gridDim.x * 8;
-  for (uint32_t q = blockIdx.x * 8 + (threadIdx.x >> 5); q < nmeds; q += warps) {
-    const uint32_t c = meds[1 + q];
+  for (uint32_t q = blockIdx.x * 8 + (threadIdx.x >> 5); q < ntot; q += warps) {
+    const uint32_t c = q < nmeds ? meds[1 + q] : runs[1 + q - nmeds];
     const uint32_t a = cellstart[c], b = cellstart[c + 1];
+    if (b - a > kWarpRun) continue;   // the same for the whole warp: a block's cell
     float m[27];
 #pragma unroll
     for (int o = 0; o < 27; ++o) m[o] = 0.0f;
-    if (a + lane < b) add_moments<VALS>(Xs, np, a + lane, log2n, vals, m);
+    for (uint32_t p = a + lane; p < b; p += 32) add_moments<VALS>(Xs, np, p, log2n, vals, m);
 #pragma unroll
     for (int o = 0; o < 27; ++o) {
 #pragma unroll
@@ -351,8 +356,8 @@ __global__ void __launch_bounds__(256) k_medium_moments(const uint32_t* __restri
   }
 }
 
-// The 27 moments of each crowded cell (more than kLongRun particles; the
-// cell sort's runs list), one block per cell: thread t weighs particles
+// The 27 moments of each crowded cell of more than kWarpRun particles (the
+// cell sort's bigs list), one block per cell: thread t weighs particles
 // a + t, a + t + CT, ... of the cell in that order, then the block adds the
 // per-thread sums in a fixed tree (warp shuffles, then the warps in order), so
 // the result does not depend on scheduling.  The moments go to
@@ -361,13 +366,13 @@ constexpr int CT = 256;
 template <bool VALS>
 __global__ void __launch_bounds__(CT) k_crowded_moments(const uint32_t* __restrict__ Xs, int64_t np,
                                                         const uint32_t* __restrict__ cellstart,
-                                                        const uint32_t* __restrict__ runs, int log2n,
+                                                        const uint32_t* __restrict__ bigs, int log2n,
                                                         const float* __restrict__ vals, float* __restrict__ crowd) {
   __shared__ float part[CT / 32][27];
-  const uint32_t nruns = runs[0];
+  const uint32_t nruns = bigs[0];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (uint32_t q = blockIdx.x; q < nruns; q += gridDim.x) {
-    const uint32_t c = runs[1 + q];
+    const uint32_t c = bigs[1 + q];
     const uint32_t a = cellstart[c], b = cellstart[c + 1];
     float m[27];
 #pragma unroll
@@ -484,17 +489,17 @@ pm_status crowded_moments(const uint32_t* Xs, int64_t np, const uint32_t* cellst
                           const Crowded& cr, cudaStream_t s) {
   if (!cr.runs || np == 0) return PM_OK;
   if (vals)
-    PM_LAUNCH(K_DEPOSIT, 0.0, k_medium_moments<true>, 8 * 152, 256, 0, s, Xs, np, cellstart, cr.meds, ilog2(n), vals,
-              cr.moments);
+    PM_LAUNCH(K_DEPOSIT, 0.0, k_medium_moments<true>, 8 * 152, 256, 0, s, Xs, np, cellstart, cr.meds, cr.runs,
+              ilog2(n), vals, cr.moments);
   else
-    PM_LAUNCH(K_DEPOSIT, 0.0, k_medium_moments<false>, 8 * 152, 256, 0, s, Xs, np, cellstart, cr.meds, ilog2(n),
-              vals, cr.moments);
+    PM_LAUNCH(K_DEPOSIT, 0.0, k_medium_moments<false>, 8 * 152, 256, 0, s, Xs, np, cellstart, cr.meds, cr.runs,
+              ilog2(n), vals, cr.moments);
   const unsigned grid = 4 * 152;
   if (vals)
-    PM_LAUNCH(K_DEPOSIT, 0.0, k_crowded_moments<true>, grid, CT, 0, s, Xs, np, cellstart, cr.runs, ilog2(n), vals,
+    PM_LAUNCH(K_DEPOSIT, 0.0, k_crowded_moments<true>, grid, CT, 0, s, Xs, np, cellstart, cr.bigs, ilog2(n), vals,
               cr.moments);
   else
-    PM_LAUNCH(K_DEPOSIT, 0.0, k_crowded_moments<false>, grid, CT, 0, s, Xs, np, cellstart, cr.runs, ilog2(n), vals,
+    PM_LAUNCH(K_DEPOSIT, 0.0, k_crowded_moments<false>, grid, CT, 0, s, Xs, np, cellstart, cr.bigs, ilog2(n), vals,
               cr.moments);
   return PM_OK;
 }

@@ -68,6 +68,6 @@ extern "C" pm_status pm_deposit_noalloc(const uint32_t* X, int64_t np, int n, fl
   PM_TRY(sort_cells(X, np, n, w, s, w.cellstart, &perm));
   PM_TRY(permute_particles(perm, np, X, nullptr, nullptr, w.Xs, nullptr, nullptr, s));
   PM_TRY(deposit_sorted(w.Xs, np, w.cellstart, n, rho, w.partials, w.scalars, s,
-                        Crowded{w.runs, w.meds, reinterpret_cast<float*>(w.keyrank)}));
+                        Crowded{w.runs, w.meds, w.bigs, reinterpret_cast<float*>(w.keyrank)}));
   return launch_status();
 }

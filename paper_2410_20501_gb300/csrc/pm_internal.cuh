@@ -49,8 +49,9 @@ inline pm_status smem_attr(K* fn, size_t bytes) {
 
 // Cells holding more particles than this are "crowded": the cell sort lists
 // them (runs[0] = their number, runs[1 ..] = their cells, in no fixed order)
-// and orders their particles with a block each; the deposit takes their 27
-// TSC moments from a block each as well.
+// and orders their particles with a warp each (a block each beyond 256
+// particles, listed in bigs as well); the deposit takes their 27 TSC moments
+// from a block each.
 constexpr uint32_t kLongRun = 32;
 // Cells holding more than kMedRun and at most kLongRun particles are
 // "medium": listed apart (meds[0] = their number, meds[1 ..] = their cells)
@@ -58,6 +59,9 @@ constexpr uint32_t kLongRun = 32;
 // kMedRun particles owns at least 28 floats of the sort's 8-byte-per-rank key
 // buffer, at twice its first rank: room for its 27 moments.
 constexpr uint32_t kMedRun = 13;
+// Crowded cells of at most kWarpRun particles are ordered, and their moments
+// summed, by a warp each; longer ones (the sort's bigs list) by a block each.
+constexpr uint32_t kWarpRun = 256;
 
 inline int ilog2(int64_t v) { int l = 0; while ((int64_t(1) << (l + 1)) <= v) ++l; return l; }
 inline bool valid_n(int n) { return n >= 4 && n <= 1024 && (n & (n - 1)) == 0; }
@@ -110,7 +114,8 @@ struct Workspace {
   char* base;
   size_t total;
   // sort
-  uint2* keyrank; uint32_t* perm; uint32_t* runs; uint32_t* meds; uint32_t* scan_blocks; uint32_t* cellstart;
+  uint2* keyrank; uint32_t* perm; uint32_t* runs; uint32_t* meds; uint32_t* bigs; uint32_t* scan_blocks;
+  uint32_t* cellstart;
   // particles in cell order
   uint32_t* Xs; float* Vs; uint32_t* ids;
   // grids
@@ -136,6 +141,7 @@ size_t layout_workspace(Workspace* w, void* base, int n, int64_t np, uint32_t fl
 int64_t sort_scan_blocks(int64_t ncells);
 int64_t sort_runs_capacity(int64_t np);
 int64_t sort_meds_capacity(int64_t np);
+int64_t sort_bigs_capacity(int64_t np);
 int64_t reduce_partials_capacity(int n, int64_t np);
 // Work items of the streaming deposit for one box of n^3 cells (n >= 32).
 int deposit_items(int n);
@@ -158,6 +164,7 @@ pm_status permute_particles(const uint32_t* perm, int64_t np, const uint32_t* X,
 struct Crowded {
   const uint32_t* runs = nullptr;
   const uint32_t* meds = nullptr;
+  const uint32_t* bigs = nullptr;
   float* moments = nullptr;
 };
 // rho = (n^3/np) TSC sum over cell-sorted particles; writes sum(rho)/n^3 to *mean_out.

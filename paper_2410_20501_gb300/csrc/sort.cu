@@ -10,8 +10,9 @@
 // into cell starts; one pass writes each particle to its cell's start plus its
 // rank.  The atomics leave the order of equal keys to the hardware, so a last
 // pass restores the stable order (ascending input index) inside every cell:
-// one thread per cell for short runs, one block per cell (bitonic chunks in
-// shared memory, then merges) for long ones.  The permutation is therefore
+// one thread per cell for short runs, one warp per cell for medium and
+// crowded runs up to kWarpRun particles, one block per cell (bitonic chunks
+// in shared memory, then merges) for longer ones.  The permutation is therefore
 // bit-exact and deterministic, equal to a stable sort by key.
 //
 // The step writes particles back in cell order, so the input of the next
@@ -27,10 +28,11 @@ constexpr int SCAN_T = 1024;
 constexpr int SCAN_CHUNK = 4 * SCAN_T;
 constexpr int KT = 256;             // threads of the key, scatter and order kernels
 constexpr int CI = 4;               // particles per thread of the counting kernel
-constexpr uint32_t SHORT_RUN = kLongRun;  // runs up to this length are ordered by one thread
-constexpr int LT = 512;             // threads of a long-run block
+constexpr uint32_t SHORT_RUN = kLongRun;  // runs up to this length are ordered by one thread or warp
+constexpr int WT = 256;             // threads of the warp-per-run kernel
+constexpr int LT = 256;             // threads of a long-run block
 constexpr int LCH = 4096;           // elements sorted in shared memory at once
-constexpr int LONG_BLOCKS = 2 * 152;
+constexpr int LONG_BLOCKS = 8 * 152;
 
 
 // key = (i n + j) n + k of the cell holding each particle; with np_box > 0
@@ -100,10 +102,11 @@ __global__ void __launch_bounds__(KT) k_cell_scatter(const uint2* __restrict__ k
 // consecutive cells (one 16-byte load of their starts).  Runs of at most
 // kMedRun are insertion-sorted here; runs of at most SHORT_RUN are listed in
 // meds[1 ..] for k_cell_order_med, longer ones in runs[1 ..] for
-// k_cell_order_long (meds[0], runs[0] count them, zeroed).
+// k_cell_order_warp and, if longer than kWarpRun, in bigs[1 ..] for
+// k_cell_order_long as well (meds[0], runs[0], bigs[0] count them, zeroed).
 __global__ void __launch_bounds__(KT) k_cell_order(const uint32_t* __restrict__ cellstart, int64_t ncells,
                                                    uint32_t* __restrict__ perm, uint32_t* __restrict__ runs,
-                                                   uint32_t* __restrict__ meds) {
+                                                   uint32_t* __restrict__ meds, uint32_t* __restrict__ bigs) {
   const int64_t c0 = (blockIdx.x * (int64_t)KT + threadIdx.x) * 4;
   if (c0 >= ncells) return;
   const uint4 s4 = __ldg(reinterpret_cast<const uint4*>(cellstart + c0));
@@ -114,6 +117,7 @@ __global__ void __launch_bounds__(KT) k_cell_order(const uint32_t* __restrict__ 
     if (b - a < 2) continue;
     if (b - a > SHORT_RUN) {
       runs[1 + atomicAdd(runs, 1u)] = (uint32_t)(c0 + k);
+      if (b - a > kWarpRun) bigs[1 + atomicAdd(bigs, 1u)] = (uint32_t)(c0 + k);
       continue;
     }
     if (b - a > kMedRun) {
@@ -153,6 +157,54 @@ __global__ void __launch_bounds__(KT) k_cell_order_med(const uint32_t* __restric
   }
 }
 
+// Ranks of the R * 32 elements a lane may hold of a run of m distinct values
+// in buf (the warp's shared-memory copy): each lane counts, for each of its
+// elements buf[lane + 32 k], the run's smaller values and stores the element
+// at that rank of seg.
+template <int R>
+__device__ __forceinline__ void warp_rank_sort(const uint32_t* buf, uint32_t m, uint32_t lane, uint32_t* seg) {
+  uint32_t v[R], r[R];
+#pragma unroll
+  for (int k = 0; k < R; ++k) {
+    v[k] = lane + 32 * k < m ? buf[lane + 32 * k] : 0xffffffffu;
+    r[k] = 0;
+  }
+  for (uint32_t j = 0; j < m; ++j) {
+    const uint32_t u = buf[j];   // the same word for every lane: one broadcast read
+#pragma unroll
+    for (int k = 0; k < R; ++k) r[k] += u < v[k];
+  }
+#pragma unroll
+  for (int k = 0; k < R; ++k)
+    if (lane + 32 * k < m) seg[r[k]] = v[k];
+}
+
+// The crowded runs listed by k_cell_order of at most kWarpRun particles, one
+// warp each (many runs in flight per SM): the run is copied to the warp's
+// shared-memory buffer and every element moved to its rank.  Longer runs are
+// skipped here (k_cell_order_long orders them).
+__global__ void __launch_bounds__(WT) k_cell_order_warp(const uint32_t* __restrict__ cellstart,
+                                                        const uint32_t* __restrict__ runs,
+                                                        uint32_t* __restrict__ perm) {
+  __shared__ uint32_t sbuf[WT / 32][kWarpRun];
+  const uint32_t nruns = runs[0];
+  const uint32_t lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  uint32_t* buf = sbuf[wib];
+  const uint32_t warps = gridDim.x * (WT / 32);
+  for (uint32_t q = blockIdx.x * (WT / 32) + wib; q < nruns; q += warps) {
+    const uint32_t c = runs[1 + q];
+    const uint32_t a = cellstart[c], m = cellstart[c + 1] - a;
+    if (m > kWarpRun) continue;   // the same for the whole warp
+    uint32_t* seg = perm + a;
+    for (uint32_t t = lane; t < m; t += 32) buf[t] = seg[t];
+    __syncwarp();
+    if (m <= 64) warp_rank_sort<2>(buf, m, lane, seg);
+    else if (m <= 128) warp_rank_sort<4>(buf, m, lane, seg);
+    else warp_rank_sort<8>(buf, m, lane, seg);
+    __syncwarp();   // the buffer is reused by the warp's next run
+  }
+}
+
 // Ascending bitonic sort of s[0 .. p2) (p2 a power of two) by the block.
 __device__ void block_bitonic(uint32_t* s, int p2) {
   for (int k = 2; k <= p2; k <<= 1) {
@@ -188,9 +240,10 @@ __device__ void block_merge(const uint32_t* A, int64_t la, const uint32_t* B, in
   }
 }
 
-// The long runs listed by k_cell_order, one block each: LCH-element chunks
-// sorted in shared memory, then pairwise merges between the run and the same
-// ranks of `scratch`.  Runs already in order are left as they are.
+// The runs longer than kWarpRun (k_cell_order's bigs list), one block each:
+// LCH-element chunks sorted in shared memory, then pairwise merges between
+// the run and the same ranks of `scratch`.  Runs already in order are left as
+// they are.
 __global__ void __launch_bounds__(LT) k_cell_order_long(const uint32_t* __restrict__ cellstart,
                                                         const uint32_t* __restrict__ runs,
                                                         uint32_t* __restrict__ perm,
@@ -356,6 +409,7 @@ int64_t sort_scan_blocks(int64_t ncells) { return (ncells + 1 + SCAN_CHUNK - 1) 
 
 int64_t sort_runs_capacity(int64_t np) { return np / (SHORT_RUN + 1) + 2; }
 int64_t sort_meds_capacity(int64_t np) { return np / (kMedRun + 1) + 2; }
+int64_t sort_bigs_capacity(int64_t np) { return np / (kWarpRun + 1) + 2; }
 
 pm_status sort_cells(const uint32_t* X, int64_t np, int n, Workspace& w, cudaStream_t s, uint32_t* cellstart,
                      uint32_t** perm_out, const Batch& bt) {
@@ -365,6 +419,7 @@ pm_status sort_cells(const uint32_t* X, int64_t np, int n, Workspace& w, cudaStr
   PM_TRY(cuda_status(cudaMemsetAsync(cellstart, 0, (size_t)(ncells + 1) * 4, s)));
   PM_TRY(cuda_status(cudaMemsetAsync(w.runs, 0, 4, s)));   // no crowded or medium cells yet
   PM_TRY(cuda_status(cudaMemsetAsync(w.meds, 0, 4, s)));
+  PM_TRY(cuda_status(cudaMemsetAsync(w.bigs, 0, 4, s)));
   if (np == 0) return PM_OK;
   const int64_t np_box = bt.B > 1 ? bt.np_box : 0;
   const unsigned gc = grid_for(np, KT * CI);
@@ -375,9 +430,10 @@ pm_status sort_cells(const uint32_t* X, int64_t np, int n, Workspace& w, cudaStr
   PM_TRY(scan_u32(cellstart, ncells + 1, w.scan_blocks, s));
   PM_LAUNCH(K_SCATTER, 16.0 * np, k_cell_scatter, gc, KT, 0, s, w.keyrank, np, cellstart, w.perm);
   PM_LAUNCH(K_ORDER, 4.0 * ncells + 8.0 * np, k_cell_order, grid_for(ncells / 4, KT), KT, 0, s, cellstart, ncells,
-            w.perm, w.runs, w.meds);
+            w.perm, w.runs, w.meds, w.bigs);
   PM_LAUNCH(K_ORDER, 0.0, k_cell_order_med, 8 * 152, KT, 0, s, cellstart, w.meds, w.perm);
-  PM_LAUNCH(K_ORDER, 0.0, k_cell_order_long, LONG_BLOCKS, LT, 0, s, cellstart, w.runs, w.perm,
+  PM_LAUNCH(K_ORDER, 0.0, k_cell_order_warp, 8 * 152, WT, 0, s, cellstart, w.runs, w.perm);
+  PM_LAUNCH(K_ORDER, 0.0, k_cell_order_long, LONG_BLOCKS, LT, 0, s, cellstart, w.bigs, w.perm,
             reinterpret_cast<uint32_t*>(w.keyrank));
   return launch_status();
 }

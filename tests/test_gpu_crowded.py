@@ -1,5 +1,6 @@
 """Crowded cells (more particles than the cell sort orders with one thread):
-their 27 TSC moments come from one block per cell, summed in a fixed tree.
+their 27 TSC moments come from one warp per cell up to 256 particles and one
+block per cell beyond, summed in fixed trees.
 Deposit, the valued deposit of the interpolation adjoint and the step's
 accelerations on clustered particles against the FP64 oracle, and reruns
 bitwise equal."""
@@ -41,6 +42,7 @@ def clustered(n, counts, seed, background=0, spread=1.0):
 
 
 CASES = [(32, [13, 14, 20, 32, 33, 40, 100, 257, 1000, 5000, 20000], 30000),
+         (32, [64, 65, 128, 129, 255, 256, 257, 258, 600], 30000),
          (64, [14, 31, 33, 64, 500, 3000, 12000] + [14 + q % 19 for q in range(200)], 200000)]
 
 

@@ -72,6 +72,7 @@ def clustered(n, counts, seed, background=0):
 @pytest.mark.parametrize("counts,background", [
     ([12, 13, 14, 15, 20, 31, 32, 33], 3000),   # around the one-thread and one-warp limits
     ([32, 33, 34, 64, 100], 3000),              # around the one-warp limit
+    ([63, 64, 65, 127, 128, 129, 255, 256, 257, 1379], 20000),   # the warp kernel's tiers and its limit
     ([4095, 4096, 4097, 8193], 20000),          # one and several shared-memory chunks
     ([150000, 999, 2], 50000),                  # a long run merged over several passes
 ])
