@@ -113,7 +113,7 @@ pm_status pm_deposit(const uint32_t* X, int64_t np, int n, float* rho,
  * cudaMalloc's implicit device synchronisation, or a foreign-language binding
  * that has no device allocator; they cannot provide the workspace pm_deposit
  * needs.  This entry point computes the same density as pm_deposit but takes
- * its scratch from one static device array of 9 MiB inside the library (held
+ * its scratch from one static device array of 16 MiB inside the library (held
  * on every GPU that loads the library until the process exits), so it
  * allocates nothing.  The paper has no counterpart.
  *   Limits: n <= 64 and np <= 262144 (2^18); larger sizes return PM_EINVAL.

@@ -100,6 +100,8 @@ size_t layout_workspace(Workspace* w, void* base, int n, int64_t np, uint32_t fl
     w->runs = (uint32_t*)take((size_t)sort_runs_capacity(np) * 4);
     w->meds = (uint32_t*)take((size_t)sort_meds_capacity(np) * 4);
     w->bigs = (uint32_t*)take((size_t)sort_bigs_capacity(np) * 4);
+    w->smalls = (uint32_t*)take((size_t)sort_smalls_capacity(np) * 4);
+    w->moments = (float*)take((size_t)np * kMomStride * 4);
     w->scan_blocks = (uint32_t*)take((size_t)sort_scan_blocks(N) * 4);
     w->cellstart = (uint32_t*)take((size_t)(N + 1) * 4);
     w->Xs = (uint32_t*)take(3 * kb);
@@ -209,10 +211,8 @@ pm_status check_ws(Workspace& w, void* ws, size_t ws_bytes, int n, int64_t np, u
 
 bool valid_np(int64_t np) { return np >= 0 && np < ((int64_t)1 << 31); }
 
-// The crowded cells of the workspace's last cell sort, with the sort's key
-// buffer (8 bytes per particle, unused until the next sort) as the moment
-// scratch.
-Crowded crowded(const Workspace& w) { return Crowded{w.runs, w.meds, w.bigs, reinterpret_cast<float*>(w.keyrank)}; }
+// The cell lists of the workspace's last cell sort and its moment buffer.
+Crowded crowded(const Workspace& w) { return Crowded{w.runs, w.meds, w.bigs, w.smalls, w.moments}; }
 
 // 3/2 a Om of the supercomoving Poisson equation (§3.1), times mu(a) =
 // 1 + mu0 Omega_L(a)/Omega_L,0 = 1 + mu0 / E(a)^2 for parametrised gravity.

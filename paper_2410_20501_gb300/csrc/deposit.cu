@@ -106,10 +106,11 @@ __global__ void __launch_bounds__(T * T * T) k_deposit(const uint32_t* __restric
 // while plane x is processed.  The particles of a cell are weighed in the
 // same order (ascending index) either way.
 //
-// Medium and crowded cells (more than kMedRun particles) are not walked here:
-// one warp or one block per cell summed their moments beforehand
-// (k_medium_moments, k_crowded_moments), and the cell's thread reads the 27
-// sums.
+// Cells of more than kWalkRun particles are not walked here: eight lanes, a
+// warp or a block per cell summed their moments beforehand
+// (k_small_moments, k_medium_moments, k_crowded_moments), and the cell's
+// thread reads the 27 sums, so a source thread weighs at most kWalkRun
+// particles per plane.
 constexpr int DTY = 16, DTZ = 16, DEY = DTY + 2, DEZ = DTZ + 2, DNT = DTY * DTZ;
 constexpr int DPL = DEY * DEZ;                     // source cells of a plane (one per source thread)
 constexpr int DSRC_T = (DPL + 31) / 32 * 32;       // source warps
@@ -118,7 +119,7 @@ constexpr int DTHREADS = DSRC_T + DDST_T;
 static_assert(DDST_T % 32 == 0 && DTY % 2 == 0, "whole destination warps, two rows per thread");
 // Staged particles per cell and words per particle (x, y, z [, value]).
 template <bool VALS> struct DepositStage {
-  static constexpr int KP = VALS ? 3 : 4, NC = VALS ? 4 : 3;
+  static constexpr int KP = kWalkRun, NC = VALS ? 4 : 3;
   static constexpr size_t smem = sizeof(float) * (2 * 27 * DPL + 2 * KP * NC * DPL);
 };
 
@@ -156,9 +157,9 @@ __global__ void __launch_bounds__(DTHREADS, 2) k_deposit_stream(const uint32_t* 
   const int dt = tid - DSRC_T;
   const int ty = dt / DTZ, tz = dt - ty * DTZ;                 // destination cells (ty, tz), (ty + DTY / 2, tz) (if dst)
   // copies the first KP particles [b, min(e, b + KP)) into slot buffer `buf`
-  // (none for a crowded cell, whose moments are ready in `crowd`)
+  // (none for a cell whose moments are ready in `crowd`)
   auto stage = [&](int buf, uint32_t b, uint32_t e) {
-    if (crowd && e - b > kMedRun) return;
+    if (crowd && e - b > kWalkRun) return;
     uint32_t* s0 = Slot + buf * KP * NC * PL + tid;
 #pragma unroll
     for (int k = 0; k < KP; ++k) {
@@ -224,9 +225,9 @@ __global__ void __launch_bounds__(DTHREADS, 2) k_deposit_stream(const uint32_t* 
         };
         const uint32_t* s0 = Slot + (xs & 1) * KP * NC * PL + tid;
         const uint32_t cnt = e0 - b0;
-        if (crowd && cnt > kMedRun) {   // a medium or crowded cell: its moments were summed already
+        if (crowd && cnt > kWalkRun) {   // its moments were summed already
 #pragma unroll
-          for (int o = 0; o < 27; ++o) m[o] = __ldg(crowd + 2 * (int64_t)b0 + o);
+          for (int o = 0; o < 27; ++o) m[o] = __ldg(crowd + kMomStride * (int64_t)b0 + o);
         } else {
 #pragma unroll
         for (int k = 0; k < KP; ++k)
@@ -315,14 +316,61 @@ __device__ __forceinline__ void add_moments(const uint32_t* __restrict__ Xs, int
     }
 }
 
+// The 27 moments of each small cell (kWalkRun < particles <= kMedRun; the
+// cell sort's smalls list), eight lanes per cell (four cells per warp): lane g
+// of the group weighs the cell's particles g and g + 8, then the group adds
+// the lanes' sums in a fixed shuffle tree.  The moments go to
+// crowd[kMomStride a .. + 26] (a = the cell's first rank).
+template <bool VALS>
+__global__ void __launch_bounds__(256) k_small_moments(const uint32_t* __restrict__ Xs, int64_t np,
+                                                       const uint32_t* __restrict__ cellstart,
+                                                       const uint32_t* __restrict__ smalls, int log2n,
+                                                       const float* __restrict__ vals, float* __restrict__ crowd) {
+  static_assert(kMedRun <= 16, "two particles per lane of a group");
+  const uint32_t nsmall = smalls[0];
+  const uint32_t lane = threadIdx.x & 31, g = lane & 7;
+  const uint32_t groups = gridDim.x * 32;
+  // the groups of a warp take consecutive list entries; a warp with no entry
+  // left stops as a whole (the shuffles below need every lane)
+  for (uint32_t q0 = (blockIdx.x * 8 + (threadIdx.x >> 5)) * 4; q0 < nsmall; q0 += groups) {
+    const uint32_t q = q0 + (lane >> 3);
+    uint32_t a = 0, b = 0;
+    if (q < nsmall) {
+      const uint32_t c = smalls[1 + q];
+      a = cellstart[c];
+      b = cellstart[c + 1];
+    }
+    float m[27];
+#pragma unroll
+    for (int o = 0; o < 27; ++o) m[o] = 0.0f;
+    if (a + g < b) add_moments<VALS>(Xs, np, a + g, log2n, vals, m);
+    if (a + g + 8 < b) add_moments<VALS>(Xs, np, a + g + 8, log2n, vals, m);
+#pragma unroll
+    for (int o = 0; o < 27; ++o) {
+#pragma unroll
+      for (int d = 4; d > 0; d >>= 1) m[o] += __shfl_down_sync(0xffffffffu, m[o], d, 8);
+    }
+    // lane 0 of the group holds the sums; lane g writes moments g, g + 8, ...
+    float out[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+    for (int o = 0; o < 27; ++o) {
+      const float v = __shfl_sync(0xffffffffu, m[o], 0, 8);
+      if (g == (uint32_t)(o & 7)) out[o >> 3] = v;
+    }
+    if (q < nsmall) {
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        if (g + 8 * k < 27) crowd[kMomStride * (int64_t)a + g + 8 * k] = out[k];
+    }
+  }
+}
+
 // The 27 moments of each medium cell (kMedRun < particles <= kLongRun; the
 // cell sort's meds list) and of each crowded cell of at most kWarpRun
 // particles (its runs list, longer runs skipped), one warp per cell: lane i
 // weighs the cell's particles i, i + 32, ... in that order, then the warp adds
 // the lanes' sums in a fixed shuffle tree.  The moments go to
-// crowd[2a .. 2a + 26] (a = the cell's first rank: a cell of more than
-// kMedRun particles owns at least 28 floats there, so cells never share
-// slots).
+// crowd[kMomStride a .. + 26] (a = the cell's first rank).
 template <bool VALS>
 __global__ void __launch_bounds__(256) k_medium_moments(const uint32_t* __restrict__ Xs, int64_t np,
                                                         const uint32_t* __restrict__ cellstart,
@@ -352,7 +400,7 @@ __global__ void __launch_bounds__(256) k_medium_moments(const uint32_t* __restri
       const float v = __shfl_sync(0xffffffffu, m[o], 0);
       if (lane == (uint32_t)o) out = v;
     }
-    if (lane < 27) crowd[2 * (int64_t)a + lane] = out;
+    if (lane < 27) crowd[kMomStride * (int64_t)a + lane] = out;
   }
 }
 
@@ -361,7 +409,7 @@ __global__ void __launch_bounds__(256) k_medium_moments(const uint32_t* __restri
 // a + t, a + t + CT, ... of the cell in that order, then the block adds the
 // per-thread sums in a fixed tree (warp shuffles, then the warps in order), so
 // the result does not depend on scheduling.  The moments go to
-// crowd[2a .. 2a + 26], as for medium cells.
+// crowd[kMomStride a .. + 26], as for medium cells.
 constexpr int CT = 256;
 template <bool VALS>
 __global__ void __launch_bounds__(CT) k_crowded_moments(const uint32_t* __restrict__ Xs, int64_t np,
@@ -389,7 +437,7 @@ __global__ void __launch_bounds__(CT) k_crowded_moments(const uint32_t* __restri
       float t = 0.0f;
 #pragma unroll
       for (int w = 0; w < CT / 32; ++w) t += part[w][threadIdx.x];
-      crowd[2 * (int64_t)a + threadIdx.x] = t;
+      crowd[kMomStride * (int64_t)a + threadIdx.x] = t;
     }
     __syncthreads();
   }
@@ -488,6 +536,12 @@ namespace {
 pm_status crowded_moments(const uint32_t* Xs, int64_t np, const uint32_t* cellstart, int n, const float* vals,
                           const Crowded& cr, cudaStream_t s) {
   if (!cr.runs || np == 0) return PM_OK;
+  if (vals)
+    PM_LAUNCH(K_DEPOSIT, 0.0, k_small_moments<true>, 8 * 152, 256, 0, s, Xs, np, cellstart, cr.smalls, ilog2(n), vals,
+              cr.moments);
+  else
+    PM_LAUNCH(K_DEPOSIT, 0.0, k_small_moments<false>, 8 * 152, 256, 0, s, Xs, np, cellstart, cr.smalls, ilog2(n),
+              vals, cr.moments);
   if (vals)
     PM_LAUNCH(K_DEPOSIT, 0.0, k_medium_moments<true>, 8 * 152, 256, 0, s, Xs, np, cellstart, cr.meds, cr.runs,
               ilog2(n), vals, cr.moments);

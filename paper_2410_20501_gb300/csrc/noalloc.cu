@@ -12,7 +12,7 @@ namespace {
 
 constexpr int kNoallocMaxN = 64;
 constexpr int64_t kNoallocMaxNp = (int64_t)1 << 18;
-constexpr size_t kNoallocBytes = (size_t)9 << 20;   // 9 MiB: the pm_deposit workspace at the limits is 8.3 MiB
+constexpr size_t kNoallocBytes = (size_t)16 << 20;   // 16 MiB: the pm_deposit workspace at the limits is 14.5 MiB
 constexpr int kMaxDevices = 64;
 
 // Shared by every call on a device; it keeps the previous call's contents.
@@ -68,6 +68,6 @@ extern "C" pm_status pm_deposit_noalloc(const uint32_t* X, int64_t np, int n, fl
   PM_TRY(sort_cells(X, np, n, w, s, w.cellstart, &perm));
   PM_TRY(permute_particles(perm, np, X, nullptr, nullptr, w.Xs, nullptr, nullptr, s));
   PM_TRY(deposit_sorted(w.Xs, np, w.cellstart, n, rho, w.partials, w.scalars, s,
-                        Crowded{w.runs, w.meds, w.bigs, reinterpret_cast<float*>(w.keyrank)}));
+                        Crowded{w.runs, w.meds, w.bigs, w.smalls, w.moments}));
   return launch_status();
 }

@@ -55,10 +55,18 @@ inline pm_status smem_attr(K* fn, size_t bytes) {
 constexpr uint32_t kLongRun = 32;
 // Cells holding more than kMedRun and at most kLongRun particles are
 // "medium": listed apart (meds[0] = their number, meds[1 ..] = their cells)
-// and ordered, and their moments summed, by a warp each.  A cell of more than
-// kMedRun particles owns at least 28 floats of the sort's 8-byte-per-rank key
-// buffer, at twice its first rank: room for its 27 moments.
+// and ordered, and their moments summed, by a warp each.
 constexpr uint32_t kMedRun = 13;
+// The deposit's streaming kernel walks the particles of cells holding at most
+// kWalkRun of them; the 27 moments of every larger cell are summed beforehand
+// (cells of kWalkRun + 1 .. kMedRun particles, the sort's smalls list, by
+// eight lanes each) and stored at kMomStride times the cell's
+// first rank of a moment buffer of kMomStride floats per particle: a cell of
+// more than kWalkRun particles owns at least 30 floats there, room for its
+// 27.
+constexpr uint32_t kWalkRun = 4;
+constexpr int kMomStride = 6;
+static_assert(kMomStride * (kWalkRun + 1) >= 27, "room for the moments of the smallest summed cell");
 // Crowded cells of at most kWarpRun particles are ordered, and their moments
 // summed, by a warp each; longer ones (the sort's bigs list) by a block each.
 constexpr uint32_t kWarpRun = 256;
@@ -114,8 +122,9 @@ struct Workspace {
   char* base;
   size_t total;
   // sort
-  uint2* keyrank; uint32_t* perm; uint32_t* runs; uint32_t* meds; uint32_t* bigs; uint32_t* scan_blocks;
-  uint32_t* cellstart;
+  uint2* keyrank; uint32_t* perm; uint32_t* runs; uint32_t* meds; uint32_t* bigs; uint32_t* smalls;
+  uint32_t* scan_blocks; uint32_t* cellstart;
+  float* moments;   // kMomStride floats per particle (the deposit's summed cell moments)
   // particles in cell order
   uint32_t* Xs; float* Vs; uint32_t* ids;
   // grids
@@ -142,6 +151,7 @@ int64_t sort_scan_blocks(int64_t ncells);
 int64_t sort_runs_capacity(int64_t np);
 int64_t sort_meds_capacity(int64_t np);
 int64_t sort_bigs_capacity(int64_t np);
+int64_t sort_smalls_capacity(int64_t np);
 int64_t reduce_partials_capacity(int n, int64_t np);
 // Work items of the streaming deposit for one box of n^3 cells (n >= 32).
 int deposit_items(int n);
@@ -157,14 +167,16 @@ pm_status sort_cells(const uint32_t* X, int64_t np, int n, Workspace& w, cudaStr
 pm_status permute_particles(const uint32_t* perm, int64_t np, const uint32_t* X, const float* V,
                             const uint32_t* id, uint32_t* Xs, float* Vs, uint32_t* ids,
                             cudaStream_t s);
-// The crowded cells of the last cell sort (its runs list) and np floats of
-// scratch that nothing reads between the sort and the deposit (the sort's key
-// buffer): the deposit stores each crowded cell's 27 moments at the ranks of
-// its first particles.  runs == NULL: every cell is walked by one thread.
+// The cell lists of the last cell sort (smalls, meds, runs, bigs) and the
+// moment buffer (kMomStride floats per particle): the deposit sums the 27
+// moments of every cell of more than kWalkRun particles into it, at
+// kMomStride times the cell's first rank.  runs == NULL: every cell is walked
+// by one thread.
 struct Crowded {
   const uint32_t* runs = nullptr;
   const uint32_t* meds = nullptr;
   const uint32_t* bigs = nullptr;
+  const uint32_t* smalls = nullptr;
   float* moments = nullptr;
 };
 // rho = (n^3/np) TSC sum over cell-sorted particles; writes sum(rho)/n^3 to *mean_out.

@@ -98,32 +98,76 @@ __global__ void __launch_bounds__(KT) k_cell_scatter(const uint2* __restrict__ k
 }
 
 // Stable order inside each cell: the ranks of cell c, cellstart[c] ..
-// cellstart[c+1]-1, in ascending particle index.  A thread takes four
-// consecutive cells (one 16-byte load of their starts).  Runs of at most
-// kMedRun are insertion-sorted here; runs of at most SHORT_RUN are listed in
+// cellstart[c+1]-1, in ascending particle index.  A thread takes OC
+// consecutive cells (16-byte loads of their starts).  Runs of at most kMedRun
+// are insertion-sorted here (and listed in smalls[1 ..] if longer than
+// kWalkRun, for the deposit); runs of at most SHORT_RUN are listed in
 // meds[1 ..] for k_cell_order_med, longer ones in runs[1 ..] for
 // k_cell_order_warp and, if longer than kWarpRun, in bigs[1 ..] for
-// k_cell_order_long as well (meds[0], runs[0], bigs[0] count them, zeroed).
+// k_cell_order_long as well (list[0] counts the entries, zeroed).  A block
+// reserves the room for its entries of each list with one atomic (the lists'
+// counters are shared by the whole grid), its warps and lanes in order after
+// it; a block without entries skips the reservation and its second barrier.
+constexpr int OC = 8;
+__device__ __forceinline__ uint32_t cell_lists(uint32_t m) {   // bit L: the run goes to list L
+  return (m > kWalkRun && m <= kMedRun ? 1u : 0u) | (m > kMedRun && m <= SHORT_RUN ? 2u : 0u) |
+         (m > SHORT_RUN ? 4u : 0u) | (m > kWarpRun ? 8u : 0u);
+}
 __global__ void __launch_bounds__(KT) k_cell_order(const uint32_t* __restrict__ cellstart, int64_t ncells,
-                                                   uint32_t* __restrict__ perm, uint32_t* __restrict__ runs,
-                                                   uint32_t* __restrict__ meds, uint32_t* __restrict__ bigs) {
-  const int64_t c0 = (blockIdx.x * (int64_t)KT + threadIdx.x) * 4;
-  if (c0 >= ncells) return;
-  const uint4 s4 = __ldg(reinterpret_cast<const uint4*>(cellstart + c0));
-  const uint32_t st[5] = {s4.x, s4.y, s4.z, s4.w, __ldg(cellstart + c0 + 4)};
+                                                   uint32_t* __restrict__ perm, uint32_t* __restrict__ smalls,
+                                                   uint32_t* __restrict__ meds, uint32_t* __restrict__ runs,
+                                                   uint32_t* __restrict__ bigs) {
+  __shared__ uint32_t wtot[4][KT / 32];
+  __shared__ uint32_t lbase[4];
+  const int64_t c0 = (blockIdx.x * (int64_t)KT + threadIdx.x) * OC;
+  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t st[OC + 1];
 #pragma unroll
-  for (int k = 0; k < 4; ++k) {
+  for (int k = 0; k <= OC; ++k) st[k] = 0u;
+  if (c0 < ncells) {   // ncells is a multiple of OC
+#pragma unroll
+    for (int k = 0; k < OC; k += 4) {
+      const uint4 v = __ldg(reinterpret_cast<const uint4*>(cellstart + c0 + k));
+      st[k] = v.x; st[k + 1] = v.y; st[k + 2] = v.z; st[k + 3] = v.w;
+    }
+    st[OC] = __ldg(cellstart + c0 + OC);
+  }
+  // entries of this lane per list, their exclusive prefix over the warp
+  uint32_t cnt[4] = {0u, 0u, 0u, 0u}, pre[4];
+#pragma unroll
+  for (int k = 0; k < OC; ++k) {
+    const uint32_t f = cell_lists(st[k + 1] - st[k]);
+#pragma unroll
+    for (int L = 0; L < 4; ++L) cnt[L] += (f >> L) & 1u;
+  }
+#pragma unroll
+  for (int L = 0; L < 4; ++L) {
+    uint32_t x = cnt[L];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= (uint32_t)o) x += y;
+    }
+    pre[L] = x - cnt[L];
+    if (lane == 31) wtot[L][warp] = x;
+  }
+  const bool any = __syncthreads_or((cnt[0] | cnt[1] | cnt[2] | cnt[3]) != 0u);
+  if (any && threadIdx.x < 4) {   // one thread per list: the warps' offsets, the block's room
+    const int L = threadIdx.x;
+    uint32_t run = 0;
+    for (int w = 0; w < KT / 32; ++w) {
+      const uint32_t t = wtot[L][w];
+      wtot[L][w] = run;
+      run += t;
+    }
+    uint32_t* list = L == 0 ? smalls : L == 1 ? meds : L == 2 ? runs : bigs;
+    lbase[L] = run ? atomicAdd(list, run) : 0u;
+  }
+  // the short runs are ordered while the room is reserved
+#pragma unroll
+  for (int k = 0; k < OC; ++k) {
     const uint32_t a = st[k], b = st[k + 1];
-    if (b - a < 2) continue;
-    if (b - a > SHORT_RUN) {
-      runs[1 + atomicAdd(runs, 1u)] = (uint32_t)(c0 + k);
-      if (b - a > kWarpRun) bigs[1 + atomicAdd(bigs, 1u)] = (uint32_t)(c0 + k);
-      continue;
-    }
-    if (b - a > kMedRun) {
-      meds[1 + atomicAdd(meds, 1u)] = (uint32_t)(c0 + k);
-      continue;
-    }
+    if (b - a < 2 || b - a > kMedRun) continue;
     for (uint32_t p = a + 1; p < b; ++p) {
       const uint32_t v = perm[p];
       uint32_t q = p;
@@ -134,6 +178,20 @@ __global__ void __launch_bounds__(KT) k_cell_order(const uint32_t* __restrict__ 
       }
       if (q != p) perm[q] = v;
     }
+  }
+  if (!any) return;   // the same for the whole block
+  __syncthreads();
+  uint32_t pos[4];
+#pragma unroll
+  for (int L = 0; L < 4; ++L) pos[L] = 1u + lbase[L] + wtot[L][warp] + pre[L];
+#pragma unroll
+  for (int k = 0; k < OC; ++k) {
+    const uint32_t c = (uint32_t)(c0 + k);
+    const uint32_t f = cell_lists(st[k + 1] - st[k]);
+    if (f & 1u) smalls[pos[0]++] = c;
+    if (f & 2u) meds[pos[1]++] = c;
+    if (f & 4u) runs[pos[2]++] = c;
+    if (f & 8u) bigs[pos[3]++] = c;
   }
 }
 
@@ -410,6 +468,7 @@ int64_t sort_scan_blocks(int64_t ncells) { return (ncells + 1 + SCAN_CHUNK - 1) 
 int64_t sort_runs_capacity(int64_t np) { return np / (SHORT_RUN + 1) + 2; }
 int64_t sort_meds_capacity(int64_t np) { return np / (kMedRun + 1) + 2; }
 int64_t sort_bigs_capacity(int64_t np) { return np / (kWarpRun + 1) + 2; }
+int64_t sort_smalls_capacity(int64_t np) { return np / (kWalkRun + 1) + 2; }
 
 pm_status sort_cells(const uint32_t* X, int64_t np, int n, Workspace& w, cudaStream_t s, uint32_t* cellstart,
                      uint32_t** perm_out, const Batch& bt) {
@@ -420,6 +479,7 @@ pm_status sort_cells(const uint32_t* X, int64_t np, int n, Workspace& w, cudaStr
   PM_TRY(cuda_status(cudaMemsetAsync(w.runs, 0, 4, s)));   // no crowded or medium cells yet
   PM_TRY(cuda_status(cudaMemsetAsync(w.meds, 0, 4, s)));
   PM_TRY(cuda_status(cudaMemsetAsync(w.bigs, 0, 4, s)));
+  PM_TRY(cuda_status(cudaMemsetAsync(w.smalls, 0, 4, s)));
   if (np == 0) return PM_OK;
   const int64_t np_box = bt.B > 1 ? bt.np_box : 0;
   const unsigned gc = grid_for(np, KT * CI);
@@ -429,8 +489,8 @@ pm_status sort_cells(const uint32_t* X, int64_t np, int n, Workspace& w, cudaStr
     PM_LAUNCH(K_KEYS, 28.0 * np, k_cell_count<false>, gc, KT, 0, s, X, np, log2n, np_box, w.keyrank, cellstart);
   PM_TRY(scan_u32(cellstart, ncells + 1, w.scan_blocks, s));
   PM_LAUNCH(K_SCATTER, 16.0 * np, k_cell_scatter, gc, KT, 0, s, w.keyrank, np, cellstart, w.perm);
-  PM_LAUNCH(K_ORDER, 4.0 * ncells + 8.0 * np, k_cell_order, grid_for(ncells / 4, KT), KT, 0, s, cellstart, ncells,
-            w.perm, w.runs, w.meds, w.bigs);
+  PM_LAUNCH(K_ORDER, 4.0 * ncells + 8.0 * np, k_cell_order, grid_for(ncells / OC, KT), KT, 0, s, cellstart, ncells,
+            w.perm, w.smalls, w.meds, w.runs, w.bigs);
   PM_LAUNCH(K_ORDER, 0.0, k_cell_order_med, 8 * 152, KT, 0, s, cellstart, w.meds, w.perm);
   PM_LAUNCH(K_ORDER, 0.0, k_cell_order_warp, 8 * 152, WT, 0, s, cellstart, w.runs, w.perm);
   PM_LAUNCH(K_ORDER, 0.0, k_cell_order_long, LONG_BLOCKS, LT, 0, s, cellstart, w.bigs, w.perm,

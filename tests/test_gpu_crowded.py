@@ -1,6 +1,6 @@
-"""Crowded cells (more particles than the cell sort orders with one thread):
-their 27 TSC moments come from one warp per cell up to 256 particles and one
-block per cell beyond, summed in fixed trees.
+"""Cells of more than four particles: their 27 TSC moments are summed before
+the streaming deposit, by eight lanes per cell up to 13 particles, one warp
+per cell up to 256 and one block per cell beyond, in fixed trees.
 Deposit, the valued deposit of the interpolation adjoint and the step's
 accelerations on clustered particles against the FP64 oracle, and reruns
 bitwise equal."""
@@ -43,6 +43,7 @@ def clustered(n, counts, seed, background=0, spread=1.0):
 
 CASES = [(32, [13, 14, 20, 32, 33, 40, 100, 257, 1000, 5000, 20000], 30000),
          (32, [64, 65, 128, 129, 255, 256, 257, 258, 600], 30000),
+         (32, [4, 5, 6, 7, 8, 9, 12, 13] + [5 + q % 9 for q in range(300)], 30000),
          (64, [14, 31, 33, 64, 500, 3000, 12000] + [14 + q % 19 for q in range(200)], 200000)]
 
 
@@ -57,7 +58,7 @@ def test_crowded_deposit_matches_oracle(pm, n, counts, background):
 
 def test_crowded_interp_adj_matches_oracle(pm):
     n = 32
-    X = clustered(n, [40, 700, 6000], 9, 20000)
+    X = clustered(n, [5, 9, 13, 40, 700, 6000], 9, 20000)
     rng = np.random.Generator(np.random.PCG64(10))
     g32 = rng.standard_normal((3, n, n, n)).astype(np.float32)
     ab32 = rng.standard_normal((3, X.shape[1])).astype(np.float32)
