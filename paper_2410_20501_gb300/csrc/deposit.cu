@@ -106,9 +106,9 @@ __global__ void __launch_bounds__(T * T * T) k_deposit(const uint32_t* __restric
 // while plane x is processed.  The particles of a cell are weighed in the
 // same order (ascending index) either way.
 //
-// Cells of more than kWalkRun particles are not walked here: eight lanes, a
-// warp or a block per cell summed their moments beforehand
-// (k_small_moments, k_medium_moments, k_crowded_moments), and the cell's
+// Cells of more than kWalkRun particles are not walked here: eight or sixteen
+// lanes, a warp or a block per cell summed their moments beforehand
+// (k_group_moments, k_medium_moments, k_crowded_moments), and the cell's
 // thread reads the 27 sums, so a source thread weighs at most kWalkRun
 // particles per plane.
 constexpr int DTY = 16, DTZ = 16, DEY = DTY + 2, DEZ = DTZ + 2, DNT = DTY * DTZ;
@@ -316,27 +316,30 @@ __device__ __forceinline__ void add_moments(const uint32_t* __restrict__ Xs, int
     }
 }
 
-// The 27 moments of each small cell (kWalkRun < particles <= kMedRun; the
-// cell sort's smalls list), eight lanes per cell (four cells per warp): lane g
-// of the group weighs the cell's particles g and g + 8, then the group adds
-// the lanes' sums in a fixed shuffle tree.  The moments go to
+// The 27 moments of each cell of a list of cells holding at most 2G
+// particles, G lanes per cell (32 / G cells per warp): the small cells
+// (kWalkRun < particles <= kMedRun, the sort's smalls list) with G = 8 and the
+// medium ones (kMedRun < particles <= kLongRun, its meds list) with G = 16.
+// Lane g of a group weighs the cell's particles g and g + G, then the group
+// adds the lanes' sums in a fixed shuffle tree.  The moments go to
 // crowd[kMomStride a .. + 26] (a = the cell's first rank).
-template <bool VALS>
-__global__ void __launch_bounds__(256) k_small_moments(const uint32_t* __restrict__ Xs, int64_t np,
+template <bool VALS, int G>
+__global__ void __launch_bounds__(256) k_group_moments(const uint32_t* __restrict__ Xs, int64_t np,
                                                        const uint32_t* __restrict__ cellstart,
-                                                       const uint32_t* __restrict__ smalls, int log2n,
+                                                       const uint32_t* __restrict__ list, int log2n,
                                                        const float* __restrict__ vals, float* __restrict__ crowd) {
-  static_assert(kMedRun <= 16, "two particles per lane of a group");
-  const uint32_t nsmall = smalls[0];
-  const uint32_t lane = threadIdx.x & 31, g = lane & 7;
-  const uint32_t groups = gridDim.x * 32;
+  static_assert(G == 8 || G == 16, "group width");
+  constexpr int PERW = 32 / G, NOUT = (27 + G - 1) / G;
+  const uint32_t ncells = list[0];
+  const uint32_t lane = threadIdx.x & 31, g = lane & (G - 1);
+  const uint32_t groups = gridDim.x * 8 * PERW;
   // the groups of a warp take consecutive list entries; a warp with no entry
   // left stops as a whole (the shuffles below need every lane)
-  for (uint32_t q0 = (blockIdx.x * 8 + (threadIdx.x >> 5)) * 4; q0 < nsmall; q0 += groups) {
-    const uint32_t q = q0 + (lane >> 3);
+  for (uint32_t q0 = (blockIdx.x * 8 + (threadIdx.x >> 5)) * PERW; q0 < ncells; q0 += groups) {
+    const uint32_t q = q0 + lane / G;
     uint32_t a = 0, b = 0;
-    if (q < nsmall) {
-      const uint32_t c = smalls[1 + q];
+    if (q < ncells) {
+      const uint32_t c = list[1 + q];
       a = cellstart[c];
       b = cellstart[c + 1];
     }
@@ -344,44 +347,44 @@ __global__ void __launch_bounds__(256) k_small_moments(const uint32_t* __restric
 #pragma unroll
     for (int o = 0; o < 27; ++o) m[o] = 0.0f;
     if (a + g < b) add_moments<VALS>(Xs, np, a + g, log2n, vals, m);
-    if (a + g + 8 < b) add_moments<VALS>(Xs, np, a + g + 8, log2n, vals, m);
+    if (a + g + G < b) add_moments<VALS>(Xs, np, a + g + G, log2n, vals, m);
 #pragma unroll
     for (int o = 0; o < 27; ++o) {
 #pragma unroll
-      for (int d = 4; d > 0; d >>= 1) m[o] += __shfl_down_sync(0xffffffffu, m[o], d, 8);
+      for (int d = G / 2; d > 0; d >>= 1) m[o] += __shfl_down_sync(0xffffffffu, m[o], d, G);
     }
-    // lane 0 of the group holds the sums; lane g writes moments g, g + 8, ...
-    float out[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    // lane 0 of the group holds the sums; lane g writes moments g, g + G, ...
+    float out[NOUT];
+#pragma unroll
+    for (int k = 0; k < NOUT; ++k) out[k] = 0.0f;
 #pragma unroll
     for (int o = 0; o < 27; ++o) {
-      const float v = __shfl_sync(0xffffffffu, m[o], 0, 8);
-      if (g == (uint32_t)(o & 7)) out[o >> 3] = v;
+      const float v = __shfl_sync(0xffffffffu, m[o], 0, G);
+      if (g == (uint32_t)(o % G)) out[o / G] = v;
     }
-    if (q < nsmall) {
+    if (q < ncells) {
 #pragma unroll
-      for (int k = 0; k < 4; ++k)
-        if (g + 8 * k < 27) crowd[kMomStride * (int64_t)a + g + 8 * k] = out[k];
+      for (int k = 0; k < NOUT; ++k)
+        if (g + G * k < 27) crowd[kMomStride * (int64_t)a + g + G * k] = out[k];
     }
   }
 }
 
-// The 27 moments of each medium cell (kMedRun < particles <= kLongRun; the
-// cell sort's meds list) and of each crowded cell of at most kWarpRun
-// particles (its runs list, longer runs skipped), one warp per cell: lane i
+// The 27 moments of each crowded cell of at most kWarpRun particles (the
+// cell sort's runs list, longer runs skipped), one warp per cell: lane i
 // weighs the cell's particles i, i + 32, ... in that order, then the warp adds
 // the lanes' sums in a fixed shuffle tree.  The moments go to
 // crowd[kMomStride a .. + 26] (a = the cell's first rank).
 template <bool VALS>
 __global__ void __launch_bounds__(256) k_medium_moments(const uint32_t* __restrict__ Xs, int64_t np,
                                                         const uint32_t* __restrict__ cellstart,
-                                                        const uint32_t* __restrict__ meds,
                                                         const uint32_t* __restrict__ runs, int log2n,
                                                         const float* __restrict__ vals, float* __restrict__ crowd) {
-  const uint32_t nmeds = meds[0], ntot = nmeds + runs[0];
+  const uint32_t ntot = runs[0];
   const uint32_t lane = threadIdx.x & 31;
   const uint32_t warps = gridDim.x * 8;
   for (uint32_t q = blockIdx.x * 8 + (threadIdx.x >> 5); q < ntot; q += warps) {
-    const uint32_t c = q < nmeds ? meds[1 + q] : runs[1 + q - nmeds];
+    const uint32_t c = runs[1 + q];
     const uint32_t a = cellstart[c], b = cellstart[c + 1];
     if (b - a > kWarpRun) continue;   // the same for the whole warp: a block's cell
     float m[27];
@@ -536,25 +539,26 @@ namespace {
 pm_status crowded_moments(const uint32_t* Xs, int64_t np, const uint32_t* cellstart, int n, const float* vals,
                           const Crowded& cr, cudaStream_t s) {
   if (!cr.runs || np == 0) return PM_OK;
-  if (vals)
-    PM_LAUNCH(K_DEPOSIT, 0.0, k_small_moments<true>, 8 * 152, 256, 0, s, Xs, np, cellstart, cr.smalls, ilog2(n), vals,
+  const int l2 = ilog2(n);
+  if (vals) {
+    PM_LAUNCH(K_DEPOSIT, 0.0, (k_group_moments<true, 8>), 8 * 152, 256, 0, s, Xs, np, cellstart, cr.smalls, l2, vals,
               cr.moments);
-  else
-    PM_LAUNCH(K_DEPOSIT, 0.0, k_small_moments<false>, 8 * 152, 256, 0, s, Xs, np, cellstart, cr.smalls, ilog2(n),
+    PM_LAUNCH(K_DEPOSIT, 0.0, (k_group_moments<true, 16>), 8 * 152, 256, 0, s, Xs, np, cellstart, cr.meds, l2, vals,
+              cr.moments);
+    PM_LAUNCH(K_DEPOSIT, 0.0, k_medium_moments<true>, 8 * 152, 256, 0, s, Xs, np, cellstart, cr.runs, l2, vals,
+              cr.moments);
+    PM_LAUNCH(K_DEPOSIT, 0.0, k_crowded_moments<true>, 4 * 152, CT, 0, s, Xs, np, cellstart, cr.bigs, l2, vals,
+              cr.moments);
+  } else {
+    PM_LAUNCH(K_DEPOSIT, 0.0, (k_group_moments<false, 8>), 8 * 152, 256, 0, s, Xs, np, cellstart, cr.smalls, l2,
               vals, cr.moments);
-  if (vals)
-    PM_LAUNCH(K_DEPOSIT, 0.0, k_medium_moments<true>, 8 * 152, 256, 0, s, Xs, np, cellstart, cr.meds, cr.runs,
-              ilog2(n), vals, cr.moments);
-  else
-    PM_LAUNCH(K_DEPOSIT, 0.0, k_medium_moments<false>, 8 * 152, 256, 0, s, Xs, np, cellstart, cr.meds, cr.runs,
-              ilog2(n), vals, cr.moments);
-  const unsigned grid = 4 * 152;
-  if (vals)
-    PM_LAUNCH(K_DEPOSIT, 0.0, k_crowded_moments<true>, grid, CT, 0, s, Xs, np, cellstart, cr.bigs, ilog2(n), vals,
+    PM_LAUNCH(K_DEPOSIT, 0.0, (k_group_moments<false, 16>), 8 * 152, 256, 0, s, Xs, np, cellstart, cr.meds, l2, vals,
               cr.moments);
-  else
-    PM_LAUNCH(K_DEPOSIT, 0.0, k_crowded_moments<false>, grid, CT, 0, s, Xs, np, cellstart, cr.bigs, ilog2(n), vals,
+    PM_LAUNCH(K_DEPOSIT, 0.0, k_medium_moments<false>, 8 * 152, 256, 0, s, Xs, np, cellstart, cr.runs, l2, vals,
               cr.moments);
+    PM_LAUNCH(K_DEPOSIT, 0.0, k_crowded_moments<false>, 4 * 152, CT, 0, s, Xs, np, cellstart, cr.bigs, l2, vals,
+              cr.moments);
+  }
   return PM_OK;
 }
 }  // namespace

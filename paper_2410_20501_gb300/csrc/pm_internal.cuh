@@ -54,8 +54,8 @@ inline pm_status smem_attr(K* fn, size_t bytes) {
 // from a block each.
 constexpr uint32_t kLongRun = 32;
 // Cells holding more than kMedRun and at most kLongRun particles are
-// "medium": listed apart (meds[0] = their number, meds[1 ..] = their cells)
-// and ordered, and their moments summed, by a warp each.
+// "medium": listed apart (meds[0] = their number, meds[1 ..] = their cells),
+// ordered by a warp each and their moments summed by sixteen lanes each.
 constexpr uint32_t kMedRun = 13;
 // The deposit's streaming kernel walks the particles of cells holding at most
 // kWalkRun of them; the 27 moments of every larger cell are summed beforehand
