@@ -327,11 +327,17 @@ __global__ void __launch_bounds__(1024) k_fr_coarse(float* __restrict__ e, Src b
   double best = norm2();
   const double target = (double)drop * (double)drop * best;
   int stale = 0;
+  // the cell of pair P (cells 2P, 2P + 1: same i, j) with colour col: k of
+  // 2P is even, so its colour is (i + j) & 1; every thread gets one cell of a
+  // pair per colour pass (the cells of one colour are independent)
+  auto cell_of = [&](int P, int col) -> int {
+    const int c0 = P << 1;
+    return c0 + ((col ^ ((c0 >> log2n) + (c0 >> (2 * log2n)))) & 1);
+  };
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
     for (int colour = 0; colour < 2; ++colour) {
-      for (int c = threadIdx.x; c < N; c += blockDim.x) {
-        const int k = c & m, j = (c >> log2n) & m, i = c >> (2 * log2n);
-        if (((i + j + k) & 1) != colour) continue;
+      for (int P = threadIdx.x; P < (N >> 1); P += blockDim.x) {
+        const int c = cell_of(P, colour);
         float nb[6];
         nbs(c, nb);
         se[c] = fr_update<NH>(se[c], nb, sbv[c], beta, kappa, q);
