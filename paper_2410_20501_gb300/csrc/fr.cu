@@ -295,8 +295,7 @@ __global__ void __launch_bounds__(1024) k_fr_coarse(float* __restrict__ e, Src b
                                                     float beta, float kappa, float q, int max_sweeps,
                                                     float drop) {
   __shared__ float se[4096], sbv[4096];
-  __shared__ double scratch[32];
-  __shared__ double r2;
+  __shared__ float2 scratch[33];
   const int n = 1 << log2n, m = n - 1, N = n * n * n;
   const float mean = load_mean(b);
   for (int c = threadIdx.x; c < N; c += blockDim.x) {
@@ -313,7 +312,9 @@ __global__ void __launch_bounds__(1024) k_fr_coarse(float* __restrict__ e, Src b
     nb[4] = se[(i << (2 * log2n)) | (j << log2n) | ((k + 1) & m)];
     nb[5] = se[(i << (2 * log2n)) | (j << log2n) | ((k - 1) & m)];
   };
-  auto norm2 = [&]() -> double {
+  // squared residual norm: per-thread compensated sums, then a compensated
+  // float pair over the block, the same in every thread
+  auto norm2 = [&]() -> float {
     float s = 0.0f, cmp = 0.0f;
     for (int c = threadIdx.x; c < N; c += blockDim.x) {
       float nb[6];
@@ -321,11 +322,11 @@ __global__ void __launch_bounds__(1024) k_fr_coarse(float* __restrict__ e, Src b
       const float d = sbv[c] - fr_op<NH>(se[c], nb, alpha, kappa);
       kahan_add(s, cmp, d * d);
     }
-    block_sum_to(&r2, s, cmp, scratch);
-    return r2;
+    const float2 r = block_pair_sum(s, cmp, scratch);
+    return r.x + r.y;
   };
-  double best = norm2();
-  const double target = (double)drop * (double)drop * best;
+  float best = norm2();
+  const float target = drop * drop * best;
   int stale = 0;
   // the cell of pair P (cells 2P, 2P + 1: same i, j) with colour col: k of
   // 2P is even, so its colour is (i + j) & 1; every thread gets one cell of a
@@ -344,9 +345,9 @@ __global__ void __launch_bounds__(1024) k_fr_coarse(float* __restrict__ e, Src b
       }
       __syncthreads();
     }
-    const double r = norm2();
+    const float r = norm2();
     if (r <= target) break;
-    if (r < 0.998 * best) {   // squared norms: a 0.1% improvement of the norm
+    if (r < 0.998f * best) {   // squared norms: a 0.1% improvement of the norm
       best = r;
       stale = 0;
     } else if (++stale >= 5) {

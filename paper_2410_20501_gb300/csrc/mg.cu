@@ -272,40 +272,6 @@ __global__ void k_prolong_correct(float* __restrict__ u, const float* __restrict
   }
 }
 
-// Sum over the block of per-thread compensated pairs (sum, comp), returned to
-// every thread as the same float pair (hi, lo): warp shuffles with error-free
-// additions, then warp 0 over the per-warp pairs, whose result thread 0
-// publishes in scratch[32] (so every thread takes the same decision from it).
-// All threads call it; scratch holds 33 pairs.
-__device__ __forceinline__ float2 block_pair_sum(float sum, float comp, float2* scratch) {
-  float s = sum - comp, c = 0.0f;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    const float os = __shfl_down_sync(0xffffffffu, s, o), oc = __shfl_down_sync(0xffffffffu, c, o);
-    float t, e;
-    two_sum(s, os, t, e);
-    s = t;
-    c = c + oc + e;
-  }
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  if (lane == 0) scratch[warp] = make_float2(s, c);
-  __syncthreads();
-  if (warp == 0) {
-    float2 v = lane < nw ? scratch[lane] : make_float2(0.0f, 0.0f);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const float os = __shfl_down_sync(0xffffffffu, v.x, o), oc = __shfl_down_sync(0xffffffffu, v.y, o);
-      float t, e;
-      two_sum(v.x, os, t, e);
-      v.x = t;
-      v.y = v.y + oc + e;
-    }
-    if (lane == 0) scratch[32] = v;
-  }
-  __syncthreads();
-  return scratch[32];
-}
-
 // Coarsest level (n <= 16) in one CTA: red-black SOR sweeps (factor omega)
 // until the residual norm dropped by `drop`, its running minimum stalls for 5
 // sweeps (float32 floor), or `max_sweeps` sweeps.  Thread t owns the cell

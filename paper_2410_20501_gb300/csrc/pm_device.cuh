@@ -68,6 +68,40 @@ __device__ __forceinline__ void block_sum_to(double* out, float sum, float comp,
   __syncthreads();
 }
 
+// Sum over the block of per-thread compensated pairs (sum, comp), returned to
+// every thread as the same float pair (hi, lo): warp shuffles with error-free
+// additions, then warp 0 over the per-warp pairs, whose result thread 0
+// publishes in scratch[32] (so every thread takes the same decision from it).
+// All threads call it; scratch holds 33 pairs.
+__device__ __forceinline__ float2 block_pair_sum(float sum, float comp, float2* scratch) {
+  float s = sum - comp, c = 0.0f;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float os = __shfl_down_sync(0xffffffffu, s, o), oc = __shfl_down_sync(0xffffffffu, c, o);
+    float t, e;
+    two_sum(s, os, t, e);
+    s = t;
+    c = c + oc + e;
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if (lane == 0) scratch[warp] = make_float2(s, c);
+  __syncthreads();
+  if (warp == 0) {
+    float2 v = lane < nw ? scratch[lane] : make_float2(0.0f, 0.0f);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const float os = __shfl_down_sync(0xffffffffu, v.x, o), oc = __shfl_down_sync(0xffffffffu, v.y, o);
+      float t, e;
+      two_sum(v.x, os, t, e);
+      v.x = t;
+      v.y = v.y + oc + e;
+    }
+    if (lane == 0) scratch[32] = v;
+  }
+  __syncthreads();
+  return scratch[32];
+}
+
 // Flat indices (32-bit: n <= 1024) of a cell's six periodic face neighbours in
 // the order x+, x-, y+, y-, z+, z-, for c = (i n + j) n + k.
 __device__ __forceinline__ void nb_index(uint32_t c, uint32_t i, uint32_t j, uint32_t k, int log2n,
