@@ -272,13 +272,16 @@ __global__ void k_prolong_correct(float* __restrict__ u, const float* __restrict
   }
 }
 
-// Coarsest level (n <= 16) in one CTA: red-black SOR sweeps (factor omega)
-// until the residual norm dropped by `drop`, its running minimum stalls for 5
-// sweeps (float32 floor), or `max_sweeps` sweeps.  Thread t owns the cell
-// pairs (2P, 2P+1), P = t, t + blockDim, ... (same i, j; k even and odd), so
-// each colour pass gives every thread one cell per pair.  The residual of a
-// black cell is taken from its own update (its neighbours are red and do not
-// move during the black pass); red residuals are recomputed after it.
+// Coarsest level (n <= 16) in one CTA of 1024 threads: red-black SOR sweeps
+// (factor omega) until the residual norm dropped by `drop`, its running
+// minimum stalls for 5 sweeps (float32 floor), or `max_sweeps` sweeps.  Thread
+// t owns the cell pairs (2P, 2P+1), P = t and t + 1024 (same i, j; k even and
+// odd), so each colour pass gives every thread one cell per pair.  The
+// residual of a black cell is taken from its own update (its neighbours are
+// red and do not move during the black pass).  The red residuals of a sweep
+// and the next sweep's red values come from the same neighbour sums (the black
+// cells do not move in between): the new red values are held in registers
+// until the sweep's norm has decided whether there is a next sweep.
 __global__ void __launch_bounds__(1024) k_mg_coarse(float* __restrict__ u, Src f, int log2n, float h2,
                                                     float omega, int max_sweeps, float drop,
                                                     int zero_guess) {
@@ -308,6 +311,12 @@ __global__ void __launch_bounds__(1024) k_mg_coarse(float* __restrict__ u, Src f
     const int c0 = P << 1;
     return c0 + ((col ^ ((c0 >> log2n) + (c0 >> (2 * log2n)))) & 1);
   };
+  // SOR update of cell c from its neighbour sum
+  auto sor = [&](int c, float nb) -> float {
+    const float ugs = (nb - h2 * sf[c]) * kSixth;
+    return (omega == 1.0f) ? ugs : omega * ugs + (1.0f - omega) * su[c];
+  };
+  const int P0 = threadIdx.x, P1 = threadIdx.x + blockDim.x;   // npair <= 2048 = 2 x 1024
   float2 r2p;
   {
     float s = 0.0f, cmp = 0.0f;
@@ -320,30 +329,41 @@ __global__ void __launch_bounds__(1024) k_mg_coarse(float* __restrict__ u, Src f
   float best = r2p.x + r2p.y;
   const float target = drop * drop * best;
   int stale = 0;
-  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
-    for (int P = threadIdx.x; P < npair; P += blockDim.x) {      // red
+  if (max_sweeps > 0) {   // the first sweep's red cells
+    for (int P = threadIdx.x; P < npair; P += blockDim.x) {
       const int c = cell_of(P, 0);
-      const float ugs = (nbsum(c) - h2 * sf[c]) * kSixth;
-      su[c] = (omega == 1.0f) ? ugs : omega * ugs + (1.0f - omega) * su[c];
+      su[c] = sor(c, nbsum(c));
     }
     __syncthreads();
+  }
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    // here the red cells hold this sweep's values
     float s = 0.0f, cmp = 0.0f;
     for (int P = threadIdx.x; P < npair; P += blockDim.x) {      // black, with its residual
       const int c = cell_of(P, 1);
       const float nb = nbsum(c);
-      const float ugs = (nb - h2 * sf[c]) * kSixth;
-      const float un = (omega == 1.0f) ? ugs : omega * ugs + (1.0f - omega) * su[c];
+      const float un = sor(c, nb);
       su[c] = un;
       const float d = sf[c] - (nb - 6.0f * un) * inv_h2;
       kahan_add(s, cmp, d * d);
     }
     __syncthreads();
-    for (int P = threadIdx.x; P < npair; P += blockDim.x) {      // red residuals
-      const int c = cell_of(P, 0);
-      const float d = sf[c] - (nbsum(c) - 6.0f * su[c]) * inv_h2;
+    // red residuals, and the next sweep's red values from the same sums
+    float pend0 = 0.0f, pend1 = 0.0f;
+    const int c0 = P0 < npair ? cell_of(P0, 0) : 0, c1 = P1 < npair ? cell_of(P1, 0) : 0;
+    if (P0 < npair) {
+      const float nb = nbsum(c0);
+      const float d = sf[c0] - (nb - 6.0f * su[c0]) * inv_h2;
       kahan_add(s, cmp, d * d);
+      pend0 = sor(c0, nb);
     }
-    r2p = block_pair_sum(s, cmp, scratch);
+    if (P1 < npair) {
+      const float nb = nbsum(c1);
+      const float d = sf[c1] - (nb - 6.0f * su[c1]) * inv_h2;
+      kahan_add(s, cmp, d * d);
+      pend1 = sor(c1, nb);
+    }
+    r2p = block_pair_sum(s, cmp, scratch);   // its barriers end every read of this sweep
     const float r = r2p.x + r2p.y;
     if (r <= target) break;
     if (r < 0.998f * best) {   // squared norms: a 0.1% improvement of the norm
@@ -351,6 +371,11 @@ __global__ void __launch_bounds__(1024) k_mg_coarse(float* __restrict__ u, Src f
       stale = 0;
     } else if (++stale >= 5) {
       break;                  // no progress for 5 sweeps: the float32 floor
+    }
+    if (sweep + 1 < max_sweeps) {   // the next sweep's red cells
+      if (P0 < npair) su[c0] = pend0;
+      if (P1 < npair) su[c1] = pend1;
+      __syncthreads();
     }
   }
   for (int c = threadIdx.x; c < N; c += blockDim.x) u[c] = su[c];
