@@ -85,16 +85,17 @@ __global__ void __launch_bounds__(T * T * T) k_deposit(const uint32_t* __restric
 
 // Streaming variant for n >= 32: a CTA owns a DTY x DTZ column of
 // destination cells and a chunk of x planes; it walks the source planes in
-// order.  Source warps compute the 27 moments of each source cell of the plane
-// (column plus a one-cell halo in y and z: one cell per thread) into shared
-// memory; destination warps (two cells per thread, rows ty and ty + DTY / 2)
-// add, in a fixed order, the moments that point at each of their cells and
-// keep the three destination planes a source plane reaches in registers.  A
-// destination plane is complete (and written) once the source plane after it
-// has been added.  The moments are double-buffered: the sources of plane x are
-// computed while the destinations add plane x - 1 (one barrier per plane), and
-// the two roles run on different warps, so a plane step lasts as long as the
-// slower of them rather than their sum.
+// order.  A source thread owns one (y, z) column of source cells (the column
+// plus a one-cell halo in y and z: one per thread) for the whole chunk and
+// keeps in registers the partial sums its column sends to the three
+// destination planes a source plane reaches (9 (y, z) offsets each): the
+// particles of source plane x add their TSC weight products to destination
+// planes x - 1, x and x + 1, after which plane x - 1 has everything from this
+// column and its 9 sums go to shared memory.  Destination warps (two cells
+// per thread, rows ty and ty + DTY / 2) add, in a fixed order, the 9 column
+// sums that point at each of their cells and write the density.  The sums
+// are double-buffered: sources emit plane x - 1 while the destinations add
+// plane x - 2 (one barrier per plane), on different warps.
 //
 // Particle loads: a source thread copies the first KP particles of its cell
 // on the next plane into its own shared-memory slots with asynchronous copies
@@ -109,7 +110,7 @@ __global__ void __launch_bounds__(T * T * T) k_deposit(const uint32_t* __restric
 // Cells of more than kWalkRun particles are not walked here: eight or sixteen
 // lanes, a warp or a block per cell summed their moments beforehand
 // (k_group_moments, k_medium_moments, k_crowded_moments), and the cell's
-// thread reads the 27 sums, so a source thread weighs at most kWalkRun
+// thread adds the 27 sums, so a source thread weighs at most kWalkRun
 // particles per plane.
 constexpr int DTY = 16, DTZ = 16, DEY = DTY + 2, DEZ = DTZ + 2, DNT = DTY * DTZ;
 constexpr int DPL = DEY * DEZ;                     // source cells of a plane (one per source thread)
@@ -120,7 +121,7 @@ static_assert(DDST_T % 32 == 0 && DTY % 2 == 0, "whole destination warps, two ro
 // Staged particles per cell and words per particle (x, y, z [, value]).
 template <bool VALS> struct DepositStage {
   static constexpr int KP = kWalkRun, NC = VALS ? 4 : 3;
-  static constexpr size_t smem = sizeof(float) * (2 * 27 * DPL + 2 * KP * NC * DPL);
+  static constexpr size_t smem = sizeof(float) * (2 * 9 * DPL + 2 * KP * NC * DPL);
 };
 
 __device__ __forceinline__ void cp_async4(void* smem_dst, const void* gsrc) {
@@ -146,14 +147,14 @@ __global__ void __launch_bounds__(DTHREADS, 2) k_deposit_stream(const uint32_t* 
     rho += off;
     partial += (int64_t)blockIdx.z * nitems;
   }
-  float* Mom = sm;                                                  // [2][27][PL]
-  uint32_t* Slot = reinterpret_cast<uint32_t*>(sm + 2 * 27 * PL);   // [2][KP][NC][PL]
+  float* Col = sm;                                                 // [2][9][PL] column sums
+  uint32_t* Slot = reinterpret_cast<uint32_t*>(sm + 2 * 9 * PL);   // [2][KP][NC][PL]
   __shared__ double wsum[DTHREADS / 32];
   const int n = 1 << log2n, mask = n - 1;
   const int tiles_z = n / DTZ, tiles = (n / DTY) * tiles_z;
   const int tid = threadIdx.x;
   const bool src = tid < PL, dst = tid >= DSRC_T;
-  const int sly = tid / DEZ, slz = tid - sly * DEZ;            // source cell of this thread (if src)
+  const int sly = tid / DEZ, slz = tid - sly * DEZ;            // source column of this thread (if src)
   const int dt = tid - DSRC_T;
   const int ty = dt / DTZ, tz = dt - ty * DTZ;                 // destination cells (ty, tz), (ty + DTY / 2, tz) (if dst)
   // copies the first KP particles [b, min(e, b + KP)) into slot buffer `buf`
@@ -176,8 +177,6 @@ __global__ void __launch_bounds__(DTHREADS, 2) k_deposit_stream(const uint32_t* 
     const int x0 = xc * chunk, x1 = x0 + chunk;
     const uint32_t cy = (uint32_t)((y0 - 1 + sly) & mask), cz = (uint32_t)((z0 - 1 + slz) & mask);
     auto cell_of = [&](int x) -> uint32_t { return ((((uint32_t)(x & mask)) << log2n | cy) << log2n) | cz; };
-    // destination ring per cell h: partial sums of planes xr - 1 (P) and xr (Q)
-    float P[2] = {0.0f, 0.0f}, Q[2] = {0.0f, 0.0f};
     float wsum_s = 0.0f, wsum_c = 0.0f;
     // pipeline registers: cell starts of planes xs and xs + 1
     uint32_t b0 = 0, e0 = 0, b1 = 0, e1 = 0;
@@ -188,12 +187,13 @@ __global__ void __launch_bounds__(DTHREADS, 2) k_deposit_stream(const uint32_t* 
       stage((x0 - 1) & 1, b0, e0);
       cp_async_commit();
     }
-    for (int xs = x0 - 1; xs <= x1 + 1; ++xs) {
-      // the moments of source plane xs go to one buffer while the
-      // destinations add those of plane xs - 1 from the other: one barrier
-      // per step
-      float* MomW = Mom + (xs & 1) * 27 * PL;
-      const float* MomR = Mom + ((xs - 1) & 1) * 27 * PL;
+    // one plane step: source plane xs adds to the column sums of destination
+    // planes xs - 1 (A), xs (B) and xs + 1 (C, started here), emits A; the
+    // destinations add the column sums of plane xs - 2 emitted in the step
+    // before.  The caller rotates the roles of the three register arrays.
+    auto step = [&](int xs, float (&A)[9], float (&B)[9], float (&C)[9]) {
+      float* ColW = Col + (xs & 1) * 9 * PL;
+      const float* ColR = Col + ((xs - 1) & 1) * 9 * PL;
       uint32_t b2 = 0, e2 = 0;
       if (src && xs <= x1) {
         if (xs + 1 <= x1) stage((xs + 1) & 1, b1, e1);   // the next plane's particles, in flight
@@ -203,9 +203,8 @@ __global__ void __launch_bounds__(DTHREADS, 2) k_deposit_stream(const uint32_t* 
           b2 = __ldg(cellstart + c2); e2 = __ldg(cellstart + c2 + 1);
         }
         cp_async_wait1();                                  // this plane's particles have arrived
-        float m[27];
 #pragma unroll
-        for (int o = 0; o < 27; ++o) m[o] = 0.0f;
+        for (int o = 0; o < 9; ++o) C[o] = 0.0f;
         auto weigh = [&](uint32_t px, uint32_t py, uint32_t pz, float v) {
           float wx[3], wy[3], wz[3];
           tsc_weights(cell_offset(px, log2n), wx);
@@ -215,72 +214,80 @@ __global__ void __launch_bounds__(DTHREADS, 2) k_deposit_stream(const uint32_t* 
             wx[0] *= v; wx[1] *= v; wx[2] *= v;
           }
 #pragma unroll
-          for (int ox = 0; ox < 3; ++ox)
+          for (int oy = 0; oy < 3; ++oy) {
+            const float w0 = wx[0] * wy[oy], w1 = wx[1] * wy[oy], w2 = wx[2] * wy[oy];
 #pragma unroll
-            for (int oy = 0; oy < 3; ++oy) {
-              const float wxy = wx[ox] * wy[oy];
-#pragma unroll
-              for (int oz = 0; oz < 3; ++oz) m[(ox * 3 + oy) * 3 + oz] = fmaf(wxy, wz[oz], m[(ox * 3 + oy) * 3 + oz]);
+            for (int oz = 0; oz < 3; ++oz) {
+              A[oy * 3 + oz] = fmaf(w0, wz[oz], A[oy * 3 + oz]);
+              B[oy * 3 + oz] = fmaf(w1, wz[oz], B[oy * 3 + oz]);
+              C[oy * 3 + oz] = fmaf(w2, wz[oz], C[oy * 3 + oz]);
             }
+          }
         };
         const uint32_t* s0 = Slot + (xs & 1) * KP * NC * PL + tid;
         const uint32_t cnt = e0 - b0;
         if (crowd && cnt > kWalkRun) {   // its moments were summed already
+          const float* mo = crowd + kMomStride * (int64_t)b0;
 #pragma unroll
-          for (int o = 0; o < 27; ++o) m[o] = __ldg(crowd + kMomStride * (int64_t)b0 + o);
+          for (int o = 0; o < 9; ++o) {
+            A[o] += __ldg(mo + o);
+            B[o] += __ldg(mo + 9 + o);
+            C[o] += __ldg(mo + 18 + o);
+          }
         } else {
 #pragma unroll
-        for (int k = 0; k < KP; ++k)
-          if ((uint32_t)k < cnt)
-            weigh(s0[(k * NC) * PL], s0[(k * NC + 1) * PL], s0[(k * NC + 2) * PL],
-                  VALS ? __uint_as_float(s0[(k * NC + 3) * PL]) : 1.0f);
-        if (cnt > (uint32_t)KP) {   // the rest from global memory
-          uint32_t p = b0 + KP;
-          uint32_t px = __ldg(Xs + p), py = __ldg(Xs + np + p), pz = __ldg(Xs + 2 * np + p);
-          for (; p < e0; ++p) {
-            // the next particle of the cell is loaded while this one is weighed
-            uint32_t qx = 0, qy = 0, qz = 0;
-            if (p + 1 < e0) { qx = __ldg(Xs + p + 1); qy = __ldg(Xs + np + p + 1); qz = __ldg(Xs + 2 * np + p + 1); }
-            weigh(px, py, pz, VALS ? __ldg(vals + p) : 1.0f);
-            px = qx;
-            py = qy;
-            pz = qz;
+          for (int k = 0; k < KP; ++k)
+            if ((uint32_t)k < cnt)
+              weigh(s0[(k * NC) * PL], s0[(k * NC + 1) * PL], s0[(k * NC + 2) * PL],
+                    VALS ? __uint_as_float(s0[(k * NC + 3) * PL]) : 1.0f);
+          if (cnt > (uint32_t)KP) {   // the rest from global memory
+            uint32_t p = b0 + KP;
+            uint32_t px = __ldg(Xs + p), py = __ldg(Xs + np + p), pz = __ldg(Xs + 2 * np + p);
+            for (; p < e0; ++p) {
+              // the next particle of the cell is loaded while this one is weighed
+              uint32_t qx = 0, qy = 0, qz = 0;
+              if (p + 1 < e0) { qx = __ldg(Xs + p + 1); qy = __ldg(Xs + np + p + 1); qz = __ldg(Xs + 2 * np + p + 1); }
+              weigh(px, py, pz, VALS ? __ldg(vals + p) : 1.0f);
+              px = qx;
+              py = qy;
+              pz = qz;
+            }
           }
         }
-        }
+        // destination plane xs - 1 has all of this column's contributions
 #pragma unroll
-        for (int o = 0; o < 27; ++o) MomW[o * PL + tid] = m[o];
+        for (int o = 0; o < 9; ++o) ColW[o * PL + tid] = A[o];
       }
-      const int xr = xs - 1;   // the source plane whose moments the destinations add now
-      if (dst && xr >= x0 - 1) {
-        // destination plane xr + ox - 1 receives the moments with x offset
-        // ox - 1; each plane sums its three source planes in the order they
-        // come (xr + 1, xr, xr - 1 for ox = 2, 1, 0)
-        const int done = xr - 1;   // complete after this source plane
+      const int done = xs - 2;   // the destination plane whose column sums were emitted in the step before
+      if (dst && done >= x0 && done < x1) {
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-          const int cy = ty + h * (DTY / 2);
-          float a[3];
+          const int ry = ty + h * (DTY / 2);
+          float a = 0.0f;
 #pragma unroll
-          for (int ox = 0; ox < 3; ++ox) {
-            a[ox] = 0.0f;
+          for (int oy = 0; oy < 3; ++oy)
 #pragma unroll
-            for (int oy = 0; oy < 3; ++oy)
-#pragma unroll
-              for (int oz = 0; oz < 3; ++oz)
-                a[ox] += MomR[((ox * 3 + oy) * 3 + oz) * PL + (cy + 2 - oy) * DEZ + (tz + 2 - oz)];
-          }
-          const float r = (P[h] + a[0]) * scale;
-          P[h] = Q[h] + a[1];
-          Q[h] = 0.0f + a[2];
-          if (done >= x0 && done < x1) {
-            rho[((((int64_t)done << log2n) | (y0 + cy)) << log2n) | (z0 + tz)] = r;
-            kahan_add(wsum_s, wsum_c, r);
-          }
+            for (int oz = 0; oz < 3; ++oz) a += ColR[(oy * 3 + oz) * PL + (ry + 2 - oy) * DEZ + (tz + 2 - oz)];
+          const float r = a * scale;
+          rho[((((int64_t)done << log2n) | (y0 + ry)) << log2n) | (z0 + tz)] = r;
+          kahan_add(wsum_s, wsum_c, r);
         }
       }
       __syncthreads();
       b0 = b1; e0 = e1; b1 = b2; e1 = e2;
+    };
+    // column sums of destination planes xs - 1 and xs (the first source plane
+    // reaches planes x0 - 2 .. x0; the first two are outside the chunk)
+    float R0[9], R1[9], R2[9];
+#pragma unroll
+    for (int o = 0; o < 9; ++o) {
+      R0[o] = 0.0f;
+      R1[o] = 0.0f;
+    }
+    for (int xs = x0 - 1; xs <= x1 + 1; xs += 3) {
+      step(xs, R0, R1, R2);
+      if (xs + 1 <= x1 + 1) step(xs + 1, R1, R2, R0);
+      if (xs + 2 <= x1 + 1) step(xs + 2, R2, R0, R1);
     }
     const double ws = warp_sum_comp(wsum_s - wsum_c);
     if ((tid & 31) == 0) wsum[tid >> 5] = ws;
