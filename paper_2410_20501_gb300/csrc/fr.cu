@@ -34,8 +34,9 @@ __device__ __forceinline__ float load_mean(const Src& f) { return f.mean ? (floa
 __device__ __forceinline__ float src_at(const Src& f, int64_t i, float mean) {
   return f.s * (__ldg(f.p + i) - mean);
 }
-__device__ __forceinline__ int64_t idx3(int i, int j, int k, int log2n) {
-  return ((int64_t)i << (2 * log2n)) | ((int64_t)j << log2n) | k;
+// Offset of cell (i, j, k) inside one box (n <= 1024: below 2^30).
+__device__ __forceinline__ uint32_t idx3(int i, int j, int k, int log2n) {
+  return ((uint32_t)i << (2 * log2n)) | ((uint32_t)j << log2n) | (uint32_t)k;
 }
 
 // Root eps > -1 of g(e) = e^3 + 3e^2 + c1 e + c0 (g(-1) = q < 0, g convex on
@@ -213,8 +214,7 @@ __global__ void k_fr_restrict(const float* __restrict__ e, Src b, int log2n, flo
   const int lc = log2n - 1, mc = (1 << lc) - 1;
   const float mean = load_mean(b);
   const int64_t total = (int64_t)1 << (3 * lc);
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
-       t += (int64_t)gridDim.x * blockDim.x) {
+  for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
     const int K = (int)(t & mc), J = (int)((t >> lc) & mc), I = (int)(t >> (2 * lc));
     float core[2][2][4], xf[2][2][2], yf[2][2][2];
     load_children_block(e, I, J, K, log2n, core, xf, yf);
@@ -256,8 +256,7 @@ __global__ void k_fr_coarse_op(const float* __restrict__ eH, float* __restrict__
                                float kappa) {
   const int m = (1 << log2n) - 1;
   const int64_t total = (int64_t)1 << (3 * log2n);
-  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < total;
-       c += (int64_t)gridDim.x * blockDim.x) {
+  for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < total; c += gridDim.x * blockDim.x) {
     const int k = (int)(c & m), j = (int)((c >> log2n) & m), i = (int)(c >> (2 * log2n));
     float nb[6];
     load_nb(eH, i, j, k, log2n, nb);
@@ -273,8 +272,7 @@ __global__ void __launch_bounds__(256) k_fr_norm(const float* __restrict__ e, Sr
   const int m = (1 << log2n) - 1;
   const int64_t total = (int64_t)1 << (3 * log2n);
   float sd = 0.0f, cd = 0.0f, sb = 0.0f, cb = 0.0f;
-  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < total;
-       c += (int64_t)gridDim.x * blockDim.x) {
+  for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < total; c += gridDim.x * blockDim.x) {
     const int k = (int)(c & m), j = (int)((c >> log2n) & m), i = (int)(c >> (2 * log2n));
     float nb[6];
     load_nb(e, i, j, k, log2n, nb);

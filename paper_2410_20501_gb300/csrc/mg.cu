@@ -25,8 +25,9 @@ __device__ __forceinline__ float src_at(const Src& f, int64_t i, float mean) {
   return f.s * (__ldg(f.p + i) - mean);
 }
 
-__device__ __forceinline__ int64_t idx3(int i, int j, int k, int log2n) {
-  return ((int64_t)i << (2 * log2n)) | ((int64_t)j << log2n) | k;
+// Offset of cell (i, j, k) inside one box (n <= 1024: below 2^30).
+__device__ __forceinline__ uint32_t idx3(int i, int j, int k, int log2n) {
+  return ((uint32_t)i << (2 * log2n)) | ((uint32_t)j << log2n) | (uint32_t)k;
 }
 
 // sum_nb (u_nb - u) with TwoSum on every difference and partial sum: S + E.
@@ -83,8 +84,7 @@ __global__ void k_rb_sweep(float* __restrict__ u, Src f, int log2n, int colour, 
   upd = upd.box(blockIdx.z);
   const float mean = load_mean(f);
   const int64_t total = (int64_t)1 << (3 * log2n - 1);
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
-       t += (int64_t)gridDim.x * blockDim.x) {
+  for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
     const int kk = (int)(t & ((1 << half) - 1));
     const int64_t rest = t >> half;
     const int j = (int)(rest & m), i = (int)(rest >> log2n);
@@ -121,8 +121,7 @@ __global__ void k_resid_restrict(const float* __restrict__ u, Src f, int log2n, 
   fc += (int64_t)blockIdx.z << (3 * lc);
   const float mean = load_mean(f);
   const int64_t total = (int64_t)1 << (3 * lc);
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
-       t += (int64_t)gridDim.x * blockDim.x) {
+  for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
     const int K = (int)(t & mc), J = (int)((t >> lc) & mc), I = (int)(t >> (2 * lc));
     float core[2][2][4], xf[2][2][2], yf[2][2][2];
     load_children_block(u, I, J, K, log2n, core, xf, yf);
@@ -189,8 +188,7 @@ __global__ void __launch_bounds__(256) k_resid_norm(const float* __restrict__ u,
   const int m = (1 << log2n) - 1;
   const int64_t total = (int64_t)1 << (3 * log2n);
   float sd = 0.0f, cd = 0.0f, sf = 0.0f, cf = 0.0f;
-  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < total;
-       c += (int64_t)gridDim.x * blockDim.x) {
+  for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < total; c += gridDim.x * blockDim.x) {
     const int k = (int)(c & m), j = (int)((c >> log2n) & m), i = (int)(c >> (2 * log2n));
     float nb[6];
     load_nb(u, i, j, k, log2n, nb);
@@ -219,8 +217,7 @@ __global__ void k_prolong_correct(float* __restrict__ u, const float* __restrict
   uc += (int64_t)blockIdx.z * total;
   if (uc2) uc2 += (int64_t)blockIdx.z * total;
   const int hz = lc - 1;   // log2 of the pairs per coarse row
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < (total >> 1);
-       t += (int64_t)gridDim.x * blockDim.x) {
+  for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < (total >> 1); t += gridDim.x * blockDim.x) {
     const int K = 2 * (int)(t & ((1 << hz) - 1));
     const int64_t row = t >> hz;
     const int J = (int)(row & mc), I = (int)(row >> lc);

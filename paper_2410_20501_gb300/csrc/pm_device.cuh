@@ -125,8 +125,8 @@ __device__ __forceinline__ void nb_index(uint32_t c, uint32_t i, uint32_t j, uin
 __device__ __forceinline__ void load_children_block(const float* __restrict__ u, int I, int J, int K, int log2n,
                                                     float core[2][2][4], float xf[2][2][2], float yf[2][2][2]) {
   const int m = (1 << log2n) - 1;
-  auto at = [&](int x, int y, int z) -> int64_t {
-    return ((int64_t)(x & m) << (2 * log2n)) | ((int64_t)(y & m) << log2n) | (z & m);
+  auto at = [&](int x, int y, int z) -> uint32_t {   // offset inside one box (below 2^30)
+    return ((uint32_t)(x & m) << (2 * log2n)) | ((uint32_t)(y & m) << log2n) | (uint32_t)(z & m);
   };
   const int x0 = 2 * I, y0 = 2 * J, z0 = 2 * K;
 #pragma unroll
