@@ -1,12 +1,20 @@
 // TSC mass assignment (§3.4) as a deterministic gather over cell-sorted
 // particles, and fixed-order float64 grid reductions.
 //
-// One CTA owns a T^3 tile of destination cells.  Stage 1: for every source
-// cell of the tile plus a one-cell halo, one thread walks that cell's particles
-// in sorted order and accumulates the 27 "moments" m[o] = sum_p W_x W_y W_z
-// (the weight each neighbour o = -1..1 per axis receives) into shared memory.
-// Stage 2: every destination cell sums the 27 moments that point at it, in a
-// fixed order.  No atomics; the result is bitwise reproducible.
+// The "moments" of a source cell are the 27 sums m[o] = sum_p W_x W_y W_z of
+// its particles' TSC weight products, one per neighbour o = -1..1 per axis:
+// what the cell sends to each of its 27 destination cells.  Every kernel here
+// forms them in a fixed order and every destination cell adds the ones that
+// point at it in a fixed order: no atomics, the density is bitwise
+// reproducible.
+//
+// n >= 32: the streaming kernel k_deposit_stream walks the x planes of a
+// column of cells (cells of up to kWalkRun particles weighed there, larger
+// ones summed beforehand by k_group_moments, k_medium_moments and
+// k_crowded_moments into the moment buffer).  n < 32: k_deposit<T>, one CTA
+// per T^3 tile: one thread per source cell of the tile plus a one-cell halo
+// walks the cell's particles into moments in shared memory, then every
+// destination cell sums its 27.
 #include "pm_device.cuh"
 #include "pm_internal.cuh"
 
