@@ -84,3 +84,28 @@ def test_crowded_step_accelerations_match_oracle(pm):
     ref, _, _ = step.accelerations(mesh.positions_from_fixed_point(X), 0.5,
                                    step.PMParams(n=n, Om=0.3, OL=0.7, boxsize=float(n)))
     assert np.linalg.norm(acc.T - ref) / np.linalg.norm(ref) < 1e-5
+
+
+def test_gravitationally_clustered_deposit_matches_oracle(pm):
+    """A state clustered by the dynamics themselves: 90 Newtonian steps of the
+    100-step ln-a schedule from 2LPT at z = 30, 128^3 particles in a 128 Mpc/h
+    box (the 1 Mpc/h cells of the 512^3 run).  Every cell size class of the
+    sort and the deposit occurs (walked cells of up to four particles, groups
+    of eight and sixteen lanes, a warp, a block); the density of the final
+    positions against the FP64 oracle."""
+    import bench
+    n = 128
+    a = bench.schedule()
+    coeffs = bench.step_coefficients(0.3, 0.7, a)
+    X, V = inputs.lpt_ics(n, float(n), 0.3, 0.7, a[0], 5, order=2, device="cuda")
+    sim = pm.Simulation(X, V, n, 0.3, 0.7, float(n), mg=pm.default_mg(tol=1e-7, fixed_cycles=2))
+    for i in range(90):
+        sim.step(*coeffs[i])
+    Xh = sim.positions()
+    counts = np.bincount(mesh.cell_key(Xh, n).astype(np.int64), minlength=n ** 3)
+    for lo, hi in ((5, 13), (14, 32), (33, 256)):
+        assert ((counts >= lo) & (counts <= hi)).sum() > 0, (lo, hi)
+    rho = pm.deposit(pm.positions_to_device(Xh), n).cpu().numpy()
+    ref = mesh.deposit_tsc(mesh.positions_from_fixed_point(Xh), n)
+    assert np.abs(rho - ref).max() <= 4e-6 * np.abs(ref).max()
+    assert np.array_equal(rho, pm.deposit(pm.positions_to_device(Xh), n).cpu().numpy())
