@@ -86,13 +86,11 @@ def test_crowded_step_accelerations_match_oracle(pm):
     assert np.linalg.norm(acc.T - ref) / np.linalg.norm(ref) < 1e-5
 
 
-def test_gravitationally_clustered_deposit_matches_oracle(pm):
+@pytest.fixture(scope="module")
+def dyn_clustered(pm):
     """A state clustered by the dynamics themselves: 90 Newtonian steps of the
     100-step ln-a schedule from 2LPT at z = 30, 128^3 particles in a 128 Mpc/h
-    box (the 1 Mpc/h cells of the 512^3 run).  Every cell size class of the
-    sort and the deposit occurs (walked cells of up to four particles, groups
-    of eight and sixteen lanes, a warp, a block); the density of the final
-    positions against the FP64 oracle."""
+    box (the 1 Mpc/h cells of the 512^3 run).  Returns (n, positions)."""
     import bench
     n = 128
     a = bench.schedule()
@@ -101,7 +99,14 @@ def test_gravitationally_clustered_deposit_matches_oracle(pm):
     sim = pm.Simulation(X, V, n, 0.3, 0.7, float(n), mg=pm.default_mg(tol=1e-7, fixed_cycles=2))
     for i in range(90):
         sim.step(*coeffs[i])
-    Xh = sim.positions()
+    return n, sim.positions()
+
+
+def test_gravitationally_clustered_deposit_matches_oracle(pm, dyn_clustered):
+    """Every cell size class of the sort and the deposit occurs in the
+    clustered state (walked cells of up to four particles, groups of eight and
+    sixteen lanes, a warp); the density against the FP64 oracle."""
+    n, Xh = dyn_clustered
     counts = np.bincount(mesh.cell_key(Xh, n).astype(np.int64), minlength=n ** 3)
     for lo, hi in ((5, 13), (14, 32), (33, 256)):
         assert ((counts >= lo) & (counts <= hi)).sum() > 0, (lo, hi)
@@ -109,3 +114,18 @@ def test_gravitationally_clustered_deposit_matches_oracle(pm):
     ref = mesh.deposit_tsc(mesh.positions_from_fixed_point(Xh), n)
     assert np.abs(rho - ref).max() <= 4e-6 * np.abs(ref).max()
     assert np.array_equal(rho, pm.deposit(pm.positions_to_device(Xh), n).cpu().numpy())
+
+
+def test_gravitationally_clustered_sort_is_the_stable_order(pm, dyn_clustered):
+    """The cell sort of the clustered state, shuffled so that every cell's run
+    arrives in pieces: permutation and cell starts bit-exact against the
+    oracle's stable order."""
+    n, Xh = dyn_clustered
+    rng = np.random.Generator(np.random.PCG64(21))
+    Xs = np.ascontiguousarray(Xh[:, rng.permutation(Xh.shape[1])])
+    perm, cs = pm.sort(pm.positions_to_device(Xs), n)
+    ref = mesh.stable_cell_order(Xs, n)
+    assert np.array_equal(perm.cpu().numpy().view(np.uint32), ref)
+    keys = mesh.cell_key(Xs, n)[ref]
+    ref_cs = np.searchsorted(keys, np.arange(n ** 3 + 1), side="left").astype(np.uint32)
+    assert np.array_equal(cs.cpu().numpy().view(np.uint32), ref_cs)
