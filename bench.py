@@ -337,6 +337,16 @@ def oracle_errors(probes):
     return out
 
 
+def headline_config(world):
+    """The headline workload (both arms print it: the reference arm times a
+    bounded sample of it, stated in its cpu_baseline)."""
+    return {"workload": "hu-sawicki f(R) n=1 pm step, 512^3 particles, 512^3 grid, L=512 Mpc/h, 2LPT z=30",
+            "global_batch": world * N_GRID ** 3, "n_grid": N_GRID, "boxsize_mpc_h": BOX, "fR0": FR0,
+            "parallelism": f"replicas{world}", "l2": "inputs larger than L2 (every array >= 537 MB)",
+            "poisson": "2 warm-started V-cycles per step (first step: to relative residual 1e-7)",
+            "fr": "one FAS F-cycle per step"}
+
+
 def run_reference(args):
     world, rank, _ = dist_env()
     if world > 1:
@@ -348,7 +358,7 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / max(1, args.steps),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "impl": "reference",
-            "config": {"workload": "hu-sawicki f(R) pm step, bounded oracle sample", "n": ORACLE_N},
+            "config": headline_config(args.gpus),
             "cpu_baseline": {"value": value, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": "particle-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -716,11 +726,7 @@ def run_gpu(args):
         "metric": METRIC, "value": value, "unit": "particle-steps/s", "n_gpus": world, "steps": K,
         "warmup": W, "ms_per_step": seg["window"] / K, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "hu-sawicki f(R) n=1 pm step, 512^3 particles, 512^3 grid, L=512 Mpc/h, "
-                               "2LPT z=30", "global_batch": world * npart, "n_grid": n, "boxsize_mpc_h": BOX,
-                   "fR0": FR0, "parallelism": f"replicas{world}", "l2": "inputs larger than L2 (every array "
-                   ">= 537 MB)", "poisson": "2 warm-started V-cycles per step (first step: to relative residual 1e-7)",
-                   "fr": "one FAS F-cycle per step"},
+        "config": headline_config(world),
         "window": {"steps": f"{W}..{W + K - 1}", "z": [1.0 / a[W] - 1.0, 1.0 / a[W + K - 1] - 1.0],
                    "what": "the headline's steps of the 100-step schedule uniform in ln a from z = 30"},
         "late": {"steps": f"{LATE}..{N_STEPS_RUN - 1}", "z": [1.0 / a[LATE] - 1.0, 1.0 / a[N_STEPS_RUN - 1] - 1.0],
