@@ -173,13 +173,17 @@ struct SideStream {
 SideStream g_side[64];   // the scalaron solve of an f(R) step
 SideStream g_copy[64];   // the velocity copies of pm_step_host
 
-pm_status lib_stream(SideStream* table, SideStream** out) {
+// priority: create the stream with the device's highest stream priority
+// (its CTAs are scheduled first when both streams have work waiting).
+pm_status lib_stream(SideStream* table, SideStream** out, bool priority = false) {
   int dev = 0;
   PM_TRY(cuda_status(cudaGetDevice(&dev)));
   if (dev < 0 || dev >= 64) return PM_EINVAL;
   SideStream& ss = table[dev];
   if (!ss.s) {
-    PM_TRY(cuda_status(cudaStreamCreateWithFlags(&ss.s, cudaStreamNonBlocking)));
+    int lowest = 0, highest = 0;
+    PM_TRY(cuda_status(cudaDeviceGetStreamPriorityRange(&lowest, &highest)));
+    PM_TRY(cuda_status(cudaStreamCreateWithPriority(&ss.s, cudaStreamNonBlocking, priority ? highest : lowest)));
     PM_TRY(cuda_status(cudaEventCreateWithFlags(&ss.fork, cudaEventDisableTiming)));
     PM_TRY(cuda_status(cudaEventCreateWithFlags(&ss.join, cudaEventDisableTiming)));
   }
@@ -187,7 +191,10 @@ pm_status lib_stream(SideStream* table, SideStream** out) {
   return PM_OK;
 }
 
-pm_status side_stream(SideStream** out) { return lib_stream(g_side, out); }
+// The scalaron chain is the longer of the step's two solver chains: its
+// stream takes the highest priority, so its latency-bound small levels run
+// first and the Poisson sweeps fill the rest of the GPU.
+pm_status side_stream(SideStream** out) { return lib_stream(g_side, out, true); }
 
 // Offset (in doubles) of the side stream's share of the partials: past the
 // 2 x (152 x 8) block sums of a residual norm on the main stream, twice.
