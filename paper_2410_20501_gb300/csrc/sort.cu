@@ -25,7 +25,8 @@ namespace pmgb {
 namespace {
 
 constexpr int SCAN_T = 1024;
-constexpr int SCAN_CHUNK = 4 * SCAN_T;
+constexpr int SCAN_V = 16;                  // values per thread of the scan passes
+constexpr int SCAN_CHUNK = SCAN_V * SCAN_T;
 constexpr int KT = 256;             // threads of the key, scatter and order kernels
 constexpr int CI = 4;               // particles per thread of the counting kernel
 constexpr uint32_t SHORT_RUN = kLongRun;  // runs up to this length are ordered by one thread or warp
@@ -376,20 +377,32 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* w
   return r;
 }
 
+// A thread's SCAN_V consecutive values (four 16-byte loads in flight where
+// the array is aligned and the run is whole; plain loads at the tail).
+__device__ __forceinline__ void scan_load(const uint32_t* __restrict__ a, int64_t len, int64_t base,
+                                          uint32_t v[SCAN_V]) {
+  if (base + SCAN_V <= len && ((uintptr_t)a & 15) == 0) {
+#pragma unroll
+    for (int q = 0; q < SCAN_V / 4; ++q) {
+      const uint4 t = __ldg(reinterpret_cast<const uint4*>(a + base) + q);
+      v[4 * q] = t.x; v[4 * q + 1] = t.y; v[4 * q + 2] = t.z; v[4 * q + 3] = t.w;
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < SCAN_V; ++k) v[k] = base + k < len ? a[base + k] : 0u;
+  }
+}
+
 __global__ void __launch_bounds__(SCAN_T) k_scan_reduce(const uint32_t* __restrict__ a, int64_t len,
                                                         uint32_t* __restrict__ sums) {
   __shared__ uint32_t wt[32];
   __shared__ uint32_t tot;
-  const int64_t base = (int64_t)blockIdx.x * SCAN_CHUNK + (int64_t)threadIdx.x * 4;
-  uint32_t v = 0;
-  if (base + 4 <= len && ((uintptr_t)a & 15) == 0) {
-    const uint4 t = __ldg(reinterpret_cast<const uint4*>(a + base));
-    v = t.x + t.y + t.z + t.w;
-  } else {
-    for (int k = 0; k < 4; ++k)
-      if (base + k < len) v += a[base + k];
-  }
-  block_exclusive_scan(v, wt, &tot);
+  const int64_t base = (int64_t)blockIdx.x * SCAN_CHUNK + (int64_t)threadIdx.x * SCAN_V;
+  uint32_t v[SCAN_V], t = 0;
+  scan_load(a, len, base, v);
+#pragma unroll
+  for (int k = 0; k < SCAN_V; ++k) t += v[k];
+  block_exclusive_scan(t, wt, &tot);
   if (threadIdx.x == 0) sums[blockIdx.x] = tot;
 }
 
@@ -411,21 +424,25 @@ __global__ void __launch_bounds__(SCAN_T) k_scan_apply(uint32_t* __restrict__ a,
                                                        const uint32_t* __restrict__ sums) {
   __shared__ uint32_t wt[32];
   __shared__ uint32_t tot;
-  const int64_t base = (int64_t)blockIdx.x * SCAN_CHUNK + (int64_t)threadIdx.x * 4;
-  const bool vec = base + 4 <= len && ((uintptr_t)a & 15) == 0;
-  uint32_t v[4], s = 0;
-  if (vec) {
-    const uint4 t = *reinterpret_cast<const uint4*>(a + base);
-    v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+  const int64_t base = (int64_t)blockIdx.x * SCAN_CHUNK + (int64_t)threadIdx.x * SCAN_V;
+  uint32_t v[SCAN_V], t = 0;
+  scan_load(a, len, base, v);
+#pragma unroll
+  for (int k = 0; k < SCAN_V; ++k) t += v[k];
+  uint32_t e = block_exclusive_scan(t, wt, &tot) + sums[blockIdx.x];
+  if (base + SCAN_V <= len && ((uintptr_t)a & 15) == 0) {
+#pragma unroll
+    for (int q = 0; q < SCAN_V / 4; ++q) {
+      uint4 o;
+      o.x = e; e += v[4 * q];
+      o.y = e; e += v[4 * q + 1];
+      o.z = e; e += v[4 * q + 2];
+      o.w = e; e += v[4 * q + 3];
+      reinterpret_cast<uint4*>(a + base)[q] = o;
+    }
   } else {
-    for (int k = 0; k < 4; ++k) v[k] = base + k < len ? a[base + k] : 0;
-  }
-  for (int k = 0; k < 4; ++k) s += v[k];
-  uint32_t e = block_exclusive_scan(s, wt, &tot) + sums[blockIdx.x];
-  if (vec) {
-    *reinterpret_cast<uint4*>(a + base) = make_uint4(e, e + v[0], e + v[0] + v[1], e + v[0] + v[1] + v[2]);
-  } else {
-    for (int k = 0; k < 4; ++k) {
+#pragma unroll
+    for (int k = 0; k < SCAN_V; ++k) {
       if (base + k < len) a[base + k] = e;
       e += v[k];
     }
