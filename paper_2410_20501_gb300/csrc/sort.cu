@@ -449,22 +449,48 @@ __global__ void __launch_bounds__(SCAN_T) k_scan_apply(uint32_t* __restrict__ a,
   }
 }
 
-__global__ void k_permute(const uint32_t* __restrict__ perm, int64_t np,
-                          const uint32_t* __restrict__ X, const float* __restrict__ V,
-                          const uint32_t* __restrict__ id, uint32_t* __restrict__ Xs,
-                          float* __restrict__ Vs, uint32_t* __restrict__ ids) {
-  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < np;
-       j += (int64_t)gridDim.x * blockDim.x) {
-    uint32_t p = __ldg(perm + j);
-    if (X) {
+// Xs[d][j] = X[d][perm[j]] (and V, ids likewise): four particles per thread,
+// PT apart (coalesced), their permutation entries and then their gathers all
+// in flight together.
+constexpr int PT = 256, PK = 4;
+__global__ void __launch_bounds__(PT) k_permute(const uint32_t* __restrict__ perm, int64_t np,
+                                                const uint32_t* __restrict__ X, const float* __restrict__ V,
+                                                const uint32_t* __restrict__ id, uint32_t* __restrict__ Xs,
+                                                float* __restrict__ Vs, uint32_t* __restrict__ ids) {
+  const int64_t j0 = (int64_t)blockIdx.x * (PT * PK) + threadIdx.x;
+  uint32_t p[PK];
 #pragma unroll
-      for (int d = 0; d < 3; ++d) Xs[d * np + j] = __ldg(X + d * np + p);
-    }
-    if (V) {
+  for (int k = 0; k < PK; ++k) p[k] = j0 + k * PT < np ? __ldg(perm + j0 + k * PT) : 0u;
+  if (X) {
+    uint32_t x[PK][3];
 #pragma unroll
-      for (int d = 0; d < 3; ++d) Vs[d * np + j] = __ldg(V + d * np + p);
-    }
-    if (id) ids[j] = __ldg(id + p);
+    for (int k = 0; k < PK; ++k)
+#pragma unroll
+      for (int d = 0; d < 3; ++d) x[k][d] = j0 + k * PT < np ? __ldg(X + d * np + p[k]) : 0u;
+#pragma unroll
+    for (int k = 0; k < PK; ++k)
+      if (j0 + k * PT < np) {
+#pragma unroll
+        for (int d = 0; d < 3; ++d) Xs[d * np + j0 + k * PT] = x[k][d];
+      }
+  }
+  if (V) {
+    float v[PK][3];
+#pragma unroll
+    for (int k = 0; k < PK; ++k)
+#pragma unroll
+      for (int d = 0; d < 3; ++d) v[k][d] = j0 + k * PT < np ? __ldg(V + d * np + p[k]) : 0.0f;
+#pragma unroll
+    for (int k = 0; k < PK; ++k)
+      if (j0 + k * PT < np) {
+#pragma unroll
+        for (int d = 0; d < 3; ++d) Vs[d * np + j0 + k * PT] = v[k][d];
+      }
+  }
+  if (id) {
+#pragma unroll
+    for (int k = 0; k < PK; ++k)
+      if (j0 + k * PT < np) ids[j0 + k * PT] = __ldg(id + p[k]);
   }
 }
 
@@ -519,7 +545,8 @@ pm_status permute_particles(const uint32_t* perm, int64_t np, const uint32_t* X,
                             const uint32_t* id, uint32_t* Xs, float* Vs, uint32_t* ids,
                             cudaStream_t s) {
   if (np == 0) return PM_OK;
-  PM_LAUNCH(K_PERMUTE, (4.0 + (X ? 24.0 : 0.0) + (V ? 24.0 : 0.0) + (id ? 8.0 : 0.0)) * np, k_permute, grid_for(np, 256), 256, 0, s, perm, np, X, V, id, Xs, Vs, ids);
+  PM_LAUNCH(K_PERMUTE, (4.0 + (X ? 24.0 : 0.0) + (V ? 24.0 : 0.0) + (id ? 8.0 : 0.0)) * np, k_permute,
+            grid_for(np, PT * PK), PT, 0, s, perm, np, X, V, id, Xs, Vs, ids);
   return launch_status();
 }
 
