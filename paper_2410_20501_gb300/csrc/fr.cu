@@ -250,17 +250,43 @@ __global__ void k_fr_restrict(const float* __restrict__ e, Src b, int log2n, flo
   }
 }
 
-// bH += N_H(eH).
+// bH += N_H(eH).  A thread takes four consecutive z cells of a row (n >= 4):
+// the rows at x +- 1, y +- 1 and its own in 16-byte loads, plus the two z
+// neighbours beyond the run; each cell sees its neighbours in the order
+// x+, x-, y+, y-, z+, z- as everywhere else.
 template <int NH>
 __global__ void k_fr_coarse_op(const float* __restrict__ eH, float* __restrict__ bH, int log2n, float alpha,
                                float kappa) {
-  const int m = (1 << log2n) - 1;
-  const int64_t total = (int64_t)1 << (3 * log2n);
-  for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < total; c += gridDim.x * blockDim.x) {
-    const int k = (int)(c & m), j = (int)((c >> log2n) & m), i = (int)(c >> (2 * log2n));
-    float nb[6];
-    load_nb(eH, i, j, k, log2n, nb);
-    bH[c] += fr_op<NH>(eH[c], nb, alpha, kappa);
+  const uint32_t m = (1u << log2n) - 1;
+  const uint32_t quads = 1u << (3 * log2n - 2);
+  for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < quads; t += gridDim.x * blockDim.x) {
+    const uint32_t c0 = t << 2;
+    const uint32_t k0 = c0 & m, j = (c0 >> log2n) & m, i = c0 >> (2 * log2n);
+    auto rowp = [&](uint32_t ii, uint32_t jj) -> const float* {
+      return eH + (((ii & m) << (2 * log2n)) | ((jj & m) << log2n));
+    };
+    const float* rc = rowp(i, j);
+    const float4 C = __ldg(reinterpret_cast<const float4*>(rc + k0));
+    const float4 XP = __ldg(reinterpret_cast<const float4*>(rowp(i + 1, j) + k0));
+    const float4 XM = __ldg(reinterpret_cast<const float4*>(rowp(i - 1, j) + k0));
+    const float4 YP = __ldg(reinterpret_cast<const float4*>(rowp(i, j + 1) + k0));
+    const float4 YM = __ldg(reinterpret_cast<const float4*>(rowp(i, j - 1) + k0));
+    const float zl = __ldg(rc + ((k0 - 1) & m)), zr = __ldg(rc + ((k0 + 4) & m));
+    float4* bp = reinterpret_cast<float4*>(bH + c0);
+    float4 B = *bp;
+    const float e[4] = {C.x, C.y, C.z, C.w}, xp[4] = {XP.x, XP.y, XP.z, XP.w}, xm[4] = {XM.x, XM.y, XM.z, XM.w},
+                yp[4] = {YP.x, YP.y, YP.z, YP.w}, ym[4] = {YM.x, YM.y, YM.z, YM.w};
+    float r[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float nb[6] = {xp[q], xm[q], yp[q], ym[q], q < 3 ? e[q + 1] : zr, q > 0 ? e[q - 1] : zl};
+      r[q] = fr_op<NH>(e[q], nb, alpha, kappa);
+    }
+    B.x += r[0];
+    B.y += r[1];
+    B.z += r[2];
+    B.w += r[3];
+    *bp = B;
   }
 }
 
@@ -489,7 +515,7 @@ pm_status fr_to_coarse(FR& f, int l) {
   const int64_t nc = (int64_t)cH.n * cH.n * cH.n;
   FR_NH(f, PM_LAUNCH(K_FR_RESTRICT, 76.0 * nc, k_fr_restrict<NH>, grid_for(nc, 256), 256, 0, f.s, f.e[l], f.b[l],
                      c.log2n, c.alpha, c.kappa, f.e[l + 1], f.r[l + 1], const_cast<float*>(f.b[l + 1].p)));
-  FR_NH(f, PM_LAUNCH(K_FR_COARSEOP, 12.0 * nc, k_fr_coarse_op<NH>, grid_for(nc, 256), 256, 0, f.s, f.e[l + 1],
+  FR_NH(f, PM_LAUNCH(K_FR_COARSEOP, 12.0 * nc, k_fr_coarse_op<NH>, grid_for(nc / 4, 256), 256, 0, f.s, f.e[l + 1],
                      const_cast<float*>(f.b[l + 1].p), cH.log2n, cH.alpha, cH.kappa));
   return PM_OK;
 }
