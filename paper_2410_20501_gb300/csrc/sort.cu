@@ -100,10 +100,10 @@ __global__ void __launch_bounds__(KT) k_cell_scatter(const uint2* __restrict__ k
 
 // Stable order inside each cell: the ranks of cell c, cellstart[c] ..
 // cellstart[c+1]-1, in ascending particle index.  A thread takes OC
-// consecutive cells (16-byte loads of their starts).  Runs of at most kMedRun
-// are insertion-sorted here (and listed in smalls[1 ..] if longer than
-// kWalkRun, for the deposit); runs of at most SHORT_RUN are listed in
-// meds[1 ..] for k_cell_order_med, longer ones in runs[1 ..] for
+// consecutive cells (16-byte loads of their starts).  Runs of at most
+// kWalkRun are insertion-sorted here; runs of at most kMedRun are listed in
+// smalls[1 ..] (for k_cell_order_med<16> and the deposit), runs of at most
+// SHORT_RUN in meds[1 ..] for k_cell_order_med<32>, longer ones in runs[1 ..] for
 // k_cell_order_warp and, if longer than kWarpRun, in bigs[1 ..] for
 // k_cell_order_long as well (list[0] counts the entries, zeroed).  A block
 // reserves the room for its entries of each list with one atomic (the lists'
@@ -168,7 +168,7 @@ __global__ void __launch_bounds__(KT) k_cell_order(const uint32_t* __restrict__ 
 #pragma unroll
   for (int k = 0; k < OC; ++k) {
     const uint32_t a = st[k], b = st[k + 1];
-    if (b - a < 2 || b - a > kMedRun) continue;
+    if (b - a < 2 || b - a > kWalkRun) continue;   // larger runs: k_cell_order_med
     for (uint32_t p = a + 1; p < b; ++p) {
       const uint32_t v = perm[p];
       uint32_t q = p;
@@ -196,23 +196,34 @@ __global__ void __launch_bounds__(KT) k_cell_order(const uint32_t* __restrict__ 
   }
 }
 
-// The medium runs listed by k_cell_order, one warp each: lane i holds the
-// run's i-th particle index and moves it to its rank among the run's
-// (distinct) indices, counted over the warp by shuffles.
+// The runs of a list whose cells hold at most G particles, G lanes per run
+// (32 / G runs per warp): lane i of a group holds the run's i-th particle
+// index and moves it to its rank among the run's (distinct) indices, counted
+// over the group by shuffles.  G = 16 for the small runs (kWalkRun + 1 ..
+// kMedRun particles), G = 32 for the medium ones (kMedRun + 1 .. SHORT_RUN).
+template <int G>
 __global__ void __launch_bounds__(KT) k_cell_order_med(const uint32_t* __restrict__ cellstart,
-                                                       const uint32_t* __restrict__ meds,
+                                                       const uint32_t* __restrict__ list,
                                                        uint32_t* __restrict__ perm) {
-  const uint32_t nmeds = meds[0];
-  const uint32_t lane = threadIdx.x & 31;
-  const uint32_t warps = gridDim.x * (KT / 32);
-  for (uint32_t q = blockIdx.x * (KT / 32) + (threadIdx.x >> 5); q < nmeds; q += warps) {
-    const uint32_t c = meds[1 + q];
-    const uint32_t a = cellstart[c], m = cellstart[c + 1] - a;
-    const uint32_t v = lane < m ? perm[a + lane] : 0xffffffffu;
+  constexpr int PERW = 32 / G;
+  const uint32_t nlist = list[0];
+  const uint32_t lane = threadIdx.x & 31, g = lane & (G - 1);
+  const uint32_t groups = gridDim.x * (KT / 32) * PERW;
+  // the groups of a warp take consecutive list entries; a warp with no entry
+  // left stops as a whole (the shuffles need every lane)
+  for (uint32_t q0 = (blockIdx.x * (KT / 32) + (threadIdx.x >> 5)) * PERW; q0 < nlist; q0 += groups) {
+    const uint32_t q = q0 + lane / G;
+    uint32_t a = 0, m = 0;
+    if (q < nlist) {
+      const uint32_t c = list[1 + q];
+      a = cellstart[c];
+      m = cellstart[c + 1] - a;
+    }
+    const uint32_t v = g < m ? perm[a + g] : 0xffffffffu;
     uint32_t rank = 0;
-    for (uint32_t j = 0; j < m; ++j) rank += __shfl_sync(0xffffffffu, v, j) < v;
+    for (uint32_t k = 0; k < (uint32_t)G; ++k) rank += __shfl_sync(0xffffffffu, v, k, G) < v;
     __syncwarp();
-    if (lane < m) perm[a + rank] = v;
+    if (g < m) perm[a + rank] = v;
   }
 }
 
@@ -534,7 +545,8 @@ pm_status sort_cells(const uint32_t* X, int64_t np, int n, Workspace& w, cudaStr
   PM_LAUNCH(K_SCATTER, 16.0 * np, k_cell_scatter, gc, KT, 0, s, w.keyrank, np, cellstart, w.perm);
   PM_LAUNCH(K_ORDER, 4.0 * ncells + 8.0 * np, k_cell_order, grid_for(ncells / OC, KT), KT, 0, s, cellstart, ncells,
             w.perm, w.smalls, w.meds, w.runs, w.bigs);
-  PM_LAUNCH(K_ORDER, 0.0, k_cell_order_med, 8 * 152, KT, 0, s, cellstart, w.meds, w.perm);
+  PM_LAUNCH(K_ORDER, 0.0, k_cell_order_med<16>, 8 * 152, KT, 0, s, cellstart, w.smalls, w.perm);
+  PM_LAUNCH(K_ORDER, 0.0, k_cell_order_med<32>, 8 * 152, KT, 0, s, cellstart, w.meds, w.perm);
   PM_LAUNCH(K_ORDER, 0.0, k_cell_order_warp, 8 * 152, WT, 0, s, cellstart, w.runs, w.perm);
   PM_LAUNCH(K_ORDER, 0.0, k_cell_order_long, LONG_BLOCKS, LT, 0, s, cellstart, w.bigs, w.perm,
             reinterpret_cast<uint32_t*>(w.keyrank));
