@@ -451,8 +451,7 @@ pm_status pm_batch_workspace_size(int n, int B, int64_t np_box, size_t* bytes);
 /* The stages of the step, one launch per kernel for B boxes (the `batch`
  * argument of the boundary): box b's particles at b np_box .. (b+1) np_box - 1
  * of every plane, its grids at b n^3 (scalar) and 3 b n^3 (vector); every box
- * gives bitwise the result of the single-box call on it.  32 <= n for the
- * deposit and the multigrid; the f(R) solver is single-box only.
+ * gives bitwise the result of the single-box call on it.  32 <= n.
  *   pm_deposit_batch: rho [B][n^3] of X [3][B np_box]; workspace
  *     pm_batch_workspace_size(n, B, np_box).
  *   mg_solve_batch: exactly prm->fixed_cycles V-cycles per box, each box's
@@ -465,6 +464,23 @@ pm_status pm_deposit_batch(const uint32_t* X, int64_t np_box, int n, int B, floa
 pm_status mg_solve_batch(const float* f, float* phi, int n, int B, const mg_params* prm, void* ws, size_t ws_bytes,
                          void* stream);
 pm_status pm_gradient_batch(const float* phi, float* g, int n, int B, int order, void* stream);
+
+/* The f(R) scalaron of B boxes (§3.6.2, §3.10, the `batch` argument of the
+ * boundary): fr_solve's FAS cycles run on every box at once, one launch per
+ * kernel and level (box = third grid dimension; the coarsest level is one CTA
+ * per box).  The boxes share *prm: one scale factor, cosmology, f_R0 and box
+ * size (ensembles over seeds).  Exactly prm->cycles cycles per box (tol and
+ * max_cycles are not used: no box waits on a residual, nothing synchronises
+ * with the host); smoother 0 is taken as 2.  Box b gives bitwise fr_solve on
+ * rho + b n^3 with the same parameters, smoother 2 (or 1) and tol <= 0.
+ *   rho  [B][n^3] float32 densities (read); each box's float64 mean is removed
+ *   eps  [B][n^3] float32 in: guesses, out: solutions (16-byte aligned)
+ *   ws   pm_fr_batch_workspace_size(n, B) bytes, 256-byte aligned
+ * Errors: PM_EINVAL (n not a power of two in 32..1024, B < 1, cycles < 1,
+ * invalid parameters, misaligned arrays), PM_ENOMEM (ws too small). */
+pm_status pm_fr_batch_workspace_size(int n, int B, size_t* bytes);
+pm_status fr_solve_batch(const float* rho, float* eps, int n, int B, const fr_params* prm, void* ws,
+                         size_t ws_bytes, void* stream);
 pm_status pm_interp_batch(const float* g, const uint32_t* X, int64_t np_box, int n, int B, float* acc, void* stream);
 
 /* One fused-kick leapfrog step of every box (pm_step's pipeline, batched):

@@ -824,6 +824,31 @@ pm_status mg_solve_batch(const float* f, float* phi, int n, int B, const mg_para
   return mg_solve_batch_src(Src{f, 1.0f, w.box_mean, nullptr}, phi, n, B, mp, nullptr, w, s);
 }
 
+pm_status pm_fr_batch_workspace_size(int n, int B, size_t* bytes) {
+  if (!valid_batch(n, B, 0) || !bytes) return PM_EINVAL;
+  *bytes = layout_workspace(nullptr, nullptr, n, 0, PM_WS_FR, B);
+  return PM_OK;
+}
+
+pm_status fr_solve_batch(const float* rho, float* eps, int n, int B, const fr_params* prm, void* ws,
+                         size_t ws_bytes, void* stream) {
+  if (!valid_batch(n, B, 0) || !rho || !eps || !valid_fr(prm) || prm->cycles < 1 || !all_a16(rho, eps))
+    return PM_EINVAL;
+  if (!ws || !aligned(ws)) return PM_EINVAL;
+  if (ws_bytes < layout_workspace(nullptr, nullptr, n, 0, PM_WS_FR, B)) return PM_ENOMEM;
+  Workspace w;
+  layout_workspace(&w, ws, n, 0, PM_WS_FR, B);
+  cudaStream_t s = as_stream(stream);
+  const int64_t N = (int64_t)n * n * n;
+  for (int b = 0; b < B; ++b) PM_TRY(grid_mean(rho + b * N, N, w.partials, w.box_mean + b, s));
+  double fbar, kappa, c2;
+  fr_background(*prm, &fbar, &kappa, &c2);
+  const float sb = (float)(-prm->Om * prm->a / c2);
+  fr_params fp = *prm;
+  if (fp.smoother == 0) fp.smoother = 2;   // the two-sweep streaming kernel is single-box
+  return fr_solve_src(Src{rho, sb, w.box_mean, nullptr}, eps, n, fp, nullptr, w, s, B);
+}
+
 pm_status pm_gradient_batch(const float* phi, float* g, int n, int B, int order, void* stream) {
   if (!valid_n(n) || B < 1 || !phi || !g || (order != 3 && order != 5 && order != 7) || !all_a16(phi, g))
     return PM_EINVAL;

@@ -182,6 +182,11 @@ __global__ void __launch_bounds__(256) k_fr_sweep(float* __restrict__ e, Src b, 
                                                   float kappa, float q) {
   const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (1u << (3 * log2n - 1))) return;
+  {   // the box of a batched launch
+    const int64_t N = (int64_t)1 << (3 * log2n);
+    e += (int64_t)blockIdx.z * N;
+    b = box_src(b, N);
+  }
   const uint32_t m = (1u << log2n) - 1;
   const uint32_t kk = t & ((1u << (log2n - 1)) - 1), row = t >> (log2n - 1);
   const uint32_t j = row & m, i = row >> log2n;
@@ -207,13 +212,22 @@ __device__ __forceinline__ float fr_flux(float enb, float ec) {
 
 // eH = rH = R eps, bH = R(b - N_h eps).  Summed over the 2x2x2 block the
 // fluxes through the 12 inner faces cancel pairwise, so only the 24 outer
-// faces enter the restricted operator.
-template <int NH>
+// faces enter the restricted operator.  BOXES: a batched launch (box =
+// blockIdx.z); the single-box form keeps its own register allocation.
+template <int NH, bool BOXES>
 __global__ void k_fr_restrict(const float* __restrict__ e, Src b, int log2n, float alpha, float kappa,
                               float* __restrict__ eH, float* __restrict__ rH, float* __restrict__ bH) {
   const int lc = log2n - 1, mc = (1 << lc) - 1;
-  const float mean = load_mean(b);
   const int64_t total = (int64_t)1 << (3 * lc);
+  if (BOXES) {   // the box of a batched launch
+    e += (int64_t)blockIdx.z << (3 * log2n);
+    b = box_src(b, (int64_t)1 << (3 * log2n));
+    const int64_t offc = (int64_t)blockIdx.z * total;
+    eH += offc;
+    rH += offc;
+    bH += offc;
+  }
+  const float mean = load_mean(b);
   for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
     const int K = (int)(t & mc), J = (int)((t >> lc) & mc), I = (int)(t >> (2 * lc));
     float core[2][2][4], xf[2][2][2], yf[2][2][2];
@@ -259,6 +273,11 @@ __global__ void k_fr_coarse_op(const float* __restrict__ eH, float* __restrict__
                                float kappa) {
   const uint32_t m = (1u << log2n) - 1;
   const uint32_t quads = 1u << (3 * log2n - 2);
+  {   // the box of a batched launch
+    const int64_t off = (int64_t)blockIdx.z << (3 * log2n);
+    eH += off;
+    bH += off;
+  }
   for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < quads; t += gridDim.x * blockDim.x) {
     const uint32_t c0 = t << 2;
     const uint32_t k0 = c0 & m, j = (c0 >> log2n) & m, i = c0 >> (2 * log2n);
@@ -321,6 +340,8 @@ __global__ void __launch_bounds__(1024) k_fr_coarse(float* __restrict__ e, Src b
   __shared__ float se[4096], sbv[4096];
   __shared__ float2 scratch[33];
   const int n = 1 << log2n, m = n - 1, N = n * n * n;
+  e += (int64_t)blockIdx.z * N;   // one CTA per box of a batched launch
+  b = box_src(b, N);
   const float mean = load_mean(b);
   for (int c = threadIdx.x; c < N; c += blockDim.x) {
     se[c] = e[c];
@@ -401,6 +422,8 @@ struct FR {
   Src b[12];
   double fbar, kappa;
   int nh;           // Hu-Sawicki exponent (1 or 2)
+  int B = 1;        // boxes of a batched solve (blockIdx.z of every launch)
+  dim3 grid(unsigned gx) const { return dim3(gx, 1, (unsigned)B); }
 };
 
 // Runs the statement with the compile-time exponent NH of f.
@@ -450,8 +473,8 @@ template <int NH>
 pm_status fr_smooth_nh(FR& f, int l, int count) {
   using FRUpdate = ::pmgb::FRUpdate<NH>;
   const LevelConst c = level_const(f, l);
-  const double N = (double)c.n * c.n * c.n;
-  if (f.p->smoother == 0 && stream_ok(c.n) && f.alt[l]) {
+  const double N = (double)c.n * c.n * c.n * f.B;
+  if (f.p->smoother == 0 && stream_ok(c.n) && f.alt[l] && f.B == 1) {
     int chunk, nitems;
     stream_plan(c.n, &chunk, &nitems);
     const unsigned grid = (unsigned)(nitems < 152 * 2 ? nitems : 152 * 2);   // 2 CTAs/SM (shared memory)
@@ -471,9 +494,11 @@ pm_status fr_smooth_nh(FR& f, int l, int count) {
     }
     return PM_OK;
   }
+  // a box of a batch takes the kernels it would take alone (fused_ok of one
+  // box), so every box evolves bitwise as in a batch of one
   if (f.p->smoother == 2 && fused_ok(c.n) && f.alt[l] && fused_aligned(f.e[l], f.alt[l], f.b[l].p)) {
     const int chunk = fused_chunk(c.n);
-    const unsigned grid = (unsigned)((c.n / kFusedT) * (c.n / kFusedT) * (c.n / chunk));
+    const dim3 grid = f.grid((unsigned)((c.n / kFusedT) * (c.n / kFusedT) * (c.n / chunk)));
     const FRUpdate upd{c.beta, c.kappa, c.q};
     for (int it = 0; it < count; ++it) {
       PM_LAUNCH(l == 0 ? K_FR_SMOOTH0 : K_FR_SMOOTH, 12.0 * N, (k_rb_fused4<FRUpdate, kFrRunsMinBlocks>), grid,
@@ -484,7 +509,7 @@ pm_status fr_smooth_nh(FR& f, int l, int count) {
     }
     return PM_OK;
   }
-  const unsigned grid = grid_for(((int64_t)c.n * c.n * c.n) / 2, 256);
+  const dim3 grid = f.grid(grid_for(((int64_t)c.n * c.n * c.n) / 2, 256));
   for (int it = 0; it < count; ++it)
     for (int colour = 0; colour < 2; ++colour)
       PM_LAUNCH(l == 0 ? K_FR_SMOOTH0 : K_FR_SMOOTH, 6.0 * N, k_fr_sweep<NH>, grid, 256, 0, f.s, f.e[l], f.b[l],
@@ -503,7 +528,8 @@ bool is_coarsest(const FR& f, int l) {
 
 pm_status fr_coarse(FR& f, int l) {
   const LevelConst c = level_const(f, l);
-  FR_NH(f, PM_LAUNCH(K_FR_COARSE, 12.0 * c.n * c.n * (double)c.n, k_fr_coarse<NH>, 1, 1024, 0, f.s, f.e[l], f.b[l],
+  FR_NH(f, PM_LAUNCH(K_FR_COARSE, 12.0 * c.n * c.n * (double)c.n * f.B, k_fr_coarse<NH>, f.grid(1), 1024, 0, f.s,
+                     f.e[l], f.b[l],
                      c.log2n, c.alpha, c.beta, c.kappa, c.q, f.p->coarse_max_sweeps, f.p->coarse_drop));
   return PM_OK;
 }
@@ -513,10 +539,15 @@ pm_status fr_to_coarse(FR& f, int l) {
   PM_TRY(fr_smooth(f, l, f.p->npre));
   const LevelConst c = level_const(f, l), cH = level_const(f, l + 1);
   const int64_t nc = (int64_t)cH.n * cH.n * cH.n;
-  FR_NH(f, PM_LAUNCH(K_FR_RESTRICT, 76.0 * nc, k_fr_restrict<NH>, grid_for(nc, 256), 256, 0, f.s, f.e[l], f.b[l],
-                     c.log2n, c.alpha, c.kappa, f.e[l + 1], f.r[l + 1], const_cast<float*>(f.b[l + 1].p)));
-  FR_NH(f, PM_LAUNCH(K_FR_COARSEOP, 12.0 * nc, k_fr_coarse_op<NH>, grid_for(nc / 4, 256), 256, 0, f.s, f.e[l + 1],
-                     const_cast<float*>(f.b[l + 1].p), cH.log2n, cH.alpha, cH.kappa));
+  if (f.B == 1)
+    FR_NH(f, PM_LAUNCH(K_FR_RESTRICT, 76.0 * nc, (k_fr_restrict<NH, false>), grid_for(nc, 256), 256, 0, f.s, f.e[l],
+                       f.b[l], c.log2n, c.alpha, c.kappa, f.e[l + 1], f.r[l + 1], const_cast<float*>(f.b[l + 1].p)));
+  else
+    FR_NH(f, PM_LAUNCH(K_FR_RESTRICT, 76.0 * nc * f.B, (k_fr_restrict<NH, true>), f.grid(grid_for(nc, 256)), 256, 0,
+                       f.s, f.e[l], f.b[l], c.log2n, c.alpha, c.kappa, f.e[l + 1], f.r[l + 1],
+                       const_cast<float*>(f.b[l + 1].p)));
+  FR_NH(f, PM_LAUNCH(K_FR_COARSEOP, 12.0 * nc * f.B, k_fr_coarse_op<NH>, f.grid(grid_for(nc / 4, 256)), 256, 0, f.s,
+                     f.e[l + 1], const_cast<float*>(f.b[l + 1].p), cH.log2n, cH.alpha, cH.kappa));
   return PM_OK;
 }
 
@@ -524,7 +555,7 @@ pm_status fr_v(FR& f, int l) {
   if (is_coarsest(f, l)) return fr_coarse(f, l);
   PM_TRY(fr_to_coarse(f, l));
   PM_TRY(fr_v(f, l + 1));
-  PM_TRY(prolong_correct_launch(f.e[l], f.e[l + 1], f.r[l + 1], f.n0 >> l, K_FR_PROLONG, f.s));
+  PM_TRY(prolong_correct_launch(f.e[l], f.e[l + 1], f.r[l + 1], f.n0 >> l, K_FR_PROLONG, f.s, f.B));
   return fr_smooth(f, l, f.p->npost);
 }
 
@@ -532,7 +563,7 @@ pm_status fr_f(FR& f, int l) {
   if (is_coarsest(f, l)) return fr_coarse(f, l);
   PM_TRY(fr_to_coarse(f, l));
   PM_TRY(fr_f(f, l + 1));
-  PM_TRY(prolong_correct_launch(f.e[l], f.e[l + 1], f.r[l + 1], f.n0 >> l, K_FR_PROLONG, f.s));
+  PM_TRY(prolong_correct_launch(f.e[l], f.e[l + 1], f.r[l + 1], f.n0 >> l, K_FR_PROLONG, f.s, f.B));
   return fr_v(f, l);
 }
 
@@ -550,9 +581,10 @@ void fr_background(const fr_params& p, double* fbar, double* kappa, double* c2) 
 }
 
 pm_status fr_solve_src(Src b, float* eps, int n, const fr_params& prm, mg_stats* st, Workspace& w,
-                       cudaStream_t s) {
+                       cudaStream_t s, int B) {
   FR f;
   f.n0 = n;
+  f.B = B;
   f.p = &prm;
   f.s = s;
   f.e[0] = eps;
@@ -571,7 +603,7 @@ pm_status fr_solve_src(Src b, float* eps, int n, const fr_params& prm, mg_stats*
   double c2;
   fr_background(prm, &f.fbar, &f.kappa, &c2);
   mg_stats local{PM_OK, 0, -1.0, -1.0, -1.0};
-  const int64_t N0 = (int64_t)n * n * n;
+  const int64_t N0 = (int64_t)n * n * n * B;
   auto one = [&]() -> pm_status {
     PM_TRY(prm.cycle == 1 ? fr_f(f, 0) : fr_v(f, 0));
     if (f.e[0] != eps) {   // the iterate ended in the ping-pong partner: bring it home
@@ -581,7 +613,7 @@ pm_status fr_solve_src(Src b, float* eps, int n, const fr_params& prm, mg_stats*
     }
     return PM_OK;
   };
-  if (prm.tol <= 0.0) {
+  if (prm.tol <= 0.0 || B > 1) {
     for (int c = 0; c < prm.cycles; ++c) PM_TRY(one());
     local.cycles = prm.cycles;
     if (st) *st = local;

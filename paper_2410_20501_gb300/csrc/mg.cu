@@ -532,10 +532,10 @@ pm_status v_cycle(MG& g, int l, bool zero_guess) {
 }  // namespace
 
 pm_status prolong_correct_launch(float* u, const float* uc, const float* uc2, int n_fine, int cls,
-                                 cudaStream_t s) {
+                                 cudaStream_t s, int B) {
   const int64_t N = (int64_t)n_fine * n_fine * n_fine;
-  PM_LAUNCH(cls, 8.0 * N + (uc2 ? 1.0 : 0.5) * N, k_prolong_correct, grid_for(N / 16, 256), 256, 0, s, u, uc, uc2,
-            ilog2(n_fine));
+  PM_LAUNCH(cls, (8.0 * N + (uc2 ? 1.0 : 0.5) * N) * B, k_prolong_correct, dim3(grid_for(N / 16, 256), 1, (unsigned)B),
+            256, 0, s, u, uc, uc2, ilog2(n_fine));
   return PM_OK;
 }
 

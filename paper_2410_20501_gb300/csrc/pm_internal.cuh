@@ -206,11 +206,14 @@ pm_status mg_solve_src(Src f, float* phi, int n, const mg_params& prm, mg_stats*
 // MG_GUESS_SCALED takes the per-box factors gbox [B] (device).
 pm_status mg_solve_batch_src(Src f, float* phi, int n, int B, const mg_params& prm, const float* gbox,
                          Workspace& w, cudaStream_t s);
+// B > 1: B boxes back to back ([B][n^3]; per-box source scale and mean as in
+// Src), prm.cycles fixed cycles each, st unused.
 pm_status fr_solve_src(Src b, float* eps, int n, const fr_params& prm, mg_stats* st,
-                       Workspace& w, cudaStream_t s);
-// u_fine += P(uc - uc2) (27/9/3/1 prolongation; uc2 may be NULL).
+                       Workspace& w, cudaStream_t s, int B = 1);
+// u_fine += P(uc - uc2) (27/9/3/1 prolongation; uc2 may be NULL), on B
+// boxes back to back.
 pm_status prolong_correct_launch(float* u, const float* uc, const float* uc2, int n_fine, int cls,
-                                 cudaStream_t s);
+                                 cudaStream_t s, int B = 1);
 // Background constants of the f(R) equation (host, float64).
 void fr_background(const fr_params& p, double* fbar, double* kappa, double* c2);
 

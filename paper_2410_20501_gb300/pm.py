@@ -142,6 +142,9 @@ _SIGS = {
                                         ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
     "mg_solve_batch": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
                                       ctypes.POINTER(mg_params), ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
+    "pm_fr_batch_workspace_size": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)]),
+    "fr_solve_batch": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
+                                      ctypes.POINTER(fr_params), ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
     "pm_gradient_batch": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                          ctypes.c_void_p]),
     "pm_interp_batch": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_int,
@@ -601,6 +604,23 @@ def mg_solve_batch(f, phi=None, ws=None, **params):
     _check(lib().mg_solve_batch(_p(f, torch.float32), _p(phi, torch.float32), n, B, ctypes.byref(prm), _p(ws),
                                 ws.numel(), _stream()), "mg_solve_batch")
     return phi
+
+
+def fr_batch_workspace(n, B, device="cuda"):
+    size = ctypes.c_size_t()
+    _check(lib().pm_fr_batch_workspace_size(n, B, ctypes.byref(size)), "pm_fr_batch_workspace_size")
+    return torch.empty(size.value, dtype=torch.uint8, device=device)
+
+
+def fr_solve_batch(rho, eps=None, ws=None, **params):
+    """fr_solve_batch: fixed FAS cycles on B boxes, rho [B, n, n, n] (shared parameters); returns eps."""
+    B, n = rho.shape[0], rho.shape[1]
+    prm = default_fr(**params)
+    eps = eps if eps is not None else torch.zeros_like(rho)
+    ws = ws if ws is not None else fr_batch_workspace(n, B, rho.device)
+    _check(lib().fr_solve_batch(_p(rho, torch.float32), _p(eps, torch.float32), n, B, ctypes.byref(prm), _p(ws),
+                                ws.numel(), _stream()), "fr_solve_batch")
+    return eps
 
 
 def gradient_batch(phi, order=5):

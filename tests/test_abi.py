@@ -129,6 +129,30 @@ def test_batch_arguments_are_checked(L):
     assert L.pm_step_batch(ctypes.byref(st), ctypes.byref(prm), None) == 2      # workspace too small
 
 
+def test_fr_batch_arguments_are_checked(L):
+    """fr_solve_batch: sizes, cycle count and workspace are checked on the host;
+    its workspace holds B boxes' levels (more than one box's, less than B
+    single-box workspaces plus nothing)."""
+    from paper_2410_20501_gb300 import pm
+    ok = ctypes.c_void_p(0x100000)
+    one, four = ctypes.c_size_t(), ctypes.c_size_t()
+    assert L.pm_fr_batch_workspace_size(64, 1, ctypes.byref(one)) == 0
+    assert L.pm_fr_batch_workspace_size(64, 4, ctypes.byref(four)) == 0
+    single = pm.workspace_size(64, 0, pm.PM_WS_FR)
+    assert one.value == single and single < four.value <= 4 * single
+    assert L.pm_fr_batch_workspace_size(16, 4, ctypes.byref(one)) == 1           # n < 32
+    assert L.pm_fr_batch_workspace_size(64, 0, ctypes.byref(one)) == 1           # no boxes
+    fr = pm.default_fr(cycles=1, tol=0.0)
+    assert L.fr_solve_batch(ok, ok, 48, 2, ctypes.byref(fr), ok, 1 << 30, None) == 1   # n not a power of two
+    assert L.fr_solve_batch(ok, ok, 64, 0, ctypes.byref(fr), ok, 1 << 30, None) == 1   # B < 1
+    assert L.fr_solve_batch(ok, ok, 64, 2, ctypes.byref(fr), ok, 16, None) == 2        # workspace too small
+    assert L.fr_solve_batch(ok, ctypes.c_void_p(0x100004), 64, 2, ctypes.byref(fr), ok, 1 << 30, None) == 1
+    fr.cycles = 0
+    assert L.fr_solve_batch(ok, ok, 64, 2, ctypes.byref(fr), ok, 1 << 30, None) == 1   # fixed cycles required
+    fr = pm.default_fr(cycles=1, fR0=1e-5)
+    assert L.fr_solve_batch(ok, ok, 64, 2, ctypes.byref(fr), ok, 1 << 30, None) == 1   # f_R0 >= 0
+
+
 
 def test_adaptive_timestep_criteria(L):
     """The §3.4 time-step rule on the host (EdS: t~(a) = -2 a^(-1/2), so the
