@@ -334,6 +334,16 @@ def oracle_errors(probes):
             out[name] = {"rel_l2_acc": errs, "boxes": p["boxes"],
                          "what": "accelerations of a warm batched step (2 V-cycles) against the exact-Poisson "
                                  "oracle at the same positions"}
+        elif p["kind"] == "refine":
+            from oracle import poisson
+            exact = poisson.solve_fft7(p["f"].astype(np.float64), 1.0 / p["n"])
+
+            def err(x):
+                x = x.astype(np.float64)
+                return float(np.linalg.norm((x - x.mean()) - exact) / np.linalg.norm(exact))
+            out[name] = {"plain_rel_l2": err(p["phi32"]), "refined_rel_l2": err(p["phi64"]),
+                         "what": f"potential of the {p['n']}^3 Poisson solve, float32 multigrid and float64 "
+                                 "iterative refinement, against the exact 7-point inverse (FFT_7pt)"}
     return out
 
 
@@ -516,6 +526,43 @@ def run_adjoint(n=128, fd_dirs=16, reps=3, eps=1.0):
              "fd_check": {"directions": fd_dirs, "eps": eps,
                           "median_rel_err": statistics.median(errs) if errs else None,
                           "max_rel_err": max(errs) if errs else None}}, probe)
+
+
+def run_refine(n=256, outer=4, cycles=3, reps=3):
+    """The precision forms of the Poisson solve on a seeded 256^3 random source:
+    mg_solve to its float32 floor (tol 1e-7) against mg_solve_refine (float64
+    residuals of a float64 iterate, ``outer`` steps of ``cycles`` float32
+    V-cycles).  CUDA-event times on the launching stream, median of ``reps``;
+    both include their host synchronisations (one per cycle, one per step)."""
+    import torch
+    from paper_2410_20501_gb300 import inputs, pm
+    f = torch.from_numpy(inputs.random_field(n, 36).astype(np.float32)).cuda()
+    ws32 = pm.workspace(n, 0, pm.PM_WS_MG)
+    ws64 = pm.workspace(n, 0, pm.PM_WS_MG | pm.PM_WS_REFINE)
+
+    def timed(fn):
+        times, out = [], None
+        for _ in range(reps):
+            t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            t0.record()
+            out = fn()
+            t1.record()
+            torch.cuda.synchronize()
+            times.append(t0.elapsed_time(t1))
+        return out, float(np.median(times))
+
+    (phi32, st32), ms32 = timed(lambda: pm.mg_solve(f, ws=ws32, tol=1e-7, max_cycles=40))
+    (phi64, st64), ms64 = timed(lambda: pm.mg_solve_refine(f, ws=ws64, outer=outer, fixed_cycles=cycles))
+    line = {"n": n,
+            "plain": {"ms": ms32, "cycles": st32["cycles"], "rel_res": st32["res"] / st32["norm_f"],
+                      "what": "mg_solve, float32 iterate, to tol 1e-7"},
+            "refined": {"ms": ms64, "outer": outer, "cycles": st64["cycles"],
+                        "rel_res": st64["res"] / st64["norm_f"],
+                        "what": f"mg_solve_refine, float64 iterate, {outer} steps of {cycles} V-cycles"}}
+    probe = {"kind": "refine", "n": n, "f": f.cpu().numpy(), "phi32": phi32.cpu().numpy(),
+             "phi64": phi64.cpu().numpy()}
+    return line, probe
 
 
 def run_ensemble(n=64, B=64, steps=50):
@@ -755,6 +802,7 @@ def run_gpu(args):
     if world == 1 and not args.lean:
         line["adjoint"], probes["adjoint"] = run_adjoint()
         line["ensemble"], probes["ensemble"] = run_ensemble()
+        line["poisson_precision"], probes["poisson_precision"] = run_refine()
     if world == 1 and not args.no_cpu_baseline and not args.lean:
         line["cpu_baseline"] = cpu_baseline()
         line["oracle_error"] = oracle_errors(probes)

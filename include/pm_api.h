@@ -79,7 +79,9 @@ enum {
   PM_WS_ADJ = 32,      /* adjoint entry points (with PM_WS_SORT or PM_WS_STEP) */
   PM_WS_FFT = 64,      /* FFT Poisson solver (pm_poisson_fft, pm_step with
                           poisson != PM_POISSON_MG): the half spectrum          */
-  PM_WS_LPT = 128      /* pm_lpt2: two half spectra and five grids             */
+  PM_WS_LPT = 128,     /* pm_lpt2: two half spectra and five grids             */
+  PM_WS_REFINE = 256   /* mg_solve_refine (with PM_WS_MG): residual and
+                          correction grids                                      */
 };
 
 /* Bytes of workspace needed for grids of n^3 cells and np particles.
@@ -190,6 +192,30 @@ void mg_default_params(mg_params* p);
  *   st   host mg_stats (may be NULL) */
 pm_status mg_solve(const float* f, float* phi, int n, const mg_params* prm,
                    mg_stats* st, void* ws, size_t ws_bytes, void* stream);
+
+/* The same Poisson problem by mixed-precision iterative refinement: float32
+ * multigrid inside, float64 only for the outer residual, the iterate's update
+ * and the global reductions.  Each of `outer` steps forms, in float64,
+ *   r = (f - <f>) - (L(phi) - 6 phi)/h^2
+ * of the float64 iterate (the six differences phi_nb - phi summed in float64),
+ * solves (L(e) - 6e)/h^2 = r - <r> in float32 from e = 0 with prm's cycles
+ * (fixed_cycles, or tol relative to ||r||), and adds e to phi in float64.  The
+ * float32 solve of mg_solve stops at the float32 resolution of its stored
+ * iterate; this one keeps converging to the float64 level (measured against
+ * the exact inverse in the tests).
+ *   f      [n^3] float32 right-hand side (read; its float64 mean is removed)
+ *   phi    [n^3] float64 in: guess (zeros: none), out: solution; 16-byte aligned
+ *   outer  refinement steps (>= 1)
+ *   prm    multigrid parameters of each correction solve (first_guess is
+ *          ignored: the correction starts from 0; MG_GUESS_SCALED is rejected)
+ *   st     host mg_stats (may be NULL): res0 / res = float64 residual norms
+ *          before the first and after the last step, norm_f = ||f - <f>||,
+ *          cycles = V-cycles of all correction solves
+ * Workspace: pm_workspace_size(n, 0, PM_WS_MG | PM_WS_REFINE).  Synchronises
+ * with the host once per step (the residual norm).  Errors: PM_EINVAL,
+ * PM_ENOMEM (ws too small), PM_ENAN (a residual not finite). */
+pm_status mg_solve_refine(const float* f, double* phi, int n, int outer, const mg_params* prm, mg_stats* st,
+                          void* ws, size_t ws_bytes, void* stream);
 
 /* Poisson solve by 3-D FFT (§3.7): phi = scale * G * (rho - <rho>), with the
  * Green's function of kind PM_POISSON_FFT7 (FFT_7pt: 1 / the Fourier symbol

@@ -82,7 +82,7 @@ size_t layout_workspace(Workspace* w, void* base, int n, int64_t np, uint32_t fl
   memset(w, 0, sizeof(*w));
   const bool step = flags & PM_WS_STEP;
   const bool sort = step || (flags & PM_WS_SORT);
-  const bool mg = step || (flags & PM_WS_MG);
+  const bool mg = step || (flags & (PM_WS_MG | PM_WS_REFINE));
   const bool fr = (step && batch == 1) || (flags & PM_WS_FR);   // batched steps are Newtonian
   const int64_t N = (int64_t)n * n * n * batch;                  // cells of all boxes
   size_t off = 0;
@@ -123,6 +123,10 @@ size_t layout_workspace(Workspace* w, void* base, int n, int64_t np, uint32_t fl
     w->lpt_a = (float2*)take((size_t)n * n * (n / 2 + 1) * 8);
     w->lpt_b = (float2*)take((size_t)n * n * (n / 2 + 1) * 8);
     w->lpt_r = (float*)take((size_t)N * 4 * 5);
+  }
+  if (flags & PM_WS_REFINE) {
+    w->ref_r = (float*)take((size_t)N * 4);
+    w->ref_e = (float*)take((size_t)N * 4);
   }
   w->partials = (double*)take((size_t)2 * reduce_partials_capacity(n, np) * 8 * batch);
   w->scalars = (double*)take(64 * 8);
@@ -355,6 +359,17 @@ pm_status mg_solve(const float* f, float* phi, int n, const mg_params* prm, mg_s
   cudaStream_t s = as_stream(stream);
   PM_TRY(grid_mean(f, (int64_t)n * n * n, w.partials, w.scalars + 1, s));
   return mg_solve_src(Src{f, 1.0f, w.scalars + 1}, phi, n, *prm, st, w, s);
+}
+
+pm_status mg_solve_refine(const float* f, double* phi, int n, int outer, const mg_params* prm, mg_stats* st,
+                          void* ws, size_t ws_bytes, void* stream) {
+  if (!valid_n(n) || !f || !phi || outer < 1 || !valid_mg(prm) || !all_a16(f, phi)) return PM_EINVAL;
+  if (prm->first_guess == MG_GUESS_SCALED) return PM_EINVAL;   // phi is float64: nothing to rescale here
+  Workspace w;
+  PM_TRY(check_ws(w, ws, ws_bytes, n, 0, PM_WS_MG | PM_WS_REFINE));
+  cudaStream_t s = as_stream(stream);
+  PM_TRY(grid_mean(f, (int64_t)n * n * n, w.partials, w.scalars + 1, s));
+  return mg_solve_refine_src(f, w.scalars + 1, phi, n, outer, *prm, st, w, s);
 }
 
 pm_status fr_solve(const float* rho, float* eps, int n, const fr_params* prm, mg_stats* st, void* ws,

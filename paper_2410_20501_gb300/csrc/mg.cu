@@ -203,6 +203,55 @@ __global__ void __launch_bounds__(256) k_resid_norm(const float* __restrict__ u,
   block_sum_to(partial + gridDim.x + blockIdx.x, sf, cf, scratch);
 }
 
+// Block sum of per-thread float64 values, written by thread 0 to *out (a
+// fixed order: shuffles, then the warps in order).
+__device__ __forceinline__ void block_sum_f64(double* out, double v, double* scratch32) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) scratch32[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += scratch32[i];
+    *out = t;
+  }
+  __syncthreads();
+}
+
+// Residual of a float64 iterate in float64: r = (f - <f>) - (L(u) - 6u)/h^2,
+// summed as the six differences u_nb - u.  r is stored rounded to float32 (the
+// source of the correction solve); the squares of r and of f - <f> are summed
+// per block in float64.
+__global__ void __launch_bounds__(256) k_resid_f64(const double* __restrict__ u, const float* __restrict__ f,
+                                                   const double* __restrict__ fmean, int log2n, double inv_h2,
+                                                   float* __restrict__ r, double* __restrict__ partial) {
+  __shared__ double scratch[32];
+  const double mean = *fmean;
+  const int m = (1 << log2n) - 1;
+  const int64_t total = (int64_t)1 << (3 * log2n);
+  double sr = 0.0, sf = 0.0;
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < total; c += (int64_t)gridDim.x * blockDim.x) {
+    const int k = (int)(c & m), j = (int)((c >> log2n) & m), i = (int)(c >> (2 * log2n));
+    const double uc = u[c];
+    const double L = ((u[idx3((i + 1) & m, j, k, log2n)] - uc) + (u[idx3((i - 1) & m, j, k, log2n)] - uc)) +
+                     ((u[idx3(i, (j + 1) & m, k, log2n)] - uc) + (u[idx3(i, (j - 1) & m, k, log2n)] - uc)) +
+                     ((u[idx3(i, j, (k + 1) & m, log2n)] - uc) + (u[idx3(i, j, (k - 1) & m, log2n)] - uc));
+    const double fv = (double)__ldg(f + c) - mean;
+    const double d = fv - inv_h2 * L;
+    r[c] = (float)d;
+    sr = fma(d, d, sr);
+    sf = fma(fv, fv, sf);
+  }
+  block_sum_f64(partial + blockIdx.x, sr, scratch);
+  block_sum_f64(partial + gridDim.x + blockIdx.x, sf, scratch);
+}
+
+// u += e (float64 iterate, float32 correction).
+__global__ void k_add_correction_f64(double* __restrict__ u, const float* __restrict__ e, int64_t count) {
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < count; c += (int64_t)gridDim.x * blockDim.x)
+    u[c] += (double)__ldg(e + c);
+}
+
 // u += P(uc - uc2): cell-centred trilinear prolongation, weights 27/9/3/1 over
 // 64 (§3.6.1); uc2 may be NULL.  One thread per two coarse cells along z
 // (K = 2G, 2G + 1): it reads their 3x3x4 coarse neighbourhood once (a float2
@@ -644,6 +693,49 @@ pm_status mg_solve_src(Src f, float* phi, int n, const mg_params& prm, mg_stats*
     // float32 floor of the stored iterate (residual below 1e-3 of the source)
     if (prev > 0.0 && prm.stall > 0.0 && res > prm.stall * prev && res <= 1e-3 * nf) { status = PM_OK; break; }
     prev = res;
+  }
+  local.status = status;
+  if (st) *st = local;
+  PM_TRY(launch_status());
+  return status;
+}
+
+pm_status mg_solve_refine_src(const float* f, const double* fmean, double* phi, int n, int outer,
+                              const mg_params& prm, mg_stats* st, Workspace& w, cudaStream_t s) {
+  const int64_t N = (int64_t)n * n * n;
+  const int log2n = ilog2(n);
+  const unsigned nb = grid_for(N, 256, 152 * 8);
+  const double inv_h2 = (double)n * (double)n;
+  mg_params cp = prm;
+  cp.first_guess = MG_GUESS_INPUT;   // the correction starts from zero
+  mg_stats local{PM_OK, 0, -1.0, -1.0, -1.0};
+  // float64 residual of the current iterate into w.ref_r; its norm and ||f - <f>||
+  auto residual = [&](double* res, double* nf) -> pm_status {
+    PM_LAUNCH(K_MG_NORM, 20.0 * N, k_resid_f64, nb, 256, 0, s, phi, f, fmean, log2n, inv_h2, w.ref_r, w.partials);
+    PM_TRY(reduce_partials(w.partials, nb, nb, 2, 1.0, w.scalars + 20, s));
+    double h[2];
+    PM_TRY(fetch_scalars(w.scalars + 20, h, 2, s));
+    *res = sqrt(h[0]);
+    *nf = sqrt(h[1]);
+    return PM_OK;
+  };
+  pm_status status = PM_OK;
+  for (int it = 0; it <= outer; ++it) {
+    double res, nf;
+    PM_TRY(residual(&res, &nf));
+    if (it == 0) local.res0 = res;
+    local.res = res;
+    local.norm_f = nf;
+    if (!isfinite(res)) { status = PM_ENAN; break; }
+    if (it == outer || res == 0.0) break;
+    // correction: (L(e) - 6e)/h^2 = r - <r>, float32 multigrid from e = 0
+    PM_TRY(grid_mean(w.ref_r, N, w.partials, w.scalars + 22, s));
+    PM_TRY(cuda_status(cudaMemsetAsync(w.ref_e, 0, N * sizeof(float), s)));
+    mg_stats cst;
+    const pm_status r = mg_solve_src(Src{w.ref_r, 1.0f, w.scalars + 22, nullptr}, w.ref_e, n, cp, &cst, w, s);
+    if (r != PM_OK && r != PM_ENOCONV) return r;
+    local.cycles += cst.cycles;
+    PM_LAUNCH(K_MISC, 12.0 * N, k_add_correction_f64, grid_for(N, 256), 256, 0, s, phi, w.ref_e, N);
   }
   local.status = status;
   if (st) *st = local;

@@ -139,6 +139,7 @@ struct Workspace {
   double* box_mean;   // per-box mean density of a batch
   float2* spec;       // half spectrum n^2 (n/2 + 1) of the FFT Poisson path
   float2* lpt_a; float2* lpt_b; float* lpt_r;   // LPT: two half spectra, five real grids
+  float* ref_r; float* ref_e;                   // refinement: float32 residual and correction
   int64_t np; int n; int batch;
 };
 
@@ -202,6 +203,12 @@ pm_status grid_mean(const float* f, int64_t count, double* partials, double* mea
 
 pm_status mg_solve_src(Src f, float* phi, int n, const mg_params& prm, mg_stats* st,
                        Workspace& w, cudaStream_t s);
+// Mixed-precision iterative refinement: `outer` steps of float64 residual of
+// the float64 iterate phi, float32 multigrid correction (prm), float64 update;
+// st->res0 / st->res: float64 residual norms before the first and after the
+// last step.  Needs the PM_WS_MG | PM_WS_REFINE workspace; fmean: <f> (device).
+pm_status mg_solve_refine_src(const float* f, const double* fmean, double* phi, int n, int outer,
+                              const mg_params& prm, mg_stats* st, Workspace& w, cudaStream_t s);
 // Batched multigrid: fixed cycles only (prm.fixed_cycles > 0); the warm start
 // MG_GUESS_SCALED takes the per-box factors gbox [B] (device).
 pm_status mg_solve_batch_src(Src f, float* phi, int n, int B, const mg_params& prm, const float* gbox,

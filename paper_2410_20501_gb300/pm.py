@@ -19,6 +19,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_lib", "libpmgb.so")
 
 PM_WS_SORT, PM_WS_MG, PM_WS_FR, PM_WS_STEP, PM_WS_IDS, PM_WS_ADJ, PM_WS_FFT, PM_WS_LPT = 1, 2, 4, 8, 16, 32, 64, 128
+PM_WS_REFINE = 256
 PM_POISSON_MG, PM_POISSON_FFT7, PM_POISSON_FFT = 0, 1, 2
 MG_GUESS_INPUT, MG_GUESS_JACOBI, MG_GUESS_SCALED = 0, 1, 2
 PM_GRAVITY_NEWTON, PM_GRAVITY_FR, PM_GRAVITY_PARAM = 0, 1, 2
@@ -109,6 +110,9 @@ _SIGS = {
     "mg_default_params": (None, [ctypes.POINTER(mg_params)]),
     "mg_solve": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(mg_params),
                                 ctypes.POINTER(mg_stats), ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
+    "mg_solve_refine": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
+                                       ctypes.POINTER(mg_params), ctypes.POINTER(mg_stats), ctypes.c_void_p,
+                                       ctypes.c_size_t, ctypes.c_void_p]),
     "fr_default_params": (None, [ctypes.POINTER(fr_params)]),
     "fr_solve": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(fr_params),
                                 ctypes.POINTER(mg_stats), ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
@@ -275,6 +279,19 @@ def mg_solve(f, phi=None, ws=None, **params):
                           _p(ws), ws.numel(), _stream())
     if code not in (0, 3):
         _check(code, "mg_solve")
+    return phi, st.as_dict()
+
+
+def mg_solve_refine(f, phi=None, outer=3, ws=None, **params):
+    """Poisson solve by iterative refinement: float64 phi (float32 multigrid
+    corrections on float64 residuals); returns (phi, stats dict)."""
+    n = f.shape[0]
+    prm = default_mg(**params)
+    phi = phi if phi is not None else torch.zeros(f.shape, dtype=torch.float64, device=f.device)
+    ws = ws if ws is not None else workspace(n, 0, PM_WS_MG | PM_WS_REFINE, f.device)
+    st = mg_stats()
+    _check(lib().mg_solve_refine(_p(f, torch.float32), _p(phi, torch.float64), n, outer, ctypes.byref(prm),
+                                 ctypes.byref(st), _p(ws), ws.numel(), _stream()), "mg_solve_refine")
     return phi, st.as_dict()
 
 

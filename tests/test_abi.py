@@ -129,6 +129,27 @@ def test_batch_arguments_are_checked(L):
     assert L.pm_step_batch(ctypes.byref(st), ctypes.byref(prm), None) == 2      # workspace too small
 
 
+def test_refine_arguments_are_checked(L):
+    """mg_solve_refine: its workspace adds exactly two float32 grids to the
+    multigrid one; bad sizes, no refinement steps, a scaled first guess, a
+    misaligned float64 iterate and a short workspace are rejected on the host."""
+    from paper_2410_20501_gb300 import pm
+    n = 64
+    assert (pm.workspace_size(n, 0, pm.PM_WS_MG | pm.PM_WS_REFINE) - pm.workspace_size(n, 0, pm.PM_WS_MG)
+            == 2 * 4 * n ** 3)
+    ok = ctypes.c_void_p(0x100000)
+    prm = pm.default_mg(fixed_cycles=2)
+    st = pm.mg_stats()
+    big = 1 << 30
+    assert L.mg_solve_refine(ok, ok, 48, 2, ctypes.byref(prm), ctypes.byref(st), ok, big, None) == 1   # n
+    assert L.mg_solve_refine(ok, ok, n, 0, ctypes.byref(prm), ctypes.byref(st), ok, big, None) == 1    # outer < 1
+    assert L.mg_solve_refine(ok, ctypes.c_void_p(0x100008), n, 2, ctypes.byref(prm), ctypes.byref(st), ok, big,
+                             None) == 1                                                                 # phi alignment
+    assert L.mg_solve_refine(ok, ok, n, 2, ctypes.byref(prm), ctypes.byref(st), ok, 16, None) == 2     # workspace
+    scaled = pm.default_mg(first_guess=pm.MG_GUESS_SCALED)
+    assert L.mg_solve_refine(ok, ok, n, 2, ctypes.byref(scaled), ctypes.byref(st), ok, big, None) == 1
+
+
 def test_fr_batch_arguments_are_checked(L):
     """fr_solve_batch: sizes, cycle count and workspace are checked on the host;
     its workspace holds B boxes' levels (more than one box's, less than B
