@@ -33,6 +33,8 @@
  *    nothing is enqueued.  Entry points that test convergence (mg_solve,
  *    fr_solve, pm_step with tolerances) synchronise `stream` once per cycle to
  *    read an 8-byte residual norm; with fixed cycle counts they never sync.
+ *    mg_solve_refine synchronises once per refinement step (its float64
+ *    residual norm).
  *  - Results are deterministic: no floating-point atomics are used anywhere,
  *    every reduction has a fixed order, so reruns are bitwise identical.
  *  - Not thread-safe: calls must come from one host thread at a time.  The
