@@ -850,10 +850,13 @@ def run_stage(args):
         rng = np.random.Generator(np.random.PCG64(61))
         X = pm.positions_to_device(inputs.to_fixed_point(inputs.lattice(n) + rng.uniform(-0.45, 0.45, (3, n ** 3)) / n))
     rho = None
-    if args.stage in ("mg", "fr", "fft"):
+    if args.stage in ("mg", "refine", "fr", "fft"):
         g = inputs.random_field(n, 62)
         r = np.exp(0.7 * g)
         rho = torch.from_numpy((r / r.mean()).astype(np.float32)).cuda()
+    elif args.stage == "fr_batch":   # eight boxes of n^3, different seeds
+        r = np.exp(0.7 * np.stack([inputs.random_field(n, 62 + b) for b in range(8)]))
+        rho = torch.from_numpy((r / r.mean(axis=(1, 2, 3), keepdims=True)).astype(np.float32)).cuda()
     ws = None
 
     def once():
@@ -867,6 +870,13 @@ def run_stage(args):
         elif args.stage == "mg":
             ws = ws if ws is not None else pm.workspace(n, 0, pm.PM_WS_MG)
             pm.mg_solve(rho * 0.45, ws=ws, fixed_cycles=1, first_guess=pm.MG_GUESS_JACOBI, smoother=args.smoother)
+        elif args.stage == "refine":
+            ws = ws if ws is not None else pm.workspace(n, 0, pm.PM_WS_MG | pm.PM_WS_REFINE)
+            pm.mg_solve_refine(rho * 0.45, ws=ws, outer=2, fixed_cycles=2)
+        elif args.stage == "fr_batch":
+            ws = ws if ws is not None else pm.fr_batch_workspace(n, rho.shape[0])
+            pm.fr_solve_batch(rho, ws=ws, a=0.6, Om=OM, OL=OL, fR0=FR0, boxsize=float(n), cycles=1, tol=0.0,
+                              smoother=args.smoother)
         elif args.stage == "fr":
             ws = ws if ws is not None else pm.workspace(n, 0, pm.PM_WS_FR)
             pm.fr_solve(rho, ws=ws, a=0.6, Om=OM, OL=OL, fR0=FR0, boxsize=float(n), cycles=1,
@@ -901,8 +911,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--lean", action="store_true",
                     help="f(R) device-timed steps only (no Newtonian line, e2e or CPU baseline): for profilers")
-    ap.add_argument("--stage", choices=["sort", "deposit", "mg", "fr", "fft", "interp", "adjoint", "ensemble", "lpt",
-                                        "step"],
+    ap.add_argument("--stage", choices=["sort", "deposit", "mg", "refine", "fr", "fr_batch", "fft", "interp",
+                                        "adjoint", "ensemble", "lpt", "step"],
                     help="time one stage alone on synthetic inputs (for profilers)")
     ap.add_argument("--n", type=int, default=256, help="grid size for --stage")
     ap.add_argument("--smoother", type=int, default=2,
