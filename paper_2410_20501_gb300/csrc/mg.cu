@@ -219,9 +219,11 @@ __device__ __forceinline__ void block_sum_f64(double* out, double v, double* scr
 }
 
 // Residual of a float64 iterate in float64: r = (f - <f>) - (L(u) - 6u)/h^2,
-// summed as the six differences u_nb - u.  r is stored rounded to float32 (the
-// source of the correction solve); the squares of r and of f - <f> are summed
-// per block in float64.
+// with L(u) - 6u as the neighbour sum minus 6u (the float64 pipe bounds this
+// kernel on GB300, so it spends 12 float64 operations per cell; the six
+// differences u_nb - u would take five more).  r is stored rounded to float32
+// (the source of the correction solve); the squares of r and of f - <f> are
+// summed per block in float64.
 __global__ void __launch_bounds__(256) k_resid_f64(const double* __restrict__ u, const float* __restrict__ f,
                                                    const double* __restrict__ fmean, int log2n, double inv_h2,
                                                    float* __restrict__ r, double* __restrict__ partial) {
@@ -233,11 +235,12 @@ __global__ void __launch_bounds__(256) k_resid_f64(const double* __restrict__ u,
   for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < total; c += (int64_t)gridDim.x * blockDim.x) {
     const int k = (int)(c & m), j = (int)((c >> log2n) & m), i = (int)(c >> (2 * log2n));
     const double uc = u[c];
-    const double L = ((u[idx3((i + 1) & m, j, k, log2n)] - uc) + (u[idx3((i - 1) & m, j, k, log2n)] - uc)) +
-                     ((u[idx3(i, (j + 1) & m, k, log2n)] - uc) + (u[idx3(i, (j - 1) & m, k, log2n)] - uc)) +
-                     ((u[idx3(i, j, (k + 1) & m, log2n)] - uc) + (u[idx3(i, j, (k - 1) & m, log2n)] - uc));
+    const double nsum = ((u[idx3((i + 1) & m, j, k, log2n)] + u[idx3((i - 1) & m, j, k, log2n)]) +
+                         (u[idx3(i, (j + 1) & m, k, log2n)] + u[idx3(i, (j - 1) & m, k, log2n)])) +
+                        (u[idx3(i, j, (k + 1) & m, log2n)] + u[idx3(i, j, (k - 1) & m, log2n)]);
+    const double L = fma(-6.0, uc, nsum);
     const double fv = (double)__ldg(f + c) - mean;
-    const double d = fv - inv_h2 * L;
+    const double d = fma(-inv_h2, L, fv);
     r[c] = (float)d;
     sr = fma(d, d, sr);
     sf = fma(fv, fv, sf);
@@ -735,7 +738,7 @@ pm_status mg_solve_refine_src(const float* f, const double* fmean, double* phi, 
     const pm_status r = mg_solve_src(Src{w.ref_r, 1.0f, w.scalars + 22, nullptr}, w.ref_e, n, cp, &cst, w, s);
     if (r != PM_OK && r != PM_ENOCONV) return r;
     local.cycles += cst.cycles;
-    PM_LAUNCH(K_MISC, 12.0 * N, k_add_correction_f64, grid_for(N, 256), 256, 0, s, phi, w.ref_e, N);
+    PM_LAUNCH(K_MISC, 20.0 * N, k_add_correction_f64, grid_for(N, 256), 256, 0, s, phi, w.ref_e, N);
   }
   local.status = status;
   if (st) *st = local;
