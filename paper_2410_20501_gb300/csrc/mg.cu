@@ -714,7 +714,7 @@ pm_status mg_solve_refine_src(const float* f, const double* fmean, double* phi, 
   mg_stats local{PM_OK, 0, -1.0, -1.0, -1.0};
   // float64 residual of the current iterate into w.ref_r; its norm and ||f - <f>||
   auto residual = [&](double* res, double* nf) -> pm_status {
-    PM_LAUNCH(K_MG_NORM, 20.0 * N, k_resid_f64, nb, 256, 0, s, phi, f, fmean, log2n, inv_h2, w.ref_r, w.partials);
+    PM_LAUNCH(K_MG_NORM, 16.0 * N, k_resid_f64, nb, 256, 0, s, phi, f, fmean, log2n, inv_h2, w.ref_r, w.partials);
     PM_TRY(reduce_partials(w.partials, nb, nb, 2, 1.0, w.scalars + 20, s));
     double h[2];
     PM_TRY(fetch_scalars(w.scalars + 20, h, 2, s));
