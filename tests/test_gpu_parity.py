@@ -339,7 +339,7 @@ def test_step_is_deterministic(pm):
 
 def test_c1_twenty_steps_positions_and_power(pm):
     """Configuration C1: 32^3 EdS, Zel'dovich ICs at a = 0.02, 20 KDK steps
-    uniform in a to 0.2.  Spec bars: final positions RMS <= 1e-4 cell,
+    uniform in a to 0.2.  Accuracy bars: final positions RMS <= 1e-4 cell,
     P(k) within 0.1% below half Nyquist."""
     from oracle import power
     n = 32
