@@ -338,8 +338,8 @@ def test_step_is_deterministic(pm):
 
 
 def test_c1_twenty_steps_positions_and_power(pm):
-    """Configuration C1: 32^3 EdS, Zel'dovich ICs at a = 0.02, 20 KDK steps
-    uniform in a to 0.2.  Accuracy bars: final positions RMS <= 1e-4 cell,
+    """The 32^3 Einstein-de Sitter workload: Zel'dovich ICs at a = 0.02, 20
+    KDK steps uniform in a to 0.2.  Accuracy bars: final positions RMS <= 1e-4 cell,
     P(k) within 0.1% below half Nyquist."""
     from oracle import power
     n = 32
@@ -376,8 +376,8 @@ def test_step_accelerations_parametrised_gravity(pm, mu0, poisson):
 
 
 def test_adaptive_steps_match_oracle_on_their_schedule(pm):
-    """C1 with the §3.4 adaptive time step (free fall, velocity, 2% in a;
-    Courant factor 0.8) on the FFT_7pt solver: the final positions after the
+    """The 32^3 Einstein-de Sitter workload with the §3.4 adaptive time step
+    (free fall, velocity, 2% in a; Courant factor 0.8) on the FFT_7pt solver: the final positions after the
     GPU-chosen schedule against the oracle's KDK on the same schedule."""
     n = 32
     X, V = inputs.zeldovich_powerlaw_ics(n, seed=1)
