@@ -29,3 +29,4 @@ def test_every_profile_gives_its_command():
         if f.endswith(".md"):
             txt = open(os.path.join(d, f)).read()
             assert "```" in txt and "--clock-control none" in txt, f
+
