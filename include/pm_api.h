@@ -199,7 +199,7 @@ pm_status mg_solve(const float* f, float* phi, int n, const mg_params* prm,
  * multigrid inside, float64 only for the outer residual, the iterate's update
  * and the global reductions.  Each of `outer` steps forms, in float64,
  *   r = (f - <f>) - (L(phi) - 6 phi)/h^2
- * of the float64 iterate (the six differences phi_nb - phi summed in float64),
+ * of the float64 iterate (the neighbour sum minus 6 phi, in float64),
  * solves (L(e) - 6e)/h^2 = r - <r> in float32 from e = 0 with prm's cycles
  * (fixed_cycles, or tol relative to ||r||), and adds e to phi in float64.  The
  * float32 solve of mg_solve stops at the float32 resolution of its stored
